@@ -1,0 +1,189 @@
+/*
+ * apic.h -- C ABI of libapic.so: the GB300 (sm_103a) particle-in-cell step of
+ * the APIC method (R.D. Smirnov, S.I. Krasheninnikov, "Aspherical PIC code
+ * (APIC) for modeling non-spherical dust in plasmas using shape-conforming
+ * coordinates", arXiv:2307.11107).
+ *
+ * One step advances electrons and ions around a conducting grain whose surface
+ * is x1 = -1 in the shape-conforming coordinates of Eq. 2,
+ *     x1 = -(1/r)(1 + alpha cos(theta)/r),   x2 = cos(theta),
+ * in this order (Sec. 1 and Sec. 2 of the paper):
+ *   charge weighing of every particle onto the (x1, x2) node grid, divided by
+ *   the node volume of Eq. 5;  the Poisson problem of Eqs. 6-7 with fixed
+ *   potentials on the grain (x1 = -1) and on the outer surface (x1 = x1_outer);
+ *   dphi/dx1, dphi/dx2 at the nodes, interpolated to each particle and turned
+ *   into E_R, E_Z by Eq. 10;  the equations of motion of Eq. 9 (leapfrog /
+ *   Boris, axial B);  absorption on the grain with per-surface-bin tallies of
+ *   charge, momentum, angular momentum and energy;  escape through the outer
+ *   surface;  Maxwellian injection through the outer surface weighted by the
+ *   area element of Eq. 4.
+ *
+ * Units (all arguments and results): lengths in R0, time in 1/omega_pe,
+ * velocity in lambda_De*omega_pe, potential in Te/e, density in n0, charge of
+ * a species in e, mass in m_e, B in m_e omega_pe / e, eps0 = 1.  The unperturbed
+ * density n0 is 1 for every species.
+ *
+ * Grid: n1 x n2 CELLS, nodes (i, j), i = 0..n1 at x1 = -1 + i*(x1_outer+1)/n1,
+ * j = 0..n2 at x2 = -1 + 2j/n2; node arrays are row-major [n1+1][n2+1].
+ *
+ * Ownership and threading: the library owns every device buffer, obtained
+ * through the caller's allocator (or cudaMallocAsync when none is given) on the
+ * caller's stream; all device work is ordered on that stream.  Host buffers
+ * passed in are owned by the caller and are read or written before the call
+ * returns.  A simulation object is not thread-safe; distinct objects are
+ * independent.
+ *
+ * Errors: every call returns APIC_OK (0) or a negative APIC_ERR_* code and never
+ * throws.  Errors are sticky: after one, every later call on the same object
+ * returns it again; apic_last_error() gives a message; only apic_destroy()
+ * clears the object.
+ */
+#ifndef APIC_H
+#define APIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define APIC_OK 0
+#define APIC_ERR_INVALID_ARG (-1)  /* bad sizes, NULL pointers, bad mode */
+#define APIC_ERR_GEOMETRY (-2)     /* |alpha| >= 0.245 or x1_outer not in (-1, 0) */
+#define APIC_ERR_CAPACITY (-3)     /* a species outgrew its particle capacity */
+#define APIC_ERR_NOT_CONVERGED (-4)/* Poisson iteration limit reached above tolerance */
+#define APIC_ERR_NONFINITE (-5)    /* NaN/Inf in the fields */
+#define APIC_ERR_TIMEOUT (-6)      /* reserved: bounded device wait gave up */
+#define APIC_ERR_CUDA (-7)         /* CUDA runtime or allocation failure */
+
+/* precision of the particle arrays and of the Poisson preconditioner */
+#define APIC_FP64 0          /* FP64 particles, FP64 multigrid (parity path) */
+#define APIC_FP32_REFINED 1  /* FP32 particles and FP32 multigrid inside an FP64 Krylov/residual loop */
+
+/* apic_inject modes */
+#define APIC_LOAD_VOLUME 0   /* n particles uniform in physical volume, Maxwellian at T */
+#define APIC_FLUX_SURFACE 1  /* n particles entering through the outer surface (Eq. 4 weighting) */
+#define APIC_EXPLICIT 2      /* n caller-given states (x1, x2, vR, vZ, vTheta), FP64 */
+
+/* config flags */
+#define APIC_NO_INJECT 1     /* no per-step surface injection */
+#define APIC_NO_FIELD 2      /* phi = 0: no Poisson solve, E = 0 (test and baseline use) */
+
+#define APIC_NT 7  /* tally components per (species, bin): hits, charge, p_R, p_Z, L_z, E_kin, E_kin + E_bind */
+#define APIC_NH 10 /* history fields per step: t, current, drag F_Z, electric F_Z, torque T_z,
+                      heat flux, grain charge Q, resident species 0, resident species 1, absorbed events */
+
+typedef struct {
+  double q;          /* charge in e (electron -1) */
+  double m;          /* mass in m_e */
+  double T;          /* temperature in Te */
+  int64_t n_init;    /* macro-particles that represent density n0 in the whole domain: w = V / n_init */
+  int64_t capacity;  /* particle slots reserved for this species */
+} apic_species_t;
+
+typedef struct {
+  double alpha;          /* shape parameter of Eqs. 1-5, |alpha| < 0.245 */
+  double x1_outer;       /* outer boundary x1 = const, in (-1, 0) */
+  double phi_grain;      /* potential on x1 = -1 */
+  double phi_outer;      /* potential on x1 = x1_outer */
+  double B;              /* axial field of Eq. 9 */
+  double dt;             /* time step */
+  double e_bind_ion;     /* energy deposited per absorbed particle of positive charge, besides E_kin */
+  int32_t n1, n2;        /* cells in x1 and x2: n1 >= 4, n2 >= 8 */
+  int32_t n_species;     /* 1 or 2 */
+  apic_species_t sp[2];
+  uint64_t seed;         /* Philox4x32-10 key */
+  int32_t instance;      /* Philox counter tag; distinct instances draw distinct streams */
+  int32_t precision;     /* APIC_FP64 or APIC_FP32_REFINED */
+  int32_t flags;         /* APIC_NO_INJECT | APIC_NO_FIELD */
+  double poisson_tol;    /* relative residual target ||b - A phi|| / ||b|| (0: 1e-10) */
+  int32_t poisson_max_iter; /* BiCGSTAB iterations per step (0: 20) */
+  int32_t sort_interval; /* sort particles by cell every this many steps (0: never) */
+  int32_t history_cap;   /* rows of the per-step history ring (0: 4096) */
+  int32_t reserved[5];
+} apic_config_t;
+
+typedef void* (*apic_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*apic_free_fn)(void* ptr, void* stream, void* ctx);
+typedef struct {
+  apic_alloc_fn alloc;   /* returns device memory (>= 256-byte aligned) or NULL */
+  apic_free_fn free;
+  void* ctx;
+} apic_allocator_t;
+
+typedef struct apic_sim apic_sim;  /* opaque, owned by the library */
+
+typedef struct {
+  /* caller-owned outputs; any pointer may be NULL */
+  double* bins;          /* [n_species][n2][APIC_NT] cumulative tallies of absorbed particles */
+  double* history;       /* [history_rows][APIC_NH], oldest first */
+  int64_t history_rows;  /* in: capacity of history; out: rows written */
+  int64_t counts[2][6];  /* out: loaded, injected, absorbed, escaped, resident, dropped */
+  int64_t step;          /* out: steps taken */
+  double grain_Q;        /* out: grain charge (surface integral of sigma), last field solve */
+  double grain_FZ;       /* out: electric force on the grain along Z, last field solve */
+  double poisson_res;    /* out: relative residual of the last solve */
+  int32_t poisson_iters; /* out: BiCGSTAB iterations of the last solve */
+  int32_t pad;
+} apic_tallies_t;
+
+/* Create one simulation (batch of one instance).  Sec. 2: grid, node volumes
+ * (Eq. 5), sampling tables (Eqs. 4-5) and the finite-difference operator of
+ * Eq. 7 are set up here.  stream: a cudaStream_t (NULL = legacy default).
+ * allocator: NULL for cudaMallocAsync.  *out receives the object, or NULL on
+ * error.  Errors: INVALID_ARG, GEOMETRY, CUDA. */
+int apic_create(const apic_config_t* cfg, void* stream, const apic_allocator_t* allocator,
+                apic_sim** out);
+
+/* Create n instances that advance together in every kernel launch (each with
+ * its own alpha, potentials, B, grid and particle counts).  Instance k is
+ * addressed as `instance = k` below. */
+int apic_create_batch(const apic_config_t* cfgs, int32_t n, void* stream,
+                      const apic_allocator_t* allocator, apic_sim** out);
+
+/* Release every buffer; safe on NULL. */
+int apic_destroy(apic_sim* sim);
+
+/* Add n particles of `species` to `instance` (Sec. 1: Maxwellian plasma of
+ * density n0 and temperature T).  explicit_state: host FP64 [n][5] rows
+ * (x1, x2, vR, vZ, vTheta) for APIC_EXPLICIT, else NULL.  Draws are
+ * counter-based (Philox4x32-10): the same sequence of calls gives the same
+ * particles.  Errors: INVALID_ARG, CAPACITY, CUDA. */
+int apic_inject(apic_sim* sim, int32_t instance, int32_t species, int64_t n, int32_t mode,
+                const double* explicit_state);
+
+/* Advance every instance by n_steps full steps (deposit -> Poisson -> gather ->
+ * push -> absorb -> escape -> inject).  Work is queued on the stream and the
+ * call waits for it once at the end to read the status word.  Errors:
+ * CAPACITY, NOT_CONVERGED, NONFINITE, CUDA. */
+int apic_step(apic_sim* sim, int32_t n_steps);
+
+/* Copy tallies, counts and the history of `instance` into caller buffers. */
+int apic_tallies(apic_sim* sim, int32_t instance, apic_tallies_t* out);
+
+/* Solve Eqs. 6-7 for `instance` with the GPU solver.  rho: host [n1+1][n2+1]
+ * charge density, or NULL for the density of the current particles.
+ * phi_out: host [n1+1][n2+1].  The simulation's own potential is unchanged. */
+int apic_solve_poisson(apic_sim* sim, int32_t instance, const double* rho, double* phi_out);
+
+/* Diagnostics: copy the live particles of (instance, species) as FP64 rows
+ * (x1, x2, vR, vZ, vTheta) into out [capacity][5]; slots of absorbed or escaped
+ * particles are skipped.  *n_out receives the row count (<= capacity). */
+int apic_get_particles(apic_sim* sim, int32_t instance, int32_t species, double* out,
+                       int64_t capacity, int64_t* n_out);
+
+/* Diagnostics: node field `which` of `instance` into out [n1+1][n2+1]:
+ * 0 rho (last deposit), 1 phi, 2 dphi/dx1, 3 dphi/dx2, 4 node volume. */
+int apic_get_field(apic_sim* sim, int32_t instance, int32_t which, double* out);
+
+/* Message of the last error (static storage of the object; never NULL). */
+const char* apic_last_error(const apic_sim* sim);
+
+/* Number of instances, and the library's compiled-in maxima. */
+int32_t apic_num_instances(const apic_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* APIC_H */

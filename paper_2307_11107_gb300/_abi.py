@@ -1,0 +1,85 @@
+"""ctypes mirror of include/apic.h and the loader of the in-tree libapic.so.
+
+Only argument marshalling lives here; every step of the computation runs in
+the CUDA kernels of libapic.so.  The library must have been built (see
+``build.py``); there is no fallback.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libapic.so")
+
+OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "GEOMETRY", -3: "CAPACITY", -4: "NOT_CONVERGED", -5: "NONFINITE",
+          -6: "TIMEOUT", -7: "CUDA"}
+FP64 = 0
+FP32_REFINED = 1
+LOAD_VOLUME, FLUX_SURFACE, EXPLICIT = 0, 1, 2
+NO_INJECT, NO_FIELD = 1, 2
+NT, NH = 7, 10
+
+SYMBOLS = ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
+           "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_last_error",
+           "apic_num_instances")
+
+
+class Species(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("T", C.c_double), ("n_init", C.c_int64),
+                ("capacity", C.c_int64)]
+
+
+class Config(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("x1_outer", C.c_double), ("phi_grain", C.c_double),
+                ("phi_outer", C.c_double), ("B", C.c_double), ("dt", C.c_double), ("e_bind_ion", C.c_double),
+                ("n1", C.c_int32), ("n2", C.c_int32), ("n_species", C.c_int32), ("sp", Species * 2),
+                ("seed", C.c_uint64), ("instance", C.c_int32), ("precision", C.c_int32), ("flags", C.c_int32),
+                ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32), ("sort_interval", C.c_int32),
+                ("history_cap", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class Tallies(C.Structure):
+    _fields_ = [("bins", C.POINTER(C.c_double)), ("history", C.POINTER(C.c_double)),
+                ("history_rows", C.c_int64), ("counts", (C.c_int64 * 6) * 2), ("step", C.c_int64),
+                ("grain_Q", C.c_double), ("grain_FZ", C.c_double), ("poisson_res", C.c_double),
+                ("poisson_iters", C.c_int32), ("pad", C.c_int32)]
+
+
+_lib = None
+
+
+def load():
+    """Load libapic.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libapic.so is not built: run paper_2307_11107_gb300/build.py (nvcc, sm_103a)")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
+    L.apic_create.argtypes = [C.POINTER(Config), vp, C.POINTER(Allocator), C.POINTER(vp)]
+    L.apic_create_batch.argtypes = [C.POINTER(Config), i32, vp, C.POINTER(Allocator), C.POINTER(vp)]
+    L.apic_destroy.argtypes = [vp]
+    L.apic_inject.argtypes = [vp, i32, i32, i64, i32, dp]
+    L.apic_step.argtypes = [vp, i32]
+    L.apic_tallies.argtypes = [vp, i32, C.POINTER(Tallies)]
+    L.apic_solve_poisson.argtypes = [vp, i32, dp, dp]
+    L.apic_get_particles.argtypes = [vp, i32, i32, dp, i64, C.POINTER(i64)]
+    L.apic_get_field.argtypes = [vp, i32, i32, dp]
+    L.apic_last_error.argtypes = [vp]
+    L.apic_last_error.restype = C.c_char_p
+    L.apic_num_instances.argtypes = [vp]
+    L.apic_num_instances.restype = i32
+    for name in ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
+                 "apic_solve_poisson", "apic_get_particles", "apic_get_field"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L

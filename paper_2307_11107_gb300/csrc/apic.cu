@@ -1,0 +1,975 @@
+// Host side of libapic: the C ABI of include/apic.h.  Set-up of the grid,
+// node volumes (Eq. 5), sampling tables (Eqs. 4-5), the finite-difference
+// operator of Eq. 7 and its Galerkin multigrid hierarchy; device memory; the
+// per-step launch sequence, captured once into a CUDA graph whose BiCGSTAB loop
+// is a device-controlled while-node.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "apic_internal.h"
+#include "geom.cuh"
+
+using namespace apic;
+
+namespace {
+
+// ---- quadrature (Gauss-Legendre, 10 points, by Newton on the three-term recurrence) ----
+struct GL10 {
+  double x[10], w[10];
+  GL10() {
+    const int n = 10;
+    for (int k = 0; k < n; ++k) {
+      double z = std::cos(kPi * (k + 0.75) / (n + 0.5)), dp = 1.0;
+      for (int it = 0; it < 200; ++it) {
+        double pm = 1.0, p = z;
+        for (int l = 2; l <= n; ++l) {
+          double pn = ((2 * l - 1) * z * p - (l - 1) * pm) / l;
+          pm = p;
+          p = pn;
+        }
+        dp = n * (pm - z * p) / (1.0 - z * z);
+        double step = p / dp;
+        z -= step;
+        if (std::fabs(step) < 1e-17) break;
+      }
+      x[k] = z;
+      w[k] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+  }
+};
+const GL10& gl10() {
+  static GL10 g;
+  return g;
+}
+
+int bits_for(long long v) {
+  int b = 0;
+  while (v > 0) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
+}
+
+double x1_node_h(const Inst& I, int i) { return i == I.n1 ? I.x1_out : -1.0 + i * I.h1; }
+double x2_node_h(const Inst& I, int j) { return j == I.n2 ? 1.0 : -1.0 + j * I.h2; }
+
+// Dense inverse by Gauss-Jordan with partial pivoting (small coarsest level).
+bool invert(std::vector<double>& a, int n) {
+  std::vector<double> inv((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(a[(size_t)r * n + c]) > std::fabs(a[(size_t)p * n + c])) p = r;
+    if (a[(size_t)p * n + c] == 0.0) return false;
+    if (p != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(a[(size_t)p * n + k], a[(size_t)c * n + k]);
+        std::swap(inv[(size_t)p * n + k], inv[(size_t)c * n + k]);
+      }
+    double piv = 1.0 / a[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) {
+      a[(size_t)c * n + k] *= piv;
+      inv[(size_t)c * n + k] *= piv;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = a[(size_t)r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        a[(size_t)r * n + k] -= f * a[(size_t)c * n + k];
+        inv[(size_t)r * n + k] -= f * inv[(size_t)c * n + k];
+      }
+    }
+  }
+  a.swap(inv);
+  return true;
+}
+
+// Host stencil of one level: kSt arrays of nodes.
+struct HostLevel {
+  int n1, n2, N1, N2;
+  std::vector<double> st;  // [kSt][nodes]
+  long long nodes() const { return (long long)N1 * N2; }
+  double& at(int k, int i, int j) { return st[(size_t)k * nodes() + (size_t)i * N2 + j]; }
+  double get(int k, int i, int j) const { return st[(size_t)k * nodes() + (size_t)i * N2 + j]; }
+};
+
+// Galerkin coarse operator R A P with bilinear P (zero on Dirichlet rows) and
+// R = P^T / 4; the result is a 3x3 stencil on every coarse row.
+bool galerkin(const HostLevel& F, HostLevel& C, bool fine_pole) {
+  C.n1 = F.n1 / 2;
+  C.n2 = F.n2 / 2;
+  C.N1 = C.n1 + 1;
+  C.N2 = C.n2 + 1;
+  C.st.assign((size_t)kSt * C.nodes(), 0.0);
+  auto w = [](int d) { return d == 0 ? 1.0 : 0.5; };
+  for (int I = 1; I < C.n1; ++I)
+    for (int J = 0; J <= C.n2; ++J) {
+      for (int di = -1; di <= 1; ++di) {
+        int i = 2 * I + di;
+        if (i < 1 || i > F.n1 - 1) continue;
+        for (int dj = -1; dj <= 1; ++dj) {
+          int j = 2 * J + dj;
+          if (j < 0 || j > F.n2) continue;
+          double wr = 0.25 * w(di) * w(dj);
+          // fine row (i, j): its entries (i2, j2, s)
+          struct E {
+            int i2, j2;
+            double s;
+          } ent[11];
+          int ne = 0;
+          for (int a = -1; a <= 1; ++a)
+            for (int b = -1; b <= 1; ++b) {
+              int j2 = j + b;
+              if (j2 < 0 || j2 > F.n2) continue;
+              double s = F.get(st_slot(a, b), i, j);
+              if (s != 0.0) ent[ne++] = {i + a, j2, s};
+            }
+          if (fine_pole) {
+            double s = F.get(kStPole, i, j);
+            if (s != 0.0) {
+              if (j == 0) ent[ne++] = {i, 2, s};
+              else if (j == F.n2) ent[ne++] = {i, F.n2 - 2, s};
+            }
+          }
+          for (int e = 0; e < ne; ++e) {
+            int i2 = ent[e].i2, j2 = ent[e].j2;
+            int Ia = i2 / 2, Ib = (i2 + 1) / 2, Ja = j2 / 2, Jb = (j2 + 1) / 2;
+            int Is[2] = {Ia, Ib}, Js[2] = {Ja, Jb};
+            double wi = (i2 % 2 == 0) ? 1.0 : 0.5, wj = (j2 % 2 == 0) ? 1.0 : 0.5;
+            int ni = (i2 % 2 == 0) ? 1 : 2, nj = (j2 % 2 == 0) ? 1 : 2;
+            for (int u = 0; u < ni; ++u)
+              for (int v = 0; v < nj; ++v) {
+                int I2 = Is[u], J2 = Js[v];
+                if (I2 <= 0 || I2 >= C.n1) continue;  // Dirichlet coarse rows carry no correction
+                int dI = I2 - I, dJ = J2 - J;
+                if (dI < -1 || dI > 1 || dJ < -1 || dJ > 1) return false;
+                C.at(st_slot(dI, dJ), I, J) += wr * ent[e].s * wi * wj;
+              }
+          }
+        }
+      }
+    }
+  return true;
+}
+
+}  // namespace
+
+struct apic_sim {
+  int precision = APIC_FP64;
+  int n_inst = 0, n_pop = 0;
+  std::vector<apic_config_t> cfg;
+  std::vector<Inst> inst;
+  std::vector<Pop> pop;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr, cap2 = nullptr;
+  apic_allocator_t alloc{};
+  bool have_alloc = false;
+  std::vector<void*> blocks;
+  DevPtrs d{};
+  SolvePlan plan{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool dirty = true;
+  int status = APIC_OK;
+  std::string msg = "ok";
+  long long max_inj = 0;
+  int push_grid = 0;
+  double* phi_save = nullptr;
+  int32_t* h_err = nullptr;
+
+  int fail(int code, const std::string& m) {
+    if (status == APIC_OK) {
+      status = code;
+      msg = m;
+    }
+    return status;
+  }
+  bool ck(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return true;
+    fail(APIC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return false;
+  }
+  void* dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (have_alloc) {
+      p = alloc.alloc(bytes, (void*)stream, alloc.ctx);
+      if (!p) {
+        fail(APIC_ERR_CUDA, "allocator returned NULL");
+        return nullptr;
+      }
+    } else {
+      if (!ck(cudaMallocAsync(&p, bytes, stream), "cudaMallocAsync")) return nullptr;
+    }
+    blocks.push_back(p);
+    if (!ck(cudaMemsetAsync(p, 0, bytes, stream), "cudaMemsetAsync")) return nullptr;
+    return p;
+  }
+  void dfree_all() {
+    for (void* p : blocks) {
+      if (have_alloc) alloc.free(p, (void*)stream, alloc.ctx);
+      else cudaFreeAsync(p, stream);
+    }
+    blocks.clear();
+  }
+  template <class T>
+  bool h2d(T* dst, const T* src, size_t n) {
+    return ck(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, stream), "H2D");
+  }
+  template <class T>
+  bool d2h(T* dst, const T* src, size_t n) {
+    return ck(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToHost, stream), "D2H");
+  }
+  bool sync() { return ck(cudaStreamSynchronize(stream), "stream sync"); }
+};
+
+namespace {
+
+int validate(const apic_config_t& c, std::string& why) {
+  if (c.n1 < 4 || c.n2 < 8) return why = "n1 >= 4 and n2 >= 8 cells required", APIC_ERR_INVALID_ARG;
+  if (c.n1 > 4096 || c.n2 > 2048) return why = "grid too large", APIC_ERR_INVALID_ARG;
+  if (!(std::fabs(c.alpha) < 0.245)) return why = "|alpha| must be < 0.245 (closed grain, Eqs. 2-5)", APIC_ERR_GEOMETRY;
+  if (!(c.x1_outer > -1.0 && c.x1_outer < 0.0)) return why = "x1_outer must lie in (-1, 0)", APIC_ERR_GEOMETRY;
+  if (c.n_species < 1 || c.n_species > 2) return why = "n_species must be 1 or 2", APIC_ERR_INVALID_ARG;
+  if (!(c.dt > 0.0)) return why = "dt must be > 0", APIC_ERR_INVALID_ARG;
+  for (int s = 0; s < c.n_species; ++s) {
+    const apic_species_t& p = c.sp[s];
+    if (!(p.m > 0.0) || !(p.T >= 0.0) || p.n_init <= 0 || p.capacity <= 0 || p.capacity >= (1ll << 31))
+      return why = "bad species parameters (m > 0, T >= 0, n_init > 0, 0 < capacity < 2^31)", APIC_ERR_INVALID_ARG;
+  }
+  if (c.precision != APIC_FP64 && c.precision != APIC_FP32_REFINED) return why = "bad precision", APIC_ERR_INVALID_ARG;
+  return APIC_OK;
+}
+
+// Inverse-CDF tables of x2 on [-1, 1]: volume dV/dx2 = (2 pi/3)(r_out^3 - r_g^3)
+// (Eq. 5 integrated along x1) and dA/dx2 of Eq. 4 at x1_out; also the grain area.
+void build_tables(Inst& I, std::vector<double>& tab) {
+  const GL10& g = gl10();
+  tab.assign(2 * (kTable + 1), 0.0);
+  double* cv = tab.data();
+  double* cs = tab.data() + kTable + 1;
+  double ht = 2.0 / kTable, ag = 0.0;
+  for (int k = 0; k < kTable; ++k) {
+    double lo = -1.0 + k * ht, sv = 0.0, ss = 0.0, sg = 0.0;
+    for (int q = 0; q < 10; ++q) {
+      double x2 = lo + 0.5 * (g.x[q] + 1.0) * ht, wq = 0.5 * g.w[q] * ht;
+      double ro = radius(I.alpha, I.x1_out, x2), rg = r_grain(I.alpha, x2);
+      sv += wq * (2.0 * kPi / 3.0) * (ro * ro * ro - rg * rg * rg);
+      ss += wq * area_density(I.alpha, I.x1_out, x2);
+      sg += wq * area_density(I.alpha, -1.0, x2);
+    }
+    cv[k + 1] = cv[k] + sv;
+    cs[k + 1] = cs[k] + ss;
+    ag += sg;
+  }
+  I.V_dom = cv[kTable];
+  I.A_out = cs[kTable];
+  I.A_grain = ag;
+}
+
+// Hat-weighted node volumes: V_ij = integral over the (up to four) adjacent
+// cells of the bilinear weight of node (i, j) times dOmega of Eq. 5.
+void build_volumes(const Inst& I, std::vector<double>& V) {
+  const GL10& g = gl10();
+  V.assign((size_t)I.nodes, 0.0);
+  for (int ci = 0; ci < I.n1; ++ci) {
+    double xa = x1_node_h(I, ci), xb = x1_node_h(I, ci + 1);
+    for (int cj = 0; cj < I.n2; ++cj) {
+      double ya = x2_node_h(I, cj), yb = x2_node_h(I, cj + 1);
+      double acc[4] = {0, 0, 0, 0};
+      for (int a = 0; a < 10; ++a) {
+        double f1 = 0.5 * (g.x[a] + 1.0), x1 = xa + f1 * (xb - xa);
+        for (int b = 0; b < 10; ++b) {
+          double f2 = 0.5 * (g.x[b] + 1.0), x2 = ya + f2 * (yb - ya);
+          double wq = 0.25 * g.w[a] * g.w[b] * (xb - xa) * (yb - ya) * volume_density(I.alpha, x1, x2);
+          acc[0] += wq * (1.0 - f1) * (1.0 - f2);
+          acc[1] += wq * f1 * (1.0 - f2);
+          acc[2] += wq * (1.0 - f1) * f2;
+          acc[3] += wq * f1 * f2;
+        }
+      }
+      V[(size_t)ci * I.N2 + cj] += acc[0];
+      V[(size_t)(ci + 1) * I.N2 + cj] += acc[1];
+      V[(size_t)ci * I.N2 + cj + 1] += acc[2];
+      V[(size_t)(ci + 1) * I.N2 + cj + 1] += acc[3];
+    }
+  }
+}
+
+// Finest-level operator: Eq. 7 with second-order differences, each row scaled
+// by rscale = 1/a1 = h1^2 / A; entries towards the Dirichlet rows are moved to
+// bbc (times phi_g or phi_out) and stored as zero.
+void build_fine(const Inst& I, HostLevel& L, std::vector<double>& rscale, std::vector<double>& bbc) {
+  L.n1 = I.n1;
+  L.n2 = I.n2;
+  L.N1 = I.N1;
+  L.N2 = I.N2;
+  L.st.assign((size_t)kSt * L.nodes(), 0.0);
+  rscale.assign((size_t)I.nodes, 0.0);
+  bbc.assign((size_t)I.nodes, 0.0);
+  for (int i = 1; i < I.n1; ++i)
+    for (int j = 0; j <= I.n2; ++j) {
+      LapCoef c = lap_coef(I.alpha, x1_node_h(I, i), x2_node_h(I, j));
+      double a1 = c.A / (I.h1 * I.h1);
+      double sc = 1.0 / a1;
+      double w[kSt] = {0};
+      w[st_slot(-1, 0)] += a1;
+      w[st_slot(1, 0)] += a1;
+      w[st_slot(0, 0)] += -2.0 * a1;
+      double e = c.E / (2.0 * I.h2);
+      if (j == 0) {
+        w[st_slot(0, 0)] += -3.0 * e;
+        w[st_slot(0, 1)] += 4.0 * e;
+        w[kStPole] += -1.0 * e;
+      } else if (j == I.n2) {
+        w[st_slot(0, 0)] += 3.0 * e;
+        w[st_slot(0, -1)] += -4.0 * e;
+        w[kStPole] += 1.0 * e;
+      } else {
+        double a2 = c.C / (I.h2 * I.h2), dd = c.D / (4.0 * I.h1 * I.h2);
+        w[st_slot(0, -1)] += a2 - e;
+        w[st_slot(0, 1)] += a2 + e;
+        w[st_slot(0, 0)] += -2.0 * a2;
+        w[st_slot(1, 1)] += dd;
+        w[st_slot(-1, -1)] += dd;
+        w[st_slot(1, -1)] -= dd;
+        w[st_slot(-1, 1)] -= dd;
+      }
+      size_t nd = (size_t)i * I.N2 + j;
+      rscale[nd] = sc;
+      double bb = 0.0;
+      for (int k = 0; k < kSt; ++k) w[k] *= sc;
+      for (int dj = -1; dj <= 1; ++dj) {
+        if (i == 1) {
+          bb -= w[st_slot(-1, dj)] * I.phi_g;
+          w[st_slot(-1, dj)] = 0.0;
+        }
+        if (i == I.n1 - 1) {
+          bb -= w[st_slot(1, dj)] * I.phi_out;
+          w[st_slot(1, dj)] = 0.0;
+        }
+      }
+      bbc[nd] = bb;
+      for (int k = 0; k < kSt; ++k) L.at(k, i, j) = w[k];
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Creation.
+// ---------------------------------------------------------------------------
+template <class Real>
+static int setup(apic_sim* S) {
+  const int ni = S->n_inst;
+  std::vector<std::vector<double>> tabs(ni), vols(ni), rscs(ni), bbcs(ni);
+  std::vector<std::vector<HostLevel>> levels(ni);
+  std::vector<std::vector<double>> cinvs(ni);
+  long long total_nodes = 0, level_nodes = 0, tab_total = 0, bins_total = 0, hist_total = 0, en_total = 0,
+            cinv_total = 0, slots = 0;
+  int pop_index = 0;
+  for (int k = 0; k < ni; ++k) {
+    const apic_config_t& c = S->cfg[k];
+    Inst I;
+    std::memset(&I, 0, sizeof(I));
+    I.alpha = c.alpha;
+    I.x1_out = c.x1_outer;
+    I.phi_g = c.phi_grain;
+    I.phi_out = c.phi_outer;
+    I.B = c.B;
+    I.dt = c.dt;
+    I.e_bind = c.e_bind_ion;
+    I.n1 = c.n1;
+    I.n2 = c.n2;
+    I.N1 = c.n1 + 1;
+    I.N2 = c.n2 + 1;
+    I.h1 = (c.x1_outer + 1.0) / c.n1;
+    I.h2 = 2.0 / c.n2;
+    I.nodes = (long long)I.N1 * I.N2;
+    I.node_off = total_nodes;
+    total_nodes += I.nodes;
+    I.tol = c.poisson_tol > 0 ? c.poisson_tol : 1e-10;
+    I.max_iter = c.poisson_max_iter > 0 ? c.poisson_max_iter : 20;
+    I.seed = c.seed;
+    I.tag = c.instance;
+    I.flags = c.flags;
+    I.n_species = c.n_species;
+    I.pop0 = pop_index;
+    I.hist_cap = c.history_cap > 0 ? c.history_cap : 4096;
+    I.tab_off = tab_total;
+    tab_total += 2 * (kTable + 1);
+    I.bin_off = bins_total;
+    bins_total += (long long)c.n_species * c.n2 * kNT;
+    I.hist_off = hist_total;
+    hist_total += (long long)I.hist_cap * kNH;
+    I.en_off = en_total;
+    en_total += I.N2;
+    build_tables(I, tabs[k]);
+    build_volumes(I, vols[k]);
+    // operator and multigrid hierarchy
+    levels[k].emplace_back();
+    build_fine(I, levels[k][0], rscs[k], bbcs[k]);
+    while (true) {
+      const HostLevel& F = levels[k].back();
+      if ((int)levels[k].size() >= kMaxLevels) break;
+      if (F.n1 % 2 || F.n2 % 2 || F.n1 < 8 || F.n2 < 4) break;
+      HostLevel C;
+      if (!galerkin(F, C, levels[k].size() == 1)) return S->fail(APIC_ERR_INVALID_ARG, "coarse stencil wider than 3x3");
+      levels[k].push_back(std::move(C));
+    }
+    I.n_levels = (int)levels[k].size();
+    I.tail_level = I.n_levels - 1;
+    for (int l = 0; l < I.n_levels; ++l)
+      if (levels[k][l].nodes() <= kTailNodes) {
+        I.tail_level = l;
+        break;
+      }
+    for (int l = 0; l < I.n_levels; ++l) {
+      Level& L = I.lv[l];
+      const HostLevel& H = levels[k][l];
+      L.n1 = H.n1;
+      L.n2 = H.n2;
+      L.N1 = H.N1;
+      L.N2 = H.N2;
+      L.off = level_nodes;
+      L.st = (long long)kSt * level_nodes;
+      L.pole_extra = l == 0 ? 1 : 0;
+      level_nodes += H.nodes();
+    }
+    // coarsest dense inverse over rows 1..n1-1
+    {
+      const HostLevel& H = levels[k].back();
+      int nu = (H.n1 - 1) * H.N2;
+      if (nu > kMaxCoarse) return S->fail(APIC_ERR_INVALID_ARG, "coarsest multigrid level too large (grid not divisible)");
+      std::vector<double> A((size_t)nu * nu, 0.0);
+      for (int i = 1; i < H.n1; ++i)
+        for (int j = 0; j <= H.n2; ++j) {
+          int r = (i - 1) * H.N2 + j;
+          for (int di = -1; di <= 1; ++di)
+            for (int dj = -1; dj <= 1; ++dj) {
+              int i2 = i + di, j2 = j + dj;
+              if (i2 < 1 || i2 > H.n1 - 1 || j2 < 0 || j2 > H.n2) continue;
+              A[(size_t)r * nu + (i2 - 1) * H.N2 + j2] += H.get(st_slot(di, dj), i, j);
+            }
+          if (I.n_levels == 1) {
+            double s = H.get(kStPole, i, j);
+            if (j == 0) A[(size_t)r * nu + (i - 1) * H.N2 + 2] += s;
+            if (j == H.n2) A[(size_t)r * nu + (i - 1) * H.N2 + H.n2 - 2] += s;
+          }
+        }
+      if (!invert(A, nu)) return S->fail(APIC_ERR_INVALID_ARG, "singular coarsest operator");
+      cinvs[k] = std::move(A);
+      I.coarse_n = nu;
+      I.cinv_off = cinv_total;
+      cinv_total += (long long)nu * nu;
+    }
+    for (int s = 0; s < c.n_species; ++s) {
+      Pop P;
+      std::memset(&P, 0, sizeof(P));
+      const apic_species_t& sp = c.sp[s];
+      P.q = sp.q;
+      P.m = sp.m;
+      P.T = sp.T;
+      P.w = I.V_dom / (double)sp.n_init;
+      P.vth = std::sqrt(sp.T / sp.m);
+      P.lam = std::sqrt(sp.T / (2.0 * kPi * sp.m)) * I.A_out * c.dt / P.w;
+      P.base = slots;
+      P.cap = sp.capacity;
+      slots += sp.capacity;
+      P.inst = k;
+      P.species = s;
+      int lg = bits_for(sp.capacity);
+      if (sizeof(Real) == 8) P.fbits = 62 - lg;
+      else P.fbits = 2 * std::min(20, (62 - lg) / 2);
+      P.dep_scale = sp.q * P.w * std::ldexp(1.0, -P.fbits);
+      P.acc_off = 2 * I.node_off + (long long)s * I.nodes;
+      S->max_inj = std::max(S->max_inj, (long long)std::ceil(P.lam) + 2);
+      S->pop.push_back(P);
+      ++pop_index;
+    }
+    S->inst.push_back(I);
+  }
+  S->n_pop = pop_index;
+  if (S->n_pop > kMaxPop) return S->fail(APIC_ERR_INVALID_ARG, "too many instances x species");
+
+  // ---- launch plan ----
+  SolvePlan& pl = S->plan;
+  std::memset(&pl, 0, sizeof(pl));
+  for (const Inst& I : S->inst) pl.max_tail = std::max(pl.max_tail, I.tail_level);
+  for (int l = 0; l < kMaxLevels; ++l) {
+    int x1l = 0, x2l = 0, k1 = 1, k2 = 1;
+    long long nodes = 1;
+    for (const Inst& I : S->inst) {
+      if (l >= I.n_levels) continue;
+      const Level& L = I.lv[l];
+      x1l = std::max(x1l, (L.n2 + 2) / 2);
+      x2l = std::max(x2l, L.n1 / 2);
+      k1 = std::max(k1, (L.n1 - 1 + 31) / 32);
+      k2 = std::max(k2, (L.n2 + 1 + 31) / 32);
+      nodes = std::max(nodes, (long long)L.N1 * L.N2);
+    }
+    pl.x1_blocks[l] = std::max(1, (x1l + 3) / 4);
+    pl.x2_blocks[l] = std::max(1, (x2l + 3) / 4);
+    pl.x1_k[l] = k1;
+    pl.x2_k[l] = k2;
+    pl.node_blocks[l] = (int)std::min<long long>(1024, std::max<long long>(1, (nodes + 255) / 256));
+  }
+  pl.tail_threads = 512;
+  pl.tail_k = 1;
+  for (const Inst& I : S->inst)
+    for (int l = I.tail_level; l < I.n_levels; ++l) {
+      pl.tail_k = std::max(pl.tail_k, (I.lv[l].n1 - 1 + 31) / 32);
+      pl.tail_k = std::max(pl.tail_k, (I.lv[l].n2 + 1 + 31) / 32);
+    }
+  while (pl.tail_threads > 64 && (size_t)(pl.tail_threads / 32) * 128 * pl.tail_k * sizeof(Real) > 200 * 1024)
+    pl.tail_threads /= 2;
+  if (!S->ck(set_poisson_smem<Real>(pl), "cudaFuncSetAttribute(smem)")) return S->status;
+
+  // ---- device memory ----
+  DevPtrs& d = S->d;
+  d.n_inst = ni;
+  d.n_pop = S->n_pop;
+  d.total_nodes = total_nodes;
+  d.level_nodes = level_nodes;
+  const size_t R = sizeof(Real);
+  auto A = [&](size_t bytes) { return S->dalloc(bytes); };
+  d.inst = (const Inst*)A(sizeof(Inst) * ni);
+  d.pop = (const Pop*)A(sizeof(Pop) * S->n_pop);
+  d.ps = (PopState*)A(sizeof(PopState) * S->n_pop);
+  d.sol = (SolverState*)A(sizeof(SolverState) * ni);
+  d.stp = (StepState*)A(sizeof(StepState) * ni);
+  d.err = (int32_t*)A(sizeof(int32_t) * 4);
+  d.x1 = A(R * slots);
+  d.x2 = A(R * slots);
+  d.vR = A(R * slots);
+  d.vZ = A(R * slots);
+  d.vT = A(R * slots);
+  d.holes = (int32_t*)A(sizeof(int32_t) * slots);
+  double** node_arrays[] = {&d.rho, &d.phi, &d.V, &d.bbc, &d.rscale, &d.b, &d.r, &d.rh, &d.p, &d.v, &d.s, &d.t, &d.ph, &d.sh};
+  for (double** a : node_arrays) *a = (double*)A(sizeof(double) * total_nodes);
+  S->phi_save = (double*)A(sizeof(double) * total_nodes);
+  d.st64 = (double*)A(sizeof(double) * kSt * total_nodes);
+  d.acc = (unsigned long long*)A(sizeof(unsigned long long) * 2 * total_nodes);
+  d.G = A(2 * R * total_nodes);
+  d.st = A(R * kSt * level_nodes);
+  d.e = A(R * level_nodes);
+  d.f = A(R * level_nodes);
+  d.cinv = A(R * std::max<long long>(1, cinv_total));
+  d.tab = (double*)A(sizeof(double) * tab_total);
+  d.bins = (double*)A(sizeof(double) * std::max<long long>(1, bins_total));
+  d.hist = (double*)A(sizeof(double) * hist_total);
+  d.en = (double*)A(sizeof(double) * en_total);
+  d.red = (double*)A(sizeof(double) * ni * kNRed * kRedBlocks);
+  if (S->status != APIC_OK) return S->status;
+
+  // ---- uploads ----
+  S->h2d((Inst*)d.inst, S->inst.data(), ni);
+  S->h2d((Pop*)d.pop, S->pop.data(), S->n_pop);
+  std::vector<Real> tmp;
+  for (int k = 0; k < ni; ++k) {
+    const Inst& I = S->inst[k];
+    S->h2d(d.tab + I.tab_off, tabs[k].data(), tabs[k].size());
+    S->h2d(d.V + I.node_off, vols[k].data(), vols[k].size());
+    S->h2d(d.rscale + I.node_off, rscs[k].data(), rscs[k].size());
+    S->h2d(d.bbc + I.node_off, bbcs[k].data(), bbcs[k].size());
+    S->h2d(d.st64 + (long long)kSt * I.node_off, levels[k][0].st.data(), levels[k][0].st.size());
+    for (int l = 0; l < I.n_levels; ++l) {
+      const HostLevel& H = levels[k][l];
+      tmp.assign(H.st.begin(), H.st.end());
+      S->h2d((Real*)d.st + I.lv[l].st, tmp.data(), tmp.size());
+    }
+    tmp.assign(cinvs[k].begin(), cinvs[k].end());
+    S->h2d((Real*)d.cinv + I.cinv_off, tmp.data(), tmp.size());
+    // initial potential: the vacuum solution, linear in x1 (phi = 0 without field)
+    std::vector<double> phi((size_t)I.nodes, 0.0);
+    if (!(I.flags & APIC_NO_FIELD))
+      for (int i = 0; i <= I.n1; ++i)
+        for (int j = 0; j <= I.n2; ++j)
+          phi[(size_t)i * I.N2 + j] = I.phi_g + (I.phi_out - I.phi_g) * (x1_node_h(I, i) + 1.0) / (I.x1_out + 1.0);
+    S->h2d(d.phi + I.node_off, phi.data(), phi.size());
+    // tables are synchronous inputs of host vectors: wait before they go out of scope
+    if (!S->sync()) return S->status;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  S->push_grid = std::max(1, sms) * 4;
+  return S->sync() ? APIC_OK : S->status;
+}
+
+extern "C" int apic_create_batch(const apic_config_t* cfgs, int32_t n, void* stream,
+                                 const apic_allocator_t* allocator, apic_sim** out) {
+  if (!out) return APIC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cfgs || n < 1) return APIC_ERR_INVALID_ARG;
+  std::string why;
+  for (int k = 0; k < n; ++k) {
+    int rc = validate(cfgs[k], why);
+    if (rc != APIC_OK) {
+      std::fprintf(stderr, "apic_create: instance %d: %s\n", k, why.c_str());
+      return rc;
+    }
+    if (cfgs[k].precision != cfgs[0].precision) return APIC_ERR_INVALID_ARG;
+  }
+  apic_sim* S = new apic_sim();
+  S->precision = cfgs[0].precision;
+  S->n_inst = n;
+  S->cfg.assign(cfgs, cfgs + n);
+  S->stream = (cudaStream_t)stream;
+  if (allocator && allocator->alloc && allocator->free) {
+    S->alloc = *allocator;
+    S->have_alloc = true;
+  }
+  if (!S->ck(cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking), "cudaStreamCreate") ||
+      !S->ck(cudaStreamCreateWithFlags(&S->cap2, cudaStreamNonBlocking), "cudaStreamCreate") ||
+      !S->ck(cudaMallocHost(&S->h_err, 16), "cudaMallocHost")) {
+    int rc = S->status;
+    apic_destroy(S);
+    return rc;
+  }
+  int rc = S->precision == APIC_FP64 ? setup<double>(S) : setup<float>(S);
+  if (rc != APIC_OK) {
+    std::fprintf(stderr, "apic_create: %s\n", S->msg.c_str());
+    apic_destroy(S);
+    return rc;
+  }
+  *out = S;
+  return APIC_OK;
+}
+
+extern "C" int apic_create(const apic_config_t* cfg, void* stream, const apic_allocator_t* allocator, apic_sim** out) {
+  return apic_create_batch(cfg, 1, stream, allocator, out);
+}
+
+extern "C" int apic_destroy(apic_sim* S) {
+  if (!S) return APIC_OK;
+  if (S->stream || S->cap) cudaStreamSynchronize(S->stream);
+  if (S->exec) cudaGraphExecDestroy(S->exec);
+  if (S->graph) cudaGraphDestroy(S->graph);
+  S->dfree_all();
+  cudaStreamSynchronize(S->stream);
+  if (S->cap) cudaStreamDestroy(S->cap);
+  if (S->cap2) cudaStreamDestroy(S->cap2);
+  if (S->h_err) cudaFreeHost(S->h_err);
+  delete S;
+  return APIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stepping.
+// ---------------------------------------------------------------------------
+template <class Real>
+static void enqueue_solver_iterations_fixed(apic_sim* S, cudaStream_t s) {
+  int most = 0;
+  for (const Inst& I : S->inst) most = std::max(most, I.max_iter);
+  for (int it = 0; it < most; ++it) {
+    launch_bicg_iter<Real>(S->d, S->plan, s);
+    launch_bicg_check(S->d, 0, 0, s);
+  }
+}
+
+// One step: deposit -> Poisson -> gradients/surface -> push -> inject -> bookkeeping.
+template <class Real>
+static bool capture_step(apic_sim* S) {
+  cudaStream_t s = S->cap;
+  if (!S->ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture")) return false;
+  launch_rho<Real>(S->d, s);
+  launch_bicg_init<Real>(S->d, s);
+  bool cond_ok = false;
+  {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd) == cudaSuccess) {
+      cudaGraphConditionalHandle h;
+      if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn;
+        if (cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp) == cudaSuccess) {
+          cudaGraph_t body = cp.conditional.phGraph_out[0];
+          if (cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                  cudaSuccess &&
+              cudaStreamBeginCaptureToGraph(S->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                  cudaSuccess) {
+            launch_bicg_iter<Real>(S->d, S->plan, S->cap2);
+            launch_bicg_check(S->d, h, 1, S->cap2);
+            cudaGraph_t tmp = nullptr;
+            cond_ok = cudaStreamEndCapture(S->cap2, &tmp) == cudaSuccess;
+          }
+        }
+      }
+    }
+  }
+  cudaGetLastError();
+  if (!cond_ok) {
+    // A capture that failed half-way is abandoned; retry with a fixed loop.
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(s, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    cudaGetLastError();
+    if (!S->ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture")) return false;
+    launch_rho<Real>(S->d, s);
+    launch_bicg_init<Real>(S->d, s);
+    enqueue_solver_iterations_fixed<Real>(S, s);
+  }
+  launch_gradients<Real>(S->d, s);
+  launch_surface(S->d, s);
+  launch_push<Real>(S->d, S->push_grid, s);
+  launch_inject<Real>(S->d, S->max_inj, s);
+  launch_step_end(S->d, s);
+  if (!S->ck(cudaStreamEndCapture(s, &S->graph), "end capture")) return false;
+  if (!S->ck(cudaGraphInstantiate(&S->exec, S->graph, 0), "graph instantiate")) return false;
+  return true;
+}
+
+static int read_status(apic_sim* S) {
+  if (!S->d2h(S->h_err, S->d.err, 1) || !S->sync()) return S->status;
+  int e = S->h_err[0];
+  if (e & kErrCapacity) return S->fail(APIC_ERR_CAPACITY, "particle capacity exceeded");
+  if (e & kErrNonFinite) return S->fail(APIC_ERR_NONFINITE, "non-finite field or residual");
+  if (e & kErrNotConverged) return S->fail(APIC_ERR_NOT_CONVERGED, "Poisson iteration limit reached");
+  return APIC_OK;
+}
+
+template <class Real>
+static int step_impl(apic_sim* S, int n) {
+  if (S->dirty) {
+    if (!S->ck(cudaMemsetAsync(S->d.acc, 0, sizeof(unsigned long long) * 2 * S->d.total_nodes, S->stream), "memset"))
+      return S->status;
+    launch_deposit_all<Real>(S->d, S->push_grid, S->stream);
+    S->dirty = false;
+  }
+  if (!S->exec) {
+    if (!S->sync()) return S->status;
+    if (!capture_step<Real>(S)) return S->status;
+  }
+  for (int k = 0; k < n; ++k)
+    if (!S->ck(cudaGraphLaunch(S->exec, S->stream), "graph launch")) return S->status;
+  if (!S->ck(cudaGetLastError(), "launch")) return S->status;
+  return read_status(S);
+}
+
+extern "C" int apic_step(apic_sim* S, int32_t n_steps) {
+  if (!S) return APIC_ERR_INVALID_ARG;
+  if (S->status != APIC_OK) return S->status;
+  if (n_steps < 0) return APIC_ERR_INVALID_ARG;
+  if (n_steps == 0) return APIC_OK;
+  return S->precision == APIC_FP64 ? step_impl<double>(S, n_steps) : step_impl<float>(S, n_steps);
+}
+
+// ---------------------------------------------------------------------------
+// Injection.
+// ---------------------------------------------------------------------------
+template <class Real>
+static int inject_impl(apic_sim* S, int inst, int species, long long n, int mode, const double* st) {
+  int pop = S->inst[inst].pop0 + species;
+  const Pop& P = S->pop[pop];
+  PopState ps;
+  if (!S->sync() || !S->d2h(&ps, S->d.ps + pop, 1) || !S->sync()) return S->status;
+  if (mode == APIC_FLUX_SURFACE) {
+    if (ps.n + n > P.cap) return APIC_ERR_CAPACITY;
+    ps.n_inj = n;
+    ps.inj_stored = 0;
+    if (!S->h2d(S->d.ps + pop, &ps, 1)) return S->status;
+    launch_inject<Real>(S->d, n, S->stream);
+    launch_finish_injection(S->d, pop, S->stream);
+    S->dirty = true;
+    return read_status(S);
+  }
+  if (ps.n + n > P.cap) return APIC_ERR_CAPACITY;
+  if (mode == APIC_LOAD_VOLUME) {
+    launch_load<Real>(S->d, pop, ps.n, n, ps.draws, 1, S->stream);
+    ps.draws += n;
+  } else {
+    double* tmp = (double*)S->dalloc(sizeof(double) * 5 * (size_t)n);
+    if (!tmp) return S->status;
+    if (!S->h2d(tmp, st, 5 * (size_t)n)) return S->status;
+    launch_explicit<Real>(S->d, pop, ps.n, n, tmp, S->stream);
+    if (!S->sync()) return S->status;
+    // release the staging buffer now
+    S->blocks.pop_back();
+    if (S->have_alloc) S->alloc.free(tmp, (void*)S->stream, S->alloc.ctx);
+    else cudaFreeAsync(tmp, S->stream);
+  }
+  ps.n += n;
+  ps.loaded += n;
+  if (!S->h2d(S->d.ps + pop, &ps, 1) || !S->sync()) return S->status;
+  S->dirty = true;
+  return S->ck(cudaGetLastError(), "inject") ? APIC_OK : S->status;
+}
+
+extern "C" int apic_inject(apic_sim* S, int32_t instance, int32_t species, int64_t n, int32_t mode,
+                           const double* explicit_state) {
+  if (!S) return APIC_ERR_INVALID_ARG;
+  if (S->status != APIC_OK) return S->status;
+  if (instance < 0 || instance >= S->n_inst || species < 0 || species >= S->inst[instance].n_species || n < 0)
+    return APIC_ERR_INVALID_ARG;
+  if (mode != APIC_LOAD_VOLUME && mode != APIC_FLUX_SURFACE && mode != APIC_EXPLICIT) return APIC_ERR_INVALID_ARG;
+  if (mode == APIC_EXPLICIT && !explicit_state && n > 0) return APIC_ERR_INVALID_ARG;
+  if (n == 0) return APIC_OK;
+  return S->precision == APIC_FP64 ? inject_impl<double>(S, instance, species, n, mode, explicit_state)
+                                   : inject_impl<float>(S, instance, species, n, mode, explicit_state);
+}
+
+// ---------------------------------------------------------------------------
+// Read-back.
+// ---------------------------------------------------------------------------
+extern "C" int apic_tallies(apic_sim* S, int32_t instance, apic_tallies_t* out) {
+  if (!S || !out) return APIC_ERR_INVALID_ARG;
+  if (instance < 0 || instance >= S->n_inst) return APIC_ERR_INVALID_ARG;
+  const Inst& I = S->inst[instance];
+  if (!S->sync()) return S->status;
+  if (out->bins) S->d2h(out->bins, S->d.bins + I.bin_off, (size_t)I.n_species * I.n2 * kNT);
+  StepState stp;
+  SolverState sol;
+  S->d2h(&stp, S->d.stp + instance, 1);
+  S->d2h(&sol, S->d.sol + instance, 1);
+  PopState ps[2];
+  std::memset(ps, 0, sizeof(ps));
+  for (int s = 0; s < I.n_species; ++s) S->d2h(&ps[s], S->d.ps + I.pop0 + s, 1);
+  std::vector<double> hist((size_t)I.hist_cap * kNH);
+  S->d2h(hist.data(), S->d.hist + I.hist_off, hist.size());
+  if (!S->sync()) return S->status;
+  for (int s = 0; s < 2; ++s) {
+    out->counts[s][0] = ps[s].loaded;
+    out->counts[s][1] = ps[s].injected;
+    out->counts[s][2] = ps[s].absorbed;
+    out->counts[s][3] = ps[s].escaped;
+    out->counts[s][4] = ps[s].loaded + ps[s].injected - ps[s].absorbed - ps[s].escaped - ps[s].dropped;
+    out->counts[s][5] = ps[s].dropped;
+  }
+  out->step = stp.step;
+  out->grain_Q = stp.Q;
+  out->grain_FZ = stp.FZ;
+  out->poisson_res = sol.res;
+  out->poisson_iters = sol.iters;
+  long long rows = std::min<long long>(stp.step, I.hist_cap);
+  if (out->history) {
+    long long cap = out->history_rows;
+    long long w = std::min(rows, cap);
+    long long first = stp.step - w;  // oldest row written
+    for (long long r = 0; r < w; ++r) {
+      long long src = (first + r) % I.hist_cap;
+      std::memcpy(out->history + r * kNH, hist.data() + src * kNH, sizeof(double) * kNH);
+    }
+    out->history_rows = w;
+  } else {
+    out->history_rows = rows;
+  }
+  return APIC_OK;
+}
+
+template <class Real>
+static int solve_impl(apic_sim* S, int inst, const double* rho, double* phi_out) {
+  const Inst& I = S->inst[inst];
+  DevPtrs& d = S->d;
+  if (!S->ck(cudaMemcpyAsync(S->phi_save, d.phi, sizeof(double) * d.total_nodes, cudaMemcpyDeviceToDevice, S->stream),
+             "save phi"))
+    return S->status;
+  if (rho && !S->h2d(d.rho + I.node_off, rho, (size_t)I.nodes)) return S->status;
+  launch_b_from_rho(d, inst, S->stream);
+  launch_bicg_init<Real>(d, S->stream);
+  int it = 0;
+  SolverState sol;
+  for (;;) {
+    launch_bicg_iter<Real>(d, S->plan, S->stream);
+    launch_bicg_check(d, 0, 0, S->stream);
+    if (!S->d2h(&sol, d.sol + inst, 1) || !S->sync()) return S->status;
+    if (sol.done || ++it > 1000) break;
+  }
+  if (phi_out) S->d2h(phi_out, d.phi + I.node_off, (size_t)I.nodes);
+  S->ck(cudaMemcpyAsync(d.phi, S->phi_save, sizeof(double) * d.total_nodes, cudaMemcpyDeviceToDevice, S->stream),
+        "restore phi");
+  return read_status(S);
+}
+
+extern "C" int apic_solve_poisson(apic_sim* S, int32_t instance, const double* rho, double* phi_out) {
+  if (!S) return APIC_ERR_INVALID_ARG;
+  if (S->status != APIC_OK) return S->status;
+  if (instance < 0 || instance >= S->n_inst) return APIC_ERR_INVALID_ARG;
+  if (S->inst[instance].flags & APIC_NO_FIELD) return APIC_ERR_INVALID_ARG;
+  return S->precision == APIC_FP64 ? solve_impl<double>(S, instance, rho, phi_out)
+                                   : solve_impl<float>(S, instance, rho, phi_out);
+}
+
+template <class Real>
+static int particles_impl(apic_sim* S, int inst, int species, double* out, long long cap, long long* n_out) {
+  int pop = S->inst[inst].pop0 + species;
+  PopState ps;
+  if (!S->sync() || !S->d2h(&ps, S->d.ps + pop, 1) || !S->sync()) return S->status;
+  long long n = ps.n;
+  std::vector<double> h((size_t)std::max<long long>(1, n) * 5);
+  if (n > 0) {
+    double* tmp = (double*)S->dalloc(sizeof(double) * 5 * (size_t)n);
+    if (!tmp) return S->status;
+    long long nn = n;
+    launch_gather_particles<Real>(S->d, pop, tmp, &nn, S->stream);
+    S->d2h(h.data(), tmp, 5 * (size_t)n);
+    if (!S->sync()) return S->status;
+    S->blocks.pop_back();
+    if (S->have_alloc) S->alloc.free(tmp, (void*)S->stream, S->alloc.ctx);
+    else cudaFreeAsync(tmp, S->stream);
+  }
+  long long w = 0;
+  for (long long k = 0; k < n; ++k) {
+    if (!(h[5 * k] < 0.0)) continue;  // freed slot
+    if (w < cap && out) std::memcpy(out + 5 * w, h.data() + 5 * k, sizeof(double) * 5);
+    ++w;
+  }
+  *n_out = std::min(w, cap);
+  return APIC_OK;
+}
+
+extern "C" int apic_get_particles(apic_sim* S, int32_t instance, int32_t species, double* out, int64_t capacity,
+                                  int64_t* n_out) {
+  if (!S || !n_out) return APIC_ERR_INVALID_ARG;
+  if (instance < 0 || instance >= S->n_inst || species < 0 || species >= S->inst[instance].n_species)
+    return APIC_ERR_INVALID_ARG;
+  long long n = 0;
+  int rc = S->precision == APIC_FP64 ? particles_impl<double>(S, instance, species, out, capacity, &n)
+                                     : particles_impl<float>(S, instance, species, out, capacity, &n);
+  *n_out = n;
+  return rc;
+}
+
+extern "C" int apic_get_field(apic_sim* S, int32_t instance, int32_t which, double* out) {
+  if (!S || !out) return APIC_ERR_INVALID_ARG;
+  if (instance < 0 || instance >= S->n_inst || which < 0 || which > 4) return APIC_ERR_INVALID_ARG;
+  const Inst& I = S->inst[instance];
+  if (!S->sync()) return S->status;
+  if (which == 0) S->d2h(out, S->d.rho + I.node_off, (size_t)I.nodes);
+  else if (which == 1) S->d2h(out, S->d.phi + I.node_off, (size_t)I.nodes);
+  else if (which == 4) S->d2h(out, S->d.V + I.node_off, (size_t)I.nodes);
+  else {
+    size_t R = S->precision == APIC_FP64 ? 8 : 4;
+    std::vector<unsigned char> g((size_t)I.nodes * 2 * R);
+    S->ck(cudaMemcpyAsync(g.data(), (unsigned char*)S->d.G + (size_t)I.node_off * 2 * R, g.size(),
+                          cudaMemcpyDeviceToHost, S->stream),
+          "D2H");
+    if (!S->sync()) return S->status;
+    int c = which - 2;
+    for (long long k = 0; k < I.nodes; ++k) {
+      if (R == 8) out[k] = ((const double*)g.data())[2 * k + c];
+      else out[k] = (double)((const float*)g.data())[2 * k + c];
+    }
+  }
+  return S->sync() ? APIC_OK : S->status;
+}
+
+extern "C" const char* apic_last_error(const apic_sim* S) { return S ? S->msg.c_str() : "null simulation"; }
+
+extern "C" int32_t apic_num_instances(const apic_sim* S) { return S ? S->n_inst : 0; }

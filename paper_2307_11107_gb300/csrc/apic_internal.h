@@ -1,0 +1,186 @@
+// Internal data layout of libapic (host and device).  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/apic.h"
+
+namespace apic {
+
+constexpr int kNT = APIC_NT;
+constexpr int kNH = APIC_NH;
+constexpr int kMaxLevels = 12;
+constexpr int kMaxPop = 128;      // populations (instance x species) per batch
+constexpr int kTable = 4096;      // intervals of the inverse-CDF sampling tables
+constexpr int kRedBlocks = 64;    // CTAs per instance in node-parallel kernels (fixed => deterministic sums)
+constexpr int kNRed = 8;          // reduction slots per CTA
+constexpr int kTailNodes = 20000; // levels with at most this many nodes run in the single-CTA tail kernel
+constexpr int kMaxCoarse = 1024;  // unknowns of the coarsest level (dense inverse)
+
+// error bits of the device status word
+constexpr int kErrCapacity = 1;
+constexpr int kErrNotConverged = 2;
+constexpr int kErrNonFinite = 4;
+
+// One multigrid level of one instance.  Unknowns are the nodes of rows
+// i = 1..n1-1 (all j); rows 0 and n1 hold Dirichlet values.
+struct Level {
+  int n1, n2, N1, N2;    // cells and nodes
+  int64_t off;           // offset of this level's node vectors in the level pool
+  int64_t st;            // offset of its stencil (kSt arrays of `nodes` entries)
+  int pole_extra;        // 1 on the finest level: pole rows reach j +- 2
+  int pad;
+};
+
+// Stencil slots: (di, dj) in {-1,0,1}^2 as 3*(di+1) + (dj+1), then the two
+// pole reaches (j=0 -> j=2, j=n2 -> j=n2-2).
+constexpr int kSt = 11;
+__host__ __device__ constexpr int st_slot(int di, int dj) { return 3 * (di + 1) + (dj + 1); }
+constexpr int kStPole = 9;  // coefficient of phi(i, 2) in row (i, 0) and of phi(i, n2-2) in row (i, n2)
+
+struct Inst {
+  double alpha, x1_out, phi_g, phi_out, B, dt, e_bind;
+  double h1, h2;
+  double V_dom, A_out, A_grain;
+  double tol;
+  uint64_t seed;
+  int n1, n2, N1, N2;
+  int64_t nodes;           // N1 * N2
+  int64_t node_off;        // offset into per-node arrays of the batch
+  int64_t tab_off;         // offset of the two CDF tables (volume, surface), (kTable+1) each
+  int64_t bin_off;         // offset of the tally bins [n_species][n2][kNT]
+  int64_t hist_off;        // offset of the history ring [hist_cap][kNH]
+  int64_t en_off;          // offset of the surface field E_n [N2]
+  int32_t hist_cap;
+  int32_t n_species;
+  int32_t pop0;            // first population of this instance
+  int32_t tag;             // Philox counter tag (user instance id)
+  int32_t flags;
+  int32_t max_iter;
+  int32_t n_levels;
+  int32_t tail_level;      // first level handled by the single-CTA tail kernel
+  int64_t cinv_off;        // dense inverse of the coarsest level [coarse_n]^2
+  int32_t coarse_n;
+  int32_t pad;
+  Level lv[kMaxLevels];
+};
+
+struct Pop {
+  double q, m, T, w, vth, lam;
+  double dep_scale;        // q * w * 2^-fbits
+  int64_t base, cap;       // particle slots [base, base + cap)
+  int32_t inst, species;
+  int32_t fbits;           // fixed-point fraction bits of the deposit
+  int32_t pad;
+  int64_t acc_off;         // offset of this population's deposit accumulator (nodes of its instance)
+};
+
+// Device-mutable counters of one population.
+struct PopState {
+  long long n;             // slots in use [0, n)
+  long long n_holes;       // free slots stacked in `holes`
+  long long draws;         // Philox draws consumed
+  long long loaded, injected, absorbed, escaped, dropped;
+  long long n_inj;         // surface injections of the current step
+  long long inj_stored;    // of which stored this step
+  double carry;            // fractional injection carry
+  long long pad[5];
+};
+
+// Per-instance solver scalars (device).
+struct SolverState {
+  double rho, alpha, omega, rho_old;
+  double bnorm2, rnorm2;
+  double res;              // relative residual of the last iterate
+  int32_t iters, done;
+  double pad[8];
+};
+
+// Per-instance step scalars (device).
+struct StepState {
+  long long step;
+  double Q, FZ;            // grain charge and electric force of the last solve
+  double tally[5];         // this step: charge, p_Z, L_z, heat, events
+  double pad[6];
+};
+
+// Pointers handed to every kernel.
+struct DevPtrs {
+  const Inst* inst;
+  const Pop* pop;
+  PopState* ps;
+  SolverState* sol;
+  StepState* stp;
+  int n_inst, n_pop;
+  int32_t* err;
+  // particles (element type = the precision of the batch)
+  void *x1, *x2, *vR, *vZ, *vT;
+  void *y1, *y2, *yR, *yZ, *yT;  // second buffer (sort)
+  int32_t* holes;
+  int32_t* keys;                  // sort scratch
+  // per-node FP64 arrays
+  double *rho, *phi, *V, *bbc, *rscale;
+  double *b, *r, *rh, *p, *v, *s, *t, *ph, *sh;
+  double* st64;                   // finest-level stencil, FP64 [kSt][nodes] per instance (same offsets)
+  unsigned long long* acc;        // deposit accumulators
+  void* G;                        // node gradients (dphi/dx1, dphi/dx2) as pairs of the particle type
+  // multigrid (particle type)
+  void* st;                       // stencils of all levels
+  void *e, *f;                    // level vectors
+  void* cinv;                     // coarsest inverses
+  // tables and diagnostics (FP64)
+  double* tab;
+  double* bins;
+  double* hist;
+  double* en;
+  double* red;                    // reduction partials [n_inst][kNRed][kRedBlocks]
+  int64_t total_nodes;
+  int64_t level_nodes;
+};
+
+// ---- launchers (defined in the kernel translation units) ----
+template <class Real>
+void launch_load(const DevPtrs& d, int pop, long long n0, long long count, long long draw0, int kind,
+                 cudaStream_t s);
+template <class Real>
+void launch_explicit(const DevPtrs& d, int pop, long long n0, long long count, const double* dstate,
+                     cudaStream_t s);
+template <class Real>
+void launch_deposit_all(const DevPtrs& d, int max_grid, cudaStream_t s);
+template <class Real>
+void launch_push(const DevPtrs& d, int grid, cudaStream_t s);
+template <class Real>
+void launch_inject(const DevPtrs& d, long long max_inj, cudaStream_t s);
+template <class Real>
+void launch_gather_particles(const DevPtrs& d, int pop, double* out, long long* n_out, cudaStream_t s);
+
+// fields (fields.cu)
+template <class Real>
+void launch_rho(const DevPtrs& d, cudaStream_t s);
+template <class Real>
+void launch_gradients(const DevPtrs& d, cudaStream_t s);
+void launch_surface(const DevPtrs& d, cudaStream_t s);
+void launch_step_end(const DevPtrs& d, cudaStream_t s);
+void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s);
+
+// Poisson (poisson.cu): host-side launch plan of the multigrid levels.
+struct SolvePlan {
+  int max_tail;                   // levels run by the multi-CTA kernels (0 .. max_tail-1)
+  int x1_blocks[kMaxLevels];      // grid.x of the x1-line kernels (lines per colour / warps per CTA)
+  int x2_blocks[kMaxLevels];
+  int x1_k[kMaxLevels];           // rows per lane of the warp line solver
+  int x2_k[kMaxLevels];
+  int node_blocks[kMaxLevels];    // grid.x of node-parallel kernels on each level
+  int tail_threads, tail_k;
+};
+template <class Real>
+void launch_bicg_init(const DevPtrs& d, cudaStream_t s);
+template <class Real>
+void launch_bicg_iter(const DevPtrs& d, const SolvePlan& plan, cudaStream_t s);
+template <class Real>
+cudaError_t set_poisson_smem(const SolvePlan& plan);
+void launch_bicg_check(const DevPtrs& d, cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
+void launch_finish_injection(const DevPtrs& d, int pop, cudaStream_t s);
+
+}  // namespace apic

@@ -1,0 +1,240 @@
+// Node-field kernels of the APIC step (arXiv:2307.11107, Sec. 2):
+//   charge density from the fixed-point accumulators divided by the node
+//   volumes of Eq. 5, and the right-hand side of Eqs. 6-7;
+//   node gradients dphi/dx1, dphi/dx2 (used by the gather of Eq. 10);
+//   surface charge and electric force on the grain (after Eq. 10);
+//   per-step bookkeeping and the history of currents, forces, torque, heat flux.
+#include <cuda_runtime.h>
+
+#include "apic_internal.h"
+#include "geom.cuh"
+
+namespace apic {
+namespace {
+
+__device__ __forceinline__ double x1_node(const Inst& I, int i) { return i == I.n1 ? I.x1_out : -1.0 + i * I.h1; }
+__device__ __forceinline__ double x2_node(const Inst& I, int j) { return j == I.n2 ? 1.0 : -1.0 + j * I.h2; }
+
+// Deterministic block sum (fixed tree) of one double per thread; blockDim 256.
+__device__ double block_sum(double v, double* sh) {
+  int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if (t < o) sh[t] += sh[t + o];
+    __syncthreads();
+  }
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// rho_ij = sum_s q_s w_s (accumulated CIC weights) / V_ij; the accumulators are
+// cleared for the next deposit.  b = rscale * (-rho) + (Dirichlet terms), and
+// per-CTA partial sums of |b|^2.
+__global__ void __launch_bounds__(256) k_rho(DevPtrs d) {
+  __shared__ double sh[256];
+  const Inst& I = d.inst[blockIdx.y];
+  double part = 0.0;
+  for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes;
+       nd += (long long)gridDim.x * blockDim.x) {
+    long long g = I.node_off + nd;
+    double q = 0.0;
+    for (int s = 0; s < I.n_species; ++s) {
+      const Pop& P = d.pop[I.pop0 + s];
+      unsigned long long a = d.acc[P.acc_off + nd];
+      d.acc[P.acc_off + nd] = 0ull;
+      q += P.dep_scale * (double)a;
+    }
+    double rho = q / d.V[g];
+    d.rho[g] = rho;
+    int i = (int)(nd / I.N2);
+    double bv = 0.0;
+    if (i > 0 && i < I.n1) bv = -rho * d.rscale[g] + d.bbc[g];
+    d.b[g] = bv;
+    part += bv * bv;
+  }
+  double tot = block_sum(part, sh);
+  if (threadIdx.x == 0) d.red[((long long)blockIdx.y * kNRed + 0) * kRedBlocks + blockIdx.x] = tot;
+}
+
+// b of one instance from an externally supplied rho (Poisson-only solves).
+__global__ void __launch_bounds__(256) k_b_from_rho(DevPtrs d, int inst) {
+  __shared__ double sh[256];
+  const Inst& I = d.inst[inst];
+  double part = 0.0;
+  for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes;
+       nd += (long long)gridDim.x * blockDim.x) {
+    long long g = I.node_off + nd;
+    int i = (int)(nd / I.N2);
+    double bv = 0.0;
+    if (i > 0 && i < I.n1) bv = -d.rho[g] * d.rscale[g] + d.bbc[g];
+    d.b[g] = bv;
+    part += bv * bv;
+  }
+  double tot = block_sum(part, sh);
+  if (threadIdx.x == 0) d.red[((long long)inst * kNRed + 0) * kRedBlocks + blockIdx.x] = tot;
+}
+
+template <class Real>
+struct Pair;
+template <>
+struct Pair<double> {
+  using T = double2;
+};
+template <>
+struct Pair<float> {
+  using T = float2;
+};
+
+// Node gradients: central differences inside, one-sided second order on the
+// four edges (Sec. 2: derivatives of phi taken numerically at the nodes).
+template <class Real>
+__global__ void __launch_bounds__(256) k_gradients(DevPtrs d) {
+  using R2 = typename Pair<Real>::T;
+  const Inst& I = d.inst[blockIdx.y];
+  const double* p = d.phi + I.node_off;
+  R2* G = (R2*)d.G + I.node_off;
+  const bool nofield = (I.flags & APIC_NO_FIELD) != 0;
+  const int n1 = I.n1, n2 = I.n2, N2 = I.N2;
+  for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes;
+       nd += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(nd / N2), j = (int)(nd % N2);
+    double g1 = 0.0, g2 = 0.0;
+    if (!nofield) {
+      if (i == 0) g1 = (-3.0 * p[j] + 4.0 * p[N2 + j] - p[2 * N2 + j]) / (2.0 * I.h1);
+      else if (i == n1) g1 = (3.0 * p[n1 * N2 + j] - 4.0 * p[(n1 - 1) * N2 + j] + p[(n1 - 2) * N2 + j]) / (2.0 * I.h1);
+      else g1 = (p[(i + 1) * N2 + j] - p[(i - 1) * N2 + j]) / (2.0 * I.h1);
+      long long b = (long long)i * N2;
+      if (j == 0) g2 = (-3.0 * p[b] + 4.0 * p[b + 1] - p[b + 2]) / (2.0 * I.h2);
+      else if (j == n2) g2 = (3.0 * p[b + n2] - 4.0 * p[b + n2 - 1] + p[b + n2 - 2]) / (2.0 * I.h2);
+      else g2 = (p[b + j + 1] - p[b + j - 1]) / (2.0 * I.h2);
+    }
+    R2 v;
+    v.x = (Real)g1;
+    v.y = (Real)g2;
+    G[nd] = v;
+  }
+}
+
+// Surface charge sigma = E_n = -(dphi/dx1)|grad x1| on x1 = -1, grain charge
+// Q = int sigma dA and electric force F_Z = int (sigma^2/2) n_Z dA with dA of
+// Eq. 4 (trapezoid over the x2 nodes).  Thread 0 also draws this step's
+// injection count from the fractional carry (floor of carry + lambda).
+__global__ void __launch_bounds__(256) k_surface(DevPtrs d) {
+  __shared__ double sh[256];
+  const int inst = blockIdx.x;
+  const Inst& I = d.inst[inst];
+  const bool nofield = (I.flags & APIC_NO_FIELD) != 0;
+  double q = 0.0, fz = 0.0;
+  const double* p = d.phi + I.node_off;
+  const int N2 = I.N2;
+  for (int j = threadIdx.x; j <= I.n2; j += blockDim.x) {
+    double En = 0.0;
+    if (!nofield) {
+      double x2 = x2_node(I, j);
+      double r = r_grain(I.alpha, x2);
+      Metric<double> m = metric(I.alpha, r, x2);
+      double g = sqrt(m.x1R * m.x1R + m.x1Z * m.x1Z);
+      double G1 = (-3.0 * p[j] + 4.0 * p[N2 + j] - p[2 * N2 + j]) / (2.0 * I.h1);
+      En = -G1 * g;
+      double nZ = m.x1Z / g;
+      double dA = area_density(I.alpha, -1.0, x2);
+      double tw = (j == 0 || j == I.n2) ? 0.5 * I.h2 : I.h2;
+      q += tw * En * dA;
+      fz += tw * 0.5 * En * En * nZ * dA;
+    }
+    d.en[I.en_off + j] = En;
+  }
+  double Q = block_sum(q, sh);
+  double FZ = block_sum(fz, sh);
+  if (threadIdx.x == 0) {
+    d.stp[inst].Q = Q;
+    d.stp[inst].FZ = FZ;
+    if (!(Q == Q) || !(FZ == FZ) || Q - Q != 0.0) atomicOr(d.err, kErrNonFinite);
+    for (int s = 0; s < I.n_species; ++s) {
+      PopState& S = d.ps[I.pop0 + s];
+      const Pop& P = d.pop[I.pop0 + s];
+      if (I.flags & APIC_NO_INJECT) {
+        S.n_inj = 0;
+      } else {
+        double c = S.carry + P.lam;
+        double nk = floor(c);
+        S.carry = c - nk;
+        S.n_inj = (long long)nk;
+      }
+      S.inj_stored = 0;
+    }
+  }
+}
+
+// Close the step: injected particles become part of the population (freed
+// slots reused first), the history row is written, per-step sums cleared.
+__device__ void finish_injection(PopState& S, const Pop& P) {
+  long long stored = S.inj_stored, nh = S.n_holes;
+  if (stored <= nh) {
+    S.n_holes = nh - stored;
+  } else {
+    long long n = S.n + (stored - nh);
+    S.n = n > P.cap ? P.cap : n;
+    S.n_holes = 0;
+  }
+  S.draws += S.n_inj;
+  S.injected += S.n_inj;
+  S.n_inj = 0;
+  S.inj_stored = 0;
+}
+
+__global__ void k_step_end(DevPtrs d) {
+  const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+  if (inst >= d.n_inst) return;
+  const Inst& I = d.inst[inst];
+  StepState& T = d.stp[inst];
+  double res[2] = {0.0, 0.0};
+  for (int s = 0; s < I.n_species; ++s) {
+    PopState& S = d.ps[I.pop0 + s];
+    finish_injection(S, d.pop[I.pop0 + s]);
+    res[s] = (double)(S.loaded + S.injected - S.absorbed - S.escaped - S.dropped);
+  }
+  double dt = I.dt;
+  double* h = d.hist + I.hist_off + (T.step % I.hist_cap) * kNH;
+  h[0] = (double)(T.step + 1) * dt;
+  h[1] = T.tally[0] / dt;
+  h[2] = T.tally[1] / dt;
+  h[3] = T.FZ;
+  h[4] = T.tally[2] / dt;
+  h[5] = T.tally[3] / dt;
+  h[6] = T.Q;
+  h[7] = res[0];
+  h[8] = res[1];
+  h[9] = T.tally[4];
+  for (int k = 0; k < 5; ++k) T.tally[k] = 0.0;
+  T.step += 1;
+}
+
+// Explicit-count surface injection outside a step: same bookkeeping.
+__global__ void k_finish_injection(DevPtrs d, int pop) {
+  finish_injection(d.ps[pop], d.pop[pop]);
+}
+
+}  // namespace
+
+template <class Real>
+void launch_rho(const DevPtrs& d, cudaStream_t s) {
+  k_rho<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d);
+}
+template <class Real>
+void launch_gradients(const DevPtrs& d, cudaStream_t s) {
+  k_gradients<Real><<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d);
+}
+template void launch_rho<double>(const DevPtrs&, cudaStream_t);
+template void launch_rho<float>(const DevPtrs&, cudaStream_t);
+template void launch_gradients<double>(const DevPtrs&, cudaStream_t);
+template void launch_gradients<float>(const DevPtrs&, cudaStream_t);
+
+void launch_surface(const DevPtrs& d, cudaStream_t s) { k_surface<<<d.n_inst, 256, 0, s>>>(d); }
+void launch_step_end(const DevPtrs& d, cudaStream_t s) { k_step_end<<<(d.n_inst + 63) / 64, 64, 0, s>>>(d); }
+void launch_finish_injection(const DevPtrs& d, int pop, cudaStream_t s) { k_finish_injection<<<1, 1, 0, s>>>(d, pop); }
+void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s) { k_b_from_rho<<<kRedBlocks, 256, 0, s>>>(d, inst); }
+
+}  // namespace apic

@@ -1,0 +1,173 @@
+"""Python binding of libapic: `Sim` wraps one simulation object of the C ABI.
+
+The binding marshals arguments only.  PyTorch provides the device memory (the
+library's allocator callback is bound to torch's caching allocator) and the
+stream (torch's current CUDA stream); all computation is in libapic.so.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _abi
+
+KEYS = ("alpha", "x1_out", "phi_g", "phi_out", "B", "dt")
+
+
+class ApicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_abi.ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+def make_config(d, precision="fp32"):
+    """Workload dict (the keys used by tests and bench) -> apic_config_t."""
+    c = _abi.Config()
+    c.alpha, c.x1_outer, c.phi_grain, c.phi_outer = (float(d[k]) for k in ("alpha", "x1_out", "phi_g", "phi_out"))
+    c.B, c.dt = float(d["B"]), float(d["dt"])
+    c.e_bind_ion = float(d.get("e_bind_ion", 0.0))
+    c.n1, c.n2 = int(d["n1"]), int(d["n2"])
+    sps = d["species"]
+    c.n_species = len(sps)
+    for k, sp in enumerate(sps):
+        c.sp[k].q, c.sp[k].m, c.sp[k].T = float(sp["q"]), float(sp["m"]), float(sp["T"])
+        c.sp[k].n_init = int(sp["n_init"])
+        c.sp[k].capacity = int(sp.get("capacity", max(1024, int(1.6 * sp["n_init"]) + 4096)))
+    c.seed = int(d.get("seed", 1))
+    c.instance = int(d.get("instance", 0))
+    prec = d.get("precision", precision)
+    c.precision = _abi.FP64 if prec in ("fp64", _abi.FP64) else _abi.FP32_REFINED
+    c.flags = (_abi.NO_INJECT if d.get("no_inject") else 0) | (_abi.NO_FIELD if d.get("no_field") else 0)
+    c.poisson_tol = float(d.get("poisson_tol", 0.0))
+    c.poisson_max_iter = int(d.get("poisson_max_iter", 0))
+    c.sort_interval = int(d.get("sort_interval", 0))
+    c.history_cap = int(d.get("history_cap", 0))
+    return c
+
+
+class _TorchAllocator:
+    """Binds the library's allocation callback to torch's caching allocator."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), device=self.device, stream=stream))
+            except Exception:
+                return None
+
+        def _free(ptr, stream, ctx):
+            try:
+                torch.cuda.caching_allocator_delete(ptr)
+            except Exception:
+                pass
+
+        self._a = _abi.ALLOC_FN(_alloc)
+        self._f = _abi.FREE_FN(_free)
+        self.struct = _abi.Allocator(self._a, self._f, None)
+
+
+class Sim:
+    """One batch of instances on the current CUDA device and stream."""
+
+    def __init__(self, cfg, precision="fp32", stream=None, use_torch_allocator=True):
+        import torch
+        self._lib = _abi.load()
+        cfgs = cfg if isinstance(cfg, (list, tuple)) else [cfg]
+        self.cfgs = [dict(c) for c in cfgs]
+        arr = (_abi.Config * len(cfgs))(*[make_config(c, precision) for c in cfgs])
+        self._cfg_arr = arr
+        dev = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._alloc = _TorchAllocator(dev) if use_torch_allocator else None
+        h = C.c_void_p()
+        rc = self._lib.apic_create_batch(arr, len(cfgs), C.c_void_p(self.stream.cuda_stream),
+                                         C.byref(self._alloc.struct) if self._alloc else None, C.byref(h))
+        if rc != 0:
+            raise ApicError(rc, "apic_create failed")
+        self.h = h
+        self.n_inst = len(cfgs)
+
+    def _check(self, rc):
+        if rc != 0:
+            msg = self._lib.apic_last_error(self.h)
+            raise ApicError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.apic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- the ABI, one method per entry point ----
+    def inject(self, species, n, mode=_abi.LOAD_VOLUME, state=None, instance=0):
+        ptr = None
+        if mode == _abi.EXPLICIT:
+            st = np.ascontiguousarray(state, dtype=np.float64).reshape(-1, 5)
+            n = st.shape[0]
+            ptr = st.ctypes.data_as(C.POINTER(C.c_double))
+        self._check(self._lib.apic_inject(self.h, instance, species, int(n), mode, ptr))
+
+    def load_volume(self, species, n, instance=0):
+        self.inject(species, n, _abi.LOAD_VOLUME, instance=instance)
+
+    def add_particles(self, species, state, instance=0):
+        self.inject(species, 0, _abi.EXPLICIT, state=state, instance=instance)
+
+    def step(self, n=1):
+        self._check(self._lib.apic_step(self.h, int(n)))
+
+    def tallies(self, instance=0, history=True):
+        c = self.cfgs[instance]
+        ns, n2 = len(c["species"]), int(c["n2"])
+        bins = np.zeros(ns * n2 * _abi.NT)
+        cap = int(c.get("history_cap", 0) or 4096)
+        hist = np.zeros(cap * _abi.NH) if history else None
+        t = _abi.Tallies()
+        t.bins = bins.ctypes.data_as(C.POINTER(C.c_double))
+        if history:
+            t.history = hist.ctypes.data_as(C.POINTER(C.c_double))
+        t.history_rows = cap if history else 0
+        self._check(self._lib.apic_tallies(self.h, instance, C.byref(t)))
+        keys = ("loaded", "injected", "absorbed", "escaped", "resident", "dropped")
+        counts = [dict(zip(keys, [int(v) for v in t.counts[s]])) for s in range(ns)]
+        out = dict(bins=bins.reshape(ns, n2, _abi.NT), counts=counts, step=int(t.step), Q=t.grain_Q,
+                   FZ=t.grain_FZ, poisson_res=t.poisson_res, poisson_iters=int(t.poisson_iters))
+        if history:
+            out["history"] = hist[: int(t.history_rows) * _abi.NH].reshape(-1, _abi.NH)
+        return out
+
+    def solve_poisson(self, rho=None, instance=0):
+        c = self.cfgs[instance]
+        shape = (int(c["n1"]) + 1, int(c["n2"]) + 1)
+        phi = np.zeros(shape)
+        r = None
+        if rho is not None:
+            rr = np.ascontiguousarray(rho, dtype=np.float64).reshape(shape)
+            r = rr.ctypes.data_as(C.POINTER(C.c_double))
+        self._check(self._lib.apic_solve_poisson(self.h, instance, r, phi.ctypes.data_as(C.POINTER(C.c_double))))
+        return phi
+
+    def particles(self, species, instance=0, capacity=None):
+        c = self.cfgs[instance]
+        sp = c["species"][species]
+        cap = capacity or int(sp.get("capacity", max(1024, int(1.6 * sp["n_init"]) + 4096)))
+        out = np.zeros((cap, 5))
+        n = C.c_int64()
+        self._check(self._lib.apic_get_particles(self.h, instance, species,
+                                                 out.ctypes.data_as(C.POINTER(C.c_double)), cap, C.byref(n)))
+        return out[: n.value]
+
+    def field(self, which, instance=0):
+        c = self.cfgs[instance]
+        idx = {"rho": 0, "phi": 1, "G1": 2, "G2": 3, "V": 4}[which]
+        out = np.zeros((int(c["n1"]) + 1, int(c["n2"]) + 1))
+        self._check(self._lib.apic_get_field(self.h, instance, idx, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
