@@ -1,0 +1,306 @@
+"""Benchmark of the APIC particle-in-cell step on GB300.
+
+Metric: particle-steps/s of full steps (deposit, Poisson solve to the stated
+tolerance, gather, push, absorption tallies, escape, injection) on the dipole
+workload: alpha = 0.15 (a = 0.3), B = 1, 256 x 128 cells, 1e7 macro-particles
+per species, FP32 particles with the FP64-refined Poisson solve.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torch.distributed.run; every rank advances an independent
+replica (the path has no data exchange between GPUs), rank 0 prints one JSON
+line with the whole-job throughput.  The reference arm (--impl reference) is
+the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (full PIC step) FP32+refined vs FP64 at stated error; % HBM roofline"
+UNIT = "particle-steps/s"
+BYTES_PER_PARTICLE_STEP = 40  # FP32 state (x1, x2, vR, vZ, vTheta) read once and written once
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--particles", type=int, default=10_000_000, help="macro-particles per species")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(n_per_species):
+    from paper_2307_11107_gb300.workloads import dipole_256
+    return dipole_256("fp32", n_per_species)
+
+
+def run_oracle(cfg, n_per_species, steps):
+    """The FP64 CPU oracle as it stands, single thread, on `steps` steps of the
+    same workload with n_per_species macro-particles per species (the macro
+    weight follows n_per_species).  Returns (particle-steps/s, seconds)."""
+    import oracle
+    c = dict(cfg)
+    c["species"] = [dict(s, n_init=n_per_species) for s in cfg["species"]]
+    sim = oracle.Sim(c)
+    for sp in range(len(c["species"])):
+        sim.load_volume(sp, n_per_species)
+    adv = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        adv += sum(sim.count(sp) for sp in range(len(c["species"])))
+        sim.step(1)
+    dt = time.perf_counter() - t0
+    return adv / dt, dt
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cfg = workload(args.particles)
+    # bounded sample: keep the whole warm-up + timed run within ~2 minutes
+    # (the oracle advances ~1e7 particle-steps/s on one core).
+    steps = max(1, args.steps)
+    n = int(max(2000, min(args.particles, 5.0e8 / (2 * steps))))
+    val, secs = run_oracle(cfg, n, steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["name"], "alpha": cfg["alpha"], "grid": [cfg["n1"], cfg["n2"]],
+                   "particles_per_species": n, "sample": "full steps with %d macro-particles per species" % n},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d steps, %d macro-particles per species, 256x128 grid" % (steps, n)},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = dist
+    import paper_2307_11107_gb300 as apic
+    apic.build()
+    cfg = workload(args.particles)
+    cfg["instance"] = rank  # independent replica per rank
+    cfg["history_cap"] = max(4096, args.steps + args.warmup + 8)
+    sim = apic.Sim(cfg)
+    for sp in range(2):
+        sim.load_volume(sp, args.particles)
+    sim.step(args.warmup)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    s0 = sim.stats()
+    with ClockSampler(local) as clk:
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    s1 = sim.stats()
+    t = sim.tallies()
+    hist = t["history"]
+    # particles advanced in timed step k = resident count after step k-1
+    res = hist[-(args.steps + 1):-1, 7] + hist[-(args.steps + 1):-1, 8]
+    advanced = float(res.sum())
+    local_val = advanced / (ms / 1e3)
+    sec = ms / 1e3
+    if pg is not None:
+        tt = torch.tensor([advanced, sec], dtype=torch.float64, device="cuda")
+        adv_t = tt.clone()
+        pg.all_reduce(adv_t)  # sum of particles advanced
+        sec_t = tt.clone()
+        pg.all_reduce(sec_t, op=pg.ReduceOp.MAX)
+        total_adv, sec = float(adv_t[0].item()), float(sec_t[1].item())
+    else:
+        total_adv = advanced
+    value = total_adv / sec
+    loop_iters = s1["poisson_loop_iters"] - s0["poisson_loop_iters"]
+    launches = args.steps * s1["kernels_per_step"] + loop_iters * s1["kernels_per_iter"]
+
+    # roofline of the dominant kernel (push): CUDA events around its phase graph
+    kt = min(args.steps, 100)
+    sim.step_timed(kt)
+    st = sim.stats()
+    push_ms = st["phase_ms"]["push"] / kt
+    n_avg = float(res.mean())
+    peaks, src = measured_peaks()
+    achieved = BYTES_PER_PARTICLE_STEP * n_avg / (push_ms / 1e3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "push_traffic.json")) as f:
+            tr = json.load(f)
+        traffic = tr["dram_bytes_per_particle"] * n_avg
+    except Exception:
+        pass
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": "k_push",
+            "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP, "peak_source": src,
+            "push_ms": push_ms, "phase_ms_per_step": {k: v / kt for k, v in st["phase_ms"].items()}}
+
+    # end to end through the public API: initial state uploaded from pinned host
+    # memory, then per step apic_step + apic_tallies (bins, counts, history row)
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        states = [sim.particles(sp) for sp in range(2)]
+        pinned = []
+        for stt in states:
+            pt = torch.empty(stt.shape, dtype=torch.float64, pin_memory=True)
+            pt.numpy()[:] = stt
+            pinned.append(pt)
+        cfg2 = dict(cfg, history_cap=64)
+        sim.close()
+        del sim
+        torch.cuda.synchronize()
+        sim2 = apic.Sim(cfg2)
+        ke = min(args.steps, 500)
+        h2d = sum(p.numel() * 8 for p in pinned)
+        barrier()
+        t0 = time.perf_counter()
+        for sp in range(2):
+            sim2.add_particles(sp, pinned[sp].numpy())
+        adv2 = 0.0
+        d2h = 0
+        for k in range(ke):
+            sim2.step(1)
+            tt2 = sim2.tallies(history=True)
+            adv2 += tt2["history"][-1, 7] + tt2["history"][-1, 8] if k < ke - 1 else 0.0
+            d2h = tt2["bins"].nbytes + tt2["history"][-1:].nbytes + 12 * 8
+        barrier()
+        t1 = time.perf_counter()
+        adv2 += float(sum(s.shape[0] for s in states))
+        e2e = {"value": adv2 / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d // ke, "d2h_bytes_per_step": d2h,
+               "steps": ke, "note": "initial state uploaded once from pinned host memory inside the timed region"}
+        sim2.close()
+    else:
+        sim.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        n = 1_000_000
+        val, secs = run_oracle(cfg, n, 10)
+        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "10 full steps of the same workload with 1e6 macro-particles per species (FP64, 1 thread)",
+               "seconds": secs}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg["name"], "alpha": cfg["alpha"], "a": 2 * cfg["alpha"], "B": cfg["B"],
+                       "grid_cells": [cfg["n1"], cfg["n2"]], "particles_per_species": args.particles,
+                       "poisson_tol": cfg["poisson_tol"], "precision": "FP32 particles, FP32 multigrid in FP64 BiCGSTAB",
+                       "l2": "inputs larger than L2 (particle state %.0f MB)" % (2 * args.particles * 20 / 1e6),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "poisson_loop_iters": int(loop_iters), "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

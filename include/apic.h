@@ -180,8 +180,28 @@ int apic_get_field(apic_sim* sim, int32_t instance, int32_t which, double* out);
 /* Message of the last error (static storage of the object; never NULL). */
 const char* apic_last_error(const apic_sim* sim);
 
-/* Number of instances, and the library's compiled-in maxima. */
+/* Number of instances of the batch. */
 int32_t apic_num_instances(const apic_sim* sim);
+
+#define APIC_NPHASE 6 /* deposit->rho, Poisson, node gradients + surface, push, inject, bookkeeping */
+
+typedef struct {
+  int64_t steps;                /* steps taken by the batch */
+  int64_t poisson_loop_iters;   /* Krylov-loop iterations executed, summed over steps */
+  int32_t kernels_per_step;     /* kernel launches per step outside the Krylov loop */
+  int32_t kernels_per_iter;     /* kernel launches per Krylov-loop iteration (incl. its test) */
+  int64_t timed_steps;          /* steps run by apic_step_timed */
+  double phase_ms[APIC_NPHASE]; /* CUDA-event time per phase, summed over timed steps */
+} apic_stats_t;
+
+/* Counters of the batch (launch counts, Krylov iterations, phase times). */
+int apic_stats(apic_sim* sim, apic_stats_t* out);
+
+/* As apic_step, but each phase is launched as its own CUDA graph with CUDA
+ * events recorded between phases on the simulation's stream, and the elapsed
+ * times are added to apic_stats_t.phase_ms.  Results are identical to
+ * apic_step. */
+int apic_step_timed(apic_sim* sim, int32_t n_steps);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,9 @@ NT, NH = 7, 10
 
 SYMBOLS = ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
            "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_last_error",
-           "apic_num_instances")
+           "apic_num_instances", "apic_stats", "apic_step_timed")
+NPHASE = 6
+PHASES = ("deposit_rho", "poisson", "fields", "push", "inject", "bookkeeping")
 
 
 class Species(C.Structure):
@@ -53,6 +55,11 @@ class Tallies(C.Structure):
                 ("poisson_iters", C.c_int32), ("pad", C.c_int32)]
 
 
+class Stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("poisson_loop_iters", C.c_int64), ("kernels_per_step", C.c_int32),
+                ("kernels_per_iter", C.c_int32), ("timed_steps", C.c_int64), ("phase_ms", C.c_double * NPHASE)]
+
+
 _lib = None
 
 
@@ -78,8 +85,10 @@ def load():
     L.apic_last_error.restype = C.c_char_p
     L.apic_num_instances.argtypes = [vp]
     L.apic_num_instances.restype = i32
+    L.apic_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.apic_step_timed.argtypes = [vp, i32]
     for name in ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
-                 "apic_solve_poisson", "apic_get_particles", "apic_get_field"):
+                 "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_stats", "apic_step_timed"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

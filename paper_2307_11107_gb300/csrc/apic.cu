@@ -185,6 +185,12 @@ struct apic_sim {
   int push_grid = 0;
   double* phi_save = nullptr;
   int32_t* h_err = nullptr;
+  bool cond_loop = true;              // Krylov loop as a graph while-node (else a fixed unrolled loop)
+  cudaGraphExec_t phase_exec[APIC_NPHASE] = {};
+  cudaGraph_t phase_graph[APIC_NPHASE] = {};
+  cudaEvent_t ev[APIC_NPHASE + 1] = {};
+  double phase_ms[APIC_NPHASE] = {};
+  long long timed_steps = 0;
 
   int fail(int code, const std::string& m) {
     if (status == APIC_OK) {
@@ -549,6 +555,7 @@ static int setup(apic_sim* S) {
   d.sol = (SolverState*)A(sizeof(SolverState) * ni);
   d.stp = (StepState*)A(sizeof(StepState) * ni);
   d.err = (int32_t*)A(sizeof(int32_t) * 4);
+  d.cnt = (long long*)A(sizeof(long long) * 8);
   d.x1 = A(R * slots);
   d.x2 = A(R * slots);
   d.vR = A(R * slots);
@@ -656,6 +663,12 @@ extern "C" int apic_destroy(apic_sim* S) {
   if (S->stream || S->cap) cudaStreamSynchronize(S->stream);
   if (S->exec) cudaGraphExecDestroy(S->exec);
   if (S->graph) cudaGraphDestroy(S->graph);
+  for (int p = 0; p < APIC_NPHASE; ++p) {
+    if (S->phase_exec[p]) cudaGraphExecDestroy(S->phase_exec[p]);
+    if (S->phase_graph[p]) cudaGraphDestroy(S->phase_graph[p]);
+  }
+  for (int p = 0; p <= APIC_NPHASE; ++p)
+    if (S->ev[p]) cudaEventDestroy(S->ev[p]);
   S->dfree_all();
   cudaStreamSynchronize(S->stream);
   if (S->cap) cudaStreamDestroy(S->cap);
@@ -678,62 +691,80 @@ static void enqueue_solver_iterations_fixed(apic_sim* S, cudaStream_t s) {
   }
 }
 
-// One step: deposit -> Poisson -> gradients/surface -> push -> inject -> bookkeeping.
+// Inside an open capture on stream s: a while-node whose body is one Krylov
+// iteration followed by the test kernel that sets the loop condition.
 template <class Real>
-static bool capture_step(apic_sim* S) {
-  cudaStream_t s = S->cap;
-  if (!S->ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture")) return false;
-  launch_rho<Real>(S->d, s);
-  launch_bicg_init<Real>(S->d, s);
-  bool cond_ok = false;
-  {
-    cudaStreamCaptureStatus st;
-    cudaGraph_t g = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t nd = 0;
-    if (cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd) == cudaSuccess) {
-      cudaGraphConditionalHandle h;
-      if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
-        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        cudaGraphNode_t cn;
-        if (cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp) == cudaSuccess) {
-          cudaGraph_t body = cp.conditional.phGraph_out[0];
-          if (cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies) ==
-                  cudaSuccess &&
-              cudaStreamBeginCaptureToGraph(S->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
-                  cudaSuccess) {
-            launch_bicg_iter<Real>(S->d, S->plan, S->cap2);
-            launch_bicg_check(S->d, h, 1, S->cap2);
-            cudaGraph_t tmp = nullptr;
-            cond_ok = cudaStreamEndCapture(S->cap2, &tmp) == cudaSuccess;
-          }
-        }
+static bool enqueue_solver_loop(apic_sim* S, cudaStream_t s) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess) return false;
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) return false;
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  if (cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp) != cudaSuccess) return false;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+    return false;
+  if (cudaStreamBeginCaptureToGraph(S->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess)
+    return false;
+  launch_bicg_iter<Real>(S->d, S->plan, S->cap2);
+  launch_bicg_check(S->d, h, 1, S->cap2);
+  cudaGraph_t tmp = nullptr;
+  return cudaStreamEndCapture(S->cap2, &tmp) == cudaSuccess;
+}
+
+// Kernels of phase p of one step (deposit->rho, Poisson, fields, push, inject, bookkeeping).
+template <class Real>
+static bool enqueue_phase(apic_sim* S, int p, cudaStream_t s) {
+  switch (p) {
+    case 0: launch_rho<Real>(S->d, s); break;
+    case 1:
+      launch_bicg_init<Real>(S->d, s);
+      if (S->cond_loop) {
+        if (!enqueue_solver_loop<Real>(S, s)) return false;
+      } else {
+        enqueue_solver_iterations_fixed<Real>(S, s);
       }
-    }
+      break;
+    case 2:
+      launch_gradients<Real>(S->d, s);
+      launch_surface(S->d, s);
+      break;
+    case 3: launch_push<Real>(S->d, S->push_grid, s); break;
+    case 4: launch_inject<Real>(S->d, S->max_inj, s); break;
+    case 5: launch_step_end(S->d, s); break;
   }
-  cudaGetLastError();
-  if (!cond_ok) {
-    // A capture that failed half-way is abandoned; retry with a fixed loop.
-    cudaGraph_t junk = nullptr;
-    cudaStreamEndCapture(s, &junk);
-    if (junk) cudaGraphDestroy(junk);
-    cudaGetLastError();
-    if (!S->ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture")) return false;
-    launch_rho<Real>(S->d, s);
-    launch_bicg_init<Real>(S->d, s);
-    enqueue_solver_iterations_fixed<Real>(S, s);
-  }
-  launch_gradients<Real>(S->d, s);
-  launch_surface(S->d, s);
-  launch_push<Real>(S->d, S->push_grid, s);
-  launch_inject<Real>(S->d, S->max_inj, s);
-  launch_step_end(S->d, s);
-  if (!S->ck(cudaStreamEndCapture(s, &S->graph), "end capture")) return false;
-  if (!S->ck(cudaGraphInstantiate(&S->exec, S->graph, 0), "graph instantiate")) return false;
   return true;
+}
+
+// Capture phases [p0, p1) into one executable graph.  If the while-node cannot
+// be built, the capture is redone once with a fixed, early-exiting loop.
+template <class Real>
+static bool capture(apic_sim* S, int p0, int p1, cudaGraph_t* graph, cudaGraphExec_t* exec) {
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    cudaStream_t s = S->cap;
+    if (!S->ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture")) return false;
+    bool ok = true;
+    for (int p = p0; p < p1 && ok; ++p) ok = enqueue_phase<Real>(S, p, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (ok && e == cudaSuccess) {
+      *graph = g;
+      return S->ck(cudaGraphInstantiate(exec, g, 0), "graph instantiate");
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (!S->cond_loop) return S->ck(e == cudaSuccess ? cudaErrorUnknown : e, "step capture");
+    S->cond_loop = false;  // retry without the conditional node
+  }
+  return false;
 }
 
 static int read_status(apic_sim* S) {
@@ -755,12 +786,71 @@ static int step_impl(apic_sim* S, int n) {
   }
   if (!S->exec) {
     if (!S->sync()) return S->status;
-    if (!capture_step<Real>(S)) return S->status;
+    if (!capture<Real>(S, 0, APIC_NPHASE, &S->graph, &S->exec)) return S->status;
   }
   for (int k = 0; k < n; ++k)
     if (!S->ck(cudaGraphLaunch(S->exec, S->stream), "graph launch")) return S->status;
   if (!S->ck(cudaGetLastError(), "launch")) return S->status;
   return read_status(S);
+}
+
+template <class Real>
+static int step_timed_impl(apic_sim* S, int n) {
+  if (S->dirty) {
+    if (!S->ck(cudaMemsetAsync(S->d.acc, 0, sizeof(unsigned long long) * 2 * S->d.total_nodes, S->stream), "memset"))
+      return S->status;
+    launch_deposit_all<Real>(S->d, S->push_grid, S->stream);
+    S->dirty = false;
+  }
+  if (!S->phase_exec[0]) {
+    if (!S->sync()) return S->status;
+    for (int p = 0; p < APIC_NPHASE; ++p)
+      if (!capture<Real>(S, p, p + 1, &S->phase_graph[p], &S->phase_exec[p])) return S->status;
+    for (int p = 0; p <= APIC_NPHASE; ++p)
+      if (!S->ck(cudaEventCreate(&S->ev[p]), "event create")) return S->status;
+  }
+  std::vector<float> acc(APIC_NPHASE, 0.0f);
+  for (int k = 0; k < n; ++k) {
+    S->ck(cudaEventRecord(S->ev[0], S->stream), "event record");
+    for (int p = 0; p < APIC_NPHASE; ++p) {
+      if (!S->ck(cudaGraphLaunch(S->phase_exec[p], S->stream), "graph launch")) return S->status;
+      S->ck(cudaEventRecord(S->ev[p + 1], S->stream), "event record");
+    }
+    if (!S->ck(cudaEventSynchronize(S->ev[APIC_NPHASE]), "event sync")) return S->status;
+    for (int p = 0; p < APIC_NPHASE; ++p) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, S->ev[p], S->ev[p + 1]);
+      S->phase_ms[p] += ms;
+    }
+  }
+  S->timed_steps += n;
+  return read_status(S);
+}
+
+extern "C" int apic_step_timed(apic_sim* S, int32_t n_steps) {
+  if (!S) return APIC_ERR_INVALID_ARG;
+  if (S->status != APIC_OK) return S->status;
+  if (n_steps < 0) return APIC_ERR_INVALID_ARG;
+  if (n_steps == 0) return APIC_OK;
+  return S->precision == APIC_FP64 ? step_timed_impl<double>(S, n_steps) : step_timed_impl<float>(S, n_steps);
+}
+
+extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
+  if (!S || !out) return APIC_ERR_INVALID_ARG;
+  long long cnt = 0;
+  StepState stp;
+  if (!S->sync() || !S->d2h(&cnt, S->d.cnt, 1) || !S->d2h(&stp, S->d.stp, 1) || !S->sync()) return S->status;
+  std::memset(out, 0, sizeof(*out));
+  out->steps = stp.step;
+  out->poisson_loop_iters = cnt;
+  int vcycle = S->plan.max_tail * 10 + 1;
+  out->kernels_per_iter = 6 + 2 * vcycle;
+  int most = 0;
+  for (const Inst& I : S->inst) most = std::max(most, I.max_iter);
+  out->kernels_per_step = 7 + (S->cond_loop ? 0 : most * out->kernels_per_iter);
+  out->timed_steps = S->timed_steps;
+  for (int p = 0; p < APIC_NPHASE; ++p) out->phase_ms[p] = S->phase_ms[p];
+  return APIC_OK;
 }
 
 extern "C" int apic_step(apic_sim* S, int32_t n_steps) {

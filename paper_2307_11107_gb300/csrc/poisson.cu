@@ -676,7 +676,10 @@ __global__ void k_bicg_check(DevPtrs d, cudaGraphConditionalHandle h, int use_ha
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(h, any ? 1u : 0u);
+  if (threadIdx.x == 0) {
+    d.cnt[0] += 1;
+    if (use_handle) cudaGraphSetConditional(h, any ? 1u : 0u);
+  }
 }
 
 template <class Real>

@@ -124,6 +124,17 @@ class Sim:
     def step(self, n=1):
         self._check(self._lib.apic_step(self.h, int(n)))
 
+    def step_timed(self, n=1):
+        self._check(self._lib.apic_step_timed(self.h, int(n)))
+
+    def stats(self):
+        st = _abi.Stats()
+        self._check(self._lib.apic_stats(self.h, C.byref(st)))
+        return dict(steps=int(st.steps), poisson_loop_iters=int(st.poisson_loop_iters),
+                    kernels_per_step=int(st.kernels_per_step), kernels_per_iter=int(st.kernels_per_iter),
+                    timed_steps=int(st.timed_steps),
+                    phase_ms=dict(zip(_abi.PHASES, [float(v) for v in st.phase_ms])))
+
     def tallies(self, instance=0, history=True):
         c = self.cfgs[instance]
         ns, n2 = len(c["species"]), int(c["n2"])
