@@ -203,6 +203,36 @@ int apic_stats(apic_sim* sim, apic_stats_t* out);
  * apic_step. */
 int apic_step_timed(apic_sim* sim, int32_t n_steps);
 
+/* ---- Charge deposit without device allocation --------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory (a component living inside another
+ * program's fixed device-memory budget, a framework that only hands out the
+ * buffers it manages, a loop that must not enter the allocator).
+ *
+ * rho[i][j] = qw * sum_p S_ij(p) / volume[i][j]: the cloud-in-cell weights S
+ * of the n particles at (x1[p], x2[p]) on the grid `grid` (n1 x n2 cells,
+ * x1 in [-1, x1_outer], x2 in [-1, 1]), the same weighing as apic_step's
+ * deposit, with 64-bit fixed-point sums.  x1, x2 (n doubles), volume and rho
+ * ((n1+1)(n2+1) doubles, row-major) are device pointers owned by the caller;
+ * work is queued on `stream` (a cudaStream_t) and the call returns without
+ * waiting.  No cudaMalloc, cudaFree or other allocating call is made.
+ *
+ * Scratch: one static accumulator of 2^20 nodes (8 MiB) per device, held
+ * from library load until process exit; grids with (n1+1)(n2+1) > 2^20 are
+ * rejected with APIC_ERR_INVALID_ARG.  Every call shares that accumulator and
+ * clears it first: calls that overlap on the GPU (different streams or host
+ * threads without ordering) race and give wrong densities.  The first call on
+ * each device looks up the accumulator's device address; make that first
+ * call before any stream capture.
+ * Errors: INVALID_ARG (NULL pointer, bad grid, too many nodes), CUDA. */
+typedef struct {
+  int32_t n1, n2;   /* cells in x1 and x2 */
+  double x1_outer;  /* outer boundary x1, in (-1, 0) */
+} apic_grid_t;
+
+int apic_deposit_static(const apic_grid_t* grid, const double* x1, const double* x2, int64_t n, double qw,
+                        const double* volume, double* rho, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

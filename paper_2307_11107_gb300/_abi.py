@@ -21,7 +21,7 @@ NT, NH = 7, 10
 
 SYMBOLS = ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
            "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_last_error",
-           "apic_num_instances", "apic_stats", "apic_step_timed")
+           "apic_num_instances", "apic_stats", "apic_step_timed", "apic_deposit_static")
 NPHASE = 6
 PHASES = ("deposit_rho", "poisson", "fields", "push", "inject", "bookkeeping")
 
@@ -53,6 +53,10 @@ class Tallies(C.Structure):
                 ("history_rows", C.c_int64), ("counts", (C.c_int64 * 6) * 2), ("step", C.c_int64),
                 ("grain_Q", C.c_double), ("grain_FZ", C.c_double), ("poisson_res", C.c_double),
                 ("poisson_iters", C.c_int32), ("pad", C.c_int32)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("n1", C.c_int32), ("n2", C.c_int32), ("x1_outer", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -87,8 +91,10 @@ def load():
     L.apic_num_instances.restype = i32
     L.apic_stats.argtypes = [vp, C.POINTER(Stats)]
     L.apic_step_timed.argtypes = [vp, i32]
+    L.apic_deposit_static.argtypes = [C.POINTER(Grid), vp, vp, i64, C.c_double, vp, vp, vp]
     for name in ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
-                 "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_stats", "apic_step_timed"):
+                 "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_stats", "apic_step_timed",
+                 "apic_deposit_static"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

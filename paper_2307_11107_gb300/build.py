@@ -5,6 +5,7 @@ Translation units (compiled in parallel):
   poisson.cu    twice: FP64 and FP32 multigrid preconditioner
   fields.cu     node fields and bookkeeping (FP64, -fmad=false)
   apic.cu       host set-up and the C ABI
+  deposit_static.cu  the deposit entry point that uses no caller-side allocation
 """
 import os
 import shutil
@@ -27,6 +28,7 @@ UNITS = [
     ("poisson.cu", "poisson_f32.o", ["-DAPIC_POISSON_REAL=float", "-DAPIC_POISSON_COMMON=0"]),
     ("fields.cu", "fields.o", ["-fmad=false"]),
     ("apic.cu", "apic.o", []),
+    ("deposit_static.cu", "deposit_static.o", ["-fmad=false"]),
 ]
 
 
