@@ -101,7 +101,8 @@ typedef struct {
   int32_t poisson_max_iter; /* BiCGSTAB iterations per step (0: 20) */
   int32_t sort_interval; /* sort particles by cell every this many steps (0: never) */
   int32_t history_cap;   /* rows of the per-step history ring (0: 4096) */
-  int32_t reserved[5];
+  int32_t poisson_guess; /* start of each step's solve: 0 previous phi, 1 linear extrapolation 2 phi^n - phi^n-1 */
+  int32_t reserved[4];
 } apic_config_t;
 
 typedef void* (*apic_alloc_fn)(size_t bytes, void* stream, void* ctx);

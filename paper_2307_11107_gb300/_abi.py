@@ -37,7 +37,7 @@ class Config(C.Structure):
                 ("n1", C.c_int32), ("n2", C.c_int32), ("n_species", C.c_int32), ("sp", Species * 2),
                 ("seed", C.c_uint64), ("instance", C.c_int32), ("precision", C.c_int32), ("flags", C.c_int32),
                 ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32), ("sort_interval", C.c_int32),
-                ("history_cap", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("history_cap", C.c_int32), ("poisson_guess", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

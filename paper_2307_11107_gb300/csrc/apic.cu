@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -59,39 +60,6 @@ int bits_for(long long v) {
 
 double x1_node_h(const Inst& I, int i) { return i == I.n1 ? I.x1_out : -1.0 + i * I.h1; }
 double x2_node_h(const Inst& I, int j) { return j == I.n2 ? 1.0 : -1.0 + j * I.h2; }
-
-// Dense inverse by Gauss-Jordan with partial pivoting (small coarsest level).
-bool invert(std::vector<double>& a, int n) {
-  std::vector<double> inv((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
-  for (int c = 0; c < n; ++c) {
-    int p = c;
-    for (int r = c + 1; r < n; ++r)
-      if (std::fabs(a[(size_t)r * n + c]) > std::fabs(a[(size_t)p * n + c])) p = r;
-    if (a[(size_t)p * n + c] == 0.0) return false;
-    if (p != c)
-      for (int k = 0; k < n; ++k) {
-        std::swap(a[(size_t)p * n + k], a[(size_t)c * n + k]);
-        std::swap(inv[(size_t)p * n + k], inv[(size_t)c * n + k]);
-      }
-    double piv = 1.0 / a[(size_t)c * n + c];
-    for (int k = 0; k < n; ++k) {
-      a[(size_t)c * n + k] *= piv;
-      inv[(size_t)c * n + k] *= piv;
-    }
-    for (int r = 0; r < n; ++r) {
-      if (r == c) continue;
-      double f = a[(size_t)r * n + c];
-      if (f == 0.0) continue;
-      for (int k = 0; k < n; ++k) {
-        a[(size_t)r * n + k] -= f * a[(size_t)c * n + k];
-        inv[(size_t)r * n + k] -= f * inv[(size_t)c * n + k];
-      }
-    }
-  }
-  a.swap(inv);
-  return true;
-}
 
 // Host stencil of one level: kSt arrays of nodes.
 struct HostLevel {
@@ -176,8 +144,13 @@ struct apic_sim {
   std::vector<void*> blocks;
   DevPtrs d{};
   SolvePlan plan{};
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph[2] = {};
+  cudaGraphExec_t exec[2] = {};       // one step graph per particle-buffer parity
+  cudaGraph_t sort_graph[2] = {};
+  cudaGraphExec_t sort_exec[2] = {};
+  int par = 0;                        // which buffer holds the particles (1: the y arrays)
+  int sort_interval = 0;
+  long long host_step = 0;
   bool dirty = true;
   int status = APIC_OK;
   std::string msg = "ok";
@@ -186,8 +159,9 @@ struct apic_sim {
   double* phi_save = nullptr;
   int32_t* h_err = nullptr;
   bool cond_loop = true;              // Krylov loop as a graph while-node (else a fixed unrolled loop)
-  cudaGraphExec_t phase_exec[APIC_NPHASE] = {};
-  cudaGraph_t phase_graph[APIC_NPHASE] = {};
+  int coop = 0;                       // CTAs of the cooperative whole-solve kernel (0: per-phase kernels)
+  cudaGraphExec_t phase_exec[2][APIC_NPHASE] = {};
+  cudaGraph_t phase_graph[2][APIC_NPHASE] = {};
   cudaEvent_t ev[APIC_NPHASE + 1] = {};
   double phase_ms[APIC_NPHASE] = {};
   long long timed_steps = 0;
@@ -237,6 +211,18 @@ struct apic_sim {
     return ck(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToHost, stream), "D2H");
   }
   bool sync() { return ck(cudaStreamSynchronize(stream), "stream sync"); }
+  // Device pointers with the particle buffers of parity p in front.
+  DevPtrs view(int p) const {
+    DevPtrs v = d;
+    if (p) {
+      std::swap(v.x1, v.y1);
+      std::swap(v.x2, v.y2);
+      std::swap(v.vR, v.yR);
+      std::swap(v.vZ, v.yZ);
+      std::swap(v.vT, v.yT);
+    }
+    return v;
+  }
 };
 
 namespace {
@@ -382,7 +368,7 @@ static int setup(apic_sim* S) {
   std::vector<std::vector<HostLevel>> levels(ni);
   std::vector<std::vector<double>> cinvs(ni);
   long long total_nodes = 0, level_nodes = 0, tab_total = 0, bins_total = 0, hist_total = 0, en_total = 0,
-            cinv_total = 0, slots = 0;
+            cinv_total = 0, slots = 0, total_cells = 0, fac_total = 0;
   int pop_index = 0;
   for (int k = 0; k < ni; ++k) {
     const apic_config_t& c = S->cfg[k];
@@ -409,6 +395,7 @@ static int setup(apic_sim* S) {
     I.seed = c.seed;
     I.tag = c.instance;
     I.flags = c.flags;
+    I.guess = c.poisson_guess == 1 ? 1 : 0;
     I.n_species = c.n_species;
     I.pop0 = pop_index;
     I.hist_cap = c.history_cap > 0 ? c.history_cap : 4096;
@@ -428,18 +415,15 @@ static int setup(apic_sim* S) {
     while (true) {
       const HostLevel& F = levels[k].back();
       if ((int)levels[k].size() >= kMaxLevels) break;
+      if ((long long)(F.n1 - 1) * F.N2 <= kMaxCoarse) break;
       if (F.n1 % 2 || F.n2 % 2 || F.n1 < 8 || F.n2 < 4) break;
       HostLevel C;
       if (!galerkin(F, C, levels[k].size() == 1)) return S->fail(APIC_ERR_INVALID_ARG, "coarse stencil wider than 3x3");
       levels[k].push_back(std::move(C));
     }
     I.n_levels = (int)levels[k].size();
+    // every level but the coarsest is smoothed; the coarsest is solved with its dense inverse
     I.tail_level = I.n_levels - 1;
-    for (int l = 0; l < I.n_levels; ++l)
-      if (levels[k][l].nodes() <= kTailNodes) {
-        I.tail_level = l;
-        break;
-      }
     for (int l = 0; l < I.n_levels; ++l) {
       Level& L = I.lv[l];
       const HostLevel& H = levels[k][l];
@@ -451,12 +435,17 @@ static int setup(apic_sim* S) {
       L.st = (long long)kSt * level_nodes;
       L.pole_extra = l == 0 ? 1 : 0;
       level_nodes += H.nodes();
+      int k1 = (H.n1 - 1 + 31) / 32, k2 = (H.n2 + 1 + 31) / 32;
+      L.fac[0] = fac_total;
+      fac_total += (long long)H.N2 * line_fac_stride(k1);
+      L.fac[1] = fac_total;
+      fac_total += (long long)H.N1 * line_fac_stride(k2);
     }
     // coarsest dense inverse over rows 1..n1-1
     {
       const HostLevel& H = levels[k].back();
       int nu = (H.n1 - 1) * H.N2;
-      if (nu > kMaxCoarse) return S->fail(APIC_ERR_INVALID_ARG, "coarsest multigrid level too large (grid not divisible)");
+      if (nu > kMaxDense) return S->fail(APIC_ERR_INVALID_ARG, "coarsest multigrid level too large (grid not divisible)");
       std::vector<double> A((size_t)nu * nu, 0.0);
       for (int i = 1; i < H.n1; ++i)
         for (int j = 0; j <= H.n2; ++j) {
@@ -473,8 +462,7 @@ static int setup(apic_sim* S) {
             if (j == H.n2) A[(size_t)r * nu + (i - 1) * H.N2 + H.n2 - 2] += s;
           }
         }
-      if (!invert(A, nu)) return S->fail(APIC_ERR_INVALID_ARG, "singular coarsest operator");
-      cinvs[k] = std::move(A);
+      cinvs[k] = std::move(A);  // inverted on the GPU below
       I.coarse_n = nu;
       I.cinv_off = cinv_total;
       cinv_total += (long long)nu * nu;
@@ -499,6 +487,9 @@ static int setup(apic_sim* S) {
       else P.fbits = 2 * std::min(20, (62 - lg) / 2);
       P.dep_scale = sp.q * P.w * std::ldexp(1.0, -P.fbits);
       P.acc_off = 2 * I.node_off + (long long)s * I.nodes;
+      P.cells = (long long)c.n1 * c.n2;
+      P.cell_off = total_cells;
+      total_cells += P.cells;
       S->max_inj = std::max(S->max_inj, (long long)std::ceil(P.lam) + 2);
       S->pop.push_back(P);
       ++pop_index;
@@ -524,21 +515,15 @@ static int setup(apic_sim* S) {
       k2 = std::max(k2, (L.n2 + 1 + 31) / 32);
       nodes = std::max(nodes, (long long)L.N1 * L.N2);
     }
-    pl.x1_blocks[l] = std::max(1, (x1l + 3) / 4);
-    pl.x2_blocks[l] = std::max(1, (x2l + 3) / 4);
+    pl.x1_blocks[l] = std::max(1, x1l);
+    pl.x2_blocks[l] = std::max(1, x2l);
     pl.x1_k[l] = k1;
     pl.x2_k[l] = k2;
     pl.node_blocks[l] = (int)std::min<long long>(1024, std::max<long long>(1, (nodes + 255) / 256));
   }
   pl.tail_threads = 512;
   pl.tail_k = 1;
-  for (const Inst& I : S->inst)
-    for (int l = I.tail_level; l < I.n_levels; ++l) {
-      pl.tail_k = std::max(pl.tail_k, (I.lv[l].n1 - 1 + 31) / 32);
-      pl.tail_k = std::max(pl.tail_k, (I.lv[l].n2 + 1 + 31) / 32);
-    }
-  while (pl.tail_threads > 64 && (size_t)(pl.tail_threads / 32) * 128 * pl.tail_k * sizeof(Real) > 200 * 1024)
-    pl.tail_threads /= 2;
+  pl.tail_bytes = 0;
   if (!S->ck(set_poisson_smem<Real>(pl), "cudaFuncSetAttribute(smem)")) return S->status;
 
   // ---- device memory ----
@@ -562,7 +547,21 @@ static int setup(apic_sim* S) {
   d.vZ = A(R * slots);
   d.vT = A(R * slots);
   d.holes = (int32_t*)A(sizeof(int32_t) * slots);
-  double** node_arrays[] = {&d.rho, &d.phi, &d.V, &d.bbc, &d.rscale, &d.b, &d.r, &d.rh, &d.p, &d.v, &d.s, &d.t, &d.ph, &d.sh};
+  d.total_cells = total_cells;
+  for (const apic_config_t& c : S->cfg)
+    if (c.sort_interval > 0) S->sort_interval = S->sort_interval ? std::min(S->sort_interval, c.sort_interval) : c.sort_interval;
+  if (S->sort_interval > 0) {
+    d.y1 = A(R * slots);
+    d.y2 = A(R * slots);
+    d.yR = A(R * slots);
+    d.yZ = A(R * slots);
+    d.yT = A(R * slots);
+    d.keys = (int32_t*)A(sizeof(int32_t) * slots);
+    d.cell_cnt = (unsigned*)A(sizeof(unsigned) * total_cells);
+    d.cell_off = (unsigned long long*)A(sizeof(unsigned long long) * (total_cells + 1));
+    d.scan_tmp = (unsigned long long*)A(sizeof(unsigned long long) * ((total_cells + 1023) / 1024 + 1));
+  }
+  double** node_arrays[] = {&d.rho, &d.phi, &d.phi_prev, &d.V, &d.bbc, &d.rscale, &d.b, &d.r, &d.rh, &d.p, &d.v, &d.s, &d.t, &d.ph, &d.sh};
   for (double** a : node_arrays) *a = (double*)A(sizeof(double) * total_nodes);
   S->phi_save = (double*)A(sizeof(double) * total_nodes);
   d.st64 = (double*)A(sizeof(double) * kSt * total_nodes);
@@ -572,11 +571,14 @@ static int setup(apic_sim* S) {
   d.e = A(R * level_nodes);
   d.f = A(R * level_nodes);
   d.cinv = A(R * std::max<long long>(1, cinv_total));
+  d.fac = A(R * std::max<long long>(1, fac_total));
   d.tab = (double*)A(sizeof(double) * tab_total);
   d.bins = (double*)A(sizeof(double) * std::max<long long>(1, bins_total));
   d.hist = (double*)A(sizeof(double) * hist_total);
   d.en = (double*)A(sizeof(double) * en_total);
   d.red = (double*)A(sizeof(double) * ni * kNRed * kRedBlocks);
+  d.cred = (double*)A(sizeof(double) * ni * kNRed * kCoopMaxBlocks);
+  d.bar = (unsigned*)A(sizeof(unsigned) * 4);
   if (S->status != APIC_OK) return S->status;
 
   // ---- uploads ----
@@ -595,8 +597,29 @@ static int setup(apic_sim* S) {
       tmp.assign(H.st.begin(), H.st.end());
       S->h2d((Real*)d.st + I.lv[l].st, tmp.data(), tmp.size());
     }
-    tmp.assign(cinvs[k].begin(), cinvs[k].end());
-    S->h2d((Real*)d.cinv + I.cinv_off, tmp.data(), tmp.size());
+    {
+      // Gauss-Jordan on the GPU: n x 2n FP64 workspace, result stored in the particle precision
+      int nu = I.coarse_n;
+      double* work = (double*)S->dalloc(sizeof(double) * 2 * (size_t)nu * nu);
+      double* fbuf = (double*)S->dalloc(sizeof(double) * (size_t)nu);
+      if (!work || !fbuf) return S->status;
+      std::vector<double> aug((size_t)nu * 2 * nu, 0.0);
+      for (int r = 0; r < nu; ++r) {
+        std::memcpy(aug.data() + (size_t)r * 2 * nu, cinvs[k].data() + (size_t)r * nu, sizeof(double) * nu);
+        aug[(size_t)r * 2 * nu + nu + r] = 1.0;
+      }
+      S->h2d(work, aug.data(), aug.size());
+      if (!S->ck(launch_dense_inverse<Real>(work, fbuf, nu, (Real*)d.cinv + I.cinv_off, S->stream), "dense inverse"))
+        return S->status;
+      if (!S->sync()) return S->status;
+      // release the workspace
+      for (void* q : {(void*)fbuf, (void*)work}) {
+        auto it = std::find(S->blocks.begin(), S->blocks.end(), q);
+        if (it != S->blocks.end()) S->blocks.erase(it);
+        if (S->have_alloc) S->alloc.free(q, (void*)S->stream, S->alloc.ctx);
+        else cudaFreeAsync(q, S->stream);
+      }
+    }
     // initial potential: the vacuum solution, linear in x1 (phi = 0 without field)
     std::vector<double> phi((size_t)I.nodes, 0.0);
     if (!(I.flags & APIC_NO_FIELD))
@@ -607,10 +630,32 @@ static int setup(apic_sim* S) {
     // tables are synchronous inputs of host vectors: wait before they go out of scope
     if (!S->sync()) return S->status;
   }
+  // line factorisations of every level (constant in time)
+  for (int l = 0; l < kMaxLevels; ++l) {
+    int lines1 = 0, lines2 = 0, k1 = 1, k2 = 1;
+    bool any = false;
+    for (const Inst& I : S->inst) {
+      if (l >= I.n_levels) continue;
+      any = true;
+      lines1 = std::max(lines1, I.lv[l].N2);
+      lines2 = std::max(lines2, I.lv[l].N1);
+      k1 = std::max(k1, (I.lv[l].n1 - 1 + 31) / 32);
+      k2 = std::max(k2, (I.lv[l].n2 + 1 + 31) / 32);
+    }
+    if (!any) break;
+    launch_line_factor<Real>(d, l, 0, lines1, k1, S->stream);
+    launch_line_factor<Real>(d, l, 1, lines2, k2, S->stream);
+  }
+  if (!S->ck(cudaGetLastError(), "line factorisation")) return S->status;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   S->push_grid = std::max(1, sms) * 4;
+  // the whole Poisson solve as one cooperative kernel, unless disabled or not co-residable
+  const char* env = std::getenv("APIC_SOLVER");
+  bool want_coop = !(env && std::string(env) == "kernels") && ni <= kCoopMaxInst;
+  S->coop = want_coop ? coop_blocks<Real>(S->plan, sms) : 0;
+  cudaGetLastError();
   return S->sync() ? APIC_OK : S->status;
 }
 
@@ -661,11 +706,15 @@ extern "C" int apic_create(const apic_config_t* cfg, void* stream, const apic_al
 extern "C" int apic_destroy(apic_sim* S) {
   if (!S) return APIC_OK;
   if (S->stream || S->cap) cudaStreamSynchronize(S->stream);
-  if (S->exec) cudaGraphExecDestroy(S->exec);
-  if (S->graph) cudaGraphDestroy(S->graph);
-  for (int p = 0; p < APIC_NPHASE; ++p) {
-    if (S->phase_exec[p]) cudaGraphExecDestroy(S->phase_exec[p]);
-    if (S->phase_graph[p]) cudaGraphDestroy(S->phase_graph[p]);
+  for (int q = 0; q < 2; ++q) {
+    if (S->exec[q]) cudaGraphExecDestroy(S->exec[q]);
+    if (S->graph[q]) cudaGraphDestroy(S->graph[q]);
+    if (S->sort_exec[q]) cudaGraphExecDestroy(S->sort_exec[q]);
+    if (S->sort_graph[q]) cudaGraphDestroy(S->sort_graph[q]);
+    for (int p = 0; p < APIC_NPHASE; ++p) {
+      if (S->phase_exec[q][p]) cudaGraphExecDestroy(S->phase_exec[q][p]);
+      if (S->phase_graph[q][p]) cudaGraphDestroy(S->phase_graph[q][p]);
+    }
   }
   for (int p = 0; p <= APIC_NPHASE; ++p)
     if (S->ev[p]) cudaEventDestroy(S->ev[p]);
@@ -682,19 +731,19 @@ extern "C" int apic_destroy(apic_sim* S) {
 // Stepping.
 // ---------------------------------------------------------------------------
 template <class Real>
-static void enqueue_solver_iterations_fixed(apic_sim* S, cudaStream_t s) {
+static void enqueue_solver_iterations_fixed(apic_sim* S, const DevPtrs& d, cudaStream_t s) {
   int most = 0;
   for (const Inst& I : S->inst) most = std::max(most, I.max_iter);
   for (int it = 0; it < most; ++it) {
-    launch_bicg_iter<Real>(S->d, S->plan, s);
-    launch_bicg_check(S->d, 0, 0, s);
+    launch_bicg_iter<Real>(d, S->plan, s);
+    launch_bicg_check(d, 0, 0, s);
   }
 }
 
 // Inside an open capture on stream s: a while-node whose body is one Krylov
 // iteration followed by the test kernel that sets the loop condition.
 template <class Real>
-static bool enqueue_solver_loop(apic_sim* S, cudaStream_t s) {
+static bool enqueue_solver_loop(apic_sim* S, const DevPtrs& d, cudaStream_t s) {
   cudaStreamCaptureStatus st;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -714,32 +763,37 @@ static bool enqueue_solver_loop(apic_sim* S, cudaStream_t s) {
   if (cudaStreamBeginCaptureToGraph(S->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
       cudaSuccess)
     return false;
-  launch_bicg_iter<Real>(S->d, S->plan, S->cap2);
-  launch_bicg_check(S->d, h, 1, S->cap2);
+  launch_bicg_iter<Real>(d, S->plan, S->cap2);
+  launch_bicg_check(d, h, 1, S->cap2);
   cudaGraph_t tmp = nullptr;
   return cudaStreamEndCapture(S->cap2, &tmp) == cudaSuccess;
 }
 
 // Kernels of phase p of one step (deposit->rho, Poisson, fields, push, inject, bookkeeping).
 template <class Real>
-static bool enqueue_phase(apic_sim* S, int p, cudaStream_t s) {
+static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) {
   switch (p) {
-    case 0: launch_rho<Real>(S->d, s); break;
+    case 0: launch_rho<Real>(d, s); break;
     case 1:
-      launch_bicg_init<Real>(S->d, s);
+      if (S->coop > 0) {
+        if (launch_solve_coop<Real>(d, S->plan, S->coop, s) != cudaSuccess) return false;
+        break;
+      }
+      launch_bicg_init<Real>(d, s);
       if (S->cond_loop) {
-        if (!enqueue_solver_loop<Real>(S, s)) return false;
+        if (!enqueue_solver_loop<Real>(S, d, s)) return false;
       } else {
-        enqueue_solver_iterations_fixed<Real>(S, s);
+        enqueue_solver_iterations_fixed<Real>(S, d, s);
       }
       break;
     case 2:
-      launch_gradients<Real>(S->d, s);
-      launch_surface(S->d, s);
+      launch_gradients<Real>(d, s);
+      launch_surface(d, s);
       break;
-    case 3: launch_push<Real>(S->d, S->push_grid, s); break;
-    case 4: launch_inject<Real>(S->d, S->max_inj, s); break;
-    case 5: launch_step_end(S->d, s); break;
+    case 3: launch_push<Real>(d, S->push_grid, s); break;
+    case 4: launch_inject<Real>(d, S->max_inj, s); break;
+    case 5: launch_step_end(d, s); break;
+    case 6: launch_sort<Real>(d, S->push_grid, s); break;  // not a step phase: the particle sort
   }
   return true;
 }
@@ -747,12 +801,12 @@ static bool enqueue_phase(apic_sim* S, int p, cudaStream_t s) {
 // Capture phases [p0, p1) into one executable graph.  If the while-node cannot
 // be built, the capture is redone once with a fixed, early-exiting loop.
 template <class Real>
-static bool capture(apic_sim* S, int p0, int p1, cudaGraph_t* graph, cudaGraphExec_t* exec) {
+static bool capture(apic_sim* S, const DevPtrs& d, int p0, int p1, cudaGraph_t* graph, cudaGraphExec_t* exec) {
   for (int attempt = 0; attempt < 2; ++attempt) {
     cudaStream_t s = S->cap;
     if (!S->ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture")) return false;
     bool ok = true;
-    for (int p = p0; p < p1 && ok; ++p) ok = enqueue_phase<Real>(S, p, s);
+    for (int p = p0; p < p1 && ok; ++p) ok = enqueue_phase<Real>(S, d, p, s);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g);
     if (ok && e == cudaSuccess) {
@@ -773,49 +827,75 @@ static int read_status(apic_sim* S) {
   if (e & kErrCapacity) return S->fail(APIC_ERR_CAPACITY, "particle capacity exceeded");
   if (e & kErrNonFinite) return S->fail(APIC_ERR_NONFINITE, "non-finite field or residual");
   if (e & kErrNotConverged) return S->fail(APIC_ERR_NOT_CONVERGED, "Poisson iteration limit reached");
+  if (e & kErrTimeout) return S->fail(APIC_ERR_TIMEOUT, "grid barrier of the cooperative solver timed out");
   return APIC_OK;
 }
 
 template <class Real>
+static bool redeposit(apic_sim* S) {
+  if (!S->dirty) return true;
+  if (!S->ck(cudaMemsetAsync(S->d.acc, 0, sizeof(unsigned long long) * 2 * S->d.total_nodes, S->stream), "memset"))
+    return false;
+  launch_deposit_all<Real>(S->view(S->par), S->push_grid, S->stream);
+  S->dirty = false;
+  return true;
+}
+
+template <class Real>
+static bool ensure_graphs(apic_sim* S) {
+  if (S->exec[0]) return true;
+  if (!S->sync()) return false;
+  int npar = S->sort_interval > 0 ? 2 : 1;
+  for (int p = 0; p < npar; ++p) {
+    DevPtrs v = S->view(p);
+    if (!capture<Real>(S, v, 0, APIC_NPHASE, &S->graph[p], &S->exec[p])) return false;
+    if (S->sort_interval > 0 && !capture<Real>(S, v, 6, 7, &S->sort_graph[p], &S->sort_exec[p])) return false;
+  }
+  return true;
+}
+
+// Sort (when due) and swap the particle buffers; then one step graph.
+template <class Real>
+static bool launch_step(apic_sim* S, cudaGraphExec_t const* step_exec) {
+  if (S->sort_interval > 0 && S->host_step % S->sort_interval == 0) {
+    if (!S->ck(cudaGraphLaunch(S->sort_exec[S->par], S->stream), "sort launch")) return false;
+    S->par ^= 1;
+  }
+  if (step_exec && !S->ck(cudaGraphLaunch(step_exec[S->par], S->stream), "graph launch")) return false;
+  S->host_step += 1;
+  return true;
+}
+
+template <class Real>
 static int step_impl(apic_sim* S, int n) {
-  if (S->dirty) {
-    if (!S->ck(cudaMemsetAsync(S->d.acc, 0, sizeof(unsigned long long) * 2 * S->d.total_nodes, S->stream), "memset"))
-      return S->status;
-    launch_deposit_all<Real>(S->d, S->push_grid, S->stream);
-    S->dirty = false;
-  }
-  if (!S->exec) {
-    if (!S->sync()) return S->status;
-    if (!capture<Real>(S, 0, APIC_NPHASE, &S->graph, &S->exec)) return S->status;
-  }
+  if (!redeposit<Real>(S) || !ensure_graphs<Real>(S)) return S->status;
   for (int k = 0; k < n; ++k)
-    if (!S->ck(cudaGraphLaunch(S->exec, S->stream), "graph launch")) return S->status;
+    if (!launch_step<Real>(S, S->exec)) return S->status;
   if (!S->ck(cudaGetLastError(), "launch")) return S->status;
   return read_status(S);
 }
 
 template <class Real>
 static int step_timed_impl(apic_sim* S, int n) {
-  if (S->dirty) {
-    if (!S->ck(cudaMemsetAsync(S->d.acc, 0, sizeof(unsigned long long) * 2 * S->d.total_nodes, S->stream), "memset"))
-      return S->status;
-    launch_deposit_all<Real>(S->d, S->push_grid, S->stream);
-    S->dirty = false;
-  }
-  if (!S->phase_exec[0]) {
+  if (!redeposit<Real>(S) || !ensure_graphs<Real>(S)) return S->status;
+  if (!S->phase_exec[0][0]) {
     if (!S->sync()) return S->status;
-    for (int p = 0; p < APIC_NPHASE; ++p)
-      if (!capture<Real>(S, p, p + 1, &S->phase_graph[p], &S->phase_exec[p])) return S->status;
+    int npar = S->sort_interval > 0 ? 2 : 1;
+    for (int q = 0; q < npar; ++q)
+      for (int p = 0; p < APIC_NPHASE; ++p)
+        if (!capture<Real>(S, S->view(q), p, p + 1, &S->phase_graph[q][p], &S->phase_exec[q][p])) return S->status;
     for (int p = 0; p <= APIC_NPHASE; ++p)
       if (!S->ck(cudaEventCreate(&S->ev[p]), "event create")) return S->status;
   }
-  std::vector<float> acc(APIC_NPHASE, 0.0f);
   for (int k = 0; k < n; ++k) {
+    if (!launch_step<Real>(S, nullptr)) return S->status;  // sort when due (not timed)
+    S->host_step -= 1;
     S->ck(cudaEventRecord(S->ev[0], S->stream), "event record");
     for (int p = 0; p < APIC_NPHASE; ++p) {
-      if (!S->ck(cudaGraphLaunch(S->phase_exec[p], S->stream), "graph launch")) return S->status;
+      if (!S->ck(cudaGraphLaunch(S->phase_exec[S->par][p], S->stream), "graph launch")) return S->status;
       S->ck(cudaEventRecord(S->ev[p + 1], S->stream), "event record");
     }
+    S->host_step += 1;
     if (!S->ck(cudaEventSynchronize(S->ev[APIC_NPHASE]), "event sync")) return S->status;
     for (int p = 0; p < APIC_NPHASE; ++p) {
       float ms = 0.0f;
@@ -844,10 +924,15 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
   out->steps = stp.step;
   out->poisson_loop_iters = cnt;
   int vcycle = S->plan.max_tail * 10 + 1;
-  out->kernels_per_iter = 6 + 2 * vcycle;
   int most = 0;
   for (const Inst& I : S->inst) most = std::max(most, I.max_iter);
-  out->kernels_per_step = 7 + (S->cond_loop ? 0 : most * out->kernels_per_iter);
+  if (S->coop > 0) {
+    out->kernels_per_iter = 0;   // the whole solve is one cooperative launch
+    out->kernels_per_step = 7;
+  } else {
+    out->kernels_per_iter = 6 + 2 * vcycle;
+    out->kernels_per_step = 7 + (S->cond_loop ? 0 : most * out->kernels_per_iter);
+  }
   out->timed_steps = S->timed_steps;
   for (int p = 0; p < APIC_NPHASE; ++p) out->phase_ms[p] = S->phase_ms[p];
   return APIC_OK;
@@ -875,20 +960,20 @@ static int inject_impl(apic_sim* S, int inst, int species, long long n, int mode
     ps.n_inj = n;
     ps.inj_stored = 0;
     if (!S->h2d(S->d.ps + pop, &ps, 1)) return S->status;
-    launch_inject<Real>(S->d, n, S->stream);
+    launch_inject<Real>(S->view(S->par), n, S->stream);
     launch_finish_injection(S->d, pop, S->stream);
     S->dirty = true;
     return read_status(S);
   }
   if (ps.n + n > P.cap) return APIC_ERR_CAPACITY;
   if (mode == APIC_LOAD_VOLUME) {
-    launch_load<Real>(S->d, pop, ps.n, n, ps.draws, 1, S->stream);
+    launch_load<Real>(S->view(S->par), pop, ps.n, n, ps.draws, 1, S->stream);
     ps.draws += n;
   } else {
     double* tmp = (double*)S->dalloc(sizeof(double) * 5 * (size_t)n);
     if (!tmp) return S->status;
     if (!S->h2d(tmp, st, 5 * (size_t)n)) return S->status;
-    launch_explicit<Real>(S->d, pop, ps.n, n, tmp, S->stream);
+    launch_explicit<Real>(S->view(S->par), pop, ps.n, n, tmp, S->stream);
     if (!S->sync()) return S->status;
     // release the staging buffer now
     S->blocks.pop_back();
@@ -972,14 +1057,18 @@ static int solve_impl(apic_sim* S, int inst, const double* rho, double* phi_out)
     return S->status;
   if (rho && !S->h2d(d.rho + I.node_off, rho, (size_t)I.nodes)) return S->status;
   launch_b_from_rho(d, inst, S->stream);
-  launch_bicg_init<Real>(d, S->stream);
-  int it = 0;
-  SolverState sol;
-  for (;;) {
-    launch_bicg_iter<Real>(d, S->plan, S->stream);
-    launch_bicg_check(d, 0, 0, S->stream);
-    if (!S->d2h(&sol, d.sol + inst, 1) || !S->sync()) return S->status;
-    if (sol.done || ++it > 1000) break;
+  if (S->coop > 0) {
+    if (!S->ck(launch_solve_coop<Real>(d, S->plan, S->coop, S->stream), "cooperative solve")) return S->status;
+  } else {
+    launch_bicg_init<Real>(d, S->stream);
+    int it = 0;
+    SolverState sol;
+    for (;;) {
+      launch_bicg_iter<Real>(d, S->plan, S->stream);
+      launch_bicg_check(d, 0, 0, S->stream);
+      if (!S->d2h(&sol, d.sol + inst, 1) || !S->sync()) return S->status;
+      if (sol.done || ++it > 1000) break;
+    }
   }
   if (phi_out) S->d2h(phi_out, d.phi + I.node_off, (size_t)I.nodes);
   S->ck(cudaMemcpyAsync(d.phi, S->phi_save, sizeof(double) * d.total_nodes, cudaMemcpyDeviceToDevice, S->stream),
@@ -1007,7 +1096,7 @@ static int particles_impl(apic_sim* S, int inst, int species, double* out, long 
     double* tmp = (double*)S->dalloc(sizeof(double) * 5 * (size_t)n);
     if (!tmp) return S->status;
     long long nn = n;
-    launch_gather_particles<Real>(S->d, pop, tmp, &nn, S->stream);
+    launch_gather_particles<Real>(S->view(S->par), pop, tmp, &nn, S->stream);
     S->d2h(h.data(), tmp, 5 * (size_t)n);
     if (!S->sync()) return S->status;
     S->blocks.pop_back();

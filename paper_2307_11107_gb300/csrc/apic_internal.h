@@ -15,13 +15,16 @@ constexpr int kMaxPop = 128;      // populations (instance x species) per batch
 constexpr int kTable = 4096;      // intervals of the inverse-CDF sampling tables
 constexpr int kRedBlocks = 64;    // CTAs per instance in node-parallel kernels (fixed => deterministic sums)
 constexpr int kNRed = 8;          // reduction slots per CTA
-constexpr int kTailNodes = 20000; // levels with at most this many nodes run in the single-CTA tail kernel
-constexpr int kMaxCoarse = 1024;  // unknowns of the coarsest level (dense inverse)
+constexpr int kMaxCoarse = 2200;  // coarsening stops at the first level with at most this many unknowns
+constexpr int kMaxDense = 9000;   // largest coarsest level accepted (its dense inverse is kept on the GPU)
 
 // error bits of the device status word
 constexpr int kErrCapacity = 1;
 constexpr int kErrNotConverged = 2;
 constexpr int kErrNonFinite = 4;
+constexpr int kErrTimeout = 8;
+constexpr int kCoopMaxBlocks = 256;  // CTAs of the cooperative solver (partial-sum slots)
+constexpr int kCoopMaxInst = 64;     // instances the cooperative solver handles
 
 // One multigrid level of one instance.  Unknowns are the nodes of rows
 // i = 1..n1-1 (all j); rows 0 and n1 hold Dirichlet values.
@@ -31,6 +34,7 @@ struct Level {
   int64_t st;            // offset of its stencil (kSt arrays of `nodes` entries)
   int pole_extra;        // 1 on the finest level: pole rows reach j +- 2
   int pad;
+  int64_t fac[2];        // offsets of the line factorisations (x1-lines, x2-lines) in the factor pool
 };
 
 // Stencil slots: (di, dj) in {-1,0,1}^2 as 3*(di+1) + (dj+1), then the two
@@ -62,7 +66,7 @@ struct Inst {
   int32_t tail_level;      // first level handled by the single-CTA tail kernel
   int64_t cinv_off;        // dense inverse of the coarsest level [coarse_n]^2
   int32_t coarse_n;
-  int32_t pad;
+  int32_t guess;           // 1: start each solve from 2 phi^n - phi^(n-1)
   Level lv[kMaxLevels];
 };
 
@@ -74,6 +78,8 @@ struct Pop {
   int32_t fbits;           // fixed-point fraction bits of the deposit
   int32_t pad;
   int64_t acc_off;         // offset of this population's deposit accumulator (nodes of its instance)
+  int64_t cell_off;        // first global cell index of this population (sort keys)
+  int64_t cells;           // n1 * n2 of its instance
 };
 
 // Device-mutable counters of one population.
@@ -119,9 +125,13 @@ struct DevPtrs {
   void *x1, *x2, *vR, *vZ, *vT;
   void *y1, *y2, *yR, *yZ, *yT;  // second buffer (sort)
   int32_t* holes;
-  int32_t* keys;                  // sort scratch
+  int32_t* keys;                  // sort keys per slot
+  unsigned* cell_cnt;             // sort: particles per global cell
+  unsigned long long* cell_off;   // sort: exclusive prefix over cells (size cells + 1)
+  unsigned long long* scan_tmp;   // sort: block sums of the scan
+  int64_t total_cells;
   // per-node FP64 arrays
-  double *rho, *phi, *V, *bbc, *rscale;
+  double *rho, *phi, *phi_prev, *V, *bbc, *rscale;
   double *b, *r, *rh, *p, *v, *s, *t, *ph, *sh;
   double* st64;                   // finest-level stencil, FP64 [kSt][nodes] per instance (same offsets)
   unsigned long long* acc;        // deposit accumulators
@@ -130,12 +140,15 @@ struct DevPtrs {
   void* st;                       // stencils of all levels
   void *e, *f;                    // level vectors
   void* cinv;                     // coarsest inverses
+  void* fac;                      // line factorisations of every level
   // tables and diagnostics (FP64)
   double* tab;
   double* bins;
   double* hist;
   double* en;
   double* red;                    // reduction partials [n_inst][kNRed][kRedBlocks]
+  double* cred;                   // cooperative solver partials [n_inst][kNRed][kCoopMaxBlocks]
+  unsigned* bar;                  // grid barrier of the cooperative solver (count, generation)
   int64_t total_nodes;
   int64_t level_nodes;
 };
@@ -153,6 +166,8 @@ template <class Real>
 void launch_push(const DevPtrs& d, int grid, cudaStream_t s);
 template <class Real>
 void launch_inject(const DevPtrs& d, long long max_inj, cudaStream_t s);
+template <class Real>
+void launch_sort(const DevPtrs& d, int grid, cudaStream_t s);
 template <class Real>
 void launch_gather_particles(const DevPtrs& d, int pop, double* out, long long* n_out, cudaStream_t s);
 
@@ -174,6 +189,7 @@ struct SolvePlan {
   int x2_k[kMaxLevels];
   int node_blocks[kMaxLevels];    // grid.x of node-parallel kernels on each level
   int tail_threads, tail_k;
+  int tail_bytes;                 // dynamic shared memory of the tail kernel
 };
 template <class Real>
 void launch_bicg_init(const DevPtrs& d, cudaStream_t s);
@@ -181,7 +197,20 @@ template <class Real>
 void launch_bicg_iter(const DevPtrs& d, const SolvePlan& plan, cudaStream_t s);
 template <class Real>
 cudaError_t set_poisson_smem(const SolvePlan& plan);
+template <class Real>
+void launch_line_factor(const DevPtrs& d, int level, int dir, int lines, int kmax, cudaStream_t s);
+__host__ __device__ constexpr int line_fac_stride(int K) { return 5 * 32 * K + 13 * 32 + 2; }
+__host__ __device__ constexpr int line_buf_len(int K) { return 32 * K + line_fac_stride(K); }
 void launch_bicg_check(const DevPtrs& d, cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
+// One cooperative launch for the whole solve (all Krylov iterations, all levels).
+template <class Real>
+cudaError_t launch_solve_coop(const DevPtrs& d, const SolvePlan& plan, int blocks, cudaStream_t s);
+template <class Real>
+int coop_blocks(const SolvePlan& plan, int sms);
+// Dense inverse of an n x n FP64 matrix on the GPU (Gauss-Jordan, partial
+// pivoting); work: n x 2n doubles, a[n][n] row-major on entry; out: Real[n][n].
+template <class Real>
+cudaError_t launch_dense_inverse(double* work, double* fbuf, int n, Real* out, cudaStream_t s);
 void launch_finish_injection(const DevPtrs& d, int pop, cudaStream_t s);
 
 }  // namespace apic

@@ -49,6 +49,12 @@ __global__ void __launch_bounds__(256) k_rho(DevPtrs d) {
     double rho = q / d.V[g];
     d.rho[g] = rho;
     int i = (int)(nd / I.N2);
+    if (i > 0 && i < I.n1) {
+      // initial guess of this step's solve: previous phi, or its linear extrapolation
+      double ph = d.phi[g];
+      if (I.guess && d.stp[blockIdx.y].step >= 2) d.phi[g] = 2.0 * ph - d.phi_prev[g];
+      d.phi_prev[g] = ph;
+    }
     double bv = 0.0;
     if (i > 0 && i < I.n1) bv = -rho * d.rscale[g] + d.bbc[g];
     d.b[g] = bv;

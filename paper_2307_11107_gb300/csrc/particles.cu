@@ -23,6 +23,9 @@ using Real = APIC_REAL;
 constexpr bool kF64 = sizeof(Real) == 8;
 constexpr int kBisect = kF64 ? 40 : 24;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPushItems = 8;    // particles per thread per chunk
+constexpr int kWinRows = 8;      // node rows of the shared-memory deposit window
+constexpr int kWinMaxN2 = 513;   // widest grid row the window holds (larger grids deposit globally)
 
 template <class T>
 struct Pair;
@@ -122,28 +125,119 @@ __device__ __forceinline__ W4 weights(const Cell& c, int F) {
   return w;
 }
 
-// Warp-cooperative deposit: when all 32 lanes hit the same cell of the same
-// population, the four corner weights are summed across the warp first and
-// one lane issues the four 64-bit atomics; otherwise each lane adds its own.
-// Integer addition makes the result independent of the order.
-__device__ __forceinline__ void deposit_warp(unsigned long long* acc, long long key, W4 w, int N2, bool active) {
-  long long k0 = __shfl_sync(kFull, key, 0);
-  bool uni = __all_sync(kFull, active && key == k0);
-  if (uni) {
+// Runs of consecutive lanes holding the same key (invalid lanes are runs of
+// their own): start lane, length and rank of every lane in its run.
+struct Run {
+  int start, len, rank;
+};
+
+__device__ __forceinline__ Run warp_runs(long long key, bool valid) {
+  const int lane = threadIdx.x & 31;
+  long long kp = __shfl_up_sync(kFull, key, 1);
+  int vp = __shfl_up_sync(kFull, (int)valid, 1);
+  bool head = lane == 0 || !valid || !vp || kp != key;
+  unsigned hm = __ballot_sync(kFull, head);
+  unsigned upto = hm & ((2u << lane) - 1u);
+  Run r;
+  r.start = 31 - __clz(upto);
+  unsigned after = hm & ~((2u << lane) - 1u);
+  int next = after ? __ffs(after) - 1 : 32;
+  r.len = next - r.start;
+  r.rank = lane - r.start;
+  return r;
+}
+
+// Sum of v over the lanes of each run, held by the run's last lane.
+__device__ __forceinline__ unsigned long long run_sum(unsigned long long v, const Run& r) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      w.w00 += __shfl_down_sync(kFull, w.w00, o);
-      w.w10 += __shfl_down_sync(kFull, w.w10, o);
-      w.w01 += __shfl_down_sync(kFull, w.w01, o);
-      w.w11 += __shfl_down_sync(kFull, w.w11, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      atomicAdd(acc + k0, w.w00);
-      atomicAdd(acc + k0 + N2, w.w10);
-      atomicAdd(acc + k0 + 1, w.w01);
-      atomicAdd(acc + k0 + N2 + 1, w.w11);
-    }
-  } else if (active) {
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long up = __shfl_up_sync(kFull, v, o);
+    if (lane - o >= r.start) v += up;
+  }
+  return v;
+}
+
+// Accumulation target of one CTA: a shared-memory window of node rows
+// [row0, row0 + rows) of one population (all columns), flushed to the global
+// accumulator once per chunk; corners outside it go straight to global memory.
+struct Window {
+  unsigned long long* s;  // shared [rows * N2]
+  unsigned long long* g;  // global accumulator of the population (node 0)
+  int row0, rows, N2;
+};
+
+__device__ __forceinline__ void win_add(const Window& W, int i, int j, unsigned long long v) {
+  if (!v) return;
+  int rr = i - W.row0;
+  if (rr >= 0 && rr < W.rows) atomicAdd(W.s + rr * W.N2 + j, v);
+  else atomicAdd(W.g + (long long)i * W.N2 + j, v);
+}
+
+__device__ __forceinline__ void add4(const Window& W, int i, int j, unsigned long long w00, unsigned long long w10,
+                                     unsigned long long w01, unsigned long long w11) {
+  win_add(W, i, j, w00);
+  win_add(W, i + 1, j, w10);
+  win_add(W, i, j + 1, w01);
+  win_add(W, i + 1, j + 1, w11);
+}
+
+// Warp-cooperative deposit: lanes that hit the same cell (consecutive in the
+// warp, as after a sort by cell) first sum their weights with a segmented
+// scan; the last lane of each run adds the four corners.  Integer addition
+// makes the result independent of the order.
+__device__ __forceinline__ void deposit_warp(const Window& W, int key, int ci, int cj, W4 w, bool active) {
+  Run r = warp_runs(key, active);
+  w.w00 = run_sum(w.w00, r);
+  w.w10 = run_sum(w.w10, r);
+  w.w01 = run_sum(w.w01, r);
+  w.w11 = run_sum(w.w11, r);
+  if (active && r.rank == r.len - 1) add4(W, ci, cj, w.w00, w.w10, w.w01, w.w11);
+}
+
+// FP32 variant: the four corner weights (S-q1)(S-q2), q1(S-q2), (S-q1)q2,
+// q1 q2 (S = 2^b) of a run follow exactly from the run's length and the sums
+// of q1, q2 and q1 q2, so only those are reduced.  A warp whose 32 lanes share
+// one cell uses the hardware warp reduction.
+__device__ __forceinline__ void deposit_warp_q(const Window& W, int key, int ci, int cj, unsigned q1, unsigned q2,
+                                               int b, bool active) {
+  const unsigned S = 1u << b;
+  unsigned long long p12 = (unsigned long long)q1 * q2;
+  int k0 = __shfl_sync(kFull, key, 0);
+  unsigned long long s1, s2, s12, n;
+  bool last;
+  if (__all_sync(kFull, active && key == k0)) {
+    s1 = __reduce_add_sync(kFull, q1);
+    s2 = __reduce_add_sync(kFull, q2);
+    unsigned lo = __reduce_add_sync(kFull, (unsigned)(p12 & 0xffffffu));
+    unsigned hi = __reduce_add_sync(kFull, (unsigned)(p12 >> 24));
+    s12 = ((unsigned long long)hi << 24) + lo;
+    n = 32;
+    last = (threadIdx.x & 31) == 31;
+  } else {
+    Run r = warp_runs(key, active);
+    s1 = run_sum(q1, r);
+    s2 = run_sum(q2, r);
+    s12 = run_sum(p12, r);
+    n = (unsigned long long)r.len;
+    last = active && r.rank == r.len - 1;
+  }
+  if (last) {
+    unsigned long long SS = (unsigned long long)S * S;
+    unsigned long long w11 = s12, w10 = (unsigned long long)S * s1 - s12, w01 = (unsigned long long)S * s2 - s12;
+    unsigned long long w00 = n * SS - (unsigned long long)S * (s1 + s2) + s12;
+    add4(W, ci, cj, w00, w10, w01, w11);
+  }
+}
+
+// Deposit without a window (standalone deposit and injection).
+__device__ __forceinline__ void deposit_warp_global(unsigned long long* acc, long long key, W4 w, int N2, bool active) {
+  Run r = warp_runs(key, active);
+  w.w00 = run_sum(w.w00, r);
+  w.w10 = run_sum(w.w10, r);
+  w.w01 = run_sum(w.w01, r);
+  w.w11 = run_sum(w.w11, r);
+  if (active && r.rank == r.len - 1) {
     if (w.w00) atomicAdd(acc + key, w.w00);
     if (w.w10) atomicAdd(acc + key + N2, w.w10);
     if (w.w01) atomicAdd(acc + key + 1, w.w01);
@@ -216,48 +310,195 @@ __device__ __forceinline__ void push_hole(const DevPtrs& d, const Pop& P, int po
   d.holes[P.base + h] = (int32_t)k;
 }
 
+// Per-population constants of the push, staged in shared memory.
+struct PushConst {
+  Real al, h1, h2, x1_out, dt, B, h;  // h = q dt / (2 m)
+  Real ih1, ih2, tz, sz;              // 1/h1, 1/h2, Boris rotation factors (constant per population)
+  int n1, n2, N2, fbits;
+  long long node_off, acc_off;
+};
+
+__device__ __forceinline__ Cell locate_c(const PushConst& C, Real x1, Real x2) {
+  Real u1 = (x1 + Real(1)) / C.h1;
+  Real u2 = (x2 + Real(1)) / C.h2;
+  Cell c;
+  c.i = (int)floor(u1);
+  c.j = (int)floor(u2);
+  c.i = c.i < 0 ? 0 : (c.i > C.n1 - 1 ? C.n1 - 1 : c.i);
+  c.j = c.j < 0 ? 0 : (c.j > C.n2 - 1 ? C.n2 - 1 : c.j);
+  c.f1 = u1 - (Real)c.i;
+  c.f2 = u2 - (Real)c.j;
+  c.f1 = c.f1 < Real(0) ? Real(0) : (c.f1 > Real(1) ? Real(1) : c.f1);
+  c.f2 = c.f2 < Real(0) ? Real(0) : (c.f2 > Real(1) ? Real(1) : c.f2);
+  return c;
+}
+
 // One full particle update for slot t of the batch (Sec. 2, Eqs. 8-10, 9).
+// The CTA works on chunks of kPushItems x blockDim consecutive slots of one
+// population (sorted by cell, so a chunk covers few grid rows) and deposits
+// into a shared-memory window of kWinRows node rows that is flushed to the
+// global accumulator after each chunk.
 __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
-  __shared__ long long s_pre[kMaxPop + 1];
+  extern __shared__ unsigned long long s_win[];
+  __shared__ long long s_pre[kMaxPop + 1];  // chunk prefix over populations
+  __shared__ PushConst s_pc[kMaxPop];
+  __shared__ int s_row0;
+  const long long CH = (long long)kPushItems * blockDim.x;
   if (threadIdx.x == 0) {
     long long a = 0;
     for (int p = 0; p < d.n_pop; ++p) {
       s_pre[p] = a;
-      a += d.ps[p].n;
+      a += (d.ps[p].n + CH - 1) / CH;
     }
     s_pre[d.n_pop] = a;
   }
+  for (int p = threadIdx.x; p < d.n_pop; p += blockDim.x) {
+    const Pop& P = d.pop[p];
+    const Inst& I = d.inst[P.inst];
+    PushConst C;
+    C.al = (Real)I.alpha;
+    C.h1 = (Real)I.h1;
+    C.h2 = (Real)I.h2;
+    C.x1_out = (Real)I.x1_out;
+    C.dt = (Real)I.dt;
+    C.B = (Real)I.B;
+    C.h = Real(0.5) * (Real)(P.q / P.m) * (Real)I.dt;
+    C.ih1 = (Real)(1.0 / I.h1);
+    C.ih2 = (Real)(1.0 / I.h2);
+    C.tz = C.h * (-(Real)I.B);
+    C.sz = Real(2) * C.tz / (Real(1) + C.tz * C.tz);
+    C.n1 = I.n1;
+    C.n2 = I.n2;
+    C.N2 = I.N2;
+    C.fbits = P.fbits;
+    C.node_off = I.node_off;
+    C.acc_off = P.acc_off;
+    s_pc[p] = C;
+  }
+  for (int k = threadIdx.x; k < kWinRows * kWinMaxN2; k += blockDim.x) s_win[k] = 0ull;
   __syncthreads();
-  const long long total = s_pre[d.n_pop];
+  const long long total_chunks = s_pre[d.n_pop];
   Real* X1 = (Real*)d.x1;
   Real* X2 = (Real*)d.x2;
   Real* VR = (Real*)d.vR;
   Real* VZ = (Real*)d.vZ;
   Real* VT = (Real*)d.vT;
   const Real2* G = (const Real2*)d.G;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
-    long long t = base + (threadIdx.x & 31);
-    bool active = t < total;
-    int pop = active ? find_pop(s_pre, d.n_pop, t) : 0;
-    const Pop& P = d.pop[pop];
-    const Inst& I = d.inst[P.inst];
-    long long k = active ? t - s_pre[pop] : 0;
-    long long slot = P.base + k;
+  for (long long chunk = blockIdx.x; chunk < total_chunks; chunk += gridDim.x) {
+   const int pop = find_pop(s_pre, d.n_pop, chunk);
+   const PushConst& C = s_pc[pop];
+   const long long npop = d.ps[pop].n, pbase = d.pop[pop].base;
+   const long long c0 = (chunk - s_pre[pop]) * CH;
+   if (threadIdx.x == 0) {
+     int row = 0;
+     for (int q = 0; q < 64 && c0 + q < npop; ++q) {
+       Real xq = X1[pbase + c0 + q];
+       if (xq < Real(0)) {
+         row = (int)floor((double)((xq + Real(1)) * C.ih1));
+         break;
+       }
+     }
+     s_row0 = row > 0 ? row - 1 : 0;
+   }
+   __syncthreads();
+   Window W;
+   W.s = s_win;
+   W.g = d.acc + C.acc_off;
+   W.row0 = s_row0;
+   W.N2 = C.N2;
+   W.rows = C.N2 <= kWinMaxN2 ? kWinRows : 0;
+   for (int it = 0; it < kPushItems; ++it) {
+    long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
+    bool active = k < npop;
+    long long slot = pbase + (active ? k : 0);
     Real x1 = active ? X1[slot] : Real(2);
     bool alive = active && x1 < Real(0);
-    long long key = -1;
+    int key = -1, di = 0, dj = 0;
     W4 w = {0, 0, 0, 0};
-    if (alive) {
+    unsigned q1 = 0, q2 = 0;
+    if (alive && !kF64) {
+      // FP32: reciprocals and rsqrt instead of divisions; the grain test
+      // r < (1 + sqrt(1 + 4 alpha x2))/2 is taken on squares.
+      float x2 = X2[slot], vR = VR[slot], vZ = VZ[slot], vT = VT[slot];
+      const float al = C.al, dt = C.dt;
+      float x1f = (float)x1;
+      float disc = 1.0f - 4.0f * al * x1f * x2;
+      float ir = __fdividef(-2.0f * x1f, 1.0f + sqrtf(disc));  // 1/r (Eq. 3)
+      float r = __frcp_rn(ir);
+      float s2 = (1.0f - x2) * (1.0f + x2);
+      float sn = sqrtf(s2);
+      float R = r * sn, Z = r * x2;
+      float u1 = (x1f + 1.0f) * C.ih1, u2 = (x2 + 1.0f) * C.ih2;
+      int ci = min(max((int)floorf(u1), 0), C.n1 - 1), cj = min(max((int)floorf(u2), 0), C.n2 - 1);
+      float f1 = fminf(fmaxf(u1 - (float)ci, 0.0f), 1.0f), f2 = fminf(fmaxf(u2 - (float)cj, 0.0f), 1.0f);
+      long long n00 = C.node_off + (long long)ci * C.N2 + cj;
+      Real2 a00 = G[n00], a10 = G[n00 + C.N2], a01 = G[n00 + 1], a11 = G[n00 + C.N2 + 1];
+      float g1 = (1.0f - f2) * ((1.0f - f1) * a00.x + f1 * a10.x) + f2 * ((1.0f - f1) * a01.x + f1 * a11.x);
+      float g2 = (1.0f - f2) * ((1.0f - f1) * a00.y + f1 * a10.y) + f2 * ((1.0f - f1) * a01.y + f1 * a11.y);
+      float ir3 = ir * ir * ir;
+      float x1R = sn * (r + 3.0f * al * x2) * ir3, x1Z = (r * x2 + al * (3.0f * x2 * x2 - 1.0f)) * ir3;
+      float x2R = -x2 * sn * ir, x2Z = s2 * ir;
+      float ER = -(x1R * g1 + x2R * g2), EZ = -(x1Z * g1 + x2Z * g2);
+      float h = C.h, tz = C.tz, sz = C.sz;
+      float vx = vR + h * ER, vy = vT, vz = vZ + h * EZ;
+      float px_ = vx + vy * tz, py_ = vy - vx * tz;
+      vx = vx + py_ * sz + h * ER;
+      vy = vy - px_ * sz;
+      vz = vz + h * EZ;
+      float Xc = R + vx * dt, Yc = vy * dt, Zn = Z + vz * dt;
+      float Rn2 = Xc * Xc + Yc * Yc;
+      float cr = 1.0f, sr = 0.0f, Rn = 0.0f;
+      if (Rn2 > 0.0f) {
+        float iR = rsqrtf(Rn2);
+        cr = Xc * iR;
+        sr = Yc * iR;
+        Rn = Rn2 * iR;
+      }
+      float vRn = cr * vx + sr * vy, vTn = -sr * vx + cr * vy;
+      float rn2 = Rn2 + Zn * Zn;
+      float irn = rsqrtf(rn2);
+      float rn = rn2 * irn;
+      float x2n = Zn * irn;
+      float tr = 2.0f * rn - 1.0f;
+      if (tr < 0.0f || tr * tr < 1.0f + 4.0f * al * x2n) {
+        const Pop& P = d.pop[pop];
+        absorb_tally(d, d.inst[P.inst], P, R, Z, vx, vz, vy, dt);
+        atomicAdd((unsigned long long*)&d.ps[pop].absorbed, 1ull);
+        X1[slot] = Real(2);
+        push_hole(d, P, pop, k);
+      } else {
+        float x1n = -irn * (1.0f + al * x2n * irn);
+        if (x1n > C.x1_out) {
+          atomicAdd((unsigned long long*)&d.ps[pop].escaped, 1ull);
+          X1[slot] = Real(2);
+          push_hole(d, d.pop[pop], pop, k);
+        } else {
+          X1[slot] = x1n;
+          X2[slot] = x2n;
+          VR[slot] = vRn;
+          VZ[slot] = vz;
+          VT[slot] = vTn;
+          float v1 = (x1n + 1.0f) * C.ih1, v2 = (x2n + 1.0f) * C.ih2;
+          int ni = min(max((int)floorf(v1), 0), C.n1 - 1), nj = min(max((int)floorf(v2), 0), C.n2 - 1);
+          float e1 = fminf(fmaxf(v1 - (float)ni, 0.0f), 1.0f), e2 = fminf(fmaxf(v2 - (float)nj, 0.0f), 1.0f);
+          const float one = (float)(1u << (C.fbits >> 1));
+          q1 = min((unsigned)(e1 * one), 1u << (C.fbits >> 1));
+          q2 = min((unsigned)(e2 * one), 1u << (C.fbits >> 1));
+          key = ni * C.N2 + nj;
+          di = ni;
+          dj = nj;
+        }
+      }
+    } else if (alive) {
       Real x2 = X2[slot], vR = VR[slot], vZ = VZ[slot], vT = VT[slot];
-      Real al = (Real)I.alpha, dt = (Real)I.dt;
+      const Real al = C.al, dt = C.dt;
       Real r = radius(al, x1, x2);
       Real sn = sqrt((Real(1) - x2) * (Real(1) + x2));
       Real R = r * sn, Z = r * x2;
       // gather (Eq. 10): bilinear node gradients, analytic metric at the particle
-      Cell c = locate(I, x1, x2);
-      long long n00 = I.node_off + (long long)c.i * I.N2 + c.j;
-      Real2 a00 = G[n00], a10 = G[n00 + I.N2], a01 = G[n00 + 1], a11 = G[n00 + I.N2 + 1];
+      Cell c = locate_c(C, x1, x2);
+      long long n00 = C.node_off + (long long)c.i * C.N2 + c.j;
+      Real2 a00 = G[n00], a10 = G[n00 + C.N2], a01 = G[n00 + 1], a11 = G[n00 + C.N2 + 1];
       Real w00 = (Real(1) - c.f1) * (Real(1) - c.f2), w10 = c.f1 * (Real(1) - c.f2);
       Real w01 = (Real(1) - c.f1) * c.f2, w11 = c.f1 * c.f2;
       Real g1 = w00 * a00.x + w10 * a10.x + w01 * a01.x + w11 * a11.x;
@@ -267,9 +508,9 @@ __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
       Real EZ = -(m.x1Z * g1 + m.x2Z * g2);
       // Boris in the local frame (R-hat, Theta-hat, Z-hat); Eq. 9's Lorentz
       // terms are those of the field vector -B z-hat.
-      Real h = Real(0.5) * (Real)(P.q / P.m) * dt;
+      Real h = C.h;
       Real vx = vR + h * ER, vy = vT, vz = vZ + h * EZ;
-      Real tz = h * (-(Real)I.B);
+      Real tz = h * (-C.B);
       Real sz = Real(2) * tz / (Real(1) + tz * tz);
       Real px_ = vx + vy * tz, py_ = vy - vx * tz;
       vx = vx + py_ * sz;
@@ -288,29 +529,44 @@ __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
       Real rn = sqrt(Rn * Rn + Zn * Zn);
       Real x2n = Zn / rn;
       if (rn < r_grain(al, x2n)) {
-        absorb_tally(d, I, P, R, Z, vx, vz, vy, dt);
+        const Pop& P = d.pop[pop];
+        absorb_tally(d, d.inst[P.inst], P, R, Z, vx, vz, vy, dt);
         atomicAdd((unsigned long long*)&d.ps[pop].absorbed, 1ull);
         X1[slot] = Real(2);
         push_hole(d, P, pop, k);
       } else {
         Real x1n = x1_at(al, rn, x2n);
-        if (x1n > (Real)I.x1_out) {
+        if (x1n > C.x1_out) {
           atomicAdd((unsigned long long*)&d.ps[pop].escaped, 1ull);
           X1[slot] = Real(2);
-          push_hole(d, P, pop, k);
+          push_hole(d, d.pop[pop], pop, k);
         } else {
           X1[slot] = x1n;
           X2[slot] = x2n;
           VR[slot] = vRn;
           VZ[slot] = vz;
           VT[slot] = vTn;
-          Cell cn = locate(I, x1n, x2n);
-          key = dep_key(I, P, cn);
-          w = weights(cn, P.fbits);
+          Cell cn = locate_c(C, x1n, x2n);
+          key = cn.i * C.N2 + cn.j;
+          di = cn.i;
+          dj = cn.j;
+          w = weights(cn, C.fbits);
         }
       }
     }
-    deposit_warp(d.acc, key, w, active ? I.N2 : 1, key >= 0);
+    if (kF64) deposit_warp(W, key, di, dj, w, key >= 0);
+    else deposit_warp_q(W, key, di, dj, q1, q2, C.fbits >> 1, key >= 0);
+   }
+   __syncthreads();
+   // flush the window and clear it for the next chunk
+   for (int e = threadIdx.x; e < W.rows * W.N2; e += blockDim.x) {
+     unsigned long long v = s_win[e];
+     if (v) {
+       atomicAdd(W.g + (long long)(W.row0 + e / W.N2) * W.N2 + e % W.N2, v);
+       s_win[e] = 0ull;
+     }
+   }
+   __syncthreads();
   }
 }
 
@@ -345,7 +601,7 @@ __global__ void __launch_bounds__(256) k_deposit_all(DevPtrs d) {
       key = dep_key(I, P, c);
       w = weights(c, P.fbits);
     }
-    deposit_warp(d.acc, key, w, active ? I.N2 : 1, key >= 0);
+    deposit_warp_global(d.acc, key, w, active ? I.N2 : 1, key >= 0);
   }
 }
 
@@ -467,6 +723,150 @@ __global__ void __launch_bounds__(256) k_inject(DevPtrs d) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Counting sort of every population by cell (i-major), which also drops freed
+// slots: count -> exclusive scan over all cells -> scatter into the second
+// buffer.  Particles of a warp then mostly share a cell, so the deposit's
+// segmented sums replace most atomics.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sort_count(DevPtrs d) {
+  __shared__ long long s_pre[kMaxPop + 1];
+  if (threadIdx.x == 0) {
+    long long a = 0;
+    for (int p = 0; p < d.n_pop; ++p) {
+      s_pre[p] = a;
+      a += d.ps[p].n;
+    }
+    s_pre[d.n_pop] = a;
+  }
+  __syncthreads();
+  const long long total = s_pre[d.n_pop];
+  const Real* X1 = (const Real*)d.x1;
+  const Real* X2 = (const Real*)d.x2;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+    long long t = base + (threadIdx.x & 31);
+    bool active = t < total;
+    int pop = active ? find_pop(s_pre, d.n_pop, t) : 0;
+    const Pop& P = d.pop[pop];
+    long long slot = P.base + (active ? t - s_pre[pop] : 0);
+    Real x1 = active ? X1[slot] : Real(2);
+    long long key = -1;
+    if (active && x1 < Real(0)) {
+      Cell c = locate(d.inst[P.inst], x1, X2[slot]);
+      key = P.cell_off + (long long)c.i * d.inst[P.inst].n2 + c.j;
+    }
+    if (active) d.keys[slot] = (int32_t)key;
+    Run r = warp_runs(key, key >= 0);
+    if (key >= 0 && r.rank == 0) atomicAdd(d.cell_cnt + key, (unsigned)r.len);
+  }
+}
+
+// Exclusive scan of cell_cnt into cell_off: per-block scan (1024 cells) ...
+__global__ void __launch_bounds__(1024) k_scan_blocks(DevPtrs d) {
+  __shared__ unsigned long long ws[32];
+  long long c = (long long)blockIdx.x * 1024 + threadIdx.x;
+  unsigned long long v = c < d.total_cells ? d.cell_cnt[c] : 0ull;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long up = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += up;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long y = ws[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long up = __shfl_up_sync(kFull, y, o);
+      if (lane >= o) y += up;
+    }
+    ws[lane] = y;
+  }
+  __syncthreads();
+  unsigned long long excl = x - v + (warp > 0 ? ws[warp - 1] : 0ull);
+  if (c < d.total_cells) d.cell_off[c] = excl;
+  if (threadIdx.x == 1023) d.scan_tmp[blockIdx.x] = excl + v;
+}
+
+// ... scan of the block sums (one CTA) ...
+__global__ void __launch_bounds__(1024) k_scan_top(DevPtrs d, int nblocks) {
+  __shared__ unsigned long long sh[1024];
+  // sequential carry over chunks of 1024 block sums
+  unsigned long long carry = 0;
+  for (int c0 = 0; c0 < nblocks; c0 += 1024) {
+    int k = c0 + threadIdx.x;
+    unsigned long long v = k < nblocks ? d.scan_tmp[k] : 0ull;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      unsigned long long add = threadIdx.x >= o ? sh[threadIdx.x - o] : 0ull;
+      __syncthreads();
+      sh[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (k < nblocks) d.scan_tmp[k] = carry + sh[threadIdx.x] - v;  // exclusive
+    unsigned long long tot = sh[1023];
+    __syncthreads();
+    carry += tot;
+  }
+  if (threadIdx.x == 0) d.cell_off[d.total_cells] = carry;
+}
+
+// ... and the block offsets added back; the counters are cleared for the scatter.
+__global__ void __launch_bounds__(1024) k_scan_add(DevPtrs d) {
+  long long c = (long long)blockIdx.x * 1024 + threadIdx.x;
+  if (c < d.total_cells) {
+    d.cell_off[c] += d.scan_tmp[blockIdx.x];
+    d.cell_cnt[c] = 0u;
+  }
+}
+
+// Scatter every live particle to its cell's range of the second buffer.
+__global__ void __launch_bounds__(256) k_sort_scatter(DevPtrs d) {
+  __shared__ long long s_pre[kMaxPop + 1];
+  if (threadIdx.x == 0) {
+    long long a = 0;
+    for (int p = 0; p < d.n_pop; ++p) {
+      s_pre[p] = a;
+      a += d.ps[p].n;
+    }
+    s_pre[d.n_pop] = a;
+  }
+  __syncthreads();
+  const long long total = s_pre[d.n_pop];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+    long long t = base + (threadIdx.x & 31);
+    bool active = t < total;
+    int pop = active ? find_pop(s_pre, d.n_pop, t) : 0;
+    const Pop& P = d.pop[pop];
+    long long slot = P.base + (active ? t - s_pre[pop] : 0);
+    long long key = active ? (long long)d.keys[slot] : -1;
+    Run r = warp_runs(key, key >= 0);
+    unsigned first = 0;
+    if (key >= 0 && r.rank == 0) first = atomicAdd(d.cell_cnt + key, (unsigned)r.len);
+    first = __shfl_sync(kFull, first, r.start);
+    if (key >= 0) {
+      long long dst = P.base + (long long)(d.cell_off[key] - d.cell_off[P.cell_off]) + first + r.rank;
+      ((Real*)d.y1)[dst] = ((const Real*)d.x1)[slot];
+      ((Real*)d.y2)[dst] = ((const Real*)d.x2)[slot];
+      ((Real*)d.yR)[dst] = ((const Real*)d.vR)[slot];
+      ((Real*)d.yZ)[dst] = ((const Real*)d.vZ)[slot];
+      ((Real*)d.yT)[dst] = ((const Real*)d.vT)[slot];
+    }
+  }
+}
+
+// Populations become dense: n = live particles, no freed slots.
+__global__ void k_sort_finish(DevPtrs d) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.n_pop) return;
+  const Pop& P = d.pop[p];
+  d.ps[p].n = (long long)(d.cell_off[P.cell_off + P.cells] - d.cell_off[P.cell_off]);
+  d.ps[p].n_holes = 0;
+}
+
 // Copy every slot [0, n) of one population to FP64 rows (dead slots keep
 // their sentinel x1 > 0; the host drops them).
 __global__ void k_copy_out(DevPtrs d, int pop, double* out, long long n) {
@@ -506,7 +906,9 @@ void launch_deposit_all<Real>(const DevPtrs& d, int max_grid, cudaStream_t s) {
 
 template <>
 void launch_push<Real>(const DevPtrs& d, int grid, cudaStream_t s) {
-  k_push<<<grid, 256, 0, s>>>(d);
+  const int sm = kWinRows * kWinMaxN2 * (int)sizeof(unsigned long long);
+  cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  k_push<<<grid, 256, sm, s>>>(d);
 }
 
 template <>
@@ -514,6 +916,18 @@ void launch_inject<Real>(const DevPtrs& d, long long max_inj, cudaStream_t s) {
   if (max_inj <= 0) return;
   dim3 g(blocks_for(max_inj, 256), d.n_pop);
   k_inject<<<g, 256, 0, s>>>(d);
+}
+
+template <>
+void launch_sort<Real>(const DevPtrs& d, int grid, cudaStream_t s) {
+  cudaMemsetAsync(d.cell_cnt, 0, sizeof(unsigned) * d.total_cells, s);
+  k_sort_count<<<grid, 256, 0, s>>>(d);
+  int nb = (int)((d.total_cells + 1023) / 1024);
+  k_scan_blocks<<<nb, 1024, 0, s>>>(d);
+  k_scan_top<<<1, 1024, 0, s>>>(d, nb);
+  k_scan_add<<<nb, 1024, 0, s>>>(d);
+  k_sort_scatter<<<grid, 256, 0, s>>>(d);
+  k_sort_finish<<<(d.n_pop + 63) / 64, 64, 0, s>>>(d);
 }
 
 template <>

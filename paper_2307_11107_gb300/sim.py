@@ -41,6 +41,7 @@ def make_config(d, precision="fp32"):
     c.poisson_max_iter = int(d.get("poisson_max_iter", 0))
     c.sort_interval = int(d.get("sort_interval", 0))
     c.history_cap = int(d.get("history_cap", 0))
+    c.poisson_guess = int(d.get("poisson_guess", 0))
     return c
 
 

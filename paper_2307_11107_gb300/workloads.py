@@ -28,7 +28,7 @@ def dipole_256(precision="fp32", n_per_species=10_000_000):
     1e7 macro-particles per species, dt = 0.1 (2000 steps)."""
     return dict(name="dipole_a0.3_256x128_2e7", alpha=0.15, x1_out=-0.05, phi_g=-2.5, phi_out=0.0, B=1.0, dt=0.1,
                 n1=256, n2=128, species=[dict(ELECTRON, n_init=n_per_species), dict(ion(0.5), n_init=n_per_species)],
-                seed=1, precision=precision, poisson_tol=1e-10, poisson_max_iter=20, steps=2000)
+                seed=1, precision=precision, poisson_tol=1e-10, poisson_max_iter=20, sort_interval=8, poisson_guess=1, steps=2000)
 
 
 def dipole_1024(precision="fp32", n_per_species=50_000_000):
@@ -38,7 +38,7 @@ def dipole_1024(precision="fp32", n_per_species=50_000_000):
     return dict(name="dipole_a0.45_1024x512_1e8", alpha=0.225, x1_out=-0.05, phi_g=-2.5, phi_out=0.0, B=1.0,
                 dt=0.1, n1=1024, n2=512,
                 species=[dict(ELECTRON, n_init=n_per_species), dict(ion(0.5), n_init=n_per_species)],
-                seed=1, precision=precision, poisson_tol=1e-10, poisson_max_iter=30, steps=1000)
+                seed=1, precision=precision, poisson_tol=1e-10, poisson_max_iter=30, sort_interval=8, steps=1000)
 
 
 def batched_48(seed=2, scale=1.0):
@@ -54,5 +54,5 @@ def batched_48(seed=2, scale=1.0):
         out.append(dict(name="inst%02d" % k, alpha=min(a / 2, 0.24), x1_out=-0.05, phi_g=rng.uniform(-4.0, -1.0),
                         phi_out=0.0, B=float(rng.integers(0, 2)), dt=0.1, n1=n1, n2=n1 // 2,
                         species=[dict(ELECTRON, n_init=npart), dict(ion(0.5), n_init=npart)], seed=2, instance=k,
-                        precision="fp32", poisson_tol=1e-8, poisson_max_iter=20))
+                        precision="fp32", poisson_tol=1e-8, poisson_max_iter=20, sort_interval=8))
     return out
