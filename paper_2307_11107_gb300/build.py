@@ -23,7 +23,7 @@ BASE = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "
 
 UNITS = [
     ("particles.cu", "particles_f64.o", ["-DAPIC_REAL=double", "-fmad=false"]),
-    ("particles.cu", "particles_f32.o", ["-DAPIC_REAL=float"]),
+    ("particles.cu", "particles_f32.o", ["-DAPIC_REAL=float", "--use_fast_math"]),
     ("poisson.cu", "poisson_f64.o", ["-DAPIC_POISSON_REAL=double", "-DAPIC_POISSON_COMMON=1"]),
     ("poisson.cu", "poisson_f32.o", ["-DAPIC_POISSON_REAL=float", "-DAPIC_POISSON_COMMON=0"]),
     ("fields.cu", "fields.o", ["-fmad=false"]),

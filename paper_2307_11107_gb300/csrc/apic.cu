@@ -487,7 +487,7 @@ static int setup(apic_sim* S) {
       else P.fbits = 2 * std::min(20, (62 - lg) / 2);
       P.dep_scale = sp.q * P.w * std::ldexp(1.0, -P.fbits);
       P.acc_off = 2 * I.node_off + (long long)s * I.nodes;
-      P.cells = (long long)c.n1 * c.n2;
+      P.cells = c.n1;  // sort bins: the grid rows of this population
       P.cell_off = total_cells;
       total_cells += P.cells;
       S->max_inj = std::max(S->max_inj, (long long)std::ceil(P.lam) + 2);

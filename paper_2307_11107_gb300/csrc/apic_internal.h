@@ -78,8 +78,8 @@ struct Pop {
   int32_t fbits;           // fixed-point fraction bits of the deposit
   int32_t pad;
   int64_t acc_off;         // offset of this population's deposit accumulator (nodes of its instance)
-  int64_t cell_off;        // first global cell index of this population (sort keys)
-  int64_t cells;           // n1 * n2 of its instance
+  int64_t cell_off;        // first sort bin of this population (bins = grid rows)
+  int64_t cells;           // sort bins of this population (n1 rows)
 };
 
 // Device-mutable counters of one population.

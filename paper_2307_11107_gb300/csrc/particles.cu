@@ -182,51 +182,35 @@ __device__ __forceinline__ void add4(const Window& W, int i, int j, unsigned lon
   win_add(W, i + 1, j + 1, w11);
 }
 
-// Warp-cooperative deposit: lanes that hit the same cell (consecutive in the
-// warp, as after a sort by cell) first sum their weights with a segmented
-// scan; the last lane of each run adds the four corners.  Integer addition
-// makes the result independent of the order.
-__device__ __forceinline__ void deposit_warp(const Window& W, int key, int ci, int cj, W4 w, bool active) {
-  Run r = warp_runs(key, active);
-  w.w00 = run_sum(w.w00, r);
-  w.w10 = run_sum(w.w10, r);
-  w.w01 = run_sum(w.w01, r);
-  w.w11 = run_sum(w.w11, r);
-  if (active && r.rank == r.len - 1) add4(W, ci, cj, w.w00, w.w10, w.w01, w.w11);
+// Deposit of one lane's four corner weights into the window (or global
+// memory).  Integer addition makes the result independent of the order.
+__device__ __forceinline__ void deposit_lane(const Window& W, int ci, int cj, const W4& w, bool active) {
+  if (active) add4(W, ci, cj, w.w00, w.w10, w.w01, w.w11);
 }
 
-// FP32 variant: the four corner weights (S-q1)(S-q2), q1(S-q2), (S-q1)q2,
-// q1 q2 (S = 2^b) of a run follow exactly from the run's length and the sums
-// of q1, q2 and q1 q2, so only those are reduced.  A warp whose 32 lanes share
-// one cell uses the hardware warp reduction.
+// FP32 variant with fractions quantised to b bits: weights (S-q1)(S-q2),
+// q1(S-q2), (S-q1)q2, q1 q2 (S = 2^b).  When all 32 lanes share one cell the
+// warp's sums follow exactly from the sums of q1, q2 and q1 q2, taken with
+// the hardware warp reduction, and one lane adds them.
 __device__ __forceinline__ void deposit_warp_q(const Window& W, int key, int ci, int cj, unsigned q1, unsigned q2,
                                                int b, bool active) {
   const unsigned S = 1u << b;
   unsigned long long p12 = (unsigned long long)q1 * q2;
   int k0 = __shfl_sync(kFull, key, 0);
-  unsigned long long s1, s2, s12, n;
-  bool last;
   if (__all_sync(kFull, active && key == k0)) {
-    s1 = __reduce_add_sync(kFull, q1);
-    s2 = __reduce_add_sync(kFull, q2);
+    unsigned long long s1 = __reduce_add_sync(kFull, q1);
+    unsigned long long s2 = __reduce_add_sync(kFull, q2);
     unsigned lo = __reduce_add_sync(kFull, (unsigned)(p12 & 0xffffffu));
     unsigned hi = __reduce_add_sync(kFull, (unsigned)(p12 >> 24));
-    s12 = ((unsigned long long)hi << 24) + lo;
-    n = 32;
-    last = (threadIdx.x & 31) == 31;
-  } else {
-    Run r = warp_runs(key, active);
-    s1 = run_sum(q1, r);
-    s2 = run_sum(q2, r);
-    s12 = run_sum(p12, r);
-    n = (unsigned long long)r.len;
-    last = active && r.rank == r.len - 1;
-  }
-  if (last) {
-    unsigned long long SS = (unsigned long long)S * S;
-    unsigned long long w11 = s12, w10 = (unsigned long long)S * s1 - s12, w01 = (unsigned long long)S * s2 - s12;
-    unsigned long long w00 = n * SS - (unsigned long long)S * (s1 + s2) + s12;
-    add4(W, ci, cj, w00, w10, w01, w11);
+    if ((threadIdx.x & 31) == 0) {
+      unsigned long long s12 = ((unsigned long long)hi << 24) + lo;
+      unsigned long long SS = (unsigned long long)S * S;
+      add4(W, ci, cj, 32ull * SS - (unsigned long long)S * (s1 + s2) + s12, (unsigned long long)S * s1 - s12,
+           (unsigned long long)S * s2 - s12, s12);
+    }
+  } else if (active) {
+    add4(W, ci, cj, (unsigned long long)(S - q1) * (S - q2), (unsigned long long)q1 * (S - q2),
+         (unsigned long long)(S - q1) * q2, p12);
   }
 }
 
@@ -554,7 +538,7 @@ __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
         }
       }
     }
-    if (kF64) deposit_warp(W, key, di, dj, w, key >= 0);
+    if (kF64) deposit_lane(W, di, dj, w, key >= 0);
     else deposit_warp_q(W, key, di, dj, q1, q2, C.fbits >> 1, key >= 0);
    }
    __syncthreads();
@@ -724,41 +708,71 @@ __global__ void __launch_bounds__(256) k_inject(DevPtrs d) {
 }
 
 // ---------------------------------------------------------------------------
-// Counting sort of every population by cell (i-major), which also drops freed
-// slots: count -> exclusive scan over all cells -> scatter into the second
-// buffer.  Particles of a warp then mostly share a cell, so the deposit's
-// segmented sums replace most atomics.
+// Counting sort of every population by grid row (the push's deposit window
+// covers whole rows), which also drops freed slots: count -> exclusive scan
+// over all (population, row) bins -> scatter into the second buffer.  Each
+// CTA histograms its chunk in shared memory and touches the global counters
+// once per row it holds.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_sort_count(DevPtrs d) {
-  __shared__ long long s_pre[kMaxPop + 1];
+constexpr int kSortItems = 8;
+
+__device__ __forceinline__ void chunk_prefix(const DevPtrs& d, long long CH, long long* pre) {
   if (threadIdx.x == 0) {
     long long a = 0;
     for (int p = 0; p < d.n_pop; ++p) {
-      s_pre[p] = a;
-      a += d.ps[p].n;
+      pre[p] = a;
+      a += (d.ps[p].n + CH - 1) / CH;
     }
-    s_pre[d.n_pop] = a;
+    pre[d.n_pop] = a;
   }
   __syncthreads();
-  const long long total = s_pre[d.n_pop];
+}
+
+// Warp-aggregated shared-memory increment of counter[key] by one per lane;
+// returns the lane's rank among the lanes of its key (keys < 0: no-op).
+__device__ __forceinline__ unsigned warp_count(unsigned* counter, int key) {
+  const int lane = threadIdx.x & 31;
+  unsigned grp = __match_any_sync(kFull, key);
+  int leader = __ffs(grp) - 1;
+  unsigned rank = __popc(grp & ((1u << lane) - 1u));
+  unsigned base = 0;
+  if (key >= 0 && lane == leader) base = atomicAdd(counter + key, (unsigned)__popc(grp));
+  base = __shfl_sync(kFull, base, leader);
+  return base + rank;
+}
+
+__global__ void __launch_bounds__(256) k_sort_count(DevPtrs d) {
+  extern __shared__ unsigned s_hist[];
+  __shared__ long long pre[kMaxPop + 1];
+  const long long CH = (long long)kSortItems * blockDim.x;
+  chunk_prefix(d, CH, pre);
   const Real* X1 = (const Real*)d.x1;
-  const Real* X2 = (const Real*)d.x2;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
-    long long t = base + (threadIdx.x & 31);
-    bool active = t < total;
-    int pop = active ? find_pop(s_pre, d.n_pop, t) : 0;
+  for (long long chunk = blockIdx.x; chunk < pre[d.n_pop]; chunk += gridDim.x) {
+    const int pop = find_pop(pre, d.n_pop, chunk);
     const Pop& P = d.pop[pop];
-    long long slot = P.base + (active ? t - s_pre[pop] : 0);
-    Real x1 = active ? X1[slot] : Real(2);
-    long long key = -1;
-    if (active && x1 < Real(0)) {
-      Cell c = locate(d.inst[P.inst], x1, X2[slot]);
-      key = P.cell_off + (long long)c.i * d.inst[P.inst].n2 + c.j;
+    const Inst& I = d.inst[P.inst];
+    const long long npop = d.ps[pop].n, c0 = (chunk - pre[pop]) * CH;
+    const int nrows = I.n1;
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) s_hist[r] = 0u;
+    __syncthreads();
+    for (int it = 0; it < kSortItems; ++it) {
+      long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
+      int row = -1;
+      if (k < npop) {
+        long long slot = P.base + k;
+        Real x1 = X1[slot];
+        if (x1 < Real(0)) {
+          row = (int)floor((double)((x1 + Real(1)) / (Real)I.h1));
+          row = row < 0 ? 0 : (row > nrows - 1 ? nrows - 1 : row);
+        }
+        d.keys[slot] = row;
+      }
+      warp_count(s_hist, row);
     }
-    if (active) d.keys[slot] = (int32_t)key;
-    Run r = warp_runs(key, key >= 0);
-    if (key >= 0 && r.rank == 0) atomicAdd(d.cell_cnt + key, (unsigned)r.len);
+    __syncthreads();
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x)
+      if (s_hist[r]) atomicAdd(d.cell_cnt + P.cell_off + r, s_hist[r]);
+    __syncthreads();
   }
 }
 
@@ -822,39 +836,50 @@ __global__ void __launch_bounds__(1024) k_scan_add(DevPtrs d) {
   }
 }
 
-// Scatter every live particle to its cell's range of the second buffer.
+// Scatter every live particle into its row's range of the second buffer.
 __global__ void __launch_bounds__(256) k_sort_scatter(DevPtrs d) {
-  __shared__ long long s_pre[kMaxPop + 1];
-  if (threadIdx.x == 0) {
-    long long a = 0;
-    for (int p = 0; p < d.n_pop; ++p) {
-      s_pre[p] = a;
-      a += d.ps[p].n;
-    }
-    s_pre[d.n_pop] = a;
-  }
-  __syncthreads();
-  const long long total = s_pre[d.n_pop];
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
-    long long t = base + (threadIdx.x & 31);
-    bool active = t < total;
-    int pop = active ? find_pop(s_pre, d.n_pop, t) : 0;
+  extern __shared__ unsigned s_hist[];  // [2][nrows]: chunk counts, then local cursors
+  __shared__ long long pre[kMaxPop + 1];
+  const long long CH = (long long)kSortItems * blockDim.x;
+  chunk_prefix(d, CH, pre);
+  for (long long chunk = blockIdx.x; chunk < pre[d.n_pop]; chunk += gridDim.x) {
+    const int pop = find_pop(pre, d.n_pop, chunk);
     const Pop& P = d.pop[pop];
-    long long slot = P.base + (active ? t - s_pre[pop] : 0);
-    long long key = active ? (long long)d.keys[slot] : -1;
-    Run r = warp_runs(key, key >= 0);
-    unsigned first = 0;
-    if (key >= 0 && r.rank == 0) first = atomicAdd(d.cell_cnt + key, (unsigned)r.len);
-    first = __shfl_sync(kFull, first, r.start);
-    if (key >= 0) {
-      long long dst = P.base + (long long)(d.cell_off[key] - d.cell_off[P.cell_off]) + first + r.rank;
-      ((Real*)d.y1)[dst] = ((const Real*)d.x1)[slot];
-      ((Real*)d.y2)[dst] = ((const Real*)d.x2)[slot];
-      ((Real*)d.yR)[dst] = ((const Real*)d.vR)[slot];
-      ((Real*)d.yZ)[dst] = ((const Real*)d.vZ)[slot];
-      ((Real*)d.yT)[dst] = ((const Real*)d.vT)[slot];
+    const Inst& I = d.inst[P.inst];
+    const long long npop = d.ps[pop].n, c0 = (chunk - pre[pop]) * CH;
+    const int nrows = I.n1;
+    unsigned* cnt = s_hist;
+    unsigned* cur = s_hist + nrows;
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) cnt[r] = 0u;
+    __syncthreads();
+    for (int it = 0; it < kSortItems; ++it) {
+      long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
+      int row = k < npop ? d.keys[P.base + k] : -1;
+      warp_count(cnt, row);
     }
+    __syncthreads();
+    // reserve this chunk's range of every row it holds
+    const unsigned long long first = d.cell_off[P.cell_off];
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+      unsigned c = cnt[r];
+      cur[r] = c ? (unsigned)(d.cell_off[P.cell_off + r] - first) + atomicAdd(d.cell_cnt + P.cell_off + r, c) : 0u;
+    }
+    __syncthreads();
+    for (int it = 0; it < kSortItems; ++it) {
+      long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
+      long long slot = P.base + (k < npop ? k : 0);
+      int row = k < npop ? d.keys[slot] : -1;
+      unsigned pos = warp_count(cur, row);
+      if (row >= 0) {
+        long long dst = P.base + (long long)pos;
+        ((Real*)d.y1)[dst] = ((const Real*)d.x1)[slot];
+        ((Real*)d.y2)[dst] = ((const Real*)d.x2)[slot];
+        ((Real*)d.yR)[dst] = ((const Real*)d.vR)[slot];
+        ((Real*)d.yZ)[dst] = ((const Real*)d.vZ)[slot];
+        ((Real*)d.yT)[dst] = ((const Real*)d.vT)[slot];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -920,13 +945,16 @@ void launch_inject<Real>(const DevPtrs& d, long long max_inj, cudaStream_t s) {
 
 template <>
 void launch_sort<Real>(const DevPtrs& d, int grid, cudaStream_t s) {
+  const int sm = 2 * 4097 * (int)sizeof(unsigned);
+  cudaFuncSetAttribute(k_sort_count, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaMemsetAsync(d.cell_cnt, 0, sizeof(unsigned) * d.total_cells, s);
-  k_sort_count<<<grid, 256, 0, s>>>(d);
+  k_sort_count<<<grid, 256, sm, s>>>(d);
   int nb = (int)((d.total_cells + 1023) / 1024);
   k_scan_blocks<<<nb, 1024, 0, s>>>(d);
   k_scan_top<<<1, 1024, 0, s>>>(d, nb);
   k_scan_add<<<nb, 1024, 0, s>>>(d);
-  k_sort_scatter<<<grid, 256, 0, s>>>(d);
+  k_sort_scatter<<<grid, 256, sm, s>>>(d);
   k_sort_finish<<<(d.n_pop + 63) / 64, 64, 0, s>>>(d);
 }
 
