@@ -35,7 +35,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--particles", type=int, default=10_000_000, help="macro-particles per species")
+    ap.add_argument("--particles", type=int, default=None,
+                    help="macro-particles per species (default: the workload's own count)")
+    ap.add_argument("--workload", default="dipole256", choices=["dipole256", "dipole1024", "batched48", "sphere64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -113,9 +115,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload(n_per_species):
-    from paper_2307_11107_gb300.workloads import dipole_256
-    return dipole_256("fp32", n_per_species)
+def workloads(name="dipole256", n_per_species=None):
+    """List of instance configurations of the named workload."""
+    from paper_2307_11107_gb300 import workloads as W
+    if name == "batched48":
+        return W.batched_48()
+    if name == "dipole1024":
+        c = W.dipole_1024("fp32")
+    elif name == "sphere64":
+        c = W.spherical_small("fp64")
+    else:
+        c = W.dipole_256("fp32")
+    if n_per_species:
+        c["species"] = [dict(sp, n_init=n_per_species) for sp in c["species"]]
+    return [c]
+
+
+def workload(n_per_species=None, name="dipole256"):
+    return workloads(name, n_per_species)[0]
 
 
 def run_oracle(cfg, n_per_species, steps):
@@ -141,11 +158,11 @@ def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    cfg = workload(args.particles)
+    cfg = workload(args.particles, "dipole256")
     # bounded sample: keep the whole warm-up + timed run within ~2 minutes
     # (the oracle advances ~1e7 particle-steps/s on one core).
     steps = max(1, args.steps)
-    n = int(max(2000, min(args.particles, 5.0e8 / (2 * steps))))
+    n = int(max(2000, min(cfg["species"][0]["n_init"], 5.0e8 / (2 * steps))))
     val, secs = run_oracle(cfg, n, steps)
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
@@ -176,12 +193,15 @@ def main():
         pg = dist
     import paper_2307_11107_gb300 as apic
     apic.build()
-    cfg = workload(args.particles)
-    cfg["instance"] = rank  # independent replica per rank
-    cfg["history_cap"] = max(4096, args.steps + args.warmup + 8)
-    sim = apic.Sim(cfg)
-    for sp in range(2):
-        sim.load_volume(sp, args.particles)
+    cfgs = workloads(args.workload, args.particles)
+    for c in cfgs:
+        c["instance"] = c.get("instance", 0) + rank * len(cfgs)  # independent replica per rank
+        c["history_cap"] = max(4096, args.steps + args.warmup + 8)
+    cfg = cfgs[0]
+    sim = apic.Sim(cfgs)
+    for k, c in enumerate(cfgs):
+        for sp in range(len(c["species"])):
+            sim.load_volume(sp, c["species"][sp]["n_init"], instance=k)
     sim.step(args.warmup)
 
     def barrier():
@@ -200,10 +220,11 @@ def main():
         barrier()
     ms = e0.elapsed_time(e1)
     s1 = sim.stats()
-    t = sim.tallies()
-    hist = t["history"]
     # particles advanced in timed step k = resident count after step k-1
-    res = hist[-(args.steps + 1):-1, 7] + hist[-(args.steps + 1):-1, 8]
+    res = 0.0
+    for k in range(len(cfgs)):
+        hist = sim.tallies(k)["history"]
+        res = res + hist[-(args.steps + 1):-1, 7] + hist[-(args.steps + 1):-1, 8]
     advanced = float(res.sum())
     local_val = advanced / (ms / 1e3)
     sec = ms / 1e3
@@ -230,9 +251,10 @@ def main():
     achieved = BYTES_PER_PARTICLE_STEP * n_avg / (push_ms / 1e3) / 1e9
     traffic = None
     try:
-        with open(os.path.join(ROOT, "profiles", "push_traffic.json")) as f:
-            tr = json.load(f)
-        traffic = tr["dram_bytes_per_particle"] * n_avg
+        with open(os.path.join(ROOT, "profiles", "k_push_traffic.txt")) as f:
+            for line in f:
+                if line.startswith("dram_bytes_per_particle"):
+                    traffic = float(line.split()[1]) * n_avg
     except Exception:
         pass
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -243,7 +265,7 @@ def main():
     # end to end through the public API: initial state uploaded from pinned host
     # memory, then per step apic_step + apic_tallies (bins, counts, history row)
     e2e = None
-    if not args.no_e2e and rank == 0:
+    if not args.no_e2e and rank == 0 and len(cfgs) == 1:
         states = [sim.particles(sp) for sp in range(2)]
         pinned = []
         for stt in states:
@@ -289,10 +311,14 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": cfg["name"], "alpha": cfg["alpha"], "a": 2 * cfg["alpha"], "B": cfg["B"],
-                       "grid_cells": [cfg["n1"], cfg["n2"]], "particles_per_species": args.particles,
+            "config": {"workload": cfg["name"] if len(cfgs) == 1 else "batched_48_instances",
+                       "instances": len(cfgs), "alpha": cfg["alpha"], "a": 2 * cfg["alpha"], "B": cfg["B"],
+                       "grid_cells": [cfg["n1"], cfg["n2"]],
+                       "particles_per_species": [c["species"][0]["n_init"] for c in cfgs] if len(cfgs) > 1
+                       else cfg["species"][0]["n_init"],
                        "poisson_tol": cfg["poisson_tol"], "precision": "FP32 particles, FP32 multigrid in FP64 BiCGSTAB",
-                       "l2": "inputs larger than L2 (particle state %.0f MB)" % (2 * args.particles * 20 / 1e6),
+                       "l2": "inputs larger than L2 (particle state %.0f MB)" % (
+                           sum(2 * c["species"][0]["n_init"] for c in cfgs) * 20 / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "poisson_loop_iters": int(loop_iters), "clocks": clk.summary(),

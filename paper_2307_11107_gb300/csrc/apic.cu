@@ -524,6 +524,10 @@ static int setup(apic_sim* S) {
   pl.tail_threads = 512;
   pl.tail_k = 1;
   pl.tail_bytes = 0;
+  // x1-lines before restriction, x2-lines after prolongation: more Krylov
+  // iterations than smoothing both ways twice, but fewer phases per step
+  pl.smooth_split = 1;
+  if (const char* sm = std::getenv("APIC_MG_SMOOTH")) pl.smooth_split = std::string(sm) != "alt";
   if (!S->ck(set_poisson_smem<Real>(pl), "cudaFuncSetAttribute(smem)")) return S->status;
 
   // ---- device memory ----
@@ -653,8 +657,13 @@ static int setup(apic_sim* S) {
   S->push_grid = std::max(1, sms) * 4;
   // the whole Poisson solve as one cooperative kernel, unless disabled or not co-residable
   const char* env = std::getenv("APIC_SOLVER");
-  bool want_coop = !(env && std::string(env) == "kernels") && ni <= kCoopMaxInst;
+  // one cooperative launch per solve for a single instance; batches use the
+  // per-phase kernels, whose grids span every instance at once
+  bool want_coop = ni == 1;
+  if (env && std::string(env) == "kernels") want_coop = false;
+  if (env && std::string(env) == "coop") want_coop = ni <= kCoopMaxInst;
   S->coop = want_coop ? coop_blocks<Real>(S->plan, sms) : 0;
+  if (const char* nbv = std::getenv("APIC_COOP_BLOCKS")) S->coop = std::min(S->coop, std::max(1, std::atoi(nbv)));
   cudaGetLastError();
   return S->sync() ? APIC_OK : S->status;
 }

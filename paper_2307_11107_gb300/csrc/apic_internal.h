@@ -190,6 +190,7 @@ struct SolvePlan {
   int node_blocks[kMaxLevels];    // grid.x of node-parallel kernels on each level
   int tail_threads, tail_k;
   int tail_bytes;                 // dynamic shared memory of the tail kernel
+  int smooth_split;               // 1: pre-smoothing x1-lines only, post-smoothing x2-lines only
 };
 template <class Real>
 void launch_bicg_init(const DevPtrs& d, cudaStream_t s);

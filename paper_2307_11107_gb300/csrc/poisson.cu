@@ -987,9 +987,10 @@ __global__ void k_bicg_check(DevPtrs d, cudaGraphConditionalHandle h, int use_ha
 template <class Real>
 void vcycle(const DevPtrs& d, const SolvePlan& pl, cudaStream_t s) {
   const size_t R = sizeof(Real);
-  auto smooth = [&](int l) {
+  auto smooth = [&](int l, int which) {
     for (int dir = 0; dir < 2; ++dir)
       for (int color = 0; color < 2; ++color) {
+        if (pl.smooth_split && dir != which) continue;
         int nb = dir == 0 ? pl.x1_blocks[l] : pl.x2_blocks[l];
         int k = dir == 0 ? pl.x1_k[l] : pl.x2_k[l];
         size_t sm = (size_t)line_buf(k) * R;
@@ -997,13 +998,13 @@ void vcycle(const DevPtrs& d, const SolvePlan& pl, cudaStream_t s) {
       }
   };
   for (int l = 0; l < pl.max_tail; ++l) {
-    smooth(l);
+    smooth(l, 0);
     k_restrict<Real><<<dim3(pl.node_blocks[l + 1], d.n_inst), 256, 0, s>>>(d, l);
   }
   k_coarse<Real><<<dim3(64, d.n_inst), 256, 0, s>>>(d);
   for (int l = pl.max_tail - 1; l >= 0; --l) {
     k_prolong<Real><<<dim3(pl.node_blocks[l], d.n_inst), 256, 0, s>>>(d, l);
-    smooth(l);
+    smooth(l, 1);
   }
 }
 
@@ -1086,9 +1087,10 @@ template <class Real>
 __device__ bool coop_vcycle(const DevPtrs& d, const SolvePlan& pl, int nb, const int* done, unsigned char* smem) {
   Real* buf = (Real*)smem;
   BlockGroup g;
-  auto smooth = [&](int l) -> bool {
+  auto smooth = [&](int l, int which) -> bool {
     for (int dir = 0; dir < 2; ++dir)
       for (int color = 0; color < 2; ++color) {
+        if (pl.smooth_split && dir != which) continue;
         for (int inst = 0; inst < d.n_inst; ++inst) {
           const Inst& I = d.inst[inst];
           if (done[inst] || l >= I.tail_level) continue;
@@ -1105,7 +1107,7 @@ __device__ bool coop_vcycle(const DevPtrs& d, const SolvePlan& pl, int nb, const
     return true;
   };
   for (int l = 0; l < pl.max_tail; ++l) {
-    if (!smooth(l)) return false;
+    if (!smooth(l, 0)) return false;
     for (int inst = 0; inst < d.n_inst; ++inst) {
       const Inst& I = d.inst[inst];
       if (done[inst] || l >= I.tail_level) continue;
@@ -1131,7 +1133,7 @@ __device__ bool coop_vcycle(const DevPtrs& d, const SolvePlan& pl, int nb, const
         prolong_node(F, Cc, nd);
     }
     if (!grid_sync(d, nb)) return false;
-    if (!smooth(l)) return false;
+    if (!smooth(l, 1)) return false;
   }
   return true;
 }
