@@ -135,6 +135,32 @@ def workload(n_per_species=None, name="dipole256"):
     return workloads(name, n_per_species)[0]
 
 
+def replica_configs(name, n_per_species, rank, history_cap):
+    """Instance configurations of rank `rank`'s replica: the workload's own
+    instances renumbered so that no two ranks share a random stream (the
+    instance number is part of every Philox counter)."""
+    cfgs = workloads(name, n_per_species)
+    for c in cfgs:
+        c["instance"] = c.get("instance", 0) + rank * len(cfgs)
+        c["history_cap"] = history_cap
+    return cfgs
+
+
+def replica_throughput(advanced, seconds, pg=None, device="cpu"):
+    """Whole-job throughput of independent replicas: the particle-steps of all
+    ranks summed, divided by the slowest rank's time.  Returns (value,
+    particle-steps, seconds)."""
+    if pg is None:
+        return advanced / seconds, float(advanced), float(seconds)
+    import torch
+    adv = torch.tensor([float(advanced)], dtype=torch.float64, device=device)
+    sec = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    pg.all_reduce(adv)
+    pg.all_reduce(sec, op=pg.ReduceOp.MAX)
+    a, t = float(adv.item()), float(sec.item())
+    return a / t, a, t
+
+
 def run_oracle(cfg, n_per_species, steps):
     """The FP64 CPU oracle as it stands, single thread, on `steps` steps of the
     same workload with n_per_species macro-particles per species (the macro
@@ -193,10 +219,7 @@ def main():
         pg = dist
     import paper_2307_11107_gb300 as apic
     apic.build()
-    cfgs = workloads(args.workload, args.particles)
-    for c in cfgs:
-        c["instance"] = c.get("instance", 0) + rank * len(cfgs)  # independent replica per rank
-        c["history_cap"] = max(4096, args.steps + args.warmup + 8)
+    cfgs = replica_configs(args.workload, args.particles, rank, max(4096, args.steps + args.warmup + 8))
     cfg = cfgs[0]
     sim = apic.Sim(cfgs)
     for k, c in enumerate(cfgs):
@@ -226,18 +249,7 @@ def main():
         hist = sim.tallies(k)["history"]
         res = res + hist[-(args.steps + 1):-1, 7] + hist[-(args.steps + 1):-1, 8]
     advanced = float(res.sum())
-    local_val = advanced / (ms / 1e3)
-    sec = ms / 1e3
-    if pg is not None:
-        tt = torch.tensor([advanced, sec], dtype=torch.float64, device="cuda")
-        adv_t = tt.clone()
-        pg.all_reduce(adv_t)  # sum of particles advanced
-        sec_t = tt.clone()
-        pg.all_reduce(sec_t, op=pg.ReduceOp.MAX)
-        total_adv, sec = float(adv_t[0].item()), float(sec_t[1].item())
-    else:
-        total_adv = advanced
-    value = total_adv / sec
+    value, total_adv, sec = replica_throughput(advanced, ms / 1e3, pg, "cuda")
     loop_iters = s1["poisson_loop_iters"] - s0["poisson_loop_iters"]
     launches = args.steps * s1["kernels_per_step"] + loop_iters * s1["kernels_per_iter"]
 
