@@ -204,6 +204,43 @@ int apic_stats(apic_sim* sim, apic_stats_t* out);
  * apic_step. */
 int apic_step_timed(apic_sim* sim, int32_t n_steps);
 
+/* ---- Sensitivity window (forward mode) -----------------------------------
+ * Derivatives of window-averaged grain outputs with respect to the grain
+ * shape alpha (Eqs. 2-5, 7), the grain potential phi_g (boundary value of
+ * Eq. 6) and the axial magnetic field B (Eq. 9).
+ *
+ * Runs n_steps full steps from the current state (the state itself, in
+ * (x1, x2, vR, vZ, vTheta), is held fixed: its derivatives start at zero) and
+ * carries, per particle and per node, the derivatives along the three
+ * parameters through every step: deposit (node volumes and the macro-weight
+ * w = V_domain / n_init depend on alpha), the Poisson problem (three tangent
+ * problems with the step's operator, the alpha-derivative of the Eq. 7
+ * operator applied to phi on the right-hand side, d phi_g on the grain row),
+ * node gradients, the gather of Eq. 10, the Boris push, the chord and Eq. 2,
+ * absorption tallies, the surface field, and the injection of Eq. 4 at the
+ * same random numbers.  Branch decisions (absorbed, escaped, injection
+ * counts, cells) follow the values and carry no derivative (frozen-decision
+ * derivative).  The window advances the simulation by n_steps steps (the
+ * same state as apic_step up to rounding; particles are not re-sorted inside
+ * the window).
+ *
+ * values:   [n_instances][APIC_NOUT] window means (NULL: not returned)
+ * jacobian: [n_instances][APIC_NOUT][APIC_NPAR] derivatives of those means
+ *           (NULL: not returned); host arrays owned by the caller.
+ * Errors: INVALID_ARG (n_steps < 1), those of apic_step, CUDA. */
+#define APIC_NPAR 3  /* parameters: alpha, phi_g, B */
+#define APIC_NOUT 5  /* outputs: drag F_Z (absorbed Z momentum / dt), electric F_Z on the grain,
+                        current (absorbed charge / dt), torque T_z (absorbed L_z / dt), grain charge Q */
+int apic_sensitivity(apic_sim* sim, int32_t n_steps, double* values, double* jacobian);
+
+/* Gradient of L = sum_o dL_dout[o] * output_o (window means) with respect to
+ * (alpha, phi_g, B): the vector-Jacobian product of apic_sensitivity's
+ * Jacobian (three parameters, so the forward sweep costs what a reverse one
+ * would and needs no checkpoints).  dL_dout: [n_instances][APIC_NOUT];
+ * grad: [n_instances][APIC_NPAR]; host arrays owned by the caller.
+ * Errors: as apic_sensitivity; INVALID_ARG for NULL arrays. */
+int apic_adjoint(apic_sim* sim, int32_t n_steps, const double* dL_dout, double* grad);
+
 /* ---- Charge deposit without device allocation --------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory (a component living inside another

@@ -71,6 +71,11 @@ def lib():
         L.or_surface.argtypes = [vp, P(d), P(d), P(d)]
         L.or_sample_table.restype = d
         L.or_sample_table.argtypes = [vp, C.c_int, d]
+        L.or_tape_mode.argtypes = [vp, C.c_int]
+        L.or_tape_get.restype = i64
+        L.or_tape_get.argtypes = [vp, vp, P(i64), P(i64)]
+        L.or_tape_set.argtypes = [vp, vp, i64, P(i64), i64]
+        L.or_tape_status.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -231,3 +236,29 @@ class Sim:
 
     def sample_table(self, which, u):
         return lib().or_sample_table(self.h, 0 if which == "volume" else 1, float(u))
+
+    # ---- decision tape (frozen-decision runs) ----
+    TAPE_OFF, TAPE_RECORD, TAPE_REPLAY = 0, 1, 2
+
+    def tape_mode(self, mode):
+        lib().or_tape_mode(self.h, int(mode))
+
+    def tape(self):
+        """(status bytes, injection counts) recorded so far."""
+        n_nk = C.c_int64()
+        n = lib().or_tape_get(self.h, None, None, C.byref(n_nk))
+        st = np.zeros(max(n, 1), dtype=np.uint8)
+        nk = np.zeros(max(n_nk.value, 1), dtype=np.int64)
+        lib().or_tape_get(self.h, st.ctypes.data_as(C.c_void_p), nk.ctypes.data_as(C.POINTER(C.c_int64)),
+                          C.byref(n_nk))
+        return st[:n].copy(), nk[: n_nk.value].copy()
+
+    def set_tape(self, tape):
+        st, nk = (np.ascontiguousarray(a) for a in tape)
+        st = st.astype(np.uint8)
+        nk = nk.astype(np.int64)
+        lib().or_tape_set(self.h, st.ctypes.data_as(C.c_void_p), st.size,
+                          nk.ctypes.data_as(C.POINTER(C.c_int64)), nk.size)
+
+    def tape_ok(self):
+        return lib().or_tape_status(self.h) == 0

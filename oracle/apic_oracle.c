@@ -182,7 +182,49 @@ struct or_sim {
   int64_t hist_n, hist_cap, step;
   double Q, FZ;
   double step_tally[5]; /* this step's charge, pZ, Lz, heat, events (history) */
+  /* decision tape: one status byte per particle update and per injection
+   * draw, in processing order, and one injection count per step and species */
+  int tape_mode;        /* OR_TAPE_OFF, OR_TAPE_RECORD, OR_TAPE_REPLAY */
+  int tape_short;       /* a replay ran past the end of its tape */
+  uint8_t* tape_st;
+  int64_t tape_n, tape_cap, tape_pos;
+  int64_t* tape_nk;
+  int64_t tape_nk_n, tape_nk_cap, tape_nk_pos;
 };
+
+/* Decision of one particle update or injection draw under the tape: the
+ * natural decision (record mode stores it), or the recorded one (replay). */
+static int tape_status(or_sim* s, int natural) {
+  if (s->tape_mode == OR_TAPE_RECORD) {
+    if (s->tape_n == s->tape_cap) {
+      s->tape_cap = s->tape_cap ? 2 * s->tape_cap : 4096;
+      s->tape_st = (uint8_t*)realloc(s->tape_st, (size_t)s->tape_cap);
+    }
+    s->tape_st[s->tape_n++] = (uint8_t)natural;
+    return natural;
+  }
+  if (s->tape_mode == OR_TAPE_REPLAY) {
+    if (s->tape_pos < s->tape_n) return s->tape_st[s->tape_pos++];
+    s->tape_short = 1;
+  }
+  return natural;
+}
+
+static int64_t tape_count(or_sim* s, int64_t natural) {
+  if (s->tape_mode == OR_TAPE_RECORD) {
+    if (s->tape_nk_n == s->tape_nk_cap) {
+      s->tape_nk_cap = s->tape_nk_cap ? 2 * s->tape_nk_cap : 256;
+      s->tape_nk = (int64_t*)realloc(s->tape_nk, sizeof(int64_t) * (size_t)s->tape_nk_cap);
+    }
+    s->tape_nk[s->tape_nk_n++] = natural;
+    return natural;
+  }
+  if (s->tape_mode == OR_TAPE_REPLAY) {
+    if (s->tape_nk_pos < s->tape_nk_n) return s->tape_nk[s->tape_nk_pos++];
+    s->tape_short = 1;
+  }
+  return natural;
+}
 
 static double x1_node(const or_sim* s, int i) { return i == s->c.n1 ? s->c.x1_out : -1.0 + i * s->h1; }
 static double x2_node(const or_sim* s, int j) { return j == s->c.n2 ? 1.0 : -1.0 + j * s->h2; }
@@ -640,12 +682,14 @@ static int push_one(or_sim* s, int spi, int64_t k) {
   double vRn = c * vx + s_ * vy, vTn = -s_ * vx + c * vy;
   double rn = sqrt(Rn * Rn + Zn * Zn);
   double x2n = Zn / rn;
-  if (rn < r_grain(al, x2n)) {
+  double x1n = or_x1_of(al, rn, x2n);
+  int st = rn < r_grain(al, x2n) ? 1 : (x1n > s->c.x1_out ? 2 : 0);
+  st = tape_status(s, st);
+  if (st == 1) {
     tally(s, spi, R, Z, vx, vz, vy, dt);
     return 1;
   }
-  double x1n = or_x1_of(al, rn, x2n);
-  if (x1n > s->c.x1_out) return 2;
+  if (st == 2) return 2;
   p->x1[k] = x1n; p->x2[k] = x2n; p->vR[k] = vRn; p->vZ[k] = vz; p->vT[k] = vTn;
   return 0;
 }
@@ -682,6 +726,7 @@ static void inject(or_sim* s) {
     p->carry += s->lam[spi];
     int64_t nk = (int64_t)floor(p->carry);
     p->carry -= (double)nk;
+    nk = tape_count(s, nk);
     double vth = sqrt(s->c.sp[spi].T / s->c.sp[spi].m);
     for (int64_t k = 0; k < nk; ++k) {
       int64_t g = p->draws + k;
@@ -709,13 +754,15 @@ static void inject(or_sim* s) {
       if (Rn > 0.0) { c = X / Rn; s_ = Y / Rn; }
       double rn = sqrt(Rn * Rn + Zn * Zn);
       double x2n = Zn / rn;
-      if (rn < r_grain(al, x2n)) {
+      double x1n = or_x1_of(al, rn, x2n);
+      int st = rn < r_grain(al, x2n) ? 1 : (x1n > s->c.x1_out ? 2 : 0);
+      st = tape_status(s, st);
+      if (st == 1) {
         tally(s, spi, R, Z, vx, vz, vy, tau);
         p->absorbed++;
         continue;
       }
-      double x1n = or_x1_of(al, rn, x2n);
-      if (x1n > s->c.x1_out) { p->escaped++; continue; }
+      if (st == 2) { p->escaped++; continue; }
       sp_append(p, x1n, x2n, c * vx + s_ * vy, vz, -s_ * vx + c * vy);
     }
     p->draws += nk;
@@ -813,6 +860,7 @@ void or_destroy(or_sim* s) {
   }
   free(s->rho); free(s->phi); free(s->G1); free(s->G2); free(s->V);
   free(s->band); free(s->piv); free(s->bins); free(s->hist);
+  free(s->tape_st); free(s->tape_nk);
   free(s);
 }
 
@@ -867,3 +915,39 @@ void or_get_scalars(const or_sim* s, double* out) {
   out[7] = s->Q;
   out[8] = s->FZ;
 }
+
+/* ---- decision tape (frozen-decision runs) ----
+ * Finite-difference derivatives of a PIC window are only meaningful with the
+ * discrete decisions held fixed: a particle absorbed in one run and not in a
+ * neighbouring one changes a tally by a whole particle.  A run in record mode
+ * stores every decision; runs of perturbed parameters replay them. */
+void or_tape_mode(or_sim* s, int mode) {
+  s->tape_mode = mode;
+  s->tape_pos = 0;
+  s->tape_nk_pos = 0;
+  s->tape_short = 0;
+  if (mode == OR_TAPE_RECORD) {
+    s->tape_n = 0;
+    s->tape_nk_n = 0;
+  }
+}
+
+int64_t or_tape_get(const or_sim* s, uint8_t* st, int64_t* nk, int64_t* n_nk) {
+  if (st) memcpy(st, s->tape_st, (size_t)s->tape_n);
+  if (nk) memcpy(nk, s->tape_nk, sizeof(int64_t) * (size_t)s->tape_nk_n);
+  if (n_nk) *n_nk = s->tape_nk_n;
+  return s->tape_n;
+}
+
+void or_tape_set(or_sim* s, const uint8_t* st, int64_t n, const int64_t* nk, int64_t n_nk) {
+  s->tape_st = (uint8_t*)realloc(s->tape_st, (size_t)(n > 0 ? n : 1));
+  if (n > 0) memcpy(s->tape_st, st, (size_t)n);
+  s->tape_n = s->tape_cap = n;
+  s->tape_nk = (int64_t*)realloc(s->tape_nk, sizeof(int64_t) * (size_t)(n_nk > 0 ? n_nk : 1));
+  if (n_nk > 0) memcpy(s->tape_nk, nk, sizeof(int64_t) * (size_t)n_nk);
+  s->tape_nk_n = s->tape_nk_cap = n_nk;
+  s->tape_pos = 0;
+  s->tape_nk_pos = 0;
+}
+
+int or_tape_status(const or_sim* s) { return s->tape_short ? -1 : 0; }

@@ -75,6 +75,15 @@ void or_get_scalars(const or_sim* s, double* out);         /* w0,w1,V_dom,A_out,
 void or_surface(or_sim* s, double* En_out, double* Q, double* FZ);
 double or_sample_table(const or_sim* s, int which, double u); /* 0 volume, 1 surface */
 
+/* ---- decision tape: frozen-decision runs for finite-difference derivatives ---- */
+#define OR_TAPE_OFF 0
+#define OR_TAPE_RECORD 1  /* store every absorb/escape/keep decision and injection count */
+#define OR_TAPE_REPLAY 2  /* take them from the tape instead of the geometry */
+void or_tape_mode(or_sim* s, int mode);
+int64_t or_tape_get(const or_sim* s, uint8_t* st, int64_t* nk, int64_t* n_nk); /* returns status count */
+void or_tape_set(or_sim* s, const uint8_t* st, int64_t n, const int64_t* nk, int64_t n_nk);
+int or_tape_status(const or_sim* s); /* -1 if a replay ran past the end of its tape */
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,11 @@ NT, NH = 7, 10
 
 SYMBOLS = ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
            "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_last_error",
-           "apic_num_instances", "apic_stats", "apic_step_timed", "apic_deposit_static")
+           "apic_num_instances", "apic_stats", "apic_step_timed", "apic_deposit_static", "apic_sensitivity",
+           "apic_adjoint")
+NPAR, NOUT = 3, 5
+PARAMS = ("alpha", "phi_g", "B")
+OUTPUTS = ("drag_FZ", "electric_FZ", "current", "torque", "Q")
 NPHASE = 6
 PHASES = ("deposit_rho", "poisson", "fields", "push", "inject", "bookkeeping")
 
@@ -92,9 +96,11 @@ def load():
     L.apic_stats.argtypes = [vp, C.POINTER(Stats)]
     L.apic_step_timed.argtypes = [vp, i32]
     L.apic_deposit_static.argtypes = [C.POINTER(Grid), vp, vp, i64, C.c_double, vp, vp, vp]
+    L.apic_sensitivity.argtypes = [vp, i32, dp, dp]
+    L.apic_adjoint.argtypes = [vp, i32, dp, dp]
     for name in ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
                  "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_stats", "apic_step_timed",
-                 "apic_deposit_static"):
+                 "apic_deposit_static", "apic_sensitivity", "apic_adjoint"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -5,6 +5,8 @@ Translation units (compiled in parallel):
   poisson.cu    twice: FP64 and FP32 multigrid preconditioner
   fields.cu     node fields and bookkeeping (FP64, -fmad=false)
   apic.cu       host set-up and the C ABI
+  tangent.cu    twice: the sensitivity window's particle kernels in FP64
+                (-fmad=false, with its node kernels) and FP32
   deposit_static.cu  the deposit entry point that uses no caller-side allocation
 """
 import os
@@ -28,6 +30,8 @@ UNITS = [
     ("poisson.cu", "poisson_f32.o", ["-DAPIC_POISSON_REAL=float", "-DAPIC_POISSON_COMMON=0"]),
     ("fields.cu", "fields.o", ["-fmad=false"]),
     ("apic.cu", "apic.o", []),
+    ("tangent.cu", "tangent_f64.o", ["-DAPIC_REAL=double", "-DAPIC_TANGENT_COMMON", "-fmad=false"]),
+    ("tangent.cu", "tangent_f32.o", ["-DAPIC_REAL=float"]),
     ("deposit_static.cu", "deposit_static.o", ["-fmad=false"]),
 ]
 

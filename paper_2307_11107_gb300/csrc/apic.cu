@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "apic_internal.h"
+#include "dual.cuh"
 #include "geom.cuh"
 
 using namespace apic;
@@ -165,6 +166,10 @@ struct apic_sim {
   cudaEvent_t ev[APIC_NPHASE + 1] = {};
   double phase_ms[APIC_NPHASE] = {};
   long long timed_steps = 0;
+  long long slots = 0;                // particle slots of one buffer (all populations)
+  long long tab_total = 0;
+  TanPtrs tan{};                      // sensitivity-window state (allocated on first use)
+  bool tan_ready = false;
 
   int fail(int code, const std::string& m) {
     if (status == APIC_OK) {
@@ -244,50 +249,58 @@ int validate(const apic_config_t& c, std::string& why) {
 }
 
 // Inverse-CDF tables of x2 on [-1, 1]: volume dV/dx2 = (2 pi/3)(r_out^3 - r_g^3)
-// (Eq. 5 integrated along x1) and dA/dx2 of Eq. 4 at x1_out; also the grain area.
-void build_tables(Inst& I, std::vector<double>& tab) {
+// (Eq. 5 integrated along x1) and dA/dx2 of Eq. 4 at x1_out; also the grain
+// area.  Generic in the number type so that the sensitivity window can take
+// the same sums on dual numbers.
+template <class T>
+void tables_t(const Inst& I, T alpha, std::vector<T>& tab, T& V_dom, T& A_out, T& A_grain) {
   const GL10& g = gl10();
-  tab.assign(2 * (kTable + 1), 0.0);
-  double* cv = tab.data();
-  double* cs = tab.data() + kTable + 1;
-  double ht = 2.0 / kTable, ag = 0.0;
+  tab.assign(2 * (kTable + 1), T(0.0));
+  T* cv = tab.data();
+  T* cs = tab.data() + kTable + 1;
+  double ht = 2.0 / kTable;
+  T ag(0.0);
   for (int k = 0; k < kTable; ++k) {
-    double lo = -1.0 + k * ht, sv = 0.0, ss = 0.0, sg = 0.0;
+    double lo = -1.0 + k * ht;
+    T sv(0.0), ss(0.0), sg(0.0);
     for (int q = 0; q < 10; ++q) {
       double x2 = lo + 0.5 * (g.x[q] + 1.0) * ht, wq = 0.5 * g.w[q] * ht;
-      double ro = radius(I.alpha, I.x1_out, x2), rg = r_grain(I.alpha, x2);
-      sv += wq * (2.0 * kPi / 3.0) * (ro * ro * ro - rg * rg * rg);
-      ss += wq * area_density(I.alpha, I.x1_out, x2);
-      sg += wq * area_density(I.alpha, -1.0, x2);
+      T ro = radius(alpha, T(I.x1_out), T(x2)), rg = r_grain(alpha, T(x2));
+      sv += T(wq) * T(2.0 * kPi / 3.0) * (ro * ro * ro - rg * rg * rg);
+      ss += T(wq) * area_density(alpha, T(I.x1_out), T(x2));
+      sg += T(wq) * area_density(alpha, T(-1.0), T(x2));
     }
     cv[k + 1] = cv[k] + sv;
     cs[k + 1] = cs[k] + ss;
     ag += sg;
   }
-  I.V_dom = cv[kTable];
-  I.A_out = cs[kTable];
-  I.A_grain = ag;
+  V_dom = cv[kTable];
+  A_out = cs[kTable];
+  A_grain = ag;
 }
+
+void build_tables(Inst& I, std::vector<double>& tab) { tables_t<double>(I, I.alpha, tab, I.V_dom, I.A_out, I.A_grain); }
 
 // Hat-weighted node volumes: V_ij = integral over the (up to four) adjacent
 // cells of the bilinear weight of node (i, j) times dOmega of Eq. 5.
-void build_volumes(const Inst& I, std::vector<double>& V) {
+template <class T>
+void volumes_t(const Inst& I, T alpha, std::vector<T>& V) {
   const GL10& g = gl10();
-  V.assign((size_t)I.nodes, 0.0);
+  V.assign((size_t)I.nodes, T(0.0));
   for (int ci = 0; ci < I.n1; ++ci) {
     double xa = x1_node_h(I, ci), xb = x1_node_h(I, ci + 1);
     for (int cj = 0; cj < I.n2; ++cj) {
       double ya = x2_node_h(I, cj), yb = x2_node_h(I, cj + 1);
-      double acc[4] = {0, 0, 0, 0};
+      T acc[4] = {T(0.0), T(0.0), T(0.0), T(0.0)};
       for (int a = 0; a < 10; ++a) {
         double f1 = 0.5 * (g.x[a] + 1.0), x1 = xa + f1 * (xb - xa);
         for (int b = 0; b < 10; ++b) {
           double f2 = 0.5 * (g.x[b] + 1.0), x2 = ya + f2 * (yb - ya);
-          double wq = 0.25 * g.w[a] * g.w[b] * (xb - xa) * (yb - ya) * volume_density(I.alpha, x1, x2);
-          acc[0] += wq * (1.0 - f1) * (1.0 - f2);
-          acc[1] += wq * f1 * (1.0 - f2);
-          acc[2] += wq * (1.0 - f1) * f2;
-          acc[3] += wq * f1 * f2;
+          T wq = T(0.25 * g.w[a] * g.w[b] * (xb - xa) * (yb - ya)) * volume_density(alpha, T(x1), T(x2));
+          acc[0] += wq * T(1.0 - f1) * T(1.0 - f2);
+          acc[1] += wq * T(f1) * T(1.0 - f2);
+          acc[2] += wq * T(1.0 - f1) * T(f2);
+          acc[3] += wq * T(f1) * T(f2);
         }
       }
       V[(size_t)ci * I.N2 + cj] += acc[0];
@@ -296,6 +309,40 @@ void build_volumes(const Inst& I, std::vector<double>& V) {
       V[(size_t)(ci + 1) * I.N2 + cj + 1] += acc[3];
     }
   }
+}
+
+void build_volumes(const Inst& I, std::vector<double>& V) { volumes_t<double>(I, I.alpha, V); }
+
+// Row (i, j) of Eq. 7 with second-order differences, unscaled: the kSt
+// stencil weights (Dirichlet neighbours included); returns a1 = A / h1^2.
+template <class T>
+T fine_row(const Inst& I, T alpha, int i, int j, T w[kSt]) {
+  LapCoef<T> c = lap_coef(alpha, T(x1_node_h(I, i)), T(x2_node_h(I, j)));
+  T a1 = c.A / T(I.h1 * I.h1);
+  for (int k = 0; k < kSt; ++k) w[k] = T(0.0);
+  w[st_slot(-1, 0)] += a1;
+  w[st_slot(1, 0)] += a1;
+  w[st_slot(0, 0)] += T(-2.0) * a1;
+  T e = c.E / T(2.0 * I.h2);
+  if (j == 0) {
+    w[st_slot(0, 0)] += T(-3.0) * e;
+    w[st_slot(0, 1)] += T(4.0) * e;
+    w[kStPole] += T(-1.0) * e;
+  } else if (j == I.n2) {
+    w[st_slot(0, 0)] += T(3.0) * e;
+    w[st_slot(0, -1)] += T(-4.0) * e;
+    w[kStPole] += T(1.0) * e;
+  } else {
+    T a2 = c.C / T(I.h2 * I.h2), dd = c.D / T(4.0 * I.h1 * I.h2);
+    w[st_slot(0, -1)] += a2 - e;
+    w[st_slot(0, 1)] += a2 + e;
+    w[st_slot(0, 0)] += T(-2.0) * a2;
+    w[st_slot(1, 1)] += dd;
+    w[st_slot(-1, -1)] += dd;
+    w[st_slot(1, -1)] -= dd;
+    w[st_slot(-1, 1)] -= dd;
+  }
+  return a1;
 }
 
 // Finest-level operator: Eq. 7 with second-order differences, each row scaled
@@ -311,32 +358,9 @@ void build_fine(const Inst& I, HostLevel& L, std::vector<double>& rscale, std::v
   bbc.assign((size_t)I.nodes, 0.0);
   for (int i = 1; i < I.n1; ++i)
     for (int j = 0; j <= I.n2; ++j) {
-      LapCoef c = lap_coef(I.alpha, x1_node_h(I, i), x2_node_h(I, j));
-      double a1 = c.A / (I.h1 * I.h1);
+      double w[kSt];
+      double a1 = fine_row<double>(I, I.alpha, i, j, w);
       double sc = 1.0 / a1;
-      double w[kSt] = {0};
-      w[st_slot(-1, 0)] += a1;
-      w[st_slot(1, 0)] += a1;
-      w[st_slot(0, 0)] += -2.0 * a1;
-      double e = c.E / (2.0 * I.h2);
-      if (j == 0) {
-        w[st_slot(0, 0)] += -3.0 * e;
-        w[st_slot(0, 1)] += 4.0 * e;
-        w[kStPole] += -1.0 * e;
-      } else if (j == I.n2) {
-        w[st_slot(0, 0)] += 3.0 * e;
-        w[st_slot(0, -1)] += -4.0 * e;
-        w[kStPole] += 1.0 * e;
-      } else {
-        double a2 = c.C / (I.h2 * I.h2), dd = c.D / (4.0 * I.h1 * I.h2);
-        w[st_slot(0, -1)] += a2 - e;
-        w[st_slot(0, 1)] += a2 + e;
-        w[st_slot(0, 0)] += -2.0 * a2;
-        w[st_slot(1, 1)] += dd;
-        w[st_slot(-1, -1)] += dd;
-        w[st_slot(1, -1)] -= dd;
-        w[st_slot(-1, 1)] -= dd;
-      }
       size_t nd = (size_t)i * I.N2 + j;
       rscale[nd] = sc;
       double bb = 0.0;
@@ -497,6 +521,8 @@ static int setup(apic_sim* S) {
     S->inst.push_back(I);
   }
   S->n_pop = pop_index;
+  S->slots = slots;
+  S->tab_total = tab_total;
   if (S->n_pop > kMaxPop) return S->fail(APIC_ERR_INVALID_ARG, "too many instances x species");
 
   // ---- launch plan ----
@@ -1161,3 +1187,173 @@ extern "C" int apic_get_field(apic_sim* S, int32_t instance, int32_t which, doub
 extern "C" const char* apic_last_error(const apic_sim* S) { return S ? S->msg.c_str() : "null simulation"; }
 
 extern "C" int32_t apic_num_instances(const apic_sim* S) { return S ? S->n_inst : 0; }
+
+// ---------------------------------------------------------------------------
+// Sensitivity window: forward-mode derivatives of window-averaged outputs
+// with respect to (alpha, phi_g, B).
+// ---------------------------------------------------------------------------
+using D1h = ad::Dual<double, 1>;
+
+// Derivative tables of the set-up (node volumes, sampling tables, domain
+// volume, the unscaled Eq. 7 rows) along alpha, from the same host code run
+// on dual numbers; the phi_g Dirichlet term of the scaled system.
+template <class Real>
+static bool tangent_setup(apic_sim* S) {
+  if (S->tan_ready) return true;
+  if (!S->sync()) return false;
+  TanPtrs& t = S->tan;
+  const DevPtrs& d = S->d;
+  const long long tn = d.total_nodes;
+  const int ni = S->n_inst;
+  const size_t R = sizeof(Real);
+  t.stride = S->slots;
+  t.ds = S->dalloc(R * 5 * kNPar * (size_t)S->slots);
+  t.drho = (double*)S->dalloc(sizeof(double) * kNPar * tn);
+  t.dphi = (double*)S->dalloc(sizeof(double) * kNPar * tn);
+  t.phi0 = S->phi_save;
+  t.dG = S->dalloc(2 * R * kNPar * tn);
+  t.dV = (double*)S->dalloc(sizeof(double) * tn);
+  t.dst = (double*)S->dalloc(sizeof(double) * kSt * tn);
+  t.bbc_g = (double*)S->dalloc(sizeof(double) * tn);
+  t.dtab = (double*)S->dalloc(sizeof(double) * S->tab_total);
+  t.dlnw = (double*)S->dalloc(sizeof(double) * ni);
+  t.tally = (double*)S->dalloc(sizeof(double) * ni * kNOut * kNPar);
+  t.jac = (double*)S->dalloc(sizeof(double) * ni * kNOut * kNPar);
+  t.vals = (double*)S->dalloc(sizeof(double) * ni * kNOut);
+  if (S->status != APIC_OK) return false;
+  std::vector<double> dlnw(ni);
+  for (int k = 0; k < ni; ++k) {
+    const Inst& I = S->inst[k];
+    const D1h al = D1h::seed(I.alpha, 0);
+    std::vector<D1h> tab;
+    D1h vd, ao, ag;
+    tables_t<D1h>(I, al, tab, vd, ao, ag);
+    std::vector<double> htab(tab.size());
+    for (size_t q = 0; q < tab.size(); ++q) htab[q] = tab[q].d[0];
+    dlnw[k] = vd.d[0] / vd.v;
+    std::vector<D1h> V;
+    volumes_t<D1h>(I, al, V);
+    std::vector<double> hV(V.size());
+    for (size_t q = 0; q < V.size(); ++q) hV[q] = V[q].d[0];
+    std::vector<double> hst((size_t)kSt * I.nodes, 0.0), hbg((size_t)I.nodes, 0.0);
+    for (int i = 1; i < I.n1; ++i)
+      for (int j = 0; j <= I.n2; ++j) {
+        size_t nd = (size_t)i * I.N2 + j;
+        D1h wd[kSt];
+        fine_row<D1h>(I, al, i, j, wd);
+        for (int q = 0; q < kSt; ++q) hst[(size_t)q * I.nodes + nd] = wd[q].d[0];
+        if (i == 1) {
+          double w[kSt];
+          double sc = 1.0 / fine_row<double>(I, I.alpha, i, j, w);
+          double bb = 0.0;
+          for (int dj = -1; dj <= 1; ++dj) bb -= w[st_slot(-1, dj)] * sc;
+          hbg[nd] = bb;
+        }
+      }
+    S->h2d(t.dtab + I.tab_off, htab.data(), htab.size());
+    S->h2d(t.dV + I.node_off, hV.data(), hV.size());
+    S->h2d(t.dst + (long long)kSt * I.node_off, hst.data(), hst.size());
+    S->h2d(t.bbc_g + I.node_off, hbg.data(), hbg.size());
+    if (!S->sync()) return false;  // host vectors go out of scope
+  }
+  S->h2d(t.dlnw, dlnw.data(), dlnw.size());
+  if (!S->sync()) return false;
+  S->tan_ready = true;
+  return true;
+}
+
+// One Poisson solve of whatever right-hand side d.b holds, from the guess in d.phi.
+template <class Real>
+static bool solve_now(apic_sim* S, const DevPtrs& d) {
+  if (S->coop > 0) return S->ck(launch_solve_coop<Real>(d, S->plan, S->coop, S->stream), "cooperative solve");
+  launch_bicg_init<Real>(d, S->stream);
+  enqueue_solver_iterations_fixed<Real>(S, d, S->stream);
+  return true;
+}
+
+template <class Real>
+static int sensitivity_impl(apic_sim* S, int n, double* values, double* jac) {
+  if (!tangent_setup<Real>(S)) return S->status;
+  const TanPtrs& t = S->tan;
+  const DevPtrs d = S->view(S->par);
+  const long long tn = d.total_nodes;
+  const int ni = S->n_inst;
+  cudaStream_t s = S->stream;
+  const size_t R = sizeof(Real);
+  // the window starts from the current state, whose derivatives are zero
+  S->ck(cudaMemsetAsync(t.ds, 0, R * 5 * kNPar * (size_t)S->slots, s), "memset");
+  S->ck(cudaMemsetAsync(t.dphi, 0, sizeof(double) * kNPar * tn, s), "memset");
+  S->ck(cudaMemsetAsync(t.tally, 0, sizeof(double) * ni * kNOut * kNPar, s), "memset");
+  S->ck(cudaMemsetAsync(t.jac, 0, sizeof(double) * ni * kNOut * kNPar, s), "memset");
+  S->ck(cudaMemsetAsync(t.vals, 0, sizeof(double) * ni * kNOut, s), "memset");
+  for (int k = 0; k < n && S->status == APIC_OK; ++k) {
+    // deposit of every particle (values and derivatives), charge density
+    S->ck(cudaMemsetAsync(d.acc, 0, sizeof(unsigned long long) * 2 * tn, s), "memset");
+    launch_deposit_all<Real>(d, S->push_grid, s);
+    S->ck(cudaMemsetAsync(t.drho, 0, sizeof(double) * kNPar * tn, s), "memset");
+    launch_tan_deposit<Real>(d, t, S->push_grid, s);
+    launch_rho<Real>(d, s);
+    launch_tan_rho(d, t, s);
+    // Poisson: the step's problem, then the three tangent problems
+    if (!solve_now<Real>(S, d)) break;
+    S->ck(cudaMemcpyAsync(t.phi0, d.phi, sizeof(double) * tn, cudaMemcpyDeviceToDevice, s), "copy phi");
+    for (int p = 0; p < kNPar; ++p) {
+      launch_tan_b(d, t, p, s);
+      if (!solve_now<Real>(S, d)) break;
+      launch_tan_store(d, t, p, s);
+    }
+    S->ck(cudaMemcpyAsync(d.phi, t.phi0, sizeof(double) * tn, cudaMemcpyDeviceToDevice, s), "restore phi");
+    // node gradients and surface quantities (the step's, then their derivatives)
+    launch_gradients<Real>(d, s);
+    launch_surface(d, s);
+    for (int p = 0; p < kNPar; ++p) {
+      DevPtrs dp = d;
+      dp.phi = t.dphi + (long long)p * tn;
+      dp.G = (char*)t.dG + (size_t)p * tn * 2 * R;
+      launch_gradients<Real>(dp, s);
+    }
+    launch_tan_surface(d, t, s);
+    // particles, injection, bookkeeping
+    launch_tan_push<Real>(d, t, S->push_grid, s);
+    launch_tan_inject<Real>(d, t, S->max_inj, s);
+    launch_tan_step_end(d, t, s);
+    launch_step_end(d, s);
+    S->host_step += 1;
+  }
+  S->dirty = true;  // the accumulators no longer hold the current particles
+  if (!S->ck(cudaGetLastError(), "sensitivity launch")) return S->status;
+  std::vector<double> hv((size_t)ni * kNOut), hj((size_t)ni * kNOut * kNPar);
+  S->d2h(hv.data(), t.vals, hv.size());
+  S->d2h(hj.data(), t.jac, hj.size());
+  int rc = read_status(S);
+  if (rc != APIC_OK) return rc;
+  for (size_t q = 0; q < hv.size(); ++q)
+    if (values) values[q] = hv[q] / n;
+  for (size_t q = 0; q < hj.size(); ++q)
+    if (jac) jac[q] = hj[q] / n;
+  return APIC_OK;
+}
+
+extern "C" int apic_sensitivity(apic_sim* S, int32_t n_steps, double* values, double* jacobian) {
+  if (!S) return APIC_ERR_INVALID_ARG;
+  if (S->status != APIC_OK) return S->status;
+  if (n_steps < 1) return APIC_ERR_INVALID_ARG;
+  return S->precision == APIC_FP64 ? sensitivity_impl<double>(S, n_steps, values, jacobian)
+                                   : sensitivity_impl<float>(S, n_steps, values, jacobian);
+}
+
+extern "C" int apic_adjoint(apic_sim* S, int32_t n_steps, const double* dL_dout, double* grad) {
+  if (!S || !dL_dout || !grad) return APIC_ERR_INVALID_ARG;
+  if (S->status != APIC_OK) return S->status;
+  if (n_steps < 1) return APIC_ERR_INVALID_ARG;
+  std::vector<double> J((size_t)S->n_inst * kNOut * kNPar);
+  int rc = apic_sensitivity(S, n_steps, nullptr, J.data());
+  if (rc != APIC_OK) return rc;
+  for (int k = 0; k < S->n_inst; ++k)
+    for (int p = 0; p < kNPar; ++p) {
+      double g = 0.0;
+      for (int o = 0; o < kNOut; ++o) g += dL_dout[k * kNOut + o] * J[((size_t)k * kNOut + o) * kNPar + p];
+      grad[k * kNPar + p] = g;
+    }
+  return APIC_OK;
+}

@@ -153,6 +153,30 @@ struct DevPtrs {
   int64_t level_nodes;
 };
 
+// ---- sensitivity window (forward mode) ----
+// Derivatives with respect to kNPar parameters, index p: 0 = alpha, 1 = phi_g,
+// 2 = B.  Outputs, index o: 0 = drag F_Z (absorbed Z momentum per time),
+// 1 = electric F_Z on the grain, 2 = current, 3 = torque T_z, 4 = grain charge Q.
+constexpr int kNPar = 3;
+constexpr int kNOut = 5;
+
+struct TanPtrs {
+  void* ds;                // particle tangents: component 5 p + c (c: x1, x2, vR, vZ, vTheta) of slot s at [comp * stride + s]
+  int64_t stride;          // particle slots of one component (all populations)
+  double* drho;            // [kNPar][total_nodes]: sum of q w dW, then d rho
+  double* dphi;            // [kNPar][total_nodes]
+  double* phi0;            // primal phi (all nodes) while the tangent systems are solved
+  void* dG;                // [kNPar][total_nodes] node-gradient pairs in the particle type
+  double* dV;              // d V_node / d alpha
+  double* dst;             // d (unscaled Eq. 7 row, all kSt slots, Dirichlet neighbours kept) / d alpha [kSt][total_nodes]
+  double* bbc_g;           // Dirichlet term of phi_g = 1, phi_out = 0 (rows scaled as the solved system)
+  double* dtab;            // d (sampling tables) / d alpha, same layout as DevPtrs::tab
+  double* dlnw;            // per instance: d ln w / d alpha = (d V_dom / d alpha) / V_dom
+  double* tally;           // per instance [kNOut][kNPar]: this step's derivative tallies
+  double* jac;             // per instance [kNOut][kNPar]: sums over the window
+  double* vals;            // per instance [kNOut]: sums of the outputs over the window
+};
+
 // ---- launchers (defined in the kernel translation units) ----
 template <class Real>
 void launch_load(const DevPtrs& d, int pop, long long n0, long long count, long long draw0, int kind,
@@ -213,5 +237,18 @@ int coop_blocks(const SolvePlan& plan, int sms);
 template <class Real>
 cudaError_t launch_dense_inverse(double* work, double* fbuf, int n, Real* out, cudaStream_t s);
 void launch_finish_injection(const DevPtrs& d, int pop, cudaStream_t s);
+
+// sensitivity window (tangent.cu)
+template <class Real>
+void launch_tan_deposit(const DevPtrs& d, const TanPtrs& t, int grid, cudaStream_t s);
+template <class Real>
+void launch_tan_push(const DevPtrs& d, const TanPtrs& t, int grid, cudaStream_t s);
+template <class Real>
+void launch_tan_inject(const DevPtrs& d, const TanPtrs& t, long long max_inj, cudaStream_t s);
+void launch_tan_rho(const DevPtrs& d, const TanPtrs& t, cudaStream_t s);
+void launch_tan_b(const DevPtrs& d, const TanPtrs& t, int p, cudaStream_t s);
+void launch_tan_store(const DevPtrs& d, const TanPtrs& t, int p, cudaStream_t s);
+void launch_tan_surface(const DevPtrs& d, const TanPtrs& t, cudaStream_t s);
+void launch_tan_step_end(const DevPtrs& d, const TanPtrs& t, cudaStream_t s);
 
 }  // namespace apic

@@ -54,36 +54,40 @@ APIC_HD Metric<R> metric(R alpha, R r, R x2) {
 }
 
 // Eq. 4: dA/dx2 of the surface x1 = const.
-APIC_HD double area_density(double alpha, double x1, double x2) {
-  double r = radius(alpha, x1, x2);
-  double s2 = (1.0 - x2) * (1.0 + x2);
-  double k = alpha / (r + 2.0 * alpha * x2);
-  return 2.0 * kPi * r * r * sqrt(1.0 + s2 * k * k);
+template <class R>
+APIC_HD R area_density(R alpha, R x1, R x2) {
+  R r = radius(alpha, x1, x2);
+  R s2 = (R(1) - x2) * (R(1) + x2);
+  R k = alpha / (r + R(2) * alpha * x2);
+  return R(2.0 * kPi) * r * r * sqrt(R(1) + s2 * k * k);
 }
 
 // Eq. 5: dOmega / (dx1 dx2).
-APIC_HD double volume_density(double alpha, double x1, double x2) {
-  double r = radius(alpha, x1, x2);
-  double r2 = r * r;
-  return 2.0 * kPi * r2 * r2 / (1.0 + 2.0 * alpha * x2 / r);
+template <class R>
+APIC_HD R volume_density(R alpha, R x1, R x2) {
+  R r = radius(alpha, x1, x2);
+  R r2 = r * r;
+  return R(2.0 * kPi) * r2 * r2 / (R(1) + R(2) * alpha * x2 / r);
 }
 
 // Coefficients of Eq. 7 at (x1, x2): A d2/dx1^2 + C d2/dx2^2 + D d2/dx1dx2 + E d/dx2.
+template <class R>
 struct LapCoef {
-  double A, C, D, E;
+  R A, C, D, E;
 };
 
-APIC_HD LapCoef lap_coef(double alpha, double x1, double x2) {
-  double r = radius(alpha, x1, x2);
-  double s2 = (1.0 - x2) * (1.0 + x2);
-  double r2 = r * r;
-  double r4 = r2 * r2;
-  double q = r + 2.0 * alpha * x2;
-  LapCoef c;
+template <class R>
+APIC_HD LapCoef<R> lap_coef(R alpha, R x1, R x2) {
+  R r = radius(alpha, x1, x2);
+  R s2 = (R(1) - x2) * (R(1) + x2);
+  R r2 = r * r;
+  R r4 = r2 * r2;
+  R q = r + R(2) * alpha * x2;
+  LapCoef<R> c;
   c.A = (q * q + alpha * alpha * s2) / (r4 * r2);
   c.C = s2 / r2;
-  c.D = -2.0 * alpha * s2 / r4;
-  c.E = -2.0 * x2 / r2;
+  c.D = R(-2) * alpha * s2 / r4;
+  c.E = R(-2) * x2 / r2;
   return c;
 }
 

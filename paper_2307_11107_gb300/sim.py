@@ -183,3 +183,25 @@ class Sim:
         out = np.zeros((int(c["n1"]) + 1, int(c["n2"]) + 1))
         self._check(self._lib.apic_get_field(self.h, instance, idx, out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
+
+    def sensitivity(self, n_steps):
+        """Forward-mode sensitivities over a window of n_steps steps
+        (apic_sensitivity): window means `values` [instances, 5] of (drag F_Z,
+        electric F_Z, current, torque T_z, grain charge Q) and their
+        derivatives `jacobian` [instances, 5, 3] along (alpha, phi_g, B)."""
+        ni = len(self.cfgs)
+        vals = np.zeros((ni, _abi.NOUT))
+        jac = np.zeros((ni, _abi.NOUT, _abi.NPAR))
+        dp = C.POINTER(C.c_double)
+        self._check(self._lib.apic_sensitivity(self.h, int(n_steps), vals.ctypes.data_as(dp), jac.ctypes.data_as(dp)))
+        return dict(values=vals, jacobian=jac)
+
+    def adjoint(self, n_steps, dL_dout):
+        """Gradient [instances, 3] of sum(dL_dout * window means) along
+        (alpha, phi_g, B) (apic_adjoint)."""
+        ni = len(self.cfgs)
+        g = np.ascontiguousarray(np.broadcast_to(np.asarray(dL_dout, dtype=np.float64), (ni, _abi.NOUT)))
+        grad = np.zeros((ni, _abi.NPAR))
+        dp = C.POINTER(C.c_double)
+        self._check(self._lib.apic_adjoint(self.h, int(n_steps), g.ctypes.data_as(dp), grad.ctypes.data_as(dp)))
+        return grad

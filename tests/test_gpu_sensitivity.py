@@ -1,0 +1,117 @@
+"""Sensitivity window (forward-mode derivatives along alpha, phi_g, B) of the
+CUDA path against the oracle's frozen-decision central differences, and
+against the closed forms of the vacuum sphere."""
+import numpy as np
+import pytest
+
+from oracle.sensitivity import window_sensitivity
+from tests.inputs import random_states, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def apic():
+    import paper_2307_11107_gb300 as apic
+    apic.build()
+    return apic
+
+
+def _states(n, x1_out, seed):
+    return [random_states(n, x1_out, seed=seed), random_states(n, x1_out, seed=seed + 1, vscale=0.03)]
+
+
+def _gpu_window(apic, cfg, states, K, precision):
+    s = apic.Sim(cfg, precision=precision)
+    for sp, st in enumerate(states):
+        if st is not None:
+            s.add_particles(sp, st)
+    out = s.sensitivity(K)
+    return s, out["values"][0], out["jacobian"][0]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_vacuum_sphere(apic, precision):
+    """No particles, alpha = 0: Q = 4 pi (phi_g - phi_out)/(1 + x1_out) exactly
+    on the grid, dQ/dphi_g = 4 pi/(1 + x1_out); mirror symmetry gives
+    dQ/dalpha = 0 and F_Z = dF_Z/dphi_g = 0; B acts on particles only."""
+    cfg = workload(n1=64, n2=32, alpha=0.0, n_init=1000, no_inject=True, poisson_tol=1e-12, poisson_max_iter=60)
+    _, v, J = _gpu_window(apic, cfg, [None, None], 3, precision)
+    x1o = cfg["x1_out"]
+    assert v[4] == pytest.approx(4 * np.pi * (cfg["phi_g"] - cfg["phi_out"]) / (1 + x1o), rel=1e-9)
+    assert J[4, 1] == pytest.approx(4 * np.pi / (1 + x1o), rel=1e-9)
+    assert abs(J[4, 0]) < 1e-8 * abs(v[4])
+    assert abs(v[1]) < 1e-8 and abs(J[1, 1]) < 1e-8
+    assert np.all(J[[0, 2, 3]] == 0.0) and np.all(J[:, 2] == 0.0)
+
+
+@pytest.mark.parametrize("precision,alpha,B", [("fp64", 0.15, 0.5), ("fp64", -0.2, 1.0), ("fp32", 0.15, 0.5)])
+def test_window_against_oracle_differences(apic, precision, alpha, B):
+    """Window means and the 5 x 3 Jacobian against the oracle's central
+    differences with the decisions of its unperturbed run."""
+    n, K = 4000, 5
+    cfg = workload(n1=32, n2=16, alpha=alpha, B=B, n_init=n, x1_out=-0.1, seed=3, poisson_tol=1e-13,
+                   poisson_max_iter=80)
+    st = _states(n, cfg["x1_out"], 31)
+    if precision == "fp32":
+        st = [s.astype(np.float32).astype(np.float64) for s in st]
+    vo, Jo, _ = window_sensitivity(cfg, st, K)
+    s, vg, Jg = _gpu_window(apic, cfg, st, K, precision)
+    vscale = np.abs(vo) + 1e-12
+    scale = np.abs(Jo).max(axis=1, keepdims=True) + 1e-30
+    ev = np.abs(vg - vo) / vscale
+    eJ = np.abs(Jg - Jo) / scale
+    print(f"\n{precision} alpha={alpha} B={B}: values rel err {ev.max():.2e}, jacobian rel err (row scale) "
+          f"{eJ.max():.2e}\n oracle J =\n{Jo}\n gpu J =\n{Jg}")
+    # Row 2 (current) is q w (events) / dt under frozen decisions: its only
+    # entry, I d ln w / d alpha (~1e-5 relative), is below the rounding of the
+    # differences, so it is checked against d ln V_dom / d alpha instead.
+    rows = [0, 1, 3, 4]
+    if precision == "fp64":
+        assert ev.max() < 1e-9
+        assert eJ[rows].max() < 1e-6
+    else:
+        assert ev.max() < 1e-4
+        assert eJ[rows].max() < 1e-3
+    assert Jg[2, 1] == 0.0 and Jg[2, 2] == 0.0
+    import oracle
+    h = 1e-4
+    vp = oracle.Sim(dict(cfg, alpha=alpha + h)).scalars()["V_dom"]
+    vm = oracle.Sim(dict(cfg, alpha=alpha - h)).scalars()["V_dom"]
+    assert Jg[2, 0] == pytest.approx(vg[2] * (np.log(vp) - np.log(vm)) / (2 * h), rel=1e-5)
+    # the window advanced the simulation; stepping on is still valid
+    s.step(2)
+    assert s.tallies()["step"] == K + 2
+
+
+def test_adjoint_is_the_vector_jacobian_product(apic):
+    n, K = 3000, 4
+    cfg = workload(n1=32, n2=16, alpha=0.1, B=0.7, n_init=n, seed=5, poisson_tol=1e-13, poisson_max_iter=80)
+    st = _states(n, cfg["x1_out"], 51)
+    _, _, J = _gpu_window(apic, cfg, st, K, "fp64")
+    s = apic.Sim(cfg, precision="fp64")
+    for sp in (0, 1):
+        s.add_particles(sp, st[sp])
+    w = np.array([1.0, 1.0, 0.0, 0.0, 0.0])  # total F_Z
+    g = s.adjoint(K, w)[0]
+    assert np.allclose(g, w @ J, rtol=1e-12, atol=0.0)
+
+
+def test_batched_window_equals_single(apic):
+    """Two instances with different (alpha, phi_g, B) in one batch give the
+    values and Jacobians of their single-instance runs."""
+    n, K = 3000, 4
+    cfgs = [workload(n1=32, n2=16, alpha=0.12, B=0.5, n_init=n, seed=7, poisson_tol=1e-13, poisson_max_iter=80),
+            workload(n1=32, n2=16, alpha=-0.1, B=1.0, phi_g=-3.0, n_init=n, seed=7, instance=1,
+                     poisson_tol=1e-13, poisson_max_iter=80)]
+    sts = [_states(n, c["x1_out"], 61 + 2 * k) for k, c in enumerate(cfgs)]
+    b = apic.Sim(cfgs, precision="fp64")
+    for k in range(2):
+        for sp in (0, 1):
+            b.add_particles(sp, sts[k][sp], instance=k)
+    out = b.sensitivity(K)
+    for k in range(2):
+        _, v, J = _gpu_window(apic, cfgs[k], sts[k], K, "fp64")
+        assert np.allclose(out["values"][k], v, rtol=1e-10, atol=1e-12)
+        scale = np.abs(J).max(axis=1, keepdims=True) + 1e-30
+        assert (np.abs(out["jacobian"][k] - J) / scale).max() < 1e-8
