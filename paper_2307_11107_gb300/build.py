@@ -4,6 +4,7 @@ Translation units (compiled in parallel):
   particles.cu  twice: FP64 particles (-fmad=false, the parity build) and FP32
   poisson.cu    twice: FP64 and FP32 multigrid preconditioner
   fields.cu     node fields and bookkeeping (FP64, -fmad=false)
+  bcr.cu        block cyclic reduction solve (FP32 blocks, FP64 refinement)
   apic.cu       host set-up and the C ABI
   tangent.cu    twice: the sensitivity window's particle kernels in FP64
                 (-fmad=false, with its node kernels) and FP32
@@ -29,6 +30,7 @@ UNITS = [
     ("poisson.cu", "poisson_f64.o", ["-DAPIC_POISSON_REAL=double", "-DAPIC_POISSON_COMMON=1"]),
     ("poisson.cu", "poisson_f32.o", ["-DAPIC_POISSON_REAL=float", "-DAPIC_POISSON_COMMON=0"]),
     ("fields.cu", "fields.o", ["-fmad=false"]),
+    ("bcr.cu", "bcr.o", []),
     ("apic.cu", "apic.o", []),
     ("tangent.cu", "tangent_f64.o", ["-DAPIC_REAL=double", "-DAPIC_TANGENT_COMMON", "-fmad=false"]),
     ("tangent.cu", "tangent_f32.o", ["-DAPIC_REAL=float"]),

@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "apic_internal.h"
@@ -380,6 +381,180 @@ void build_fine(const Inst& I, HostLevel& L, std::vector<double>& rscale, std::v
     }
 }
 
+// ---- block cyclic reduction set-up (FP64 on the host, blocks stored in FP32) ----
+using Mat = std::vector<double>;  // row-major n x n
+
+void mat_mul(const Mat& a, const Mat& b, Mat& c, int n) {
+  c.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double* ci = c.data() + (size_t)i * n;
+    for (int k = 0; k < n; ++k) {
+      double aik = a[(size_t)i * n + k];
+      if (aik == 0.0) continue;
+      const double* bk = b.data() + (size_t)k * n;
+      for (int j = 0; j < n; ++j) ci[j] += aik * bk[j];
+    }
+  }
+}
+
+// Gauss-Jordan elimination with partial pivoting; false if singular.
+bool mat_inv(const Mat& a, Mat& inv, int n) {
+  Mat w(a);
+  inv.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    double best = std::fabs(w[(size_t)c * n + c]);
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(w[(size_t)r * n + c]) > best) {
+        best = std::fabs(w[(size_t)r * n + c]);
+        p = r;
+      }
+    if (!(best > 0.0)) return false;
+    if (p != c)
+      for (int j = 0; j < n; ++j) {
+        std::swap(w[(size_t)c * n + j], w[(size_t)p * n + j]);
+        std::swap(inv[(size_t)c * n + j], inv[(size_t)p * n + j]);
+      }
+    double s = 1.0 / w[(size_t)c * n + c];
+    for (int j = 0; j < n; ++j) {
+      w[(size_t)c * n + j] *= s;
+      inv[(size_t)c * n + j] *= s;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = w[(size_t)r * n + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        w[(size_t)r * n + j] -= f * w[(size_t)c * n + j];
+        inv[(size_t)r * n + j] -= f * inv[(size_t)c * n + j];
+      }
+    }
+  }
+  return true;
+}
+
+template <class F>
+void parallel_for(int n, F f) {
+  int T = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+  T = std::min(T, n);
+  if (T <= 1) {
+    for (int q = 0; q < n; ++q) f(q);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < T; ++t)
+    th.emplace_back([&, t] {
+      for (int q = t; q < n; q += T) f(q);
+    });
+  for (auto& x : th) x.join();
+}
+
+// Blocks of the reduction of the finest-level system (stencil of level L,
+// rows scaled, Dirichlet neighbours zero): returns false (multigrid is used
+// instead) if n1 is not a power of two or a pivot vanishes.
+bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float>& out) {
+  int K = 0;
+  while ((1 << K) < I.n1) ++K;
+  if ((1 << K) != I.n1 || K < 2 || K >= kBcrMaxK || I.N2 > kBcrMaxN) return false;
+  const int N = I.N2, M = I.n1 - 1;
+  std::vector<Mat> A(M + 2), Bm(M + 2), C(M + 2);
+  for (int i = 1; i <= M; ++i) {
+    A[i].assign((size_t)N * N, 0.0);
+    Bm[i].assign((size_t)N * N, 0.0);
+    C[i].assign((size_t)N * N, 0.0);
+    for (int j = 0; j < N; ++j) {
+      for (int dj = -1; dj <= 1; ++dj) {
+        int jj = j + dj;
+        if (jj < 0 || jj >= N) continue;
+        A[i][(size_t)j * N + jj] = L.get(st_slot(-1, dj), i, j);
+        Bm[i][(size_t)j * N + jj] = L.get(st_slot(0, dj), i, j);
+        C[i][(size_t)j * N + jj] = L.get(st_slot(1, dj), i, j);
+      }
+    }
+    Bm[i][2] += L.get(kStPole, i, 0);
+    Bm[i][(size_t)(N - 1) * N + N - 3] += L.get(kStPole, i, N - 1);
+  }
+  std::memset(&bp, 0, sizeof(bp));
+  long long nblk = 0;
+  for (int l = 1; l < K; ++l) {
+    long long ne = 1ll << (K - l), nk = ne - 1;
+    bp.P[l] = nblk;
+    nblk += nk;
+    bp.Q[l] = nblk;
+    nblk += nk;
+    bp.Binv[l] = nblk;
+    nblk += ne;
+    bp.G[l] = nblk;
+    nblk += ne;
+    bp.H[l] = nblk;
+    nblk += ne;
+  }
+  bp.last = nblk++;
+  bp.blocks = nblk;
+  bp.blk = (long long)N * N;
+  bp.K = K;
+  bp.N = N;
+  out.assign((size_t)nblk * N * N, 0.0f);
+  auto store = [&](long long idx, const Mat& m) {
+    float* o = out.data() + (size_t)idx * N * N;
+    for (int r = 0; r < N; ++r)
+      for (int c = 0; c < N; ++c) o[(size_t)c * N + r] = (float)m[(size_t)r * N + c];
+  };
+  bool ok = true;
+  for (int l = 1; l < K && ok; ++l) {
+    const int h = 1 << (l - 1), ne = 1 << (K - l), nk = ne - 1;
+    std::vector<Mat> Binv(ne);
+    std::vector<char> good(ne, 1);
+    parallel_for(ne, [&](int q) {
+      const int k = h * (2 * q + 1);
+      if (!mat_inv(Bm[k], Binv[q], N)) {
+        good[q] = 0;
+        return;
+      }
+      Mat t;
+      store(bp.Binv[l] + q, Binv[q]);
+      mat_mul(Binv[q], A[k], t, N);
+      store(bp.G[l] + q, t);
+      mat_mul(Binv[q], C[k], t, N);
+      store(bp.H[l] + q, t);
+    });
+    for (char g : good) ok = ok && g;
+    if (!ok) break;
+    std::vector<Mat> nA(nk), nB(nk), nC(nk);
+    parallel_for(nk, [&](int q) {
+      const int i = 2 * h * (q + 1);
+      Mat P, Q, t;
+      mat_mul(A[i], Binv[q], P, N);
+      mat_mul(C[i], Binv[q + 1], Q, N);
+      store(bp.P[l] + q, P);
+      store(bp.Q[l] + q, Q);
+      mat_mul(P, A[i - h], t, N);
+      nA[q].assign((size_t)N * N, 0.0);
+      for (size_t e = 0; e < t.size(); ++e) nA[q][e] = -t[e];
+      mat_mul(Q, C[i + h], t, N);
+      nC[q].assign((size_t)N * N, 0.0);
+      for (size_t e = 0; e < t.size(); ++e) nC[q][e] = -t[e];
+      nB[q] = Bm[i];
+      mat_mul(P, C[i - h], t, N);
+      for (size_t e = 0; e < t.size(); ++e) nB[q][e] -= t[e];
+      mat_mul(Q, A[i + h], t, N);
+      for (size_t e = 0; e < t.size(); ++e) nB[q][e] -= t[e];
+    });
+    for (int q = 0; q < nk; ++q) {
+      const int i = 2 * h * (q + 1);
+      A[i].swap(nA[q]);
+      Bm[i].swap(nB[q]);
+      C[i].swap(nC[q]);
+    }
+  }
+  if (!ok) return false;
+  Mat inv;
+  if (!mat_inv(Bm[1 << (K - 1)], inv, N)) return false;
+  store(bp.last, inv);
+  return true;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -555,6 +730,17 @@ static int setup(apic_sim* S) {
   pl.smooth_split = 1;
   if (const char* sm = std::getenv("APIC_MG_SMOOTH")) pl.smooth_split = std::string(sm) != "alt";
   if (!S->ck(set_poisson_smem<Real>(pl), "cudaFuncSetAttribute(smem)")) return S->status;
+  // Direct block cyclic reduction in place of multigrid: FP32 particles, one
+  // instance, n1 = 2^K, blocks within the memory budget (APIC_PRECOND=mg
+  // keeps multigrid).
+  std::vector<float> bcr_h;
+  {
+    const char* pc = std::getenv("APIC_PRECOND");
+    const Inst& I0 = S->inst[0];
+    bool want = sizeof(Real) == 4 && ni == 1 && !(I0.flags & APIC_NO_FIELD) && !(pc && std::string(pc) == "mg");
+    double bytes = 4.0 * I0.N2 * I0.N2 * 5.0 * I0.n1;
+    if (!(want && bytes <= kBcrMaxBytes && bcr_setup(I0, levels[0][0], pl.bcr, bcr_h))) pl.bcr.K = 0;
+  }
 
   // ---- device memory ----
   DevPtrs& d = S->d;
@@ -609,6 +795,12 @@ static int setup(apic_sim* S) {
   d.red = (double*)A(sizeof(double) * ni * kNRed * kRedBlocks);
   d.cred = (double*)A(sizeof(double) * ni * kNRed * kCoopMaxBlocks);
   d.bar = (unsigned*)A(sizeof(unsigned) * 4);
+  if (pl.bcr.K > 0) {
+    d.bcr = (float*)A(sizeof(float) * bcr_h.size());
+    d.bcr_f = (float*)A(sizeof(float) * (size_t)(S->inst[0].n1 - 1) * S->inst[0].N2);
+    d.bcr_e = (float*)A(sizeof(float) * (size_t)(S->inst[0].n1 - 1) * S->inst[0].N2);
+    if (d.bcr) S->h2d(d.bcr, bcr_h.data(), bcr_h.size());
+  }
   if (S->status != APIC_OK) return S->status;
 
   // ---- uploads ----
@@ -690,6 +882,11 @@ static int setup(apic_sim* S) {
   if (env && std::string(env) == "coop") want_coop = ni <= kCoopMaxInst;
   S->coop = want_coop ? coop_blocks<Real>(S->plan, sms) : 0;
   if (const char* nbv = std::getenv("APIC_COOP_BLOCKS")) S->coop = std::min(S->coop, std::max(1, std::atoi(nbv)));
+  if (pl.bcr.K > 0) {
+    int nb = bcr_blocks(sms);
+    if (nb > 0) S->coop = nb;
+    else pl.bcr.K = 0;
+  }
   cudaGetLastError();
   return S->sync() ? APIC_OK : S->status;
 }
@@ -804,6 +1001,14 @@ static bool enqueue_solver_loop(apic_sim* S, const DevPtrs& d, cudaStream_t s) {
   return cudaStreamEndCapture(S->cap2, &tmp) == cudaSuccess;
 }
 
+// One cooperative launch for the whole solve: block cyclic reduction when
+// set up, else the multigrid-preconditioned BiCGSTAB.
+template <class Real>
+static cudaError_t solve_coop(apic_sim* S, const DevPtrs& d, cudaStream_t s) {
+  if (S->plan.bcr.K > 0) return launch_solve_bcr(d, S->plan, S->coop, s);
+  return launch_solve_coop<Real>(d, S->plan, S->coop, s);
+}
+
 // Kernels of phase p of one step (deposit->rho, Poisson, fields, push, inject, bookkeeping).
 template <class Real>
 static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) {
@@ -811,7 +1016,7 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
     case 0: launch_rho<Real>(d, s); break;
     case 1:
       if (S->coop > 0) {
-        if (launch_solve_coop<Real>(d, S->plan, S->coop, s) != cudaSuccess) return false;
+        if (solve_coop<Real>(S, d, s) != cudaSuccess) return false;
         break;
       }
       launch_bicg_init<Real>(d, s);
@@ -1093,7 +1298,7 @@ static int solve_impl(apic_sim* S, int inst, const double* rho, double* phi_out)
   if (rho && !S->h2d(d.rho + I.node_off, rho, (size_t)I.nodes)) return S->status;
   launch_b_from_rho(d, inst, S->stream);
   if (S->coop > 0) {
-    if (!S->ck(launch_solve_coop<Real>(d, S->plan, S->coop, S->stream), "cooperative solve")) return S->status;
+    if (!S->ck(solve_coop<Real>(S, d, S->stream), "cooperative solve")) return S->status;
   } else {
     launch_bicg_init<Real>(d, S->stream);
     int it = 0;
@@ -1265,7 +1470,7 @@ static bool tangent_setup(apic_sim* S) {
 // One Poisson solve of whatever right-hand side d.b holds, from the guess in d.phi.
 template <class Real>
 static bool solve_now(apic_sim* S, const DevPtrs& d) {
-  if (S->coop > 0) return S->ck(launch_solve_coop<Real>(d, S->plan, S->coop, S->stream), "cooperative solve");
+  if (S->coop > 0) return S->ck(solve_coop<Real>(S, d, S->stream), "cooperative solve");
   launch_bicg_init<Real>(d, S->stream);
   enqueue_solver_iterations_fixed<Real>(S, d, S->stream);
   return true;

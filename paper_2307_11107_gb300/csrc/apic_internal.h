@@ -151,6 +151,10 @@ struct DevPtrs {
   unsigned* bar;                  // grid barrier of the cooperative solver (count, generation)
   int64_t total_nodes;
   int64_t level_nodes;
+  // block cyclic reduction (single instance): factor blocks, reduced right-hand side, correction
+  float* bcr;
+  float* bcr_f;
+  float* bcr_e;
 };
 
 // ---- sensitivity window (forward mode) ----
@@ -204,6 +208,27 @@ void launch_surface(const DevPtrs& d, cudaStream_t s);
 void launch_step_end(const DevPtrs& d, cudaStream_t s);
 void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s);
 
+// Block cyclic reduction (bcr.cu) of the finest-level system of a single
+// instance whose n1 is a power of two, 2^K: rows i = 1..2^K - 1 of N2
+// unknowns.  Reduction level l = 1..K-1 (row stride h = 2^(l-1)) eliminates
+// the rows k = h (2q + 1), q = 0..2^(K-l) - 1, and keeps i = 2h (q + 1),
+// q = 0..2^(K-l) - 2.  Dense FP32 blocks, column-major N2 x N2:
+//   kept row i:       P = A_i B_{i-h}^-1,  Q = C_i B_{i+h}^-1   (forward: f_i -= P f_{i-h} + Q f_{i+h})
+//   eliminated row k: B_k^-1, G = B_k^-1 A_k, H = B_k^-1 C_k    (back: e_k = B_k^-1 f_k - G e_{k-h} - H e_{k+h})
+//   the last row 2^(K-1): B^-1 of its fully reduced block.
+constexpr int kBcrMaxK = 13;
+constexpr int kBcrMaxN = 256;
+constexpr double kBcrMaxBytes = 256.0 * 1024 * 1024;  // FP32 blocks held on the device
+struct BcrPlan {
+  int K;                    // 0: not in use
+  int N;                    // block size N2
+  int64_t blk;              // floats per block (N * N)
+  int64_t P[kBcrMaxK], Q[kBcrMaxK];                  // first block of each kind at level l
+  int64_t Binv[kBcrMaxK], G[kBcrMaxK], H[kBcrMaxK];
+  int64_t last;
+  int64_t blocks;           // total blocks
+};
+
 // Poisson (poisson.cu): host-side launch plan of the multigrid levels.
 struct SolvePlan {
   int max_tail;                   // levels run by the multi-CTA kernels (0 .. max_tail-1)
@@ -215,6 +240,7 @@ struct SolvePlan {
   int tail_threads, tail_k;
   int tail_bytes;                 // dynamic shared memory of the tail kernel
   int smooth_split;               // 1: pre-smoothing x1-lines only, post-smoothing x2-lines only
+  BcrPlan bcr;                    // block cyclic reduction in place of multigrid (bcr.K > 0)
 };
 template <class Real>
 void launch_bicg_init(const DevPtrs& d, cudaStream_t s);
@@ -237,6 +263,11 @@ int coop_blocks(const SolvePlan& plan, int sms);
 template <class Real>
 cudaError_t launch_dense_inverse(double* work, double* fbuf, int n, Real* out, cudaStream_t s);
 void launch_finish_injection(const DevPtrs& d, int pop, cudaStream_t s);
+
+// Block cyclic reduction solve (bcr.cu): iterative refinement with an FP64
+// residual and the FP32 reduction as the correction, one cooperative launch.
+cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& plan, int blocks, cudaStream_t s);
+int bcr_blocks(int sms);
 
 // sensitivity window (tangent.cu)
 template <class Real>

@@ -33,11 +33,15 @@ def _run(apic, cfgs, steps):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_batch_equals_solo(prec):
+def test_batch_equals_solo(prec, monkeypatch):
+    """Same solver path (per-phase multigrid kernels) for the batch and each
+    instance alone: the results agree bit for bit."""
     import paper_2307_11107_gb300 as apic
     apic.build()
     cfgs = _instances(prec)
     batched = _run(apic, cfgs, 6)
+    monkeypatch.setenv("APIC_SOLVER", "kernels")
+    monkeypatch.setenv("APIC_PRECOND", "mg")
     for k, c in enumerate(cfgs):
         (rb, pb, qb, tb), = [batched[k]]
         (rs, ps, qs, ts), = _run(apic, [c], 6)
