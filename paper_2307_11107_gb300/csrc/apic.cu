@@ -282,6 +282,41 @@ void tables_t(const Inst& I, T alpha, std::vector<T>& tab, T& V_dom, T& A_out, T
 
 void build_tables(Inst& I, std::vector<double>& tab) { tables_t<double>(I, I.alpha, tab, I.V_dom, I.A_out, I.A_grain); }
 
+// Guide of each of the two tables: entry g holds the largest interval lo
+// with cdf[lo] <= (g / kTable) * cdf[kTable] (the sampler scans forward from it).
+std::vector<int32_t> guide_tables(const std::vector<double>& tab) {
+  std::vector<int32_t> g(tab.size(), 0);
+  for (int w = 0; w < 2; ++w) {
+    const double* cdf = tab.data() + w * (kTable + 1);
+    int32_t* out = g.data() + w * (kTable + 1);
+    int lo = 0;
+    for (int q = 0; q <= kTable; ++q) {
+      double t = ((double)q / kTable) * cdf[kTable];
+      while (lo + 1 < kTable && cdf[lo + 1] <= t) ++lo;
+      out[q] = lo;
+    }
+  }
+  return g;
+}
+
+// Geometry of the grain surface x1 = -1 at the x2 nodes (constant in time):
+// |grad x1| and n_Z = (dx1/dZ) / |grad x1| from the metric of Eq. 2 at
+// r_g(x2), dA/dx2 of Eq. 4, and the trapezoid weight.
+std::vector<double> surface_geometry(const Inst& I) {
+  std::vector<double> g(4 * (size_t)I.N2);
+  for (int j = 0; j <= I.n2; ++j) {
+    double x2 = x2_node_h(I, j);
+    double r = r_grain(I.alpha, x2);
+    Metric<double> m = metric(I.alpha, r, x2);
+    double gn = std::sqrt(m.x1R * m.x1R + m.x1Z * m.x1Z);
+    g[4 * j + 0] = gn;
+    g[4 * j + 1] = m.x1Z / gn;
+    g[4 * j + 2] = area_density(I.alpha, -1.0, x2);
+    g[4 * j + 3] = (j == 0 || j == I.n2) ? 0.5 * I.h2 : I.h2;
+  }
+  return g;
+}
+
 // Hat-weighted node volumes: V_ij = integral over the (up to four) adjacent
 // cells of the bilinear weight of node (i, j) times dOmega of Eq. 5.
 template <class T>
@@ -451,9 +486,10 @@ void parallel_for(int n, F f) {
 }
 
 // Blocks of the reduction of the finest-level system (stencil of level L,
-// rows scaled, Dirichlet neighbours zero): returns false (multigrid is used
-// instead) if n1 is not a power of two or a pivot vanishes.
-bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float>& out) {
+// rows scaled, Dirichlet neighbours zero) and the dense tail system T
+// (FP64, row-major, inverted on the GPU by the caller): returns false
+// (multigrid is used instead) if n1 is not a power of two or a pivot vanishes.
+bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float>& out, std::vector<double>& T) {
   int K = 0;
   while ((1 << K) < I.n1) ++K;
   if ((1 << K) != I.n1 || K < 2 || K >= kBcrMaxK || I.N2 > kBcrMaxN) return false;
@@ -476,8 +512,10 @@ bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float
     Bm[i][(size_t)(N - 1) * N + N - 3] += L.get(kStPole, i, N - 1);
   }
   std::memset(&bp, 0, sizeof(bp));
+  int Lt = 0;
+  while (Lt < K - 1 && (long long)((1 << (K - Lt)) - 1) * N > kBcrTailMax) ++Lt;
   long long nblk = 0;
-  for (int l = 1; l < K; ++l) {
+  for (int l = 1; l <= Lt; ++l) {
     long long ne = 1ll << (K - l), nk = ne - 1;
     bp.P[l] = nblk;
     nblk += nk;
@@ -490,19 +528,23 @@ bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float
     bp.H[l] = nblk;
     nblk += ne;
   }
-  bp.last = nblk++;
   bp.blocks = nblk;
-  bp.blk = (long long)N * N;
   bp.K = K;
   bp.N = N;
-  out.assign((size_t)nblk * N * N, 0.0f);
+  bp.Np = (N + 3) & ~3;
+  bp.blk = (long long)N * bp.Np;
+  bp.Lt = Lt;
+  bp.tail_m = (1 << (K - Lt)) - 1;
+  bp.tail_n = bp.tail_m * N;
+  out.assign((size_t)std::max<long long>(1, nblk) * bp.blk, 0.0f);
+  const int Np = bp.Np;
   auto store = [&](long long idx, const Mat& m) {
-    float* o = out.data() + (size_t)idx * N * N;
+    float* o = out.data() + (size_t)idx * bp.blk;
     for (int r = 0; r < N; ++r)
-      for (int c = 0; c < N; ++c) o[(size_t)c * N + r] = (float)m[(size_t)r * N + c];
+      for (int c = 0; c < N; ++c) o[(size_t)c * Np + r] = (float)m[(size_t)r * N + c];
   };
   bool ok = true;
-  for (int l = 1; l < K && ok; ++l) {
+  for (int l = 1; l <= Lt && ok; ++l) {
     const int h = 1 << (l - 1), ne = 1 << (K - l), nk = ne - 1;
     std::vector<Mat> Binv(ne);
     std::vector<char> good(ne, 1);
@@ -549,9 +591,19 @@ bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float
     }
   }
   if (!ok) return false;
-  Mat inv;
-  if (!mat_inv(Bm[1 << (K - 1)], inv, N)) return false;
-  store(bp.last, inv);
+  // the rows left, i = 2^Lt (q + 1): dense block tridiagonal system
+  const int m = bp.tail_m, n = bp.tail_n, hs = 1 << Lt;
+  T.assign((size_t)n * n, 0.0);
+  for (int q = 0; q < m; ++q) {
+    const int i = hs * (q + 1);
+    for (int r = 0; r < N; ++r)
+      for (int c = 0; c < N; ++c) {
+        size_t row = (size_t)q * N + r;
+        T[row * n + (size_t)q * N + c] = Bm[i][(size_t)r * N + c];
+        if (q > 0) T[row * n + (size_t)(q - 1) * N + c] = A[i][(size_t)r * N + c];
+        if (q < m - 1) T[row * n + (size_t)(q + 1) * N + c] = C[i][(size_t)r * N + c];
+      }
+  }
   return true;
 }
 
@@ -734,13 +786,21 @@ static int setup(apic_sim* S) {
   // instance, n1 = 2^K, blocks within the memory budget (APIC_PRECOND=mg
   // keeps multigrid).
   std::vector<float> bcr_h;
+  std::vector<double> bcr_T;
   {
     const char* pc = std::getenv("APIC_PRECOND");
     const Inst& I0 = S->inst[0];
     bool want = sizeof(Real) == 4 && ni == 1 && !(I0.flags & APIC_NO_FIELD) && !(pc && std::string(pc) == "mg");
-    double bytes = 4.0 * I0.N2 * I0.N2 * 5.0 * I0.n1;
-    if (!(want && bytes <= kBcrMaxBytes && bcr_setup(I0, levels[0][0], pl.bcr, bcr_h))) pl.bcr.K = 0;
+    double bytes = 4.0 * I0.N2 * (I0.N2 + 3) * 5.0 * I0.n1;
+    if (!(want && bytes <= kBcrMaxBytes && bcr_setup(I0, levels[0][0], pl.bcr, bcr_h, bcr_T))) pl.bcr.K = 0;
+    if (pl.bcr.K > 0) {
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (bcr_blocks(pl, sms) <= 0) pl.bcr.K = 0;  // not co-residable: multigrid
+    }
   }
+  const bool use_mg = pl.bcr.K == 0;  // the multigrid hierarchy is only set up when it is used
 
   // ---- device memory ----
   DevPtrs& d = S->d;
@@ -789,6 +849,8 @@ static int setup(apic_sim* S) {
   d.cinv = A(R * std::max<long long>(1, cinv_total));
   d.fac = A(R * std::max<long long>(1, fac_total));
   d.tab = (double*)A(sizeof(double) * tab_total);
+  d.guide = (int32_t*)A(sizeof(int32_t) * tab_total);
+  d.sgeo = (double*)A(sizeof(double) * 4 * en_total);
   d.bins = (double*)A(sizeof(double) * std::max<long long>(1, bins_total));
   d.hist = (double*)A(sizeof(double) * hist_total);
   d.en = (double*)A(sizeof(double) * en_total);
@@ -797,9 +859,30 @@ static int setup(apic_sim* S) {
   d.bar = (unsigned*)A(sizeof(unsigned) * 4);
   if (pl.bcr.K > 0) {
     d.bcr = (float*)A(sizeof(float) * bcr_h.size());
+    d.bcr_tail = (float*)A(sizeof(float) * (size_t)pl.bcr.tail_n * pl.bcr.tail_n);
     d.bcr_f = (float*)A(sizeof(float) * (size_t)(S->inst[0].n1 - 1) * S->inst[0].N2);
     d.bcr_e = (float*)A(sizeof(float) * (size_t)(S->inst[0].n1 - 1) * S->inst[0].N2);
     if (d.bcr) S->h2d(d.bcr, bcr_h.data(), bcr_h.size());
+    if (S->status != APIC_OK) return S->status;
+    // dense inverse of the tail system: Gauss-Jordan on the GPU (FP64), stored in FP32
+    const int n = pl.bcr.tail_n;
+    double* work = (double*)S->dalloc(sizeof(double) * 2 * (size_t)n * n);
+    double* fbuf = (double*)S->dalloc(sizeof(double) * (size_t)n);
+    if (!work || !fbuf) return S->status;
+    std::vector<double> aug((size_t)n * 2 * n, 0.0);
+    for (int r = 0; r < n; ++r) {
+      std::memcpy(aug.data() + (size_t)r * 2 * n, bcr_T.data() + (size_t)r * n, sizeof(double) * n);
+      aug[(size_t)r * 2 * n + n + r] = 1.0;
+    }
+    S->h2d(work, aug.data(), aug.size());
+    if (!S->ck(launch_dense_inverse<float>(work, fbuf, n, d.bcr_tail, S->stream), "dense inverse (tail)")) return S->status;
+    if (!S->sync()) return S->status;
+    for (void* q : {(void*)fbuf, (void*)work}) {
+      auto it = std::find(S->blocks.begin(), S->blocks.end(), q);
+      if (it != S->blocks.end()) S->blocks.erase(it);
+      if (S->have_alloc) S->alloc.free(q, (void*)S->stream, S->alloc.ctx);
+      else cudaFreeAsync(q, S->stream);
+    }
   }
   if (S->status != APIC_OK) return S->status;
 
@@ -810,6 +893,10 @@ static int setup(apic_sim* S) {
   for (int k = 0; k < ni; ++k) {
     const Inst& I = S->inst[k];
     S->h2d(d.tab + I.tab_off, tabs[k].data(), tabs[k].size());
+    std::vector<int32_t> guide = guide_tables(tabs[k]);
+    S->h2d(d.guide + I.tab_off, guide.data(), guide.size());
+    std::vector<double> sgeo = surface_geometry(I);
+    S->h2d(d.sgeo + 4 * I.en_off, sgeo.data(), sgeo.size());
     S->h2d(d.V + I.node_off, vols[k].data(), vols[k].size());
     S->h2d(d.rscale + I.node_off, rscs[k].data(), rscs[k].size());
     S->h2d(d.bbc + I.node_off, bbcs[k].data(), bbcs[k].size());
@@ -819,7 +906,7 @@ static int setup(apic_sim* S) {
       tmp.assign(H.st.begin(), H.st.end());
       S->h2d((Real*)d.st + I.lv[l].st, tmp.data(), tmp.size());
     }
-    {
+    if (use_mg) {
       // Gauss-Jordan on the GPU: n x 2n FP64 workspace, result stored in the particle precision
       int nu = I.coarse_n;
       double* work = (double*)S->dalloc(sizeof(double) * 2 * (size_t)nu * nu);
@@ -853,7 +940,7 @@ static int setup(apic_sim* S) {
     if (!S->sync()) return S->status;
   }
   // line factorisations of every level (constant in time)
-  for (int l = 0; l < kMaxLevels; ++l) {
+  for (int l = 0; l < kMaxLevels && use_mg; ++l) {
     int lines1 = 0, lines2 = 0, k1 = 1, k2 = 1;
     bool any = false;
     for (const Inst& I : S->inst) {
@@ -882,11 +969,7 @@ static int setup(apic_sim* S) {
   if (env && std::string(env) == "coop") want_coop = ni <= kCoopMaxInst;
   S->coop = want_coop ? coop_blocks<Real>(S->plan, sms) : 0;
   if (const char* nbv = std::getenv("APIC_COOP_BLOCKS")) S->coop = std::min(S->coop, std::max(1, std::atoi(nbv)));
-  if (pl.bcr.K > 0) {
-    int nb = bcr_blocks(sms);
-    if (nb > 0) S->coop = nb;
-    else pl.bcr.K = 0;
-  }
+  if (pl.bcr.K > 0) S->coop = bcr_blocks(pl, sms);
   cudaGetLastError();
   return S->sync() ? APIC_OK : S->status;
 }

@@ -55,7 +55,7 @@ struct Inst {
   int64_t tab_off;         // offset of the two CDF tables (volume, surface), (kTable+1) each
   int64_t bin_off;         // offset of the tally bins [n_species][n2][kNT]
   int64_t hist_off;        // offset of the history ring [hist_cap][kNH]
-  int64_t en_off;          // offset of the surface field E_n [N2]
+  int64_t en_off;          // offset of the surface field E_n [N2] (and of the surface geometry, 4 per node)
   int32_t hist_cap;
   int32_t n_species;
   int32_t pop0;            // first population of this instance
@@ -143,6 +143,8 @@ struct DevPtrs {
   void* fac;                      // line factorisations of every level
   // tables and diagnostics (FP64)
   double* tab;
+  int32_t* guide;                 // per table entry g: interval of (g / kTable) * total (same layout as tab)
+  double* sgeo;                   // grain-surface geometry per x2 node: |grad x1|, n_Z, dA/dx2, trapezoid weight
   double* bins;
   double* hist;
   double* en;
@@ -153,6 +155,7 @@ struct DevPtrs {
   int64_t level_nodes;
   // block cyclic reduction (single instance): factor blocks, reduced right-hand side, correction
   float* bcr;
+  float* bcr_tail;                // dense inverse of the tail system [tail_n][tail_n]
   float* bcr_f;
   float* bcr_e;
 };
@@ -210,22 +213,32 @@ void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s);
 
 // Block cyclic reduction (bcr.cu) of the finest-level system of a single
 // instance whose n1 is a power of two, 2^K: rows i = 1..2^K - 1 of N2
-// unknowns.  Reduction level l = 1..K-1 (row stride h = 2^(l-1)) eliminates
+// unknowns.  Reduction level l = 1..Lt (row stride h = 2^(l-1)) eliminates
 // the rows k = h (2q + 1), q = 0..2^(K-l) - 1, and keeps i = 2h (q + 1),
-// q = 0..2^(K-l) - 2.  Dense FP32 blocks, column-major N2 x N2:
+// q = 0..2^(K-l) - 2.  Dense FP32 blocks, column-major N2 x N2 (column
+// stride Np):
 //   kept row i:       P = A_i B_{i-h}^-1,  Q = C_i B_{i+h}^-1   (forward: f_i -= P f_{i-h} + Q f_{i+h})
 //   eliminated row k: B_k^-1, G = B_k^-1 A_k, H = B_k^-1 C_k    (back: e_k = B_k^-1 f_k - G e_{k-h} - H e_{k+h})
-//   the last row 2^(K-1): B^-1 of its fully reduced block.
+// The m = 2^(K-Lt) - 1 rows left after level Lt (i = 2^Lt (q + 1)) form a
+// block tridiagonal system of tail_n = m N2 unknowns whose dense inverse
+// (FP32, row-major, set up in FP64) is applied in one phase; Lt is the
+// fewest levels that bring tail_n under kBcrTailMax.
 constexpr int kBcrMaxK = 13;
 constexpr int kBcrMaxN = 256;
+constexpr int kBcrTailMax = 2048;
 constexpr double kBcrMaxBytes = 256.0 * 1024 * 1024;  // FP32 blocks held on the device
 struct BcrPlan {
   int K;                    // 0: not in use
   int N;                    // block size N2
-  int64_t blk;              // floats per block (N * N)
+  int Np;                   // column stride (N rounded up to 4 floats: 16-byte aligned columns)
+  int smem;                 // 1: a task's blocks are staged in shared memory by bulk async copies
+  int Lt;                   // reduction levels before the dense tail (0..K-1)
+  int tail_m;               // rows of the tail system
+  int tail_n;               // its unknowns (tail_m * N)
+  int pad;
+  int64_t blk;              // floats per block (N * Np)
   int64_t P[kBcrMaxK], Q[kBcrMaxK];                  // first block of each kind at level l
   int64_t Binv[kBcrMaxK], G[kBcrMaxK], H[kBcrMaxK];
-  int64_t last;
   int64_t blocks;           // total blocks
 };
 
@@ -267,7 +280,7 @@ void launch_finish_injection(const DevPtrs& d, int pop, cudaStream_t s);
 // Block cyclic reduction solve (bcr.cu): iterative refinement with an FP64
 // residual and the FP32 reduction as the correction, one cooperative launch.
 cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& plan, int blocks, cudaStream_t s);
-int bcr_blocks(int sms);
+int bcr_blocks(SolvePlan& plan, int sms);  // CTAs of the launch (0: not co-residable); sets plan.bcr.smem
 
 // sensitivity window (tangent.cu)
 template <class Real>

@@ -28,26 +28,83 @@ constexpr int kBcrThreads = 512;
 constexpr int kBcrWarps = kBcrThreads / 32;
 constexpr int kMC = kBcrMaxN / 32;  // outputs per lane
 
-// res = sum_t M_t v_t for NT column-major N x N blocks M_t (v_t in shared
-// memory), by the whole CTA: warp w takes the columns w, w + kBcrWarps, ...,
-// lane l the rows l + 32 m; the per-warp partial sums are added in warp order
-// (the result does not depend on scheduling).
-template <int NT>
-__device__ __forceinline__ void task_mv(const float* const* Mt, const float* const* vt, int N, float* red,
+// ---- bulk asynchronous copies (global -> shared, completion on an mbarrier) ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of the copy barrier (every thread).  On
+// time-out the error word gets kErrTimeout, the copies still in flight are
+// waited for (again bounded) and false is returned by every thread.
+__device__ bool mbar_wait(uint64_t* bar, unsigned parity, int32_t* err) {
+  bool ok = false;
+  for (long long k = 0; k < (1ll << 22); ++k) {
+    if (mbar_try_wait(bar, parity)) {
+      ok = true;
+      break;
+    }
+    if ((k & 1023) == 1023 && ((*(volatile int32_t*)err) & kErrTimeout)) break;
+    __nanosleep(32);
+  }
+  if (!ok) {
+    atomicOr(err, kErrTimeout);
+    for (long long k = 0; k < (1ll << 22); ++k) {
+      if (mbar_try_wait(bar, parity)) break;
+      __nanosleep(64);
+    }
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// res = sum_t M_t v_t for NT column-major blocks (column stride Np) and
+// vectors v_t in shared memory, by the whole CTA: warp w takes the columns
+// w, w + kBcrWarps, ..., lane l the rows l + 32 m; the per-warp partial sums
+// are added in warp order (the result does not depend on scheduling).
+template <int NT, bool kShared>
+__device__ __forceinline__ void task_mv(const float* const* Mt, const float* const* vt, int N, int Np, float* red,
                                         float* res) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float acc[kMC];
 #pragma unroll
   for (int m = 0; m < kMC; ++m) acc[m] = 0.0f;
+#pragma unroll 2
   for (int c = warp; c < N; c += kBcrWarps) {
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-      const float* col = Mt[t] + (long long)c * N;
+      const float* col = Mt[t] + (long long)c * Np;
       const float x = vt[t][c];
 #pragma unroll
       for (int m = 0; m < kMC; ++m) {
         const int j = lane + 32 * m;
-        if (j < N) acc[m] = fmaf(__ldg(col + j), x, acc[m]);
+        if (j < N) acc[m] = fmaf(kShared ? col[j] : __ldg(col + j), x, acc[m]);
       }
     }
   }
@@ -65,11 +122,50 @@ __device__ __forceinline__ void task_mv(const float* const* Mt, const float* con
   __syncthreads();
 }
 
+struct Ctx {
+  const BcrPlan* B;
+  const float* blk;
+  float* sbuf;      // NT staged blocks (shared memory mode)
+  uint64_t* bar;
+  unsigned parity;
+  float* red;
+  float* sres;
+  int32_t* err;
+};
+
+// res = sum_t src_t v_t: the blocks are staged in shared memory by one bulk
+// copy each (when they fit), else read from global memory.  False on a copy
+// time-out (every thread).
+template <int NT>
+__device__ bool run_task(Ctx& c, const float* const* src, const float* const* vt) {
+  const int N = c.B->N, Np = c.B->Np;
+  if (c.B->smem) {
+    const unsigned bytes = (unsigned)(c.B->blk * sizeof(float));
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(c.bar, bytes * NT);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) bulk_g2s(c.sbuf + t * c.B->blk, src[t], bytes, c.bar);
+    }
+    if (!mbar_wait(c.bar, c.parity, c.err)) return false;
+    c.parity ^= 1u;
+    const float* Ms[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) Ms[t] = c.sbuf + t * c.B->blk;
+    task_mv<NT, true>(Ms, vt, N, Np, c.red, c.sres);
+  } else {
+    task_mv<NT, false>(src, vt, N, Np, c.red, c.sres);
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePlan pl) {
+  extern __shared__ __align__(128) float s_blocks[];
   __shared__ double sh[40];
   __shared__ float sv[3][kBcrMaxN];
   __shared__ float sres[kBcrMaxN];
   __shared__ float red[kBcrWarps * kBcrMaxN];
+  __shared__ __align__(8) uint64_t s_bar;
   const BcrPlan& B = pl.bcr;
   const int nb = gridDim.x;
   const Inst& I = d.inst[0];
@@ -79,6 +175,28 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePl
   float* f = d.bcr_f;
   float* e = d.bcr_e;
   double* x = d.phi;
+  Ctx c{&B, blk, s_blocks, &s_bar, 0u, red, sres, d.err};
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    // bring this CTA's blocks of the whole reduction (and its share of the
+    // tail inverse) into L2 while the first residual is formed
+    const unsigned bytes = (unsigned)(B.blk * sizeof(float));
+    for (int l = 1; l <= B.Lt; ++l) {
+      const int ne = 1 << (K - l), nk = ne - 1;
+      for (int q = blockIdx.x; q < nk; q += nb) {
+        prefetch_l2(blk + (B.P[l] + q) * B.blk, bytes);
+        prefetch_l2(blk + (B.Q[l] + q) * B.blk, bytes);
+      }
+      for (int q = blockIdx.x; q < ne; q += nb) {
+        prefetch_l2(blk + (B.Binv[l] + q) * B.blk, bytes);
+        prefetch_l2(blk + (B.G[l] + q) * B.blk, bytes);
+        prefetch_l2(blk + (B.H[l] + q) * B.blk, bytes);
+      }
+    }
+    const long long tb = (long long)B.tail_n * B.tail_n * (long long)sizeof(float);
+    const long long share = (tb / nb) & ~15ll;
+    if (share > 0) prefetch_l2((const char*)d.bcr_tail + share * blockIdx.x, (unsigned)share);
+  }
   // |b|^2 from the right-hand-side kernel's partials (fixed order)
   if (threadIdx.x == 0) {
     double bn = 0.0;
@@ -115,7 +233,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePl
       return;
     }
     // forward reduction: f_i -= P_i f_{i-h} + Q_i f_{i+h} on the kept rows
-    for (int l = 1; l < K; ++l) {
+    for (int l = 1; l <= B.Lt; ++l) {
       const int h = 1 << (l - 1);
       const int nk = (1 << (K - l)) - 1;
       for (int q = blockIdx.x; q < nk; q += nb) {
@@ -127,29 +245,40 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePl
         __syncthreads();
         const float* Mt[2] = {blk + (B.P[l] + q) * B.blk, blk + (B.Q[l] + q) * B.blk};
         const float* vt[2] = {sv[0], sv[1]};
-        task_mv<2>(Mt, vt, N, red, sres);
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-          float v = f[(long long)(i - 1) * N + j] - sres[j];
-          f[(long long)(i - 1) * N + j] = v;
-          sv[2][j] = v;
-        }
+        if (!run_task<2>(c, Mt, vt)) return;
+        for (int j = threadIdx.x; j < N; j += blockDim.x) f[(long long)(i - 1) * N + j] -= sres[j];
         __syncthreads();
-        if (l == K - 1) {
-          // the one row left: its correction directly
-          const float* Ml[1] = {blk + B.last * B.blk};
-          const float* vl[1] = {sv[2]};
-          task_mv<1>(Ml, vl, N, red, sres);
-          for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            e[(long long)(i - 1) * N + j] = sres[j];
-            x[(long long)i * N + j] += (double)sres[j];
-          }
-          __syncthreads();
+      }
+      if (!grid_sync(d, nb)) return;
+    }
+    // the rows left, i = 2^Lt (q + 1): e = T^-1 f with the dense inverse, one
+    // output per warp (lanes over the columns, fixed-order shuffle sum)
+    {
+      const int tn = B.tail_n, hs = 1 << B.Lt;
+      float* fs = s_blocks;  // the staging buffer is free between tasks
+      for (int o = threadIdx.x; o < tn; o += blockDim.x) {
+        const int q = o / N, j = o - q * N;
+        fs[o] = f[(long long)(hs * (q + 1) - 1) * N + j];
+      }
+      __syncthreads();
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int o = blockIdx.x * kBcrWarps + warp; o < tn; o += nb * kBcrWarps) {
+        const float* row = d.bcr_tail + (long long)o * tn;
+        float a = 0.0f;
+#pragma unroll 4
+        for (int cc = lane; cc < tn; cc += 32) a = fmaf(__ldg(row + cc), fs[cc], a);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(kFull, a, off);
+        if (lane == 0) {
+          const int q = o / N, j = o - q * N, i = hs * (q + 1);
+          e[(long long)(i - 1) * N + j] = a;
+          x[(long long)i * N + j] += (double)a;
         }
       }
       if (!grid_sync(d, nb)) return;
     }
     // back substitution: e_k = B_k^-1 f_k - G_k e_{k-h} - H_k e_{k+h}; x += e
-    for (int l = K - 1; l >= 1; --l) {
+    for (int l = B.Lt; l >= 1; --l) {
       const int h = 1 << (l - 1);
       const int ne = 1 << (K - l);
       for (int q = blockIdx.x; q < ne; q += nb) {
@@ -163,7 +292,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePl
         const float* Mt[3] = {blk + (B.Binv[l] + q) * B.blk, blk + (B.G[l] + q) * B.blk,
                               blk + (B.H[l] + q) * B.blk};
         const float* vt[3] = {sv[0], sv[1], sv[2]};
-        task_mv<3>(Mt, vt, N, red, sres);
+        if (!run_task<3>(c, Mt, vt)) return;
         for (int j = threadIdx.x; j < N; j += blockDim.x) {
           e[(long long)(k - 1) * N + j] = sres[j];
           x[(long long)k * N + j] += (double)sres[j];
@@ -176,21 +305,39 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePl
   }
 }
 
+constexpr int kStaticSmem = 40 * 8 + 3 * kBcrMaxN * 4 + kBcrMaxN * 4 + kBcrWarps * kBcrMaxN * 4 + 64;
+
 }  // namespace
 
-int bcr_blocks(int sms) {
+// Dynamic shared memory: the staged blocks of one task (when they fit) or at
+// least the tail right-hand side.
+static long long dyn_bytes(const BcrPlan& b) {
+  const long long tail = (long long)b.tail_n * (long long)sizeof(float);
+  const long long staged = b.smem ? 3ll * b.blk * (long long)sizeof(float) : 0;
+  return staged > tail ? staged : tail;
+}
+
+int bcr_blocks(SolvePlan& pl, int sms) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const long long staged = 3ll * pl.bcr.blk * (long long)sizeof(float);
+  pl.bcr.smem = staged + kStaticSmem <= optin ? 1 : 0;
+  const int dyn = (int)dyn_bytes(pl.bcr);
+  if (dyn + kStaticSmem > optin) return 0;
+  if (cudaFuncSetAttribute(k_solve_bcr, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess) return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_bcr, kBcrThreads, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_bcr, kBcrThreads, dyn) != cudaSuccess) return 0;
   if (per_sm < 1) return 0;
-  int nb = sms < kCoopMaxBlocks ? sms : kCoopMaxBlocks;
-  return nb;
+  return sms < kCoopMaxBlocks ? sms : kCoopMaxBlocks;
 }
 
 cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& pl, int blocks, cudaStream_t s) {
   DevPtrs dd = d;
   SolvePlan pp = pl;
   void* args[] = {&dd, &pp};
-  return cudaLaunchCooperativeKernel((const void*)k_solve_bcr, dim3(blocks), dim3(kBcrThreads), args, 0, s);
+  const size_t dyn = (size_t)dyn_bytes(pl.bcr);
+  return cudaLaunchCooperativeKernel((const void*)k_solve_bcr, dim3(blocks), dim3(kBcrThreads), args, dyn, s);
 }
 
 }  // namespace apic

@@ -135,18 +135,13 @@ __global__ void __launch_bounds__(256) k_surface(DevPtrs d) {
   double q = 0.0, fz = 0.0;
   const double* p = d.phi + I.node_off;
   const int N2 = I.N2;
+  const double* geo = d.sgeo + 4 * I.en_off;  // |grad x1|, n_Z, dA/dx2, trapezoid weight per node
   for (int j = threadIdx.x; j <= I.n2; j += blockDim.x) {
     double En = 0.0;
     if (!nofield) {
-      double x2 = x2_node(I, j);
-      double r = r_grain(I.alpha, x2);
-      Metric<double> m = metric(I.alpha, r, x2);
-      double g = sqrt(m.x1R * m.x1R + m.x1Z * m.x1Z);
+      double g = geo[4 * j + 0], nZ = geo[4 * j + 1], dA = geo[4 * j + 2], tw = geo[4 * j + 3];
       double G1 = (-3.0 * p[j] + 4.0 * p[N2 + j] - p[2 * N2 + j]) / (2.0 * I.h1);
       En = -G1 * g;
-      double nZ = m.x1Z / g;
-      double dA = area_density(I.alpha, -1.0, x2);
-      double tw = (j == 0 || j == I.n2) ? 0.5 * I.h2 : I.h2;
       q += tw * En * dA;
       fz += tw * 0.5 * En * En * nZ * dA;
     }

@@ -42,14 +42,20 @@ __device__ __forceinline__ void draws8(const Inst& I, const Pop& P, long long g,
   out[4] = b.a; out[5] = b.b; out[6] = b.c; out[7] = b.d;
 }
 
+// Interval of a cumulative table holding t = u * cdf[kTable]: the largest lo
+// with cdf[lo] <= t.  The guide table gives the first candidate (the interval
+// of (floor(u * kTable) / kTable) * cdf[kTable] <= t), a short forward scan the
+// rest: the same interval as a binary search, in one or two dependent loads.
+__device__ __forceinline__ int table_interval(const double* cdf, const int32_t* guide, double u, double t) {
+  int lo = guide[(int)(u * kTable)];
+  while (lo + 1 < kTable && cdf[lo + 1] <= t) ++lo;
+  return lo;
+}
+
 // Inverse of a cumulative table over x2 in [-1, 1] with linear interpolation.
-__device__ Real sample_x2(const double* cdf, Real u) {
+__device__ Real sample_x2(const double* cdf, const int32_t* guide, Real u) {
   double t = (double)u * cdf[kTable];
-  int lo = 0, hi = kTable;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (cdf[mid] <= t) lo = mid; else hi = mid;
-  }
+  int lo = table_interval(cdf, guide, (double)u, t);
   double dlt = cdf[lo + 1] - cdf[lo];
   double f = dlt > 0.0 ? (t - cdf[lo]) / dlt : 0.5;
   double ht = 2.0 / kTable;

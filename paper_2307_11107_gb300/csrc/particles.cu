@@ -261,19 +261,37 @@ __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
    W.row0 = s_row0;
    W.N2 = C.N2;
    W.rows = C.N2 <= kWinMaxN2 ? kWinRows : 0;
+   // the state of the next item is loaded while the current one is pushed
+   Real nx1 = Real(2), nx2 = Real(0), nvR = Real(0), nvZ = Real(0), nvT = Real(0);
+   auto fetch = [&](int it) {
+     long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
+     if (k < npop) {
+       long long slot = pbase + k;
+       nx1 = X1[slot];
+       nx2 = X2[slot];
+       nvR = VR[slot];
+       nvZ = VZ[slot];
+       nvT = VT[slot];
+     } else {
+       nx1 = Real(2);
+     }
+   };
+   fetch(0);
    for (int it = 0; it < kPushItems; ++it) {
     long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
     bool active = k < npop;
     long long slot = pbase + (active ? k : 0);
-    Real x1 = active ? X1[slot] : Real(2);
+    const Real x1 = nx1, cx2 = nx2, cvR = nvR, cvZ = nvZ, cvT = nvT;
+    if (it + 1 < kPushItems) fetch(it + 1);
     bool alive = active && x1 < Real(0);
+    int fate = 0;  // 1 absorbed, 2 escaped
     int key = -1, di = 0, dj = 0;
     W4 w = {0, 0, 0, 0};
     unsigned q1 = 0, q2 = 0;
     if (alive && !kF64) {
       // FP32: reciprocals and rsqrt instead of divisions; the grain test
       // r < (1 + sqrt(1 + 4 alpha x2))/2 is taken on squares.
-      float x2 = X2[slot], vR = VR[slot], vZ = VZ[slot], vT = VT[slot];
+      float x2 = cx2, vR = cvR, vZ = cvZ, vT = cvT;
       const float al = C.al, dt = C.dt;
       float x1f = (float)x1;
       float disc = 1.0f - 4.0f * al * x1f * x2;
@@ -317,15 +335,13 @@ __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
       if (tr < 0.0f || tr * tr < 1.0f + 4.0f * al * x2n) {
         const Pop& P = d.pop[pop];
         absorb_tally(d, d.inst[P.inst], P, R, Z, vx, vz, vy, dt);
-        atomicAdd((unsigned long long*)&d.ps[pop].absorbed, 1ull);
         X1[slot] = Real(2);
-        push_hole(d, P, pop, k);
+        fate = 1;
       } else {
         float x1n = -irn * (1.0f + al * x2n * irn);
         if (x1n > C.x1_out) {
-          atomicAdd((unsigned long long*)&d.ps[pop].escaped, 1ull);
           X1[slot] = Real(2);
-          push_hole(d, d.pop[pop], pop, k);
+          fate = 2;
         } else {
           X1[slot] = x1n;
           X2[slot] = x2n;
@@ -344,7 +360,7 @@ __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
         }
       }
     } else if (alive) {
-      Real x2 = X2[slot], vR = VR[slot], vZ = VZ[slot], vT = VT[slot];
+      Real x2 = cx2, vR = cvR, vZ = cvZ, vT = cvT;
       const Real al = C.al, dt = C.dt;
       Real r = radius(al, x1, x2);
       Real sn = sqrt((Real(1) - x2) * (Real(1) + x2));
@@ -385,15 +401,13 @@ __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
       if (rn < r_grain(al, x2n)) {
         const Pop& P = d.pop[pop];
         absorb_tally(d, d.inst[P.inst], P, R, Z, vx, vz, vy, dt);
-        atomicAdd((unsigned long long*)&d.ps[pop].absorbed, 1ull);
         X1[slot] = Real(2);
-        push_hole(d, P, pop, k);
+        fate = 1;
       } else {
         Real x1n = x1_at(al, rn, x2n);
         if (x1n > C.x1_out) {
-          atomicAdd((unsigned long long*)&d.ps[pop].escaped, 1ull);
           X1[slot] = Real(2);
-          push_hole(d, d.pop[pop], pop, k);
+          fate = 2;
         } else {
           X1[slot] = x1n;
           X2[slot] = x2n;
@@ -406,6 +420,24 @@ __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
           dj = cn.j;
           w = weights(cn, C.fbits);
         }
+      }
+    }
+    // counters and freed slots, one atomic per warp and outcome (every lane of
+    // the chunk's warp belongs to the same population)
+    {
+      const unsigned lane = threadIdx.x & 31;
+      const unsigned m_abs = __ballot_sync(kFull, fate == 1), m_gone = __ballot_sync(kFull, fate != 0);
+      if (m_gone) {
+        const int leader = __ffs(m_gone) - 1;
+        long long h0 = 0;
+        if ((int)lane == leader) {
+          PopState& S = d.ps[pop];
+          if (m_abs) atomicAdd((unsigned long long*)&S.absorbed, (unsigned long long)__popc(m_abs));
+          if (m_gone & ~m_abs) atomicAdd((unsigned long long*)&S.escaped, (unsigned long long)__popc(m_gone & ~m_abs));
+          h0 = (long long)atomicAdd((unsigned long long*)&S.n_holes, (unsigned long long)__popc(m_gone));
+        }
+        h0 = __shfl_sync(kFull, h0, leader);
+        if (fate != 0) d.holes[d.pop[pop].base + h0 + __popc(m_gone & ((1u << lane) - 1u))] = (int32_t)k;
       }
     }
     if (kF64) deposit_lane(W, di, dj, w, key >= 0);
@@ -470,7 +502,7 @@ __global__ void k_load(DevPtrs d, int pop, long long n0, long long count, long l
   uint32_t u[8];
   draws8(I, P, draw0 + k, 1u, u);
   Real al = (Real)I.alpha;
-  Real x2 = sample_x2(d.tab + I.tab_off, unit(u[0]));
+  Real x2 = sample_x2(d.tab + I.tab_off, d.guide + I.tab_off, unit(u[0]));
   Real rg = r_grain(al, x2), ro = radius(al, (Real)I.x1_out, x2);
   Real r3 = rg * rg * rg + unit(u[1]) * (ro * ro * ro - rg * rg * rg);
   Real r = cbrt(r3);
@@ -510,11 +542,13 @@ __global__ void __launch_bounds__(256) k_inject(DevPtrs d) {
   bool active = k < S.n_inj;
   long long key = -1;
   W4 w = {0, 0, 0, 0};
+  int fate = 0;  // 1 absorbed, 2 escaped, 3 stored
+  Real x1n = Real(0), x2n = Real(0), vRn = Real(0), vZn = Real(0), vTn = Real(0);
   if (active) {
     uint32_t u[8];
     draws8(I, P, S.draws + k, 2u, u);
     Real al = (Real)I.alpha, dt = (Real)I.dt;
-    Real x2 = sample_x2(d.tab + I.tab_off + (kTable + 1), unit(u[0]));
+    Real x2 = sample_x2(d.tab + I.tab_off + (kTable + 1), d.guide + I.tab_off + (kTable + 1), unit(u[0]));
     Real vth = (Real)P.vth;
     Real vn = vth * sqrt(Real(-2) * log(unit(u[1])));
     Real ra = sqrt(Real(-2) * log(unit(u[2])));
@@ -537,35 +571,54 @@ __global__ void __launch_bounds__(256) k_inject(DevPtrs d) {
       sr = Yc / Rn;
     }
     Real rn = sqrt(Rn * Rn + Zn * Zn);
-    Real x2n = Zn / rn;
+    x2n = Zn / rn;
     if (rn < r_grain(al, x2n)) {
       absorb_tally(d, I, P, R, Z, vx, vz, vy, tau);
-      atomicAdd((unsigned long long*)&S.absorbed, 1ull);
+      fate = 1;
     } else {
-      Real x1n = x1_at(al, rn, x2n);
+      x1n = x1_at(al, rn, x2n);
       if (x1n > (Real)I.x1_out) {
-        atomicAdd((unsigned long long*)&S.escaped, 1ull);
+        fate = 2;
       } else {
-        long long sidx = (long long)atomicAdd((unsigned long long*)&S.inj_stored, 1ull);
-        long long nh = S.n_holes, n = S.n;
-        long long kk;
-        if (sidx < nh) kk = d.holes[P.base + nh - 1 - sidx];
-        else kk = n + (sidx - nh);
-        if (kk >= P.cap) {
-          atomicAdd((unsigned long long*)&S.dropped, 1ull);
-          atomicOr(d.err, kErrCapacity);
-        } else {
-          long long slot = P.base + kk;
-          ((Real*)d.x1)[slot] = x1n;
-          ((Real*)d.x2)[slot] = x2n;
-          ((Real*)d.vR)[slot] = cr * vx + sr * vy;
-          ((Real*)d.vZ)[slot] = vz;
-          ((Real*)d.vT)[slot] = -sr * vx + cr * vy;
-          Cell c = locate(I, x1n, x2n);
-          key = dep_key(I, P, c);
-          w = weights(c, P.fbits);
-        }
+        fate = 3;
+        vRn = cr * vx + sr * vy;
+        vZn = vz;
+        vTn = -sr * vx + cr * vy;
       }
+    }
+  }
+  // warp-aggregated counters: one atomic per warp and outcome (the storage
+  // counter is shared by every injected particle of the population)
+  const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+  const unsigned m_abs = __ballot_sync(kFull, fate == 1), m_esc = __ballot_sync(kFull, fate == 2);
+  const unsigned m_st = __ballot_sync(kFull, fate == 3);
+  if (lane == 0) {
+    if (m_abs) atomicAdd((unsigned long long*)&S.absorbed, (unsigned long long)__popc(m_abs));
+    if (m_esc) atomicAdd((unsigned long long*)&S.escaped, (unsigned long long)__popc(m_esc));
+  }
+  long long base = 0;
+  if (m_st) {
+    const int leader = __ffs(m_st) - 1;
+    if ((int)lane == leader) base = (long long)atomicAdd((unsigned long long*)&S.inj_stored, (unsigned long long)__popc(m_st));
+    base = __shfl_sync(kFull, base, leader);
+  }
+  if (fate == 3) {
+    const long long sidx = base + __popc(m_st & lt);
+    const long long nh = S.n_holes, n = S.n;
+    const long long kk = sidx < nh ? d.holes[P.base + nh - 1 - sidx] : n + (sidx - nh);
+    if (kk >= P.cap) {
+      atomicAdd((unsigned long long*)&S.dropped, 1ull);
+      atomicOr(d.err, kErrCapacity);
+    } else {
+      long long slot = P.base + kk;
+      ((Real*)d.x1)[slot] = x1n;
+      ((Real*)d.x2)[slot] = x2n;
+      ((Real*)d.vR)[slot] = vRn;
+      ((Real*)d.vZ)[slot] = vZn;
+      ((Real*)d.vT)[slot] = vTn;
+      Cell c = locate(I, x1n, x2n);
+      key = dep_key(I, P, c);
+      w = weights(c, P.fbits);
     }
   }
   // per-lane atomics: injected particles of a warp rarely share a cell

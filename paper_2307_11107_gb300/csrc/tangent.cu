@@ -263,11 +263,7 @@ __global__ void __launch_bounds__(256) k_tan_inject(DevPtrs d, TanPtrs t) {
   const double* dcdf = t.dtab + I.tab_off + (kTable + 1);
   Real u0 = unit(u[0]);
   double tq = (double)u0 * cdf[kTable];
-  int lo = 0, hi = kTable;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (cdf[mid] <= tq) lo = mid; else hi = mid;
-  }
+  int lo = table_interval(cdf, d.guide + I.tab_off + (kTable + 1), (double)u0, tq);
   double dlt = cdf[lo + 1] - cdf[lo];
   double f = dlt > 0.0 ? (tq - cdf[lo]) / dlt : 0.5;
   double ht = 2.0 / kTable;
