@@ -328,7 +328,8 @@ def main():
                        "grid_cells": [cfg["n1"], cfg["n2"]],
                        "particles_per_species": [c["species"][0]["n_init"] for c in cfgs] if len(cfgs) > 1
                        else cfg["species"][0]["n_init"],
-                       "poisson_tol": cfg["poisson_tol"], "precision": "FP32 particles, FP32 multigrid in FP64 BiCGSTAB",
+                       "poisson_tol": cfg["poisson_tol"],
+                       "precision": "FP32 particles; Poisson: " + st["solver"],
                        "l2": "inputs larger than L2 (particle state %.0f MB)" % (
                            sum(2 * c["species"][0]["n_init"] for c in cfgs) * 20 / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},

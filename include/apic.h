@@ -193,7 +193,15 @@ typedef struct {
   int32_t kernels_per_iter;     /* kernel launches per Krylov-loop iteration (incl. its test) */
   int64_t timed_steps;          /* steps run by apic_step_timed */
   double phase_ms[APIC_NPHASE]; /* CUDA-event time per phase, summed over timed steps */
+  int32_t solver;               /* Poisson solver in use: APIC_SOLVER_* */
+  int32_t pad;
 } apic_stats_t;
+
+/* Poisson solvers (chosen at creation) */
+#define APIC_SOLVER_MG_KERNELS 0 /* BiCGSTAB + multigrid V-cycle, one kernel per phase (batches) */
+#define APIC_SOLVER_MG_COOP 1    /* the same in one cooperative launch per solve */
+#define APIC_SOLVER_BCR 2        /* FP64 iterative refinement around an FP32 block cyclic reduction
+                                    (one instance, FP32 particles, n1 a power of two) */
 
 /* Counters of the batch (launch counts, Krylov iterations, phase times). */
 int apic_stats(apic_sim* sim, apic_stats_t* out);

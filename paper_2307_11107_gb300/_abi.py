@@ -65,7 +65,12 @@ class Grid(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("poisson_loop_iters", C.c_int64), ("kernels_per_step", C.c_int32),
-                ("kernels_per_iter", C.c_int32), ("timed_steps", C.c_int64), ("phase_ms", C.c_double * NPHASE)]
+                ("kernels_per_iter", C.c_int32), ("timed_steps", C.c_int64), ("phase_ms", C.c_double * NPHASE),
+                ("solver", C.c_int32), ("pad", C.c_int32)]
+
+
+SOLVERS = ("multigrid BiCGSTAB, per-phase kernels", "multigrid BiCGSTAB, one cooperative launch",
+           "FP32 block cyclic reduction in FP64 iterative refinement, one cooperative launch")
 
 
 _lib = None

@@ -158,6 +158,7 @@ struct apic_sim {
   std::string msg = "ok";
   long long max_inj = 0;
   int push_grid = 0;
+  int max_n2 = 0;                     // widest grid of the batch (cells in x2)
   double* phi_save = nullptr;
   int32_t* h_err = nullptr;
   bool cond_loop = true;              // Krylov loop as a graph while-node (else a fixed unrolled loop)
@@ -514,6 +515,10 @@ bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float
   std::memset(&bp, 0, sizeof(bp));
   int Lt = 0;
   while (Lt < K - 1 && (long long)((1 << (K - Lt)) - 1) * N > kBcrTailMax) ++Lt;
+  if (const char* e = std::getenv("APIC_BCR_LEVELS")) {  // tuning: more reduction levels, smaller tail
+    int v = std::atoi(e);
+    if (v >= Lt && v <= K - 1) Lt = v;
+  }
   long long nblk = 0;
   for (int l = 1; l <= Lt; ++l) {
     long long ne = 1ll << (K - l), nk = ne - 1;
@@ -536,6 +541,7 @@ bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float
   bp.Lt = Lt;
   bp.tail_m = (1 << (K - Lt)) - 1;
   bp.tail_n = bp.tail_m * N;
+  bp.tail_np = (bp.tail_n + 3) & ~3;
   out.assign((size_t)std::max<long long>(1, nblk) * bp.blk, 0.0f);
   const int Np = bp.Np;
   auto store = [&](long long idx, const Mat& m) {
@@ -859,7 +865,7 @@ static int setup(apic_sim* S) {
   d.bar = (unsigned*)A(sizeof(unsigned) * 4);
   if (pl.bcr.K > 0) {
     d.bcr = (float*)A(sizeof(float) * bcr_h.size());
-    d.bcr_tail = (float*)A(sizeof(float) * (size_t)pl.bcr.tail_n * pl.bcr.tail_n);
+    d.bcr_tail = (float*)A(sizeof(float) * (size_t)pl.bcr.tail_n * pl.bcr.tail_np);
     d.bcr_f = (float*)A(sizeof(float) * (size_t)(S->inst[0].n1 - 1) * S->inst[0].N2);
     d.bcr_e = (float*)A(sizeof(float) * (size_t)(S->inst[0].n1 - 1) * S->inst[0].N2);
     if (d.bcr) S->h2d(d.bcr, bcr_h.data(), bcr_h.size());
@@ -875,9 +881,16 @@ static int setup(apic_sim* S) {
       aug[(size_t)r * 2 * n + n + r] = 1.0;
     }
     S->h2d(work, aug.data(), aug.size());
-    if (!S->ck(launch_dense_inverse<float>(work, fbuf, n, d.bcr_tail, S->stream), "dense inverse (tail)")) return S->status;
+    float* dense = (float*)S->dalloc(sizeof(float) * (size_t)n * n);
+    if (!dense) return S->status;
+    if (!S->ck(launch_dense_inverse<float>(work, fbuf, n, dense, S->stream), "dense inverse (tail)")) return S->status;
+    // rows padded to 16 bytes (one bulk copy per CTA's row range)
+    if (!S->ck(cudaMemcpy2DAsync(d.bcr_tail, sizeof(float) * pl.bcr.tail_np, dense, sizeof(float) * n, sizeof(float) * n, n,
+                                 cudaMemcpyDeviceToDevice, S->stream),
+               "tail copy"))
+      return S->status;
     if (!S->sync()) return S->status;
-    for (void* q : {(void*)fbuf, (void*)work}) {
+    for (void* q : {(void*)dense, (void*)fbuf, (void*)work}) {
       auto it = std::find(S->blocks.begin(), S->blocks.end(), q);
       if (it != S->blocks.end()) S->blocks.erase(it);
       if (S->have_alloc) S->alloc.free(q, (void*)S->stream, S->alloc.ctx);
@@ -960,6 +973,7 @@ static int setup(apic_sim* S) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   S->push_grid = std::max(1, sms) * 4;
+  for (const Inst& I : S->inst) S->max_n2 = std::max(S->max_n2, I.n2);
   // the whole Poisson solve as one cooperative kernel, unless disabled or not co-residable
   const char* env = std::getenv("APIC_SOLVER");
   // one cooperative launch per solve for a single instance; batches use the
@@ -1113,7 +1127,7 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
       launch_gradients<Real>(d, s);
       launch_surface(d, s);
       break;
-    case 3: launch_push<Real>(d, S->push_grid, s); break;
+    case 3: launch_push<Real>(d, S->push_grid, S->max_n2, s); break;
     case 4: launch_inject<Real>(d, S->max_inj, s); break;
     case 5: launch_step_end(d, s); break;
     case 6: launch_sort<Real>(d, S->push_grid, s); break;  // not a step phase: the particle sort
@@ -1257,6 +1271,7 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
     out->kernels_per_step = 7 + (S->cond_loop ? 0 : most * out->kernels_per_iter);
   }
   out->timed_steps = S->timed_steps;
+  out->solver = S->plan.bcr.K > 0 ? APIC_SOLVER_BCR : (S->coop > 0 ? APIC_SOLVER_MG_COOP : APIC_SOLVER_MG_KERNELS);
   for (int p = 0; p < APIC_NPHASE; ++p) out->phase_ms[p] = S->phase_ms[p];
   return APIC_OK;
 }

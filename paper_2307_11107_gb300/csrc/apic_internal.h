@@ -155,7 +155,7 @@ struct DevPtrs {
   int64_t level_nodes;
   // block cyclic reduction (single instance): factor blocks, reduced right-hand side, correction
   float* bcr;
-  float* bcr_tail;                // dense inverse of the tail system [tail_n][tail_n]
+  float* bcr_tail;                // dense inverse of the tail system [tail_n][tail_np]
   float* bcr_f;
   float* bcr_e;
 };
@@ -194,7 +194,7 @@ void launch_explicit(const DevPtrs& d, int pop, long long n0, long long count, c
 template <class Real>
 void launch_deposit_all(const DevPtrs& d, int max_grid, cudaStream_t s);
 template <class Real>
-void launch_push(const DevPtrs& d, int grid, cudaStream_t s);
+void launch_push(const DevPtrs& d, int grid, int max_n2, cudaStream_t s);
 template <class Real>
 void launch_inject(const DevPtrs& d, long long max_inj, cudaStream_t s);
 template <class Real>
@@ -235,6 +235,8 @@ struct BcrPlan {
   int Lt;                   // reduction levels before the dense tail (0..K-1)
   int tail_m;               // rows of the tail system
   int tail_n;               // its unknowns (tail_m * N)
+  int tail_np;              // row stride of the tail inverse (tail_n rounded up to 4 floats)
+  int tail_rpc;             // tail rows per CTA (contiguous; set with the launch size)
   int pad;
   int64_t blk;              // floats per block (N * Np)
   int64_t P[kBcrMaxK], Q[kBcrMaxK];                  // first block of each kind at level l

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 
 #include "apic_internal.h"
 
@@ -193,9 +194,9 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePl
         prefetch_l2(blk + (B.H[l] + q) * B.blk, bytes);
       }
     }
-    const long long tb = (long long)B.tail_n * B.tail_n * (long long)sizeof(float);
-    const long long share = (tb / nb) & ~15ll;
-    if (share > 0) prefetch_l2((const char*)d.bcr_tail + share * blockIdx.x, (unsigned)share);
+    const int r0 = blockIdx.x * B.tail_rpc, r1 = min(B.tail_n, r0 + B.tail_rpc);
+    if (r1 > r0)
+      prefetch_l2(d.bcr_tail + (long long)r0 * B.tail_np, (unsigned)((r1 - r0) * B.tail_np * sizeof(float)));
   }
   // |b|^2 from the right-hand-side kernel's partials (fixed order)
   if (threadIdx.x == 0) {
@@ -251,22 +252,38 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePl
       }
       if (!grid_sync(d, nb)) return;
     }
-    // the rows left, i = 2^Lt (q + 1): e = T^-1 f with the dense inverse, one
-    // output per warp (lanes over the columns, fixed-order shuffle sum)
+    // the rows left, i = 2^Lt (q + 1): e = T^-1 f with the dense inverse; each
+    // CTA owns a contiguous range of its rows (staged in shared memory by one
+    // bulk copy when the blocks are), one row per warp, lanes over the
+    // columns, fixed-order shuffle sums
     {
-      const int tn = B.tail_n, hs = 1 << B.Lt;
-      float* fs = s_blocks;  // the staging buffer is free between tasks
+      const int tn = B.tail_n, tnp = B.tail_np, hs = 1 << B.Lt;
+      const int r0 = blockIdx.x * B.tail_rpc, r1 = min(tn, r0 + B.tail_rpc);
+      float* rows = s_blocks;
+      float* fs = s_blocks + (B.smem ? (long long)B.tail_rpc * tnp : 0);
+      const bool stage = B.smem && r1 > r0;
+      if (stage && threadIdx.x == 0) {
+        const unsigned bytes = (unsigned)((r1 - r0) * tnp * sizeof(float));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(c.bar, bytes);
+        bulk_g2s(rows, d.bcr_tail + (long long)r0 * tnp, bytes, c.bar);
+      }
       for (int o = threadIdx.x; o < tn; o += blockDim.x) {
         const int q = o / N, j = o - q * N;
         fs[o] = f[(long long)(hs * (q + 1) - 1) * N + j];
       }
-      __syncthreads();
+      if (stage) {
+        if (!mbar_wait(c.bar, c.parity, c.err)) return;
+        c.parity ^= 1u;
+      } else {
+        __syncthreads();
+      }
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      for (int o = blockIdx.x * kBcrWarps + warp; o < tn; o += nb * kBcrWarps) {
-        const float* row = d.bcr_tail + (long long)o * tn;
+      for (int o = r0 + warp; o < r1; o += kBcrWarps) {
+        const float* row = stage ? rows + (long long)(o - r0) * tnp : d.bcr_tail + (long long)o * tnp;
         float a = 0.0f;
 #pragma unroll 4
-        for (int cc = lane; cc < tn; cc += 32) a = fmaf(__ldg(row + cc), fs[cc], a);
+        for (int cc = lane; cc < tn; cc += 32) a = fmaf(row[cc], fs[cc], a);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(kFull, a, off);
         if (lane == 0) {
@@ -312,7 +329,8 @@ constexpr int kStaticSmem = 40 * 8 + 3 * kBcrMaxN * 4 + kBcrMaxN * 4 + kBcrWarps
 // Dynamic shared memory: the staged blocks of one task (when they fit) or at
 // least the tail right-hand side.
 static long long dyn_bytes(const BcrPlan& b) {
-  const long long tail = (long long)b.tail_n * (long long)sizeof(float);
+  long long tail = (long long)b.tail_np * (long long)sizeof(float);  // right-hand side
+  if (b.smem) tail += (long long)b.tail_rpc * b.tail_np * (long long)sizeof(float);  // + the CTA's rows
   const long long staged = b.smem ? 3ll * b.blk * (long long)sizeof(float) : 0;
   return staged > tail ? staged : tail;
 }
@@ -321,15 +339,19 @@ int bcr_blocks(SolvePlan& pl, int sms) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int nb = sms < kCoopMaxBlocks ? sms : kCoopMaxBlocks;
+  pl.bcr.tail_rpc = (pl.bcr.tail_n + nb - 1) / nb;
   const long long staged = 3ll * pl.bcr.blk * (long long)sizeof(float);
-  pl.bcr.smem = staged + kStaticSmem <= optin ? 1 : 0;
+  const long long tail = (long long)(pl.bcr.tail_rpc + 1) * pl.bcr.tail_np * (long long)sizeof(float);
+  pl.bcr.smem = (staged > tail ? staged : tail) + kStaticSmem <= optin ? 1 : 0;
+  if (const char* e = std::getenv("APIC_BCR_STAGE")) pl.bcr.smem = pl.bcr.smem && std::atoi(e) != 0;
   const int dyn = (int)dyn_bytes(pl.bcr);
   if (dyn + kStaticSmem > optin) return 0;
   if (cudaFuncSetAttribute(k_solve_bcr, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess) return 0;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_bcr, kBcrThreads, dyn) != cudaSuccess) return 0;
   if (per_sm < 1) return 0;
-  return sms < kCoopMaxBlocks ? sms : kCoopMaxBlocks;
+  return nb;
 }
 
 cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& pl, int blocks, cudaStream_t s) {

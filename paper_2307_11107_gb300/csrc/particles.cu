@@ -119,29 +119,64 @@ __device__ __forceinline__ void deposit_lane(const Window& W, int ci, int cj, co
   if (active) add4(W, ci, cj, w.w00, w.w10, w.w01, w.w11);
 }
 
-// FP32 variant with fractions quantised to b bits: weights (S-q1)(S-q2),
-// q1(S-q2), (S-q1)q2, q1 q2 (S = 2^b).  When all 32 lanes share one cell the
-// warp's sums follow exactly from the sums of q1, q2 and q1 q2, taken with
-// the hardware warp reduction, and one lane adds them.
-__device__ __forceinline__ void deposit_warp_q(const Window& W, int key, int ci, int cj, unsigned q1, unsigned q2,
-                                               int b, bool active) {
+// FP32 deposit through cell moments.  With fractions quantised to b bits
+// (S = 2^b) the four corner weights of a particle are (S-q1)(S-q2),
+// q1(S-q2), (S-q1)q2, q1 q2: linear in the moments (1, q1, q2, q1 q2), so a
+// cell accumulates only those, packed in two words (q1 << 32 | q2, and
+// q1 q2 + 2^52), and the corner weights of all its particles follow exactly
+// from the sums at the flush.  Within a chunk of at most 2048 particles the
+// fields cannot carry into each other (sum q1 <= 2^31, sum q1 q2 < 2^52,
+// count < 2^12).
+struct CellWin {
+  unsigned long long* s;  // shared [rows * n2 * 2]
+  unsigned long long* g;  // global node accumulator of the population (node 0)
+  int row0, rows, n2, N2;
+};
+
+__device__ __forceinline__ void corner_weights(unsigned long long a, unsigned long long m, unsigned S,
+                                               unsigned long long w[4]) {
+  const unsigned long long n = m >> 52, s12 = m & ((1ull << 52) - 1ull), s1 = a >> 32, s2 = a & 0xffffffffull;
+  const unsigned long long SS = (unsigned long long)S * S;
+  w[0] = n * SS - (unsigned long long)S * (s1 + s2) + s12;
+  w[1] = (unsigned long long)S * s1 - s12;
+  w[2] = (unsigned long long)S * s2 - s12;
+  w[3] = s12;
+}
+
+__device__ __forceinline__ void cell_add(const CellWin& W, int ci, int cj, unsigned long long a, unsigned long long m,
+                                         unsigned S) {
+  const int rr = ci - W.row0;
+  if (rr >= 0 && rr < W.rows) {
+    unsigned long long* c = W.s + 2 * (rr * W.n2 + cj);
+    atomicAdd(c, a);
+    atomicAdd(c + 1, m);
+  } else {
+    unsigned long long w[4];
+    corner_weights(a, m, S, w);
+    unsigned long long* g = W.g + (long long)ci * W.N2 + cj;
+    if (w[0]) atomicAdd(g, w[0]);
+    if (w[1]) atomicAdd(g + W.N2, w[1]);
+    if (w[2]) atomicAdd(g + 1, w[2]);
+    if (w[3]) atomicAdd(g + W.N2 + 1, w[3]);
+  }
+}
+
+// One particle per lane; when all 32 lanes share one cell the sums of the
+// moments are taken with the hardware warp reduction and one lane adds them.
+__device__ __forceinline__ void deposit_moments(const CellWin& W, int key, int ci, int cj, unsigned q1, unsigned q2,
+                                                int b, bool active) {
   const unsigned S = 1u << b;
-  unsigned long long p12 = (unsigned long long)q1 * q2;
-  int k0 = __shfl_sync(kFull, key, 0);
+  const unsigned long long p12 = (unsigned long long)q1 * q2;
+  const int k0 = __shfl_sync(kFull, key, 0);
   if (__all_sync(kFull, active && key == k0)) {
     unsigned long long s1 = __reduce_add_sync(kFull, q1);
     unsigned long long s2 = __reduce_add_sync(kFull, q2);
     unsigned lo = __reduce_add_sync(kFull, (unsigned)(p12 & 0xffffffu));
     unsigned hi = __reduce_add_sync(kFull, (unsigned)(p12 >> 24));
-    if ((threadIdx.x & 31) == 0) {
-      unsigned long long s12 = ((unsigned long long)hi << 24) + lo;
-      unsigned long long SS = (unsigned long long)S * S;
-      add4(W, ci, cj, 32ull * SS - (unsigned long long)S * (s1 + s2) + s12, (unsigned long long)S * s1 - s12,
-           (unsigned long long)S * s2 - s12, s12);
-    }
+    if ((threadIdx.x & 31) == 0)
+      cell_add(W, ci, cj, (s1 << 32) | s2, ((unsigned long long)hi << 24) + lo + (32ull << 52), S);
   } else if (active) {
-    add4(W, ci, cj, (unsigned long long)(S - q1) * (S - q2), (unsigned long long)q1 * (S - q2),
-         (unsigned long long)(S - q1) * q2, p12);
+    cell_add(W, ci, cj, ((unsigned long long)q1 << 32) | q2, p12 + (1ull << 52), S);
   }
 }
 
@@ -192,7 +227,7 @@ __device__ __forceinline__ Cell locate_c(const PushConst& C, Real x1, Real x2) {
 // population (sorted by cell, so a chunk covers few grid rows) and deposits
 // into a shared-memory window of kWinRows node rows that is flushed to the
 // global accumulator after each chunk.
-__global__ void __launch_bounds__(256) k_push(DevPtrs d) {
+__global__ void __launch_bounds__(256) k_push(DevPtrs d, int win_n2) {
   extern __shared__ unsigned long long s_win[];
   __shared__ long long s_pre[kMaxPop + 1];  // chunk prefix over populations
   __shared__ PushConst s_pc[kMaxPop];
@@ -229,7 +264,8 @@ __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
     C.acc_off = P.acc_off;
     s_pc[p] = C;
   }
-  for (int k = threadIdx.x; k < kWinRows * kWinMaxN2; k += blockDim.x) s_win[k] = 0ull;
+  const int win_words = kF64 ? kWinRows * (win_n2 + 1) : 2 * kWinRows * win_n2;
+  for (int k = threadIdx.x; k < win_words; k += blockDim.x) s_win[k] = 0ull;
   __syncthreads();
   const long long total_chunks = s_pre[d.n_pop];
   Real* X1 = (Real*)d.x1;
@@ -240,7 +276,9 @@ __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
   const Real2* G = (const Real2*)d.G;
   for (long long chunk = blockIdx.x; chunk < total_chunks; chunk += gridDim.x) {
    const int pop = find_pop(s_pre, d.n_pop, chunk);
-   const PushConst& C = s_pc[pop];
+   // by value: the constants stay in registers instead of being reloaded from
+   // shared memory around every window atomic
+   const PushConst C = s_pc[pop];
    const long long npop = d.ps[pop].n, pbase = d.pop[pop].base;
    const long long c0 = (chunk - s_pre[pop]) * CH;
    if (threadIdx.x == 0) {
@@ -260,7 +298,14 @@ __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
    W.g = d.acc + C.acc_off;
    W.row0 = s_row0;
    W.N2 = C.N2;
-   W.rows = C.N2 <= kWinMaxN2 ? kWinRows : 0;
+   W.rows = C.n2 <= win_n2 ? kWinRows : 0;
+   CellWin CW;
+   CW.s = s_win;
+   CW.g = W.g;
+   CW.row0 = W.row0;
+   CW.rows = W.rows;
+   CW.n2 = C.n2;
+   CW.N2 = C.N2;
    // the state of the next item is loaded while the current one is pushed
    Real nx1 = Real(2), nx2 = Real(0), nvR = Real(0), nvZ = Real(0), nvT = Real(0);
    auto fetch = [&](int it) {
@@ -319,12 +364,11 @@ __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
       vz = vz + h * EZ;
       float Xc = R + vx * dt, Yc = vy * dt, Zn = Z + vz * dt;
       float Rn2 = Xc * Xc + Yc * Yc;
-      float cr = 1.0f, sr = 0.0f, Rn = 0.0f;
+      float cr = 1.0f, sr = 0.0f;
       if (Rn2 > 0.0f) {
         float iR = rsqrtf(Rn2);
         cr = Xc * iR;
         sr = Yc * iR;
-        Rn = Rn2 * iR;
       }
       float vRn = cr * vx + sr * vy, vTn = -sr * vx + cr * vy;
       float rn2 = Rn2 + Zn * Zn;
@@ -441,16 +485,38 @@ __global__ void __launch_bounds__(256) k_push(DevPtrs d) {
       }
     }
     if (kF64) deposit_lane(W, di, dj, w, key >= 0);
-    else deposit_warp_q(W, key, di, dj, q1, q2, C.fbits >> 1, key >= 0);
+    else deposit_moments(CW, key, di, dj, q1, q2, C.fbits >> 1, key >= 0);
    }
    __syncthreads();
    // flush the window and clear it for the next chunk
-   for (int e = threadIdx.x; e < W.rows * W.N2; e += blockDim.x) {
-     unsigned long long v = s_win[e];
-     if (v) {
-       atomicAdd(W.g + (long long)(W.row0 + e / W.N2) * W.N2 + e % W.N2, v);
-       s_win[e] = 0ull;
+   if (kF64) {
+     for (int e = threadIdx.x; e < W.rows * W.N2; e += blockDim.x) {
+       unsigned long long v = s_win[e];
+       if (v) {
+         atomicAdd(W.g + (long long)(W.row0 + e / W.N2) * W.N2 + e % W.N2, v);
+         s_win[e] = 0ull;
+       }
      }
+   } else {
+     // node (ni, nj) of rows row0..row0+rows gathers w00 of cell (ni, nj),
+     // w10 of (ni-1, nj), w01 of (ni, nj-1) and w11 of (ni-1, nj-1)
+     const unsigned S = 1u << (C.fbits >> 1);
+     for (int e = threadIdx.x; e < (CW.rows + 1) * CW.N2; e += blockDim.x) {
+       const int rr = e / CW.N2, nj = e - rr * CW.N2;
+       unsigned long long v = 0, w[4];
+#pragma unroll
+       for (int t = 0; t < 4; ++t) {
+         const int cr = rr - (t & 1), cj = nj - (t >> 1);
+         if (cr < 0 || cr >= CW.rows || cj < 0 || cj >= CW.n2) continue;
+         const unsigned long long* c = s_win + 2 * (cr * CW.n2 + cj);
+         if (c[1] == 0ull) continue;
+         corner_weights(c[0], c[1], S, w);
+         v += w[t];  // t = 0: w00 (own cell), 1: w10 (cell below in x1), 2: w01, 3: w11
+       }
+       if (v) atomicAdd(CW.g + (long long)(CW.row0 + rr) * CW.N2 + nj, v);
+     }
+     __syncthreads();
+     for (int e = threadIdx.x; e < 2 * CW.rows * CW.n2; e += blockDim.x) s_win[e] = 0ull;
    }
    __syncthreads();
   }
@@ -853,10 +919,14 @@ void launch_deposit_all<Real>(const DevPtrs& d, int max_grid, cudaStream_t s) {
 }
 
 template <>
-void launch_push<Real>(const DevPtrs& d, int grid, cudaStream_t s) {
-  const int sm = kWinRows * kWinMaxN2 * (int)sizeof(unsigned long long);
+void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, cudaStream_t s) {
+  // window capacity: the widest grid of the batch, up to kWinMaxN2 - 1 cells
+  // (wider grids deposit straight to global memory)
+  const int win_n2 = max_n2 < kWinMaxN2 - 1 ? max_n2 : kWinMaxN2 - 1;
+  const int words = kF64 ? kWinRows * (win_n2 + 1) : 2 * kWinRows * win_n2;
+  const int sm = words * (int)sizeof(unsigned long long);
   cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  k_push<<<grid, 256, sm, s>>>(d);
+  k_push<<<grid, 256, sm, s>>>(d, win_n2);
 }
 
 template <>

@@ -29,34 +29,55 @@ __device__ __forceinline__ S apply_st(const S* st, long long nodes, const V* x, 
   return acc;
 }
 
-// Grid barrier (co-residency is guaranteed by the cooperative launch).  The
-// wait is bounded: on time-out the error word gets kErrTimeout and every CTA
-// leaves the kernel at its next barrier.
+// Grid barrier (co-residency is guaranteed by the cooperative launch).  A
+// 64-bit arrival counter that only grows: each CTA adds 1 (release) and waits
+// (acquire) until the counter reaches the next multiple of the CTA count, so
+// no reset and no generation word are needed; every launch of a simulation
+// uses the same CTA count, so each starts on a multiple.  The wait is bounded
+// (about two seconds of global time): on time-out the error word gets
+// kErrTimeout and every CTA leaves the kernel at its next barrier.
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long atom_add_release_u64(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ bool grid_sync(const DevPtrs& d, unsigned nb) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = d.bar + 1;
-    unsigned g = *vgen;
-    __threadfence();
+    unsigned long long* cnt = (unsigned long long*)d.bar;
+    const unsigned long long old = atom_add_release_u64(cnt, 1ull);
+    const unsigned long long target = (old / nb + 1ull) * nb;
     int ok = 1;
-    if (atomicAdd(d.bar, 1u) == nb - 1) {
-      d.bar[0] = 0u;
-      __threadfence();
-      atomicAdd(d.bar + 1, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == g) {
-        if ((++spins & 1023) == 0 && ((*(volatile int*)d.err) & kErrTimeout)) break;
-        if (spins > (1ll << 24)) {
-          atomicOr(d.err, kErrTimeout);
+    unsigned long long t0 = 0;
+    for (long long spins = 0; ld_acquire_u64(cnt) < target; ++spins) {
+      if ((spins & 255) == 255) {
+        if ((*(volatile int*)d.err) & kErrTimeout) {
+          ok = 0;
           break;
         }
-        __nanosleep(64);
+        const unsigned long long now = global_ns();
+        if (t0 == 0) t0 = now;
+        else if (now - t0 > 2000000000ull) {
+          atomicOr(d.err, kErrTimeout);
+          ok = 0;
+          break;
+        }
       }
     }
-    __threadfence();
-    if ((*(volatile int*)d.err) & kErrTimeout) ok = 0;
     s_ok = ok;
   }
   __syncthreads();

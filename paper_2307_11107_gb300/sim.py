@@ -134,7 +134,8 @@ class Sim:
         return dict(steps=int(st.steps), poisson_loop_iters=int(st.poisson_loop_iters),
                     kernels_per_step=int(st.kernels_per_step), kernels_per_iter=int(st.kernels_per_iter),
                     timed_steps=int(st.timed_steps),
-                    phase_ms=dict(zip(_abi.PHASES, [float(v) for v in st.phase_ms])))
+                    phase_ms=dict(zip(_abi.PHASES, [float(v) for v in st.phase_ms])),
+                    solver=_abi.SOLVERS[int(st.solver)])
 
     def tallies(self, instance=0, history=True):
         c = self.cfgs[instance]
