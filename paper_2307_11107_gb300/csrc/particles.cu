@@ -25,6 +25,8 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPushItems = 8;    // particles per thread per chunk
 constexpr int kWinRows = 8;      // node rows of the shared-memory deposit window
 constexpr int kWinMaxN2 = 513;   // widest grid row the window holds (larger grids deposit globally)
+constexpr int kInjRows = 3;      // node rows of the injection window (the last two cell rows)
+constexpr int kInjMaxN2 = 512;   // widest grid (cells in x2) the injection window holds
 
 struct W4 {
   unsigned long long w00, w10, w01, w11;
@@ -600,14 +602,27 @@ __global__ void k_explicit(DevPtrs d, int pop, long long n0, long long count, co
 // free flight for a uniform fraction of dt, then absorption / escape tests.
 // Stored particles fill freed slots first, then extend the population.
 __global__ void __launch_bounds__(256) k_inject(DevPtrs d) {
-  int pop = blockIdx.y;
-  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // The injected particles land within a cell row or two of the outer
+  // surface: their corner weights are summed in a shared-memory window of the
+  // last kInjRows node rows and added to the global accumulator once per CTA
+  // (every particle's weights on the same few hundred nodes would otherwise
+  // serialise on them).
+  __shared__ unsigned long long s_nodes[kInjRows * (kInjMaxN2 + 1)];
+  const int pop = blockIdx.y;
   PopState& S = d.ps[pop];
   const Pop& P = d.pop[pop];
   const Inst& I = d.inst[P.inst];
-  bool active = k < S.n_inj;
+  const long long n_inj = S.n_inj;
+  const int wrow0 = I.n1 + 1 - kInjRows;  // first node row of the window
+  const bool win = I.N2 <= kInjMaxN2 + 1;
+  for (int e = threadIdx.x; e < kInjRows * I.N2 && win; e += blockDim.x) s_nodes[e] = 0ull;
+  __syncthreads();
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n_inj; base += (long long)gridDim.x * blockDim.x) {
+  const long long k = base + threadIdx.x;
+  bool active = k < n_inj;
   long long key = -1;
   W4 w = {0, 0, 0, 0};
+  int ci = 0, cj = 0;
   int fate = 0;  // 1 absorbed, 2 escaped, 3 stored
   Real x1n = Real(0), x2n = Real(0), vRn = Real(0), vZn = Real(0), vTn = Real(0);
   if (active) {
@@ -662,14 +677,14 @@ __global__ void __launch_bounds__(256) k_inject(DevPtrs d) {
     if (m_abs) atomicAdd((unsigned long long*)&S.absorbed, (unsigned long long)__popc(m_abs));
     if (m_esc) atomicAdd((unsigned long long*)&S.escaped, (unsigned long long)__popc(m_esc));
   }
-  long long base = 0;
+  long long sbase = 0;
   if (m_st) {
     const int leader = __ffs(m_st) - 1;
-    if ((int)lane == leader) base = (long long)atomicAdd((unsigned long long*)&S.inj_stored, (unsigned long long)__popc(m_st));
-    base = __shfl_sync(kFull, base, leader);
+    if ((int)lane == leader) sbase = (long long)atomicAdd((unsigned long long*)&S.inj_stored, (unsigned long long)__popc(m_st));
+    sbase = __shfl_sync(kFull, sbase, leader);
   }
   if (fate == 3) {
-    const long long sidx = base + __popc(m_st & lt);
+    const long long sidx = sbase + __popc(m_st & lt);
     const long long nh = S.n_holes, n = S.n;
     const long long kk = sidx < nh ? d.holes[P.base + nh - 1 - sidx] : n + (sidx - nh);
     if (kk >= P.cap) {
@@ -684,15 +699,30 @@ __global__ void __launch_bounds__(256) k_inject(DevPtrs d) {
       ((Real*)d.vT)[slot] = vTn;
       Cell c = locate(I, x1n, x2n);
       key = dep_key(I, P, c);
+      ci = c.i;
+      cj = c.j;
       w = weights(c, P.fbits);
     }
   }
-  // per-lane atomics: injected particles of a warp rarely share a cell
   if (key >= 0) {
-    if (w.w00) atomicAdd(d.acc + key, w.w00);
-    if (w.w10) atomicAdd(d.acc + key + I.N2, w.w10);
-    if (w.w01) atomicAdd(d.acc + key + 1, w.w01);
-    if (w.w11) atomicAdd(d.acc + key + I.N2 + 1, w.w11);
+    if (win && ci >= wrow0) {
+      unsigned long long* sn0 = s_nodes + (ci - wrow0) * I.N2 + cj;
+      if (w.w00) atomicAdd(sn0, w.w00);
+      if (w.w10) atomicAdd(sn0 + I.N2, w.w10);
+      if (w.w01) atomicAdd(sn0 + 1, w.w01);
+      if (w.w11) atomicAdd(sn0 + I.N2 + 1, w.w11);
+    } else {
+      if (w.w00) atomicAdd(d.acc + key, w.w00);
+      if (w.w10) atomicAdd(d.acc + key + I.N2, w.w10);
+      if (w.w01) atomicAdd(d.acc + key + 1, w.w01);
+      if (w.w11) atomicAdd(d.acc + key + I.N2 + 1, w.w11);
+    }
+  }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kInjRows * I.N2 && win; e += blockDim.x) {
+    const unsigned long long v = s_nodes[e];
+    if (v) atomicAdd(d.acc + P.acc_off + (long long)wrow0 * I.N2 + e, v);
   }
 }
 
@@ -751,7 +781,8 @@ __global__ void __launch_bounds__(256) k_sort_count(DevPtrs d) {
         long long slot = P.base + k;
         Real x1 = X1[slot];
         if (x1 < Real(0)) {
-          row = (int)floor((double)((x1 + Real(1)) / (Real)I.h1));
+          // grid row in the particle precision (the key only orders the particles)
+          row = (int)floor((x1 + Real(1)) * (Real)(1.0 / I.h1));
           row = row < 0 ? 0 : (row > nrows - 1 ? nrows - 1 : row);
         }
         d.keys[slot] = row;
@@ -854,18 +885,35 @@ __global__ void __launch_bounds__(256) k_sort_scatter(DevPtrs d) {
       cur[r] = c ? (unsigned)(d.cell_off[P.cell_off + r] - first) + atomicAdd(d.cell_cnt + P.cell_off + r, c) : 0u;
     }
     __syncthreads();
-    for (int it = 0; it < kSortItems; ++it) {
+    // the key and state of the next item are loaded while the current one is placed
+    int nrow = -1;
+    Real n1v = Real(0), n2v = Real(0), nRv = Real(0), nZv = Real(0), nTv = Real(0);
+    auto fetch = [&](int it) {
       long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
-      long long slot = P.base + (k < npop ? k : 0);
-      int row = k < npop ? d.keys[slot] : -1;
+      nrow = -1;
+      if (k < npop) {
+        long long slot = P.base + k;
+        nrow = d.keys[slot];
+        n1v = ((const Real*)d.x1)[slot];
+        n2v = ((const Real*)d.x2)[slot];
+        nRv = ((const Real*)d.vR)[slot];
+        nZv = ((const Real*)d.vZ)[slot];
+        nTv = ((const Real*)d.vT)[slot];
+      }
+    };
+    fetch(0);
+    for (int it = 0; it < kSortItems; ++it) {
+      const int row = nrow;
+      const Real v1 = n1v, v2 = n2v, vR = nRv, vZ = nZv, vT = nTv;
+      if (it + 1 < kSortItems) fetch(it + 1);
       unsigned pos = warp_count(cur, row);
       if (row >= 0) {
         long long dst = P.base + (long long)pos;
-        ((Real*)d.y1)[dst] = ((const Real*)d.x1)[slot];
-        ((Real*)d.y2)[dst] = ((const Real*)d.x2)[slot];
-        ((Real*)d.yR)[dst] = ((const Real*)d.vR)[slot];
-        ((Real*)d.yZ)[dst] = ((const Real*)d.vZ)[slot];
-        ((Real*)d.yT)[dst] = ((const Real*)d.vT)[slot];
+        ((Real*)d.y1)[dst] = v1;
+        ((Real*)d.y2)[dst] = v2;
+        ((Real*)d.yR)[dst] = vR;
+        ((Real*)d.yZ)[dst] = vZ;
+        ((Real*)d.yT)[dst] = vT;
       }
     }
     __syncthreads();
@@ -932,7 +980,10 @@ void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, cudaStream_t s) {
 template <>
 void launch_inject<Real>(const DevPtrs& d, long long max_inj, cudaStream_t s) {
   if (max_inj <= 0) return;
-  dim3 g(blocks_for(max_inj, 256), d.n_pop);
+  // few CTAs, several injections per thread: fewer window flushes
+  unsigned gx = blocks_for(max_inj, 256);
+  gx = gx < 64 ? gx : 64;
+  dim3 g(gx, d.n_pop);
   k_inject<<<g, 256, 0, s>>>(d);
 }
 
