@@ -229,7 +229,10 @@ __device__ __forceinline__ Cell locate_c(const PushConst& C, Real x1, Real x2) {
 // population (sorted by cell, so a chunk covers few grid rows) and deposits
 // into a shared-memory window of kWinRows node rows that is flushed to the
 // global accumulator after each chunk.
-__global__ void __launch_bounds__(256) k_push(DevPtrs d, int win_n2) {
+#ifndef APIC_PUSH_MIN_BLOCKS
+#define APIC_PUSH_MIN_BLOCKS 4  // 64 registers: four CTAs of 256 threads per SM
+#endif
+__global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, int win_n2) {
   extern __shared__ unsigned long long s_win[];
   __shared__ long long s_pre[kMaxPop + 1];  // chunk prefix over populations
   __shared__ PushConst s_pc[kMaxPop];
@@ -772,6 +775,9 @@ __global__ void __launch_bounds__(256) k_sort_count(DevPtrs d) {
     const Inst& I = d.inst[P.inst];
     const long long npop = d.ps[pop].n, c0 = (chunk - pre[pop]) * CH;
     const int nrows = I.n1;
+    // grid row in the particle precision (the key only orders the particles);
+    // the reciprocal once per chunk, not an FP64 division per particle
+    const Real ih1 = (Real)(1.0 / I.h1);
     for (int r = threadIdx.x; r < nrows; r += blockDim.x) s_hist[r] = 0u;
     __syncthreads();
     for (int it = 0; it < kSortItems; ++it) {
@@ -781,8 +787,7 @@ __global__ void __launch_bounds__(256) k_sort_count(DevPtrs d) {
         long long slot = P.base + k;
         Real x1 = X1[slot];
         if (x1 < Real(0)) {
-          // grid row in the particle precision (the key only orders the particles)
-          row = (int)floor((x1 + Real(1)) * (Real)(1.0 / I.h1));
+          row = (int)floor((x1 + Real(1)) * ih1);
           row = row < 0 ? 0 : (row > nrows - 1 ? nrows - 1 : row);
         }
         d.keys[slot] = row;
