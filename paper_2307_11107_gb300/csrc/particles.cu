@@ -229,14 +229,20 @@ __device__ __forceinline__ Cell locate_c(const PushConst& C, Real x1, Real x2) {
 // population (sorted by cell, so a chunk covers few grid rows) and deposits
 // into a shared-memory window of kWinRows node rows that is flushed to the
 // global accumulator after each chunk.
+#ifndef APIC_PUSH_UNROLL
+#define APIC_PUSH_UNROLL 2
+#endif
+constexpr int kPushUnroll = APIC_PUSH_UNROLL;  // items of the chunk loop unrolled
 #ifndef APIC_PUSH_MIN_BLOCKS
-#define APIC_PUSH_MIN_BLOCKS 4  // 64 registers: four CTAs of 256 threads per SM
+// FP32: 64 registers, four CTAs of 256 threads per SM; FP64 (parity build): two
+#define APIC_PUSH_MIN_BLOCKS (sizeof(APIC_REAL) == 4 ? 4 : 2)
 #endif
 __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, int win_n2) {
   extern __shared__ unsigned long long s_win[];
   __shared__ long long s_pre[kMaxPop + 1];  // chunk prefix over populations
   __shared__ PushConst s_pc[kMaxPop];
   __shared__ int s_row0;
+  __shared__ unsigned s_rowmask;  // FP32 window: cell rows that received moments in this chunk
   const long long CH = (long long)kPushItems * blockDim.x;
   if (threadIdx.x == 0) {
     long long a = 0;
@@ -296,6 +302,7 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
        }
      }
      s_row0 = row > 0 ? row - 1 : 0;
+     s_rowmask = 0u;
    }
    __syncthreads();
    Window W;
@@ -311,26 +318,31 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
    CW.rows = W.rows;
    CW.n2 = C.n2;
    CW.N2 = C.N2;
-   // the state of the next item is loaded while the current one is pushed
+   // this thread's items sit at 32-bit offsets it * blockDim.x from per-chunk
+   // pointers; the state of the next item is loaded while the current one is pushed
+   const long long t0 = pbase + c0 + threadIdx.x;
+   const long long left = npop - c0 - threadIdx.x;
+   const int nleft = left > CH ? (int)CH : (int)left;  // offsets below nleft are in the population
+   const Real2* Gi = G + C.node_off;
    Real nx1 = Real(2), nx2 = Real(0), nvR = Real(0), nvZ = Real(0), nvT = Real(0);
    auto fetch = [&](int it) {
-     long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
-     if (k < npop) {
-       long long slot = pbase + k;
-       nx1 = X1[slot];
-       nx2 = X2[slot];
-       nvR = VR[slot];
-       nvZ = VZ[slot];
-       nvT = VT[slot];
+     const int o = it * (int)blockDim.x;
+     if (o < nleft) {
+       const long long q = t0 + o;
+       nx1 = X1[q];
+       nx2 = X2[q];
+       nvR = VR[q];
+       nvZ = VZ[q];
+       nvT = VT[q];
      } else {
        nx1 = Real(2);
      }
    };
    fetch(0);
+#pragma unroll kPushUnroll
    for (int it = 0; it < kPushItems; ++it) {
-    long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
-    bool active = k < npop;
-    long long slot = pbase + (active ? k : 0);
+    const int o = it * (int)blockDim.x;
+    const bool active = o < nleft;
     const Real x1 = nx1, cx2 = nx2, cvR = nvR, cvZ = nvZ, cvT = nvT;
     if (it + 1 < kPushItems) fetch(it + 1);
     bool alive = active && x1 < Real(0);
@@ -346,15 +358,15 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
       float x1f = (float)x1;
       float disc = 1.0f - 4.0f * al * x1f * x2;
       float ir = __fdividef(-2.0f * x1f, 1.0f + sqrtf(disc));  // 1/r (Eq. 3)
-      float r = __frcp_rn(ir);
+      float r = __fdividef(1.0f, ir);
       float s2 = (1.0f - x2) * (1.0f + x2);
       float sn = sqrtf(s2);
       float R = r * sn, Z = r * x2;
       float u1 = (x1f + 1.0f) * C.ih1, u2 = (x2 + 1.0f) * C.ih2;
       int ci = min(max((int)floorf(u1), 0), C.n1 - 1), cj = min(max((int)floorf(u2), 0), C.n2 - 1);
       float f1 = fminf(fmaxf(u1 - (float)ci, 0.0f), 1.0f), f2 = fminf(fmaxf(u2 - (float)cj, 0.0f), 1.0f);
-      long long n00 = C.node_off + (long long)ci * C.N2 + cj;
-      Real2 a00 = G[n00], a10 = G[n00 + C.N2], a01 = G[n00 + 1], a11 = G[n00 + C.N2 + 1];
+      const int n00 = ci * C.N2 + cj;
+      Real2 a00 = Gi[n00], a10 = Gi[n00 + C.N2], a01 = Gi[n00 + 1], a11 = Gi[n00 + C.N2 + 1];
       float g1 = (1.0f - f2) * ((1.0f - f1) * a00.x + f1 * a10.x) + f2 * ((1.0f - f1) * a01.x + f1 * a11.x);
       float g2 = (1.0f - f2) * ((1.0f - f1) * a00.y + f1 * a10.y) + f2 * ((1.0f - f1) * a01.y + f1 * a11.y);
       float ir3 = ir * ir * ir;
@@ -384,19 +396,19 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
       if (tr < 0.0f || tr * tr < 1.0f + 4.0f * al * x2n) {
         const Pop& P = d.pop[pop];
         absorb_tally(d, d.inst[P.inst], P, R, Z, vx, vz, vy, dt);
-        X1[slot] = Real(2);
+        X1[t0 + o] = Real(2);
         fate = 1;
       } else {
         float x1n = -irn * (1.0f + al * x2n * irn);
         if (x1n > C.x1_out) {
-          X1[slot] = Real(2);
+          X1[t0 + o] = Real(2);
           fate = 2;
         } else {
-          X1[slot] = x1n;
-          X2[slot] = x2n;
-          VR[slot] = vRn;
-          VZ[slot] = vz;
-          VT[slot] = vTn;
+          X1[t0 + o] = x1n;
+          X2[t0 + o] = x2n;
+          VR[t0 + o] = vRn;
+          VZ[t0 + o] = vz;
+          VT[t0 + o] = vTn;
           float v1 = (x1n + 1.0f) * C.ih1, v2 = (x2n + 1.0f) * C.ih2;
           int ni = min(max((int)floorf(v1), 0), C.n1 - 1), nj = min(max((int)floorf(v2), 0), C.n2 - 1);
           float e1 = fminf(fmaxf(v1 - (float)ni, 0.0f), 1.0f), e2 = fminf(fmaxf(v2 - (float)nj, 0.0f), 1.0f);
@@ -416,8 +428,8 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
       Real R = r * sn, Z = r * x2;
       // gather (Eq. 10): bilinear node gradients, analytic metric at the particle
       Cell c = locate_c(C, x1, x2);
-      long long n00 = C.node_off + (long long)c.i * C.N2 + c.j;
-      Real2 a00 = G[n00], a10 = G[n00 + C.N2], a01 = G[n00 + 1], a11 = G[n00 + C.N2 + 1];
+      const int n00 = c.i * C.N2 + c.j;
+      Real2 a00 = Gi[n00], a10 = Gi[n00 + C.N2], a01 = Gi[n00 + 1], a11 = Gi[n00 + C.N2 + 1];
       Real w00 = (Real(1) - c.f1) * (Real(1) - c.f2), w10 = c.f1 * (Real(1) - c.f2);
       Real w01 = (Real(1) - c.f1) * c.f2, w11 = c.f1 * c.f2;
       Real g1 = w00 * a00.x + w10 * a10.x + w01 * a01.x + w11 * a11.x;
@@ -450,19 +462,19 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
       if (rn < r_grain(al, x2n)) {
         const Pop& P = d.pop[pop];
         absorb_tally(d, d.inst[P.inst], P, R, Z, vx, vz, vy, dt);
-        X1[slot] = Real(2);
+        X1[t0 + o] = Real(2);
         fate = 1;
       } else {
         Real x1n = x1_at(al, rn, x2n);
         if (x1n > C.x1_out) {
-          X1[slot] = Real(2);
+          X1[t0 + o] = Real(2);
           fate = 2;
         } else {
-          X1[slot] = x1n;
-          X2[slot] = x2n;
-          VR[slot] = vRn;
-          VZ[slot] = vz;
-          VT[slot] = vTn;
+          X1[t0 + o] = x1n;
+          X2[t0 + o] = x2n;
+          VR[t0 + o] = vRn;
+          VZ[t0 + o] = vz;
+          VT[t0 + o] = vTn;
           Cell cn = locate_c(C, x1n, x2n);
           key = cn.i * C.N2 + cn.j;
           di = cn.i;
@@ -486,11 +498,18 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
           h0 = (long long)atomicAdd((unsigned long long*)&S.n_holes, (unsigned long long)__popc(m_gone));
         }
         h0 = __shfl_sync(kFull, h0, leader);
-        if (fate != 0) d.holes[d.pop[pop].base + h0 + __popc(m_gone & ((1u << lane) - 1u))] = (int32_t)k;
+        if (fate != 0)
+          d.holes[d.pop[pop].base + h0 + __popc(m_gone & ((1u << lane) - 1u))] = (int32_t)(c0 + threadIdx.x + o);
       }
     }
-    if (kF64) deposit_lane(W, di, dj, w, key >= 0);
-    else deposit_moments(CW, key, di, dj, q1, q2, C.fbits >> 1, key >= 0);
+    if (kF64) {
+      deposit_lane(W, di, dj, w, key >= 0);
+    } else {
+      deposit_moments(CW, key, di, dj, q1, q2, C.fbits >> 1, key >= 0);
+      const int rr = di - CW.row0;
+      const unsigned rows_hit = __reduce_or_sync(kFull, (key >= 0 && rr >= 0 && rr < CW.rows) ? (1u << rr) : 0u);
+      if ((threadIdx.x & 31) == 0 && rows_hit) atomicOr(&s_rowmask, rows_hit);
+    }
    }
    __syncthreads();
    // flush the window and clear it for the next chunk
@@ -505,14 +524,21 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
    } else {
      // node (ni, nj) of rows row0..row0+rows gathers w00 of cell (ni, nj),
      // w10 of (ni-1, nj), w01 of (ni, nj-1) and w11 of (ni-1, nj-1)
+     // (only the node rows next to the cell rows that received moments)
      const unsigned S = 1u << (C.fbits >> 1);
-     for (int e = threadIdx.x; e < (CW.rows + 1) * CW.N2; e += blockDim.x) {
-       const int rr = e / CW.N2, nj = e - rr * CW.N2;
+     const unsigned cm = s_rowmask;
+     const unsigned nm = cm | (cm << 1);  // node rows rr with cell row rr or rr - 1 in use
+     const int nrows = __popc(nm);
+     for (int e = threadIdx.x; e < nrows * CW.N2; e += blockDim.x) {
+       const int q = e / CW.N2, nj = e - q * CW.N2;
+       unsigned mm = nm;
+       for (int z = 0; z < q; ++z) mm &= mm - 1u;
+       const int rr = __ffs(mm) - 1;  // the q-th node row in use
        unsigned long long v = 0, w[4];
 #pragma unroll
        for (int t = 0; t < 4; ++t) {
          const int cr = rr - (t & 1), cj = nj - (t >> 1);
-         if (cr < 0 || cr >= CW.rows || cj < 0 || cj >= CW.n2) continue;
+         if (cr < 0 || cr >= CW.rows || !((cm >> cr) & 1u) || cj < 0 || cj >= CW.n2) continue;
          const unsigned long long* c = s_win + 2 * (cr * CW.n2 + cj);
          if (c[1] == 0ull) continue;
          corner_weights(c[0], c[1], S, w);
@@ -521,7 +547,13 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
        if (v) atomicAdd(CW.g + (long long)(CW.row0 + rr) * CW.N2 + nj, v);
      }
      __syncthreads();
-     for (int e = threadIdx.x; e < 2 * CW.rows * CW.n2; e += blockDim.x) s_win[e] = 0ull;
+     const int crows = __popc(cm);
+     for (int e = threadIdx.x; e < 2 * crows * CW.n2; e += blockDim.x) {
+       const int q = e / (2 * CW.n2), o = e - q * 2 * CW.n2;
+       unsigned mm = cm;
+       for (int z = 0; z < q; ++z) mm &= mm - 1u;
+       s_win[2 * (__ffs(mm) - 1) * CW.n2 + o] = 0ull;
+     }
    }
    __syncthreads();
   }
