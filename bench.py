@@ -251,7 +251,8 @@ def main():
     advanced = float(res.sum())
     value, total_adv, sec = replica_throughput(advanced, ms / 1e3, pg, "cuda")
     loop_iters = s1["poisson_loop_iters"] - s0["poisson_loop_iters"]
-    launches = args.steps * s1["kernels_per_step"] + loop_iters * s1["kernels_per_iter"]
+    launches = (args.steps * s1["kernels_per_step"] + loop_iters * s1["kernels_per_iter"] +
+                (s1["sorts"] - s0["sorts"]) * s1["kernels_per_sort"])
 
     # roofline of the dominant kernel (push): CUDA events around its phase graph
     kt = min(args.steps, 100)

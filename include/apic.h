@@ -194,7 +194,8 @@ typedef struct {
   int64_t timed_steps;          /* steps run by apic_step_timed */
   double phase_ms[APIC_NPHASE]; /* CUDA-event time per phase, summed over timed steps */
   int32_t solver;               /* Poisson solver in use: APIC_SOLVER_* */
-  int32_t pad;
+  int32_t kernels_per_sort;     /* kernel launches of one particle sort */
+  int64_t sorts;                /* particle sorts launched (every sort_interval steps) */
 } apic_stats_t;
 
 /* Poisson solvers (chosen at creation) */

@@ -169,6 +169,7 @@ struct apic_sim {
   double phase_ms[APIC_NPHASE] = {};
   long long timed_steps = 0;
   long long slots = 0;                // particle slots of one buffer (all populations)
+  long long sorts = 0;                // particle sorts launched
   long long tab_total = 0;
   TanPtrs tan{};                      // sensitivity-window state (allocated on first use)
   bool tan_ready = false;
@@ -1101,8 +1102,8 @@ static bool enqueue_solver_loop(apic_sim* S, const DevPtrs& d, cudaStream_t s) {
 // One cooperative launch for the whole solve: block cyclic reduction when
 // set up, else the multigrid-preconditioned BiCGSTAB.
 template <class Real>
-static cudaError_t solve_coop(apic_sim* S, const DevPtrs& d, cudaStream_t s) {
-  if (S->plan.bcr.K > 0) return launch_solve_bcr(d, S->plan, S->coop, s);
+static cudaError_t solve_coop(apic_sim* S, const DevPtrs& d, cudaStream_t s, int bcr_mode = 0) {
+  if (S->plan.bcr.K > 0) return launch_solve_bcr(d, S->plan, S->coop, bcr_mode, s);
   return launch_solve_coop<Real>(d, S->plan, S->coop, s);
 }
 
@@ -1110,10 +1111,12 @@ static cudaError_t solve_coop(apic_sim* S, const DevPtrs& d, cudaStream_t s) {
 template <class Real>
 static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) {
   switch (p) {
-    case 0: launch_rho<Real>(d, s); break;
+    case 0:
+      if (S->plan.bcr.K == 0) launch_rho<Real>(d, s);  // the reduction solve forms rho itself
+      break;
     case 1:
       if (S->coop > 0) {
-        if (solve_coop<Real>(S, d, s) != cudaSuccess) return false;
+        if (solve_coop<Real>(S, d, s, kBcrRho | kBcrFields) != cudaSuccess) return false;
         break;
       }
       launch_bicg_init<Real>(d, s);
@@ -1124,8 +1127,10 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
       }
       break;
     case 2:
-      launch_gradients<Real>(d, s);
-      launch_surface(d, s);
+      if (S->plan.bcr.K == 0) {  // the reduction solve ends with them
+        launch_gradients<Real>(d, s);
+        launch_surface(d, s);
+      }
       break;
     case 3: launch_push<Real>(d, S->push_grid, S->max_n2, s); break;
     case 4: launch_inject<Real>(d, S->max_inj, s); break;
@@ -1197,6 +1202,7 @@ static bool launch_step(apic_sim* S, cudaGraphExec_t const* step_exec) {
   if (S->sort_interval > 0 && S->host_step % S->sort_interval == 0) {
     if (!S->ck(cudaGraphLaunch(S->sort_exec[S->par], S->stream), "sort launch")) return false;
     S->par ^= 1;
+    S->sorts += 1;
   }
   if (step_exec && !S->ck(cudaGraphLaunch(step_exec[S->par], S->stream), "graph launch")) return false;
   S->host_step += 1;
@@ -1263,7 +1269,10 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
   int vcycle = S->plan.max_tail * 10 + 1;
   int most = 0;
   for (const Inst& I : S->inst) most = std::max(most, I.max_iter);
-  if (S->coop > 0) {
+  if (S->plan.bcr.K > 0) {
+    out->kernels_per_iter = 0;   // solve, density and fields in one cooperative launch
+    out->kernels_per_step = 4;   // + push, injection, bookkeeping
+  } else if (S->coop > 0) {
     out->kernels_per_iter = 0;   // the whole solve is one cooperative launch
     out->kernels_per_step = 7;
   } else {
@@ -1272,6 +1281,8 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
   }
   out->timed_steps = S->timed_steps;
   out->solver = S->plan.bcr.K > 0 ? APIC_SOLVER_BCR : (S->coop > 0 ? APIC_SOLVER_MG_COOP : APIC_SOLVER_MG_KERNELS);
+  out->sorts = S->sorts;
+  out->kernels_per_sort = 6;
   for (int p = 0; p < APIC_NPHASE; ++p) out->phase_ms[p] = S->phase_ms[p];
   return APIC_OK;
 }

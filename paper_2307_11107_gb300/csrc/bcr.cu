@@ -24,6 +24,7 @@ namespace apic {
 namespace {
 
 #include "solver_common.cuh"
+#include "fields_common.cuh"
 
 constexpr int kBcrThreads = 512;
 constexpr int kBcrWarps = kBcrThreads / 32;
@@ -160,7 +161,10 @@ __device__ bool run_task(Ctx& c, const float* const* src, const float* const* vt
   return true;
 }
 
-__global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePlan pl) {
+// mode: kBcrRho = the step's density, initial guess and right-hand side are
+// formed here (else b and its |b|^2 partials come from the caller);
+// kBcrFields = node gradients and surface quantities after the solve.
+__global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePlan pl, int mode) {
   extern __shared__ __align__(128) float s_blocks[];
   __shared__ double sh[40];
   __shared__ float sv[3][kBcrMaxN];
@@ -198,15 +202,29 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePl
     if (r1 > r0)
       prefetch_l2(d.bcr_tail + (long long)r0 * B.tail_np, (unsigned)((r1 - r0) * B.tail_np * sizeof(float)));
   }
-  // |b|^2 from the right-hand-side kernel's partials (fixed order)
-  if (threadIdx.x == 0) {
-    double bn = 0.0;
-    for (int k = 0; k < kRedBlocks; ++k) bn += d.red[k];
-    sh[34] = bn;
+  double bn = 0.0;
+  if (mode & kBcrRho) {
+    // rho, the initial guess and b at every node; |b|^2 over the grid
+    double pb = 0.0;
+    for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes; nd += stride) {
+      const double bv = rho_node(d, I, 0, nd);
+      pb += bv * bv;
+    }
+    const double tb = block_sum_any(pb, sh);
+    if (threadIdx.x == 0) d.cred[0 * kCoopMaxBlocks + blockIdx.x] = tb;
+    if (!grid_sync(d, nb)) return;
+    bn = coop_sum(d, 0, 0, nb, sh);
+  } else {
+    // |b|^2 from the right-hand-side kernel's partials (fixed order)
+    if (threadIdx.x == 0) {
+      double s0 = 0.0;
+      for (int k = 0; k < kRedBlocks; ++k) s0 += d.red[k];
+      sh[34] = s0;
+    }
+    __syncthreads();
+    bn = sh[34];
+    __syncthreads();
   }
-  __syncthreads();
-  const double bn = sh[34];
-  __syncthreads();
   for (int it = 0;; ++it) {
     // FP64 residual, stored as the FP32 right-hand side of the reduction
     double pr = 0.0;
@@ -231,7 +249,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePl
         S.done = 1;
         if (!conv) atomicOr(d.err, bad ? kErrNonFinite : kErrNotConverged);
       }
-      return;
+      break;
     }
     // forward reduction: f_i -= P_i f_{i-h} + Q_i f_{i+h} on the kept rows
     for (int l = 1; l <= B.Lt; ++l) {
@@ -320,6 +338,12 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePl
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt[0] += 1;
   }
+  if (mode & kBcrFields) {
+    // phi is final everywhere (the last pass ended at a grid barrier)
+    for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes; nd += stride)
+      grad_node<float, float2>(d, I, nd);
+    if (blockIdx.x == nb - 1) surface_block(d, 0, sh);
+  }
 }
 
 constexpr int kStaticSmem = 40 * 8 + 3 * kBcrMaxN * 4 + kBcrMaxN * 4 + kBcrWarps * kBcrMaxN * 4 + 64;
@@ -354,10 +378,11 @@ int bcr_blocks(SolvePlan& pl, int sms) {
   return nb;
 }
 
-cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& pl, int blocks, cudaStream_t s) {
+cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& pl, int blocks, int mode, cudaStream_t s) {
   DevPtrs dd = d;
   SolvePlan pp = pl;
-  void* args[] = {&dd, &pp};
+  int mm = mode;
+  void* args[] = {&dd, &pp, &mm};
   const size_t dyn = (size_t)dyn_bytes(pl.bcr);
   return cudaLaunchCooperativeKernel((const void*)k_solve_bcr, dim3(blocks), dim3(kBcrThreads), args, dyn, s);
 }

@@ -12,8 +12,8 @@
 namespace apic {
 namespace {
 
-__device__ __forceinline__ double x1_node(const Inst& I, int i) { return i == I.n1 ? I.x1_out : -1.0 + i * I.h1; }
-__device__ __forceinline__ double x2_node(const Inst& I, int j) { return j == I.n2 ? 1.0 : -1.0 + j * I.h2; }
+#include "fields_common.cuh"
+
 
 // Deterministic block sum (fixed tree) of one double per thread; blockDim 256.
 __device__ double block_sum(double v, double* sh) {
@@ -29,35 +29,15 @@ __device__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// rho_ij = sum_s q_s w_s (accumulated CIC weights) / V_ij; the accumulators are
-// cleared for the next deposit.  b = rscale * (-rho) + (Dirichlet terms), and
-// per-CTA partial sums of |b|^2.
+// rho, the initial guess and the right-hand side at every node (rho_node),
+// with per-CTA partial sums of |b|^2.
 __global__ void __launch_bounds__(256) k_rho(DevPtrs d) {
   __shared__ double sh[256];
   const Inst& I = d.inst[blockIdx.y];
   double part = 0.0;
   for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes;
        nd += (long long)gridDim.x * blockDim.x) {
-    long long g = I.node_off + nd;
-    double q = 0.0;
-    for (int s = 0; s < I.n_species; ++s) {
-      const Pop& P = d.pop[I.pop0 + s];
-      unsigned long long a = d.acc[P.acc_off + nd];
-      d.acc[P.acc_off + nd] = 0ull;
-      q += P.dep_scale * (double)a;
-    }
-    double rho = q / d.V[g];
-    d.rho[g] = rho;
-    int i = (int)(nd / I.N2);
-    if (i > 0 && i < I.n1) {
-      // initial guess of this step's solve: previous phi, or its linear extrapolation
-      double ph = d.phi[g];
-      if (I.guess && d.stp[blockIdx.y].step >= 2) d.phi[g] = 2.0 * ph - d.phi_prev[g];
-      d.phi_prev[g] = ph;
-    }
-    double bv = 0.0;
-    if (i > 0 && i < I.n1) bv = -rho * d.rscale[g] + d.bbc[g];
-    d.b[g] = bv;
+    const double bv = rho_node(d, I, blockIdx.y, nd);
     part += bv * bv;
   }
   double tot = block_sum(part, sh);
@@ -93,80 +73,20 @@ struct Pair<float> {
   using T = float2;
 };
 
-// Node gradients: central differences inside, one-sided second order on the
-// four edges (Sec. 2: derivatives of phi taken numerically at the nodes).
+// Node gradients of every node (grad_node).
 template <class Real>
 __global__ void __launch_bounds__(256) k_gradients(DevPtrs d) {
   using R2 = typename Pair<Real>::T;
   const Inst& I = d.inst[blockIdx.y];
-  const double* p = d.phi + I.node_off;
-  R2* G = (R2*)d.G + I.node_off;
-  const bool nofield = (I.flags & APIC_NO_FIELD) != 0;
-  const int n1 = I.n1, n2 = I.n2, N2 = I.N2;
   for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes;
-       nd += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(nd / N2), j = (int)(nd % N2);
-    double g1 = 0.0, g2 = 0.0;
-    if (!nofield) {
-      if (i == 0) g1 = (-3.0 * p[j] + 4.0 * p[N2 + j] - p[2 * N2 + j]) / (2.0 * I.h1);
-      else if (i == n1) g1 = (3.0 * p[n1 * N2 + j] - 4.0 * p[(n1 - 1) * N2 + j] + p[(n1 - 2) * N2 + j]) / (2.0 * I.h1);
-      else g1 = (p[(i + 1) * N2 + j] - p[(i - 1) * N2 + j]) / (2.0 * I.h1);
-      long long b = (long long)i * N2;
-      if (j == 0) g2 = (-3.0 * p[b] + 4.0 * p[b + 1] - p[b + 2]) / (2.0 * I.h2);
-      else if (j == n2) g2 = (3.0 * p[b + n2] - 4.0 * p[b + n2 - 1] + p[b + n2 - 2]) / (2.0 * I.h2);
-      else g2 = (p[b + j + 1] - p[b + j - 1]) / (2.0 * I.h2);
-    }
-    R2 v;
-    v.x = (Real)g1;
-    v.y = (Real)g2;
-    G[nd] = v;
-  }
+       nd += (long long)gridDim.x * blockDim.x)
+    grad_node<Real, R2>(d, I, nd);
 }
 
-// Surface charge sigma = E_n = -(dphi/dx1)|grad x1| on x1 = -1, grain charge
-// Q = int sigma dA and electric force F_Z = int (sigma^2/2) n_Z dA with dA of
-// Eq. 4 (trapezoid over the x2 nodes).  Thread 0 also draws this step's
-// injection count from the fractional carry (floor of carry + lambda).
+// Surface quantities and this step's injection counts, one CTA per instance (surface_block).
 __global__ void __launch_bounds__(256) k_surface(DevPtrs d) {
-  __shared__ double sh[256];
-  const int inst = blockIdx.x;
-  const Inst& I = d.inst[inst];
-  const bool nofield = (I.flags & APIC_NO_FIELD) != 0;
-  double q = 0.0, fz = 0.0;
-  const double* p = d.phi + I.node_off;
-  const int N2 = I.N2;
-  const double* geo = d.sgeo + 4 * I.en_off;  // |grad x1|, n_Z, dA/dx2, trapezoid weight per node
-  for (int j = threadIdx.x; j <= I.n2; j += blockDim.x) {
-    double En = 0.0;
-    if (!nofield) {
-      double g = geo[4 * j + 0], nZ = geo[4 * j + 1], dA = geo[4 * j + 2], tw = geo[4 * j + 3];
-      double G1 = (-3.0 * p[j] + 4.0 * p[N2 + j] - p[2 * N2 + j]) / (2.0 * I.h1);
-      En = -G1 * g;
-      q += tw * En * dA;
-      fz += tw * 0.5 * En * En * nZ * dA;
-    }
-    d.en[I.en_off + j] = En;
-  }
-  double Q = block_sum(q, sh);
-  double FZ = block_sum(fz, sh);
-  if (threadIdx.x == 0) {
-    d.stp[inst].Q = Q;
-    d.stp[inst].FZ = FZ;
-    if (!(Q == Q) || !(FZ == FZ) || Q - Q != 0.0) atomicOr(d.err, kErrNonFinite);
-    for (int s = 0; s < I.n_species; ++s) {
-      PopState& S = d.ps[I.pop0 + s];
-      const Pop& P = d.pop[I.pop0 + s];
-      if (I.flags & APIC_NO_INJECT) {
-        S.n_inj = 0;
-      } else {
-        double c = S.carry + P.lam;
-        double nk = floor(c);
-        S.carry = c - nk;
-        S.n_inj = (long long)nk;
-      }
-      S.inj_stored = 0;
-    }
-  }
+  __shared__ double sh[40];
+  surface_block(d, blockIdx.x, sh);
 }
 
 // Close the step: injected particles become part of the population (freed

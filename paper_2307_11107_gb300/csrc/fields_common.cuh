@@ -1,0 +1,121 @@
+// Per-node and per-instance bodies of the node-field work of a step (Sec. 2),
+// shared by the separate kernels of fields.cu and by the prologue and
+// epilogue of the block-cyclic-reduction solve (bcr.cu), so both compute the
+// same values.  Included inside namespace apic::{anonymous}.
+#pragma once
+
+// rho_ij = sum_s q_s w_s (accumulated CIC weights) / V_ij (Eq. 5); the
+// accumulators are cleared for the next deposit; the initial guess of this
+// step's solve (previous phi, or its linear extrapolation); the right-hand
+// side b = rscale * (-rho) + (Dirichlet terms).  Returns b at the node.
+__device__ __forceinline__ double rho_node(const DevPtrs& d, const Inst& I, int inst, long long nd) {
+  const long long g = I.node_off + nd;
+  double q = 0.0;
+  for (int s = 0; s < I.n_species; ++s) {
+    const Pop& P = d.pop[I.pop0 + s];
+    unsigned long long a = d.acc[P.acc_off + nd];
+    d.acc[P.acc_off + nd] = 0ull;
+    q += P.dep_scale * (double)a;
+  }
+  const double rho = q / d.V[g];
+  d.rho[g] = rho;
+  const int i = (int)(nd / I.N2);
+  double bv = 0.0;
+  if (i > 0 && i < I.n1) {
+    const double ph = d.phi[g];
+    if (I.guess && d.stp[inst].step >= 2) d.phi[g] = 2.0 * ph - d.phi_prev[g];
+    d.phi_prev[g] = ph;
+    bv = -rho * d.rscale[g] + d.bbc[g];
+  }
+  d.b[g] = bv;
+  return bv;
+}
+
+// Node gradients: central differences inside, one-sided second order on the
+// four edges (Sec. 2: derivatives of phi taken numerically at the nodes).
+template <class Real, class R2>
+__device__ __forceinline__ void grad_node(const DevPtrs& d, const Inst& I, long long nd) {
+  const double* p = d.phi + I.node_off;
+  const bool nofield = (I.flags & APIC_NO_FIELD) != 0;
+  const int n1 = I.n1, n2 = I.n2, N2 = I.N2;
+  const int i = (int)(nd / N2), j = (int)(nd % N2);
+  double g1 = 0.0, g2 = 0.0;
+  if (!nofield) {
+    if (i == 0) g1 = (-3.0 * p[j] + 4.0 * p[N2 + j] - p[2 * N2 + j]) / (2.0 * I.h1);
+    else if (i == n1) g1 = (3.0 * p[n1 * N2 + j] - 4.0 * p[(n1 - 1) * N2 + j] + p[(n1 - 2) * N2 + j]) / (2.0 * I.h1);
+    else g1 = (p[(i + 1) * N2 + j] - p[(i - 1) * N2 + j]) / (2.0 * I.h1);
+    const long long b = (long long)i * N2;
+    if (j == 0) g2 = (-3.0 * p[b] + 4.0 * p[b + 1] - p[b + 2]) / (2.0 * I.h2);
+    else if (j == n2) g2 = (3.0 * p[b + n2] - 4.0 * p[b + n2 - 1] + p[b + n2 - 2]) / (2.0 * I.h2);
+    else g2 = (p[b + j + 1] - p[b + j - 1]) / (2.0 * I.h2);
+  }
+  R2 v;
+  v.x = (Real)g1;
+  v.y = (Real)g2;
+  ((R2*)d.G)[I.node_off + nd] = v;
+}
+
+// Fixed-order block sum (warp shuffles, then warp 0 over the warp sums); any
+// blockDim that is a multiple of 32, at most 1024; sh holds 33 doubles.
+__device__ __forceinline__ double block_total(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) sh[32] = t;
+  }
+  __syncthreads();
+  const double r = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// Surface charge sigma = E_n = -(dphi/dx1)|grad x1| on x1 = -1, grain charge
+// Q = int sigma dA and electric force F_Z = int (sigma^2/2) n_Z dA with dA of
+// Eq. 4 (trapezoid over the x2 nodes, geometry tabulated at set-up).  Thread
+// 0 also draws this step's injection count from the fractional carry.  One
+// CTA per instance.
+__device__ __forceinline__ void surface_block(const DevPtrs& d, int inst, double* sh) {
+  const Inst& I = d.inst[inst];
+  const bool nofield = (I.flags & APIC_NO_FIELD) != 0;
+  double q = 0.0, fz = 0.0;
+  const double* p = d.phi + I.node_off;
+  const int N2 = I.N2;
+  const double* geo = d.sgeo + 4 * I.en_off;  // |grad x1|, n_Z, dA/dx2, trapezoid weight per node
+  for (int j = threadIdx.x; j <= I.n2; j += blockDim.x) {
+    double En = 0.0;
+    if (!nofield) {
+      double g = geo[4 * j + 0], nZ = geo[4 * j + 1], dA = geo[4 * j + 2], tw = geo[4 * j + 3];
+      double G1 = (-3.0 * p[j] + 4.0 * p[N2 + j] - p[2 * N2 + j]) / (2.0 * I.h1);
+      En = -G1 * g;
+      q += tw * En * dA;
+      fz += tw * 0.5 * En * En * nZ * dA;
+    }
+    d.en[I.en_off + j] = En;
+  }
+  const double Q = block_total(q, sh);
+  const double FZ = block_total(fz, sh);
+  if (threadIdx.x == 0) {
+    d.stp[inst].Q = Q;
+    d.stp[inst].FZ = FZ;
+    if (!(Q == Q) || !(FZ == FZ) || Q - Q != 0.0) atomicOr(d.err, kErrNonFinite);
+    for (int s = 0; s < I.n_species; ++s) {
+      PopState& S = d.ps[I.pop0 + s];
+      const Pop& P = d.pop[I.pop0 + s];
+      if (I.flags & APIC_NO_INJECT) {
+        S.n_inj = 0;
+      } else {
+        double c = S.carry + P.lam;
+        double nk = floor(c);
+        S.carry = c - nk;
+        S.n_inj = (long long)nk;
+      }
+      S.inj_stored = 0;
+    }
+  }
+}

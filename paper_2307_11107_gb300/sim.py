@@ -135,7 +135,8 @@ class Sim:
                     kernels_per_step=int(st.kernels_per_step), kernels_per_iter=int(st.kernels_per_iter),
                     timed_steps=int(st.timed_steps),
                     phase_ms=dict(zip(_abi.PHASES, [float(v) for v in st.phase_ms])),
-                    solver=_abi.SOLVERS[int(st.solver)])
+                    solver=_abi.SOLVERS[int(st.solver)], sorts=int(st.sorts),
+                    kernels_per_sort=int(st.kernels_per_sort))
 
     def tallies(self, instance=0, history=True):
         c = self.cfgs[instance]
