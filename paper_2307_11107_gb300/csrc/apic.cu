@@ -170,6 +170,8 @@ struct apic_sim {
   long long timed_steps = 0;
   long long slots = 0;                // particle slots of one buffer (all populations)
   long long sorts = 0;                // particle sorts launched
+  size_t bcr_bytes = 0;               // reduction blocks + tail inverse (one device range)
+  size_t l2_persist = 0;              // bytes of L2 set aside for them (0: none)
   long long tab_total = 0;
   TanPtrs tan{};                      // sensitivity-window state (allocated on first use)
   bool tan_ready = false;
@@ -865,8 +867,11 @@ static int setup(apic_sim* S) {
   d.cred = (double*)A(sizeof(double) * ni * kNRed * kCoopMaxBlocks);
   d.bar = (unsigned*)A(sizeof(unsigned) * 4);
   if (pl.bcr.K > 0) {
-    d.bcr = (float*)A(sizeof(float) * bcr_h.size());
-    d.bcr_tail = (float*)A(sizeof(float) * (size_t)pl.bcr.tail_n * pl.bcr.tail_np);
+    // blocks and tail inverse in one range (one L2 access-policy window covers both)
+    const size_t tail_floats = (size_t)pl.bcr.tail_n * pl.bcr.tail_np;
+    d.bcr = (float*)A(sizeof(float) * (bcr_h.size() + tail_floats));
+    d.bcr_tail = d.bcr ? d.bcr + bcr_h.size() : nullptr;
+    S->bcr_bytes = sizeof(float) * (bcr_h.size() + tail_floats);
     d.bcr_f = (float*)A(sizeof(float) * (size_t)(S->inst[0].n1 - 1) * S->inst[0].N2);
     d.bcr_e = (float*)A(sizeof(float) * (size_t)(S->inst[0].n1 - 1) * S->inst[0].N2);
     if (d.bcr) S->h2d(d.bcr, bcr_h.data(), bcr_h.size());
@@ -985,6 +990,20 @@ static int setup(apic_sim* S) {
   S->coop = want_coop ? coop_blocks<Real>(S->plan, sms) : 0;
   if (const char* nbv = std::getenv("APIC_COOP_BLOCKS")) S->coop = std::min(S->coop, std::max(1, std::atoi(nbv)));
   if (pl.bcr.K > 0) S->coop = bcr_blocks(pl, sms);
+  // Optionally (APIC_L2_PERSIST=1) keep the reduction's blocks in L2 across
+  // steps: a persisting access window on the solve's graph node, with this
+  // context's L2 set-aside (released with the context).  Off by default: on
+  // the bench the set-aside slowed the push and injection by more than it
+  // saved in the solve.
+  if (pl.bcr.K > 0 && std::getenv("APIC_L2_PERSIST") && std::string(std::getenv("APIC_L2_PERSIST")) == "1") {
+    int maxp = 0, maxw = 0;
+    cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev);
+    cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+    size_t want = std::min<size_t>(S->bcr_bytes, (size_t)std::max(0, maxp));
+    if (want > 0 && maxw > 0 && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess)
+      S->l2_persist = want;
+    cudaGetLastError();
+  }
   cudaGetLastError();
   return S->sync() ? APIC_OK : S->status;
 }
@@ -1140,6 +1159,34 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
   return true;
 }
 
+// Persisting L2 window over the reduction blocks on the solve's kernel node.
+static void set_persisting_window(apic_sim* S, const DevPtrs& d, cudaGraph_t g) {
+  if (S->l2_persist == 0 || !d.bcr) return;
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return;
+  int dev = 0, maxw = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+  for (cudaGraphNode_t node : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(node, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp;
+    if (cudaGraphKernelNodeGetParams(node, &kp) != cudaSuccess || kp.func != bcr_kernel()) continue;
+    cudaKernelNodeAttrValue v;
+    std::memset(&v, 0, sizeof(v));
+    v.accessPolicyWindow.base_ptr = (void*)d.bcr;
+    v.accessPolicyWindow.num_bytes = std::min<size_t>(S->bcr_bytes, (size_t)maxw);
+    v.accessPolicyWindow.hitRatio =
+        (float)std::min(1.0, (double)S->l2_persist / (double)v.accessPolicyWindow.num_bytes);
+    v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cudaGraphKernelNodeSetAttribute(node, cudaKernelNodeAttributeAccessPolicyWindow, &v);
+  }
+  cudaGetLastError();
+}
+
 // Capture phases [p0, p1) into one executable graph.  If the while-node cannot
 // be built, the capture is redone once with a fixed, early-exiting loop.
 template <class Real>
@@ -1153,6 +1200,7 @@ static bool capture(apic_sim* S, const DevPtrs& d, int p0, int p1, cudaGraph_t* 
     cudaError_t e = cudaStreamEndCapture(s, &g);
     if (ok && e == cudaSuccess) {
       *graph = g;
+      set_persisting_window(S, d, g);
       return S->ck(cudaGraphInstantiate(exec, g, 0), "graph instantiate");
     }
     if (g) cudaGraphDestroy(g);

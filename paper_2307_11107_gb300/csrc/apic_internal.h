@@ -284,7 +284,8 @@ void launch_finish_injection(const DevPtrs& d, int pop, cudaStream_t s);
 constexpr int kBcrRho = 1;     // form rho, the guess and b inside the solve
 constexpr int kBcrFields = 2;  // node gradients and surface quantities after the solve
 cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& plan, int blocks, int mode, cudaStream_t s);
-int bcr_blocks(SolvePlan& plan, int sms);  // CTAs of the launch (0: not co-residable); sets plan.bcr.smem
+int bcr_blocks(SolvePlan& plan, int sms);
+const void* bcr_kernel();  // the solve kernel (to find its graph node)  // CTAs of the launch (0: not co-residable); sets plan.bcr.smem
 
 // sensitivity window (tangent.cu)
 template <class Real>

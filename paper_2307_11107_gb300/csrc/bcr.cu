@@ -359,6 +359,8 @@ static long long dyn_bytes(const BcrPlan& b) {
   return staged > tail ? staged : tail;
 }
 
+const void* bcr_kernel() { return (const void*)k_solve_bcr; }
+
 int bcr_blocks(SolvePlan& pl, int sms) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);

@@ -1019,7 +1019,7 @@ void launch_inject<Real>(const DevPtrs& d, long long max_inj, cudaStream_t s) {
   if (max_inj <= 0) return;
   // few CTAs, several injections per thread: fewer window flushes
   unsigned gx = blocks_for(max_inj, 256);
-  gx = gx < 64 ? gx : 64;
+  gx = gx < 160 ? gx : 160;
   dim3 g(gx, d.n_pop);
   k_inject<<<g, 256, 0, s>>>(d);
 }
