@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--workload", default="dipole256", choices=["dipole256", "dipole1024", "batched48", "sphere64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="choose the sort interval with apic_autotune after the warm-up (untimed)")
     return ap.parse_args()
 
 
@@ -226,6 +228,9 @@ def main():
         for sp in range(len(c["species"])):
             sim.load_volume(sp, c["species"][sp]["n_init"], instance=k)
     sim.step(args.warmup)
+    tuned = None
+    if args.autotune:
+        tuned = sim.autotune(max(2, args.warmup // 7))[0]
 
     def barrier():
         if pg is not None:
@@ -333,7 +338,8 @@ def main():
                        "precision": "FP32 particles; Poisson: " + st["solver"],
                        "l2": "inputs larger than L2 (particle state %.0f MB)" % (
                            sum(2 * c["species"][0]["n_init"] for c in cfgs) * 20 / 1e6),
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "sort_interval": tuned if tuned is not None else cfg.get("sort_interval", 0)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "poisson_loop_iters": int(loop_iters), "clocks": clk.summary(),
         }

@@ -213,6 +213,22 @@ int apic_stats(apic_sim* sim, apic_stats_t* out);
  * apic_step. */
 int apic_step_timed(apic_sim* sim, int32_t n_steps);
 
+/* ---- Autotuning ------------------------------------------------------------
+ * The particle sort's interval trades the sort's cost against the push's
+ * locality (the push deposits through a shared-memory window of grid rows,
+ * which works best on recently sorted particles).  apic_autotune runs
+ * steps_per_trial full steps with each of APIC_TUNE_CANDIDATES intervals
+ * (2, 4, 6, 8, 12, 16, 24; every trial starts with a sort), timed with CUDA
+ * events on the simulation's stream, and keeps the fastest for the following
+ * steps.  The simulation advances by APIC_TUNE_CANDIDATES * steps_per_trial
+ * steps (results as apic_step).  Without sorting (sort_interval = 0 at
+ * creation) nothing runs and 0 is returned in *sort_interval.
+ * ms_per_step: [APIC_TUNE_CANDIDATES] host array (or NULL) for the measured
+ * times.  Errors: INVALID_ARG (NULL sort_interval, steps_per_trial < 1),
+ * those of apic_step. */
+#define APIC_TUNE_CANDIDATES 7
+int apic_autotune(apic_sim* sim, int32_t steps_per_trial, int32_t* sort_interval, double* ms_per_step);
+
 /* ---- Sensitivity window (forward mode) -----------------------------------
  * Derivatives of window-averaged grain outputs with respect to the grain
  * shape alpha (Eqs. 2-5, 7), the grain potential phi_g (boundary value of

@@ -1335,6 +1335,60 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
   return APIC_OK;
 }
 
+// Sort-interval autotuning: `trial` steps with each candidate interval (each
+// trial starts with a sort), CUDA events on the simulation's stream; the
+// fastest interval is kept.  Advances the simulation by 7 * trial steps.
+static const int kTuneIntervals[APIC_TUNE_CANDIDATES] = {2, 4, 6, 8, 12, 16, 24};
+
+template <class Real>
+static int autotune_impl(apic_sim* S, int trial, int32_t* chosen, double* ms_out) {
+  if (!redeposit<Real>(S) || !ensure_graphs<Real>(S)) return S->status;
+  if (S->sort_interval <= 0) {  // sorting is off (no second particle buffer)
+    *chosen = 0;
+    return APIC_OK;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (!S->ck(cudaEventCreate(&a), "event") || !S->ck(cudaEventCreate(&b), "event")) return S->status;
+  double best = 1e300;
+  int best_c = S->sort_interval;
+  for (int q = 0; q < APIC_TUNE_CANDIDATES && S->status == APIC_OK; ++q) {
+    const int c = kTuneIntervals[q];
+    S->ck(cudaEventRecord(a, S->stream), "event record");
+    for (int k = 0; k < trial; ++k) {
+      if (k % c == 0) {
+        if (!S->ck(cudaGraphLaunch(S->sort_exec[S->par], S->stream), "sort launch")) break;
+        S->par ^= 1;
+        S->sorts += 1;
+      }
+      if (!S->ck(cudaGraphLaunch(S->exec[S->par], S->stream), "graph launch")) break;
+      S->host_step += 1;
+    }
+    S->ck(cudaEventRecord(b, S->stream), "event record");
+    if (!S->ck(cudaEventSynchronize(b), "event sync")) break;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    const double per = (double)ms / trial;
+    if (ms_out) ms_out[q] = per;
+    if (per < best) {
+      best = per;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (S->status != APIC_OK) return S->status;
+  S->sort_interval = best_c;
+  *chosen = best_c;
+  return read_status(S);
+}
+
+extern "C" int apic_autotune(apic_sim* S, int32_t steps_per_trial, int32_t* sort_interval, double* ms_per_step) {
+  if (!S || !sort_interval || steps_per_trial < 1) return APIC_ERR_INVALID_ARG;
+  if (S->status != APIC_OK) return S->status;
+  return S->precision == APIC_FP64 ? autotune_impl<double>(S, steps_per_trial, sort_interval, ms_per_step)
+                                   : autotune_impl<float>(S, steps_per_trial, sort_interval, ms_per_step);
+}
+
 extern "C" int apic_step(apic_sim* S, int32_t n_steps) {
   if (!S) return APIC_ERR_INVALID_ARG;
   if (S->status != APIC_OK) return S->status;

@@ -207,3 +207,12 @@ class Sim:
         dp = C.POINTER(C.c_double)
         self._check(self._lib.apic_adjoint(self.h, int(n_steps), g.ctypes.data_as(dp), grad.ctypes.data_as(dp)))
         return grad
+
+    def autotune(self, steps_per_trial=16):
+        """Sort-interval autotuning (apic_autotune): returns the interval kept
+        and the measured ms per step of every candidate."""
+        ms = np.zeros(len(_abi.TUNE_INTERVALS))
+        chosen = C.c_int32()
+        self._check(self._lib.apic_autotune(self.h, int(steps_per_trial), C.byref(chosen),
+                                            ms.ctypes.data_as(C.POINTER(C.c_double))))
+        return int(chosen.value), dict(zip(_abi.TUNE_INTERVALS, ms.tolist()))

@@ -54,3 +54,27 @@ def test_batch_equals_solo(prec, monkeypatch):
             assert tb["counts"][sp] == ts["counts"][sp]
         assert np.allclose(tb["bins"], ts["bins"], rtol=1e-12, atol=1e-300)
         assert np.allclose(tb["history"], ts["history"], rtol=1e-12, atol=1e-12)
+
+
+def test_autotune_keeps_a_candidate_and_stepping_stays_valid():
+    """The sort-interval autotuner times every candidate, keeps the fastest
+    and leaves a simulation that steps on with consistent counts."""
+    import paper_2307_11107_gb300 as apic
+    apic.build()
+    cfgs = _instances("fp32")
+    s = apic.Sim(cfgs)
+    for k, c in enumerate(cfgs):
+        for sp in range(len(c["species"])):
+            s.load_volume(sp, c["species"][sp]["n_init"], instance=k)
+    s.step(4)
+    chosen, ms = s.autotune(4)
+    assert chosen in ms and all(v > 0.0 for v in ms.values())
+    assert ms[chosen] == min(ms.values())
+    s.step(5)
+    for k in range(len(cfgs)):
+        t = s.tallies(k)
+        assert t["step"] == 4 + 4 * len(ms) + 5
+        for sp in (0, 1):
+            cnt = t["counts"][sp]
+            assert cnt["resident"] == s.particles(sp, instance=k).shape[0]
+    s.close()
