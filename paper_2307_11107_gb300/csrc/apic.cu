@@ -423,15 +423,27 @@ void build_fine(const Inst& I, HostLevel& L, std::vector<double>& rscale, std::v
 // ---- block cyclic reduction set-up (FP64 on the host, blocks stored in FP32) ----
 using Mat = std::vector<double>;  // row-major n x n
 
+// c = a b; zeros of a are skipped and each row of b is visited over its
+// nonzero range only, so products with the tridiagonal blocks of Eq. 7 cost
+// O(n^2).
 void mat_mul(const Mat& a, const Mat& b, Mat& c, int n) {
   c.assign((size_t)n * n, 0.0);
+  std::vector<int> lo(n), hi(n);
+  for (int k = 0; k < n; ++k) {
+    const double* bk = b.data() + (size_t)k * n;
+    int l = 0, h = n - 1;
+    while (l < n && bk[l] == 0.0) ++l;
+    while (h >= l && bk[h] == 0.0) --h;
+    lo[k] = l;
+    hi[k] = h;
+  }
   for (int i = 0; i < n; ++i) {
     double* ci = c.data() + (size_t)i * n;
     for (int k = 0; k < n; ++k) {
       double aik = a[(size_t)i * n + k];
-      if (aik == 0.0) continue;
+      if (aik == 0.0 || lo[k] > hi[k]) continue;
       const double* bk = b.data() + (size_t)k * n;
-      for (int j = 0; j < n; ++j) ci[j] += aik * bk[j];
+      for (int j = lo[k]; j <= hi[k]; ++j) ci[j] += aik * bk[j];
     }
   }
 }
@@ -489,42 +501,31 @@ void parallel_for(int n, F f) {
   for (auto& x : th) x.join();
 }
 
-// Blocks of the reduction of the finest-level system (stencil of level L,
-// rows scaled, Dirichlet neighbours zero) and the dense tail system T
-// (FP64, row-major, inverted on the GPU by the caller): returns false
-// (multigrid is used instead) if n1 is not a power of two or a pivot vanishes.
-bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float>& out, std::vector<double>& T) {
+// Layout of instance I's reduction: block size, levels before the dense
+// tail, first block of each kind per level (real rows only).  False if the
+// reduction does not apply (N2 > kBcrMaxN, n1 < 4, n1 > 2^(kBcrMaxK-1)).
+bool bcr_layout(const Inst& I, BcrInst& bp) {
+  std::memset(&bp, 0, sizeof(bp));
+  const int N = I.N2, M = I.n1 - 1;
+  if (I.n1 < 4 || N > kBcrMaxN) return false;
   int K = 0;
   while ((1 << K) < I.n1) ++K;
-  if ((1 << K) != I.n1 || K < 2 || K >= kBcrMaxK || I.N2 > kBcrMaxN) return false;
-  const int N = I.N2, M = I.n1 - 1;
-  std::vector<Mat> A(M + 2), Bm(M + 2), C(M + 2);
-  for (int i = 1; i <= M; ++i) {
-    A[i].assign((size_t)N * N, 0.0);
-    Bm[i].assign((size_t)N * N, 0.0);
-    C[i].assign((size_t)N * N, 0.0);
-    for (int j = 0; j < N; ++j) {
-      for (int dj = -1; dj <= 1; ++dj) {
-        int jj = j + dj;
-        if (jj < 0 || jj >= N) continue;
-        A[i][(size_t)j * N + jj] = L.get(st_slot(-1, dj), i, j);
-        Bm[i][(size_t)j * N + jj] = L.get(st_slot(0, dj), i, j);
-        C[i][(size_t)j * N + jj] = L.get(st_slot(1, dj), i, j);
-      }
-    }
-    Bm[i][2] += L.get(kStPole, i, 0);
-    Bm[i][(size_t)(N - 1) * N + N - 3] += L.get(kStPole, i, N - 1);
-  }
-  std::memset(&bp, 0, sizeof(bp));
+  if (K >= kBcrMaxK) return false;
   int Lt = 0;
-  while (Lt < K - 1 && (long long)((1 << (K - Lt)) - 1) * N > kBcrTailMax) ++Lt;
+  while (Lt < K - 1 && (long long)(M >> Lt) * N > kBcrTailMax) ++Lt;
   if (const char* e = std::getenv("APIC_BCR_LEVELS")) {  // tuning: more reduction levels, smaller tail
     int v = std::atoi(e);
     if (v >= Lt && v <= K - 1) Lt = v;
   }
   long long nblk = 0;
   for (int l = 1; l <= Lt; ++l) {
-    long long ne = 1ll << (K - l), nk = ne - 1;
+    const int h = 1 << (l - 1);
+    const long long ne = (M / h + 1) / 2, nk = M / (2 * h);
+    if (l == 1) {
+      bp.Binv[l] = nblk;
+      nblk += ne;
+      continue;
+    }
     bp.P[l] = nblk;
     nblk += nk;
     bp.Q[l] = nblk;
@@ -542,11 +543,38 @@ bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float
   bp.Np = (N + 3) & ~3;
   bp.blk = (long long)N * bp.Np;
   bp.Lt = Lt;
-  bp.tail_m = (1 << (K - Lt)) - 1;
+  bp.M = M;
+  bp.tail_m = M >> Lt;
   bp.tail_n = bp.tail_m * N;
   bp.tail_np = (bp.tail_n + 3) & ~3;
-  out.assign((size_t)std::max<long long>(1, nblk) * bp.blk, 0.0f);
-  const int Np = bp.Np;
+  return bp.tail_n <= kBcrTailMax;
+}
+
+// Blocks of the reduction of instance I's finest-level system (stencil of
+// level L, rows scaled, Dirichlet neighbours zero) in the layout bp, and the
+// dense tail system T (FP64, row-major, inverted on the GPU by the caller);
+// false if a pivot vanishes.
+bool bcr_factor(const HostLevel& L, const BcrInst& bp, std::vector<float>& out, std::vector<double>& T) {
+  const int N = bp.N, M = bp.M, Np = bp.Np, Lt = bp.Lt;
+  std::vector<Mat> A(M + 2), Bm(M + 2), C(M + 2);
+  parallel_for(M, [&](int r) {
+    const int i = r + 1;
+    A[i].assign((size_t)N * N, 0.0);
+    Bm[i].assign((size_t)N * N, 0.0);
+    C[i].assign((size_t)N * N, 0.0);
+    for (int j = 0; j < N; ++j) {
+      for (int dj = -1; dj <= 1; ++dj) {
+        int jj = j + dj;
+        if (jj < 0 || jj >= N) continue;
+        A[i][(size_t)j * N + jj] = L.get(st_slot(-1, dj), i, j);
+        Bm[i][(size_t)j * N + jj] = L.get(st_slot(0, dj), i, j);
+        C[i][(size_t)j * N + jj] = L.get(st_slot(1, dj), i, j);
+      }
+    }
+    Bm[i][2] += L.get(kStPole, i, 0);
+    Bm[i][(size_t)(N - 1) * N + N - 3] += L.get(kStPole, i, N - 1);
+  });
+  out.assign((size_t)std::max<long long>(1, bp.blocks) * bp.blk, 0.0f);
   auto store = [&](long long idx, const Mat& m) {
     float* o = out.data() + (size_t)idx * bp.blk;
     for (int r = 0; r < N; ++r)
@@ -554,7 +582,7 @@ bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float
   };
   bool ok = true;
   for (int l = 1; l <= Lt && ok; ++l) {
-    const int h = 1 << (l - 1), ne = 1 << (K - l), nk = ne - 1;
+    const int h = 1 << (l - 1), ne = (M / h + 1) / 2, nk = M / (2 * h);
     std::vector<Mat> Binv(ne);
     std::vector<char> good(ne, 1);
     parallel_for(ne, [&](int q) {
@@ -563,8 +591,9 @@ bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float
         good[q] = 0;
         return;
       }
-      Mat t;
       store(bp.Binv[l] + q, Binv[q]);
+      if (l == 1) return;  // level 1 applies A_k and C_k from the stencil
+      Mat t;
       mat_mul(Binv[q], A[k], t, N);
       store(bp.G[l] + q, t);
       mat_mul(Binv[q], C[k], t, N);
@@ -575,23 +604,36 @@ bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float
     std::vector<Mat> nA(nk), nB(nk), nC(nk);
     parallel_for(nk, [&](int q) {
       const int i = 2 * h * (q + 1);
+      const bool right = i + h <= M;  // else C_i = 0: row i + h carries no unknowns
       Mat P, Q, t;
       mat_mul(A[i], Binv[q], P, N);
-      mat_mul(C[i], Binv[q + 1], Q, N);
-      store(bp.P[l] + q, P);
-      store(bp.Q[l] + q, Q);
+      if (right) mat_mul(C[i], Binv[q + 1], Q, N);
+      else Q.assign((size_t)N * N, 0.0);
+      if (l > 1) {
+        store(bp.P[l] + q, P);
+        store(bp.Q[l] + q, Q);
+      }
       mat_mul(P, A[i - h], t, N);
       nA[q].assign((size_t)N * N, 0.0);
       for (size_t e = 0; e < t.size(); ++e) nA[q][e] = -t[e];
-      mat_mul(Q, C[i + h], t, N);
       nC[q].assign((size_t)N * N, 0.0);
-      for (size_t e = 0; e < t.size(); ++e) nC[q][e] = -t[e];
       nB[q] = Bm[i];
       mat_mul(P, C[i - h], t, N);
       for (size_t e = 0; e < t.size(); ++e) nB[q][e] -= t[e];
-      mat_mul(Q, A[i + h], t, N);
-      for (size_t e = 0; e < t.size(); ++e) nB[q][e] -= t[e];
+      if (right) {
+        mat_mul(Q, C[i + h], t, N);
+        for (size_t e = 0; e < t.size(); ++e) nC[q][e] = -t[e];
+        mat_mul(Q, A[i + h], t, N);
+        for (size_t e = 0; e < t.size(); ++e) nB[q][e] -= t[e];
+      }
     });
+    // the eliminated rows are no longer needed
+    for (int q = 0; q < ne; ++q) {
+      const int k = h * (2 * q + 1);
+      Mat().swap(A[k]);
+      Mat().swap(Bm[k]);
+      Mat().swap(C[k]);
+    }
     for (int q = 0; q < nk; ++q) {
       const int i = 2 * h * (q + 1);
       A[i].swap(nA[q]);
@@ -600,7 +642,7 @@ bool bcr_setup(const Inst& I, const HostLevel& L, BcrPlan& bp, std::vector<float
     }
   }
   if (!ok) return false;
-  // the rows left, i = 2^Lt (q + 1): dense block tridiagonal system
+  // the rows left, i = 2^Lt (q + 1) <= M: dense block tridiagonal system
   const int m = bp.tail_m, n = bp.tail_n, hs = 1 << Lt;
   T.assign((size_t)n * n, 0.0);
   for (int q = 0; q < m; ++q) {
@@ -791,25 +833,92 @@ static int setup(apic_sim* S) {
   pl.smooth_split = 1;
   if (const char* sm = std::getenv("APIC_MG_SMOOTH")) pl.smooth_split = std::string(sm) != "alt";
   if (!S->ck(set_poisson_smem<Real>(pl), "cudaFuncSetAttribute(smem)")) return S->status;
-  // Direct block cyclic reduction in place of multigrid: FP32 particles, one
-  // instance, n1 = 2^K, blocks within the memory budget (APIC_PRECOND=mg
-  // keeps multigrid).
-  std::vector<float> bcr_h;
-  std::vector<double> bcr_T;
+  // Direct block cyclic reduction in place of multigrid: FP32 particles, every
+  // instance with a field, N2 <= kBcrMaxN, the blocks of the batch within the
+  // memory budget (APIC_PRECOND=mg keeps multigrid).
+  std::vector<BcrInst> bcr_in;
+  std::vector<int32_t> bcr_kind, bcr_pre, bcr_npre;
+  long long bcr_rows = 0;  // floats of bcr_f (and of bcr_e)
+  int bcr_nb = 0;          // CTAs of the reduction solve
   {
     const char* pc = std::getenv("APIC_PRECOND");
-    const Inst& I0 = S->inst[0];
-    bool want = sizeof(Real) == 4 && ni == 1 && !(I0.flags & APIC_NO_FIELD) && !(pc && std::string(pc) == "mg");
-    double bytes = 4.0 * I0.N2 * (I0.N2 + 3) * 5.0 * I0.n1;
-    if (!(want && bytes <= kBcrMaxBytes && bcr_setup(I0, levels[0][0], pl.bcr, bcr_h, bcr_T))) pl.bcr.K = 0;
-    if (pl.bcr.K > 0) {
+    bool want = sizeof(Real) == 4 && ni <= kCoopMaxInst && !(pc && std::string(pc) == "mg");
+    for (const Inst& I : S->inst) want = want && !(I.flags & APIC_NO_FIELD);
+    long long off = 0;
+    if (want) {
+      bcr_in.resize(ni);
+      for (int k = 0; k < ni && want; ++k) {
+        BcrInst& B = bcr_in[k];
+        if (!bcr_layout(S->inst[k], B)) {
+          want = false;
+          break;
+        }
+        auto up = [](long long v) { return (v + 63) & ~63ll; };  // 256-byte aligned ranges
+        B.base = off;
+        off += up(B.blocks * B.blk);
+        B.tail = off;
+        off += up((long long)B.tail_n * B.tail_np);
+        B.foff = bcr_rows;
+        bcr_rows += (long long)B.M * B.N;
+      }
+    }
+    const double bytes = 4.0 * (double)off;
+    if (want) {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
+      cudaGetLastError();
+      want = bytes <= kBcrMaxBytes && bytes <= 0.6 * (double)fr;
+    }
+    if (want) {
       int dev = 0, sms = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (bcr_blocks(pl, sms) <= 0) pl.bcr.K = 0;  // not co-residable: multigrid
+      want = (bcr_nb = bcr_configure(pl, bcr_in.data(), ni, sms)) > 0;  // else not co-residable: multigrid
+    }
+    if (want) {
+      // stages of each instance, aligned at the first phase
+      std::vector<std::vector<std::pair<int, int>>> stages(ni);  // (kind << 8 | level, tasks)
+      int phases = 0;
+      for (int k = 0; k < ni; ++k) {
+        const BcrInst& B = bcr_in[k];
+        auto& st = stages[k];
+        const int M = B.M;
+        auto ne = [&](int l) { return (M / (1 << (l - 1)) + 1) / 2; };
+        auto nk = [&](int l) { return M / (2 << (l - 1)); };
+        if (B.Lt >= 1) {
+          st.push_back({kBcrFwd1 << 8 | 1, ne(1)});
+          st.push_back({kBcrUpd1 << 8 | 1, (nk(1) + kBcrUpdRows - 1) / kBcrUpdRows});
+          for (int l = 2; l <= B.Lt; ++l) st.push_back({kBcrFwd << 8 | l, nk(l)});
+        }
+        st.push_back({kBcrTail << 8, (B.tail_n + B.tail_rows - 1) / B.tail_rows});
+        for (int l = B.Lt; l >= 2; --l) st.push_back({kBcrBack << 8 | l, ne(l)});
+        if (B.Lt >= 1) st.push_back({kBcrBack1 << 8 | 1, ne(1)});
+        phases = std::max(phases, (int)st.size());
+      }
+      bcr_kind.assign((size_t)phases * ni, 0);
+      bcr_pre.assign((size_t)phases * (ni + 1), 0);
+      for (int p = 0; p < phases; ++p)
+        for (int k = 0; k < ni; ++k) {
+          int cnt = 0;
+          if (p < (int)stages[k].size()) {
+            bcr_kind[(size_t)p * ni + k] = stages[k][p].first;
+            cnt = stages[k][p].second;
+          }
+          bcr_pre[(size_t)p * (ni + 1) + k + 1] = bcr_pre[(size_t)p * (ni + 1) + k] + cnt;
+        }
+      bcr_npre.assign(ni + 1, 0);
+      for (int k = 0; k < ni; ++k)
+        bcr_npre[k + 1] = bcr_npre[k] + (int)((S->inst[k].nodes + kBcrNodeChunk - 1) / kBcrNodeChunk);
+      pl.bcr.chunks = bcr_npre[ni];
+      pl.bcr.n_inst = ni;
+      pl.bcr.phases = phases;
+      pl.bcr.bytes = (int64_t)(4 * off);
+      pl.bcr.prefetch = bytes <= 112.0 * 1024 * 1024 ? 1 : 0;  // the whole reduction fits in L2
+    } else {
+      pl.bcr.n_inst = 0;
     }
   }
-  const bool use_mg = pl.bcr.K == 0;  // the multigrid hierarchy is only set up when it is used
+  const bool use_mg = pl.bcr.n_inst == 0;  // the multigrid hierarchy is only set up when it is used
 
   // ---- device memory ----
   DevPtrs& d = S->d;
@@ -866,41 +975,57 @@ static int setup(apic_sim* S) {
   d.red = (double*)A(sizeof(double) * ni * kNRed * kRedBlocks);
   d.cred = (double*)A(sizeof(double) * ni * kNRed * kCoopMaxBlocks);
   d.bar = (unsigned*)A(sizeof(unsigned) * 4);
-  if (pl.bcr.K > 0) {
-    // blocks and tail inverse in one range (one L2 access-policy window covers both)
-    const size_t tail_floats = (size_t)pl.bcr.tail_n * pl.bcr.tail_np;
-    d.bcr = (float*)A(sizeof(float) * (bcr_h.size() + tail_floats));
-    d.bcr_tail = d.bcr ? d.bcr + bcr_h.size() : nullptr;
-    S->bcr_bytes = sizeof(float) * (bcr_h.size() + tail_floats);
-    d.bcr_f = (float*)A(sizeof(float) * (size_t)(S->inst[0].n1 - 1) * S->inst[0].N2);
-    d.bcr_e = (float*)A(sizeof(float) * (size_t)(S->inst[0].n1 - 1) * S->inst[0].N2);
-    if (d.bcr) S->h2d(d.bcr, bcr_h.data(), bcr_h.size());
+  if (pl.bcr.n_inst > 0) {
+    // blocks and tail inverses of every instance in one range (one L2
+    // access-policy window covers them)
+    d.bcr = (float*)A((size_t)pl.bcr.bytes);
+    S->bcr_bytes = (size_t)pl.bcr.bytes;
+    d.bcr_f = (float*)A(sizeof(float) * (size_t)bcr_rows);
+    d.bcr_e = (float*)A(sizeof(float) * (size_t)bcr_rows);
+    d.bcr_inst = (const BcrInst*)A(sizeof(BcrInst) * ni);
+    d.bcr_kind = (const int32_t*)A(sizeof(int32_t) * bcr_kind.size());
+    d.bcr_pre = (const int32_t*)A(sizeof(int32_t) * bcr_pre.size());
+    d.bcr_npre = (const int32_t*)A(sizeof(int32_t) * bcr_npre.size());
+    d.bcr_part = (double*)A(sizeof(double) * 2 * (size_t)pl.bcr.chunks);
     if (S->status != APIC_OK) return S->status;
-    // dense inverse of the tail system: Gauss-Jordan on the GPU (FP64), stored in FP32
-    const int n = pl.bcr.tail_n;
-    double* work = (double*)S->dalloc(sizeof(double) * 2 * (size_t)n * n);
-    double* fbuf = (double*)S->dalloc(sizeof(double) * (size_t)n);
-    if (!work || !fbuf) return S->status;
-    std::vector<double> aug((size_t)n * 2 * n, 0.0);
-    for (int r = 0; r < n; ++r) {
-      std::memcpy(aug.data() + (size_t)r * 2 * n, bcr_T.data() + (size_t)r * n, sizeof(double) * n);
-      aug[(size_t)r * 2 * n + n + r] = 1.0;
-    }
-    S->h2d(work, aug.data(), aug.size());
-    float* dense = (float*)S->dalloc(sizeof(float) * (size_t)n * n);
-    if (!dense) return S->status;
-    if (!S->ck(launch_dense_inverse<float>(work, fbuf, n, dense, S->stream), "dense inverse (tail)")) return S->status;
-    // rows padded to 16 bytes (one bulk copy per CTA's row range)
-    if (!S->ck(cudaMemcpy2DAsync(d.bcr_tail, sizeof(float) * pl.bcr.tail_np, dense, sizeof(float) * n, sizeof(float) * n, n,
-                                 cudaMemcpyDeviceToDevice, S->stream),
-               "tail copy"))
-      return S->status;
+    S->h2d((BcrInst*)d.bcr_inst, bcr_in.data(), bcr_in.size());
+    S->h2d((int32_t*)d.bcr_kind, bcr_kind.data(), bcr_kind.size());
+    S->h2d((int32_t*)d.bcr_pre, bcr_pre.data(), bcr_pre.size());
+    S->h2d((int32_t*)d.bcr_npre, bcr_npre.data(), bcr_npre.size());
     if (!S->sync()) return S->status;
-    for (void* q : {(void*)dense, (void*)fbuf, (void*)work}) {
-      auto it = std::find(S->blocks.begin(), S->blocks.end(), q);
-      if (it != S->blocks.end()) S->blocks.erase(it);
-      if (S->have_alloc) S->alloc.free(q, (void*)S->stream, S->alloc.ctx);
-      else cudaFreeAsync(q, S->stream);
+    std::vector<float> blocks;
+    std::vector<double> T, aug;
+    for (int k = 0; k < ni; ++k) {
+      const BcrInst& B = bcr_in[k];
+      if (!bcr_factor(levels[k][0], B, blocks, T))
+        return S->fail(APIC_ERR_INVALID_ARG, "block cyclic reduction: singular diagonal block");
+      if (B.blocks > 0) S->h2d(d.bcr + B.base, blocks.data(), (size_t)(B.blocks * B.blk));
+      // dense inverse of the tail system: Gauss-Jordan on the GPU (FP64), stored in FP32
+      const int n = B.tail_n;
+      double* work = (double*)S->dalloc(sizeof(double) * 2 * (size_t)n * n);
+      double* fbuf = (double*)S->dalloc(sizeof(double) * (size_t)n);
+      float* dense = (float*)S->dalloc(sizeof(float) * (size_t)n * n);
+      if (!work || !fbuf || !dense) return S->status;
+      aug.assign((size_t)n * 2 * n, 0.0);
+      for (int r = 0; r < n; ++r) {
+        std::memcpy(aug.data() + (size_t)r * 2 * n, T.data() + (size_t)r * n, sizeof(double) * n);
+        aug[(size_t)r * 2 * n + n + r] = 1.0;
+      }
+      S->h2d(work, aug.data(), aug.size());
+      if (!S->ck(launch_dense_inverse<float>(work, fbuf, n, dense, S->stream), "dense inverse (tail)"))
+        return S->status;
+      // rows padded to 16 bytes (bulk copies of row chunks)
+      if (!S->ck(cudaMemcpy2DAsync(d.bcr + B.tail, sizeof(float) * B.tail_np, dense, sizeof(float) * n,
+                                   sizeof(float) * n, n, cudaMemcpyDeviceToDevice, S->stream),
+                 "tail copy"))
+        return S->status;
+      if (!S->sync()) return S->status;  // the host vectors are refilled for the next instance
+      for (void* q : {(void*)dense, (void*)fbuf, (void*)work}) {
+        auto it = std::find(S->blocks.begin(), S->blocks.end(), q);
+        if (it != S->blocks.end()) S->blocks.erase(it);
+        if (S->have_alloc) S->alloc.free(q, (void*)S->stream, S->alloc.ctx);
+        else cudaFreeAsync(q, S->stream);
+      }
     }
   }
   if (S->status != APIC_OK) return S->status;
@@ -979,6 +1104,10 @@ static int setup(apic_sim* S) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   S->push_grid = std::max(1, sms) * 4;
+  // APIC_COND_LOOP=0: the fixed, early-exiting Krylov loop instead of the
+  // conditional while node (profilers do not replay kernels of graphs that
+  // hold conditional nodes)
+  if (const char* cl = std::getenv("APIC_COND_LOOP")) S->cond_loop = std::atoi(cl) != 0;
   for (const Inst& I : S->inst) S->max_n2 = std::max(S->max_n2, I.n2);
   // the whole Poisson solve as one cooperative kernel, unless disabled or not co-residable
   const char* env = std::getenv("APIC_SOLVER");
@@ -989,13 +1118,13 @@ static int setup(apic_sim* S) {
   if (env && std::string(env) == "coop") want_coop = ni <= kCoopMaxInst;
   S->coop = want_coop ? coop_blocks<Real>(S->plan, sms) : 0;
   if (const char* nbv = std::getenv("APIC_COOP_BLOCKS")) S->coop = std::min(S->coop, std::max(1, std::atoi(nbv)));
-  if (pl.bcr.K > 0) S->coop = bcr_blocks(pl, sms);
+  if (pl.bcr.n_inst > 0) S->coop = bcr_nb;
   // Optionally (APIC_L2_PERSIST=1) keep the reduction's blocks in L2 across
   // steps: a persisting access window on the solve's graph node, with this
   // context's L2 set-aside (released with the context).  Off by default: on
   // the bench the set-aside slowed the push and injection by more than it
   // saved in the solve.
-  if (pl.bcr.K > 0 && std::getenv("APIC_L2_PERSIST") && std::string(std::getenv("APIC_L2_PERSIST")) == "1") {
+  if (pl.bcr.n_inst > 0 && std::getenv("APIC_L2_PERSIST") && std::string(std::getenv("APIC_L2_PERSIST")) == "1") {
     int maxp = 0, maxw = 0;
     cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev);
     cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, dev);
@@ -1121,8 +1250,8 @@ static bool enqueue_solver_loop(apic_sim* S, const DevPtrs& d, cudaStream_t s) {
 // One cooperative launch for the whole solve: block cyclic reduction when
 // set up, else the multigrid-preconditioned BiCGSTAB.
 template <class Real>
-static cudaError_t solve_coop(apic_sim* S, const DevPtrs& d, cudaStream_t s, int bcr_mode = 0) {
-  if (S->plan.bcr.K > 0) return launch_solve_bcr(d, S->plan, S->coop, bcr_mode, s);
+static cudaError_t solve_coop(apic_sim* S, const DevPtrs& d, cudaStream_t s, int bcr_mode = 0, int only = -1) {
+  if (S->plan.bcr.n_inst > 0) return launch_solve_bcr(d, S->plan, S->coop, bcr_mode, only, s);
   return launch_solve_coop<Real>(d, S->plan, S->coop, s);
 }
 
@@ -1131,7 +1260,7 @@ template <class Real>
 static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) {
   switch (p) {
     case 0:
-      if (S->plan.bcr.K == 0) launch_rho<Real>(d, s);  // the reduction solve forms rho itself
+      if (S->plan.bcr.n_inst == 0) launch_rho<Real>(d, s);  // the reduction solve forms rho itself
       break;
     case 1:
       if (S->coop > 0) {
@@ -1146,7 +1275,7 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
       }
       break;
     case 2:
-      if (S->plan.bcr.K == 0) {  // the reduction solve ends with them
+      if (S->plan.bcr.n_inst == 0) {  // the reduction solve ends with them
         launch_gradients<Real>(d, s);
         launch_surface(d, s);
       }
@@ -1317,7 +1446,7 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
   int vcycle = S->plan.max_tail * 10 + 1;
   int most = 0;
   for (const Inst& I : S->inst) most = std::max(most, I.max_iter);
-  if (S->plan.bcr.K > 0) {
+  if (S->plan.bcr.n_inst > 0) {
     out->kernels_per_iter = 0;   // solve, density and fields in one cooperative launch
     out->kernels_per_step = 4;   // + push, injection, bookkeeping
   } else if (S->coop > 0) {
@@ -1328,7 +1457,7 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
     out->kernels_per_step = 7 + (S->cond_loop ? 0 : most * out->kernels_per_iter);
   }
   out->timed_steps = S->timed_steps;
-  out->solver = S->plan.bcr.K > 0 ? APIC_SOLVER_BCR : (S->coop > 0 ? APIC_SOLVER_MG_COOP : APIC_SOLVER_MG_KERNELS);
+  out->solver = S->plan.bcr.n_inst > 0 ? APIC_SOLVER_BCR : (S->coop > 0 ? APIC_SOLVER_MG_COOP : APIC_SOLVER_MG_KERNELS);
   out->sorts = S->sorts;
   out->kernels_per_sort = 6;
   for (int p = 0; p < APIC_NPHASE; ++p) out->phase_ms[p] = S->phase_ms[p];
@@ -1509,7 +1638,7 @@ static int solve_impl(apic_sim* S, int inst, const double* rho, double* phi_out)
   if (rho && !S->h2d(d.rho + I.node_off, rho, (size_t)I.nodes)) return S->status;
   launch_b_from_rho(d, inst, S->stream);
   if (S->coop > 0) {
-    if (!S->ck(solve_coop<Real>(S, d, S->stream), "cooperative solve")) return S->status;
+    if (!S->ck(solve_coop<Real>(S, d, S->stream, 0, inst), "cooperative solve")) return S->status;
   } else {
     launch_bicg_init<Real>(d, S->stream);
     int it = 0;

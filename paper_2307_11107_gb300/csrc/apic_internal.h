@@ -111,6 +111,8 @@ struct StepState {
   double pad[6];
 };
 
+struct BcrInst;
+
 // Pointers handed to every kernel.
 struct DevPtrs {
   const Inst* inst;
@@ -153,11 +155,16 @@ struct DevPtrs {
   unsigned* bar;                  // grid barrier of the cooperative solver (count, generation)
   int64_t total_nodes;
   int64_t level_nodes;
-  // block cyclic reduction (single instance): factor blocks, reduced right-hand side, correction
+  // block cyclic reduction: factor blocks and tail inverses of every instance,
+  // reduced right-hand side and correction rows, per-instance tables, phase schedule
   float* bcr;
-  float* bcr_tail;                // dense inverse of the tail system [tail_n][tail_np]
   float* bcr_f;
   float* bcr_e;
+  const BcrInst* bcr_inst;        // [n_inst]
+  const int32_t* bcr_kind;        // [phases][n_inst]: kind << 8 | level of instance k's tasks in a phase (0: none)
+  const int32_t* bcr_pre;         // [phases][n_inst + 1]: prefix sums of the instances' task counts
+  const int32_t* bcr_npre;        // [n_inst + 1]: prefix sums of the instances' node chunks
+  double* bcr_part;               // [2][chunks]: |b|^2 and |r|^2 of each node chunk
 };
 
 // ---- sensitivity window (forward mode) ----
@@ -211,37 +218,71 @@ void launch_surface(const DevPtrs& d, cudaStream_t s);
 void launch_step_end(const DevPtrs& d, cudaStream_t s);
 void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s);
 
-// Block cyclic reduction (bcr.cu) of the finest-level system of a single
-// instance whose n1 is a power of two, 2^K: rows i = 1..2^K - 1 of N2
-// unknowns.  Reduction level l = 1..Lt (row stride h = 2^(l-1)) eliminates
-// the rows k = h (2q + 1), q = 0..2^(K-l) - 1, and keeps i = 2h (q + 1),
-// q = 0..2^(K-l) - 2.  Dense FP32 blocks, column-major N2 x N2 (column
-// stride Np):
-//   kept row i:       P = A_i B_{i-h}^-1,  Q = C_i B_{i+h}^-1   (forward: f_i -= P f_{i-h} + Q f_{i+h})
-//   eliminated row k: B_k^-1, G = B_k^-1 A_k, H = B_k^-1 C_k    (back: e_k = B_k^-1 f_k - G e_{k-h} - H e_{k+h})
-// The m = 2^(K-Lt) - 1 rows left after level Lt (i = 2^Lt (q + 1)) form a
-// block tridiagonal system of tail_n = m N2 unknowns whose dense inverse
-// (FP32, row-major, set up in FP64) is applied in one phase; Lt is the
-// fewest levels that bring tail_n under kBcrTailMax.
+// Block cyclic reduction (bcr.cu) of the finest-level system of every
+// instance of a batch.  Instance k has the unknown rows i = 1..M (M = n1 - 1)
+// of N = N2 unknowns each; rows beyond M carry a zero correction and are
+// neither stored nor visited, so n1 need not be a power of two (K is the
+// smallest with 2^K >= n1).  Reduction level l = 1..Lt (row stride
+// h = 2^(l-1)) eliminates the rows k = h (2q + 1) <= M and keeps
+// i = 2h (q + 1) <= M.
+//   Level 1: the x1 couplings A_i, C_i of Eq. 7 are tridiagonal in j, so only
+//   B_k^-1 is stored.  Forward: y_k = B_k^-1 f_k, then f_i -= A_i y_{i-1} +
+//   C_i y_{i+1} with the stencil's A_i, C_i.  Back: e_k = B_k^-1 (f_k - A_k
+//   e_{k-1} - C_k e_{k+1}).
+//   Level >= 2 (dense blocks):
+//     kept row i:       P = A_i B_{i-h}^-1,  Q = C_i B_{i+h}^-1   (forward: f_i -= P f_{i-h} + Q f_{i+h})
+//     eliminated row k: B_k^-1, G = B_k^-1 A_k, H = B_k^-1 C_k    (back: e_k = B_k^-1 f_k - G e_{k-h} - H e_{k+h})
+// Blocks are FP32, column-major N x N with column stride Np (16-byte aligned
+// columns); a block whose neighbour row is beyond M is zero.  The
+// tail_m = M >> Lt rows left after level Lt (i = 2^Lt (q + 1)) form a block
+// tridiagonal system of tail_n = tail_m N unknowns whose dense inverse (FP32,
+// row-major, row stride tail_np, set up in FP64) is applied in one phase, in
+// chunks of tail_rows rows; Lt is the fewest levels that bring tail_n under
+// kBcrTailMax.
 constexpr int kBcrMaxK = 13;
 constexpr int kBcrMaxN = 256;
 constexpr int kBcrTailMax = 2048;
-constexpr double kBcrMaxBytes = 256.0 * 1024 * 1024;  // FP32 blocks held on the device
-struct BcrPlan {
-  int K;                    // 0: not in use
+constexpr double kBcrMaxBytes = 24.0 * 1024 * 1024 * 1024;  // FP32 blocks of a whole batch held on the device
+constexpr int kBcrUpdRows = 4;       // level-1 kept rows per update task
+constexpr int kBcrNodeChunk = 2048;  // nodes per node task (density, residual, gradients)
+// task kinds of a phase of one instance
+constexpr int kBcrFwd1 = 1;   // y_k = B_k^-1 f_k, level-1 eliminated rows
+constexpr int kBcrUpd1 = 2;   // f_i -= A_i y_{i-1} + C_i y_{i+1}, level-1 kept rows
+constexpr int kBcrFwd = 3;    // f_i -= P f_{i-h} + Q f_{i+h}, level >= 2
+constexpr int kBcrTail = 4;   // e = T^-1 f on a chunk of tail rows
+constexpr int kBcrBack = 5;   // e_k = B_k^-1 f_k - G e_{k-h} - H e_{k+h}, level >= 2
+constexpr int kBcrBack1 = 6;  // e_k = B_k^-1 (f_k - A_k e_{k-1} - C_k e_{k+1}), level 1
+struct BcrInst {
+  int K;                    // 2^K >= n1
   int N;                    // block size N2
-  int Np;                   // column stride (N rounded up to 4 floats: 16-byte aligned columns)
-  int smem;                 // 1: a task's blocks are staged in shared memory by bulk async copies
+  int Np;                   // column stride (N rounded up to 4 floats)
   int Lt;                   // reduction levels before the dense tail (0..K-1)
+  int M;                    // unknown rows (n1 - 1)
   int tail_m;               // rows of the tail system
   int tail_n;               // its unknowns (tail_m * N)
   int tail_np;              // row stride of the tail inverse (tail_n rounded up to 4 floats)
-  int tail_rpc;             // tail rows per CTA (contiguous; set with the launch size)
-  int pad;
+  int tail_rows;            // tail-inverse rows per task
+  int smem;                 // 1: a task's blocks are staged in shared memory by bulk async copies
   int64_t blk;              // floats per block (N * Np)
-  int64_t P[kBcrMaxK], Q[kBcrMaxK];                  // first block of each kind at level l
+  int64_t base;             // first float of this instance's blocks in DevPtrs::bcr
+  int64_t tail;             // first float of its tail inverse in DevPtrs::bcr
+  int64_t foff;             // first float of its rows in bcr_f / bcr_e (M * N floats each)
+  int64_t P[kBcrMaxK], Q[kBcrMaxK];                  // block index (from base) of the first block of each kind at level l
   int64_t Binv[kBcrMaxK], G[kBcrMaxK], H[kBcrMaxK];
-  int64_t blocks;           // total blocks
+  int64_t blocks;           // blocks of this instance
+};
+// Phase schedule: instance k runs its stages Fwd1, Upd1, Fwd(2..Lt), Tail,
+// Back(Lt..2), Back1 (Lt = 0: Tail alone) in phases 0, 1, ..., one grid
+// barrier after each phase.
+struct BcrPlan {
+  int n_inst;               // 0: not in use
+  int phases;               // phases of one reduction pass
+  int smem;                 // 1: dynamic shared memory holds staged blocks
+  int prefetch;             // 1: every CTA brings its blocks into L2 at the start (they fit)
+  int dyn;                  // dynamic shared memory bytes of the solve kernel
+  int pad;
+  int64_t bytes;            // device bytes of all blocks and tail inverses
+  int64_t chunks;           // node chunks of all instances (kBcrNodeChunk nodes each)
 };
 
 // Poisson (poisson.cu): host-side launch plan of the multigrid levels.
@@ -283,9 +324,12 @@ void launch_finish_injection(const DevPtrs& d, int pop, cudaStream_t s);
 // residual and the FP32 reduction as the correction, one cooperative launch.
 constexpr int kBcrRho = 1;     // form rho, the guess and b inside the solve
 constexpr int kBcrFields = 2;  // node gradients and surface quantities after the solve
-cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& plan, int blocks, int mode, cudaStream_t s);
-int bcr_blocks(SolvePlan& plan, int sms);
-const void* bcr_kernel();  // the solve kernel (to find its graph node)  // CTAs of the launch (0: not co-residable); sets plan.bcr.smem
+// only >= 0: solve that instance alone (its b and |b|^2 partials from the caller)
+cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& plan, int blocks, int mode, int only, cudaStream_t s);
+// CTAs of the solve (0: not co-residable); sets each instance's staging flag
+// and tail chunk, and the kernel's shared memory (plan.bcr.smem, plan.bcr.dyn).
+int bcr_configure(SolvePlan& plan, BcrInst* inst, int n_inst, int sms);
+const void* bcr_kernel();  // the solve kernel (to find its graph node)
 
 // sensitivity window (tangent.cu)
 template <class Real>

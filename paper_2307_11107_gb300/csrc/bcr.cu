@@ -1,15 +1,18 @@
 // Direct FP32 solver of the Poisson problem of Eqs. 6-7 (Sec. 2) inside an
-// FP64 iterative refinement, for one instance whose grid has n1 = 2^K cells
-// in x1.
+// FP64 iterative refinement, for every instance of a batch in one
+// cooperative launch.
 //
-// The finite-difference system is block tridiagonal in x1: row i of N2
-// unknowns couples to rows i - 1 and i + 1 through the blocks A_i and C_i and
-// to itself through B_i.  Block cyclic reduction eliminates the odd rows, then
-// the odd rows of what is left, and so on, until one row remains; the blocks
-// of every level are formed once at set-up (FP64 on the host) and stored in
-// FP32.  A solve is then 2K - 1 phases of dense matrix-vector products whose
-// tasks (one row each) are spread over the CTAs, instead of the dozens of
-// line-relaxation phases per multigrid cycle.  The refinement loop
+// The finite-difference system of an instance is block tridiagonal in x1:
+// row i of N2 unknowns couples to rows i - 1 and i + 1 through the blocks A_i
+// and C_i and to itself through B_i.  Block cyclic reduction eliminates the
+// odd rows, then the odd rows of what is left, and so on; the blocks of every
+// level are formed once at set-up (FP64 on the host) and stored in FP32, and
+// the few rows left after Lt levels are solved with a dense inverse.  Rows
+// beyond n1 - 1 carry a zero correction, so any n1 works.  A solve is then a
+// fixed sequence of phases of dense matrix-vector products whose tasks (one
+// row of one instance each) are spread over the CTAs, one grid barrier per
+// phase, instead of the dozens of line-relaxation phases per multigrid cycle.
+// The refinement loop of each instance
 //   r = b - A x (FP64),  e = (FP32 reduction) r,  x += e
 // stops when |r| <= tol |b|; the FP32 reduction leaves about 1e-5 of the
 // residual, so two passes reach 1e-10.
@@ -29,6 +32,9 @@ namespace {
 constexpr int kBcrThreads = 512;
 constexpr int kBcrWarps = kBcrThreads / 32;
 constexpr int kMC = kBcrMaxN / 32;  // outputs per lane
+constexpr int kTailChunk = 16;      // tail rows per task at most (one per warp)
+constexpr int kUpdRows = kBcrUpdRows;
+constexpr int kNodeChunk = kBcrNodeChunk;
 
 // ---- bulk asynchronous copies (global -> shared, completion on an mbarrier) ----
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -125,9 +131,7 @@ __device__ __forceinline__ void task_mv(const float* const* Mt, const float* con
 }
 
 struct Ctx {
-  const BcrPlan* B;
-  const float* blk;
-  float* sbuf;      // NT staged blocks (shared memory mode)
+  float* sbuf;  // dynamic shared memory: staged blocks or a tail chunk and its right-hand side
   uint64_t* bar;
   unsigned parity;
   float* red;
@@ -136,203 +140,378 @@ struct Ctx {
 };
 
 // res = sum_t src_t v_t: the blocks are staged in shared memory by one bulk
-// copy each (when they fit), else read from global memory.  False on a copy
-// time-out (every thread).
+// copy each when the instance's blocks fit, else read from global memory.
+// False on a copy time-out (every thread).
 template <int NT>
-__device__ bool run_task(Ctx& c, const float* const* src, const float* const* vt) {
-  const int N = c.B->N, Np = c.B->Np;
-  if (c.B->smem) {
-    const unsigned bytes = (unsigned)(c.B->blk * sizeof(float));
+__device__ bool run_task(Ctx& c, const BcrInst& B, const float* const* src, const float* const* vt) {
+  if (B.smem) {
+    const unsigned bytes = (unsigned)(B.blk * sizeof(float));
     if (threadIdx.x == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_expect_tx(c.bar, bytes * NT);
 #pragma unroll
-      for (int t = 0; t < NT; ++t) bulk_g2s(c.sbuf + t * c.B->blk, src[t], bytes, c.bar);
+      for (int t = 0; t < NT; ++t) bulk_g2s(c.sbuf + t * B.blk, src[t], bytes, c.bar);
     }
     if (!mbar_wait(c.bar, c.parity, c.err)) return false;
     c.parity ^= 1u;
     const float* Ms[NT];
 #pragma unroll
-    for (int t = 0; t < NT; ++t) Ms[t] = c.sbuf + t * c.B->blk;
-    task_mv<NT, true>(Ms, vt, N, Np, c.red, c.sres);
+    for (int t = 0; t < NT; ++t) Ms[t] = c.sbuf + t * B.blk;
+    task_mv<NT, true>(Ms, vt, B.N, B.Np, c.red, c.sres);
   } else {
-    task_mv<NT, false>(src, vt, N, Np, c.red, c.sres);
+    task_mv<NT, false>(src, vt, B.N, B.Np, c.red, c.sres);
   }
   return true;
 }
 
-// mode: kBcrRho = the step's density, initial guess and right-hand side are
-// formed here (else b and its |b|^2 partials come from the caller);
-// kBcrFields = node gradients and surface quantities after the solve.
-__global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePlan pl, int mode) {
-  extern __shared__ __align__(128) float s_blocks[];
-  __shared__ double sh[40];
-  __shared__ float sv[3][kBcrMaxN];
-  __shared__ float sres[kBcrMaxN];
-  __shared__ float red[kBcrWarps * kBcrMaxN];
-  __shared__ __align__(8) uint64_t s_bar;
-  const BcrPlan& B = pl.bcr;
-  const int nb = gridDim.x;
-  const Inst& I = d.inst[0];
-  const int N = I.N2, K = B.K, M = (1 << K) - 1;
-  const long long stride = (long long)nb * blockDim.x;
-  const float* blk = d.bcr;
-  float* f = d.bcr_f;
-  float* e = d.bcr_e;
-  double* x = d.phi;
-  Ctx c{&B, blk, s_blocks, &s_bar, 0u, red, sres, d.err};
-  if (threadIdx.x == 0) {
-    mbar_init(&s_bar, 1);
-    // bring this CTA's blocks of the whole reduction (and its share of the
-    // tail inverse) into L2 while the first residual is formed
-    const unsigned bytes = (unsigned)(B.blk * sizeof(float));
-    for (int l = 1; l <= B.Lt; ++l) {
-      const int ne = 1 << (K - l), nk = ne - 1;
-      for (int q = blockIdx.x; q < nk; q += nb) {
-        prefetch_l2(blk + (B.P[l] + q) * B.blk, bytes);
-        prefetch_l2(blk + (B.Q[l] + q) * B.blk, bytes);
-      }
-      for (int q = blockIdx.x; q < ne; q += nb) {
-        prefetch_l2(blk + (B.Binv[l] + q) * B.blk, bytes);
-        prefetch_l2(blk + (B.G[l] + q) * B.blk, bytes);
-        prefetch_l2(blk + (B.H[l] + q) * B.blk, bytes);
-      }
-    }
-    const int r0 = blockIdx.x * B.tail_rpc, r1 = min(B.tail_n, r0 + B.tail_rpc);
-    if (r1 > r0)
-      prefetch_l2(d.bcr_tail + (long long)r0 * B.tail_np, (unsigned)((r1 - r0) * B.tail_np * sizeof(float)));
+// Instance of task t of a phase: pre[k] <= t < pre[k + 1] (global table).
+__device__ __forceinline__ int task_inst(const int32_t* pre, int ni, int t) {
+  int lo = 0, hi = ni - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(pre + mid) <= t) lo = mid;
+    else hi = mid - 1;
   }
-  double bn = 0.0;
-  if (mode & kBcrRho) {
-    // rho, the initial guess and b at every node; |b|^2 over the grid
-    double pb = 0.0;
-    for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes; nd += stride) {
-      const double bv = rho_node(d, I, 0, nd);
-      pb += bv * bv;
-    }
-    const double tb = block_sum_any(pb, sh);
-    if (threadIdx.x == 0) d.cred[0 * kCoopMaxBlocks + blockIdx.x] = tb;
-    if (!grid_sync(d, nb)) return;
-    bn = coop_sum(d, 0, 0, nb, sh);
-  } else {
-    // |b|^2 from the right-hand-side kernel's partials (fixed order)
-    if (threadIdx.x == 0) {
-      double s0 = 0.0;
-      for (int k = 0; k < kRedBlocks; ++k) s0 += d.red[k];
-      sh[34] = s0;
-    }
-    __syncthreads();
-    bn = sh[34];
-    __syncthreads();
+  return lo;
+}
+
+// The same search over a prefix held in shared memory.
+__device__ __forceinline__ int task_inst_s(const int* pre, int ni, int t) {
+  int lo = 0, hi = ni - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= t) lo = mid;
+    else hi = mid - 1;
   }
-  for (int it = 0;; ++it) {
-    // FP64 residual, stored as the FP32 right-hand side of the reduction
-    double pr = 0.0;
-    for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes; nd += stride) {
-      const int i = (int)(nd / N), j = (int)(nd % N);
-      if (i > 0 && i < I.n1) {
-        double r = d.b[nd] - apply_st<double, double>(d.st64, I.nodes, x, nd, i, j, I.n2, N, 1);
-        f[(long long)(i - 1) * N + j] = (float)r;
-        pr += r * r;
-      }
+  return lo;
+}
+
+// Blocks (or tail rows) read by task q of kind `kind` at level l of instance
+// B: up to three ranges (pointer, bytes); returns their count.
+__device__ int task_ranges(const DevPtrs& d, const BcrInst& B, int kind, int l, int q, const float** p,
+                           unsigned* bytes) {
+  const float* blk = d.bcr + B.base;
+  const unsigned bb = (unsigned)(B.blk * sizeof(float));
+  switch (kind) {
+    case kBcrFwd1:
+    case kBcrBack1:
+      p[0] = blk + (B.Binv[1] + q) * B.blk;
+      bytes[0] = bb;
+      return 1;
+    case kBcrFwd:
+      p[0] = blk + (B.P[l] + q) * B.blk;
+      p[1] = blk + (B.Q[l] + q) * B.blk;
+      bytes[0] = bytes[1] = bb;
+      return 2;
+    case kBcrBack:
+      p[0] = blk + (B.Binv[l] + q) * B.blk;
+      p[1] = blk + (B.G[l] + q) * B.blk;
+      p[2] = blk + (B.H[l] + q) * B.blk;
+      bytes[0] = bytes[1] = bytes[2] = bb;
+      return 3;
+    case kBcrTail: {
+      const int r0 = q * B.tail_rows, r1 = min(B.tail_n, r0 + B.tail_rows);
+      p[0] = d.bcr + B.tail + (long long)r0 * B.tail_np;
+      bytes[0] = (unsigned)((r1 - r0) * B.tail_np * sizeof(float));
+      return 1;
     }
-    const double t = block_sum_any(pr, sh);
-    if (threadIdx.x == 0) d.cred[2 * kCoopMaxBlocks + blockIdx.x] = t;
-    if (!grid_sync(d, nb)) return;
-    const double rn = coop_sum(d, 0, 2, nb, sh);
-    const bool conv = rn <= I.tol * I.tol * bn, bad = !(rn == rn);
-    if (conv || bad || it >= I.max_iter) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
-        SolverState& S = d.sol[0];
-        S.res = bn > 0.0 ? sqrt(rn / bn) : 0.0;
-        S.iters = it;
-        S.done = 1;
-        if (!conv) atomicOr(d.err, bad ? kErrNonFinite : kErrNotConverged);
-      }
-      break;
+    default: return 0;
+  }
+}
+
+// Thread 0: bring the ranges of task t of phase p into L2 (if the task exists).
+__device__ void prefetch_task(const DevPtrs& d, int p, int t) {
+  const int ni = d.n_inst;
+  const int32_t* pre = d.bcr_pre + (long long)p * (ni + 1);
+  if (t >= __ldg(pre + ni)) return;
+  const int k = task_inst(pre, ni, t);
+  const int kl = __ldg(d.bcr_kind + (long long)p * ni + k);
+  const float* rp[3];
+  unsigned rb[3];
+  const int n = task_ranges(d, d.bcr_inst[k], kl >> 8, kl & 255, t - __ldg(pre + k), rp, rb);
+  for (int r = 0; r < n; ++r) prefetch_l2(rp[r], rb[r]);
+}
+
+// Task q of kind `kind` at level l of instance k (the whole CTA).  Row r of
+// the reduced right-hand side f and of the correction e is at (r - 1) N.
+__device__ bool run_stage(const DevPtrs& d, Ctx& c, int k, int kind, int l, int q, float (*sv)[kBcrMaxN]) {
+  const Inst& I = d.inst[k];
+  const BcrInst& B = d.bcr_inst[k];
+  const int N = B.N, M = B.M;
+  float* f = d.bcr_f + B.foff;
+  float* e = d.bcr_e + B.foff;
+  double* x = d.phi + I.node_off;
+  const float* rp[3];
+  unsigned rb[3];
+  task_ranges(d, B, kind, l, q, rp, rb);
+  switch (kind) {
+    case kBcrFwd1: {  // y_k = B_k^-1 f_k, kept in e until the back substitution
+      const int kr = 2 * q + 1;
+      for (int j = threadIdx.x; j < N; j += blockDim.x) sv[0][j] = f[(long long)(kr - 1) * N + j];
+      __syncthreads();
+      const float* vt[1] = {sv[0]};
+      if (!run_task<1>(c, B, rp, vt)) return false;
+      for (int j = threadIdx.x; j < N; j += blockDim.x) e[(long long)(kr - 1) * N + j] = c.sres[j];
+      __syncthreads();
+      return true;
     }
-    // forward reduction: f_i -= P_i f_{i-h} + Q_i f_{i+h} on the kept rows
-    for (int l = 1; l <= B.Lt; ++l) {
-      const int h = 1 << (l - 1);
-      const int nk = (1 << (K - l)) - 1;
-      for (int q = blockIdx.x; q < nk; q += nb) {
-        const int i = 2 * h * (q + 1);
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-          sv[0][j] = f[(long long)(i - h - 1) * N + j];
-          sv[1][j] = f[(long long)(i + h - 1) * N + j];
+    case kBcrUpd1: {  // f_i -= A_i y_{i-1} + C_i y_{i+1} (tridiagonal in j) on kUpdRows kept rows
+      const float* st = (const float*)d.st + I.lv[0].st;
+      const long long nodes = I.nodes;
+      const int nk = M / 2, q0 = q * kUpdRows, nq = min(kUpdRows, nk - q0);
+      for (int o = threadIdx.x; o < nq * N; o += blockDim.x) {
+        const int qq = o / N, j = o - qq * N, i = 2 * (q0 + qq + 1);
+        const bool right = i + 1 <= M;
+        const long long nd = (long long)i * N + j;
+        float a = 0.0f;
+#pragma unroll
+        for (int dj = -1; dj <= 1; ++dj) {
+          const int jj = j + dj;
+          if (jj < 0 || jj >= N) continue;
+          a = fmaf(st[st_slot(-1, dj) * nodes + nd], e[(long long)(i - 2) * N + jj], a);
+          if (right) a = fmaf(st[st_slot(1, dj) * nodes + nd], e[(long long)i * N + jj], a);
         }
-        __syncthreads();
-        const float* Mt[2] = {blk + (B.P[l] + q) * B.blk, blk + (B.Q[l] + q) * B.blk};
-        const float* vt[2] = {sv[0], sv[1]};
-        if (!run_task<2>(c, Mt, vt)) return;
-        for (int j = threadIdx.x; j < N; j += blockDim.x) f[(long long)(i - 1) * N + j] -= sres[j];
-        __syncthreads();
+        f[(long long)(i - 1) * N + j] -= a;
       }
-      if (!grid_sync(d, nb)) return;
+      return true;
     }
-    // the rows left, i = 2^Lt (q + 1): e = T^-1 f with the dense inverse; each
-    // CTA owns a contiguous range of its rows (staged in shared memory by one
-    // bulk copy when the blocks are), one row per warp, lanes over the
-    // columns, fixed-order shuffle sums
-    {
+    case kBcrFwd: {  // f_i -= P f_{i-h} + Q f_{i+h}
+      const int h = 1 << (l - 1), i = 2 * h * (q + 1);
+      const bool right = i + h <= M;
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        sv[0][j] = f[(long long)(i - h - 1) * N + j];
+        sv[1][j] = right ? f[(long long)(i + h - 1) * N + j] : 0.0f;
+      }
+      __syncthreads();
+      const float* vt[2] = {sv[0], sv[1]};
+      if (!run_task<2>(c, B, rp, vt)) return false;
+      for (int j = threadIdx.x; j < N; j += blockDim.x) f[(long long)(i - 1) * N + j] -= c.sres[j];
+      __syncthreads();
+      return true;
+    }
+    case kBcrTail: {  // e = T^-1 f on rows r0..r1 of the tail: one row per warp, lanes over the columns
       const int tn = B.tail_n, tnp = B.tail_np, hs = 1 << B.Lt;
-      const int r0 = blockIdx.x * B.tail_rpc, r1 = min(tn, r0 + B.tail_rpc);
-      float* rows = s_blocks;
-      float* fs = s_blocks + (B.smem ? (long long)B.tail_rpc * tnp : 0);
-      const bool stage = B.smem && r1 > r0;
-      if (stage && threadIdx.x == 0) {
-        const unsigned bytes = (unsigned)((r1 - r0) * tnp * sizeof(float));
+      const int r0 = q * B.tail_rows, r1 = min(tn, r0 + B.tail_rows);
+      float* rows = c.sbuf;
+      float* fs = c.sbuf + (long long)B.tail_rows * tnp;
+      if (threadIdx.x == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(c.bar, bytes);
-        bulk_g2s(rows, d.bcr_tail + (long long)r0 * tnp, bytes, c.bar);
+        mbar_expect_tx(c.bar, rb[0]);
+        bulk_g2s(rows, rp[0], rb[0], c.bar);
       }
       for (int o = threadIdx.x; o < tn; o += blockDim.x) {
-        const int q = o / N, j = o - q * N;
-        fs[o] = f[(long long)(hs * (q + 1) - 1) * N + j];
+        const int qq = o / N, j = o - qq * N;
+        fs[o] = f[(long long)(hs * (qq + 1) - 1) * N + j];
       }
-      if (stage) {
-        if (!mbar_wait(c.bar, c.parity, c.err)) return;
-        c.parity ^= 1u;
-      } else {
-        __syncthreads();
-      }
+      if (!mbar_wait(c.bar, c.parity, c.err)) return false;
+      c.parity ^= 1u;
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
       for (int o = r0 + warp; o < r1; o += kBcrWarps) {
-        const float* row = stage ? rows + (long long)(o - r0) * tnp : d.bcr_tail + (long long)o * tnp;
+        const float* row = rows + (long long)(o - r0) * tnp;
         float a = 0.0f;
 #pragma unroll 4
         for (int cc = lane; cc < tn; cc += 32) a = fmaf(row[cc], fs[cc], a);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(kFull, a, off);
         if (lane == 0) {
-          const int q = o / N, j = o - q * N, i = hs * (q + 1);
+          const int qq = o / N, j = o - qq * N, i = hs * (qq + 1);
           e[(long long)(i - 1) * N + j] = a;
           x[(long long)i * N + j] += (double)a;
         }
       }
-      if (!grid_sync(d, nb)) return;
+      __syncthreads();
+      return true;
     }
-    // back substitution: e_k = B_k^-1 f_k - G_k e_{k-h} - H_k e_{k+h}; x += e
-    for (int l = B.Lt; l >= 1; --l) {
-      const int h = 1 << (l - 1);
-      const int ne = 1 << (K - l);
-      for (int q = blockIdx.x; q < ne; q += nb) {
-        const int k = h * (2 * q + 1);
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-          sv[0][j] = f[(long long)(k - 1) * N + j];
-          sv[1][j] = k - h >= 1 ? -e[(long long)(k - h - 1) * N + j] : 0.0f;
-          sv[2][j] = k + h <= M ? -e[(long long)(k + h - 1) * N + j] : 0.0f;
+    case kBcrBack: {  // e_k = B_k^-1 f_k - G e_{k-h} - H e_{k+h}; x += e
+      const int h = 1 << (l - 1), kr = h * (2 * q + 1);
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        sv[0][j] = f[(long long)(kr - 1) * N + j];
+        sv[1][j] = kr - h >= 1 ? -e[(long long)(kr - h - 1) * N + j] : 0.0f;
+        sv[2][j] = kr + h <= M ? -e[(long long)(kr + h - 1) * N + j] : 0.0f;
+      }
+      __syncthreads();
+      const float* vt[3] = {sv[0], sv[1], sv[2]};
+      if (!run_task<3>(c, B, rp, vt)) return false;
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        e[(long long)(kr - 1) * N + j] = c.sres[j];
+        x[(long long)kr * N + j] += (double)c.sres[j];
+      }
+      __syncthreads();
+      return true;
+    }
+    case kBcrBack1: {  // e_k = B_k^-1 (f_k - A_k e_{k-1} - C_k e_{k+1}); x += e
+      const int kr = 2 * q + 1;
+      const float* st = (const float*)d.st + I.lv[0].st;
+      const long long nodes = I.nodes;
+      const bool left = kr - 1 >= 1, right = kr + 1 <= M;
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const long long nd = (long long)kr * N + j;
+        float a = f[(long long)(kr - 1) * N + j];
+#pragma unroll
+        for (int dj = -1; dj <= 1; ++dj) {
+          const int jj = j + dj;
+          if (jj < 0 || jj >= N) continue;
+          if (left) a = fmaf(-st[st_slot(-1, dj) * nodes + nd], e[(long long)(kr - 2) * N + jj], a);
+          if (right) a = fmaf(-st[st_slot(1, dj) * nodes + nd], e[(long long)kr * N + jj], a);
         }
-        __syncthreads();
-        const float* Mt[3] = {blk + (B.Binv[l] + q) * B.blk, blk + (B.G[l] + q) * B.blk,
-                              blk + (B.H[l] + q) * B.blk};
-        const float* vt[3] = {sv[0], sv[1], sv[2]};
-        if (!run_task<3>(c, Mt, vt)) return;
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-          e[(long long)(k - 1) * N + j] = sres[j];
-          x[(long long)k * N + j] += (double)sres[j];
+        sv[0][j] = a;
+      }
+      __syncthreads();
+      const float* vt[1] = {sv[0]};
+      if (!run_task<1>(c, B, rp, vt)) return false;
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        e[(long long)(kr - 1) * N + j] = c.sres[j];
+        x[(long long)kr * N + j] += (double)c.sres[j];
+      }
+      __syncthreads();
+      return true;
+    }
+  }
+  return true;
+}
+
+// Fixed-order sum of part[npre[k] .. npre[k+1]) for every instance k with
+// sel[k] (all when sel is null), one warp per instance; out[k] in shared
+// memory, the same in every CTA.
+__device__ void inst_sums(const double* part, const int* npre, int ni, const int* sel, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = warp; k < ni; k += kBcrWarps) {
+    if (sel && !sel[k]) continue;
+    double v = 0.0;
+    for (int c = npre[k] + lane; c < npre[k + 1]; c += 32) v += part[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if (lane == 0) out[k] = v;
+  }
+  __syncthreads();
+}
+
+// Node tasks: chunk c of instance k holds its nodes c kNodeChunk ..
+// (c + 1) kNodeChunk - 1; the chunks of all instances are spread over the
+// CTAs.  body(k, I, nd) returns the node's contribution to the chunk's sum,
+// which goes to part[npre[k] + c] (when part is not null): the sums do not
+// depend on the CTA that runs a chunk nor on the other instances of a batch.
+template <class F>
+__device__ void node_tasks(const DevPtrs& d, const int* npre, const int* sel, double* part, double* sh, F body) {
+  const int ni = d.n_inst, nb = gridDim.x;
+  const int total = npre[ni];
+  for (int t = blockIdx.x; t < total; t += nb) {
+    const int k = task_inst_s(npre, ni, t);
+    if (sel && !sel[k]) continue;
+    const Inst& I = d.inst[k];
+    const long long nd0 = (long long)(t - npre[k]) * kNodeChunk;
+    double acc = 0.0;
+#pragma unroll
+    for (int u = 0; u < kNodeChunk / kBcrThreads; ++u) {
+      const long long nd = nd0 + u * kBcrThreads + threadIdx.x;
+      if (nd < I.nodes) acc += body(k, I, nd);
+    }
+    if (part) {
+      const double tot = block_sum_any(acc, sh);
+      if (threadIdx.x == 0) part[t] = tot;
+    }
+  }
+}
+
+// mode: kBcrRho = the step's density, initial guess and right-hand side are
+// formed here (else b and its |b|^2 partials come from the caller);
+// kBcrFields = node gradients and surface quantities after the solve.
+// only >= 0: that instance alone is solved (the others keep their phi).  An
+// instance computes the same values alone or in a batch.
+__global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan pl, int mode, int only) {
+  extern __shared__ __align__(128) float s_dyn[];
+  __shared__ double sh[40];
+  __shared__ float sv[3][kBcrMaxN];
+  __shared__ float sres[kBcrMaxN];
+  __shared__ float red[kBcrWarps * kBcrMaxN];
+  __shared__ double s_bn[kCoopMaxInst];
+  __shared__ double s_rn[kCoopMaxInst];
+  __shared__ int s_act[kCoopMaxInst];
+  __shared__ int s_npre[kCoopMaxInst + 1];
+  __shared__ __align__(8) uint64_t s_bar;
+  const int nb = gridDim.x, ni = d.n_inst;
+  Ctx c{s_dyn, &s_bar, 0u, red, sres, d.err};
+  double* part_b = d.bcr_part;              // |b|^2 per node chunk
+  double* part_r = d.bcr_part + pl.chunks;  // |r|^2 per node chunk
+  for (int k = threadIdx.x; k <= ni; k += blockDim.x) s_npre[k] = d.bcr_npre[k];
+  for (int k = threadIdx.x; k < ni; k += blockDim.x) s_act[k] = only < 0 || k == only;
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    // the whole reduction fits in L2: bring this CTA's blocks of every phase
+    // there while the density and the first residual are formed
+    if (pl.prefetch)
+      for (int p = 0; p < pl.phases; ++p) {
+        const int total = __ldg(d.bcr_pre + (long long)p * (ni + 1) + ni);
+        for (int t = blockIdx.x; t < total; t += nb) prefetch_task(d, p, t);
+      }
+  }
+  __syncthreads();
+  if (mode & kBcrRho) {
+    // rho, the initial guess and b at every node; |b|^2 per instance
+    node_tasks(d, s_npre, nullptr, part_b, sh, [&](int k, const Inst& I, long long nd) {
+      const double bv = rho_node(d, I, k, nd);
+      return bv * bv;
+    });
+    if (!grid_sync(d, nb)) return;
+    inst_sums(part_b, s_npre, ni, nullptr, s_bn);
+  } else {
+    // |b|^2 from the right-hand-side kernel's partials (fixed order)
+    for (int k = threadIdx.x; k < ni; k += blockDim.x) {
+      const double* pr = d.red + (long long)k * kNRed * kRedBlocks;
+      double s0 = 0.0;
+      for (int r = 0; r < kRedBlocks; ++r) s0 += pr[r];
+      s_bn[k] = s0;
+    }
+    __syncthreads();
+  }
+  for (int it = 0;; ++it) {
+    // FP64 residual of every instance still iterating, stored as the FP32
+    // right-hand side of its reduction
+    node_tasks(d, s_npre, s_act, part_r, sh, [&](int k, const Inst& I, long long nd) {
+      const int N = I.N2;
+      const int i = (int)(nd / N), j = (int)(nd % N);
+      double rr = 0.0;
+      if (i > 0 && i < I.n1) {
+        const double r = d.b[I.node_off + nd] - apply_st<double, double>(d.st64 + (long long)kSt * I.node_off, I.nodes,
+                                                                         d.phi + I.node_off, nd, i, j, I.n2, N, 1);
+        d.bcr_f[d.bcr_inst[k].foff + (long long)(i - 1) * N + j] = (float)r;
+        rr = r * r;
+      }
+      return rr;
+    });
+    if (!grid_sync(d, nb)) return;
+    inst_sums(part_r, s_npre, ni, s_act, s_rn);
+    int more = 0;
+    for (int k = threadIdx.x; k < ni; k += blockDim.x) {
+      if (!s_act[k]) continue;
+      const Inst& I = d.inst[k];
+      const double rn = s_rn[k], bn = s_bn[k];
+      const bool conv = rn <= I.tol * I.tol * bn, bad = !(rn == rn);
+      if (conv || bad || it >= I.max_iter) {
+        if (blockIdx.x == 0) {
+          SolverState& S = d.sol[k];
+          S.res = bn > 0.0 ? sqrt(rn / bn) : 0.0;
+          S.iters = it;
+          S.done = 1;
+          if (!conv) atomicOr(d.err, bad ? kErrNonFinite : kErrNotConverged);
         }
-        __syncthreads();
+        s_act[k] = 0;
+      } else {
+        more = 1;
+      }
+    }
+    if (!__syncthreads_or(more)) break;
+    // the reduction passes: phase p runs the p-th stage of every instance
+    for (int p = 0; p < pl.phases; ++p) {
+      const int32_t* pre = d.bcr_pre + (long long)p * (ni + 1);
+      const int32_t* kind = d.bcr_kind + (long long)p * ni;
+      const int total = __ldg(pre + ni);
+      for (int t = blockIdx.x; t < total; t += nb) {
+        const int k = task_inst(pre, ni, t);
+        if (!s_act[k]) continue;
+        if (!pl.prefetch && threadIdx.x == 0) prefetch_task(d, p, t + nb);  // this CTA's next task
+        const int kl = __ldg(kind + k);
+        if (!run_stage(d, c, k, kl >> 8, kl & 255, t - __ldg(pre + k), sv)) return;
       }
       if (!grid_sync(d, nb)) return;
     }
@@ -340,53 +519,73 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, SolvePl
   }
   if (mode & kBcrFields) {
     // phi is final everywhere (the last pass ended at a grid barrier)
-    for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes; nd += stride)
+    node_tasks(d, s_npre, nullptr, nullptr, sh, [&](int k, const Inst& I, long long nd) {
+      (void)k;
       grad_node<float, float2>(d, I, nd);
-    if (blockIdx.x == nb - 1) surface_block(d, 0, sh);
+      return 0.0;
+    });
+    for (int k = nb - 1 - (int)blockIdx.x; k < ni; k += nb) surface_block(d, k, sh);
   }
 }
 
-constexpr int kStaticSmem = 40 * 8 + 3 * kBcrMaxN * 4 + kBcrMaxN * 4 + kBcrWarps * kBcrMaxN * 4 + 64;
+constexpr int kStaticSmem =
+    40 * 8 + 3 * kBcrMaxN * 4 + kBcrMaxN * 4 + kBcrWarps * kBcrMaxN * 4 + kCoopMaxInst * 24 + 4 + 64;
 
 }  // namespace
 
-// Dynamic shared memory: the staged blocks of one task (when they fit) or at
-// least the tail right-hand side.
-static long long dyn_bytes(const BcrPlan& b) {
-  long long tail = (long long)b.tail_np * (long long)sizeof(float);  // right-hand side
-  if (b.smem) tail += (long long)b.tail_rpc * b.tail_np * (long long)sizeof(float);  // + the CTA's rows
-  const long long staged = b.smem ? 3ll * b.blk * (long long)sizeof(float) : 0;
-  return staged > tail ? staged : tail;
-}
-
 const void* bcr_kernel() { return (const void*)k_solve_bcr; }
 
-int bcr_blocks(SolvePlan& pl, int sms) {
+int bcr_configure(SolvePlan& pl, BcrInst* bi, int ni, int sms) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int nb = sms < kCoopMaxBlocks ? sms : kCoopMaxBlocks;
-  pl.bcr.tail_rpc = (pl.bcr.tail_n + nb - 1) / nb;
-  const long long staged = 3ll * pl.bcr.blk * (long long)sizeof(float);
-  const long long tail = (long long)(pl.bcr.tail_rpc + 1) * pl.bcr.tail_np * (long long)sizeof(float);
-  pl.bcr.smem = (staged > tail ? staged : tail) + kStaticSmem <= optin ? 1 : 0;
-  if (const char* e = std::getenv("APIC_BCR_STAGE")) pl.bcr.smem = pl.bcr.smem && std::atoi(e) != 0;
-  const int dyn = (int)dyn_bytes(pl.bcr);
-  if (dyn + kStaticSmem > optin) return 0;
-  if (cudaFuncSetAttribute(k_solve_bcr, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess) return 0;
+  const long long budget = (long long)optin - kStaticSmem;
+  // tail chunks: about one per CTA when the tails are few, else one row per warp
+  long long tail_total = 0;
+  for (int k = 0; k < ni; ++k) tail_total += bi[k].tail_n;
+  int rows = (int)((tail_total + nb - 1) / nb);
+  rows = rows < 1 ? 1 : (rows > kTailChunk ? kTailChunk : rows);
+  bool stage_ok = true;
+  if (const char* e = std::getenv("APIC_BCR_STAGE")) stage_ok = std::atoi(e) != 0;
+  long long dyn = 0;
+  int any = 0;
+  for (int k = 0; k < ni; ++k) {
+    BcrInst& B = bi[k];
+    B.tail_rows = rows;
+    while (B.tail_rows > 1 && (long long)(B.tail_rows + 1) * B.tail_np * 4 > budget) --B.tail_rows;
+    const long long tail = (long long)(B.tail_rows + 1) * B.tail_np * 4;  // rows + right-hand side
+    if (tail > budget) return 0;
+    dyn = tail > dyn ? tail : dyn;
+    const long long staged = 3ll * B.blk * (long long)sizeof(float);
+    B.smem = stage_ok && staged <= budget ? 1 : 0;
+    if (B.smem) {
+      any = 1;
+      dyn = staged > dyn ? staged : dyn;
+    }
+  }
+  pl.bcr.smem = any;
+  pl.bcr.dyn = (int)dyn;
+  if (cudaFuncSetAttribute(k_solve_bcr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_bcr, kBcrThreads, dyn) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_bcr, kBcrThreads, (size_t)dyn) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   if (per_sm < 1) return 0;
   return nb;
 }
 
-cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& pl, int blocks, int mode, cudaStream_t s) {
+cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& pl, int blocks, int mode, int only, cudaStream_t s) {
   DevPtrs dd = d;
-  SolvePlan pp = pl;
-  int mm = mode;
-  void* args[] = {&dd, &pp, &mm};
-  const size_t dyn = (size_t)dyn_bytes(pl.bcr);
-  return cudaLaunchCooperativeKernel((const void*)k_solve_bcr, dim3(blocks), dim3(kBcrThreads), args, dyn, s);
+  BcrPlan pp = pl.bcr;
+  int mm = mode, oo = only;
+  void* args[] = {&dd, &pp, &mm, &oo};
+  return cudaLaunchCooperativeKernel((const void*)k_solve_bcr, dim3(blocks), dim3(kBcrThreads), args,
+                                     (size_t)pl.bcr.dyn, s);
 }
 
 }  // namespace apic

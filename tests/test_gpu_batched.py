@@ -18,8 +18,13 @@ def _instances(prec):
     ]
 
 
-def _run(apic, cfgs, steps):
+_SOLVER = {"bcr": "FP32 block cyclic reduction", "mg": "multigrid BiCGSTAB, per-phase kernels"}
+
+
+def _run(apic, cfgs, steps, solver=None):
     s = apic.Sim(cfgs)
+    if solver is not None:
+        assert s.stats()["solver"].startswith(_SOLVER[solver])
     for k, c in enumerate(cfgs):
         for sp in range(len(c["species"])):
             s.load_volume(sp, c["species"][sp]["n_init"], instance=k)
@@ -32,19 +37,22 @@ def _run(apic, cfgs, steps):
     return out
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_batch_equals_solo(prec, monkeypatch):
-    """Same solver path (per-phase multigrid kernels) for the batch and each
-    instance alone: the results agree bit for bit."""
+@pytest.mark.parametrize("prec,solver", [("fp64", "mg"), ("fp32", "bcr"), ("fp32", "mg")])
+def test_batch_equals_solo(prec, solver, monkeypatch):
+    """Same solver path for the batch and each instance alone (the block
+    cyclic reduction of every instance in one launch, or the per-phase
+    multigrid kernels): the results agree bit for bit."""
     import paper_2307_11107_gb300 as apic
     apic.build()
     cfgs = _instances(prec)
-    batched = _run(apic, cfgs, 6)
-    monkeypatch.setenv("APIC_SOLVER", "kernels")
-    monkeypatch.setenv("APIC_PRECOND", "mg")
+    if solver == "mg":
+        monkeypatch.setenv("APIC_PRECOND", "mg")
+    batched = _run(apic, cfgs, 6, solver)
+    if solver == "mg":
+        monkeypatch.setenv("APIC_SOLVER", "kernels")
     for k, c in enumerate(cfgs):
         (rb, pb, qb, tb), = [batched[k]]
-        (rs, ps, qs, ts), = _run(apic, [c], 6)
+        (rs, ps, qs, ts), = _run(apic, [c], 6, solver)
         assert np.array_equal(rb, rs)
         assert np.array_equal(pb, ps)
         for a, b in zip(qb, qs):
@@ -54,6 +62,31 @@ def test_batch_equals_solo(prec, monkeypatch):
             assert tb["counts"][sp] == ts["counts"][sp]
         assert np.allclose(tb["bins"], ts["bins"], rtol=1e-12, atol=1e-300)
         assert np.allclose(tb["history"], ts["history"], rtol=1e-12, atol=1e-12)
+
+
+def test_batched_reduction_poisson_matches_banded_lu():
+    """Every instance of an uneven FP32 batch (different alpha and grid, n1
+    a power of two or not) solved by the batched block cyclic reduction
+    against the oracle's banded LU; solving one instance leaves the others'
+    potential alone."""
+    import oracle
+    import paper_2307_11107_gb300 as apic
+    from tests.inputs import random_rho
+    apic.build()
+    grids = [(64, 32, 0.1), (96, 48, 0.2), (160, 80, -0.24), (256, 128, 0.15)]
+    cfgs = [workload(n1=a, n2=b, alpha=al, x1_out=-0.05, n_init=1000, precision="fp32", poisson_tol=1e-12,
+                     poisson_max_iter=60, instance=k) for k, (a, b, al) in enumerate(grids)]
+    s = apic.Sim(cfgs)
+    assert s.stats()["solver"].startswith(_SOLVER["bcr"])
+    before = [s.field("phi", k) for k in range(len(cfgs))]
+    for k, c in enumerate(cfgs):
+        rho = random_rho(c["n1"], c["n2"], seed=40 + k, scale=0.3)
+        ref = oracle.Sim(c).solve(rho)
+        got = s.solve_poisson(rho, instance=k)
+        assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-9
+    for k in range(len(cfgs)):
+        assert np.array_equal(s.field("phi", k), before[k])
+    s.close()
 
 
 def test_autotune_keeps_a_candidate_and_stepping_stays_valid():

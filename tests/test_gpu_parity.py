@@ -42,14 +42,18 @@ def test_poisson_fp64_matches_banded_lu(apic, alpha, grid):
     assert rel(s.solve_poisson(rho), o.solve(rho)) < 1e-10
 
 
-@pytest.mark.parametrize("alpha", [0.15, 0.225])
-def test_poisson_fp32_refined_matches_banded_lu(apic, alpha):
-    """FP32 multigrid inside the FP64 residual loop reaches the FP64 solution."""
-    n1, n2 = 256, 128
+@pytest.mark.parametrize("alpha,grid", [(0.15, (256, 128)), (0.225, (256, 128)), (0.15, (96, 48)),
+                                        (0.225, (288, 144)), (-0.24, (160, 80))])
+def test_poisson_fp32_refined_matches_banded_lu(apic, alpha, grid):
+    """FP32 block cyclic reduction inside the FP64 residual loop reaches the
+    FP64 solution, for n1 a power of two and not (rows beyond n1 - 1 padded
+    with a zero correction)."""
+    n1, n2 = grid
     cfg = workload(n1=n1, n2=n2, alpha=alpha, x1_out=-0.05, n_init=1000, precision="fp32",
                    poisson_tol=1e-12, poisson_max_iter=60)
-    rho = random_rho(n1, n2, seed=3, scale=0.3)
+    rho = random_rho(n1, n2, seed=n1 + 3, scale=0.3)
     s, o = apic.Sim(cfg), oracle.Sim(cfg)
+    assert s.stats()["solver"].startswith("FP32 block cyclic reduction")
     assert rel(s.solve_poisson(rho), o.solve(rho)) < 1e-9
 
 
