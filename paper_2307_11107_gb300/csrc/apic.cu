@@ -837,7 +837,7 @@ static int setup(apic_sim* S) {
   // instance with a field, N2 <= kBcrMaxN, the blocks of the batch within the
   // memory budget (APIC_PRECOND=mg keeps multigrid).
   std::vector<BcrInst> bcr_in;
-  std::vector<int32_t> bcr_kind, bcr_pre, bcr_npre;
+  std::vector<int32_t> bcr_kind, bcr_pre, bcr_npre, bcr_tpre;
   long long bcr_rows = 0;  // floats of bcr_f (and of bcr_e)
   int bcr_nb = 0;          // CTAs of the reduction solve
   {
@@ -873,6 +873,8 @@ static int setup(apic_sim* S) {
       int dev = 0, sms = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      pl.bcr.bytes = (int64_t)(4 * off);
+      pl.bcr.prefetch = bytes <= 112.0 * 1024 * 1024 ? 1 : 0;  // the whole reduction fits in L2
       want = (bcr_nb = bcr_configure(pl, bcr_in.data(), ni, sms)) > 0;  // else not co-residable: multigrid
     }
     if (want) {
@@ -906,14 +908,19 @@ static int setup(apic_sim* S) {
           }
           bcr_pre[(size_t)p * (ni + 1) + k + 1] = bcr_pre[(size_t)p * (ni + 1) + k] + cnt;
         }
+      // node phases: partial sums over kBcrSub-node ranges of each instance
+      // (the same alone or in a batch), task_sub ranges per task, about two
+      // tasks per CTA or more
       bcr_npre.assign(ni + 1, 0);
       for (int k = 0; k < ni; ++k)
-        bcr_npre[k + 1] = bcr_npre[k] + (int)((S->inst[k].nodes + kBcrNodeChunk - 1) / kBcrNodeChunk);
+        bcr_npre[k + 1] = bcr_npre[k] + (int)((S->inst[k].nodes + kBcrSub - 1) / kBcrSub);
       pl.bcr.chunks = bcr_npre[ni];
+      pl.bcr.task_sub = (int)std::max<long long>(1, std::min<long long>(kBcrMaxTaskSub, pl.bcr.chunks / (2ll * bcr_nb)));
+      bcr_tpre.assign(ni + 1, 0);
+      for (int k = 0; k < ni; ++k)
+        bcr_tpre[k + 1] = bcr_tpre[k] + (bcr_npre[k + 1] - bcr_npre[k] + pl.bcr.task_sub - 1) / pl.bcr.task_sub;
       pl.bcr.n_inst = ni;
       pl.bcr.phases = phases;
-      pl.bcr.bytes = (int64_t)(4 * off);
-      pl.bcr.prefetch = bytes <= 112.0 * 1024 * 1024 ? 1 : 0;  // the whole reduction fits in L2
     } else {
       pl.bcr.n_inst = 0;
     }
@@ -986,12 +993,14 @@ static int setup(apic_sim* S) {
     d.bcr_kind = (const int32_t*)A(sizeof(int32_t) * bcr_kind.size());
     d.bcr_pre = (const int32_t*)A(sizeof(int32_t) * bcr_pre.size());
     d.bcr_npre = (const int32_t*)A(sizeof(int32_t) * bcr_npre.size());
+    d.bcr_tpre = (const int32_t*)A(sizeof(int32_t) * bcr_tpre.size());
     d.bcr_part = (double*)A(sizeof(double) * 2 * (size_t)pl.bcr.chunks);
     if (S->status != APIC_OK) return S->status;
     S->h2d((BcrInst*)d.bcr_inst, bcr_in.data(), bcr_in.size());
     S->h2d((int32_t*)d.bcr_kind, bcr_kind.data(), bcr_kind.size());
     S->h2d((int32_t*)d.bcr_pre, bcr_pre.data(), bcr_pre.size());
     S->h2d((int32_t*)d.bcr_npre, bcr_npre.data(), bcr_npre.size());
+    S->h2d((int32_t*)d.bcr_tpre, bcr_tpre.data(), bcr_tpre.size());
     if (!S->sync()) return S->status;
     std::vector<float> blocks;
     std::vector<double> T, aug;

@@ -163,8 +163,9 @@ struct DevPtrs {
   const BcrInst* bcr_inst;        // [n_inst]
   const int32_t* bcr_kind;        // [phases][n_inst]: kind << 8 | level of instance k's tasks in a phase (0: none)
   const int32_t* bcr_pre;         // [phases][n_inst + 1]: prefix sums of the instances' task counts
-  const int32_t* bcr_npre;        // [n_inst + 1]: prefix sums of the instances' node chunks
-  double* bcr_part;               // [2][chunks]: |b|^2 and |r|^2 of each node chunk
+  const int32_t* bcr_npre;        // [n_inst + 1]: prefix sums of the instances' partial-sum ranges (kBcrSub nodes)
+  const int32_t* bcr_tpre;        // [n_inst + 1]: prefix sums of the instances' node tasks
+  double* bcr_part;               // [2][chunks]: |b|^2 and |r|^2 of each range
 };
 
 // ---- sensitivity window (forward mode) ----
@@ -244,7 +245,8 @@ constexpr int kBcrMaxN = 256;
 constexpr int kBcrTailMax = 2048;
 constexpr double kBcrMaxBytes = 24.0 * 1024 * 1024 * 1024;  // FP32 blocks of a whole batch held on the device
 constexpr int kBcrUpdRows = 4;       // level-1 kept rows per update task
-constexpr int kBcrNodeChunk = 2048;  // nodes per node task (density, residual, gradients)
+constexpr int kBcrSub = 256;         // nodes per partial sum of the node phases (density, residual)
+constexpr int kBcrMaxTaskSub = 8;    // partial-sum ranges per node task at most
 // task kinds of a phase of one instance
 constexpr int kBcrFwd1 = 1;   // y_k = B_k^-1 f_k, level-1 eliminated rows
 constexpr int kBcrUpd1 = 2;   // f_i -= A_i y_{i-1} + C_i y_{i+1}, level-1 kept rows
@@ -282,7 +284,9 @@ struct BcrPlan {
   int dyn;                  // dynamic shared memory bytes of the solve kernel
   int pad;
   int64_t bytes;            // device bytes of all blocks and tail inverses
-  int64_t chunks;           // node chunks of all instances (kBcrNodeChunk nodes each)
+  int64_t chunks;           // partial-sum ranges of all instances (kBcrSub nodes each)
+  int task_sub;             // partial-sum ranges per node task (1..kBcrMaxTaskSub)
+  int pad2;
 };
 
 // Poisson (poisson.cu): host-side launch plan of the multigrid levels.

@@ -34,7 +34,7 @@ constexpr int kBcrWarps = kBcrThreads / 32;
 constexpr int kMC = kBcrMaxN / 32;  // outputs per lane
 constexpr int kTailChunk = 16;      // tail rows per task at most (one per warp)
 constexpr int kUpdRows = kBcrUpdRows;
-constexpr int kNodeChunk = kBcrNodeChunk;
+static_assert(kBcrThreads == 2 * kBcrSub, "node tasks cover two partial-sum ranges per pass");
 
 // ---- bulk asynchronous copies (global -> shared, completion on an mbarrier) ----
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -99,22 +99,37 @@ __device__ bool mbar_wait(uint64_t* bar, unsigned parity, int32_t* err) {
 template <int NT, bool kShared>
 __device__ __forceinline__ void task_mv(const float* const* Mt, const float* const* vt, int N, int Np, float* red,
                                         float* res) {
+  // U columns per warp and block are loaded before their products, so that
+  // U * NT * kMC loads per lane are in flight when the blocks stream from
+  // global memory
+  constexpr int U = kShared ? 2 : (NT == 1 ? 8 : (NT == 2 ? 4 : 2));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float acc[kMC];
 #pragma unroll
   for (int m = 0; m < kMC; ++m) acc[m] = 0.0f;
-#pragma unroll 2
-  for (int c = warp; c < N; c += kBcrWarps) {
+  for (int c0 = warp; c0 < N; c0 += U * kBcrWarps) {
+    float v[U][NT][kMC], xs[U][NT];
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const float* col = Mt[t] + (long long)c * Np;
-      const float x = vt[t][c];
+    for (int u = 0; u < U; ++u) {
+      const int c = c0 + u * kBcrWarps;
+      const bool ok = c < N;
 #pragma unroll
-      for (int m = 0; m < kMC; ++m) {
-        const int j = lane + 32 * m;
-        if (j < N) acc[m] = fmaf(kShared ? col[j] : __ldg(col + j), x, acc[m]);
+      for (int t = 0; t < NT; ++t) {
+        const float* col = Mt[t] + (long long)(ok ? c : 0) * Np;
+        xs[u][t] = ok ? vt[t][c] : 0.0f;
+#pragma unroll
+        for (int m = 0; m < kMC; ++m) {
+          const int j = lane + 32 * m;
+          v[u][t][m] = ok && j < N ? (kShared ? col[j] : __ldg(col + j)) : 0.0f;
+        }
       }
     }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int m = 0; m < kMC; ++m) acc[m] = fmaf(v[u][t][m], xs[u][t], acc[m]);
   }
 #pragma unroll
   for (int m = 0; m < kMC; ++m) {
@@ -229,6 +244,17 @@ __device__ void prefetch_task(const DevPtrs& d, int p, int t) {
   const float* rp[3];
   unsigned rb[3];
   const int n = task_ranges(d, d.bcr_inst[k], kl >> 8, kl & 255, t - __ldg(pre + k), rp, rb);
+  for (int r = 0; r < n; ++r) prefetch_l2(rp[r], rb[r]);
+}
+
+// The same from the phase's tables in shared memory.
+__device__ void prefetch_task_s(const DevPtrs& d, const int* pre, const int* kind, int t) {
+  const int ni = d.n_inst;
+  if (t >= pre[ni]) return;
+  const int k = task_inst_s(pre, ni, t);
+  const float* rp[3];
+  unsigned rb[3];
+  const int n = task_ranges(d, d.bcr_inst[k], kind[k] >> 8, kind[k] & 255, t - pre[k], rp, rb);
   for (int r = 0; r < n; ++r) prefetch_l2(rp[r], rb[r]);
 }
 
@@ -386,30 +412,51 @@ __device__ void inst_sums(const double* part, const int* npre, int ni, const int
   __syncthreads();
 }
 
-// Node tasks: chunk c of instance k holds its nodes c kNodeChunk ..
-// (c + 1) kNodeChunk - 1; the chunks of all instances are spread over the
-// CTAs.  body(k, I, nd) returns the node's contribution to the chunk's sum,
-// which goes to part[npre[k] + c] (when part is not null): the sums do not
-// depend on the CTA that runs a chunk nor on the other instances of a batch.
+// Node tasks over the ranges of kBcrSub nodes of every instance (range c of
+// instance k: nodes c kBcrSub .. (c + 1) kBcrSub - 1).  A task covers tsub
+// consecutive ranges of one instance, two per pass of the CTA; the tasks of
+// all instances are spread over the CTAs.  body(k, I, nd) returns the node's
+// contribution to its range's sum, which goes to part[npre[k] + c] (when part
+// is not null) as a warp-shuffle tree per warp and the warps in order: the
+// sums do not depend on the task size, the CTA or the other instances of a
+// batch.  ws: kBcrMaxTaskSub / 2 * kBcrWarps doubles of shared memory.
 template <class F>
-__device__ void node_tasks(const DevPtrs& d, const int* npre, const int* sel, double* part, double* sh, F body) {
+__device__ void node_tasks(const DevPtrs& d, const int* npre, const int* tpre, int tsub, const int* sel, double* part,
+                           double* ws, F body) {
+  constexpr int kPairs = kBcrMaxTaskSub / 2;
   const int ni = d.n_inst, nb = gridDim.x;
-  const int total = npre[ni];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int half = threadIdx.x / kBcrSub, r = threadIdx.x % kBcrSub;
+  const int total = tpre[ni];
   for (int t = blockIdx.x; t < total; t += nb) {
-    const int k = task_inst_s(npre, ni, t);
+    const int k = task_inst_s(tpre, ni, t);
     if (sel && !sel[k]) continue;
     const Inst& I = d.inst[k];
-    const long long nd0 = (long long)(t - npre[k]) * kNodeChunk;
-    double acc = 0.0;
+    const int s0 = (t - tpre[k]) * tsub, s1 = min(npre[k + 1] - npre[k], s0 + tsub);
+    double v[kPairs];
 #pragma unroll
-    for (int u = 0; u < kNodeChunk / kBcrThreads; ++u) {
-      const long long nd = nd0 + u * kBcrThreads + threadIdx.x;
-      if (nd < I.nodes) acc += body(k, I, nd);
+    for (int u = 0; u < kPairs; ++u) {
+      const int sc = s0 + 2 * u + half;
+      const long long nd = (long long)sc * kBcrSub + r;
+      v[u] = sc < s1 && nd < I.nodes ? body(k, I, nd) : 0.0;
     }
-    if (part) {
-      const double tot = block_sum_any(acc, sh);
-      if (threadIdx.x == 0) part[t] = tot;
+    if (!part) continue;
+#pragma unroll
+    for (int u = 0; u < kPairs; ++u) {
+      if (s0 + 2 * u >= s1) break;
+      double x = v[u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+      if (lane == 0) ws[u * kBcrWarps + warp] = x;
     }
+    __syncthreads();
+    if (threadIdx.x < s1 - s0) {
+      const int i = threadIdx.x, u = i >> 1, w0 = (i & 1) * (kBcrWarps / 2);
+      double sum = 0.0;
+      for (int w = w0; w < w0 + kBcrWarps / 2; ++w) sum += ws[u * kBcrWarps + w];
+      part[npre[k] + s0 + i] = sum;
+    }
+    __syncthreads();
   }
 }
 
@@ -428,12 +475,20 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   __shared__ double s_rn[kCoopMaxInst];
   __shared__ int s_act[kCoopMaxInst];
   __shared__ int s_npre[kCoopMaxInst + 1];
+  __shared__ int s_tpre[kCoopMaxInst + 1];
+  __shared__ double s_ws[kBcrMaxTaskSub / 2 * kBcrWarps];
+  __shared__ int s_pre[kCoopMaxInst + 1];
+  __shared__ int s_kind[kCoopMaxInst];
   __shared__ __align__(8) uint64_t s_bar;
   const int nb = gridDim.x, ni = d.n_inst;
   Ctx c{s_dyn, &s_bar, 0u, red, sres, d.err};
   double* part_b = d.bcr_part;              // |b|^2 per node chunk
   double* part_r = d.bcr_part + pl.chunks;  // |r|^2 per node chunk
-  for (int k = threadIdx.x; k <= ni; k += blockDim.x) s_npre[k] = d.bcr_npre[k];
+  for (int k = threadIdx.x; k <= ni; k += blockDim.x) {
+    s_npre[k] = d.bcr_npre[k];
+    s_tpre[k] = d.bcr_tpre[k];
+  }
+  const int tsub = pl.task_sub;
   for (int k = threadIdx.x; k < ni; k += blockDim.x) s_act[k] = only < 0 || k == only;
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
@@ -448,7 +503,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   __syncthreads();
   if (mode & kBcrRho) {
     // rho, the initial guess and b at every node; |b|^2 per instance
-    node_tasks(d, s_npre, nullptr, part_b, sh, [&](int k, const Inst& I, long long nd) {
+    node_tasks(d, s_npre, s_tpre, tsub, nullptr, part_b, s_ws, [&](int k, const Inst& I, long long nd) {
       const double bv = rho_node(d, I, k, nd);
       return bv * bv;
     });
@@ -467,7 +522,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   for (int it = 0;; ++it) {
     // FP64 residual of every instance still iterating, stored as the FP32
     // right-hand side of its reduction
-    node_tasks(d, s_npre, s_act, part_r, sh, [&](int k, const Inst& I, long long nd) {
+    node_tasks(d, s_npre, s_tpre, tsub, s_act, part_r, s_ws, [&](int k, const Inst& I, long long nd) {
       const int N = I.N2;
       const int i = (int)(nd / N), j = (int)(nd % N);
       double rr = 0.0;
@@ -503,15 +558,18 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
     if (!__syncthreads_or(more)) break;
     // the reduction passes: phase p runs the p-th stage of every instance
     for (int p = 0; p < pl.phases; ++p) {
-      const int32_t* pre = d.bcr_pre + (long long)p * (ni + 1);
-      const int32_t* kind = d.bcr_kind + (long long)p * ni;
-      const int total = __ldg(pre + ni);
+      // the phase's task tables (the previous readers passed a barrier)
+      for (int k = threadIdx.x; k <= ni; k += blockDim.x) {
+        s_pre[k] = __ldg(d.bcr_pre + (long long)p * (ni + 1) + k);
+        if (k < ni) s_kind[k] = __ldg(d.bcr_kind + (long long)p * ni + k);
+      }
+      __syncthreads();
+      const int total = s_pre[ni];
       for (int t = blockIdx.x; t < total; t += nb) {
-        const int k = task_inst(pre, ni, t);
+        const int k = task_inst_s(s_pre, ni, t);
         if (!s_act[k]) continue;
-        if (!pl.prefetch && threadIdx.x == 0) prefetch_task(d, p, t + nb);  // this CTA's next task
-        const int kl = __ldg(kind + k);
-        if (!run_stage(d, c, k, kl >> 8, kl & 255, t - __ldg(pre + k), sv)) return;
+        if (!pl.prefetch && threadIdx.x == 0) prefetch_task_s(d, s_pre, s_kind, t + nb);  // this CTA's next task
+        if (!run_stage(d, c, k, s_kind[k] >> 8, s_kind[k] & 255, t - s_pre[k], sv)) return;
       }
       if (!grid_sync(d, nb)) return;
     }
@@ -519,7 +577,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   }
   if (mode & kBcrFields) {
     // phi is final everywhere (the last pass ended at a grid barrier)
-    node_tasks(d, s_npre, nullptr, nullptr, sh, [&](int k, const Inst& I, long long nd) {
+    node_tasks(d, s_npre, s_tpre, tsub, nullptr, nullptr, s_ws, [&](int k, const Inst& I, long long nd) {
       (void)k;
       grad_node<float, float2>(d, I, nd);
       return 0.0;
@@ -529,7 +587,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
 }
 
 constexpr int kStaticSmem =
-    40 * 8 + 3 * kBcrMaxN * 4 + kBcrMaxN * 4 + kBcrWarps * kBcrMaxN * 4 + kCoopMaxInst * 24 + 4 + 64;
+    40 * 8 + 3 * kBcrMaxN * 4 + kBcrMaxN * 4 + kBcrWarps * kBcrMaxN * 4 + kCoopMaxInst * 36 + 12 + kBcrMaxTaskSub / 2 * kBcrWarps * 8 + 64;
 
 }  // namespace
 
@@ -558,7 +616,9 @@ int bcr_configure(SolvePlan& pl, BcrInst* bi, int ni, int sms) {
     if (tail > budget) return 0;
     dyn = tail > dyn ? tail : dyn;
     const long long staged = 3ll * B.blk * (long long)sizeof(float);
-    B.smem = stage_ok && staged <= budget ? 1 : 0;
+    // staging pays when the blocks come from L2; streamed from DRAM the
+    // direct loads keep more bytes in flight
+    B.smem = stage_ok && pl.bcr.prefetch && staged <= budget ? 1 : 0;
     if (B.smem) {
       any = 1;
       dyn = staged > dyn ? staged : dyn;
