@@ -504,8 +504,9 @@ void parallel_for(int n, F f) {
 // Layout of instance I's reduction: block size, levels before the dense
 // tail, first block of each kind per level (real rows only).  False if the
 // reduction does not apply (N2 > kBcrMaxN, n1 < 4, n1 > 2^(kBcrMaxK-1)).
-bool bcr_layout(const Inst& I, BcrInst& bp) {
+bool bcr_layout(const Inst& I, BcrInst& bp, bool dense1) {
   std::memset(&bp, 0, sizeof(bp));
+  bp.dense1 = dense1 ? 1 : 0;
   const int N = I.N2, M = I.n1 - 1;
   if (I.n1 < 4 || N > kBcrMaxN) return false;
   int K = 0;
@@ -521,7 +522,7 @@ bool bcr_layout(const Inst& I, BcrInst& bp) {
   for (int l = 1; l <= Lt; ++l) {
     const int h = 1 << (l - 1);
     const long long ne = (M / h + 1) / 2, nk = M / (2 * h);
-    if (l == 1) {
+    if (l == 1 && !dense1) {
       bp.Binv[l] = nblk;
       nblk += ne;
       continue;
@@ -592,7 +593,7 @@ bool bcr_factor(const HostLevel& L, const BcrInst& bp, std::vector<float>& out, 
         return;
       }
       store(bp.Binv[l] + q, Binv[q]);
-      if (l == 1) return;  // level 1 applies A_k and C_k from the stencil
+      if (l == 1 && !bp.dense1) return;  // level 1 applies A_k and C_k from the stencil
       Mat t;
       mat_mul(Binv[q], A[k], t, N);
       store(bp.G[l] + q, t);
@@ -609,7 +610,7 @@ bool bcr_factor(const HostLevel& L, const BcrInst& bp, std::vector<float>& out, 
       mat_mul(A[i], Binv[q], P, N);
       if (right) mat_mul(C[i], Binv[q + 1], Q, N);
       else Q.assign((size_t)N * N, 0.0);
-      if (l > 1) {
+      if (l > 1 || bp.dense1) {
         store(bp.P[l] + q, P);
         store(bp.Q[l] + q, Q);
       }
@@ -845,11 +846,17 @@ static int setup(apic_sim* S) {
     bool want = sizeof(Real) == 4 && ni <= kCoopMaxInst && !(pc && std::string(pc) == "mg");
     for (const Inst& I : S->inst) want = want && !(I.flags & APIC_NO_FIELD);
     long long off = 0;
-    if (want) {
-      bcr_in.resize(ni);
+    // dense level-1 blocks when the whole reduction then still fits in L2
+    // (fewer phases); else level 1 applies the stencil's couplings (fewer
+    // bytes streamed from DRAM)
+    const double l2_fit = 112.0 * 1024 * 1024;
+    for (int dense1 = 1; dense1 >= 0 && want; --dense1) {
+      off = 0;
+      bcr_rows = 0;
+      bcr_in.assign(ni, BcrInst{});
       for (int k = 0; k < ni && want; ++k) {
         BcrInst& B = bcr_in[k];
-        if (!bcr_layout(S->inst[k], B)) {
+        if (!bcr_layout(S->inst[k], B, dense1 != 0)) {
           want = false;
           break;
         }
@@ -861,6 +868,7 @@ static int setup(apic_sim* S) {
         B.foff = bcr_rows;
         bcr_rows += (long long)B.M * B.N;
       }
+      if (4.0 * (double)off <= l2_fit) break;
     }
     const double bytes = 4.0 * (double)off;
     if (want) {
@@ -874,7 +882,7 @@ static int setup(apic_sim* S) {
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       pl.bcr.bytes = (int64_t)(4 * off);
-      pl.bcr.prefetch = bytes <= 112.0 * 1024 * 1024 ? 1 : 0;  // the whole reduction fits in L2
+      pl.bcr.prefetch = bytes <= l2_fit ? 1 : 0;  // the whole reduction fits in L2
       want = (bcr_nb = bcr_configure(pl, bcr_in.data(), ni, sms)) > 0;  // else not co-residable: multigrid
     }
     if (want) {
@@ -887,14 +895,15 @@ static int setup(apic_sim* S) {
         const int M = B.M;
         auto ne = [&](int l) { return (M / (1 << (l - 1)) + 1) / 2; };
         auto nk = [&](int l) { return M / (2 << (l - 1)); };
-        if (B.Lt >= 1) {
+        const int l0 = B.dense1 ? 1 : 2;  // first level with dense blocks
+        if (B.Lt >= 1 && !B.dense1) {
           st.push_back({kBcrFwd1 << 8 | 1, ne(1)});
           st.push_back({kBcrUpd1 << 8 | 1, (nk(1) + kBcrUpdRows - 1) / kBcrUpdRows});
-          for (int l = 2; l <= B.Lt; ++l) st.push_back({kBcrFwd << 8 | l, nk(l)});
         }
+        for (int l = l0; l <= B.Lt; ++l) st.push_back({kBcrFwd << 8 | l, nk(l)});
         st.push_back({kBcrTail << 8, (B.tail_n + B.tail_rows - 1) / B.tail_rows});
-        for (int l = B.Lt; l >= 2; --l) st.push_back({kBcrBack << 8 | l, ne(l)});
-        if (B.Lt >= 1) st.push_back({kBcrBack1 << 8 | 1, ne(1)});
+        for (int l = B.Lt; l >= l0; --l) st.push_back({kBcrBack << 8 | l, ne(l)});
+        if (B.Lt >= 1 && !B.dense1) st.push_back({kBcrBack1 << 8 | 1, ne(1)});
         phases = std::max(phases, (int)st.size());
       }
       bcr_kind.assign((size_t)phases * ni, 0);

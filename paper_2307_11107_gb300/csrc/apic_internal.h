@@ -226,11 +226,11 @@ void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s);
 // smallest with 2^K >= n1).  Reduction level l = 1..Lt (row stride
 // h = 2^(l-1)) eliminates the rows k = h (2q + 1) <= M and keeps
 // i = 2h (q + 1) <= M.
-//   Level 1: the x1 couplings A_i, C_i of Eq. 7 are tridiagonal in j, so only
-//   B_k^-1 is stored.  Forward: y_k = B_k^-1 f_k, then f_i -= A_i y_{i-1} +
+//   Level 1 (unless dense1): the x1 couplings A_i, C_i of Eq. 7 are
+//   tridiagonal in j, so only B_k^-1 is stored.  Forward: y_k = B_k^-1 f_k, then f_i -= A_i y_{i-1} +
 //   C_i y_{i+1} with the stencil's A_i, C_i.  Back: e_k = B_k^-1 (f_k - A_k
 //   e_{k-1} - C_k e_{k+1}).
-//   Level >= 2 (dense blocks):
+//   Level >= 2, and level 1 with dense1 (dense blocks):
 //     kept row i:       P = A_i B_{i-h}^-1,  Q = C_i B_{i+h}^-1   (forward: f_i -= P f_{i-h} + Q f_{i+h})
 //     eliminated row k: B_k^-1, G = B_k^-1 A_k, H = B_k^-1 C_k    (back: e_k = B_k^-1 f_k - G e_{k-h} - H e_{k+h})
 // Blocks are FP32, column-major N x N with column stride Np (16-byte aligned
@@ -265,6 +265,7 @@ struct BcrInst {
   int tail_np;              // row stride of the tail inverse (tail_n rounded up to 4 floats)
   int tail_rows;            // tail-inverse rows per task
   int smem;                 // 1: a task's blocks are staged in shared memory by bulk async copies
+  int dense1;               // 1: level 1 stores P, Q, G, H too (one phase fewer per pass, more bytes)
   int64_t blk;              // floats per block (N * Np)
   int64_t base;             // first float of this instance's blocks in DevPtrs::bcr
   int64_t tail;             // first float of its tail inverse in DevPtrs::bcr
