@@ -165,6 +165,8 @@ struct DevPtrs {
   const int32_t* bcr_pre;         // [phases][n_inst + 1]: prefix sums of the instances' task counts
   const int32_t* bcr_npre;        // [n_inst + 1]: prefix sums of the instances' partial-sum ranges (kBcrSub nodes)
   const int32_t* bcr_tpre;        // [n_inst + 1]: prefix sums of the instances' node tasks
+  const unsigned long long* bcr_pf;  // L2 prefetch ranges of each CTA's tasks: float offset << 20 | bytes / 16
+  const int32_t* bcr_pf_pre;      // [CTAs + 1]: prefix sums of the CTAs' ranges (null: no prefetch)
   double* bcr_part;               // [2][chunks]: |b|^2 and |r|^2 of each range
 };
 

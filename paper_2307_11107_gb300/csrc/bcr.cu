@@ -490,16 +490,30 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   }
   const int tsub = pl.task_sub;
   for (int k = threadIdx.x; k < ni; k += blockDim.x) s_act[k] = only < 0 || k == only;
-  if (threadIdx.x == 0) {
-    mbar_init(&s_bar, 1);
-    // the whole reduction fits in L2: bring this CTA's blocks of every phase
-    // there while the density and the first residual are formed
-    if (pl.prefetch)
-      for (int p = 0; p < pl.phases; ++p) {
-        const int total = __ldg(d.bcr_pre + (long long)p * (ni + 1) + ni);
-        for (int t = blockIdx.x; t < total; t += nb) prefetch_task(d, p, t);
-      }
-  }
+  if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+  // the whole reduction fits in L2: bring this CTA's blocks of every phase
+  // there (its list of ranges, one per thread) while the density and the
+  // first residual are formed
+  if (pl.prefetch && d.bcr_pf)
+    for (int i = d.bcr_pf_pre[blockIdx.x] + threadIdx.x; i < d.bcr_pf_pre[blockIdx.x + 1]; i += blockDim.x) {
+      const unsigned long long e = d.bcr_pf[i];
+      prefetch_l2(d.bcr + (e >> 20), (unsigned)(e & 0xFFFFFull) * 16u);
+    }
+  // this thread's entries of the next phase's task tables, loaded before a
+  // barrier and stored after it
+  int r_pre = 0, r_kind = 0;
+  auto load_tab = [&](int p) {
+    if (threadIdx.x <= ni) {
+      r_pre = __ldg(d.bcr_pre + (long long)p * (ni + 1) + threadIdx.x);
+      r_kind = threadIdx.x < ni ? __ldg(d.bcr_kind + (long long)p * ni + threadIdx.x) : 0;
+    }
+  };
+  auto store_tab = [&]() {
+    if (threadIdx.x <= ni) {
+      s_pre[threadIdx.x] = r_pre;
+      if (threadIdx.x < ni) s_kind[threadIdx.x] = r_kind;
+    }
+  };
   __syncthreads();
   if (mode & kBcrRho) {
     // rho, the initial guess and b at every node; |b|^2 per instance
@@ -534,7 +548,9 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
       }
       return rr;
     });
+    load_tab(0);
     if (!grid_sync(d, nb)) return;
+    store_tab();  // read after the synchronisation that ends inst_sums
     inst_sums(part_r, s_npre, ni, s_act, s_rn);
     int more = 0;
     for (int k = threadIdx.x; k < ni; k += blockDim.x) {
@@ -558,12 +574,10 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
     if (!__syncthreads_or(more)) break;
     // the reduction passes: phase p runs the p-th stage of every instance
     for (int p = 0; p < pl.phases; ++p) {
-      // the phase's task tables (the previous readers passed a barrier)
-      for (int k = threadIdx.x; k <= ni; k += blockDim.x) {
-        s_pre[k] = __ldg(d.bcr_pre + (long long)p * (ni + 1) + k);
-        if (k < ni) s_kind[k] = __ldg(d.bcr_kind + (long long)p * ni + k);
+      if (p > 0) {  // the phase's task tables (loaded before the last barrier)
+        store_tab();
+        __syncthreads();
       }
-      __syncthreads();
       const int total = s_pre[ni];
       for (int t = blockIdx.x; t < total; t += nb) {
         const int k = task_inst_s(s_pre, ni, t);
@@ -571,6 +585,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
         if (!pl.prefetch && threadIdx.x == 0) prefetch_task_s(d, s_pre, s_kind, t + nb);  // this CTA's next task
         if (!run_stage(d, c, k, s_kind[k] >> 8, s_kind[k] & 255, t - s_pre[k], sv)) return;
       }
+      if (p + 1 < pl.phases) load_tab(p + 1);
       if (!grid_sync(d, nb)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt[0] += 1;
