@@ -868,6 +868,9 @@ static int setup(apic_sim* S) {
         off += up((long long)B.tail_n * B.tail_np);
         B.foff = bcr_rows;
         bcr_rows += (long long)B.M * B.N;
+        B.node_off = S->inst[k].node_off;
+        B.nodes = S->inst[k].nodes;
+        B.st_off = S->inst[k].lv[0].st;
       }
       if (4.0 * (double)off <= l2_fit) break;
     }

@@ -272,6 +272,9 @@ struct BcrInst {
   int64_t base;             // first float of this instance's blocks in DevPtrs::bcr
   int64_t tail;             // first float of its tail inverse in DevPtrs::bcr
   int64_t foff;             // first float of its rows in bcr_f / bcr_e (M * N floats each)
+  int64_t node_off;         // the instance's node offset (Inst::node_off)
+  int64_t nodes;            // its nodes (Inst::nodes)
+  int64_t st_off;           // offset of its finest-level FP32 stencil (Inst::lv[0].st)
   int64_t P[kBcrMaxK], Q[kBcrMaxK];                  // block index (from base) of the first block of each kind at level l
   int64_t Binv[kBcrMaxK], G[kBcrMaxK], H[kBcrMaxK];
   int64_t blocks;           // blocks of this instance

@@ -260,13 +260,11 @@ __device__ void prefetch_task_s(const DevPtrs& d, const int* pre, const int* kin
 
 // Task q of kind `kind` at level l of instance k (the whole CTA).  Row r of
 // the reduced right-hand side f and of the correction e is at (r - 1) N.
-__device__ bool run_stage(const DevPtrs& d, Ctx& c, int k, int kind, int l, int q, float (*sv)[kBcrMaxN]) {
-  const Inst& I = d.inst[k];
-  const BcrInst& B = d.bcr_inst[k];
+__device__ bool run_stage(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int l, int q, float (*sv)[kBcrMaxN]) {
   const int N = B.N, M = B.M;
   float* f = d.bcr_f + B.foff;
   float* e = d.bcr_e + B.foff;
-  double* x = d.phi + I.node_off;
+  double* x = d.phi + B.node_off;
   const float* rp[3];
   unsigned rb[3];
   task_ranges(d, B, kind, l, q, rp, rb);
@@ -282,8 +280,8 @@ __device__ bool run_stage(const DevPtrs& d, Ctx& c, int k, int kind, int l, int 
       return true;
     }
     case kBcrUpd1: {  // f_i -= A_i y_{i-1} + C_i y_{i+1} (tridiagonal in j) on kUpdRows kept rows
-      const float* st = (const float*)d.st + I.lv[0].st;
-      const long long nodes = I.nodes;
+      const float* st = (const float*)d.st + B.st_off;
+      const long long nodes = B.nodes;
       const int nk = M / 2, q0 = q * kUpdRows, nq = min(kUpdRows, nk - q0);
       for (int o = threadIdx.x; o < nq * N; o += blockDim.x) {
         const int qq = o / N, j = o - qq * N, i = 2 * (q0 + qq + 1);
@@ -367,8 +365,8 @@ __device__ bool run_stage(const DevPtrs& d, Ctx& c, int k, int kind, int l, int 
     }
     case kBcrBack1: {  // e_k = B_k^-1 (f_k - A_k e_{k-1} - C_k e_{k+1}); x += e
       const int kr = 2 * q + 1;
-      const float* st = (const float*)d.st + I.lv[0].st;
-      const long long nodes = I.nodes;
+      const float* st = (const float*)d.st + B.st_off;
+      const long long nodes = B.nodes;
       const bool left = kr - 1 >= 1, right = kr + 1 <= M;
       for (int j = threadIdx.x; j < N; j += blockDim.x) {
         const long long nd = (long long)kr * N + j;
@@ -480,6 +478,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   __shared__ int s_pre[kCoopMaxInst + 1];
   __shared__ int s_kind[kCoopMaxInst];
   __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(16) BcrInst s_b0;  // instance 0's table (one load per kernel instead of one per task)
   const int nb = gridDim.x, ni = d.n_inst;
   Ctx c{s_dyn, &s_bar, 0u, red, sres, d.err};
   double* part_b = d.bcr_part;              // |b|^2 per node chunk
@@ -491,6 +490,8 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   const int tsub = pl.task_sub;
   for (int k = threadIdx.x; k < ni; k += blockDim.x) s_act[k] = only < 0 || k == only;
   if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+  for (int w = threadIdx.x; w < (int)(sizeof(BcrInst) / 4); w += blockDim.x)
+    ((int*)&s_b0)[w] = ((const int*)d.bcr_inst)[w];
   // the whole reduction fits in L2: bring this CTA's blocks of every phase
   // there (its list of ranges, one per thread) while the density and the
   // first residual are formed
@@ -583,7 +584,8 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
         const int k = task_inst_s(s_pre, ni, t);
         if (!s_act[k]) continue;
         if (!pl.prefetch && threadIdx.x == 0) prefetch_task_s(d, s_pre, s_kind, t + nb);  // this CTA's next task
-        if (!run_stage(d, c, k, s_kind[k] >> 8, s_kind[k] & 255, t - s_pre[k], sv)) return;
+        const BcrInst& B = k == 0 ? s_b0 : d.bcr_inst[k];
+        if (!run_stage(d, c, B, s_kind[k] >> 8, s_kind[k] & 255, t - s_pre[k], sv)) return;
       }
       if (p + 1 < pl.phases) load_tab(p + 1);
       if (!grid_sync(d, nb)) return;
@@ -602,7 +604,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
 }
 
 constexpr int kStaticSmem =
-    40 * 8 + 3 * kBcrMaxN * 4 + kBcrMaxN * 4 + kBcrWarps * kBcrMaxN * 4 + kCoopMaxInst * 36 + 12 + kBcrMaxTaskSub / 2 * kBcrWarps * 8 + 64;
+    40 * 8 + 3 * kBcrMaxN * 4 + kBcrMaxN * 4 + kBcrWarps * kBcrMaxN * 4 + kCoopMaxInst * 36 + 12 + kBcrMaxTaskSub / 2 * kBcrWarps * 8 + (int)sizeof(BcrInst) + 16 + 64;
 
 }  // namespace
 
