@@ -690,6 +690,8 @@ static int setup(apic_sim* S) {
     I.N2 = c.n2 + 1;
     I.h1 = (c.x1_outer + 1.0) / c.n1;
     I.h2 = 2.0 / c.n2;
+    I.i2h1 = 1.0 / (2.0 * I.h1);
+    I.i2h2 = 1.0 / (2.0 * I.h2);
     I.nodes = (long long)I.N1 * I.N2;
     I.node_off = total_nodes;
     total_nodes += I.nodes;
@@ -1010,7 +1012,7 @@ static int setup(apic_sim* S) {
     d.cell_off = (unsigned long long*)A(sizeof(unsigned long long) * (total_cells + 1));
     d.scan_tmp = (unsigned long long*)A(sizeof(unsigned long long) * ((total_cells + 1023) / 1024 + 1));
   }
-  double** node_arrays[] = {&d.rho, &d.phi, &d.phi_prev, &d.V, &d.bbc, &d.rscale, &d.b, &d.r, &d.rh, &d.p, &d.v, &d.s, &d.t, &d.ph, &d.sh};
+  double** node_arrays[] = {&d.rho, &d.phi, &d.phi_prev, &d.V, &d.Vinv, &d.bbc, &d.rscale, &d.b, &d.r, &d.rh, &d.p, &d.v, &d.s, &d.t, &d.ph, &d.sh};
   for (double** a : node_arrays) *a = (double*)A(sizeof(double) * total_nodes);
   S->phi_save = (double*)A(sizeof(double) * total_nodes);
   d.st64 = (double*)A(sizeof(double) * kSt * total_nodes);
@@ -1107,6 +1109,10 @@ static int setup(apic_sim* S) {
     std::vector<double> sgeo = surface_geometry(I);
     S->h2d(d.sgeo + 4 * I.en_off, sgeo.data(), sgeo.size());
     S->h2d(d.V + I.node_off, vols[k].data(), vols[k].size());
+    std::vector<double> vinv(vols[k].size());
+    for (size_t q = 0; q < vinv.size(); ++q) vinv[q] = 1.0 / vols[k][q];
+    S->h2d(d.Vinv + I.node_off, vinv.data(), vinv.size());
+    if (!S->sync()) return S->status;  // vinv goes out of scope
     S->h2d(d.rscale + I.node_off, rscs[k].data(), rscs[k].size());
     S->h2d(d.bbc + I.node_off, bbcs[k].data(), bbcs[k].size());
     S->h2d(d.st64 + (long long)kSt * I.node_off, levels[k][0].st.data(), levels[k][0].st.size());

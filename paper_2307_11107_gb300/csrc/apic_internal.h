@@ -48,6 +48,7 @@ struct Inst {
   double h1, h2;
   double V_dom, A_out, A_grain;
   double tol;
+  double i2h1, i2h2;       // 1 / (2 h1), 1 / (2 h2) (central differences without a division per node)
   uint64_t seed;
   int n1, n2, N1, N2;
   int64_t nodes;           // N1 * N2
@@ -134,6 +135,7 @@ struct DevPtrs {
   int64_t total_cells;
   // per-node FP64 arrays
   double *rho, *phi, *phi_prev, *V, *bbc, *rscale;
+  double* Vinv;                   // 1 / V (the density without a division per node)
   double *b, *r, *rh, *p, *v, *s, *t, *ph, *sh;
   double* st64;                   // finest-level stencil, FP64 [kSt][nodes] per instance (same offsets)
   unsigned long long* acc;        // deposit accumulators

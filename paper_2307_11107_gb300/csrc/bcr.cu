@@ -179,18 +179,7 @@ __device__ bool run_task(Ctx& c, const BcrInst& B, const float* const* src, cons
   return true;
 }
 
-// Instance of task t of a phase: pre[k] <= t < pre[k + 1] (global table).
-__device__ __forceinline__ int task_inst(const int32_t* pre, int ni, int t) {
-  int lo = 0, hi = ni - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(pre + mid) <= t) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-// The same search over a prefix held in shared memory.
+// Instance of task t of a phase: pre[k] <= t < pre[k + 1] (prefix in shared memory).
 __device__ __forceinline__ int task_inst_s(const int* pre, int ni, int t) {
   int lo = 0, hi = ni - 1;
   while (lo < hi) {
@@ -232,30 +221,6 @@ __device__ int task_ranges(const DevPtrs& d, const BcrInst& B, int kind, int l, 
     }
     default: return 0;
   }
-}
-
-// Thread 0: bring the ranges of task t of phase p into L2 (if the task exists).
-__device__ void prefetch_task(const DevPtrs& d, int p, int t) {
-  const int ni = d.n_inst;
-  const int32_t* pre = d.bcr_pre + (long long)p * (ni + 1);
-  if (t >= __ldg(pre + ni)) return;
-  const int k = task_inst(pre, ni, t);
-  const int kl = __ldg(d.bcr_kind + (long long)p * ni + k);
-  const float* rp[3];
-  unsigned rb[3];
-  const int n = task_ranges(d, d.bcr_inst[k], kl >> 8, kl & 255, t - __ldg(pre + k), rp, rb);
-  for (int r = 0; r < n; ++r) prefetch_l2(rp[r], rb[r]);
-}
-
-// The same from the phase's tables in shared memory.
-__device__ void prefetch_task_s(const DevPtrs& d, const int* pre, const int* kind, int t) {
-  const int ni = d.n_inst;
-  if (t >= pre[ni]) return;
-  const int k = task_inst_s(pre, ni, t);
-  const float* rp[3];
-  unsigned rb[3];
-  const int n = task_ranges(d, d.bcr_inst[k], kind[k] >> 8, kind[k] & 255, t - pre[k], rp, rb);
-  for (int r = 0; r < n; ++r) prefetch_l2(rp[r], rb[r]);
 }
 
 // Task q of kind `kind` at level l of instance k (the whole CTA).  Row r of
@@ -583,7 +548,6 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
       for (int t = blockIdx.x; t < total; t += nb) {
         const int k = task_inst_s(s_pre, ni, t);
         if (!s_act[k]) continue;
-        if (!pl.prefetch && threadIdx.x == 0) prefetch_task_s(d, s_pre, s_kind, t + nb);  // this CTA's next task
         const BcrInst& B = k == 0 ? s_b0 : d.bcr_inst[k];
         if (!run_stage(d, c, B, s_kind[k] >> 8, s_kind[k] & 255, t - s_pre[k], sv)) return;
       }

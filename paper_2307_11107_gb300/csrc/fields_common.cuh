@@ -4,7 +4,8 @@
 // same values.  Included inside namespace apic::{anonymous}.
 #pragma once
 
-// rho_ij = sum_s q_s w_s (accumulated CIC weights) / V_ij (Eq. 5); the
+// rho_ij = sum_s q_s w_s (accumulated CIC weights) / V_ij (Eq. 5, as a
+// product with the stored 1 / V_ij: FP64 division is slow on this GPU); the
 // accumulators are cleared for the next deposit; the initial guess of this
 // step's solve (previous phi, or its linear extrapolation); the right-hand
 // side b = rscale * (-rho) + (Dirichlet terms).  Returns b at the node.
@@ -17,7 +18,7 @@ __device__ __forceinline__ double rho_node(const DevPtrs& d, const Inst& I, int 
     d.acc[P.acc_off + nd] = 0ull;
     q += P.dep_scale * (double)a;
   }
-  const double rho = q / d.V[g];
+  const double rho = q * d.Vinv[g];
   d.rho[g] = rho;
   const int i = (int)(nd / I.N2);
   double bv = 0.0;
@@ -32,7 +33,8 @@ __device__ __forceinline__ double rho_node(const DevPtrs& d, const Inst& I, int 
 }
 
 // Node gradients: central differences inside, one-sided second order on the
-// four edges (Sec. 2: derivatives of phi taken numerically at the nodes).
+// four edges (Sec. 2: derivatives of phi taken numerically at the nodes),
+// scaled by the stored 1 / (2 h).
 template <class Real, class R2>
 __device__ __forceinline__ void grad_node(const DevPtrs& d, const Inst& I, long long nd) {
   const double* p = d.phi + I.node_off;
@@ -41,13 +43,13 @@ __device__ __forceinline__ void grad_node(const DevPtrs& d, const Inst& I, long 
   const int i = (int)(nd / N2), j = (int)(nd % N2);
   double g1 = 0.0, g2 = 0.0;
   if (!nofield) {
-    if (i == 0) g1 = (-3.0 * p[j] + 4.0 * p[N2 + j] - p[2 * N2 + j]) / (2.0 * I.h1);
-    else if (i == n1) g1 = (3.0 * p[n1 * N2 + j] - 4.0 * p[(n1 - 1) * N2 + j] + p[(n1 - 2) * N2 + j]) / (2.0 * I.h1);
-    else g1 = (p[(i + 1) * N2 + j] - p[(i - 1) * N2 + j]) / (2.0 * I.h1);
+    if (i == 0) g1 = (-3.0 * p[j] + 4.0 * p[N2 + j] - p[2 * N2 + j]) * I.i2h1;
+    else if (i == n1) g1 = (3.0 * p[n1 * N2 + j] - 4.0 * p[(n1 - 1) * N2 + j] + p[(n1 - 2) * N2 + j]) * I.i2h1;
+    else g1 = (p[(i + 1) * N2 + j] - p[(i - 1) * N2 + j]) * I.i2h1;
     const long long b = (long long)i * N2;
-    if (j == 0) g2 = (-3.0 * p[b] + 4.0 * p[b + 1] - p[b + 2]) / (2.0 * I.h2);
-    else if (j == n2) g2 = (3.0 * p[b + n2] - 4.0 * p[b + n2 - 1] + p[b + n2 - 2]) / (2.0 * I.h2);
-    else g2 = (p[b + j + 1] - p[b + j - 1]) / (2.0 * I.h2);
+    if (j == 0) g2 = (-3.0 * p[b] + 4.0 * p[b + 1] - p[b + 2]) * I.i2h2;
+    else if (j == n2) g2 = (3.0 * p[b + n2] - 4.0 * p[b + n2 - 1] + p[b + n2 - 2]) * I.i2h2;
+    else g2 = (p[b + j + 1] - p[b + j - 1]) * I.i2h2;
   }
   R2 v;
   v.x = (Real)g1;
