@@ -9,24 +9,40 @@
 // accumulators are cleared for the next deposit; the initial guess of this
 // step's solve (previous phi, or its linear extrapolation); the right-hand
 // side b = rscale * (-rho) + (Dirichlet terms).  Returns b at the node.
+// Every load comes before the first store: a load placed after a store that
+// might alias it waits for that store, which made this node loop a chain of
+// memory round trips.
 __device__ __forceinline__ double rho_node(const DevPtrs& d, const Inst& I, int inst, long long nd) {
   const long long g = I.node_off + nd;
-  double q = 0.0;
-  for (int s = 0; s < I.n_species; ++s) {
-    const Pop& P = d.pop[I.pop0 + s];
-    unsigned long long a = d.acc[P.acc_off + nd];
-    d.acc[P.acc_off + nd] = 0ull;
-    q += P.dep_scale * (double)a;
-  }
-  const double rho = q * d.Vinv[g];
-  d.rho[g] = rho;
+  const int ns = I.n_species;  // 1 or 2
   const int i = (int)(nd / I.N2);
-  double bv = 0.0;
-  if (i > 0 && i < I.n1) {
-    const double ph = d.phi[g];
-    if (I.guess && d.stp[inst].step >= 2) d.phi[g] = 2.0 * ph - d.phi_prev[g];
+  const bool interior = i > 0 && i < I.n1;
+  const bool extrap = I.guess && d.stp[inst].step >= 2;
+  const Pop& P0 = d.pop[I.pop0];
+  const Pop& P1 = d.pop[I.pop0 + (ns > 1 ? 1 : 0)];
+  const long long o0 = P0.acc_off + nd, o1 = P1.acc_off + nd;
+  const double s0 = P0.dep_scale, s1 = P1.dep_scale;
+  const unsigned long long a0 = d.acc[o0];
+  const unsigned long long a1 = ns > 1 ? d.acc[o1] : 0ull;
+  const double vinv = d.Vinv[g];
+  double ph = 0.0, prev = 0.0, rs = 0.0, bc = 0.0;
+  if (interior) {
+    ph = d.phi[g];
+    prev = d.phi_prev[g];
+    rs = d.rscale[g];
+    bc = d.bbc[g];
+  }
+  double q = 0.0;
+  q += s0 * (double)a0;
+  if (ns > 1) q += s1 * (double)a1;
+  const double rho = q * vinv;
+  const double bv = interior ? -rho * rs + bc : 0.0;
+  d.acc[o0] = 0ull;
+  if (ns > 1) d.acc[o1] = 0ull;
+  d.rho[g] = rho;
+  if (interior) {
+    if (extrap) d.phi[g] = 2.0 * ph - prev;
     d.phi_prev[g] = ph;
-    bv = -rho * d.rscale[g] + d.bbc[g];
   }
   d.b[g] = bv;
   return bv;
