@@ -840,8 +840,7 @@ static int setup(apic_sim* S) {
   // instance with a field, N2 <= kBcrMaxN, the blocks of the batch within the
   // memory budget (APIC_PRECOND=mg keeps multigrid).
   std::vector<BcrInst> bcr_in;
-  std::vector<int32_t> bcr_kind, bcr_pre, bcr_npre, bcr_tpre, bcr_pf_pre;
-  std::vector<unsigned long long> bcr_pf;
+  std::vector<int32_t> bcr_kind, bcr_pre, bcr_npre, bcr_tpre;
   long long bcr_rows = 0;  // floats of bcr_f (and of bcr_e)
   int bcr_nb = 0;          // CTAs of the reduction solve
   {
@@ -888,7 +887,7 @@ static int setup(apic_sim* S) {
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       pl.bcr.bytes = (int64_t)(4 * off);
-      pl.bcr.prefetch = bytes <= l2_fit ? 1 : 0;  // the whole reduction fits in L2
+      pl.bcr.resident = bytes <= l2_fit ? 1 : 0;  // the whole reduction fits in L2 (blocks are staged)
       want = (bcr_nb = bcr_configure(pl, bcr_in.data(), ni, sms)) > 0;  // else not co-residable: multigrid
     }
     if (want) {
@@ -934,41 +933,6 @@ static int setup(apic_sim* S) {
       bcr_tpre.assign(ni + 1, 0);
       for (int k = 0; k < ni; ++k)
         bcr_tpre[k + 1] = bcr_tpre[k] + (bcr_npre[k + 1] - bcr_npre[k] + pl.bcr.task_sub - 1) / pl.bcr.task_sub;
-      // each CTA's L2 prefetch ranges (every phase), when the reduction fits in L2
-      if (pl.bcr.prefetch) {
-        std::vector<std::vector<unsigned long long>> per(bcr_nb);
-        for (int p = 0; p < phases; ++p)
-          for (int k = 0; k < ni; ++k) {
-            const BcrInst& B = bcr_in[k];
-            const int kind = bcr_kind[(size_t)p * ni + k] >> 8, l = bcr_kind[(size_t)p * ni + k] & 255;
-            const int t0 = bcr_pre[(size_t)p * (ni + 1) + k], t1 = bcr_pre[(size_t)p * (ni + 1) + k + 1];
-            for (int t = t0; t < t1; ++t) {
-              const long long q = t - t0, bb = B.blk * 4;
-              auto add = [&](long long off, long long bytes) {
-                per[t % bcr_nb].push_back((unsigned long long)off << 20 | (unsigned long long)(bytes / 16));
-              };
-              if (kind == kBcrFwd1 || kind == kBcrBack1) add(B.base + (B.Binv[1] + q) * B.blk, bb);
-              if (kind == kBcrFwd) {
-                add(B.base + (B.P[l] + q) * B.blk, bb);
-                add(B.base + (B.Q[l] + q) * B.blk, bb);
-              }
-              if (kind == kBcrBack) {
-                add(B.base + (B.Binv[l] + q) * B.blk, bb);
-                add(B.base + (B.G[l] + q) * B.blk, bb);
-                add(B.base + (B.H[l] + q) * B.blk, bb);
-              }
-              if (kind == kBcrTail) {
-                const long long r0 = q * B.tail_rows, r1 = std::min<long long>(B.tail_n, r0 + B.tail_rows);
-                add(B.tail + r0 * B.tail_np, (r1 - r0) * B.tail_np * 4);
-              }
-            }
-          }
-        bcr_pf_pre.assign(bcr_nb + 1, 0);
-        for (int b = 0; b < bcr_nb; ++b) {
-          bcr_pf_pre[b + 1] = bcr_pf_pre[b] + (int32_t)per[b].size();
-          bcr_pf.insert(bcr_pf.end(), per[b].begin(), per[b].end());
-        }
-      }
       pl.bcr.n_inst = ni;
       pl.bcr.phases = phases;
     } else {
@@ -1044,10 +1008,6 @@ static int setup(apic_sim* S) {
     d.bcr_pre = (const int32_t*)A(sizeof(int32_t) * bcr_pre.size());
     d.bcr_npre = (const int32_t*)A(sizeof(int32_t) * bcr_npre.size());
     d.bcr_tpre = (const int32_t*)A(sizeof(int32_t) * bcr_tpre.size());
-    if (!bcr_pf.empty()) {
-      d.bcr_pf = (const unsigned long long*)A(sizeof(unsigned long long) * bcr_pf.size());
-      d.bcr_pf_pre = (const int32_t*)A(sizeof(int32_t) * bcr_pf_pre.size());
-    }
     d.bcr_part = (double*)A(sizeof(double) * 2 * (size_t)pl.bcr.chunks);
     if (S->status != APIC_OK) return S->status;
     S->h2d((BcrInst*)d.bcr_inst, bcr_in.data(), bcr_in.size());
@@ -1055,10 +1015,6 @@ static int setup(apic_sim* S) {
     S->h2d((int32_t*)d.bcr_pre, bcr_pre.data(), bcr_pre.size());
     S->h2d((int32_t*)d.bcr_npre, bcr_npre.data(), bcr_npre.size());
     S->h2d((int32_t*)d.bcr_tpre, bcr_tpre.data(), bcr_tpre.size());
-    if (!bcr_pf.empty()) {
-      S->h2d((unsigned long long*)d.bcr_pf, bcr_pf.data(), bcr_pf.size());
-      S->h2d((int32_t*)d.bcr_pf_pre, bcr_pf_pre.data(), bcr_pf_pre.size());
-    }
     if (!S->sync()) return S->status;
     std::vector<float> blocks;
     std::vector<double> T, aug;

@@ -167,8 +167,6 @@ struct DevPtrs {
   const int32_t* bcr_pre;         // [phases][n_inst + 1]: prefix sums of the instances' task counts
   const int32_t* bcr_npre;        // [n_inst + 1]: prefix sums of the instances' partial-sum ranges (kBcrSub nodes)
   const int32_t* bcr_tpre;        // [n_inst + 1]: prefix sums of the instances' node tasks
-  const unsigned long long* bcr_pf;  // L2 prefetch ranges of each CTA's tasks: float offset << 20 | bytes / 16
-  const int32_t* bcr_pf_pre;      // [CTAs + 1]: prefix sums of the CTAs' ranges (null: no prefetch)
   double* bcr_part;               // [2][chunks]: |b|^2 and |r|^2 of each range
 };
 
@@ -288,7 +286,7 @@ struct BcrPlan {
   int n_inst;               // 0: not in use
   int phases;               // phases of one reduction pass
   int smem;                 // 1: dynamic shared memory holds staged blocks
-  int prefetch;             // 1: every CTA brings its blocks into L2 at the start (they fit)
+  int resident;             // 1: the whole reduction fits in L2 (dense level 1, blocks staged in shared memory)
   int dyn;                  // dynamic shared memory bytes of the solve kernel
   int pad;
   int64_t bytes;            // device bytes of all blocks and tail inverses

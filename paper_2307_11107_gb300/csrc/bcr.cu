@@ -55,9 +55,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                : "memory");
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* src, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   uint32_t ok;
@@ -457,14 +454,6 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   if (threadIdx.x == 0) mbar_init(&s_bar, 1);
   for (int w = threadIdx.x; w < (int)(sizeof(BcrInst) / 4); w += blockDim.x)
     ((int*)&s_b0)[w] = ((const int*)d.bcr_inst)[w];
-  // the whole reduction fits in L2: bring this CTA's blocks of every phase
-  // there (its list of ranges, one per thread) while the density and the
-  // first residual are formed
-  if (pl.prefetch && d.bcr_pf)
-    for (int i = d.bcr_pf_pre[blockIdx.x] + threadIdx.x; i < d.bcr_pf_pre[blockIdx.x + 1]; i += blockDim.x) {
-      const unsigned long long e = d.bcr_pf[i];
-      prefetch_l2(d.bcr + (e >> 20), (unsigned)(e & 0xFFFFFull) * 16u);
-    }
   // this thread's entries of the next phase's task tables, loaded before a
   // barrier and stored after it
   int r_pre = 0, r_kind = 0;
@@ -599,7 +588,7 @@ int bcr_configure(SolvePlan& pl, BcrInst* bi, int ni, int sms) {
     const long long staged = 3ll * B.blk * (long long)sizeof(float);
     // staging pays when the blocks come from L2; streamed from DRAM the
     // direct loads keep more bytes in flight
-    B.smem = stage_ok && pl.bcr.prefetch && staged <= budget ? 1 : 0;
+    B.smem = stage_ok && pl.bcr.resident && staged <= budget ? 1 : 0;
     if (B.smem) {
       any = 1;
       dyn = staged > dyn ? staged : dyn;
