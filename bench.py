@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--particles", type=int, default=None,
                     help="macro-particles per species (default: the workload's own count)")
     ap.add_argument("--workload", default="dipole256", choices=["dipole256", "dipole1024", "batched48", "sphere64"])
+    ap.add_argument("--instances", type=int, default=None,
+                    help="batched48 only: the first N instances (smaller runs, e.g. under a profiler)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--autotune", action="store_true",
@@ -117,11 +119,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workloads(name="dipole256", n_per_species=None):
-    """List of instance configurations of the named workload."""
+def workloads(name="dipole256", n_per_species=None, n_instances=None):
+    """List of instance configurations of the named workload (batched48:
+    its first n_instances instances when given, e.g. for a profiler capture
+    that must stay small)."""
     from paper_2307_11107_gb300 import workloads as W
     if name == "batched48":
-        return W.batched_48()
+        cs = W.batched_48()[:n_instances] if n_instances else W.batched_48()
+        if n_per_species:
+            for c in cs:
+                c["species"] = [dict(sp, n_init=n_per_species) for sp in c["species"]]
+        return cs
     if name == "dipole1024":
         c = W.dipole_1024("fp32")
     elif name == "sphere64":
@@ -137,11 +145,11 @@ def workload(n_per_species=None, name="dipole256"):
     return workloads(name, n_per_species)[0]
 
 
-def replica_configs(name, n_per_species, rank, history_cap):
+def replica_configs(name, n_per_species, rank, history_cap, n_instances=None):
     """Instance configurations of rank `rank`'s replica: the workload's own
     instances renumbered so that no two ranks share a random stream (the
     instance number is part of every Philox counter)."""
-    cfgs = workloads(name, n_per_species)
+    cfgs = workloads(name, n_per_species, n_instances)
     for c in cfgs:
         c["instance"] = c.get("instance", 0) + rank * len(cfgs)
         c["history_cap"] = history_cap
@@ -221,7 +229,7 @@ def main():
         pg = dist
     import paper_2307_11107_gb300 as apic
     apic.build()
-    cfgs = replica_configs(args.workload, args.particles, rank, max(4096, args.steps + args.warmup + 8))
+    cfgs = replica_configs(args.workload, args.particles, rank, max(4096, args.steps + args.warmup + 8), args.instances)
     cfg = cfgs[0]
     sim = apic.Sim(cfgs)
     for k, c in enumerate(cfgs):
@@ -329,7 +337,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": cfg["name"] if len(cfgs) == 1 else "batched_48_instances",
+            "config": {"workload": cfg["name"] if len(cfgs) == 1 else "batched_48_instances" + (" (first %d)" % len(cfgs) if args.instances else ""),
                        "instances": len(cfgs), "alpha": cfg["alpha"], "a": 2 * cfg["alpha"], "B": cfg["B"],
                        "grid_cells": [cfg["n1"], cfg["n2"]],
                        "particles_per_species": [c["species"][0]["n_init"] for c in cfgs] if len(cfgs) > 1
