@@ -1136,6 +1136,7 @@ static int setup(apic_sim* S) {
   // hold conditional nodes)
   if (const char* cl = std::getenv("APIC_COND_LOOP")) S->cond_loop = std::atoi(cl) != 0;
   for (const Inst& I : S->inst) S->max_n2 = std::max(S->max_n2, I.n2);
+  push_window_rows<Real>(S->max_n2);  // the occupancy query happens here, not inside a graph capture
   // the whole Poisson solve as one cooperative kernel, unless disabled or not co-residable
   const char* env = std::getenv("APIC_SOLVER");
   // one cooperative launch per solve for a single instance; batches use the

@@ -205,6 +205,10 @@ template <class Real>
 void launch_deposit_all(const DevPtrs& d, int max_grid, cudaStream_t s);
 template <class Real>
 void launch_push(const DevPtrs& d, int grid, int max_n2, cudaStream_t s);
+// Node rows of the push's shared-memory deposit window for grids up to max_n2
+// cells in x2 (queried once per width; call at set-up, before any capture).
+template <class Real>
+int push_window_rows(int max_n2);
 template <class Real>
 void launch_inject(const DevPtrs& d, long long max_inj, cudaStream_t s);
 template <class Real>

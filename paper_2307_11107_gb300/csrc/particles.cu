@@ -7,6 +7,9 @@
 // -fmad=false, the parity build) and -DAPIC_REAL=float.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstdlib>
+
 #include <cstdint>
 
 #include "apic_internal.h"
@@ -23,7 +26,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPushItems = 8;    // particles per thread per chunk
-constexpr int kWinRows = 8;      // node rows of the shared-memory deposit window
+constexpr int kWinRows = 8;      // node rows of the shared-memory deposit window at most
 constexpr int kWinMaxN2 = 513;   // widest grid row the window holds (larger grids deposit globally)
 constexpr int kInjRows = 3;      // node rows of the injection window (the last two cell rows)
 constexpr int kInjMaxN2 = 512;   // widest grid (cells in x2) the injection window holds
@@ -227,7 +230,7 @@ __device__ __forceinline__ Cell locate_c(const PushConst& C, Real x1, Real x2) {
 // One full particle update for slot t of the batch (Sec. 2, Eqs. 8-10, 9).
 // The CTA works on chunks of kPushItems x blockDim consecutive slots of one
 // population (sorted by cell, so a chunk covers few grid rows) and deposits
-// into a shared-memory window of kWinRows node rows that is flushed to the
+// into a shared-memory window of win_rows (<= kWinRows) node rows that is flushed to the
 // global accumulator after each chunk.
 #ifndef APIC_PUSH_UNROLL
 #define APIC_PUSH_UNROLL 2
@@ -237,7 +240,7 @@ constexpr int kPushUnroll = APIC_PUSH_UNROLL;  // items of the chunk loop unroll
 // FP32: 64 registers, four CTAs of 256 threads per SM; FP64 (parity build): two
 #define APIC_PUSH_MIN_BLOCKS (sizeof(APIC_REAL) == 4 ? 4 : 2)
 #endif
-__global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, int win_n2) {
+__global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, int win_n2, int win_rows) {
   extern __shared__ unsigned long long s_win[];
   __shared__ long long s_pre[kMaxPop + 1];  // chunk prefix over populations
   __shared__ PushConst s_pc[kMaxPop];
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
     C.acc_off = P.acc_off;
     s_pc[p] = C;
   }
-  const int win_words = kF64 ? kWinRows * (win_n2 + 1) : 2 * kWinRows * win_n2;
+  const int win_words = kF64 ? win_rows * (win_n2 + 1) : 2 * win_rows * win_n2;
   for (int k = threadIdx.x; k < win_words; k += blockDim.x) s_win[k] = 0ull;
   __syncthreads();
   const long long total_chunks = s_pre[d.n_pop];
@@ -310,7 +313,7 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
    W.g = d.acc + C.acc_off;
    W.row0 = s_row0;
    W.N2 = C.N2;
-   W.rows = C.n2 <= win_n2 ? kWinRows : 0;
+   W.rows = C.n2 <= win_n2 ? win_rows : 0;
    CellWin CW;
    CW.s = s_win;
    CW.g = W.g;
@@ -1004,14 +1007,44 @@ void launch_deposit_all<Real>(const DevPtrs& d, int max_grid, cudaStream_t s) {
 }
 
 template <>
-void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, cudaStream_t s) {
+int push_window_rows<Real>(int max_n2) {
   // window capacity: the widest grid of the batch, up to kWinMaxN2 - 1 cells
-  // (wider grids deposit straight to global memory)
+  // (wider grids deposit straight to global memory); node rows up to
+  // kWinRows within 32 KB (a 512-cell row of FP32 cell moments takes 8 KB;
+  // a smaller window leaves more L1 for the gather: on the 1024 x 512 grid 4
+  // rows pushed in 2.47 ms, 5 in 2.75, 8 in 3.67) and as many as keep
+  // APIC_PUSH_MIN_BLOCKS CTAs per SM resident.  Cached per width: the first
+  // call (at set-up, before any capture) queries the occupancy.
   const int win_n2 = max_n2 < kWinMaxN2 - 1 ? max_n2 : kWinMaxN2 - 1;
-  const int words = kF64 ? kWinRows * (win_n2 + 1) : 2 * kWinRows * win_n2;
+  static int rows_for[kWinMaxN2 + 1] = {};
+  int rows = rows_for[win_n2];
+  if (rows == 0) {
+    const int row_bytes = (kF64 ? (win_n2 + 1) : 2 * win_n2) * (int)sizeof(unsigned long long);
+    rows = std::max(2, std::min(kWinRows, 32768 / std::max(1, row_bytes)));
+    const char* e = std::getenv("APIC_WIN_ROWS");  // tuning: a fixed row count
+    if (e) rows = std::max(2, std::min(kWinRows, std::atoi(e)));
+    for (; !e && rows > 2; --rows) {
+      const int sm = (kF64 ? rows * (win_n2 + 1) : 2 * rows * win_n2) * (int)sizeof(unsigned long long);
+      cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      int per = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push, 256, sm) == cudaSuccess &&
+          per >= (int)APIC_PUSH_MIN_BLOCKS)
+        break;
+    }
+    cudaGetLastError();
+    rows_for[win_n2] = rows;
+  }
+  return rows;
+}
+
+template <>
+void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, cudaStream_t s) {
+  const int win_n2 = max_n2 < kWinMaxN2 - 1 ? max_n2 : kWinMaxN2 - 1;
+  const int rows = push_window_rows<Real>(max_n2);
+  const int words = kF64 ? rows * (win_n2 + 1) : 2 * rows * win_n2;
   const int sm = words * (int)sizeof(unsigned long long);
   cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  k_push<<<grid, 256, sm, s>>>(d, win_n2);
+  k_push<<<grid, 256, sm, s>>>(d, win_n2, rows);
 }
 
 template <>
