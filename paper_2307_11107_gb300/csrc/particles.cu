@@ -241,9 +241,13 @@ constexpr int kPushUnroll = APIC_PUSH_UNROLL;  // items of the chunk loop unroll
 #define APIC_PUSH_MIN_BLOCKS (sizeof(APIC_REAL) == 4 ? 4 : 2)
 #endif
 __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, int win_n2, int win_rows) {
+  // dynamic shared memory: the deposit window, then the chunk prefix over the
+  // populations and their constants (sized by the batch, so that a small
+  // batch leaves more of the SM's memory to L1 for the field gather)
   extern __shared__ unsigned long long s_win[];
-  __shared__ long long s_pre[kMaxPop + 1];  // chunk prefix over populations
-  __shared__ PushConst s_pc[kMaxPop];
+  const int win_words = kF64 ? win_rows * (win_n2 + 1) : 2 * win_rows * win_n2;
+  long long* s_pre = (long long*)(s_win + win_words);
+  PushConst* s_pc = (PushConst*)(s_pre + d.n_pop + 1);
   __shared__ int s_row0;
   __shared__ unsigned s_rowmask;  // FP32 window: cell rows that received moments in this chunk
   const long long CH = (long long)kPushItems * blockDim.x;
@@ -278,7 +282,6 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
     C.acc_off = P.acc_off;
     s_pc[p] = C;
   }
-  const int win_words = kF64 ? win_rows * (win_n2 + 1) : 2 * win_rows * win_n2;
   for (int k = threadIdx.x; k < win_words; k += blockDim.x) s_win[k] = 0ull;
   __syncthreads();
   const long long total_chunks = s_pre[d.n_pop];
@@ -1006,6 +1009,13 @@ void launch_deposit_all<Real>(const DevPtrs& d, int max_grid, cudaStream_t s) {
   k_deposit_all<<<max_grid, 256, 0, s>>>(d);
 }
 
+// Dynamic shared memory of the push: window, chunk prefix, population constants.
+static int push_smem(int rows, int win_n2, int n_pop) {
+  const int words = kF64 ? rows * (win_n2 + 1) : 2 * rows * win_n2;
+  return words * (int)sizeof(unsigned long long) + (n_pop + 1) * (int)sizeof(long long) +
+         n_pop * (int)sizeof(PushConst);
+}
+
 template <>
 int push_window_rows<Real>(int max_n2) {
   // window capacity: the widest grid of the batch, up to kWinMaxN2 - 1 cells
@@ -1024,7 +1034,7 @@ int push_window_rows<Real>(int max_n2) {
     const char* e = std::getenv("APIC_WIN_ROWS");  // tuning: a fixed row count
     if (e) rows = std::max(2, std::min(kWinRows, std::atoi(e)));
     for (; !e && rows > 2; --rows) {
-      const int sm = (kF64 ? rows * (win_n2 + 1) : 2 * rows * win_n2) * (int)sizeof(unsigned long long);
+      const int sm = push_smem(rows, win_n2, kMaxPop);
       cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
       int per = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push, 256, sm) == cudaSuccess &&
@@ -1041,8 +1051,7 @@ template <>
 void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, cudaStream_t s) {
   const int win_n2 = max_n2 < kWinMaxN2 - 1 ? max_n2 : kWinMaxN2 - 1;
   const int rows = push_window_rows<Real>(max_n2);
-  const int words = kF64 ? rows * (win_n2 + 1) : 2 * rows * win_n2;
-  const int sm = words * (int)sizeof(unsigned long long);
+  const int sm = push_smem(rows, win_n2, d.n_pop);
   cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   k_push<<<grid, 256, sm, s>>>(d, win_n2, rows);
 }
