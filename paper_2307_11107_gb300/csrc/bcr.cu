@@ -34,7 +34,8 @@ constexpr int kBcrWarps = kBcrThreads / 32;
 constexpr int kMC = kBcrMaxN / 32;  // outputs per lane
 constexpr int kTailChunk = 16;      // tail rows per task at most (one per warp)
 constexpr int kUpdRows = kBcrUpdRows;
-static_assert(kBcrThreads == 2 * kBcrSub, "node tasks cover two partial-sum ranges per pass");
+constexpr int kRangesPerPass = kBcrThreads / kBcrSub;  // partial-sum ranges a CTA covers at once
+static_assert(kRangesPerPass * kBcrSub == kBcrThreads, "whole ranges per pass");
 
 // ---- bulk asynchronous copies (global -> shared, completion on an mbarrier) ----
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -374,36 +375,36 @@ __device__ void inst_sums(const double* part, const int* npre, int ni, const int
 
 // Node tasks over the ranges of kBcrSub nodes of every instance (range c of
 // instance k: nodes c kBcrSub .. (c + 1) kBcrSub - 1).  A task covers tsub
-// consecutive ranges of one instance, two per pass of the CTA; the tasks of
+// consecutive ranges of one instance, kRangesPerPass per pass of the CTA; the tasks of
 // all instances are spread over the CTAs.  body(k, I, nd) returns the node's
 // contribution to its range's sum, which goes to part[npre[k] + c] (when part
-// is not null) as a warp-shuffle tree per warp and the warps in order: the
+// is not null) as a warp-shuffle tree per warp and the range's warps in order: the
 // sums do not depend on the task size, the CTA or the other instances of a
-// batch.  ws: kBcrMaxTaskSub / 2 * kBcrWarps doubles of shared memory.
+// batch.  ws: kBcrMaxTaskSub / kRangesPerPass * kBcrWarps doubles of shared memory.
 template <class F>
 __device__ void node_tasks(const DevPtrs& d, const int* npre, const int* tpre, int tsub, const int* sel, double* part,
                            double* ws, F body) {
-  constexpr int kPairs = kBcrMaxTaskSub / 2;
+  constexpr int kPasses = kBcrMaxTaskSub / kRangesPerPass;
   const int ni = d.n_inst, nb = gridDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int half = threadIdx.x / kBcrSub, r = threadIdx.x % kBcrSub;
+  const int half = threadIdx.x / kBcrSub, r = threadIdx.x % kBcrSub;  // range within the pass, node within it
   const int total = tpre[ni];
   for (int t = blockIdx.x; t < total; t += nb) {
     const int k = task_inst_s(tpre, ni, t);
     if (sel && !sel[k]) continue;
     const Inst& I = d.inst[k];
     const int s0 = (t - tpre[k]) * tsub, s1 = min(npre[k + 1] - npre[k], s0 + tsub);
-    double v[kPairs];
+    double v[kPasses];
 #pragma unroll
-    for (int u = 0; u < kPairs; ++u) {
-      const int sc = s0 + 2 * u + half;
+    for (int u = 0; u < kPasses; ++u) {
+      const int sc = s0 + kRangesPerPass * u + half;
       const long long nd = (long long)sc * kBcrSub + r;
       v[u] = sc < s1 && nd < I.nodes ? body(k, I, nd) : 0.0;
     }
     if (!part) continue;
 #pragma unroll
-    for (int u = 0; u < kPairs; ++u) {
-      if (s0 + 2 * u >= s1) break;
+    for (int u = 0; u < kPasses; ++u) {
+      if (s0 + kRangesPerPass * u >= s1) break;
       double x = v[u];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
@@ -411,9 +412,9 @@ __device__ void node_tasks(const DevPtrs& d, const int* npre, const int* tpre, i
     }
     __syncthreads();
     if (threadIdx.x < s1 - s0) {
-      const int i = threadIdx.x, u = i >> 1, w0 = (i & 1) * (kBcrWarps / 2);
+      const int i = threadIdx.x, u = i / kRangesPerPass, w0 = (i % kRangesPerPass) * (kBcrSub / 32);
       double sum = 0.0;
-      for (int w = w0; w < w0 + kBcrWarps / 2; ++w) sum += ws[u * kBcrWarps + w];
+      for (int w = w0; w < w0 + kBcrSub / 32; ++w) sum += ws[u * kBcrWarps + w];
       part[npre[k] + s0 + i] = sum;
     }
     __syncthreads();
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   __shared__ int s_act[kCoopMaxInst];
   __shared__ int s_npre[kCoopMaxInst + 1];
   __shared__ int s_tpre[kCoopMaxInst + 1];
-  __shared__ double s_ws[kBcrMaxTaskSub / 2 * kBcrWarps];
+  __shared__ double s_ws[kBcrMaxTaskSub / kRangesPerPass * kBcrWarps];
   __shared__ int s_pre[kCoopMaxInst + 1];
   __shared__ int s_kind[kCoopMaxInst];
   __shared__ __align__(8) uint64_t s_bar;
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
 }
 
 constexpr int kStaticSmem =
-    40 * 8 + 3 * kBcrMaxN * 4 + kBcrMaxN * 4 + kBcrWarps * kBcrMaxN * 4 + kCoopMaxInst * 36 + 12 + kBcrMaxTaskSub / 2 * kBcrWarps * 8 + (int)sizeof(BcrInst) + 16 + 64;
+    40 * 8 + 3 * kBcrMaxN * 4 + kBcrMaxN * 4 + kBcrWarps * kBcrMaxN * 4 + kCoopMaxInst * 36 + 12 + kBcrMaxTaskSub / kRangesPerPass * kBcrWarps * 8 + (int)sizeof(BcrInst) + 16 + 64;
 
 }  // namespace
 
