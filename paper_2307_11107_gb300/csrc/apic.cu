@@ -503,12 +503,12 @@ void parallel_for(int n, F f) {
 
 // Layout of instance I's reduction: block size, levels before the dense
 // tail, first block of each kind per level (real rows only).  False if the
-// reduction does not apply (N2 > kBcrMaxN, n1 < 4, n1 > 2^(kBcrMaxK-1)).
+// reduction does not apply (N2 > kBcrMaxNWide, n1 < 4, n1 > 2^(kBcrMaxK-1)).
 bool bcr_layout(const Inst& I, BcrInst& bp, bool dense1) {
   std::memset(&bp, 0, sizeof(bp));
   bp.dense1 = dense1 ? 1 : 0;
   const int N = I.N2, M = I.n1 - 1;
-  if (I.n1 < 4 || N > kBcrMaxN) return false;
+  if (I.n1 < 4 || N > kBcrMaxNWide) return false;
   int K = 0;
   while ((1 << K) < I.n1) ++K;
   if (K >= kBcrMaxK) return false;
@@ -837,7 +837,7 @@ static int setup(apic_sim* S) {
   if (const char* sm = std::getenv("APIC_MG_SMOOTH")) pl.smooth_split = std::string(sm) != "alt";
   if (!S->ck(set_poisson_smem<Real>(pl), "cudaFuncSetAttribute(smem)")) return S->status;
   // Direct block cyclic reduction in place of multigrid: FP32 particles, every
-  // instance with a field, N2 <= kBcrMaxN, the blocks of the batch within the
+  // instance with a field, N2 <= kBcrMaxNWide, the blocks of the batch within the
   // memory budget (APIC_PRECOND=mg keeps multigrid).
   std::vector<BcrInst> bcr_in;
   std::vector<int32_t> bcr_kind, bcr_pre, bcr_npre, bcr_tpre;
@@ -1330,7 +1330,7 @@ static void set_persisting_window(apic_sim* S, const DevPtrs& d, cudaGraph_t g) 
     cudaGraphNodeType t;
     if (cudaGraphNodeGetType(node, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
     cudaKernelNodeParams kp;
-    if (cudaGraphKernelNodeGetParams(node, &kp) != cudaSuccess || kp.func != bcr_kernel()) continue;
+    if (cudaGraphKernelNodeGetParams(node, &kp) != cudaSuccess || kp.func != bcr_kernel(S->plan)) continue;
     cudaKernelNodeAttrValue v;
     std::memset(&v, 0, sizeof(v));
     v.accessPolicyWindow.base_ptr = (void*)d.bcr;

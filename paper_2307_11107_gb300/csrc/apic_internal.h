@@ -247,7 +247,8 @@ void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s);
 // chunks of tail_rows rows; Lt is the fewest levels that bring tail_n under
 // kBcrTailMax.
 constexpr int kBcrMaxK = 13;
-constexpr int kBcrMaxN = 256;
+constexpr int kBcrMaxN = 256;       // blocks up to this size use the narrow solve kernel
+constexpr int kBcrMaxNWide = 544;   // the wide one (17 outputs per lane): grids up to 543 cells in x2
 constexpr int kBcrTailMax = 2048;
 constexpr double kBcrMaxBytes = 24.0 * 1024 * 1024 * 1024;  // FP32 blocks of a whole batch held on the device
 constexpr int kBcrUpdRows = 4;       // level-1 kept rows per update task
@@ -292,7 +293,7 @@ struct BcrPlan {
   int smem;                 // 1: dynamic shared memory holds staged blocks
   int resident;             // 1: the whole reduction fits in L2 (dense level 1, blocks staged in shared memory)
   int dyn;                  // dynamic shared memory bytes of the solve kernel
-  int pad;
+  int wide;                 // 1: some block is larger than kBcrMaxN (the wide kernel)
   int64_t bytes;            // device bytes of all blocks and tail inverses
   int64_t chunks;           // partial-sum ranges of all instances (kBcrSub nodes each)
   int task_sub;             // partial-sum ranges per node task (1..kBcrMaxTaskSub)
@@ -343,7 +344,7 @@ cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& plan, int blocks
 // CTAs of the solve (0: not co-residable); sets each instance's staging flag
 // and tail chunk, and the kernel's shared memory (plan.bcr.smem, plan.bcr.dyn).
 int bcr_configure(SolvePlan& plan, BcrInst* inst, int n_inst, int sms);
-const void* bcr_kernel();  // the solve kernel (to find its graph node)
+const void* bcr_kernel(const SolvePlan& plan);  // the solve kernel (to find its graph node)
 
 // sensitivity window (tangent.cu)
 template <class Real>

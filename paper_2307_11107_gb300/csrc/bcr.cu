@@ -31,7 +31,6 @@ namespace {
 
 constexpr int kBcrThreads = 512;
 constexpr int kBcrWarps = kBcrThreads / 32;
-constexpr int kMC = kBcrMaxN / 32;  // outputs per lane
 constexpr int kTailChunk = 16;      // tail rows per task at most (one per warp)
 constexpr int kUpdRows = kBcrUpdRows;
 constexpr int kRangesPerPass = kBcrThreads / kBcrSub;  // partial-sum ranges a CTA covers at once
@@ -94,13 +93,16 @@ __device__ bool mbar_wait(uint64_t* bar, unsigned parity, int32_t* err) {
 // vectors v_t in shared memory, by the whole CTA: warp w takes the columns
 // w, w + kBcrWarps, ..., lane l the rows l + 32 m; the per-warp partial sums
 // are added in warp order (the result does not depend on scheduling).
-template <int NT, bool kShared>
+// kMC outputs per lane: blocks of up to 32 kMC unknowns.
+template <int NT, bool kShared, int kMC>
 __device__ __forceinline__ void task_mv(const float* const* Mt, const float* const* vt, int N, int Np, float* red,
                                         float* res) {
   // U columns per warp and block are loaded before their products, so that
   // U * NT * kMC loads per lane are in flight when the blocks stream from
-  // global memory
-  constexpr int U = kShared ? 2 : (NT == 1 ? 8 : (NT == 2 ? 4 : 2));
+  // global memory (about 64 values per lane: U = 8 / 4 / 2 for NT = 1 / 2 / 3
+  // with 8 outputs per lane)
+  constexpr int Ug = 64 / (NT * kMC) > 8 ? 8 : (64 / (NT * kMC) < 1 ? 1 : 64 / (NT * kMC));
+  constexpr int U = kShared ? (Ug < 2 ? Ug : 2) : Ug;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float acc[kMC];
 #pragma unroll
@@ -155,7 +157,7 @@ struct Ctx {
 // res = sum_t src_t v_t: the blocks are staged in shared memory by one bulk
 // copy each when the instance's blocks fit, else read from global memory.
 // False on a copy time-out (every thread).
-template <int NT>
+template <int NT, int kMC>
 __device__ bool run_task(Ctx& c, const BcrInst& B, const float* const* src, const float* const* vt) {
   if (B.smem) {
     const unsigned bytes = (unsigned)(B.blk * sizeof(float));
@@ -170,9 +172,9 @@ __device__ bool run_task(Ctx& c, const BcrInst& B, const float* const* src, cons
     const float* Ms[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) Ms[t] = c.sbuf + t * B.blk;
-    task_mv<NT, true>(Ms, vt, B.N, B.Np, c.red, c.sres);
+    task_mv<NT, true, kMC>(Ms, vt, B.N, B.Np, c.red, c.sres);
   } else {
-    task_mv<NT, false>(src, vt, B.N, B.Np, c.red, c.sres);
+    task_mv<NT, false, kMC>(src, vt, B.N, B.Np, c.red, c.sres);
   }
   return true;
 }
@@ -223,7 +225,9 @@ __device__ int task_ranges(const DevPtrs& d, const BcrInst& B, int kind, int l, 
 
 // Task q of kind `kind` at level l of instance k (the whole CTA).  Row r of
 // the reduced right-hand side f and of the correction e is at (r - 1) N.
-__device__ bool run_stage(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int l, int q, float (*sv)[kBcrMaxN]) {
+template <int MAXN>
+__device__ bool run_stage(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int l, int q, float (*sv)[MAXN]) {
+  constexpr int kMC = MAXN / 32;
   const int N = B.N, M = B.M;
   float* f = d.bcr_f + B.foff;
   float* e = d.bcr_e + B.foff;
@@ -237,7 +241,7 @@ __device__ bool run_stage(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, 
       for (int j = threadIdx.x; j < N; j += blockDim.x) sv[0][j] = f[(long long)(kr - 1) * N + j];
       __syncthreads();
       const float* vt[1] = {sv[0]};
-      if (!run_task<1>(c, B, rp, vt)) return false;
+      if (!run_task<1, kMC>(c, B, rp, vt)) return false;
       for (int j = threadIdx.x; j < N; j += blockDim.x) e[(long long)(kr - 1) * N + j] = c.sres[j];
       __syncthreads();
       return true;
@@ -271,7 +275,7 @@ __device__ bool run_stage(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, 
       }
       __syncthreads();
       const float* vt[2] = {sv[0], sv[1]};
-      if (!run_task<2>(c, B, rp, vt)) return false;
+      if (!run_task<2, kMC>(c, B, rp, vt)) return false;
       for (int j = threadIdx.x; j < N; j += blockDim.x) f[(long long)(i - 1) * N + j] -= c.sres[j];
       __syncthreads();
       return true;
@@ -318,7 +322,7 @@ __device__ bool run_stage(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, 
       }
       __syncthreads();
       const float* vt[3] = {sv[0], sv[1], sv[2]};
-      if (!run_task<3>(c, B, rp, vt)) return false;
+      if (!run_task<3, kMC>(c, B, rp, vt)) return false;
       for (int j = threadIdx.x; j < N; j += blockDim.x) {
         e[(long long)(kr - 1) * N + j] = c.sres[j];
         x[(long long)kr * N + j] += (double)c.sres[j];
@@ -345,7 +349,7 @@ __device__ bool run_stage(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, 
       }
       __syncthreads();
       const float* vt[1] = {sv[0]};
-      if (!run_task<1>(c, B, rp, vt)) return false;
+      if (!run_task<1, kMC>(c, B, rp, vt)) return false;
       for (int j = threadIdx.x; j < N; j += blockDim.x) {
         e[(long long)(kr - 1) * N + j] = c.sres[j];
         x[(long long)kr * N + j] += (double)c.sres[j];
@@ -426,12 +430,15 @@ __device__ void node_tasks(const DevPtrs& d, const int* npre, const int* tpre, i
 // kBcrFields = node gradients and surface quantities after the solve.
 // only >= 0: that instance alone is solved (the others keep their phi).  An
 // instance computes the same values alone or in a batch.
+// MAXN: the largest block size of the batch this instantiation handles (256
+// or 544 = 17 x 32, for grids up to 543 cells in x2).
+template <int MAXN>
 __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan pl, int mode, int only) {
   extern __shared__ __align__(128) float s_dyn[];
   __shared__ double sh[40];
-  __shared__ float sv[3][kBcrMaxN];
-  __shared__ float sres[kBcrMaxN];
-  __shared__ float red[kBcrWarps * kBcrMaxN];
+  __shared__ float sv[3][MAXN];
+  __shared__ float sres[MAXN];
+  __shared__ float red[kBcrWarps * MAXN];
   __shared__ double s_bn[kCoopMaxInst];
   __shared__ double s_rn[kCoopMaxInst];
   __shared__ int s_act[kCoopMaxInst];
@@ -539,7 +546,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
         const int k = task_inst_s(s_pre, ni, t);
         if (!s_act[k]) continue;
         const BcrInst& B = k == 0 ? s_b0 : d.bcr_inst[k];
-        if (!run_stage(d, c, B, s_kind[k] >> 8, s_kind[k] & 255, t - s_pre[k], sv)) return;
+        if (!run_stage<MAXN>(d, c, B, s_kind[k] >> 8, s_kind[k] & 255, t - s_pre[k], sv)) return;
       }
       if (p + 1 < pl.phases) load_tab(p + 1);
       if (!grid_sync(d, nb)) return;
@@ -557,19 +564,29 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   }
 }
 
-constexpr int kStaticSmem =
-    40 * 8 + 3 * kBcrMaxN * 4 + kBcrMaxN * 4 + kBcrWarps * kBcrMaxN * 4 + kCoopMaxInst * 36 + 12 + kBcrMaxTaskSub / kRangesPerPass * kBcrWarps * 8 + (int)sizeof(BcrInst) + 16 + 64;
+constexpr int static_smem(int maxn) {
+  return 40 * 8 + 3 * maxn * 4 + maxn * 4 + kBcrWarps * maxn * 4 + kCoopMaxInst * 36 + 12 +
+         kBcrMaxTaskSub / kRangesPerPass * kBcrWarps * 8 + (int)sizeof(BcrInst) + 16 + 64;
+}
+
+const void* kernel_for(const BcrPlan& b) {
+  return b.wide ? (const void*)k_solve_bcr<kBcrMaxNWide> : (const void*)k_solve_bcr<kBcrMaxN>;
+}
 
 }  // namespace
 
-const void* bcr_kernel() { return (const void*)k_solve_bcr; }
+const void* bcr_kernel(const SolvePlan& pl) { return kernel_for(pl.bcr); }
 
 int bcr_configure(SolvePlan& pl, BcrInst* bi, int ni, int sms) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int nb = sms < kCoopMaxBlocks ? sms : kCoopMaxBlocks;
-  const long long budget = (long long)optin - kStaticSmem;
+  int widest = 0;
+  for (int k = 0; k < ni; ++k) widest = bi[k].N > widest ? bi[k].N : widest;
+  pl.bcr.wide = widest > kBcrMaxN ? 1 : 0;
+  const long long budget = (long long)optin - static_smem(pl.bcr.wide ? kBcrMaxNWide : kBcrMaxN);
+  const void* kern = kernel_for(pl.bcr);
   // tail chunks: about one per CTA when the tails are few, else one row per warp
   long long tail_total = 0;
   for (int k = 0; k < ni; ++k) tail_total += bi[k].tail_n;
@@ -597,12 +614,12 @@ int bcr_configure(SolvePlan& pl, BcrInst* bi, int ni, int sms) {
   }
   pl.bcr.smem = any;
   pl.bcr.dyn = (int)dyn;
-  if (cudaFuncSetAttribute(k_solve_bcr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_bcr, kBcrThreads, (size_t)dyn) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBcrThreads, (size_t)dyn) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -615,7 +632,7 @@ cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& pl, int blocks, 
   BcrPlan pp = pl.bcr;
   int mm = mode, oo = only;
   void* args[] = {&dd, &pp, &mm, &oo};
-  return cudaLaunchCooperativeKernel((const void*)k_solve_bcr, dim3(blocks), dim3(kBcrThreads), args,
+  return cudaLaunchCooperativeKernel(kernel_for(pl.bcr), dim3(blocks), dim3(kBcrThreads), args,
                                      (size_t)pl.bcr.dyn, s);
 }
 

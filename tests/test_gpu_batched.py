@@ -66,14 +66,15 @@ def test_batch_equals_solo(prec, solver, monkeypatch):
 
 def test_batched_reduction_poisson_matches_banded_lu():
     """Every instance of an uneven FP32 batch (different alpha and grid, n1
-    a power of two or not) solved by the batched block cyclic reduction
-    against the oracle's banded LU; solving one instance leaves the others'
-    potential alone."""
+    a power of two or not, one instance wider than 256 unknowns per row, so
+    the wide kernel runs the narrow ones too) solved by the batched block
+    cyclic reduction against the oracle's banded LU; solving one instance
+    leaves the others' potential alone."""
     import oracle
     import paper_2307_11107_gb300 as apic
     from tests.inputs import random_rho
     apic.build()
-    grids = [(64, 32, 0.1), (96, 48, 0.2), (160, 80, -0.24), (256, 128, 0.15)]
+    grids = [(64, 32, 0.1), (96, 48, 0.2), (160, 80, -0.24), (256, 128, 0.15), (32, 300, 0.05)]
     cfgs = [workload(n1=a, n2=b, alpha=al, x1_out=-0.05, n_init=1000, precision="fp32", poisson_tol=1e-12,
                      poisson_max_iter=60, instance=k) for k, (a, b, al) in enumerate(grids)]
     s = apic.Sim(cfgs)

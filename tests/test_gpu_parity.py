@@ -43,11 +43,13 @@ def test_poisson_fp64_matches_banded_lu(apic, alpha, grid):
 
 
 @pytest.mark.parametrize("alpha,grid", [(0.15, (256, 128)), (0.225, (256, 128)), (0.15, (96, 48)),
-                                        (0.225, (288, 144)), (-0.24, (160, 80))])
+                                        (0.225, (288, 144)), (-0.24, (160, 80)), (0.15, (64, 300)),
+                                        (0.225, (32, 512))])
 def test_poisson_fp32_refined_matches_banded_lu(apic, alpha, grid):
     """FP32 block cyclic reduction inside the FP64 residual loop reaches the
     FP64 solution, for n1 a power of two and not (rows beyond n1 - 1 padded
-    with a zero correction)."""
+    with a zero correction), and for blocks wider than 256 unknowns (the
+    wide kernel, 17 outputs per lane)."""
     n1, n2 = grid
     cfg = workload(n1=n1, n2=n2, alpha=alpha, x1_out=-0.05, n_init=1000, precision="fp32",
                    poisson_tol=1e-12, poisson_max_iter=60)
