@@ -789,7 +789,7 @@ static int setup(apic_sim* S) {
       P.species = s;
       int lg = bits_for(sp.capacity);
       if (sizeof(Real) == 8) P.fbits = 62 - lg;
-      else P.fbits = 2 * std::min(20, (62 - lg) / 2);
+      else P.fbits = 2 * std::min(16, (62 - lg) / 2);  // 16-bit cell fractions (the push's packed moments)
       P.dep_scale = sp.q * P.w * std::ldexp(1.0, -P.fbits);
       P.acc_off = 2 * I.node_off + (long long)s * I.nodes;
       P.cells = c.n1;  // sort bins: the grid rows of this population

@@ -26,6 +26,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPushItems = 8;    // particles per thread per chunk
+constexpr int kFlushChunks = 31;  // chunks (of 2048 particles) between window flushes at most
 constexpr int kWinRows = 8;      // node rows of the shared-memory deposit window at most
 constexpr int kWinMaxN2 = 513;   // widest grid row the window holds (larger grids deposit globally)
 constexpr int kInjRows = 3;      // node rows of the injection window (the last two cell rows)
@@ -50,7 +51,7 @@ __device__ __forceinline__ W4 weights(const Cell& c, int F) {
   } else {
     int b = F >> 1;
     unsigned one = 1u << b;
-    unsigned q1 = (unsigned)((float)c.f1 * (float)one), q2 = (unsigned)((float)c.f2 * (float)one);
+    unsigned q1 = (unsigned)((float)c.f1 * (float)one + 0.5f), q2 = (unsigned)((float)c.f2 * (float)one + 0.5f);
     q1 = q1 > one ? one : q1;
     q2 = q2 > one ? one : q2;
     w.w00 = (unsigned long long)(one - q1) * (one - q2);
@@ -124,14 +125,15 @@ __device__ __forceinline__ void deposit_lane(const Window& W, int ci, int cj, co
   if (active) add4(W, ci, cj, w.w00, w.w10, w.w01, w.w11);
 }
 
-// FP32 deposit through cell moments.  With fractions quantised to b bits
-// (S = 2^b) the four corner weights of a particle are (S-q1)(S-q2),
+// FP32 deposit through cell moments.  With fractions quantised to b = 16
+// bits (S = 2^16, rounded to nearest; an FP32 position resolves about 2^-16
+// of a cell anyway) the four corner weights of a particle are (S-q1)(S-q2),
 // q1(S-q2), (S-q1)q2, q1 q2: linear in the moments (1, q1, q2, q1 q2), so a
 // cell accumulates only those, packed in two words (q1 << 32 | q2, and
-// q1 q2 + 2^52), and the corner weights of all its particles follow exactly
-// from the sums at the flush.  Within a chunk of at most 2048 particles the
-// fields cannot carry into each other (sum q1 <= 2^31, sum q1 q2 < 2^52,
-// count < 2^12).
+// q1 q2 + 2^48), and the corner weights of all its particles follow exactly
+// from the sums at the flush.  For at most 65535 particles in a cell between
+// flushes the fields cannot carry into each other (sum q2 < 2^32, sum q1 q2
+// < 2^48, count < 2^16): kFlushChunks chunks of 2048 particles.
 struct CellWin {
   unsigned long long* s;  // shared [rows * n2 * 2]
   unsigned long long* g;  // global node accumulator of the population (node 0)
@@ -140,7 +142,7 @@ struct CellWin {
 
 __device__ __forceinline__ void corner_weights(unsigned long long a, unsigned long long m, unsigned S,
                                                unsigned long long w[4]) {
-  const unsigned long long n = m >> 52, s12 = m & ((1ull << 52) - 1ull), s1 = a >> 32, s2 = a & 0xffffffffull;
+  const unsigned long long n = m >> 48, s12 = m & ((1ull << 48) - 1ull), s1 = a >> 32, s2 = a & 0xffffffffull;
   const unsigned long long SS = (unsigned long long)S * S;
   w[0] = n * SS - (unsigned long long)S * (s1 + s2) + s12;
   w[1] = (unsigned long long)S * s1 - s12;
@@ -179,9 +181,9 @@ __device__ __forceinline__ void deposit_moments(const CellWin& W, int key, int c
     unsigned lo = __reduce_add_sync(kFull, (unsigned)(p12 & 0xffffffu));
     unsigned hi = __reduce_add_sync(kFull, (unsigned)(p12 >> 24));
     if ((threadIdx.x & 31) == 0)
-      cell_add(W, ci, cj, (s1 << 32) | s2, ((unsigned long long)hi << 24) + lo + (32ull << 52), S);
+      cell_add(W, ci, cj, (s1 << 32) | s2, ((unsigned long long)hi << 24) + lo + (32ull << 48), S);
   } else if (active) {
-    cell_add(W, ci, cj, ((unsigned long long)q1 << 32) | q2, p12 + (1ull << 52), S);
+    cell_add(W, ci, cj, ((unsigned long long)q1 << 32) | q2, p12 + (1ull << 48), S);
   }
 }
 
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
   const int win_words = kF64 ? win_rows * (win_n2 + 1) : 2 * win_rows * win_n2;
   long long* s_pre = (long long*)(s_win + win_words);
   PushConst* s_pc = (PushConst*)(s_pre + d.n_pop + 1);
-  __shared__ int s_row0;
+  __shared__ int s_row0, s_wpop, s_nsince, s_newrow0, s_flush;
   __shared__ unsigned s_rowmask;  // FP32 window: cell rows that received moments in this chunk
   const long long CH = (long long)kPushItems * blockDim.x;
   if (threadIdx.x == 0) {
@@ -291,7 +293,71 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
   Real* VZ = (Real*)d.vZ;
   Real* VT = (Real*)d.vT;
   const Real2* G = (const Real2*)d.G;
-  for (long long chunk = blockIdx.x; chunk < total_chunks; chunk += gridDim.x) {
+  // Flush of the window (population wp, node rows from row0) to the global
+  // accumulator, and its clearing.
+  auto flush = [&](int wp, int row0) {
+    const PushConst& Cw = s_pc[wp];
+    const int rows = Cw.n2 <= win_n2 ? win_rows : 0;
+    unsigned long long* g = d.acc + Cw.acc_off;
+    if (kF64) {
+      for (int e = threadIdx.x; e < rows * Cw.N2; e += blockDim.x) {
+        unsigned long long v = s_win[e];
+        if (v) {
+          atomicAdd(g + (long long)(row0 + e / Cw.N2) * Cw.N2 + e % Cw.N2, v);
+          s_win[e] = 0ull;
+        }
+      }
+    } else {
+      // node (ni, nj) of rows row0..row0+rows gathers w00 of cell (ni, nj),
+      // w10 of (ni-1, nj), w01 of (ni, nj-1) and w11 of (ni-1, nj-1)
+      // (only the node rows next to the cell rows that received moments)
+      const unsigned S = 1u << (Cw.fbits >> 1);
+      const unsigned cm = s_rowmask;
+      const unsigned nm = cm | (cm << 1);  // node rows rr with cell row rr or rr - 1 in use
+      const int nrows = __popc(nm);
+      for (int e = threadIdx.x; e < nrows * Cw.N2; e += blockDim.x) {
+        const int q = e / Cw.N2, nj = e - q * Cw.N2;
+        unsigned mm = nm;
+        for (int z = 0; z < q; ++z) mm &= mm - 1u;
+        const int rr = __ffs(mm) - 1;  // the q-th node row in use
+        unsigned long long v = 0, w[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int cr = rr - (t & 1), cj = nj - (t >> 1);
+          if (cr < 0 || cr >= rows || !((cm >> cr) & 1u) || cj < 0 || cj >= Cw.n2) continue;
+          const unsigned long long* c = s_win + 2 * (cr * Cw.n2 + cj);
+          if (c[1] == 0ull) continue;
+          corner_weights(c[0], c[1], S, w);
+          v += w[t];  // t = 0: w00 (own cell), 1: w10 (cell below in x1), 2: w01, 3: w11
+        }
+        if (v) atomicAdd(g + (long long)(row0 + rr) * Cw.N2 + nj, v);
+      }
+      __syncthreads();
+      const int crows = __popc(cm);
+      for (int e = threadIdx.x; e < 2 * crows * Cw.n2; e += blockDim.x) {
+        const int q = e / (2 * Cw.n2), o = e - q * 2 * Cw.n2;
+        unsigned mm = cm;
+        for (int z = 0; z < q; ++z) mm &= mm - 1u;
+        s_win[2 * (__ffs(mm) - 1) * Cw.n2 + o] = 0ull;
+      }
+    }
+    __syncthreads();
+  };
+  // This CTA's chunks are a contiguous range of the sorted particles (few
+  // grid rows), deposited into one window that is flushed only when a chunk's
+  // rows or population leave it, or after kFlushChunks chunks: the global
+  // atomics of the flushes, which all CTAs working on one grid row send to
+  // the same addresses, are what the window saves.
+  const long long per = (total_chunks + gridDim.x - 1) / gridDim.x;
+  const long long cbeg = (long long)blockIdx.x * per;
+  const long long cend = cbeg + per < total_chunks ? cbeg + per : total_chunks;
+  if (threadIdx.x == 0) {
+    s_wpop = -1;
+    s_nsince = 0;
+    s_rowmask = 0u;
+  }
+  __syncthreads();
+  for (long long chunk = cbeg; chunk < cend; ++chunk) {
    const int pop = find_pop(s_pre, d.n_pop, chunk);
    // by value: the constants stay in registers instead of being reloaded from
    // shared memory around every window atomic
@@ -307,8 +373,23 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
          break;
        }
      }
-     s_row0 = row > 0 ? row - 1 : 0;
-     s_rowmask = 0u;
+     const int r0 = row > 0 ? row - 1 : 0;
+     const int rows = C.n2 <= win_n2 ? win_rows : 0;
+     // keep the window while this chunk's first rows lie inside it
+     const bool keep = s_wpop == pop && s_nsince < kFlushChunks && r0 >= s_row0 && r0 + 2 < s_row0 + rows;
+     s_flush = s_wpop >= 0 && !keep;
+     s_newrow0 = keep ? s_row0 : r0;
+   }
+   __syncthreads();
+   if (s_flush) flush(s_wpop, s_row0);
+   if (threadIdx.x == 0) {
+     if (s_row0 != s_newrow0 || s_wpop != pop || s_flush) {
+       s_row0 = s_newrow0;
+       s_wpop = pop;
+       s_rowmask = 0u;
+       s_nsince = 0;
+     }
+     s_nsince += 1;
    }
    __syncthreads();
    Window W;
@@ -419,8 +500,8 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
           int ni = min(max((int)floorf(v1), 0), C.n1 - 1), nj = min(max((int)floorf(v2), 0), C.n2 - 1);
           float e1 = fminf(fmaxf(v1 - (float)ni, 0.0f), 1.0f), e2 = fminf(fmaxf(v2 - (float)nj, 0.0f), 1.0f);
           const float one = (float)(1u << (C.fbits >> 1));
-          q1 = min((unsigned)(e1 * one), 1u << (C.fbits >> 1));
-          q2 = min((unsigned)(e2 * one), 1u << (C.fbits >> 1));
+          q1 = min((unsigned)(e1 * one + 0.5f), 1u << (C.fbits >> 1));
+          q2 = min((unsigned)(e2 * one + 0.5f), 1u << (C.fbits >> 1));
           key = ni * C.N2 + nj;
           di = ni;
           dj = nj;
@@ -518,51 +599,8 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
     }
    }
    __syncthreads();
-   // flush the window and clear it for the next chunk
-   if (kF64) {
-     for (int e = threadIdx.x; e < W.rows * W.N2; e += blockDim.x) {
-       unsigned long long v = s_win[e];
-       if (v) {
-         atomicAdd(W.g + (long long)(W.row0 + e / W.N2) * W.N2 + e % W.N2, v);
-         s_win[e] = 0ull;
-       }
-     }
-   } else {
-     // node (ni, nj) of rows row0..row0+rows gathers w00 of cell (ni, nj),
-     // w10 of (ni-1, nj), w01 of (ni, nj-1) and w11 of (ni-1, nj-1)
-     // (only the node rows next to the cell rows that received moments)
-     const unsigned S = 1u << (C.fbits >> 1);
-     const unsigned cm = s_rowmask;
-     const unsigned nm = cm | (cm << 1);  // node rows rr with cell row rr or rr - 1 in use
-     const int nrows = __popc(nm);
-     for (int e = threadIdx.x; e < nrows * CW.N2; e += blockDim.x) {
-       const int q = e / CW.N2, nj = e - q * CW.N2;
-       unsigned mm = nm;
-       for (int z = 0; z < q; ++z) mm &= mm - 1u;
-       const int rr = __ffs(mm) - 1;  // the q-th node row in use
-       unsigned long long v = 0, w[4];
-#pragma unroll
-       for (int t = 0; t < 4; ++t) {
-         const int cr = rr - (t & 1), cj = nj - (t >> 1);
-         if (cr < 0 || cr >= CW.rows || !((cm >> cr) & 1u) || cj < 0 || cj >= CW.n2) continue;
-         const unsigned long long* c = s_win + 2 * (cr * CW.n2 + cj);
-         if (c[1] == 0ull) continue;
-         corner_weights(c[0], c[1], S, w);
-         v += w[t];  // t = 0: w00 (own cell), 1: w10 (cell below in x1), 2: w01, 3: w11
-       }
-       if (v) atomicAdd(CW.g + (long long)(CW.row0 + rr) * CW.N2 + nj, v);
-     }
-     __syncthreads();
-     const int crows = __popc(cm);
-     for (int e = threadIdx.x; e < 2 * crows * CW.n2; e += blockDim.x) {
-       const int q = e / (2 * CW.n2), o = e - q * 2 * CW.n2;
-       unsigned mm = cm;
-       for (int z = 0; z < q; ++z) mm &= mm - 1u;
-       s_win[2 * (__ffs(mm) - 1) * CW.n2 + o] = 0ull;
-     }
-   }
-   __syncthreads();
   }
+  if (s_wpop >= 0) flush(s_wpop, s_row0);
 }
 
 // Deposit every live particle (after external changes to the particle set).
