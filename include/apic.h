@@ -216,12 +216,13 @@ int apic_step_timed(apic_sim* sim, int32_t n_steps);
 /* ---- Autotuning ------------------------------------------------------------
  * The particle sort's interval trades the sort's cost against the push's
  * locality (the push deposits through a shared-memory window of grid rows,
- * which works best on recently sorted particles).  apic_autotune runs
- * steps_per_trial full steps with each of APIC_TUNE_CANDIDATES intervals
- * (2, 4, 6, 8, 12, 16, 24; every trial starts with a sort), timed with CUDA
- * events on the simulation's stream, and keeps the fastest for the following
- * steps.  The simulation advances by APIC_TUNE_CANDIDATES * steps_per_trial
- * steps (results as apic_step).  Without sorting (sort_interval = 0 at
+ * which works best on recently sorted particles).  apic_autotune runs, for
+ * each of APIC_TUNE_CANDIDATES intervals c (2, 4, 6, 8, 12, 16, 24), whole
+ * sort intervals: c * ceil(steps_per_trial / c) full steps, each interval
+ * starting with a sort, timed with CUDA events on the simulation's stream,
+ * and keeps the interval with the least time per step for the following
+ * steps.  The simulation advances by the sum of those step counts (results
+ * as apic_step).  Without sorting (sort_interval = 0 at
  * creation) nothing runs and 0 is returned in *sort_interval.
  * ms_per_step: [APIC_TUNE_CANDIDATES] host array (or NULL) for the measured
  * times.  Errors: INVALID_ARG (NULL sort_interval, steps_per_trial < 1),

@@ -1510,8 +1510,11 @@ static int autotune_impl(apic_sim* S, int trial, int32_t* chosen, double* ms_out
   int best_c = S->sort_interval;
   for (int q = 0; q < APIC_TUNE_CANDIDATES && S->status == APIC_OK; ++q) {
     const int c = kTuneIntervals[q];
+    // whole sort intervals: a trial shorter than the interval would time only
+    // the freshly sorted steps and favour long intervals
+    const int n = c * ((trial + c - 1) / c);
     S->ck(cudaEventRecord(a, S->stream), "event record");
-    for (int k = 0; k < trial; ++k) {
+    for (int k = 0; k < n; ++k) {
       if (k % c == 0) {
         if (!S->ck(cudaGraphLaunch(S->sort_exec[S->par], S->stream), "sort launch")) break;
         S->par ^= 1;
@@ -1524,7 +1527,7 @@ static int autotune_impl(apic_sim* S, int trial, int32_t* chosen, double* ms_out
     if (!S->ck(cudaEventSynchronize(b), "event sync")) break;
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, a, b);
-    const double per = (double)ms / trial;
+    const double per = (double)ms / n;
     if (ms_out) ms_out[q] = per;
     if (per < best) {
       best = per;

@@ -107,7 +107,8 @@ def test_autotune_keeps_a_candidate_and_stepping_stays_valid():
     s.step(5)
     for k in range(len(cfgs)):
         t = s.tallies(k)
-        assert t["step"] == 4 + 4 * len(ms) + 5
+        # each candidate runs whole intervals: c * ceil(4 / c) steps
+        assert t["step"] == 4 + sum(c * -(-4 // c) for c in ms) + 5
         for sp in (0, 1):
             cnt = t["counts"][sp]
             assert cnt["resident"] == s.particles(sp, instance=k).shape[0]
