@@ -37,7 +37,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--particles", type=int, default=None,
                     help="macro-particles per species (default: the workload's own count)")
-    ap.add_argument("--workload", default="dipole256", choices=["dipole256", "dipole1024", "batched48", "sphere64"])
+    ap.add_argument("--workload", default="dipole256",
+                    choices=["dipole256", "dipole1024", "batched48", "sphere64", "window"],
+                    help="window: the sensitivity window (forward-mode derivatives along alpha, phi_g, B) on the "
+                         "256x128 dipole, 1e6 particles per species, K = 10 steps per window")
     ap.add_argument("--instances", type=int, default=None,
                     help="batched48 only: the first N instances (smaller runs, e.g. under a profiler)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -213,10 +216,56 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def window_bench(args):
+    """Sensitivity window (apic_sensitivity): the 256x128 dipole with 1e6
+    macro-particles per species (or --particles), K = 10 steps per window,
+    --steps windows timed with CUDA events after --warmup plain steps.  The
+    value is the particle-steps advanced inside the windows per second."""
+    import torch
+    import paper_2307_11107_gb300 as apic
+    from paper_2307_11107_gb300 import workloads as W
+    apic.build()
+    torch.cuda.set_device(0)
+    K = 10
+    cfg = W.dipole_256("fp32")
+    n = args.particles or 1_000_000
+    cfg["species"] = [dict(sp, n_init=n) for sp in cfg["species"]]
+    cfg["history_cap"] = max(4096, (args.steps + 1) * K + args.warmup + 8)
+    sim = apic.Sim(cfg)
+    for sp in range(2):
+        sim.load_volume(sp, n)
+    sim.step(args.warmup)
+    sim.sensitivity(2)  # tangent set-up outside the timed region
+    stream = torch.cuda.current_stream()
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sim.sensitivity(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    hist = sim.tallies()["history"]
+    steps = args.steps * K
+    advanced = float((hist[-(steps + 1):-1, 7] + hist[-(steps + 1):-1, 8]).sum())
+    line = {"metric": METRIC, "value": advanced / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sensitivity_window_256x128_2e6_K10", "window_steps": K, "windows": args.steps,
+                       "particles_per_species": n, "parameters": ["alpha", "phi_g", "B"],
+                       "outputs": ["drag F_Z", "electric F_Z", "current", "torque T_z", "grain charge Q"],
+                       "precision": "FP32 particles and tangents; Poisson: " + sim.stats()["solver"]},
+            "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "window":
+        return window_bench(args)
     assert args.warmup >= 3, "at least 3 warm-up steps"
     import numpy as np
     import torch
