@@ -1383,7 +1383,7 @@ static bool redeposit(apic_sim* S) {
   if (!S->dirty) return true;
   if (!S->ck(cudaMemsetAsync(S->d.acc, 0, sizeof(unsigned long long) * 2 * S->d.total_nodes, S->stream), "memset"))
     return false;
-  launch_deposit_all<Real>(S->view(S->par), S->push_grid, S->stream);
+  launch_deposit_all<Real>(S->view(S->par), S->push_grid, S->max_n2, S->stream);
   S->dirty = false;
   return true;
 }
@@ -1865,9 +1865,9 @@ static int sensitivity_impl(apic_sim* S, int n, double* values, double* jac) {
   for (int k = 0; k < n && S->status == APIC_OK; ++k) {
     // deposit of every particle (values and derivatives), charge density
     S->ck(cudaMemsetAsync(d.acc, 0, sizeof(unsigned long long) * 2 * tn, s), "memset");
-    launch_deposit_all<Real>(d, S->push_grid, s);
+    launch_deposit_all<Real>(d, S->push_grid, S->max_n2, s);
     S->ck(cudaMemsetAsync(t.drho, 0, sizeof(double) * kNPar * tn, s), "memset");
-    launch_tan_deposit<Real>(d, t, S->push_grid, s);
+    launch_tan_deposit<Real>(d, t, S->push_grid, S->max_n2, s);
     launch_rho<Real>(d, s);
     launch_tan_rho(d, t, s);
     // Poisson: the step's problem, then the three tangent problems

@@ -202,7 +202,7 @@ template <class Real>
 void launch_explicit(const DevPtrs& d, int pop, long long n0, long long count, const double* dstate,
                      cudaStream_t s);
 template <class Real>
-void launch_deposit_all(const DevPtrs& d, int max_grid, cudaStream_t s);
+void launch_deposit_all(const DevPtrs& d, int max_grid, int max_n2, cudaStream_t s);
 template <class Real>
 void launch_push(const DevPtrs& d, int grid, int max_n2, cudaStream_t s);
 // Node rows of the push's shared-memory deposit window for grids up to max_n2
@@ -348,7 +348,7 @@ const void* bcr_kernel(const SolvePlan& plan);  // the solve kernel (to find its
 
 // sensitivity window (tangent.cu)
 template <class Real>
-void launch_tan_deposit(const DevPtrs& d, const TanPtrs& t, int grid, cudaStream_t s);
+void launch_tan_deposit(const DevPtrs& d, const TanPtrs& t, int grid, int max_n2, cudaStream_t s);
 template <class Real>
 void launch_tan_push(const DevPtrs& d, const TanPtrs& t, int grid, cudaStream_t s);
 template <class Real>

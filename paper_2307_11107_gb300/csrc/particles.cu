@@ -603,9 +603,18 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
   if (s_wpop >= 0) flush(s_wpop, s_row0);
 }
 
-// Deposit every live particle (after external changes to the particle set).
-__global__ void __launch_bounds__(256) k_deposit_all(DevPtrs d) {
+// Deposit every live particle (after external changes to the particle set,
+// and in every step of the sensitivity window).  Each CTA takes a contiguous
+// range of the (row-sorted) particles in chunks of kDepItems x blockDim and
+// adds the corner weights into a shared-memory window of kWinRows node rows
+// of one population, flushed to the global accumulator only when a chunk's
+// first row or population leaves it; corners outside the window go to global
+// memory directly.  Integer sums: the result does not depend on the order.
+constexpr int kDepItems = 8;
+__global__ void __launch_bounds__(256) k_deposit_all(DevPtrs d, int win_n2) {
+  extern __shared__ unsigned long long s_dw[];  // [kWinRows][win_n2 + 1]
   __shared__ long long s_pre[kMaxPop + 1];
+  __shared__ int s_row0, s_wpop, s_newrow0, s_newpop, s_flush;
   if (threadIdx.x == 0) {
     long long a = 0;
     for (int p = 0; p < d.n_pop; ++p) {
@@ -613,29 +622,90 @@ __global__ void __launch_bounds__(256) k_deposit_all(DevPtrs d) {
       a += d.ps[p].n;
     }
     s_pre[d.n_pop] = a;
+    s_wpop = -1;
   }
+  const int WN = win_n2 + 1;
+  for (int k = threadIdx.x; k < kWinRows * WN; k += blockDim.x) s_dw[k] = 0ull;
   __syncthreads();
   const long long total = s_pre[d.n_pop];
   const Real* X1 = (const Real*)d.x1;
   const Real* X2 = (const Real*)d.x2;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
-    long long t = base + (threadIdx.x & 31);
-    bool active = t < total;
-    int pop = active ? find_pop(s_pre, d.n_pop, t) : 0;
-    const Pop& P = d.pop[pop];
+  const long long CH = (long long)kDepItems * blockDim.x;
+  const long long nch = (total + CH - 1) / CH;
+  const long long per = (nch + gridDim.x - 1) / gridDim.x;
+  const long long cb = (long long)blockIdx.x * per, ce = cb + per < nch ? cb + per : nch;
+  auto flush = [&](int wp, int row0) {
+    const Pop& P = d.pop[wp];
     const Inst& I = d.inst[P.inst];
-    long long slot = P.base + (active ? t - s_pre[pop] : 0);
-    Real x1 = active ? X1[slot] : Real(2);
-    long long key = -1;
-    W4 w = {0, 0, 0, 0};
-    if (active && x1 < Real(0)) {
-      Cell c = locate(I, x1, X2[slot]);
-      key = dep_key(I, P, c);
-      w = weights(c, P.fbits);
+    const int rows = I.n2 <= win_n2 ? kWinRows : 0;
+    unsigned long long* g = d.acc + P.acc_off;
+    for (int e = threadIdx.x; e < rows * I.N2; e += blockDim.x) {
+      const int r = e / I.N2, j = e - r * I.N2;
+      const unsigned long long v = s_dw[r * WN + j];
+      if (v && row0 + r <= I.n1) {
+        atomicAdd(g + (long long)(row0 + r) * I.N2 + j, v);
+        s_dw[r * WN + j] = 0ull;
+      }
     }
-    deposit_warp_global(d.acc, key, w, active ? I.N2 : 1, key >= 0);
+    __syncthreads();
+  };
+  for (long long ch = cb; ch < ce; ++ch) {
+    const long long t0 = ch * CH;
+    if (threadIdx.x == 0) {
+      // window rows from the chunk's first live particle
+      int pop = find_pop(s_pre, d.n_pop, t0), row = 0;
+      for (long long q = t0; q < t0 + 64 && q < total; ++q) {
+        const int pq = find_pop(s_pre, d.n_pop, q);
+        const Real xq = X1[d.pop[pq].base + (q - s_pre[pq])];
+        if (xq < Real(0)) {
+          pop = pq;
+          row = (int)floor((double)((xq + Real(1)) / (Real)d.inst[d.pop[pq].inst].h1));
+          break;
+        }
+      }
+      const int r0 = row > 0 ? row - 1 : 0;
+      const bool keep = s_wpop == pop && r0 >= s_row0 && r0 + 2 < s_row0 + kWinRows;
+      s_flush = s_wpop >= 0 && !keep;
+      s_newrow0 = keep ? s_row0 : r0;
+      s_newpop = pop;
+    }
+    __syncthreads();
+    if (s_flush) flush(s_wpop, s_row0);
+    if (threadIdx.x == 0) {
+      s_row0 = s_newrow0;
+      s_wpop = s_newpop;
+    }
+    __syncthreads();
+    const int wpop = s_wpop, row0 = s_row0;
+    for (int it = 0; it < kDepItems; ++it) {
+      const long long t = t0 + (long long)it * blockDim.x + threadIdx.x;
+      if (t >= total) break;
+      const int pop = find_pop(s_pre, d.n_pop, t);
+      const Pop& P = d.pop[pop];
+      const Inst& I = d.inst[P.inst];
+      const long long slot = P.base + (t - s_pre[pop]);
+      const Real x1 = X1[slot];
+      if (!(x1 < Real(0))) continue;
+      const Cell c = locate(I, x1, X2[slot]);
+      const W4 w = weights(c, P.fbits);
+      const int rr = c.i - row0;
+      if (pop == wpop && I.n2 <= win_n2 && rr >= 0 && rr + 1 < kWinRows) {
+        unsigned long long* sw = s_dw + rr * WN + c.j;
+        if (w.w00) atomicAdd(sw, w.w00);
+        if (w.w10) atomicAdd(sw + WN, w.w10);
+        if (w.w01) atomicAdd(sw + 1, w.w01);
+        if (w.w11) atomicAdd(sw + WN + 1, w.w11);
+      } else {
+        unsigned long long* g = d.acc + dep_key(I, P, c);
+        if (w.w00) atomicAdd(g, w.w00);
+        if (w.w10) atomicAdd(g + I.N2, w.w10);
+        if (w.w01) atomicAdd(g + 1, w.w01);
+        if (w.w11) atomicAdd(g + I.N2 + 1, w.w11);
+      }
+    }
+    __syncthreads();
   }
+  if (s_wpop >= 0) flush(s_wpop, s_row0);
 }
 
 // Initial load, uniform in physical volume: x2 from the inverse CDF of
@@ -1043,8 +1113,11 @@ void launch_explicit<Real>(const DevPtrs& d, int pop, long long n0, long long co
 }
 
 template <>
-void launch_deposit_all<Real>(const DevPtrs& d, int max_grid, cudaStream_t s) {
-  k_deposit_all<<<max_grid, 256, 0, s>>>(d);
+void launch_deposit_all<Real>(const DevPtrs& d, int max_grid, int max_n2, cudaStream_t s) {
+  const int win_n2 = max_n2 < kWinMaxN2 - 1 ? max_n2 : kWinMaxN2 - 1;
+  const int sm = kWinRows * (win_n2 + 1) * (int)sizeof(unsigned long long);
+  cudaFuncSetAttribute(k_deposit_all, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  k_deposit_all<<<max_grid, 256, sm, s>>>(d, win_n2);
 }
 
 // Dynamic shared memory of the push: window, chunk prefix, population constants.

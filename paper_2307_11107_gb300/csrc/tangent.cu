@@ -120,36 +120,107 @@ __device__ __forceinline__ void pop_prefix(const DevPtrs& d, long long* pre) {
 }
 
 // d rho (before the division by the node volume): sum over live particles of
-// q w dW for the four cloud-in-cell corners, per parameter.
-__global__ void __launch_bounds__(256) k_tan_deposit(DevPtrs d, TanPtrs t) {
+// q w dW for the four cloud-in-cell corners, per parameter.  Each CTA takes a
+// contiguous range of the (row-sorted) particles in chunks and adds into a
+// shared-memory window of `rows` node rows of one population ([kNPar][rows]
+// [win_n2 + 1] doubles), flushed to global memory when a chunk's first row or
+// population leaves it; corners outside the window go to global memory.
+constexpr int kTanDepItems = 8;
+__global__ void __launch_bounds__(256) k_tan_deposit(DevPtrs d, TanPtrs t, int win_n2, int rows) {
+  extern __shared__ double s_tw[];
   __shared__ long long s_pre[kMaxPop + 1];
+  __shared__ int s_row0, s_wpop, s_newrow0, s_newpop, s_flush;
   pop_prefix(d, s_pre);
+  const int WN = win_n2 + 1, plane = rows * WN;
+  for (int k = threadIdx.x; k < kNPar * plane; k += blockDim.x) s_tw[k] = 0.0;
+  if (threadIdx.x == 0) s_wpop = -1;
+  __syncthreads();
   const long long total = s_pre[d.n_pop];
   const Real* X1 = (const Real*)d.x1;
   const Real* X2 = (const Real*)d.x2;
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-       k += (long long)gridDim.x * blockDim.x) {
-    int pop = find_pop(s_pre, d.n_pop, k);
-    const Pop& P = d.pop[pop];
-    const Inst& I = d.inst[P.inst];
-    long long slot = P.base + (k - s_pre[pop]);
-    Real x1v = X1[slot];
-    if (!(x1v < Real(0))) continue;
-    D x1 = load_d(t, x1v, 0, slot), x2 = load_d(t, X2[slot], 1, slot);
-    CellD c = locate_d(I, x1, x2);
-    D g1 = Real(1) - c.f1, g2 = Real(1) - c.f2;
-    D w00 = g1 * g2, w10 = c.f1 * g2, w01 = g1 * c.f2, w11 = c.f1 * c.f2;
-    long long n00 = I.node_off + (long long)c.i * I.N2 + c.j;
-    double qw = P.q * P.w;
-#pragma unroll
-    for (int p = 0; p < kNPar; ++p) {
-      double* r = t.drho + (long long)p * d.total_nodes;
-      if (w00.d[p] != Real(0)) atomicAdd(r + n00, qw * (double)w00.d[p]);
-      if (w10.d[p] != Real(0)) atomicAdd(r + n00 + I.N2, qw * (double)w10.d[p]);
-      if (w01.d[p] != Real(0)) atomicAdd(r + n00 + 1, qw * (double)w01.d[p]);
-      if (w11.d[p] != Real(0)) atomicAdd(r + n00 + I.N2 + 1, qw * (double)w11.d[p]);
+  const long long CH = (long long)kTanDepItems * blockDim.x;
+  const long long nch = (total + CH - 1) / CH;
+  const long long per = (nch + gridDim.x - 1) / gridDim.x;
+  const long long cb = (long long)blockIdx.x * per, ce = cb + per < nch ? cb + per : nch;
+  auto flush = [&](int wp, int row0) {
+    const Inst& I = d.inst[d.pop[wp].inst];
+    const int nr = I.n2 <= win_n2 ? rows : 0;
+    for (int e = threadIdx.x; e < kNPar * nr * I.N2; e += blockDim.x) {
+      const int p = e / (nr * I.N2), rem = e - p * nr * I.N2, r = rem / I.N2, j = rem - r * I.N2;
+      double* sw = s_tw + p * plane + r * WN + j;
+      if (*sw != 0.0 && row0 + r <= I.n1) {
+        atomicAdd(t.drho + (long long)p * d.total_nodes + I.node_off + (long long)(row0 + r) * I.N2 + j, *sw);
+        *sw = 0.0;
+      }
     }
+    __syncthreads();
+  };
+  for (long long ch = cb; ch < ce; ++ch) {
+    const long long t0 = ch * CH;
+    if (threadIdx.x == 0) {
+      int pop = find_pop(s_pre, d.n_pop, t0), row = 0;
+      for (long long q = t0; q < t0 + 64 && q < total; ++q) {
+        const int pq = find_pop(s_pre, d.n_pop, q);
+        const Real xq = X1[d.pop[pq].base + (q - s_pre[pq])];
+        if (xq < Real(0)) {
+          pop = pq;
+          row = (int)floor((double)((xq + Real(1)) / (Real)d.inst[d.pop[pq].inst].h1));
+          break;
+        }
+      }
+      const int r0 = row > 0 ? row - 1 : 0;
+      const bool keep = s_wpop == pop && r0 >= s_row0 && r0 + 2 < s_row0 + rows;
+      s_flush = s_wpop >= 0 && !keep;
+      s_newrow0 = keep ? s_row0 : r0;
+      s_newpop = pop;
+    }
+    __syncthreads();
+    if (s_flush) flush(s_wpop, s_row0);
+    if (threadIdx.x == 0) {
+      s_row0 = s_newrow0;
+      s_wpop = s_newpop;
+    }
+    __syncthreads();
+    const int wpop = s_wpop, row0 = s_row0;
+    for (int it = 0; it < kTanDepItems; ++it) {
+      const long long k = t0 + (long long)it * blockDim.x + threadIdx.x;
+      if (k >= total) break;
+      const int pop = find_pop(s_pre, d.n_pop, k);
+      const Pop& P = d.pop[pop];
+      const Inst& I = d.inst[P.inst];
+      const long long slot = P.base + (k - s_pre[pop]);
+      const Real x1v = X1[slot];
+      if (!(x1v < Real(0))) continue;
+      D x1 = load_d(t, x1v, 0, slot), x2 = load_d(t, X2[slot], 1, slot);
+      CellD c = locate_d(I, x1, x2);
+      D g1 = Real(1) - c.f1, g2 = Real(1) - c.f2;
+      D w00 = g1 * g2, w10 = c.f1 * g2, w01 = g1 * c.f2, w11 = c.f1 * c.f2;
+      const double qw = P.q * P.w;
+      const int rr = c.i - row0;
+      if (pop == wpop && I.n2 <= win_n2 && rr >= 0 && rr + 1 < rows) {
+#pragma unroll
+        for (int p = 0; p < kNPar; ++p) {
+          double* sw = s_tw + p * plane + rr * WN + c.j;
+          if (w00.d[p] != Real(0)) atomicAdd(sw, qw * (double)w00.d[p]);
+          if (w10.d[p] != Real(0)) atomicAdd(sw + WN, qw * (double)w10.d[p]);
+          if (w01.d[p] != Real(0)) atomicAdd(sw + 1, qw * (double)w01.d[p]);
+          if (w11.d[p] != Real(0)) atomicAdd(sw + WN + 1, qw * (double)w11.d[p]);
+        }
+      } else {
+        const long long n00 = I.node_off + (long long)c.i * I.N2 + c.j;
+#pragma unroll
+        for (int p = 0; p < kNPar; ++p) {
+          double* r = t.drho + (long long)p * d.total_nodes;
+          if (w00.d[p] != Real(0)) atomicAdd(r + n00, qw * (double)w00.d[p]);
+          if (w10.d[p] != Real(0)) atomicAdd(r + n00 + I.N2, qw * (double)w10.d[p]);
+          if (w01.d[p] != Real(0)) atomicAdd(r + n00 + 1, qw * (double)w01.d[p]);
+          if (w11.d[p] != Real(0)) atomicAdd(r + n00 + I.N2 + 1, qw * (double)w11.d[p]);
+        }
+      }
+    }
+    __syncthreads();
   }
+  if (s_wpop >= 0) flush(s_wpop, s_row0);
 }
 
 // One particle over one step on dual numbers: the same sequence as the step's
@@ -486,8 +557,14 @@ unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs);
 }  // namespace
 
 template <>
-void launch_tan_deposit<Real>(const DevPtrs& d, const TanPtrs& t, int grid, cudaStream_t s) {
-  k_tan_deposit<<<grid, 256, 0, s>>>(d, t);
+void launch_tan_deposit<Real>(const DevPtrs& d, const TanPtrs& t, int grid, int max_n2, cudaStream_t s) {
+  // window: up to 8 node rows of up to 512 cells, within 48 KB of doubles
+  const int win_n2 = max_n2 < 512 ? max_n2 : 512;
+  int rows = 49152 / (kNPar * (win_n2 + 1) * (int)sizeof(double));
+  rows = rows > 8 ? 8 : (rows < 2 ? 2 : rows);
+  const int sm = kNPar * rows * (win_n2 + 1) * (int)sizeof(double);
+  cudaFuncSetAttribute(k_tan_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  k_tan_deposit<<<grid, 256, sm, s>>>(d, t, win_n2, rows);
 }
 
 template <>
