@@ -929,6 +929,7 @@ static int setup(apic_sim* S) {
       for (int k = 0; k < ni; ++k)
         bcr_npre[k + 1] = bcr_npre[k] + (int)((S->inst[k].nodes + kBcrSub - 1) / kBcrSub);
       pl.bcr.chunks = bcr_npre[ni];
+      pl.bcr.rows = bcr_rows;
       pl.bcr.task_sub = (int)std::max<long long>(1, std::min<long long>(kBcrMaxTaskSub, pl.bcr.chunks / (2ll * bcr_nb)));
       bcr_tpre.assign(ni + 1, 0);
       for (int k = 0; k < ni; ++k)
@@ -1001,14 +1002,14 @@ static int setup(apic_sim* S) {
     // access-policy window covers them)
     d.bcr = (float*)A((size_t)pl.bcr.bytes);
     S->bcr_bytes = (size_t)pl.bcr.bytes;
-    d.bcr_f = (float*)A(sizeof(float) * (size_t)bcr_rows);
-    d.bcr_e = (float*)A(sizeof(float) * (size_t)bcr_rows);
+    d.bcr_f = (float*)A(sizeof(float) * kBcrMaxRhs * (size_t)bcr_rows);  // up to kBcrMaxRhs right-hand sides
+    d.bcr_e = (float*)A(sizeof(float) * kBcrMaxRhs * (size_t)bcr_rows);
     d.bcr_inst = (const BcrInst*)A(sizeof(BcrInst) * ni);
     d.bcr_kind = (const int32_t*)A(sizeof(int32_t) * bcr_kind.size());
     d.bcr_pre = (const int32_t*)A(sizeof(int32_t) * bcr_pre.size());
     d.bcr_npre = (const int32_t*)A(sizeof(int32_t) * bcr_npre.size());
     d.bcr_tpre = (const int32_t*)A(sizeof(int32_t) * bcr_tpre.size());
-    d.bcr_part = (double*)A(sizeof(double) * 2 * (size_t)pl.bcr.chunks);
+    d.bcr_part = (double*)A(sizeof(double) * (1 + kBcrMaxRhs) * (size_t)pl.bcr.chunks);
     if (S->status != APIC_OK) return S->status;
     S->h2d((BcrInst*)d.bcr_inst, bcr_in.data(), bcr_in.size());
     S->h2d((int32_t*)d.bcr_kind, bcr_kind.data(), bcr_kind.size());
@@ -1786,6 +1787,7 @@ static bool tangent_setup(apic_sim* S) {
   t.ds = S->dalloc(R * 5 * kNPar * (size_t)S->slots);
   t.drho = (double*)S->dalloc(sizeof(double) * kNPar * tn);
   t.dphi = (double*)S->dalloc(sizeof(double) * kNPar * tn);
+  t.bt = (double*)S->dalloc(sizeof(double) * kNPar * tn);
   t.phi0 = S->phi_save;
   t.dG = S->dalloc(2 * R * kNPar * tn);
   t.dV = (double*)S->dalloc(sizeof(double) * tn);
@@ -1873,10 +1875,24 @@ static int sensitivity_impl(apic_sim* S, int n, double* values, double* jac) {
     // Poisson: the step's problem, then the three tangent problems
     if (!solve_now<Real>(S, d)) break;
     S->ck(cudaMemcpyAsync(t.phi0, d.phi, sizeof(double) * tn, cudaMemcpyDeviceToDevice, s), "copy phi");
-    for (int p = 0; p < kNPar; ++p) {
-      launch_tan_b(d, t, p, s);
-      if (!solve_now<Real>(S, d)) break;
-      launch_tan_store(d, t, p, s);
+    if (S->plan.bcr.n_inst > 0 && kNPar <= kBcrMaxRhs && kNPar * ni <= kCoopMaxInst) {
+      // the three tangent systems share the reduction's blocks: one launch
+      BcrRhs rh{};
+      rh.n = kNPar;
+      for (int p = 0; p < kNPar; ++p) {
+        launch_tan_b(d, t, p, 1, s);
+        rh.slot[p] = kTanSlot + p;
+        rh.x[p] = t.dphi + (long long)p * tn;
+        rh.b[p] = t.bt + (long long)p * tn;
+      }
+      if (!S->ck(launch_solve_bcr_rhs(d, S->plan, S->coop, rh, s), "tangent solves")) break;
+      for (int p = 0; p < kNPar; ++p) launch_tan_store(d, t, p, 1, s);
+    } else {
+      for (int p = 0; p < kNPar; ++p) {
+        launch_tan_b(d, t, p, 0, s);
+        if (!solve_now<Real>(S, d)) break;
+        launch_tan_store(d, t, p, 0, s);
+      }
     }
     S->ck(cudaMemcpyAsync(d.phi, t.phi0, sizeof(double) * tn, cudaMemcpyDeviceToDevice, s), "restore phi");
     // node gradients and surface quantities (the step's, then their derivatives)

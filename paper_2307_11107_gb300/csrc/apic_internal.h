@@ -183,6 +183,7 @@ struct TanPtrs {
   double* drho;            // [kNPar][total_nodes]: sum of q w dW, then d rho
   double* dphi;            // [kNPar][total_nodes]
   double* phi0;            // primal phi (all nodes) while the tangent systems are solved
+  double* bt;              // [kNPar][total_nodes]: right-hand sides of the tangent systems (solved together)
   void* dG;                // [kNPar][total_nodes] node-gradient pairs in the particle type
   double* dV;              // d V_node / d alpha
   double* dst;             // d (unscaled Eq. 7 row, all kSt slots, Dirichlet neighbours kept) / d alpha [kSt][total_nodes]
@@ -296,6 +297,7 @@ struct BcrPlan {
   int wide;                 // 1: some block is larger than kBcrMaxN (the wide kernel)
   int64_t bytes;            // device bytes of all blocks and tail inverses
   int64_t chunks;           // partial-sum ranges of all instances (kBcrSub nodes each)
+  int64_t rows;             // floats of one right-hand side's rows in bcr_f / bcr_e (all instances)
   int task_sub;             // partial-sum ranges per node task (1..kBcrMaxTaskSub)
   int pad2;
 };
@@ -341,6 +343,18 @@ constexpr int kBcrRho = 1;     // form rho, the guess and b inside the solve
 constexpr int kBcrFields = 2;  // node gradients and surface quantities after the solve
 // only >= 0: solve that instance alone (its b and |b|^2 partials from the caller)
 cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& plan, int blocks, int mode, int only, cudaStream_t s);
+// Several right-hand sides of the same systems in one launch (they share the
+// blocks): the solution of system r of instance k is x[r] + node_off (initial
+// guess on entry), its right-hand side b[r] + node_off, its |b|^2 partials in
+// reduction slot slot[r]; n * n_inst <= kCoopMaxInst.
+constexpr int kBcrMaxRhs = 3;
+struct BcrRhs {
+  int n;
+  int slot[kBcrMaxRhs];
+  double* x[kBcrMaxRhs];
+  const double* b[kBcrMaxRhs];
+};
+cudaError_t launch_solve_bcr_rhs(const DevPtrs& d, const SolvePlan& plan, int blocks, const BcrRhs& rhs, cudaStream_t s);
 // CTAs of the solve (0: not co-residable); sets each instance's staging flag
 // and tail chunk, and the kernel's shared memory (plan.bcr.smem, plan.bcr.dyn).
 int bcr_configure(SolvePlan& plan, BcrInst* inst, int n_inst, int sms);
@@ -354,8 +368,14 @@ void launch_tan_push(const DevPtrs& d, const TanPtrs& t, int grid, cudaStream_t 
 template <class Real>
 void launch_tan_inject(const DevPtrs& d, const TanPtrs& t, long long max_inj, cudaStream_t s);
 void launch_tan_rho(const DevPtrs& d, const TanPtrs& t, cudaStream_t s);
-void launch_tan_b(const DevPtrs& d, const TanPtrs& t, int p, cudaStream_t s);
-void launch_tan_store(const DevPtrs& d, const TanPtrs& t, int p, cudaStream_t s);
+// direct = 0: b into DevPtrs::b (|b|^2 partials in slot 0) and the guess into
+// DevPtrs::phi; direct = 1: b into TanPtrs::bt[p] (partials in slot
+// kTanSlot + p), the guess stays in TanPtrs::dphi[p].
+constexpr int kTanSlot = 5;
+void launch_tan_b(const DevPtrs& d, const TanPtrs& t, int p, int direct, cudaStream_t s);
+// direct = 0: dphi[p] = DevPtrs::phi inside, Dirichlet values on the
+// boundary rows; direct = 1: the boundary rows only.
+void launch_tan_store(const DevPtrs& d, const TanPtrs& t, int p, int direct, cudaStream_t s);
 void launch_tan_surface(const DevPtrs& d, const TanPtrs& t, cudaStream_t s);
 void launch_tan_step_end(const DevPtrs& d, const TanPtrs& t, cudaStream_t s);
 

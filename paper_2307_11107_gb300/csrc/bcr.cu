@@ -226,12 +226,13 @@ __device__ int task_ranges(const DevPtrs& d, const BcrInst& B, int kind, int l, 
 // Task q of kind `kind` at level l of instance k (the whole CTA).  Row r of
 // the reduced right-hand side f and of the correction e is at (r - 1) N.
 template <int MAXN>
-__device__ bool run_stage(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int l, int q, float (*sv)[MAXN]) {
+__device__ bool run_stage(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int l, int q, float (*sv)[MAXN],
+                          float* fb, float* eb, double* xb) {
   constexpr int kMC = MAXN / 32;
   const int N = B.N, M = B.M;
-  float* f = d.bcr_f + B.foff;
-  float* e = d.bcr_e + B.foff;
-  double* x = d.phi + B.node_off;
+  float* f = fb + B.foff;
+  float* e = eb + B.foff;
+  double* x = xb + B.node_off;
   const float* rp[3];
   unsigned rb[3];
   task_ranges(d, B, kind, l, q, rp, rb);
@@ -361,18 +362,22 @@ __device__ bool run_stage(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, 
   return true;
 }
 
-// Fixed-order sum of part[npre[k] .. npre[k+1]) for every instance k with
-// sel[k] (all when sel is null), one warp per instance; out[k] in shared
+// Fixed-order sum of part[r chunks + npre[k] .. r chunks + npre[k+1]) for
+// every system v = r ni + k (right-hand side r < nrhs, instance k) with
+// sel[v] (all when sel is null), one warp per system; out[v] in shared
 // memory, the same in every CTA.
-__device__ void inst_sums(const double* part, const int* npre, int ni, const int* sel, double* out) {
+__device__ void inst_sums(const double* part, const int* npre, int ni, int nrhs, long long chunks, const int* sel,
+                          double* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = warp; k < ni; k += kBcrWarps) {
-    if (sel && !sel[k]) continue;
-    double v = 0.0;
-    for (int c = npre[k] + lane; c < npre[k + 1]; c += 32) v += part[c];
+  for (int v = warp; v < nrhs * ni; v += kBcrWarps) {
+    if (sel && !sel[v]) continue;
+    const int r = v / ni, k = v - r * ni;
+    const double* pr = part + (long long)r * chunks;
+    double x = 0.0;
+    for (int c = npre[k] + lane; c < npre[k + 1]; c += 32) x += pr[c];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    if (lane == 0) out[k] = v;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+    if (lane == 0) out[v] = x;
   }
   __syncthreads();
 }
@@ -380,30 +385,32 @@ __device__ void inst_sums(const double* part, const int* npre, int ni, const int
 // Node tasks over the ranges of kBcrSub nodes of every instance (range c of
 // instance k: nodes c kBcrSub .. (c + 1) kBcrSub - 1).  A task covers tsub
 // consecutive ranges of one instance, kRangesPerPass per pass of the CTA; the tasks of
-// all instances are spread over the CTAs.  body(k, I, nd) returns the node's
-// contribution to its range's sum, which goes to part[npre[k] + c] (when part
+// all instances (and right-hand sides r < nrhs) are spread over the CTAs.
+// body(r, k, I, nd) returns the node's contribution to its range's sum,
+// which goes to part[r chunks + npre[k] + c] (when part
 // is not null) as a warp-shuffle tree per warp and the range's warps in order: the
 // sums do not depend on the task size, the CTA or the other instances of a
 // batch.  ws: kBcrMaxTaskSub / kRangesPerPass * kBcrWarps doubles of shared memory.
 template <class F>
-__device__ void node_tasks(const DevPtrs& d, const int* npre, const int* tpre, int tsub, const int* sel, double* part,
-                           double* ws, F body) {
+__device__ void node_tasks(const DevPtrs& d, const int* npre, const int* tpre, int tsub, int nrhs, long long chunks,
+                           const int* sel, double* part, double* ws, F body) {
   constexpr int kPasses = kBcrMaxTaskSub / kRangesPerPass;
   const int ni = d.n_inst, nb = gridDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int half = threadIdx.x / kBcrSub, r = threadIdx.x % kBcrSub;  // range within the pass, node within it
-  const int total = tpre[ni];
+  const int per_rhs = tpre[ni], total = nrhs * per_rhs;
   for (int t = blockIdx.x; t < total; t += nb) {
-    const int k = task_inst_s(tpre, ni, t);
-    if (sel && !sel[k]) continue;
+    const int rh = t / per_rhs, tt = t - rh * per_rhs;
+    const int k = task_inst_s(tpre, ni, tt);
+    if (sel && !sel[rh * ni + k]) continue;
     const Inst& I = d.inst[k];
-    const int s0 = (t - tpre[k]) * tsub, s1 = min(npre[k + 1] - npre[k], s0 + tsub);
+    const int s0 = (tt - tpre[k]) * tsub, s1 = min(npre[k + 1] - npre[k], s0 + tsub);
     double v[kPasses];
 #pragma unroll
     for (int u = 0; u < kPasses; ++u) {
       const int sc = s0 + kRangesPerPass * u + half;
       const long long nd = (long long)sc * kBcrSub + r;
-      v[u] = sc < s1 && nd < I.nodes ? body(k, I, nd) : 0.0;
+      v[u] = sc < s1 && nd < I.nodes ? body(rh, k, I, nd) : 0.0;
     }
     if (!part) continue;
 #pragma unroll
@@ -419,7 +426,7 @@ __device__ void node_tasks(const DevPtrs& d, const int* npre, const int* tpre, i
       const int i = threadIdx.x, u = i / kRangesPerPass, w0 = (i % kRangesPerPass) * (kBcrSub / 32);
       double sum = 0.0;
       for (int w = w0; w < w0 + kBcrSub / 32; ++w) sum += ws[u * kBcrWarps + w];
-      part[npre[k] + s0 + i] = sum;
+      part[(long long)rh * chunks + npre[k] + s0 + i] = sum;
     }
     __syncthreads();
   }
@@ -428,12 +435,13 @@ __device__ void node_tasks(const DevPtrs& d, const int* npre, const int* tpre, i
 // mode: kBcrRho = the step's density, initial guess and right-hand side are
 // formed here (else b and its |b|^2 partials come from the caller);
 // kBcrFields = node gradients and surface quantities after the solve.
-// only >= 0: that instance alone is solved (the others keep their phi).  An
-// instance computes the same values alone or in a batch.
+// only >= 0: that instance alone is solved (the others keep their phi).
+// rhs: the right-hand sides solved together (one for a step's solve: x = phi,
+// b = DevPtrs::b).  An instance computes the same values alone or in a batch.
 // MAXN: the largest block size of the batch this instantiation handles (256
 // or 544 = 17 x 32, for grids up to 543 cells in x2).
 template <int MAXN>
-__global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan pl, int mode, int only) {
+__global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan pl, int mode, int only, BcrRhs rhs) {
   extern __shared__ __align__(128) float s_dyn[];
   __shared__ double sh[40];
   __shared__ float sv[3][MAXN];
@@ -449,16 +457,21 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   __shared__ int s_kind[kCoopMaxInst];
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ __align__(16) BcrInst s_b0;  // instance 0's table (one load per kernel instead of one per task)
-  const int nb = gridDim.x, ni = d.n_inst;
+  const int nb = gridDim.x, ni = d.n_inst, R = rhs.n, nv = R * ni;
+  static_assert(kBcrMaxRhs == 3, "selections below");
+  // selections instead of dynamic indexing (which would put the parameter
+  // arrays in local memory)
+  auto x_of = [&](int r) { return r == 0 ? rhs.x[0] : (r == 1 ? rhs.x[1] : rhs.x[2]); };
+  auto b_of = [&](int r) { return r == 0 ? rhs.b[0] : (r == 1 ? rhs.b[1] : rhs.b[2]); };
   Ctx c{s_dyn, &s_bar, 0u, red, sres, d.err};
-  double* part_b = d.bcr_part;              // |b|^2 per node chunk
-  double* part_r = d.bcr_part + pl.chunks;  // |r|^2 per node chunk
+  double* part_b = d.bcr_part;                           // |b|^2 per range
+  double* part_r = d.bcr_part + kBcrMaxRhs * pl.chunks;  // |r|^2 per range and right-hand side
   for (int k = threadIdx.x; k <= ni; k += blockDim.x) {
     s_npre[k] = d.bcr_npre[k];
     s_tpre[k] = d.bcr_tpre[k];
   }
   const int tsub = pl.task_sub;
-  for (int k = threadIdx.x; k < ni; k += blockDim.x) s_act[k] = only < 0 || k == only;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) s_act[v] = only < 0 || v % ni == only;
   if (threadIdx.x == 0) mbar_init(&s_bar, 1);
   for (int w = threadIdx.x; w < (int)(sizeof(BcrInst) / 4); w += blockDim.x)
     ((int*)&s_b0)[w] = ((const int*)d.bcr_inst)[w];
@@ -480,56 +493,64 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   __syncthreads();
   if (mode & kBcrRho) {
     // rho, the initial guess and b at every node; |b|^2 per instance
-    node_tasks(d, s_npre, s_tpre, tsub, nullptr, part_b, s_ws, [&](int k, const Inst& I, long long nd) {
-      const double bv = rho_node(d, I, k, nd);
-      return bv * bv;
-    });
+    node_tasks(d, s_npre, s_tpre, tsub, 1, pl.chunks, nullptr, part_b, s_ws,
+               [&](int, int k, const Inst& I, long long nd) {
+                 const double bv = rho_node(d, I, k, nd);
+                 return bv * bv;
+               });
     if (!grid_sync(d, nb)) return;
-    inst_sums(part_b, s_npre, ni, nullptr, s_bn);
+    inst_sums(part_b, s_npre, ni, 1, pl.chunks, nullptr, s_bn);
   } else {
-    // |b|^2 from the right-hand-side kernel's partials (fixed order)
-    for (int k = threadIdx.x; k < ni; k += blockDim.x) {
-      const double* pr = d.red + (long long)k * kNRed * kRedBlocks;
+    // |b|^2 from the right-hand-side kernels' partials (fixed order)
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      const int r = v / ni, k = v - r * ni;
+      const int slot = r == 0 ? rhs.slot[0] : (r == 1 ? rhs.slot[1] : rhs.slot[2]);
+      const double* pr = d.red + ((long long)k * kNRed + slot) * kRedBlocks;
       double s0 = 0.0;
-      for (int r = 0; r < kRedBlocks; ++r) s0 += pr[r];
-      s_bn[k] = s0;
+      for (int q = 0; q < kRedBlocks; ++q) s0 += pr[q];
+      s_bn[v] = s0;
     }
     __syncthreads();
   }
   for (int it = 0;; ++it) {
     // FP64 residual of every instance still iterating, stored as the FP32
     // right-hand side of its reduction
-    node_tasks(d, s_npre, s_tpre, tsub, s_act, part_r, s_ws, [&](int k, const Inst& I, long long nd) {
-      const int N = I.N2;
-      const int i = (int)(nd / N), j = (int)(nd % N);
-      double rr = 0.0;
-      if (i > 0 && i < I.n1) {
-        const double r = d.b[I.node_off + nd] - apply_st<double, double>(d.st64 + (long long)kSt * I.node_off, I.nodes,
-                                                                         d.phi + I.node_off, nd, i, j, I.n2, N, 1);
-        d.bcr_f[d.bcr_inst[k].foff + (long long)(i - 1) * N + j] = (float)r;
-        rr = r * r;
-      }
-      return rr;
-    });
+    node_tasks(d, s_npre, s_tpre, tsub, R, pl.chunks, s_act, part_r, s_ws,
+               [&](int rh, int k, const Inst& I, long long nd) {
+                 const int N = I.N2;
+                 const int i = (int)(nd / N), j = (int)(nd % N);
+                 double rr = 0.0;
+                 if (i > 0 && i < I.n1) {
+                   const double r = b_of(rh)[I.node_off + nd] -
+                                    apply_st<double, double>(d.st64 + (long long)kSt * I.node_off, I.nodes,
+                                                             x_of(rh) + I.node_off, nd, i, j, I.n2, N, 1);
+                   d.bcr_f[rh * pl.rows + d.bcr_inst[k].foff + (long long)(i - 1) * N + j] = (float)r;
+                   rr = r * r;
+                 }
+                 return rr;
+               });
     load_tab(0);
     if (!grid_sync(d, nb)) return;
     store_tab();  // read after the synchronisation that ends inst_sums
-    inst_sums(part_r, s_npre, ni, s_act, s_rn);
+    inst_sums(part_r, s_npre, ni, R, pl.chunks, s_act, s_rn);
     int more = 0;
-    for (int k = threadIdx.x; k < ni; k += blockDim.x) {
-      if (!s_act[k]) continue;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+      if (!s_act[v]) continue;
+      const int k = v % ni;
       const Inst& I = d.inst[k];
-      const double rn = s_rn[k], bn = s_bn[k];
+      const double rn = s_rn[v], bn = s_bn[v];
       const bool conv = rn <= I.tol * I.tol * bn, bad = !(rn == rn);
       if (conv || bad || it >= I.max_iter) {
         if (blockIdx.x == 0) {
-          SolverState& S = d.sol[k];
-          S.res = bn > 0.0 ? sqrt(rn / bn) : 0.0;
-          S.iters = it;
-          S.done = 1;
+          if (v < ni) {  // the first right-hand side reports the solver state
+            SolverState& S = d.sol[k];
+            S.res = bn > 0.0 ? sqrt(rn / bn) : 0.0;
+            S.iters = it;
+            S.done = 1;
+          }
           if (!conv) atomicOr(d.err, bad ? kErrNonFinite : kErrNotConverged);
         }
-        s_act[k] = 0;
+        s_act[v] = 0;
       } else {
         more = 1;
       }
@@ -541,12 +562,15 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
         store_tab();
         __syncthreads();
       }
-      const int total = s_pre[ni];
+      const int per_rhs = s_pre[ni], total = R * per_rhs;
       for (int t = blockIdx.x; t < total; t += nb) {
-        const int k = task_inst_s(s_pre, ni, t);
-        if (!s_act[k]) continue;
+        const int rh = t / per_rhs, tt = t - rh * per_rhs;
+        const int k = task_inst_s(s_pre, ni, tt);
+        if (!s_act[rh * ni + k]) continue;
         const BcrInst& B = k == 0 ? s_b0 : d.bcr_inst[k];
-        if (!run_stage<MAXN>(d, c, B, s_kind[k] >> 8, s_kind[k] & 255, t - s_pre[k], sv)) return;
+        if (!run_stage<MAXN>(d, c, B, s_kind[k] >> 8, s_kind[k] & 255, tt - s_pre[k], sv, d.bcr_f + rh * pl.rows,
+                             d.bcr_e + rh * pl.rows, x_of(rh)))
+          return;
       }
       if (p + 1 < pl.phases) load_tab(p + 1);
       if (!grid_sync(d, nb)) return;
@@ -555,11 +579,11 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   }
   if (mode & kBcrFields) {
     // phi is final everywhere (the last pass ended at a grid barrier)
-    node_tasks(d, s_npre, s_tpre, tsub, nullptr, nullptr, s_ws, [&](int k, const Inst& I, long long nd) {
-      (void)k;
-      grad_node<float, float2>(d, I, nd);
-      return 0.0;
-    });
+    node_tasks(d, s_npre, s_tpre, tsub, 1, pl.chunks, nullptr, nullptr, s_ws,
+               [&](int, int, const Inst& I, long long nd) {
+                 grad_node<float, float2>(d, I, nd);
+                 return 0.0;
+               });
     for (int k = nb - 1 - (int)blockIdx.x; k < ni; k += nb) surface_block(d, k, sh);
   }
 }
@@ -627,13 +651,29 @@ int bcr_configure(SolvePlan& pl, BcrInst* bi, int ni, int sms) {
   return nb;
 }
 
-cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& pl, int blocks, int mode, int only, cudaStream_t s) {
+static cudaError_t launch_bcr(const DevPtrs& d, const SolvePlan& pl, int blocks, int mode, int only, const BcrRhs& rhs,
+                              cudaStream_t s) {
   DevPtrs dd = d;
   BcrPlan pp = pl.bcr;
+  BcrRhs rr = rhs;
   int mm = mode, oo = only;
-  void* args[] = {&dd, &pp, &mm, &oo};
+  void* args[] = {&dd, &pp, &mm, &oo, &rr};
   return cudaLaunchCooperativeKernel(kernel_for(pl.bcr), dim3(blocks), dim3(kBcrThreads), args,
                                      (size_t)pl.bcr.dyn, s);
+}
+
+cudaError_t launch_solve_bcr(const DevPtrs& d, const SolvePlan& pl, int blocks, int mode, int only, cudaStream_t s) {
+  BcrRhs one{};
+  one.n = 1;
+  one.slot[0] = 0;
+  one.x[0] = d.phi;
+  one.b[0] = d.b;
+  return launch_bcr(d, pl, blocks, mode, only, one, s);
+}
+
+cudaError_t launch_solve_bcr_rhs(const DevPtrs& d, const SolvePlan& pl, int blocks, const BcrRhs& rhs, cudaStream_t s) {
+  if (rhs.n < 1 || rhs.n > kBcrMaxRhs || rhs.n * d.n_inst > kCoopMaxInst) return cudaErrorInvalidValue;
+  return launch_bcr(d, pl, blocks, 0, -1, rhs, s);
 }
 
 }  // namespace apic

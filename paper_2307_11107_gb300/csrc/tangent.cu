@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(256) k_tan_rho(DevPtrs d, TanPtrs t) {
 // system, b = -(d rho + [alpha] dL/dalpha phi) rscale + [phi_g] bbc_g, with
 // |b|^2 partials for the convergence test; the previous step's solution of
 // the same problem is the initial guess.
-__global__ void __launch_bounds__(256) k_tan_b(DevPtrs d, TanPtrs t, int p) {
+__global__ void __launch_bounds__(256) k_tan_b(DevPtrs d, TanPtrs t, int p, int direct) {
   __shared__ double sh[256];
   const int inst = blockIdx.y;
   const Inst& I = d.inst[inst];
@@ -458,27 +458,30 @@ __global__ void __launch_bounds__(256) k_tan_b(DevPtrs d, TanPtrs t, int p) {
         rhs += a;
       }
       bv = -rhs * d.rscale[g] + (p == 1 ? t.bbc_g[g] : 0.0);
-      d.phi[g] = t.dphi[(long long)p * d.total_nodes + g];
+      if (!direct) d.phi[g] = t.dphi[(long long)p * d.total_nodes + g];
     }
-    d.b[g] = bv;
+    if (direct) t.bt[(long long)p * d.total_nodes + g] = bv;
+    else d.b[g] = bv;
     part += bv * bv;
   }
   double tot = block_sum(part, sh);
-  if (threadIdx.x == 0) d.red[((long long)inst * kNRed + 0) * kRedBlocks + blockIdx.x] = tot;
+  if (threadIdx.x == 0) d.red[((long long)inst * kNRed + (direct ? kTanSlot + p : 0)) * kRedBlocks + blockIdx.x] = tot;
 }
 
 // dphi of problem p: the solver's interior values, d phi_g on the grain row,
 // zero on the outer row (phi_out is not a parameter); zero without a field.
-__global__ void __launch_bounds__(256) k_tan_store(DevPtrs d, TanPtrs t, int p) {
+__global__ void __launch_bounds__(256) k_tan_store(DevPtrs d, TanPtrs t, int p, int direct) {
   const Inst& I = d.inst[blockIdx.y];
   const bool nofield = (I.flags & APIC_NO_FIELD) != 0;
   for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes;
        nd += (long long)gridDim.x * blockDim.x) {
     int i = (int)(nd / I.N2);
     long long g = I.node_off + nd;
+    const bool inside = i > 0 && i < I.n1;
+    if (direct && inside && !nofield) continue;  // solved in place
     double v = 0.0;
     if (!nofield) {
-      if (i > 0 && i < I.n1) v = d.phi[g];
+      if (inside) v = d.phi[g];
       else if (i == 0 && p == 1) v = 1.0;
     }
     t.dphi[(long long)p * d.total_nodes + g] = v;
@@ -582,11 +585,11 @@ void launch_tan_inject<Real>(const DevPtrs& d, const TanPtrs& t, long long max_i
 void launch_tan_rho(const DevPtrs& d, const TanPtrs& t, cudaStream_t s) {
   k_tan_rho<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d, t);
 }
-void launch_tan_b(const DevPtrs& d, const TanPtrs& t, int p, cudaStream_t s) {
-  k_tan_b<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d, t, p);
+void launch_tan_b(const DevPtrs& d, const TanPtrs& t, int p, int direct, cudaStream_t s) {
+  k_tan_b<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d, t, p, direct);
 }
-void launch_tan_store(const DevPtrs& d, const TanPtrs& t, int p, cudaStream_t s) {
-  k_tan_store<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d, t, p);
+void launch_tan_store(const DevPtrs& d, const TanPtrs& t, int p, int direct, cudaStream_t s) {
+  k_tan_store<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d, t, p, direct);
 }
 void launch_tan_surface(const DevPtrs& d, const TanPtrs& t, cudaStream_t s) {
   k_tan_surface<<<d.n_inst, 256, 0, s>>>(d, t);
