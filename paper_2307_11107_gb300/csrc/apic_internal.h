@@ -167,7 +167,7 @@ struct DevPtrs {
   const int32_t* bcr_pre;         // [phases][n_inst + 1]: prefix sums of the instances' task counts
   const int32_t* bcr_npre;        // [n_inst + 1]: prefix sums of the instances' partial-sum ranges (kBcrSub nodes)
   const int32_t* bcr_tpre;        // [n_inst + 1]: prefix sums of the instances' node tasks
-  double* bcr_part;               // [2][chunks]: |b|^2 and |r|^2 of each range
+  double* bcr_part;               // [1 + kBcrMaxRhs][chunks]: |b|^2, then |r|^2 per right-hand side, of each range
 };
 
 // ---- sensitivity window (forward mode) ----

@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   auto b_of = [&](int r) { return r == 0 ? rhs.b[0] : (r == 1 ? rhs.b[1] : rhs.b[2]); };
   Ctx c{s_dyn, &s_bar, 0u, red, sres, d.err};
   double* part_b = d.bcr_part;                           // |b|^2 per range
-  double* part_r = d.bcr_part + kBcrMaxRhs * pl.chunks;  // |r|^2 per range and right-hand side
+  double* part_r = d.bcr_part + pl.chunks;  // |r|^2 per range and right-hand side ([kBcrMaxRhs][chunks])
   for (int k = threadIdx.x; k <= ni; k += blockDim.x) {
     s_npre[k] = d.bcr_npre[k];
     s_tpre[k] = d.bcr_tpre[k];
