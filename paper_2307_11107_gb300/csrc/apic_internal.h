@@ -123,7 +123,7 @@ struct DevPtrs {
   StepState* stp;
   int n_inst, n_pop;
   int32_t* err;
-  long long* cnt;                 // [0] Krylov-loop iterations executed (all steps)
+  long long* cnt;                 // [0] Krylov-loop iterations executed (all steps); [1] the push's next chunk group
   // particles (element type = the precision of the batch)
   void *x1, *x2, *vR, *vZ, *vT;
   void *y1, *y2, *yR, *yZ, *yT;  // second buffer (sort)

@@ -242,7 +242,7 @@ constexpr int kPushUnroll = APIC_PUSH_UNROLL;  // items of the chunk loop unroll
 // FP32: 64 registers, four CTAs of 256 threads per SM; FP64 (parity build): two
 #define APIC_PUSH_MIN_BLOCKS (sizeof(APIC_REAL) == 4 ? 4 : 2)
 #endif
-__global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, int win_n2, int win_rows) {
+__global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, int win_n2, int win_rows, int group) {
   // dynamic shared memory: the deposit window, then the chunk prefix over the
   // populations and their constants (sized by the batch, so that a small
   // batch leaves more of the SM's memory to L1 for the field gather)
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
   const int win_words = kF64 ? win_rows * (win_n2 + 1) : 2 * win_rows * win_n2;
   long long* s_pre = (long long*)(s_win + win_words);
   PushConst* s_pc = (PushConst*)(s_pre + d.n_pop + 1);
-  __shared__ int s_row0, s_wpop, s_nsince, s_newrow0, s_flush;
+  __shared__ int s_row0, s_wpop, s_nsince, s_newrow0, s_flush, s_gi;
   __shared__ unsigned s_rowmask;  // FP32 window: cell rows that received moments in this chunk
   const long long CH = (long long)kPushItems * blockDim.x;
   if (threadIdx.x == 0) {
@@ -348,16 +348,27 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
   // rows or population leave it, or after kFlushChunks chunks: the global
   // atomics of the flushes, which all CTAs working on one grid row send to
   // the same addresses, are what the window saves.
-  const long long per = (total_chunks + gridDim.x - 1) / gridDim.x;
-  const long long cbeg = (long long)blockIdx.x * per;
-  const long long cend = cbeg + per < total_chunks ? cbeg + per : total_chunks;
+  // groups of `group` consecutive chunks, taken in order from a counter that
+  // is cleared before each launch: the CTAs balance themselves, and the CTAs
+  // at work read neighbouring memory
+  const int nch = (int)total_chunks;  // chunks of 2048 particles: far below 2^31
+  const int GS = group > 0 ? group : 1;
+  const int ngroups = (nch + GS - 1) / GS;
   if (threadIdx.x == 0) {
     s_wpop = -1;
     s_nsince = 0;
     s_rowmask = 0u;
   }
   __syncthreads();
-  for (long long chunk = cbeg; chunk < cend; ++chunk) {
+  for (int q = 0;; ++q) {
+   if (q % GS == 0) {
+     if (threadIdx.x == 0) s_gi = (int)atomicAdd((unsigned long long*)(d.cnt + 1), 1ull);
+     __syncthreads();
+   }
+   const int gi = s_gi;
+   if (gi >= ngroups) break;
+   const long long chunk = (long long)gi * GS + q % GS;
+   if (chunk >= nch) continue;
    const int pop = find_pop(s_pre, d.n_pop, chunk);
    // by value: the constants stay in registers instead of being reloaded from
    // shared memory around every window atomic
@@ -1164,7 +1175,13 @@ void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, cudaStream_t s) {
   const int rows = push_window_rows<Real>(max_n2);
   const int sm = push_smem(rows, win_n2, d.n_pop);
   cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  k_push<<<grid, 256, sm, s>>>(d, win_n2, rows);
+  static int group = -1;  // chunks per group (APIC_PUSH_GROUP, default 4: the fastest of 1, 2, 4, 8 measured)
+  if (group < 0) {
+    const char* e = std::getenv("APIC_PUSH_GROUP");
+    group = e ? std::max(1, std::atoi(e)) : 4;
+  }
+  cudaMemsetAsync(d.cnt + 1, 0, sizeof(long long), s);  // the group counter
+  k_push<<<grid, 256, sm, s>>>(d, win_n2, rows, group);
 }
 
 template <>
