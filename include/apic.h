@@ -59,7 +59,8 @@ extern "C" {
 
 /* precision of the particle arrays and of the Poisson preconditioner */
 #define APIC_FP64 0          /* FP64 particles, FP64 multigrid (parity path) */
-#define APIC_FP32_REFINED 1  /* FP32 particles and FP32 multigrid inside an FP64 Krylov/residual loop */
+#define APIC_FP32_REFINED 1  /* FP32 particles; FP32 block cyclic reduction (or FP32 multigrid) inside an
+                                FP64 residual loop */
 
 /* apic_inject modes */
 #define APIC_LOAD_VOLUME 0   /* n particles uniform in physical volume, Maxwellian at T */
@@ -139,7 +140,12 @@ int apic_create(const apic_config_t* cfg, void* stream, const apic_allocator_t* 
 
 /* Create n instances that advance together in every kernel launch (each with
  * its own alpha, potentials, B, grid and particle counts).  Instance k is
- * addressed as `instance = k` below. */
+ * addressed as `instance = k` below.  With FP32 particles the Poisson
+ * problems of all instances are solved by one block-cyclic-reduction launch
+ * whose blocks are formed here on the host (a few seconds for large batches;
+ * up to 24 GB of device memory, and at most 60 % of the free memory, else
+ * multigrid is used); an instance computes the same values alone or in the
+ * batch.  At most 64 instances share the reduction solve. */
 int apic_create_batch(const apic_config_t* cfgs, int32_t n, void* stream,
                       const apic_allocator_t* allocator, apic_sim** out);
 
@@ -199,10 +205,11 @@ typedef struct {
 } apic_stats_t;
 
 /* Poisson solvers (chosen at creation) */
-#define APIC_SOLVER_MG_KERNELS 0 /* BiCGSTAB + multigrid V-cycle, one kernel per phase (batches) */
-#define APIC_SOLVER_MG_COOP 1    /* the same in one cooperative launch per solve */
-#define APIC_SOLVER_BCR 2        /* FP64 iterative refinement around an FP32 block cyclic reduction
-                                    (one instance, FP32 particles, n1 a power of two) */
+#define APIC_SOLVER_MG_KERNELS 0 /* BiCGSTAB + multigrid V-cycle, one kernel per phase (FP64 batches) */
+#define APIC_SOLVER_MG_COOP 1    /* the same in one cooperative launch per solve (FP64, one instance) */
+#define APIC_SOLVER_BCR 2        /* FP64 iterative refinement around an FP32 block cyclic reduction of
+                                    every instance in one cooperative launch (FP32 particles, any n1,
+                                    grids up to 543 cells in x2) */
 
 /* Counters of the batch (launch counts, Krylov iterations, phase times). */
 int apic_stats(apic_sim* sim, apic_stats_t* out);
