@@ -62,3 +62,15 @@ def test_replica_instances_draw_independent_particles():
         st.append(o.particles(0)[0])
     assert st[0].shape == st[1].shape
     assert not np.allclose(st[0], st[1])
+
+
+def test_batch_subset_keeps_the_first_instances():
+    """bench --instances N --particles P: the first N instances of the
+    48-instance batch, unchanged except for the particle count (small runs,
+    e.g. under a profiler)."""
+    sub = bench.workloads("batched48", 2000, 8)
+    full = bench.workloads("batched48")
+    assert len(sub) == 8 and len(full) == 48
+    assert [(c["n1"], c["n2"], c["alpha"], c["B"]) for c in sub] == [(c["n1"], c["n2"], c["alpha"], c["B"])
+                                                                  for c in full[:8]]
+    assert all(sp["n_init"] == 2000 for c in sub for sp in c["species"])
