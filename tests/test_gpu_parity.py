@@ -62,9 +62,10 @@ def test_poisson_fp32_refined_matches_banded_lu(apic, alpha, grid):
 @pytest.mark.parametrize("alpha,B", [(0.0, 0.0), (0.15, 1.0), (-0.24, 0.5)])
 def test_single_step_fp64(apic, alpha, B):
     """One full step from identical explicit states (no injection): rho, phi,
-    node gradients and every surviving particle agree with the oracle."""
+    node gradients, every surviving particle and the tallies (with a binding
+    energy for absorbed ions) agree with the oracle."""
     cfg = workload(n1=64, n2=32, alpha=alpha, B=B, n_init=20000, precision="fp64", no_inject=True,
-                   poisson_tol=1e-13, poisson_max_iter=60)
+                   poisson_tol=1e-13, poisson_max_iter=60, e_bind_ion=2.0)
     s, o = apic.Sim(cfg), oracle.Sim(cfg)
     for sp, seed, vs in ((0, 11, 1.0), (1, 12, 0.03)):
         st = random_states(20000, cfg["x1_out"], seed=seed, vscale=vs)

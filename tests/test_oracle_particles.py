@@ -126,6 +126,32 @@ def test_radial_infall_impact_point_and_tallies():
     assert bins[k, 5] == pytest.approx(0.5 * 0.81 * w, rel=1e-12)
 
 
+def test_binding_energy_counts_for_positive_charges_only():
+    """The heat-flux component of the tallies (E_kin + E_bind) adds the
+    binding energy per absorbed particle of positive charge (weighted like
+    every tally), and nothing for electrons (Sec. 1: energy transferred to
+    the grain at the point of impact)."""
+    e_bind = 3.5
+    cfg = _free_cfg(dt=0.5, n2=16, e_bind_ion=e_bind,
+                    species=[dict(EL, n_init=1000), dict(q=1.0, m=1836.0, T=1.0, n_init=1000)])
+    s = oracle.Sim(cfg)
+    for sp, x2, speed in ((0, 0.3, 0.9), (1, -0.4, 0.7)):
+        u = np.array([np.sqrt(1 - x2 * x2), x2])
+        st = _state_at(0.0, 1.2 * u[0], 1.2 * u[1], -speed * u[0], -speed * u[1], 0.0)
+        s.add_particles(sp, st)
+    s.push_only()
+    assert s.count(0) == 0 and s.count(1) == 0
+    b = s.bins()
+    sc = s.scalars()
+    for sp, m, speed, w in ((0, 1.0, 0.9, sc["w0"]), (1, 1836.0, 0.7, sc["w1"])):
+        hit = b[sp][:, 0] > 0
+        assert hit.sum() == 1
+        ek = b[sp][hit, 5][0]
+        assert ek == pytest.approx(0.5 * m * speed * speed * w, rel=1e-12)
+        extra = b[sp][hit, 6][0] - ek
+        assert extra == pytest.approx(e_bind * w if sp == 1 else 0.0, rel=1e-12, abs=1e-300)
+
+
 @pytest.mark.slow
 def test_field_free_thermal_flux_to_sphere():
     """No field: the absorption rate onto a convex grain in a uniform isotropic
