@@ -376,10 +376,11 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        n = 1_000_000
-        val, secs = run_oracle(cfg, n, 10)
+        n, k = 2_000_000, 50  # about 10-15 s of single-thread work
+        val, secs = run_oracle(cfg, n, k)
         cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "10 full steps of the same workload with 1e6 macro-particles per species (FP64, 1 thread)",
+               "sample": "%d full steps of the same workload with %.0e macro-particles per species (FP64, 1 thread)"
+                         % (k, n),
                "seconds": secs}
     if rank == 0:
         line = {

@@ -70,6 +70,11 @@ extern "C" {
 /* config flags */
 #define APIC_NO_INJECT 1     /* no per-step surface injection */
 #define APIC_NO_FIELD 2      /* phi = 0: no Poisson solve, E = 0 (test and baseline use) */
+#define APIC_CHORD_ABSORB 4  /* also absorb a particle whose straight chord of the step passes through
+                                the grain while its end point lies outside (grazing orbits; the chord is
+                                tested at 7 interior points once it comes closer to the origin than the
+                                grain's largest radius; impact point by bisection up to the first point
+                                inside).  Not with apic_sensitivity (INVALID_ARG). */
 
 #define APIC_NT 7  /* tally components per (species, bin): hits, charge, p_R, p_Z, L_z, E_kin, E_kin + E_bind */
 #define APIC_NH 10 /* history fields per step: t, current, drag F_Z, electric F_Z, torque T_z,

@@ -13,6 +13,7 @@ from . import build as _build
 
 NO_INJECT = 1
 NO_FIELD = 2
+CHORD = 4
 NT = 7
 NH = 10
 
@@ -139,6 +140,8 @@ def make_config(d):
         flags |= NO_INJECT
     if d.get("no_field"):
         flags |= NO_FIELD
+    if d.get("chord_absorb"):
+        flags |= CHORD
     c.flags = flags
     return c
 

@@ -41,6 +41,30 @@ static double r_grain(double alpha, double x2) {
   return (1.0 + sqrt(1.0 + 4.0 * alpha * x2)) / 2.0;
 }
 
+/* Grazing orbits (option OR_CHORD): the step's straight chord P(s) = (R + s dx,
+ * s dy, Z + s dz), s in [0, 1], in the local Cartesian frame of the start
+ * point, may pass through the grain although its end point lies outside.
+ * Returns the first of the points s = k / OR_CHORD_SAMPLES (k = 1..7) that
+ * lies inside the grain, or 0 if none does.  Chords whose closest approach
+ * to the origin stays beyond the grain's largest radius (1 + sqrt(1 +
+ * 4 |alpha|)) / 2 are not sampled. */
+static double chord_entry(double al, double R, double Z, double dx, double dy, double dz) {
+  double dd = dx * dx + dy * dy + dz * dz;
+  double s0 = dd > 0.0 ? -(R * dx + Z * dz) / dd : 0.0;
+  if (s0 < 0.0) s0 = 0.0;
+  if (s0 > 1.0) s0 = 1.0;
+  double px = R + s0 * dx, py = s0 * dy, pz = Z + s0 * dz;
+  double rmax = 0.5 * (1.0 + sqrt(1.0 + 4.0 * fabs(al)));
+  if (px * px + py * py + pz * pz >= rmax * rmax) return 0.0;
+  for (int k = 1; k < OR_CHORD_SAMPLES; ++k) {
+    double sk = (double)k / OR_CHORD_SAMPLES;
+    double qx = R + sk * dx, qy = sk * dy, qz = Z + sk * dz;
+    double rr = sqrt(qx * qx + qy * qy + qz * qz);
+    if (rr < r_grain(al, qz / rr)) return sk;
+  }
+  return 0.0;
+}
+
 /* Partial derivatives of (x1, x2) with respect to the cylindrical (R, Z) of
  * Eq. 8, obtained by the chain rule from Eq. 2 with r^2 = R^2 + Z^2 and
  * x2 = Z/r.  They are the "coordinate derivatives found analytically" that
@@ -683,10 +707,19 @@ static int push_one(or_sim* s, int spi, int64_t k) {
   double rn = sqrt(Rn * Rn + Zn * Zn);
   double x2n = Zn / rn;
   double x1n = or_x1_of(al, rn, x2n);
-  int st = rn < r_grain(al, x2n) ? 1 : (x1n > s->c.x1_out ? 2 : 0);
+  double tau = dt; /* chord time up to a point inside the grain */
+  int st = rn < r_grain(al, x2n) ? 1 : 0;
+  if (!st && (s->c.flags & OR_CHORD)) {
+    double se = chord_entry(al, R, Z, vx * dt, vy * dt, vz * dt);
+    if (se > 0.0) {
+      st = 1;
+      tau = dt * se;
+    }
+  }
+  if (!st && x1n > s->c.x1_out) st = 2;
   st = tape_status(s, st);
   if (st == 1) {
-    tally(s, spi, R, Z, vx, vz, vy, dt);
+    tally(s, spi, R, Z, vx, vz, vy, tau);
     return 1;
   }
   if (st == 2) return 2;
@@ -755,10 +788,19 @@ static void inject(or_sim* s) {
       double rn = sqrt(Rn * Rn + Zn * Zn);
       double x2n = Zn / rn;
       double x1n = or_x1_of(al, rn, x2n);
-      int st = rn < r_grain(al, x2n) ? 1 : (x1n > s->c.x1_out ? 2 : 0);
+      double tau_in = tau; /* flight time up to a point inside the grain */
+      int st = rn < r_grain(al, x2n) ? 1 : 0;
+      if (!st && (s->c.flags & OR_CHORD)) {
+        double se = chord_entry(al, R, Z, vx * tau, vy * tau, vz * tau);
+        if (se > 0.0) {
+          st = 1;
+          tau_in = tau * se;
+        }
+      }
+      if (!st && x1n > s->c.x1_out) st = 2;
       st = tape_status(s, st);
       if (st == 1) {
-        tally(s, spi, R, Z, vx, vz, vy, tau);
+        tally(s, spi, R, Z, vx, vz, vy, tau_in);
         p->absorbed++;
         continue;
       }

@@ -24,6 +24,8 @@ extern "C" {
 
 #define OR_NO_INJECT 1   /* skip surface injection (Sec. 1 injection) */
 #define OR_NO_FIELD 2    /* phi == 0 everywhere: no deposit/Poisson feed-back */
+#define OR_CHORD 4       /* also absorb when the step's chord passes through the grain */
+#define OR_CHORD_SAMPLES 8 /* the chord is tested at s = k / OR_CHORD_SAMPLES, k = 1..7 */
 
 #define OR_NT 7          /* tally components per bin */
 #define OR_NH 10         /* history fields per step */

@@ -171,6 +171,7 @@ struct apic_sim {
   long long slots = 0;                // particle slots of one buffer (all populations)
   long long sorts = 0;                // particle sorts launched
   size_t bcr_bytes = 0;               // reduction blocks + tail inverse (one device range)
+  bool chord = false;                 // some instance absorbs grazing orbits (APIC_CHORD_ABSORB)
   size_t l2_persist = 0;              // bytes of L2 set aside for them (0: none)
   long long tab_total = 0;
   TanPtrs tan{};                      // sensitivity-window state (allocated on first use)
@@ -1138,6 +1139,7 @@ static int setup(apic_sim* S) {
   if (const char* cl = std::getenv("APIC_COND_LOOP")) S->cond_loop = std::atoi(cl) != 0;
   for (const Inst& I : S->inst) S->max_n2 = std::max(S->max_n2, I.n2);
   push_window_rows<Real>(S->max_n2);  // the occupancy query happens here, not inside a graph capture
+  for (const Inst& I : S->inst) S->chord = S->chord || (I.flags & APIC_CHORD_ABSORB) != 0;
   // the whole Poisson solve as one cooperative kernel, unless disabled or not co-residable
   const char* env = std::getenv("APIC_SOLVER");
   // one cooperative launch per solve for a single instance; batches use the
@@ -1309,7 +1311,7 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
         launch_surface(d, s);
       }
       break;
-    case 3: launch_push<Real>(d, S->push_grid, S->max_n2, s); break;
+    case 3: launch_push<Real>(d, S->push_grid, S->max_n2, S->chord, s); break;
     case 4: launch_inject<Real>(d, S->max_inj, s); break;
     case 5: launch_step_end(d, s); break;
     case 6: launch_sort<Real>(d, S->push_grid, s); break;  // not a step phase: the particle sort
@@ -1851,6 +1853,7 @@ static bool solve_now(apic_sim* S, const DevPtrs& d) {
 
 template <class Real>
 static int sensitivity_impl(apic_sim* S, int n, double* values, double* jac) {
+  if (S->chord) return S->fail(APIC_ERR_INVALID_ARG, "the sensitivity window does not take APIC_CHORD_ABSORB");
   if (!tangent_setup<Real>(S)) return S->status;
   const TanPtrs& t = S->tan;
   const DevPtrs d = S->view(S->par);

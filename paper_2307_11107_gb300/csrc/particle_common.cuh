@@ -8,6 +8,7 @@
 using Real = APIC_REAL;
 constexpr bool kF64 = sizeof(Real) == 8;
 constexpr int kBisect = kF64 ? 40 : 24;
+constexpr int kChordSamples = 8;  // the chord option tests s = k / kChordSamples, k = 1..7
 
 template <class T>
 struct Pair;
@@ -89,6 +90,29 @@ __device__ __forceinline__ Cell locate(const Inst& I, Real x1, Real x2) {
 // start point), then the transferred charge, momentum (R at the impact
 // azimuth, Z), angular momentum L_z = m R v_Theta and energy are added to the
 // surface bin of the impact x2 (Sec. 1).
+// Grazing orbits (APIC_CHORD_ABSORB): the step's straight chord P(s) = (R +
+// s dx, s dy, Z + s dz), s in [0, 1], in the local Cartesian frame of the
+// start point, may pass through the grain although its end point lies
+// outside.  Returns the first of the points s = k / kChordSamples that lies
+// inside the grain, or 0; chords whose closest approach to the origin stays
+// beyond the grain's largest radius (1 + sqrt(1 + 4 |alpha|)) / 2 are not
+// sampled.
+__device__ __noinline__ Real chord_entry(Real al, Real R, Real Z, Real dx, Real dy, Real dz) {
+  const Real dd = dx * dx + dy * dy + dz * dz;
+  Real s0 = dd > Real(0) ? -(R * dx + Z * dz) / dd : Real(0);
+  s0 = s0 < Real(0) ? Real(0) : (s0 > Real(1) ? Real(1) : s0);
+  const Real px = R + s0 * dx, py = s0 * dy, pz = Z + s0 * dz;
+  const Real rmax = Real(0.5) * (Real(1) + sqrt(Real(1) + Real(4) * fabs(al)));
+  if (px * px + py * py + pz * pz >= rmax * rmax) return Real(0);
+  for (int k = 1; k < kChordSamples; ++k) {
+    const Real sk = (Real)k / (Real)kChordSamples;
+    const Real qx = R + sk * dx, qy = sk * dy, qz = Z + sk * dz;
+    const Real rr = sqrt(qx * qx + qy * qy + qz * qz);
+    if (rr < r_grain(al, qz / rr)) return sk;
+  }
+  return Real(0);
+}
+
 __device__ void absorb_tally(const DevPtrs& d, const Inst& I, const Pop& P, Real R, Real Z, Real vx, Real vz,
                              Real vy, Real tau) {
   Real al = (Real)I.alpha;

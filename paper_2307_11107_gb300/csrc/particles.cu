@@ -242,6 +242,9 @@ constexpr int kPushUnroll = APIC_PUSH_UNROLL;  // items of the chunk loop unroll
 // FP32: 64 registers, four CTAs of 256 threads per SM; FP64 (parity build): two
 #define APIC_PUSH_MIN_BLOCKS (sizeof(APIC_REAL) == 4 ? 4 : 2)
 #endif
+// kChord: some instance absorbs grazing orbits (APIC_CHORD_ABSORB); the
+// instantiation without it carries no trace of the test.
+template <bool kChord>
 __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, int win_n2, int win_rows, int group) {
   // dynamic shared memory: the deposit window, then the chunk prefix over the
   // populations and their constants (sized by the batch, so that a small
@@ -491,9 +494,18 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
       float rn = rn2 * irn;
       float x2n = Zn * irn;
       float tr = 2.0f * rn - 1.0f;
-      if (tr < 0.0f || tr * tr < 1.0f + 4.0f * al * x2n) {
+      bool hit = tr < 0.0f || tr * tr < 1.0f + 4.0f * al * x2n;
+      float tau = dt;  // chord time up to a point inside the grain
+      if (kChord && !hit && (d.inst[d.pop[pop].inst].flags & APIC_CHORD_ABSORB)) {
+        const float se = chord_entry(al, R, Z, vx * dt, vy * dt, vz * dt);
+        if (se > 0.0f) {
+          hit = true;
+          tau = dt * se;
+        }
+      }
+      if (hit) {
         const Pop& P = d.pop[pop];
-        absorb_tally(d, d.inst[P.inst], P, R, Z, vx, vz, vy, dt);
+        absorb_tally(d, d.inst[P.inst], P, R, Z, vx, vz, vy, tau);
         X1[t0 + o] = Real(2);
         fate = 1;
       } else {
@@ -557,9 +569,18 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
       Real vRn = cr * vx + sr * vy, vTn = -sr * vx + cr * vy;
       Real rn = sqrt(Rn * Rn + Zn * Zn);
       Real x2n = Zn / rn;
-      if (rn < r_grain(al, x2n)) {
+      bool hit = rn < r_grain(al, x2n);
+      Real tau = dt;  // chord time up to a point inside the grain
+      if (kChord && !hit && (d.inst[d.pop[pop].inst].flags & APIC_CHORD_ABSORB)) {
+        const Real se = chord_entry(al, R, Z, vx * dt, vy * dt, vz * dt);
+        if (se > Real(0)) {
+          hit = true;
+          tau = dt * se;
+        }
+      }
+      if (hit) {
         const Pop& P = d.pop[pop];
-        absorb_tally(d, d.inst[P.inst], P, R, Z, vx, vz, vy, dt);
+        absorb_tally(d, d.inst[P.inst], P, R, Z, vx, vz, vy, tau);
         X1[t0 + o] = Real(2);
         fate = 1;
       } else {
@@ -813,8 +834,17 @@ __global__ void __launch_bounds__(256) k_inject(DevPtrs d) {
     }
     Real rn = sqrt(Rn * Rn + Zn * Zn);
     x2n = Zn / rn;
-    if (rn < r_grain(al, x2n)) {
-      absorb_tally(d, I, P, R, Z, vx, vz, vy, tau);
+    bool hit = rn < r_grain(al, x2n);
+    Real tau_in = tau;  // flight time up to a point inside the grain
+    if (!hit && (I.flags & APIC_CHORD_ABSORB)) {
+      const Real se = chord_entry(al, R, Z, vx * tau, vy * tau, vz * tau);
+      if (se > Real(0)) {
+        hit = true;
+        tau_in = tau * se;
+      }
+    }
+    if (hit) {
+      absorb_tally(d, I, P, R, Z, vx, vz, vy, tau_in);
       fate = 1;
     } else {
       x1n = x1_at(al, rn, x2n);
@@ -1157,9 +1187,9 @@ int push_window_rows<Real>(int max_n2) {
     if (e) rows = std::max(2, std::min(kWinRows, std::atoi(e)));
     for (; !e && rows > 2; --rows) {
       const int sm = push_smem(rows, win_n2, kMaxPop);
-      cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      cudaFuncSetAttribute(k_push<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
       int per = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push, 256, sm) == cudaSuccess &&
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push<false>, 256, sm) == cudaSuccess &&
           per >= (int)APIC_PUSH_MIN_BLOCKS)
         break;
     }
@@ -1170,18 +1200,20 @@ int push_window_rows<Real>(int max_n2) {
 }
 
 template <>
-void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, cudaStream_t s) {
+void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, bool chord, cudaStream_t s) {
   const int win_n2 = max_n2 < kWinMaxN2 - 1 ? max_n2 : kWinMaxN2 - 1;
   const int rows = push_window_rows<Real>(max_n2);
   const int sm = push_smem(rows, win_n2, d.n_pop);
-  cudaFuncSetAttribute(k_push, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  const void* kern = chord ? (const void*)k_push<true> : (const void*)k_push<false>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   static int group = -1;  // chunks per group (APIC_PUSH_GROUP, default 4: the fastest of 1, 2, 4, 8 measured)
   if (group < 0) {
     const char* e = std::getenv("APIC_PUSH_GROUP");
     group = e ? std::max(1, std::atoi(e)) : 4;
   }
   cudaMemsetAsync(d.cnt + 1, 0, sizeof(long long), s);  // the group counter
-  k_push<<<grid, 256, sm, s>>>(d, win_n2, rows, group);
+  if (chord) k_push<true><<<grid, 256, sm, s>>>(d, win_n2, rows, group);
+  else k_push<false><<<grid, 256, sm, s>>>(d, win_n2, rows, group);
 }
 
 template <>
