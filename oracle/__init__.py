@@ -14,8 +14,9 @@ from . import build as _build
 NO_INJECT = 1
 NO_FIELD = 2
 CHORD = 4
+FLOATING = 8
 NT = 7
-NH = 10
+NH = 11
 
 
 class _Species(C.Structure):
@@ -142,6 +143,8 @@ def make_config(d):
         flags |= NO_FIELD
     if d.get("chord_absorb"):
         flags |= CHORD
+    if d.get("floating"):
+        flags |= FLOATING
     c.flags = flags
     return c
 

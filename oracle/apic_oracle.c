@@ -206,6 +206,11 @@ struct or_sim {
   int64_t hist_n, hist_cap, step;
   double Q, FZ;
   double step_tally[5]; /* this step's charge, pZ, Lz, heat, events (history) */
+  /* isolated grain (OR_FLOATING): potential of this step, collected charge,
+   * and the vacuum field of a grain at potential 1 (outer boundary at 0) */
+  double phig, Qg, C_vac;
+  int qg_set;
+  double* phi_vac;
   /* decision tape: one status byte per particle update and per injection
    * draw, in processing order, and one injection count per step and species */
   int tape_mode;        /* OR_TAPE_OFF, OR_TAPE_RECORD, OR_TAPE_REPLAY */
@@ -434,19 +439,19 @@ static void build_matrix(or_sim* s) {
   }
 }
 
-int or_solve(or_sim* s, const double* rho_in, double* phi_out) {
-  if (!s->band) return -1;
-  const double* rho = rho_in ? rho_in : s->rho;
+/* The Dirichlet problem of Eqs. 6-7 for charge density rho (NULL: zero) with
+ * phi = phig on the grain and phi = phiout on the outer surface. */
+static void solve_dirichlet(or_sim* s, const double* rho, double phig, double phiout, double* phi) {
   int n = s->nu, kl = s->kl, kuu = s->kl + s->ku;
   double* b = (double*)malloc(sizeof(double) * (size_t)n);
   for (int i = 1; i < s->c.n1; ++i)
     for (int j = 0; j < s->N2; ++j) {
       double w[3][5];
       stencil(s, i, j, w);
-      double rhs = -rho[i * s->N2 + j];
+      double rhs = rho ? -rho[i * s->N2 + j] : 0.0;
       for (int dj = -2; dj <= 2; ++dj) {
-        if (i - 1 == 0) rhs -= w[0][dj + 2] * s->c.phi_g;
-        if (i + 1 == s->c.n1) rhs -= w[2][dj + 2] * s->c.phi_out;
+        if (i - 1 == 0) rhs -= w[0][dj + 2] * phig;
+        if (i + 1 == s->c.n1) rhs -= w[2][dj + 2] * phiout;
       }
       b[UIDX(s, i, j)] = rhs;
     }
@@ -461,14 +466,19 @@ int or_solve(or_sim* s, const double* rho_in, double* phi_out) {
     int r0 = j - kuu > 0 ? j - kuu : 0;
     for (int r = r0; r < j; ++r) b[r] -= BAND(s, r, j) * b[j];
   }
-  double* phi = phi_out ? phi_out : s->phi;
   for (int j = 0; j < s->N2; ++j) {
-    phi[j] = s->c.phi_g;
-    phi[s->c.n1 * s->N2 + j] = s->c.phi_out;
+    phi[j] = phig;
+    phi[s->c.n1 * s->N2 + j] = phiout;
   }
   for (int i = 1; i < s->c.n1; ++i)
     for (int j = 0; j < s->N2; ++j) phi[i * s->N2 + j] = b[UIDX(s, i, j)];
   free(b);
+}
+
+/* The configured boundary values (phi_g, phi_out). */
+int or_solve(or_sim* s, const double* rho_in, double* phi_out) {
+  if (!s->band) return -1;
+  solve_dirichlet(s, rho_in ? rho_in : s->rho, s->c.phi_g, s->c.phi_out, phi_out ? phi_out : s->phi);
   return 0;
 }
 
@@ -515,6 +525,23 @@ void or_surface(or_sim* s, double* En_out, double* Q, double* FZ) {
   }
   *Q = q;
   *FZ = fz;
+}
+
+/* The grain charge Q of or_surface for an arbitrary potential phi (its rows
+ * i = 0..2 enter through the one-sided dphi/dx1 on the grain). */
+static double grain_charge(const or_sim* s, const double* phi) {
+  int N2 = s->N2;
+  double q = 0.0;
+  for (int j = 0; j <= s->c.n2; ++j) {
+    double x2 = x2_node(s, j);
+    double m[4];
+    or_metric(s->c.alpha, r_grain(s->c.alpha, x2), x2, m);
+    double g1 = (-3.0 * phi[j] + 4.0 * phi[N2 + j] - phi[2 * N2 + j]) / (2.0 * s->h1);
+    double En = -g1 * sqrt(m[0] * m[0] + m[1] * m[1]);
+    double tw = (j == 0 || j == s->c.n2) ? 0.5 * s->h2 : s->h2;
+    q += tw * En * or_dA_dx2(s->c.alpha, -1.0, x2);
+  }
+  return q;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -829,6 +856,7 @@ static void record_history(or_sim* s) {
   h[7] = (double)s->sp[0].n;
   h[8] = s->c.n_species > 1 ? (double)s->sp[1].n : 0.0;
   h[9] = s->step_tally[4];
+  h[10] = s->phig;
 }
 
 static void field_phase(or_sim* s) {
@@ -842,7 +870,26 @@ static void field_phase(or_sim* s) {
     s->FZ = 0.0;
     return;
   }
-  or_solve(s, NULL, NULL);
+  if (s->c.flags & OR_FLOATING) {
+    /* Isolated grain (an option; the paper holds phi_g fixed, Sec. 1): the
+     * grain is an equipotential whose charge is what it has collected.  The
+     * problem is linear, so phi = phi_0 + phi_g phi_vac, with phi_0 the
+     * solution for this rho with the grain at 0 and phi_vac the vacuum field
+     * of a grain at 1 (outer boundary at 0); phi_g follows from
+     * Q(phi) = Q_grain, Q being linear in phi.  The first step fixes
+     * Q_grain as the charge that holds the grain at the configured phi_g. */
+    size_t nn = (size_t)s->N1 * s->N2;
+    solve_dirichlet(s, s->rho, 0.0, s->c.phi_out, s->phi);
+    double q0 = grain_charge(s, s->phi);
+    if (!s->qg_set) {
+      s->Qg = q0 + s->c.phi_g * s->C_vac;
+      s->qg_set = 1;
+    }
+    s->phig = (s->Qg - q0) / s->C_vac;
+    for (size_t k = 0; k < nn; ++k) s->phi[k] += s->phig * s->phi_vac[k];
+  } else {
+    or_solve(s, NULL, NULL);
+  }
   or_gradients(s);
   or_surface(s, NULL, &s->Q, &s->FZ);
 }
@@ -855,6 +902,7 @@ int or_step(or_sim* s, int n_steps) {
     memset(s->step_tally, 0, sizeof(s->step_tally));
     compact_push(s);
     if (!(s->c.flags & OR_NO_INJECT)) inject(s);
+    if (s->c.flags & OR_FLOATING) s->Qg += s->step_tally[0]; /* charge collected this step */
     record_history(s);
     s->step++;
   }
@@ -885,6 +933,16 @@ or_sim* or_create(const or_config* cfg) {
   build_volumes(s);
   build_tables(s);
   if (!(cfg->flags & OR_NO_FIELD)) build_matrix(s);
+  s->phig = cfg->phi_g;
+  if ((cfg->flags & OR_FLOATING) && (cfg->flags & OR_NO_FIELD)) {
+    or_destroy(s);
+    return NULL;
+  }
+  if (cfg->flags & OR_FLOATING) {
+    s->phi_vac = (double*)calloc(nn, sizeof(double));
+    solve_dirichlet(s, NULL, 1.0, 0.0, s->phi_vac);
+    s->C_vac = grain_charge(s, s->phi_vac);
+  }
   for (int k = 0; k < cfg->n_species; ++k) {
     s->w[k] = s->V_dom / (double)cfg->sp[k].n_init;
     double gam = sqrt(cfg->sp[k].T / (2.0 * OR_PI * cfg->sp[k].m));
@@ -901,7 +959,7 @@ void or_destroy(or_sim* s) {
     free(p->x1); free(p->x2); free(p->vR); free(p->vZ); free(p->vT); free(p->id);
   }
   free(s->rho); free(s->phi); free(s->G1); free(s->G2); free(s->V);
-  free(s->band); free(s->piv); free(s->bins); free(s->hist);
+  free(s->band); free(s->piv); free(s->bins); free(s->hist); free(s->phi_vac);
   free(s->tape_st); free(s->tape_nk);
   free(s);
 }

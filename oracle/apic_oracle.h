@@ -26,9 +26,10 @@ extern "C" {
 #define OR_NO_FIELD 2    /* phi == 0 everywhere: no deposit/Poisson feed-back */
 #define OR_CHORD 4       /* also absorb when the step's chord passes through the grain */
 #define OR_CHORD_SAMPLES 8 /* the chord is tested at s = k / OR_CHORD_SAMPLES, k = 1..7 */
+#define OR_FLOATING 8    /* isolated grain: its potential follows the charge it collects */
 
 #define OR_NT 7          /* tally components per bin */
-#define OR_NH 10         /* history fields per step */
+#define OR_NH 11         /* history fields per step (the last: the grain potential used) */
 
 typedef struct {
   double q, m, T;

@@ -201,7 +201,7 @@ def test_count_balance_and_history_with_field():
     for c in s.counts():
         assert c["loaded"] + c["injected"] == c["absorbed"] + c["escaped"] + c["resident"]
     h = s.history()
-    assert h.shape == (20, 10) and np.isfinite(h).all()
+    assert h.shape == (20, 11) and np.isfinite(h).all()
     b = s.bins()
     assert b[:, :, 0].sum() == sum(c["absorbed"] for c in s.counts())
 
