@@ -75,10 +75,18 @@ extern "C" {
                                 tested at 7 interior points once it comes closer to the origin than the
                                 grain's largest radius; impact point by bisection up to the first point
                                 inside).  Not with apic_sensitivity (INVALID_ARG). */
+#define APIC_FLOATING 8      /* isolated grain: phi_grain is the potential of the first step only; from then
+                                on the grain keeps the charge it held then plus every charge it absorbs, and
+                                its potential follows (history column 10).  Each step's field is the solve
+                                at the last potential plus the multiple of the grain's vacuum field (phi = 1
+                                on the grain, 0 outside, computed at creation) that restores that charge.
+                                Not with APIC_NO_FIELD, nor with apic_sensitivity (INVALID_ARG);
+                                apic_solve_poisson keeps using phi_grain. */
 
 #define APIC_NT 7  /* tally components per (species, bin): hits, charge, p_R, p_Z, L_z, E_kin, E_kin + E_bind */
-#define APIC_NH 10 /* history fields per step: t, current, drag F_Z, electric F_Z, torque T_z,
-                      heat flux, grain charge Q, resident species 0, resident species 1, absorbed events */
+#define APIC_NH 11 /* history fields per step: t, current, drag F_Z, electric F_Z, torque T_z,
+                      heat flux, grain charge Q, resident species 0, resident species 1, absorbed events,
+                      grain potential of the step's field */
 
 typedef struct {
   double q;          /* charge in e (electron -1) */
@@ -102,7 +110,7 @@ typedef struct {
   uint64_t seed;         /* Philox4x32-10 key */
   int32_t instance;      /* Philox counter tag; distinct instances draw distinct streams */
   int32_t precision;     /* APIC_FP64 or APIC_FP32_REFINED */
-  int32_t flags;         /* APIC_NO_INJECT | APIC_NO_FIELD */
+  int32_t flags;         /* APIC_NO_INJECT | APIC_NO_FIELD | APIC_CHORD_ABSORB | APIC_FLOATING */
   double poisson_tol;    /* relative residual target ||b - A phi|| / ||b|| (0: 1e-10) */
   int32_t poisson_max_iter; /* BiCGSTAB iterations per step (0: 20) */
   int32_t sort_interval; /* sort particles by cell every this many steps (0: never) */

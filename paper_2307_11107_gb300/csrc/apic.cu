@@ -172,6 +172,7 @@ struct apic_sim {
   long long sorts = 0;                // particle sorts launched
   size_t bcr_bytes = 0;               // reduction blocks + tail inverse (one device range)
   bool chord = false;                 // some instance absorbs grazing orbits (APIC_CHORD_ABSORB)
+  bool floating = false;              // some instance has an isolated grain (APIC_FLOATING)
   size_t l2_persist = 0;              // bytes of L2 set aside for them (0: none)
   long long tab_total = 0;
   TanPtrs tan{};                      // sensitivity-window state (allocated on first use)
@@ -251,6 +252,8 @@ int validate(const apic_config_t& c, std::string& why) {
       return why = "bad species parameters (m > 0, T >= 0, n_init > 0, 0 < capacity < 2^31)", APIC_ERR_INVALID_ARG;
   }
   if (c.precision != APIC_FP64 && c.precision != APIC_FP32_REFINED) return why = "bad precision", APIC_ERR_INVALID_ARG;
+  if ((c.flags & APIC_FLOATING) && (c.flags & APIC_NO_FIELD))
+    return why = "APIC_FLOATING needs the field (not with APIC_NO_FIELD)", APIC_ERR_INVALID_ARG;
   return APIC_OK;
 }
 
@@ -419,6 +422,19 @@ void build_fine(const Inst& I, HostLevel& L, std::vector<double>& rscale, std::v
       bbc[nd] = bb;
       for (int k = 0; k < kSt; ++k) L.at(k, i, j) = w[k];
     }
+}
+
+// The Dirichlet term of the problem with phi = 1 on the grain and 0 on the
+// outer surface, rows scaled as build_fine's (nonzero on the row i = 1 only).
+void grain_bbc(const Inst& I, std::vector<double>& hbg) {
+  hbg.assign((size_t)I.nodes, 0.0);
+  for (int j = 0; j <= I.n2; ++j) {
+    double w[kSt];
+    double sc = 1.0 / fine_row<double>(I, I.alpha, 1, j, w);
+    double bb = 0.0;
+    for (int dj = -1; dj <= 1; ++dj) bb -= w[st_slot(-1, dj)] * sc;
+    hbg[(size_t)I.N2 + j] = bb;
+  }
 }
 
 // ---- block cyclic reduction set-up (FP64 on the host, blocks stored in FP32) ----
@@ -665,6 +681,9 @@ bool bcr_factor(const HostLevel& L, const BcrInst& bp, std::vector<float>& out, 
 // ---------------------------------------------------------------------------
 // Creation.
 // ---------------------------------------------------------------------------
+template <class Real>
+static bool vacuum_fields(apic_sim* S);
+
 template <class Real>
 static int setup(apic_sim* S) {
   const int ni = S->n_inst;
@@ -980,6 +999,11 @@ static int setup(apic_sim* S) {
   }
   double** node_arrays[] = {&d.rho, &d.phi, &d.phi_prev, &d.V, &d.Vinv, &d.bbc, &d.rscale, &d.b, &d.r, &d.rh, &d.p, &d.v, &d.s, &d.t, &d.ph, &d.sh};
   for (double** a : node_arrays) *a = (double*)A(sizeof(double) * total_nodes);
+  for (const Inst& I : S->inst) S->floating = S->floating || (I.flags & APIC_FLOATING) != 0;
+  if (S->floating) {
+    d.bbc_g = (double*)A(sizeof(double) * total_nodes);
+    d.phi_vac = (double*)A(sizeof(double) * total_nodes);
+  }
   S->phi_save = (double*)A(sizeof(double) * total_nodes);
   d.st64 = (double*)A(sizeof(double) * kSt * total_nodes);
   d.acc = (unsigned long long*)A(sizeof(unsigned long long) * 2 * total_nodes);
@@ -1165,6 +1189,7 @@ static int setup(apic_sim* S) {
     cudaGetLastError();
   }
   cudaGetLastError();
+  if (S->floating && !vacuum_fields<Real>(S)) return S->status;
   return S->sync() ? APIC_OK : S->status;
 }
 
@@ -1309,6 +1334,10 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
       if (S->plan.bcr.n_inst == 0) {  // the reduction solve ends with them
         launch_gradients<Real>(d, s);
         launch_surface(d, s);
+      }
+      if (S->floating) {  // the isolated grains' correction (chosen by the surface step), then the gradients again
+        launch_float_phi(d, s);
+        launch_gradients<Real>(d, s);
       }
       break;
     case 3: launch_push<Real>(d, S->push_grid, S->max_n2, S->chord, s); break;
@@ -1662,6 +1691,24 @@ extern "C" int apic_tallies(apic_sim* S, int32_t instance, apic_tallies_t* out) 
   return APIC_OK;
 }
 
+// Solve of instance inst for the right-hand side in d.b (with its |b|^2
+// partials), from the guess in d.phi; the other instances keep their phi.
+template <class Real>
+static bool solve_instance(apic_sim* S, int inst) {
+  DevPtrs& d = S->d;
+  if (S->coop > 0) return S->ck(solve_coop<Real>(S, d, S->stream, 0, inst), "cooperative solve");
+  launch_bicg_init<Real>(d, S->stream);
+  int it = 0;
+  SolverState sol;
+  for (;;) {
+    launch_bicg_iter<Real>(d, S->plan, S->stream);
+    launch_bicg_check(d, 0, 0, S->stream);
+    if (!S->d2h(&sol, d.sol + inst, 1) || !S->sync()) return false;
+    if (sol.done || ++it > 1000) break;
+  }
+  return true;
+}
+
 template <class Real>
 static int solve_impl(apic_sim* S, int inst, const double* rho, double* phi_out) {
   const Inst& I = S->inst[inst];
@@ -1671,23 +1718,41 @@ static int solve_impl(apic_sim* S, int inst, const double* rho, double* phi_out)
     return S->status;
   if (rho && !S->h2d(d.rho + I.node_off, rho, (size_t)I.nodes)) return S->status;
   launch_b_from_rho(d, inst, S->stream);
-  if (S->coop > 0) {
-    if (!S->ck(solve_coop<Real>(S, d, S->stream, 0, inst), "cooperative solve")) return S->status;
-  } else {
-    launch_bicg_init<Real>(d, S->stream);
-    int it = 0;
-    SolverState sol;
-    for (;;) {
-      launch_bicg_iter<Real>(d, S->plan, S->stream);
-      launch_bicg_check(d, 0, 0, S->stream);
-      if (!S->d2h(&sol, d.sol + inst, 1) || !S->sync()) return S->status;
-      if (sol.done || ++it > 1000) break;
-    }
-  }
+  if (!solve_instance<Real>(S, inst)) return S->status;
   if (phi_out) S->d2h(phi_out, d.phi + I.node_off, (size_t)I.nodes);
   S->ck(cudaMemcpyAsync(d.phi, S->phi_save, sizeof(double) * d.total_nodes, cudaMemcpyDeviceToDevice, S->stream),
         "restore phi");
   return read_status(S);
+}
+
+// Vacuum field of every isolated grain (APIC_FLOATING): the solve with no
+// charge, phi = 1 on the grain and 0 on the outer surface, kept in phi_vac
+// (its boundary rows included); each grain's potential starts at the
+// configured one.  The step's phi is restored afterwards.
+template <class Real>
+static bool vacuum_fields(apic_sim* S) {
+  DevPtrs& d = S->d;
+  std::vector<StepState> st((size_t)S->n_inst);
+  std::memset((void*)st.data(), 0, sizeof(StepState) * st.size());
+  for (int k = 0; k < S->n_inst; ++k) st[k].phig = S->inst[k].phi_g;
+  if (!S->h2d(d.stp, st.data(), st.size()) ||
+      !S->ck(cudaMemcpyAsync(S->phi_save, d.phi, sizeof(double) * d.total_nodes, cudaMemcpyDeviceToDevice, S->stream),
+             "save phi"))
+    return false;
+  for (int k = 0; k < S->n_inst; ++k) {
+    const Inst& I = S->inst[k];
+    if (!(I.flags & APIC_FLOATING)) continue;
+    std::vector<double> hbg;
+    grain_bbc(I, hbg);
+    if (!S->h2d(d.bbc_g + I.node_off, hbg.data(), hbg.size())) return false;
+    launch_b_vacuum(d, k, S->stream);
+    if (!solve_instance<Real>(S, k)) return false;
+    launch_store_vacuum(d, k, S->stream);
+    if (!S->sync()) return false;  // hbg goes out of scope
+  }
+  return S->ck(cudaMemcpyAsync(d.phi, S->phi_save, sizeof(double) * d.total_nodes, cudaMemcpyDeviceToDevice, S->stream),
+               "restore phi") &&
+         S->ck(cudaGetLastError(), "vacuum field") && S->sync() && read_status(S) == APIC_OK;
 }
 
 extern "C" int apic_solve_poisson(apic_sim* S, int32_t instance, const double* rho, double* phi_out) {
@@ -1815,21 +1880,15 @@ static bool tangent_setup(apic_sim* S) {
     volumes_t<D1h>(I, al, V);
     std::vector<double> hV(V.size());
     for (size_t q = 0; q < V.size(); ++q) hV[q] = V[q].d[0];
-    std::vector<double> hst((size_t)kSt * I.nodes, 0.0), hbg((size_t)I.nodes, 0.0);
+    std::vector<double> hst((size_t)kSt * I.nodes, 0.0), hbg;
     for (int i = 1; i < I.n1; ++i)
       for (int j = 0; j <= I.n2; ++j) {
         size_t nd = (size_t)i * I.N2 + j;
         D1h wd[kSt];
         fine_row<D1h>(I, al, i, j, wd);
         for (int q = 0; q < kSt; ++q) hst[(size_t)q * I.nodes + nd] = wd[q].d[0];
-        if (i == 1) {
-          double w[kSt];
-          double sc = 1.0 / fine_row<double>(I, I.alpha, i, j, w);
-          double bb = 0.0;
-          for (int dj = -1; dj <= 1; ++dj) bb -= w[st_slot(-1, dj)] * sc;
-          hbg[nd] = bb;
-        }
       }
+    grain_bbc(I, hbg);
     S->h2d(t.dtab + I.tab_off, htab.data(), htab.size());
     S->h2d(t.dV + I.node_off, hV.data(), hV.size());
     S->h2d(t.dst + (long long)kSt * I.node_off, hst.data(), hst.size());
@@ -1854,6 +1913,7 @@ static bool solve_now(apic_sim* S, const DevPtrs& d) {
 template <class Real>
 static int sensitivity_impl(apic_sim* S, int n, double* values, double* jac) {
   if (S->chord) return S->fail(APIC_ERR_INVALID_ARG, "the sensitivity window does not take APIC_CHORD_ABSORB");
+  if (S->floating) return S->fail(APIC_ERR_INVALID_ARG, "the sensitivity window does not take APIC_FLOATING");
   if (!tangent_setup<Real>(S)) return S->status;
   const TanPtrs& t = S->tan;
   const DevPtrs d = S->view(S->par);

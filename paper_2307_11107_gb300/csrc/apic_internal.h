@@ -109,7 +109,10 @@ struct StepState {
   long long step;
   double Q, FZ;            // grain charge and electric force of the last solve
   double tally[5];         // this step: charge, p_Z, L_z, heat, events
-  double pad[6];
+  // isolated grain (APIC_FLOATING): potential of the last field, the grain
+  // charge it holds, the last correction, whether qg has been fixed yet
+  double phig, qg, dphig, qg_set;
+  double pad[2];
 };
 
 struct BcrInst;
@@ -136,6 +139,8 @@ struct DevPtrs {
   // per-node FP64 arrays
   double *rho, *phi, *phi_prev, *V, *bbc, *rscale;
   double* Vinv;                   // 1 / V (the density without a division per node)
+  double* bbc_g;                  // Dirichlet term of phi = 1 on the grain, 0 outside (APIC_FLOATING; else null)
+  double* phi_vac;                // vacuum field of that problem, boundary rows included (APIC_FLOATING)
   double *b, *r, *rh, *p, *v, *s, *t, *ph, *sh;
   double* st64;                   // finest-level stencil, FP64 [kSt][nodes] per instance (same offsets)
   unsigned long long* acc;        // deposit accumulators
@@ -225,6 +230,9 @@ void launch_gradients(const DevPtrs& d, cudaStream_t s);
 void launch_surface(const DevPtrs& d, cudaStream_t s);
 void launch_step_end(const DevPtrs& d, cudaStream_t s);
 void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s);
+void launch_b_vacuum(const DevPtrs& d, int inst, cudaStream_t s);
+void launch_store_vacuum(const DevPtrs& d, int inst, cudaStream_t s);
+void launch_float_phi(const DevPtrs& d, cudaStream_t s);
 
 // Block cyclic reduction (bcr.cu) of the finest-level system of every
 // instance of a batch.  Instance k has the unknown rows i = 1..M (M = n1 - 1)

@@ -62,6 +62,49 @@ __global__ void __launch_bounds__(256) k_b_from_rho(DevPtrs d, int inst) {
   if (threadIdx.x == 0) d.red[((long long)inst * kNRed + 0) * kRedBlocks + blockIdx.x] = tot;
 }
 
+// b = the Dirichlet term of a grain at potential 1 (outer boundary at 0) and
+// no charge, for the vacuum field of an isolated grain; |b|^2 partials as
+// k_b_from_rho.
+__global__ void __launch_bounds__(256) k_b_vacuum(DevPtrs d, int inst) {
+  __shared__ double sh[256];
+  const Inst& I = d.inst[inst];
+  double part = 0.0;
+  for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes;
+       nd += (long long)gridDim.x * blockDim.x) {
+    long long g = I.node_off + nd;
+    int i = (int)(nd / I.N2);
+    double bv = i > 0 && i < I.n1 ? d.bbc_g[g] : 0.0;
+    d.b[g] = bv;
+    part += bv * bv;
+  }
+  double tot = block_sum(part, sh);
+  if (threadIdx.x == 0) d.red[((long long)inst * kNRed + 0) * kRedBlocks + blockIdx.x] = tot;
+}
+
+// phi_vac = the solver's interior values, 1 on the grain row, 0 on the outer row.
+__global__ void __launch_bounds__(256) k_store_vacuum(DevPtrs d, int inst) {
+  const Inst& I = d.inst[inst];
+  for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes;
+       nd += (long long)gridDim.x * blockDim.x) {
+    long long g = I.node_off + nd;
+    int i = (int)(nd / I.N2);
+    d.phi_vac[g] = i == 0 ? 1.0 : (i == I.n1 ? 0.0 : d.phi[g]);
+  }
+}
+
+// phi += dphig * phi_vac at every node of every isolated grain (the correction
+// surface_block chose; the gradients are taken again afterwards).
+__global__ void __launch_bounds__(256) k_float_phi(DevPtrs d) {
+  const Inst& I = d.inst[blockIdx.y];
+  if (!(I.flags & APIC_FLOATING)) return;
+  const double dl = d.stp[blockIdx.y].dphig;
+  for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes;
+       nd += (long long)gridDim.x * blockDim.x) {
+    long long g = I.node_off + nd;
+    d.phi[g] += dl * d.phi_vac[g];
+  }
+}
+
 template <class Real>
 struct Pair;
 template <>
@@ -129,6 +172,8 @@ __global__ void k_step_end(DevPtrs d) {
   h[7] = res[0];
   h[8] = res[1];
   h[9] = T.tally[4];
+  h[10] = (I.flags & APIC_FLOATING) ? T.phig : I.phi_g;
+  if (I.flags & APIC_FLOATING) T.qg += T.tally[0];  // charge the grain collected this step
   for (int k = 0; k < 5; ++k) T.tally[k] = 0.0;
   T.step += 1;
 }
@@ -157,5 +202,8 @@ void launch_surface(const DevPtrs& d, cudaStream_t s) { k_surface<<<d.n_inst, 25
 void launch_step_end(const DevPtrs& d, cudaStream_t s) { k_step_end<<<(d.n_inst + 63) / 64, 64, 0, s>>>(d); }
 void launch_finish_injection(const DevPtrs& d, int pop, cudaStream_t s) { k_finish_injection<<<1, 1, 0, s>>>(d, pop); }
 void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s) { k_b_from_rho<<<kRedBlocks, 256, 0, s>>>(d, inst); }
+void launch_b_vacuum(const DevPtrs& d, int inst, cudaStream_t s) { k_b_vacuum<<<kRedBlocks, 256, 0, s>>>(d, inst); }
+void launch_store_vacuum(const DevPtrs& d, int inst, cudaStream_t s) { k_store_vacuum<<<kRedBlocks, 256, 0, s>>>(d, inst); }
+void launch_float_phi(const DevPtrs& d, cudaStream_t s) { k_float_phi<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d); }
 
 }  // namespace apic

@@ -8,7 +8,8 @@
 // product with the stored 1 / V_ij: FP64 division is slow on this GPU); the
 // accumulators are cleared for the next deposit; the initial guess of this
 // step's solve (previous phi, or its linear extrapolation); the right-hand
-// side b = rscale * (-rho) + (Dirichlet terms).  Returns b at the node.
+// side b = rscale * (-rho) + (Dirichlet terms; an isolated grain, APIC_FLOATING,
+// at its last potential phig).  Returns b at the node.
 // Every load comes before the first store: a load placed after a store that
 // might alias it waits for that store, which made this node loop a chain of
 // memory round trips.
@@ -25,18 +26,23 @@ __device__ __forceinline__ double rho_node(const DevPtrs& d, const Inst& I, int 
   const unsigned long long a0 = d.acc[o0];
   const unsigned long long a1 = ns > 1 ? d.acc[o1] : 0ull;
   const double vinv = d.Vinv[g];
-  double ph = 0.0, prev = 0.0, rs = 0.0, bc = 0.0;
+  const bool fl = (I.flags & APIC_FLOATING) != 0;
+  double ph = 0.0, prev = 0.0, rs = 0.0, bc = 0.0, bg = 0.0, dg = 0.0;
   if (interior) {
     ph = d.phi[g];
     prev = d.phi_prev[g];
     rs = d.rscale[g];
     bc = d.bbc[g];
+    if (fl) {
+      bg = d.bbc_g[g];
+      dg = d.stp[inst].phig - I.phi_g;
+    }
   }
   double q = 0.0;
   q += s0 * (double)a0;
   if (ns > 1) q += s1 * (double)a1;
   const double rho = q * vinv;
-  const double bv = interior ? -rho * rs + bc : 0.0;
+  const double bv = interior ? -rho * rs + (fl ? bc + dg * bg : bc) : 0.0;
   d.acc[o0] = 0ull;
   if (ns > 1) d.acc[o1] = 0ull;
   d.rho[g] = rho;
@@ -98,11 +104,21 @@ __device__ __forceinline__ double block_total(double v, double* sh) {
 // Eq. 4 (trapezoid over the x2 nodes, geometry tabulated at set-up).  Thread
 // 0 also draws this step's injection count from the fractional carry.  One
 // CTA per instance.
+//
+// Isolated grain (APIC_FLOATING): the problem is linear, so adding
+// dphig * phi_vac (the vacuum field of a grain at 1, outer boundary at 0)
+// moves the grain to phig + dphig and its charge to Q + dphig * C_vac, C_vac
+// the charge of phi_vac.  dphig is chosen so that the charge is the one the
+// grain holds (fixed at the first step, then grown by what it absorbs); E_n
+// and F_Z here are those of the corrected field, whose nodes the next kernel
+// (k_float_phi) updates.
 __device__ __forceinline__ void surface_block(const DevPtrs& d, int inst, double* sh) {
   const Inst& I = d.inst[inst];
   const bool nofield = (I.flags & APIC_NO_FIELD) != 0;
-  double q = 0.0, fz = 0.0;
+  const bool fl = (I.flags & APIC_FLOATING) != 0;
+  double q = 0.0, fz = 0.0, cv = 0.0;
   const double* p = d.phi + I.node_off;
+  const double* pv = d.phi_vac + I.node_off;
   const int N2 = I.N2;
   const double* geo = d.sgeo + 4 * I.en_off;  // |grad x1|, n_Z, dA/dx2, trapezoid weight per node
   for (int j = threadIdx.x; j <= I.n2; j += blockDim.x) {
@@ -113,11 +129,35 @@ __device__ __forceinline__ void surface_block(const DevPtrs& d, int inst, double
       En = -G1 * g;
       q += tw * En * dA;
       fz += tw * 0.5 * En * En * nZ * dA;
+      if (fl) cv += tw * (-(-3.0 * pv[j] + 4.0 * pv[N2 + j] - pv[2 * N2 + j]) / (2.0 * I.h1) * g) * dA;
     }
     d.en[I.en_off + j] = En;
   }
-  const double Q = block_total(q, sh);
-  const double FZ = block_total(fz, sh);
+  double Q = block_total(q, sh);
+  double FZ = block_total(fz, sh);
+  if (fl) {
+    StepState& T = d.stp[inst];
+    const double CV = block_total(cv, sh);
+    const double qg = T.qg_set != 0.0 ? T.qg : Q;
+    const double dl = (qg - Q) / CV;
+    __syncthreads();  // every thread has read T before thread 0 writes it
+    fz = 0.0;
+    for (int j = threadIdx.x; j <= I.n2; j += blockDim.x) {
+      double g = geo[4 * j + 0], nZ = geo[4 * j + 1], dA = geo[4 * j + 2], tw = geo[4 * j + 3];
+      double Ev = -(-3.0 * pv[j] + 4.0 * pv[N2 + j] - pv[2 * N2 + j]) / (2.0 * I.h1) * g;
+      double En = d.en[I.en_off + j] + dl * Ev;
+      fz += tw * 0.5 * En * En * nZ * dA;
+      d.en[I.en_off + j] = En;
+    }
+    FZ = block_total(fz, sh);
+    Q += dl * CV;
+    if (threadIdx.x == 0) {
+      T.qg = qg;
+      T.qg_set = 1.0;
+      T.dphig = dl;
+      T.phig += dl;
+    }
+  }
   if (threadIdx.x == 0) {
     d.stp[inst].Q = Q;
     d.stp[inst].FZ = FZ;

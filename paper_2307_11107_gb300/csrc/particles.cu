@@ -187,21 +187,6 @@ __device__ __forceinline__ void deposit_moments(const CellWin& W, int key, int c
   }
 }
 
-// Deposit without a window (standalone deposit and injection).
-__device__ __forceinline__ void deposit_warp_global(unsigned long long* acc, long long key, W4 w, int N2, bool active) {
-  Run r = warp_runs(key, active);
-  w.w00 = run_sum(w.w00, r);
-  w.w10 = run_sum(w.w10, r);
-  w.w01 = run_sum(w.w01, r);
-  w.w11 = run_sum(w.w11, r);
-  if (active && r.rank == r.len - 1) {
-    if (w.w00) atomicAdd(acc + key, w.w00);
-    if (w.w10) atomicAdd(acc + key + N2, w.w10);
-    if (w.w01) atomicAdd(acc + key + 1, w.w01);
-    if (w.w11) atomicAdd(acc + key + N2 + 1, w.w11);
-  }
-}
-
 __device__ __forceinline__ long long dep_key(const Inst& I, const Pop& P, const Cell& c) {
   return P.acc_off + (long long)c.i * I.N2 + c.j;
 }
