@@ -15,6 +15,7 @@ NO_INJECT = 1
 NO_FIELD = 2
 CHORD = 4
 FLOATING = 8
+BOLTZMANN = 16
 NT = 7
 NH = 11
 
@@ -59,6 +60,8 @@ def lib():
         L.or_step.argtypes = [vp, C.c_int]
         L.or_deposit.argtypes = [vp]
         L.or_solve.argtypes = [vp, P(d), P(d)]
+        L.or_solve_linear.argtypes = [vp, P(d), P(d)]
+        L.or_newton_iterations.argtypes = [vp]
         L.or_gradients.argtypes = [vp]
         L.or_push_only.argtypes = [vp]
         L.or_count.restype = i64
@@ -145,6 +148,8 @@ def make_config(d):
         flags |= CHORD
     if d.get("floating"):
         flags |= FLOATING
+    if d.get("boltzmann"):
+        flags |= BOLTZMANN
     c.flags = flags
     return c
 
@@ -184,9 +189,22 @@ class Sim:
         phi = np.zeros((self.n1 + 1) * (self.n2 + 1))
         r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64).ravel()
         rc = lib().or_solve(self.h, None if r is None else _dp(r), _dp(phi))
+        if rc == -2:
+            raise RuntimeError("Newton iteration did not converge")
         if rc != 0:
             raise RuntimeError("oracle has no Poisson matrix (no_field)")
         return phi.reshape(self.n1 + 1, self.n2 + 1)
+
+    def solve_linear(self, rho):
+        """Eqs. 6-7 for the charge density rho, whatever the electron model."""
+        phi = np.zeros((self.n1 + 1) * (self.n2 + 1))
+        r = np.ascontiguousarray(rho, dtype=np.float64).ravel()
+        if lib().or_solve_linear(self.h, _dp(r), _dp(phi)) != 0:
+            raise RuntimeError("oracle has no Poisson matrix (no_field)")
+        return phi.reshape(self.n1 + 1, self.n2 + 1)
+
+    def newton_iterations(self):
+        return int(lib().or_newton_iterations(self.h))
 
     def push_only(self):
         lib().or_push_only(self.h)

@@ -210,6 +210,7 @@ struct or_sim {
    * and the vacuum field of a grain at potential 1 (outer boundary at 0) */
   double phig, Qg, C_vac;
   int qg_set;
+  int newton_its; /* Boltzmann electrons: Newton iterations of the last solve (-1: no convergence) */
   double* phi_vac;
   /* decision tape: one status byte per particle update and per injection
    * draw, in processing order, and one injection count per step and species */
@@ -358,7 +359,7 @@ double or_sample_table(const or_sim* s, int which, double u) {
 /* (the matrix is constant in time), as the paper's LAPACK LU (Sec. 2).      */
 /* ------------------------------------------------------------------------ */
 #define UIDX(s, i, j) (((i) - 1) * (s)->N2 + (j))
-#define BAND(s, r, c) (s)->band[(size_t)(c) * (s)->ld + ((r) - (c) + (s)->kl + (s)->ku)]
+#define BANDA(a, s, r, c) (a)[(size_t)(c) * (s)->ld + ((r) - (c) + (s)->kl + (s)->ku)]
 
 /* The nine stencil weights of node (i, j): w[di+1][dj+2] for di in -1..1,
  * dj in -2..2 (the pole rows reach two nodes in j). */
@@ -391,6 +392,68 @@ static void stencil(const or_sim* s, int i, int j, double w[3][5]) {
   }
 }
 
+/* The matrix of the interior unknowns in band storage, plus shift[node] on
+ * the diagonal (NULL: none), then its LU factors with partial pivoting
+ * (column c keeps rows c-(kl+ku) .. c+kl; fill-in from row swaps stays inside
+ * that band). */
+static void assemble_factor(or_sim* s, const double* shift, double* band, int* piv) {
+  memset(band, 0, sizeof(double) * (size_t)s->ld * s->nu);
+  for (int i = 1; i < s->c.n1; ++i)
+    for (int j = 0; j < s->N2; ++j) {
+      double w[3][5];
+      stencil(s, i, j, w);
+      int r = UIDX(s, i, j);
+      if (shift) w[1][2] += shift[i * s->N2 + j];
+      for (int di = -1; di <= 1; ++di)
+        for (int dj = -2; dj <= 2; ++dj) {
+          double v = w[di + 1][dj + 2];
+          if (v == 0.0) continue;
+          int ii = i + di, jj = j + dj;
+          if (ii < 1 || ii > s->c.n1 - 1) continue; /* Dirichlet: goes to the rhs */
+          BANDA(band, s, r, UIDX(s, ii, jj)) += v;
+        }
+    }
+  int n = s->nu, kl = s->kl, kuu = s->kl + s->ku;
+  for (int j = 0; j < n; ++j) {
+    int km = kl < n - 1 - j ? kl : n - 1 - j;
+    int p = j;
+    double best = fabs(BANDA(band, s, j, j));
+    for (int r = j + 1; r <= j + km; ++r)
+      if (fabs(BANDA(band, s, r, j)) > best) { best = fabs(BANDA(band, s, r, j)); p = r; }
+    piv[j] = p;
+    int cmax = j + kuu < n - 1 ? j + kuu : n - 1;
+    if (p != j)
+      for (int c = j; c <= cmax; ++c) {
+        double t = BANDA(band, s, j, c);
+        BANDA(band, s, j, c) = BANDA(band, s, p, c);
+        BANDA(band, s, p, c) = t;
+      }
+    double inv = 1.0 / BANDA(band, s, j, j);
+    for (int r = j + 1; r <= j + km; ++r) BANDA(band, s, r, j) *= inv;
+    for (int c = j + 1; c <= cmax; ++c) {
+      double u = BANDA(band, s, j, c);
+      if (u == 0.0) continue;
+      for (int r = j + 1; r <= j + km; ++r) BANDA(band, s, r, c) -= BANDA(band, s, r, j) * u;
+    }
+  }
+}
+
+/* b <- A^-1 b with the factors of assemble_factor. */
+static void lu_solve(const or_sim* s, const double* band, const int* piv, double* b) {
+  int n = s->nu, kl = s->kl, kuu = s->kl + s->ku;
+  for (int j = 0; j < n; ++j) {
+    int p = piv[j];
+    if (p != j) { double t = b[j]; b[j] = b[p]; b[p] = t; }
+    int km = kl < n - 1 - j ? kl : n - 1 - j;
+    for (int r = j + 1; r <= j + km; ++r) b[r] -= BANDA(band, s, r, j) * b[j];
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    b[j] /= BANDA(band, s, j, j);
+    int r0 = j - kuu > 0 ? j - kuu : 0;
+    for (int r = r0; r < j; ++r) b[r] -= BANDA(band, s, r, j) * b[j];
+  }
+}
+
 static void build_matrix(or_sim* s) {
   s->nu = (s->c.n1 - 1) * s->N2;
   s->kl = s->N2 + 2;
@@ -398,74 +461,29 @@ static void build_matrix(or_sim* s) {
   s->ld = 2 * s->kl + s->ku + 1;
   s->band = (double*)calloc((size_t)s->ld * s->nu, sizeof(double));
   s->piv = (int*)calloc((size_t)s->nu, sizeof(int));
-  for (int i = 1; i < s->c.n1; ++i)
-    for (int j = 0; j < s->N2; ++j) {
-      double w[3][5];
-      stencil(s, i, j, w);
-      int r = UIDX(s, i, j);
-      for (int di = -1; di <= 1; ++di)
-        for (int dj = -2; dj <= 2; ++dj) {
-          double v = w[di + 1][dj + 2];
-          if (v == 0.0) continue;
-          int ii = i + di, jj = j + dj;
-          if (ii < 1 || ii > s->c.n1 - 1) continue; /* Dirichlet: goes to the rhs */
-          BAND(s, r, UIDX(s, ii, jj)) += v;
-        }
-    }
-  /* LU with partial pivoting in band storage (column c keeps rows
-   * c-(kl+ku) .. c+kl; fill-in from row swaps stays inside that band). */
-  int n = s->nu, kl = s->kl, kuu = s->kl + s->ku;
-  for (int j = 0; j < n; ++j) {
-    int km = kl < n - 1 - j ? kl : n - 1 - j;
-    int p = j;
-    double best = fabs(BAND(s, j, j));
-    for (int r = j + 1; r <= j + km; ++r)
-      if (fabs(BAND(s, r, j)) > best) { best = fabs(BAND(s, r, j)); p = r; }
-    s->piv[j] = p;
-    int cmax = j + kuu < n - 1 ? j + kuu : n - 1;
-    if (p != j)
-      for (int c = j; c <= cmax; ++c) {
-        double t = BAND(s, j, c);
-        BAND(s, j, c) = BAND(s, p, c);
-        BAND(s, p, c) = t;
-      }
-    double inv = 1.0 / BAND(s, j, j);
-    for (int r = j + 1; r <= j + km; ++r) BAND(s, r, j) *= inv;
-    for (int c = j + 1; c <= cmax; ++c) {
-      double u = BAND(s, j, c);
-      if (u == 0.0) continue;
-      for (int r = j + 1; r <= j + km; ++r) BAND(s, r, c) -= BAND(s, r, j) * u;
-    }
+  assemble_factor(s, NULL, s->band, s->piv);
+}
+
+/* Right-hand side of row (i, j): -rho plus the Dirichlet terms moved from
+ * the grain row (phig) and the outer row (phiout). */
+static double row_rhs(const or_sim* s, int i, int j, double rho, double phig, double phiout) {
+  double w[3][5];
+  stencil(s, i, j, w);
+  double rhs = -rho;
+  for (int dj = -2; dj <= 2; ++dj) {
+    if (i - 1 == 0) rhs -= w[0][dj + 2] * phig;
+    if (i + 1 == s->c.n1) rhs -= w[2][dj + 2] * phiout;
   }
+  return rhs;
 }
 
 /* The Dirichlet problem of Eqs. 6-7 for charge density rho (NULL: zero) with
  * phi = phig on the grain and phi = phiout on the outer surface. */
 static void solve_dirichlet(or_sim* s, const double* rho, double phig, double phiout, double* phi) {
-  int n = s->nu, kl = s->kl, kuu = s->kl + s->ku;
-  double* b = (double*)malloc(sizeof(double) * (size_t)n);
+  double* b = (double*)malloc(sizeof(double) * (size_t)s->nu);
   for (int i = 1; i < s->c.n1; ++i)
-    for (int j = 0; j < s->N2; ++j) {
-      double w[3][5];
-      stencil(s, i, j, w);
-      double rhs = rho ? -rho[i * s->N2 + j] : 0.0;
-      for (int dj = -2; dj <= 2; ++dj) {
-        if (i - 1 == 0) rhs -= w[0][dj + 2] * phig;
-        if (i + 1 == s->c.n1) rhs -= w[2][dj + 2] * phiout;
-      }
-      b[UIDX(s, i, j)] = rhs;
-    }
-  for (int j = 0; j < n; ++j) {
-    int p = s->piv[j];
-    if (p != j) { double t = b[j]; b[j] = b[p]; b[p] = t; }
-    int km = kl < n - 1 - j ? kl : n - 1 - j;
-    for (int r = j + 1; r <= j + km; ++r) b[r] -= BAND(s, r, j) * b[j];
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    b[j] /= BAND(s, j, j);
-    int r0 = j - kuu > 0 ? j - kuu : 0;
-    for (int r = r0; r < j; ++r) b[r] -= BAND(s, r, j) * b[j];
-  }
+    for (int j = 0; j < s->N2; ++j) b[UIDX(s, i, j)] = row_rhs(s, i, j, rho ? rho[i * s->N2 + j] : 0.0, phig, phiout);
+  lu_solve(s, s->band, s->piv, b);
   for (int j = 0; j < s->N2; ++j) {
     phi[j] = phig;
     phi[s->c.n1 * s->N2 + j] = phiout;
@@ -475,10 +493,67 @@ static void solve_dirichlet(or_sim* s, const double* rho, double phig, double ph
   free(b);
 }
 
-/* The configured boundary values (phi_g, phi_out). */
+/* Boltzmann electrons (the paper's Sec. 2 option; n0 = 1, Te = 1 units, with
+ * the sign of a negative electron charge): Eq. 6 becomes
+ * Delta phi = -(rho_i - exp(phi)), rho_i the particles' charge density, with
+ * the same Dirichlet values.  Solved by Newton's method: each iteration
+ * solves (L - diag(exp(phi_k))) phi_{k+1} = -rho_i + exp(phi_k)(1 - phi_k)
+ * (plus the Dirichlet terms) by banded LU, until the largest update is below
+ * 1e-13 (1 + max |phi|).  phi holds the start on entry.  Returns the
+ * iterations, or -1 without convergence in 100. */
+static int solve_boltzmann(or_sim* s, const double* rho, double* phi) {
+  size_t nn = (size_t)s->N1 * s->N2;
+  double* band = (double*)malloc(sizeof(double) * (size_t)s->ld * s->nu);
+  int* piv = (int*)malloc(sizeof(int) * (size_t)s->nu);
+  double* shift = (double*)calloc(nn, sizeof(double));
+  double* b = (double*)malloc(sizeof(double) * (size_t)s->nu);
+  int it, ok = 0;
+  for (int j = 0; j < s->N2; ++j) {
+    phi[j] = s->c.phi_g;
+    phi[s->c.n1 * s->N2 + j] = s->c.phi_out;
+  }
+  for (it = 1; it <= 100; ++it) {
+    for (int i = 1; i < s->c.n1; ++i)
+      for (int j = 0; j < s->N2; ++j) {
+        double p = phi[i * s->N2 + j], e = exp(p);
+        shift[i * s->N2 + j] = -e;
+        b[UIDX(s, i, j)] = row_rhs(s, i, j, rho[i * s->N2 + j], s->c.phi_g, s->c.phi_out) + e * (1.0 - p);
+      }
+    assemble_factor(s, shift, band, piv);
+    lu_solve(s, band, piv, b);
+    double dmax = 0.0, pmax = 0.0;
+    for (int i = 1; i < s->c.n1; ++i)
+      for (int j = 0; j < s->N2; ++j) {
+        double* p = &phi[i * s->N2 + j];
+        double nw = b[UIDX(s, i, j)];
+        if (fabs(nw - *p) > dmax) dmax = fabs(nw - *p);
+        if (fabs(nw) > pmax) pmax = fabs(nw);
+        *p = nw;
+      }
+    if (dmax <= 1e-13 * (1.0 + pmax)) { ok = 1; break; }
+  }
+  free(band); free(piv); free(shift); free(b);
+  return ok ? it : -1;
+}
+
+/* The configured boundary values (phi_g, phi_out); with Boltzmann electrons
+ * the nonlinear problem, from phi = 0 inside. */
 int or_solve(or_sim* s, const double* rho_in, double* phi_out) {
   if (!s->band) return -1;
-  solve_dirichlet(s, rho_in ? rho_in : s->rho, s->c.phi_g, s->c.phi_out, phi_out ? phi_out : s->phi);
+  const double* rho = rho_in ? rho_in : s->rho;
+  double* phi = phi_out ? phi_out : s->phi;
+  if (s->c.flags & OR_BOLTZMANN) {
+    memset(phi, 0, sizeof(double) * (size_t)s->N1 * s->N2);
+    return solve_boltzmann(s, rho, phi) > 0 ? 0 : -2;
+  }
+  solve_dirichlet(s, rho, s->c.phi_g, s->c.phi_out, phi);
+  return 0;
+}
+
+/* The linear problem of Eqs. 6-7 whatever the electron model. */
+int or_solve_linear(or_sim* s, const double* rho, double* phi_out) {
+  if (!s->band) return -1;
+  solve_dirichlet(s, rho, s->c.phi_g, s->c.phi_out, phi_out);
   return 0;
 }
 
@@ -887,6 +962,9 @@ static void field_phase(or_sim* s) {
     }
     s->phig = (s->Qg - q0) / s->C_vac;
     for (size_t k = 0; k < nn; ++k) s->phi[k] += s->phig * s->phi_vac[k];
+  } else if (s->c.flags & OR_BOLTZMANN) {
+    /* Newton from the previous step's potential */
+    s->newton_its = solve_boltzmann(s, s->rho, s->phi);
   } else {
     or_solve(s, NULL, NULL);
   }
@@ -934,7 +1012,8 @@ or_sim* or_create(const or_config* cfg) {
   build_tables(s);
   if (!(cfg->flags & OR_NO_FIELD)) build_matrix(s);
   s->phig = cfg->phi_g;
-  if ((cfg->flags & OR_FLOATING) && (cfg->flags & OR_NO_FIELD)) {
+  if (((cfg->flags & (OR_FLOATING | OR_BOLTZMANN)) && (cfg->flags & OR_NO_FIELD)) ||
+      ((cfg->flags & OR_FLOATING) && (cfg->flags & OR_BOLTZMANN))) {
     or_destroy(s);
     return NULL;
   }
@@ -986,6 +1065,8 @@ void or_get_grid(const or_sim* s, int which, double* out) {
 void or_get_bins(const or_sim* s, double* out) {
   memcpy(out, s->bins, sizeof(double) * (size_t)s->c.n_species * s->c.n2 * OR_NT);
 }
+
+int or_newton_iterations(const or_sim* s) { return s->newton_its; }
 
 int64_t or_get_history(const or_sim* s, double* out) {
   if (out) memcpy(out, s->hist, sizeof(double) * OR_NH * (size_t)s->hist_n);
