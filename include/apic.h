@@ -82,6 +82,13 @@ extern "C" {
                                 on the grain, 0 outside, computed at creation) that restores that charge.
                                 Not with APIC_NO_FIELD, nor with apic_sensitivity (INVALID_ARG);
                                 apic_solve_poisson keeps using phi_grain. */
+#define APIC_BOLTZMANN 16    /* electrons are not simulated: their density is n0 exp(phi) (Te = 1, potential
+                                zero at the outer surface) in Eq. 6, whose nonlinear problem is solved by
+                                newton_iters Newton iterations, each a BiCGSTAB solve preconditioned by the
+                                multigrid of the linear operator (the species given are the ions).  Forces the
+                                multigrid solver with per-phase kernels.  apic_solve_poisson solves the same
+                                nonlinear problem for the given ion density.  Not with APIC_NO_FIELD,
+                                APIC_FLOATING or apic_sensitivity (INVALID_ARG). */
 
 #define APIC_NT 7  /* tally components per (species, bin): hits, charge, p_R, p_Z, L_z, E_kin, E_kin + E_bind */
 #define APIC_NH 11 /* history fields per step: t, current, drag F_Z, electric F_Z, torque T_z,
@@ -110,13 +117,15 @@ typedef struct {
   uint64_t seed;         /* Philox4x32-10 key */
   int32_t instance;      /* Philox counter tag; distinct instances draw distinct streams */
   int32_t precision;     /* APIC_FP64 or APIC_FP32_REFINED */
-  int32_t flags;         /* APIC_NO_INJECT | APIC_NO_FIELD | APIC_CHORD_ABSORB | APIC_FLOATING */
+  int32_t flags;         /* APIC_NO_INJECT | APIC_NO_FIELD | APIC_CHORD_ABSORB | APIC_FLOATING | APIC_BOLTZMANN */
   double poisson_tol;    /* relative residual target ||b - A phi|| / ||b|| (0: 1e-10) */
   int32_t poisson_max_iter; /* BiCGSTAB iterations per step (0: 20) */
   int32_t sort_interval; /* sort particles by cell every this many steps (0: never) */
   int32_t history_cap;   /* rows of the per-step history ring (0: 4096) */
   int32_t poisson_guess; /* start of each step's solve: 0 previous phi, 1 linear extrapolation 2 phi^n - phi^n-1 */
-  int32_t reserved[4];
+  int32_t newton_iters;  /* APIC_BOLTZMANN: Newton iterations per solve (0: 8); once the nonlinear residual
+                            is below poisson_tol the remaining iterations do no solver work */
+  int32_t reserved[3];
 } apic_config_t;
 
 typedef void* (*apic_alloc_fn)(size_t bytes, void* stream, void* ctx);

@@ -16,7 +16,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "GEOMETRY", -3: "CAPACITY", -4: "NOT_CONVERGED"
 FP64 = 0
 FP32_REFINED = 1
 LOAD_VOLUME, FLUX_SURFACE, EXPLICIT = 0, 1, 2
-NO_INJECT, NO_FIELD, CHORD_ABSORB, FLOATING = 1, 2, 4, 8
+NO_INJECT, NO_FIELD, CHORD_ABSORB, FLOATING, BOLTZMANN = 1, 2, 4, 8, 16
 NT, NH = 7, 11
 
 SYMBOLS = ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
@@ -42,7 +42,8 @@ class Config(C.Structure):
                 ("n1", C.c_int32), ("n2", C.c_int32), ("n_species", C.c_int32), ("sp", Species * 2),
                 ("seed", C.c_uint64), ("instance", C.c_int32), ("precision", C.c_int32), ("flags", C.c_int32),
                 ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32), ("sort_interval", C.c_int32),
-                ("history_cap", C.c_int32), ("poisson_guess", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("history_cap", C.c_int32), ("poisson_guess", C.c_int32), ("newton_iters", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

@@ -173,6 +173,8 @@ struct apic_sim {
   size_t bcr_bytes = 0;               // reduction blocks + tail inverse (one device range)
   bool chord = false;                 // some instance absorbs grazing orbits (APIC_CHORD_ABSORB)
   bool floating = false;              // some instance has an isolated grain (APIC_FLOATING)
+  bool boltz = false;                 // some instance has Boltzmann electrons (APIC_BOLTZMANN)
+  int newton = 0;                     // Newton iterations per solve (the largest of those instances)
   size_t l2_persist = 0;              // bytes of L2 set aside for them (0: none)
   long long tab_total = 0;
   TanPtrs tan{};                      // sensitivity-window state (allocated on first use)
@@ -252,8 +254,11 @@ int validate(const apic_config_t& c, std::string& why) {
       return why = "bad species parameters (m > 0, T >= 0, n_init > 0, 0 < capacity < 2^31)", APIC_ERR_INVALID_ARG;
   }
   if (c.precision != APIC_FP64 && c.precision != APIC_FP32_REFINED) return why = "bad precision", APIC_ERR_INVALID_ARG;
-  if ((c.flags & APIC_FLOATING) && (c.flags & APIC_NO_FIELD))
-    return why = "APIC_FLOATING needs the field (not with APIC_NO_FIELD)", APIC_ERR_INVALID_ARG;
+  if ((c.flags & (APIC_FLOATING | APIC_BOLTZMANN)) && (c.flags & APIC_NO_FIELD))
+    return why = "APIC_FLOATING and APIC_BOLTZMANN need the field (not with APIC_NO_FIELD)", APIC_ERR_INVALID_ARG;
+  if ((c.flags & APIC_FLOATING) && (c.flags & APIC_BOLTZMANN))
+    return why = "APIC_FLOATING does not take APIC_BOLTZMANN (no electron current)", APIC_ERR_INVALID_ARG;
+  if (c.newton_iters < 0 || c.newton_iters > 100) return why = "newton_iters in [0, 100]", APIC_ERR_INVALID_ARG;
   return APIC_OK;
 }
 
@@ -866,7 +871,7 @@ static int setup(apic_sim* S) {
   {
     const char* pc = std::getenv("APIC_PRECOND");
     bool want = sizeof(Real) == 4 && ni <= kCoopMaxInst && !(pc && std::string(pc) == "mg");
-    for (const Inst& I : S->inst) want = want && !(I.flags & APIC_NO_FIELD);
+    for (const Inst& I : S->inst) want = want && !(I.flags & (APIC_NO_FIELD | APIC_BOLTZMANN));
     long long off = 0;
     // dense level-1 blocks when the whole reduction then still fits in L2
     // (fewer phases); else level 1 applies the stencil's couplings (fewer
@@ -1004,6 +1009,12 @@ static int setup(apic_sim* S) {
     d.bbc_g = (double*)A(sizeof(double) * total_nodes);
     d.phi_vac = (double*)A(sizeof(double) * total_nodes);
   }
+  for (int k = 0; k < ni; ++k)
+    if (S->inst[k].flags & APIC_BOLTZMANN) {
+      S->boltz = true;
+      S->newton = std::max(S->newton, S->cfg[k].newton_iters > 0 ? S->cfg[k].newton_iters : 8);
+    }
+  if (S->boltz) d.diag0 = (double*)A(sizeof(double) * total_nodes);
   S->phi_save = (double*)A(sizeof(double) * total_nodes);
   d.st64 = (double*)A(sizeof(double) * kSt * total_nodes);
   d.acc = (unsigned long long*)A(sizeof(unsigned long long) * 2 * total_nodes);
@@ -1098,6 +1109,8 @@ static int setup(apic_sim* S) {
     S->h2d(d.rscale + I.node_off, rscs[k].data(), rscs[k].size());
     S->h2d(d.bbc + I.node_off, bbcs[k].data(), bbcs[k].size());
     S->h2d(d.st64 + (long long)kSt * I.node_off, levels[k][0].st.data(), levels[k][0].st.size());
+    if (I.flags & APIC_BOLTZMANN)
+      S->h2d(d.diag0 + I.node_off, levels[k][0].st.data() + (size_t)st_slot(0, 0) * I.nodes, (size_t)I.nodes);
     for (int l = 0; l < I.n_levels; ++l) {
       const HostLevel& H = levels[k][l];
       tmp.assign(H.st.begin(), H.st.end());
@@ -1168,9 +1181,9 @@ static int setup(apic_sim* S) {
   const char* env = std::getenv("APIC_SOLVER");
   // one cooperative launch per solve for a single instance; batches use the
   // per-phase kernels, whose grids span every instance at once
-  bool want_coop = ni == 1;
+  bool want_coop = ni == 1 && !S->boltz;  // the Newton loop runs on the per-phase kernels
   if (env && std::string(env) == "kernels") want_coop = false;
-  if (env && std::string(env) == "coop") want_coop = ni <= kCoopMaxInst;
+  if (env && std::string(env) == "coop") want_coop = ni <= kCoopMaxInst && !S->boltz;
   S->coop = want_coop ? coop_blocks<Real>(S->plan, sms) : 0;
   if (const char* nbv = std::getenv("APIC_COOP_BLOCKS")) S->coop = std::min(S->coop, std::max(1, std::atoi(nbv)));
   if (pl.bcr.n_inst > 0) S->coop = bcr_nb;
@@ -1323,12 +1336,17 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
         if (solve_coop<Real>(S, d, s, kBcrRho | kBcrFields) != cudaSuccess) return false;
         break;
       }
-      launch_bicg_init<Real>(d, s);
-      if (S->cond_loop) {
-        if (!enqueue_solver_loop<Real>(S, d, s)) return false;
-      } else {
-        enqueue_solver_iterations_fixed<Real>(S, d, s);
+      // Boltzmann electrons: newton Newton iterations, each a linear solve
+      for (int k = 0; k < (S->boltz ? S->newton : 1); ++k) {
+        if (S->boltz) launch_newton(d, -1, s);
+        launch_bicg_init<Real>(d, s);
+        if (S->cond_loop) {
+          if (!enqueue_solver_loop<Real>(S, d, s)) return false;
+        } else {
+          enqueue_solver_iterations_fixed<Real>(S, d, s);
+        }
       }
+      if (S->boltz) launch_newton_end(d, s);
       break;
     case 2:
       if (S->plan.bcr.n_inst == 0) {  // the reduction solve ends with them
@@ -1512,10 +1530,14 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
   } else if (S->coop > 0) {
     out->kernels_per_iter = 0;   // the whole solve is one cooperative launch
     out->kernels_per_step = 7;
+  } else if (S->boltz) {  // per Newton iteration: linearisation and BiCGSTAB set-up; then the diagonal back
+    out->kernels_per_iter = 6 + 2 * vcycle;
+    out->kernels_per_step = 6 + 1 + S->newton * (2 + (S->cond_loop ? 0 : most * out->kernels_per_iter));
   } else {
     out->kernels_per_iter = 6 + 2 * vcycle;
     out->kernels_per_step = 7 + (S->cond_loop ? 0 : most * out->kernels_per_iter);
   }
+  if (S->floating) out->kernels_per_step += 2;  // the isolated grains' correction and the gradients again
   out->timed_steps = S->timed_steps;
   out->solver = S->plan.bcr.n_inst > 0 ? APIC_SOLVER_BCR : (S->coop > 0 ? APIC_SOLVER_MG_COOP : APIC_SOLVER_MG_KERNELS);
   out->sorts = S->sorts;
@@ -1718,7 +1740,15 @@ static int solve_impl(apic_sim* S, int inst, const double* rho, double* phi_out)
     return S->status;
   if (rho && !S->h2d(d.rho + I.node_off, rho, (size_t)I.nodes)) return S->status;
   launch_b_from_rho(d, inst, S->stream);
-  if (!solve_instance<Real>(S, inst)) return S->status;
+  if (I.flags & APIC_BOLTZMANN) {  // Newton from the current phi
+    for (int k = 0; k < S->newton; ++k) {
+      launch_newton(d, inst, S->stream);
+      if (!solve_instance<Real>(S, inst)) return S->status;
+    }
+    launch_newton_end(d, S->stream);
+  } else if (!solve_instance<Real>(S, inst)) {
+    return S->status;
+  }
   if (phi_out) S->d2h(phi_out, d.phi + I.node_off, (size_t)I.nodes);
   S->ck(cudaMemcpyAsync(d.phi, S->phi_save, sizeof(double) * d.total_nodes, cudaMemcpyDeviceToDevice, S->stream),
         "restore phi");
@@ -1914,6 +1944,7 @@ template <class Real>
 static int sensitivity_impl(apic_sim* S, int n, double* values, double* jac) {
   if (S->chord) return S->fail(APIC_ERR_INVALID_ARG, "the sensitivity window does not take APIC_CHORD_ABSORB");
   if (S->floating) return S->fail(APIC_ERR_INVALID_ARG, "the sensitivity window does not take APIC_FLOATING");
+  if (S->boltz) return S->fail(APIC_ERR_INVALID_ARG, "the sensitivity window does not take APIC_BOLTZMANN");
   if (!tangent_setup<Real>(S)) return S->status;
   const TanPtrs& t = S->tan;
   const DevPtrs d = S->view(S->par);

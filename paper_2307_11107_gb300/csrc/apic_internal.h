@@ -141,6 +141,7 @@ struct DevPtrs {
   double* Vinv;                   // 1 / V (the density without a division per node)
   double* bbc_g;                  // Dirichlet term of phi = 1 on the grain, 0 outside (APIC_FLOATING; else null)
   double* phi_vac;                // vacuum field of that problem, boundary rows included (APIC_FLOATING)
+  double* diag0;                  // diagonal of the linear FP64 operator st64 (APIC_BOLTZMANN; else null)
   double *b, *r, *rh, *p, *v, *s, *t, *ph, *sh;
   double* st64;                   // finest-level stencil, FP64 [kSt][nodes] per instance (same offsets)
   unsigned long long* acc;        // deposit accumulators
@@ -233,6 +234,8 @@ void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s);
 void launch_b_vacuum(const DevPtrs& d, int inst, cudaStream_t s);
 void launch_store_vacuum(const DevPtrs& d, int inst, cudaStream_t s);
 void launch_float_phi(const DevPtrs& d, cudaStream_t s);
+void launch_newton(const DevPtrs& d, int only, cudaStream_t s);
+void launch_newton_end(const DevPtrs& d, cudaStream_t s);
 
 // Block cyclic reduction (bcr.cu) of the finest-level system of every
 // instance of a batch.  Instance k has the unknown rows i = 1..M (M = n1 - 1)

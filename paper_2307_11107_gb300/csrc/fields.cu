@@ -105,6 +105,47 @@ __global__ void __launch_bounds__(256) k_float_phi(DevPtrs d) {
   }
 }
 
+// Boltzmann electrons (APIC_BOLTZMANN): the Newton linearisation of
+// L phi = -(rho_i - exp(phi)) about the current phi_k.  In the row-scaled
+// system the FP64 operator's diagonal becomes diag0 - rscale exp(phi_k) and
+// b = -rho_i rscale + (Dirichlet terms) + rscale exp(phi_k) (1 - phi_k); the
+// |b|^2 partials as k_rho, so that the BiCGSTAB solve that follows stops at
+// once when phi_k already satisfies the nonlinear equations to its
+// tolerance.  only >= 0: that instance alone.
+__global__ void __launch_bounds__(256) k_newton(DevPtrs d, int only) {
+  __shared__ double sh[256];
+  const int inst = blockIdx.y;
+  const Inst& I = d.inst[inst];
+  if (!(I.flags & APIC_BOLTZMANN) || (only >= 0 && inst != only)) return;
+  double* dg = d.st64 + (long long)kSt * I.node_off + (long long)st_slot(0, 0) * I.nodes;
+  double part = 0.0;
+  for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes;
+       nd += (long long)gridDim.x * blockDim.x) {
+    const long long g = I.node_off + nd;
+    const int i = (int)(nd / I.N2);
+    if (i == 0 || i == I.n1) continue;
+    const double ph = d.phi[g], rs = d.rscale[g], rho = d.rho[g], bc = d.bbc[g], d0 = d.diag0[g];
+    const double e = rs * exp(ph);
+    const double bv = -rho * rs + bc + e * (1.0 - ph);
+    dg[nd] = d0 - e;
+    d.b[g] = bv;
+    part += bv * bv;
+  }
+  double tot = block_sum(part, sh);
+  if (threadIdx.x == 0) d.red[((long long)inst * kNRed + 0) * kRedBlocks + blockIdx.x] = tot;
+}
+
+// The linear operator's diagonal back (after a Boltzmann solve).
+__global__ void __launch_bounds__(256) k_newton_end(DevPtrs d) {
+  const int inst = blockIdx.y;
+  const Inst& I = d.inst[inst];
+  if (!(I.flags & APIC_BOLTZMANN)) return;
+  double* dg = d.st64 + (long long)kSt * I.node_off + (long long)st_slot(0, 0) * I.nodes;
+  for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes;
+       nd += (long long)gridDim.x * blockDim.x)
+    dg[nd] = d.diag0[I.node_off + nd];
+}
+
 template <class Real>
 struct Pair;
 template <>
@@ -205,5 +246,7 @@ void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s) { k_b_from_rh
 void launch_b_vacuum(const DevPtrs& d, int inst, cudaStream_t s) { k_b_vacuum<<<kRedBlocks, 256, 0, s>>>(d, inst); }
 void launch_store_vacuum(const DevPtrs& d, int inst, cudaStream_t s) { k_store_vacuum<<<kRedBlocks, 256, 0, s>>>(d, inst); }
 void launch_float_phi(const DevPtrs& d, cudaStream_t s) { k_float_phi<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d); }
+void launch_newton(const DevPtrs& d, int only, cudaStream_t s) { k_newton<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d, only); }
+void launch_newton_end(const DevPtrs& d, cudaStream_t s) { k_newton_end<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d); }
 
 }  // namespace apic
