@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--particles", type=int, default=None,
                     help="macro-particles per species (default: the workload's own count)")
     ap.add_argument("--workload", default="dipole256",
-                    choices=["dipole256", "dipole1024", "batched48", "sphere64", "window"],
+                    choices=["dipole256", "dipole1024", "batched48", "sphere64", "window", "boltzmann256",
+                             "floating256"],
                     help="window: the sensitivity window (forward-mode derivatives along alpha, phi_g, B) on the "
                          "256x128 dipole, 1e6 particles per species, K = 10 steps per window")
     ap.add_argument("--instances", type=int, default=None,
@@ -135,6 +136,10 @@ def workloads(name="dipole256", n_per_species=None, n_instances=None):
         return cs
     if name == "dipole1024":
         c = W.dipole_1024("fp32")
+    elif name == "boltzmann256":
+        c = W.dipole_256_boltzmann("fp32")
+    elif name == "floating256":
+        c = W.dipole_256_floating("fp32")
     elif name == "sphere64":
         c = W.spherical_small("fp64")
     else:
@@ -341,7 +346,7 @@ def main():
     # memory, then per step apic_step + apic_tallies (bins, counts, history row)
     e2e = None
     if not args.no_e2e and rank == 0 and len(cfgs) == 1:
-        states = [sim.particles(sp) for sp in range(2)]
+        states = [sim.particles(sp) for sp in range(len(cfg["species"]))]
         pinned = []
         for stt in states:
             pt = torch.empty(stt.shape, dtype=torch.float64, pin_memory=True)
@@ -356,7 +361,7 @@ def main():
         h2d = sum(p.numel() * 8 for p in pinned)
         barrier()
         t0 = time.perf_counter()
-        for sp in range(2):
+        for sp in range(len(pinned)):
             sim2.add_particles(sp, pinned[sp].numpy())
         adv2 = 0.0
         d2h = 0
@@ -395,7 +400,10 @@ def main():
                        "poisson_tol": cfg["poisson_tol"],
                        "precision": "FP32 particles; Poisson: " + st["solver"],
                        "l2": "inputs larger than L2 (particle state %.0f MB)" % (
-                           sum(2 * c["species"][0]["n_init"] for c in cfgs) * 20 / 1e6),
+                           sum(len(c["species"]) * c["species"][0]["n_init"] for c in cfgs) * 20 / 1e6),
+                       "electrons": "Boltzmann, n_e = exp(phi), Newton" if cfg.get("boltzmann") else "particles",
+                       "grain": "isolated (floating potential)" if cfg.get("floating") else "fixed potential",
+                       "dt": cfg["dt"],
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "sort_interval": tuned if tuned is not None else cfg.get("sort_interval", 0)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),

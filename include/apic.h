@@ -86,7 +86,8 @@ extern "C" {
                                 zero at the outer surface) in Eq. 6, whose nonlinear problem is solved by
                                 newton_iters Newton iterations, each a BiCGSTAB solve preconditioned by the
                                 multigrid of the linear operator (the species given are the ions).  Forces the
-                                multigrid solver with per-phase kernels.  apic_solve_poisson solves the same
+                                multigrid solver (one cooperative launch per Newton iteration for a single
+                                instance, per-phase kernels for a batch).  apic_solve_poisson solves the same
                                 nonlinear problem for the given ion density.  Not with APIC_NO_FIELD,
                                 APIC_FLOATING or apic_sensitivity (INVALID_ARG). */
 

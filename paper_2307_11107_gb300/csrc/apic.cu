@@ -1181,9 +1181,9 @@ static int setup(apic_sim* S) {
   const char* env = std::getenv("APIC_SOLVER");
   // one cooperative launch per solve for a single instance; batches use the
   // per-phase kernels, whose grids span every instance at once
-  bool want_coop = ni == 1 && !S->boltz;  // the Newton loop runs on the per-phase kernels
+  bool want_coop = ni == 1;
   if (env && std::string(env) == "kernels") want_coop = false;
-  if (env && std::string(env) == "coop") want_coop = ni <= kCoopMaxInst && !S->boltz;
+  if (env && std::string(env) == "coop") want_coop = ni <= kCoopMaxInst;
   S->coop = want_coop ? coop_blocks<Real>(S->plan, sms) : 0;
   if (const char* nbv = std::getenv("APIC_COOP_BLOCKS")) S->coop = std::min(S->coop, std::max(1, std::atoi(nbv)));
   if (pl.bcr.n_inst > 0) S->coop = bcr_nb;
@@ -1332,13 +1332,13 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
       if (S->plan.bcr.n_inst == 0) launch_rho<Real>(d, s);  // the reduction solve forms rho itself
       break;
     case 1:
-      if (S->coop > 0) {
-        if (solve_coop<Real>(S, d, s, kBcrRho | kBcrFields) != cudaSuccess) return false;
-        break;
-      }
       // Boltzmann electrons: newton Newton iterations, each a linear solve
       for (int k = 0; k < (S->boltz ? S->newton : 1); ++k) {
         if (S->boltz) launch_newton(d, -1, s);
+        if (S->coop > 0) {
+          if (solve_coop<Real>(S, d, s, kBcrRho | kBcrFields) != cudaSuccess) return false;
+          continue;
+        }
         launch_bicg_init<Real>(d, s);
         if (S->cond_loop) {
           if (!enqueue_solver_loop<Real>(S, d, s)) return false;
@@ -1529,7 +1529,7 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
     out->kernels_per_step = 4;   // + push, injection, bookkeeping
   } else if (S->coop > 0) {
     out->kernels_per_iter = 0;   // the whole solve is one cooperative launch
-    out->kernels_per_step = 7;
+    out->kernels_per_step = S->boltz ? 7 + 2 * S->newton : 7;  // per Newton iteration: linearisation + solve
   } else if (S->boltz) {  // per Newton iteration: linearisation and BiCGSTAB set-up; then the diagonal back
     out->kernels_per_iter = 6 + 2 * vcycle;
     out->kernels_per_step = 6 + 1 + S->newton * (2 + (S->cond_loop ? 0 : most * out->kernels_per_iter));

@@ -31,6 +31,24 @@ def dipole_256(precision="fp32", n_per_species=10_000_000):
                 seed=1, precision=precision, poisson_tol=1e-10, poisson_max_iter=20, sort_interval=8, poisson_guess=1, steps=2000)
 
 
+def dipole_256_boltzmann(precision="fp32", n_ions=10_000_000):
+    """The 256 x 128 dipole with Boltzmann electrons: 1e7 ions only, the
+    nonlinear Poisson problem solved by Newton each step, dt = 1.0 (ten times
+    the two-species step; the ion plasma period is 43 times the electron one)."""
+    c = dipole_256(precision)
+    c.update(name="dipole_a0.3_256x128_1e7ions_boltzmann", species=[dict(ion(0.5), n_init=n_ions)], dt=1.0,
+             boltzmann=True, poisson_tol=1e-10, poisson_max_iter=30, newton_iters=8, steps=200)
+    return c
+
+
+def dipole_256_floating(precision="fp32", n_per_species=10_000_000):
+    """The 256 x 128 dipole with an isolated grain (its potential follows the
+    collected charge, starting from -2.5)."""
+    c = dipole_256(precision, n_per_species)
+    c.update(name="dipole_a0.3_256x128_2e7_floating", floating=True)
+    return c
+
+
 def dipole_1024(precision="fp32", n_per_species=50_000_000):
     """Precision form at scale: a = 0.45 (alpha = 0.225), 1024 x 512 cells,
     5e7 macro-particles per species, FP32 particles and multigrid inside the

@@ -38,7 +38,7 @@ def test_newton_solve_matches_oracle(apic, alpha, precision):
     g = s.solve_poisson(rho)
     r = o.solve(rho)
     assert np.abs(g - r).max() < 1e-9 * np.abs(r).max()
-    assert s.stats()["solver"].startswith("multigrid BiCGSTAB, per-phase kernels")
+    assert s.stats()["solver"].startswith("multigrid BiCGSTAB")
 
 
 def test_single_step_fp64(apic):
@@ -80,6 +80,41 @@ def test_ion_only_run_fp32(apic):
     assert np.isfinite(hg).all()
     assert t["poisson_res"] <= 1e-10
     assert np.abs(hg[:, 6] - ho[:, 6]).max() < 0.03 * np.abs(ho[:, 6]).max()
+
+
+def test_boltzmann_batch_equals_solo(apic):
+    """A Boltzmann instance and a two-species instance in one batch (per-phase
+    multigrid kernels, the Newton loop skipping the linear instance) compute
+    what each computes alone on the same kernels."""
+    import os
+    base = dict(alpha=0.1, x1_out=-0.1, phi_g=-2.0, phi_out=0.0, B=0.5, dt=0.2, n1=32, n2=16, seed=4,
+                precision="fp64", poisson_tol=1e-12, poisson_max_iter=80)
+    from tests.inputs import ELECTRON
+    cfgs = [dict(base, species=[dict(ION, n_init=10000)], boltzmann=True, newton_iters=10),
+            dict(base, species=[dict(ELECTRON, n_init=10000), dict(ION, n_init=10000)], instance=1)]
+    old = os.environ.get("APIC_SOLVER")
+    os.environ["APIC_SOLVER"] = "kernels"
+    try:
+        solo = []
+        for c in cfgs:
+            s = apic.Sim(c)
+            for sp in range(len(c["species"])):
+                s.load_volume(sp, 10000)
+            s.step(4)
+            solo.append((s.field("phi"), s.tallies(history=True)["history"]))
+        b = apic.Sim(cfgs)
+        for k, c in enumerate(cfgs):
+            for sp in range(len(c["species"])):
+                b.load_volume(sp, 10000, instance=k)
+        b.step(4)
+    finally:
+        if old is None:
+            os.environ.pop("APIC_SOLVER")
+        else:
+            os.environ["APIC_SOLVER"] = old
+    for k in range(2):
+        assert np.array_equal(b.field("phi", k), solo[k][0])
+        assert np.allclose(b.tallies(k, history=True)["history"], solo[k][1], rtol=1e-12, atol=1e-12)
 
 
 def test_boltzmann_rejections(apic):
