@@ -16,6 +16,7 @@ NO_FIELD = 2
 CHORD = 4
 FLOATING = 8
 BOLTZMANN = 16
+FE = 32
 NT = 7
 NH = 11
 
@@ -62,6 +63,7 @@ def lib():
         L.or_solve.argtypes = [vp, P(d), P(d)]
         L.or_solve_linear.argtypes = [vp, P(d), P(d)]
         L.or_newton_iterations.argtypes = [vp]
+        L.or_apply_operator.argtypes = [vp, P(d), P(d)]
         L.or_gradients.argtypes = [vp]
         L.or_push_only.argtypes = [vp]
         L.or_count.restype = i64
@@ -150,6 +152,8 @@ def make_config(d):
         flags |= FLOATING
     if d.get("boltzmann"):
         flags |= BOLTZMANN
+    if d.get("fe_operator"):
+        flags |= FE
     c.flags = flags
     return c
 
@@ -202,6 +206,13 @@ class Sim:
         if lib().or_solve_linear(self.h, _dp(r), _dp(phi)) != 0:
             raise RuntimeError("oracle has no Poisson matrix (no_field)")
         return phi.reshape(self.n1 + 1, self.n2 + 1)
+
+    def apply_operator(self, phi):
+        """L phi at every node (see or_apply_operator)."""
+        p = np.ascontiguousarray(phi, dtype=np.float64).ravel()
+        out = np.zeros_like(p)
+        lib().or_apply_operator(self.h, _dp(p), _dp(out))
+        return out.reshape(self.n1 + 1, self.n2 + 1)
 
     def newton_iterations(self):
         return int(lib().or_newton_iterations(self.h))

@@ -361,9 +361,65 @@ double or_sample_table(const or_sim* s, int which, double u) {
 #define UIDX(s, i, j) (((i) - 1) * (s)->N2 + (j))
 #define BANDA(a, s, r, c) (a)[(size_t)(c) * (s)->ld + ((r) - (c) + (s)->kl + (s)->ku)]
 
+/* Conservative form (option OR_FE; the paper discretises Eq. 7 by finite
+ * differences, Sec. 2): the weak form of Eq. 6 with the bilinear hat
+ * functions N_a of the logical grid, whose own weights are the charge
+ * assignment, int rho N_a dOmega = rho_a V_a (Eq. 5's V_a):
+ *   sum_b K_ab phi_b = rho_a V_a,
+ *   K_ab = int grad N_a . grad N_b dOmega
+ *        = int (J g^kl dN_a/dx_k dN_b/dx_l) dx1 dx2,
+ * g^kl = grad x_k . grad x_l from the chain rule of Eq. 2 (or_metric) and
+ * J = dOmega / (dx1 dx2) of Eq. 5, both taken at the cell centre (midpoint
+ * rule per cell).  K is symmetric, and its rows over all nodes sum to zero
+ * (the hat functions sum to one), so the discrete Gauss law holds exactly.
+ * The cell matrix of cell (ci, cj), corners p = px + 2 py at node
+ * (ci + px, cj + py): with s(0) = -1, s(1) = +1 and
+ * int f_a f_b = 1/3 (a = b) or 1/6 over the unit interval (f_0 = 1 - t,
+ * f_1 = t),
+ *   K_pq = J g11 h2/h1 s(px)s(qx) F(py,qy) + J g22 h1/h2 s(py)s(qy) F(px,qx)
+ *        + J g12 (s(px)s(qy) + s(qx)s(py)) / 4. */
+static void fe_cell(const or_sim* s, int ci, int cj, double K[4][4]) {
+  double x1c = 0.5 * (x1_node(s, ci) + x1_node(s, ci + 1));
+  double x2c = 0.5 * (x2_node(s, cj) + x2_node(s, cj + 1));
+  double m[4];
+  or_metric(s->c.alpha, or_r_of(s->c.alpha, x1c, x2c), x2c, m);
+  double g11 = m[0] * m[0] + m[1] * m[1], g22 = m[2] * m[2] + m[3] * m[3], g12 = m[0] * m[2] + m[1] * m[3];
+  double J = or_dOmega(s->c.alpha, x1c, x2c);
+  double a = J * g11 * s->h2 / s->h1, c = J * g22 * s->h1 / s->h2, b = J * g12;
+  for (int p = 0; p < 4; ++p)
+    for (int q = 0; q < 4; ++q) {
+      int px = p & 1, py = p >> 1, qx = q & 1, qy = q >> 1;
+      double sxp = px ? 1.0 : -1.0, syp = py ? 1.0 : -1.0, sxq = qx ? 1.0 : -1.0, syq = qy ? 1.0 : -1.0;
+      double fy = py == qy ? 1.0 / 3.0 : 1.0 / 6.0, fx = px == qx ? 1.0 / 3.0 : 1.0 / 6.0;
+      K[p][q] = a * sxp * sxq * fy + c * syp * syq * fx + b * 0.25 * (sxp * syq + sxq * syp);
+    }
+}
+
+/* Row (i, j) of the conservative form divided by -V_ij, in the layout of
+ * stencil(): sum_b w_b phi_b = -rho_ij. */
+static void stencil_fe(const or_sim* s, int i, int j, double w[3][5]) {
+  memset(w, 0, sizeof(double) * 15);
+  double V = s->V[i * s->N2 + j];
+  for (int ci = i - 1; ci <= i; ++ci)
+    for (int cj = j - 1; cj <= j; ++cj) {
+      if (ci < 0 || ci >= s->c.n1 || cj < 0 || cj >= s->c.n2) continue;
+      double K[4][4];
+      fe_cell(s, ci, cj, K);
+      int pa = (i - ci) | ((j - cj) << 1);
+      for (int q = 0; q < 4; ++q) {
+        int di = ci + (q & 1) - i, dj = cj + (q >> 1) - j;
+        w[di + 1][dj + 2] -= K[pa][q] / V;
+      }
+    }
+}
+
 /* The nine stencil weights of node (i, j): w[di+1][dj+2] for di in -1..1,
  * dj in -2..2 (the pole rows reach two nodes in j). */
 static void stencil(const or_sim* s, int i, int j, double w[3][5]) {
+  if (s->c.flags & OR_FE) {
+    stencil_fe(s, i, j, w);
+    return;
+  }
   memset(w, 0, sizeof(double) * 15);
   double c[4];
   lap_coef(s->c.alpha, x1_node(s, i), x2_node(s, j), c);
@@ -534,6 +590,39 @@ static int solve_boltzmann(or_sim* s, const double* rho, double* phi) {
   }
   free(band); free(piv); free(shift); free(b);
   return ok ? it : -1;
+}
+
+/* out = L phi at every node where the operator has a row: the interior rows
+ * of Eq. 7's differences (boundary rows 0), or, with OR_FE, every node's
+ * -(K phi)_a / V_a including the boundary rows (their sum weighted by V is
+ * the total flux, zero for any phi). */
+void or_apply_operator(const or_sim* s, const double* phi, double* out) {
+  size_t nn = (size_t)s->N1 * s->N2;
+  memset(out, 0, sizeof(double) * nn);
+  if (s->c.flags & OR_FE) {
+    for (int ci = 0; ci < s->c.n1; ++ci)
+      for (int cj = 0; cj < s->c.n2; ++cj) {
+        double K[4][4];
+        fe_cell(s, ci, cj, K);
+        for (int p = 0; p < 4; ++p) {
+          size_t a = (size_t)(ci + (p & 1)) * s->N2 + cj + (p >> 1);
+          for (int q = 0; q < 4; ++q) out[a] -= K[p][q] * phi[(size_t)(ci + (q & 1)) * s->N2 + cj + (q >> 1)];
+        }
+      }
+    for (size_t a = 0; a < nn; ++a) out[a] /= s->V[a];
+    return;
+  }
+  for (int i = 1; i < s->c.n1; ++i)
+    for (int j = 0; j < s->N2; ++j) {
+      double w[3][5], acc = 0.0;
+      stencil(s, i, j, w);
+      for (int di = -1; di <= 1; ++di)
+        for (int dj = -2; dj <= 2; ++dj) {
+          int jj = j + dj;
+          if (w[di + 1][dj + 2] != 0.0 && jj >= 0 && jj < s->N2) acc += w[di + 1][dj + 2] * phi[(i + di) * s->N2 + jj];
+        }
+      out[i * s->N2 + j] = acc;
+    }
 }
 
 /* The configured boundary values (phi_g, phi_out); with Boltzmann electrons

@@ -28,6 +28,7 @@ extern "C" {
 #define OR_CHORD_SAMPLES 8 /* the chord is tested at s = k / OR_CHORD_SAMPLES, k = 1..7 */
 #define OR_FLOATING 8    /* isolated grain: its potential follows the charge it collects */
 #define OR_BOLTZMANN 16  /* electrons not simulated: n_e = exp(phi) in Eq. 6, solved by Newton */
+#define OR_FE 32         /* conservative (bilinear finite-element) form of Eqs. 6-7 instead of Eq. 7's differences */
 
 #define OR_NT 7          /* tally components per bin */
 #define OR_NH 11         /* history fields per step (the last: the grain potential used) */
@@ -67,6 +68,7 @@ int or_deposit(or_sim* s);                  /* rho from the current particles */
 int or_solve(or_sim* s, const double* rho_or_null, double* phi_out);
 int or_solve_linear(or_sim* s, const double* rho, double* phi_out); /* Eqs. 6-7 with rho, any electron model */
 int or_newton_iterations(const or_sim* s);  /* Boltzmann electrons: Newton iterations of the last step's solve */
+void or_apply_operator(const or_sim* s, const double* phi, double* out); /* L phi per node (see apic_oracle.c) */
 void or_gradients(or_sim* s);               /* G1, G2 from the current phi */
 int or_push_only(or_sim* s);                /* gather + push + absorb + escape, no inject */
 
