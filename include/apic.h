@@ -82,6 +82,10 @@ extern "C" {
                                 on the grain, 0 outside, computed at creation) that restores that charge.
                                 Not with APIC_NO_FIELD, nor with apic_sensitivity (INVALID_ARG);
                                 apic_solve_poisson keeps using phi_grain. */
+#define APIC_FE_OPERATOR 32  /* the conservative form of Eqs. 6-7 instead of Eq. 7's finite differences: the
+                                bilinear finite-element weak form on the logical grid, sum_b K_ab phi_b =
+                                rho_a V_a with K_ab = int grad N_a . grad N_b dOmega (metric at cell centres),
+                                symmetric after weighting by V, exact discrete Gauss law; same solvers */
 #define APIC_BOLTZMANN 16    /* electrons are not simulated: their density is n0 exp(phi) (Te = 1, potential
                                 zero at the outer surface) in Eq. 6, whose nonlinear problem is solved by
                                 newton_iters Newton iterations, each a BiCGSTAB solve preconditioned by the
@@ -118,7 +122,8 @@ typedef struct {
   uint64_t seed;         /* Philox4x32-10 key */
   int32_t instance;      /* Philox counter tag; distinct instances draw distinct streams */
   int32_t precision;     /* APIC_FP64 or APIC_FP32_REFINED */
-  int32_t flags;         /* APIC_NO_INJECT | APIC_NO_FIELD | APIC_CHORD_ABSORB | APIC_FLOATING | APIC_BOLTZMANN */
+  int32_t flags;         /* APIC_NO_INJECT | APIC_NO_FIELD | APIC_CHORD_ABSORB | APIC_FLOATING | APIC_BOLTZMANN |
+                            APIC_FE_OPERATOR */
   double poisson_tol;    /* relative residual target ||b - A phi|| / ||b|| (0: 1e-10) */
   int32_t poisson_max_iter; /* BiCGSTAB iterations per step (0: 20) */
   int32_t sort_interval; /* sort particles by cell every this many steps (0: never) */

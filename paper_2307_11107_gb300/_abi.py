@@ -16,7 +16,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "GEOMETRY", -3: "CAPACITY", -4: "NOT_CONVERGED"
 FP64 = 0
 FP32_REFINED = 1
 LOAD_VOLUME, FLUX_SURFACE, EXPLICIT = 0, 1, 2
-NO_INJECT, NO_FIELD, CHORD_ABSORB, FLOATING, BOLTZMANN = 1, 2, 4, 8, 16
+NO_INJECT, NO_FIELD, CHORD_ABSORB, FLOATING, BOLTZMANN, FE_OPERATOR = 1, 2, 4, 8, 16, 32
 NT, NH = 7, 11
 
 SYMBOLS = ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",

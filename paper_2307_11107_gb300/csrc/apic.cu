@@ -362,13 +362,58 @@ void volumes_t(const Inst& I, T alpha, std::vector<T>& V) {
 
 void build_volumes(const Inst& I, std::vector<double>& V) { volumes_t<double>(I, I.alpha, V); }
 
-// Row (i, j) of Eq. 7 with second-order differences, unscaled: the kSt
-// stencil weights (Dirichlet neighbours included); returns a1 = A / h1^2.
+// Conservative form of Eqs. 6-7 (APIC_FE_OPERATOR): the weak form of Eq. 6
+// with the bilinear hat functions N_a of the logical grid, which are also the
+// charge-assignment weights, so that sum_b K_ab phi_b = rho_a V_a (Eq. 5's
+// node volume) with
+//   K_ab = int grad N_a . grad N_b dOmega = int J g^kl dN_a/dx_k dN_b/dx_l dx1 dx2,
+// g^kl = grad x_k . grad x_l (the chain rule of Eq. 2) and J = dOmega/(dx1 dx2)
+// (Eq. 5), both at the cell centre.  Cell (ci, cj), corner p = px + 2 py at
+// node (ci + px, cj + py); with s(0) = -1, s(1) = 1 and F = 1/3 on equal
+// corners' coordinates, 1/6 otherwise (products of the linear factors
+// integrated over a unit interval):
+//   K_pq = J g11 h2/h1 s(px) s(qx) F(py, qy) + J g22 h1/h2 s(py) s(qy) F(px, qx)
+//        + J g12 (s(px) s(qy) + s(qx) s(py)) / 4.
 template <class T>
-T fine_row(const Inst& I, T alpha, int i, int j, T w[kSt]) {
+void fe_cell_h(const Inst& I, T alpha, int ci, int cj, T K[4][4]) {
+  const double x1c = 0.5 * (x1_node_h(I, ci) + x1_node_h(I, ci + 1));
+  const double x2c = 0.5 * (x2_node_h(I, cj) + x2_node_h(I, cj + 1));
+  const Metric<T> m = metric(alpha, radius(alpha, T(x1c), T(x2c)), T(x2c));
+  const T g11 = m.x1R * m.x1R + m.x1Z * m.x1Z, g22 = m.x2R * m.x2R + m.x2Z * m.x2Z;
+  const T g12 = m.x1R * m.x2R + m.x1Z * m.x2Z;
+  const T J = volume_density(alpha, T(x1c), T(x2c));
+  const T a = J * g11 * T(I.h2 / I.h1), c = J * g22 * T(I.h1 / I.h2), b = J * g12;
+  for (int p = 0; p < 4; ++p)
+    for (int q = 0; q < 4; ++q) {
+      const int px = p & 1, py = p >> 1, qx = q & 1, qy = q >> 1;
+      const double sxp = px ? 1.0 : -1.0, syp = py ? 1.0 : -1.0, sxq = qx ? 1.0 : -1.0, syq = qy ? 1.0 : -1.0;
+      const double fy = py == qy ? 1.0 / 3.0 : 1.0 / 6.0, fx = px == qx ? 1.0 / 3.0 : 1.0 / 6.0;
+      K[p][q] = a * T(sxp * sxq * fy) + c * T(syp * syq * fx) + b * T(0.25 * (sxp * syq + sxq * syp));
+    }
+}
+
+// Row (i, j) of the discrete operator, unscaled, in the form L phi = -rho:
+// the kSt stencil weights (Dirichlet neighbours included).  Eq. 7 with
+// second-order differences, or with APIC_FE_OPERATOR the conservative form's
+// row -K_a / V_a (V: the node volumes).  Returns a1 = A / h1^2 of Eq. 7, the
+// row scale of both forms.
+template <class T>
+T fine_row(const Inst& I, T alpha, int i, int j, T w[kSt], const T* V) {
   LapCoef<T> c = lap_coef(alpha, T(x1_node_h(I, i)), T(x2_node_h(I, j)));
   T a1 = c.A / T(I.h1 * I.h1);
   for (int k = 0; k < kSt; ++k) w[k] = T(0.0);
+  if (I.flags & APIC_FE_OPERATOR) {
+    const T Va = V[(size_t)i * I.N2 + j];
+    for (int ci = i - 1; ci <= i; ++ci)
+      for (int cj = j - 1; cj <= j; ++cj) {
+        if (ci < 0 || ci >= I.n1 || cj < 0 || cj >= I.n2) continue;
+        T K[4][4];
+        fe_cell_h<T>(I, alpha, ci, cj, K);
+        const int pa = (i - ci) | ((j - cj) << 1);
+        for (int q = 0; q < 4; ++q) w[st_slot(ci + (q & 1) - i, cj + (q >> 1) - j)] -= K[pa][q] / Va;
+      }
+    return a1;
+  }
   w[st_slot(-1, 0)] += a1;
   w[st_slot(1, 0)] += a1;
   w[st_slot(0, 0)] += T(-2.0) * a1;
@@ -394,10 +439,11 @@ T fine_row(const Inst& I, T alpha, int i, int j, T w[kSt]) {
   return a1;
 }
 
-// Finest-level operator: Eq. 7 with second-order differences, each row scaled
-// by rscale = 1/a1 = h1^2 / A; entries towards the Dirichlet rows are moved to
-// bbc (times phi_g or phi_out) and stored as zero.
-void build_fine(const Inst& I, HostLevel& L, std::vector<double>& rscale, std::vector<double>& bbc) {
+// Finest-level operator (fine_row), each row scaled by rscale = 1/a1 =
+// h1^2 / A; entries towards the Dirichlet rows are moved to bbc (times phi_g
+// or phi_out) and stored as zero.
+void build_fine(const Inst& I, const std::vector<double>& V, HostLevel& L, std::vector<double>& rscale,
+                std::vector<double>& bbc) {
   L.n1 = I.n1;
   L.n2 = I.n2;
   L.N1 = I.N1;
@@ -408,7 +454,7 @@ void build_fine(const Inst& I, HostLevel& L, std::vector<double>& rscale, std::v
   for (int i = 1; i < I.n1; ++i)
     for (int j = 0; j <= I.n2; ++j) {
       double w[kSt];
-      double a1 = fine_row<double>(I, I.alpha, i, j, w);
+      double a1 = fine_row<double>(I, I.alpha, i, j, w, V.data());
       double sc = 1.0 / a1;
       size_t nd = (size_t)i * I.N2 + j;
       rscale[nd] = sc;
@@ -432,10 +478,12 @@ void build_fine(const Inst& I, HostLevel& L, std::vector<double>& rscale, std::v
 // The Dirichlet term of the problem with phi = 1 on the grain and 0 on the
 // outer surface, rows scaled as build_fine's (nonzero on the row i = 1 only).
 void grain_bbc(const Inst& I, std::vector<double>& hbg) {
+  std::vector<double> V;
+  build_volumes(I, V);
   hbg.assign((size_t)I.nodes, 0.0);
   for (int j = 0; j <= I.n2; ++j) {
     double w[kSt];
-    double sc = 1.0 / fine_row<double>(I, I.alpha, 1, j, w);
+    double sc = 1.0 / fine_row<double>(I, I.alpha, 1, j, w, V.data());
     double bb = 0.0;
     for (int dj = -1; dj <= 1; ++dj) bb -= w[st_slot(-1, dj)] * sc;
     hbg[(size_t)I.N2 + j] = bb;
@@ -741,7 +789,7 @@ static int setup(apic_sim* S) {
     build_volumes(I, vols[k]);
     // operator and multigrid hierarchy
     levels[k].emplace_back();
-    build_fine(I, levels[k][0], rscs[k], bbcs[k]);
+    build_fine(I, vols[k], levels[k][0], rscs[k], bbcs[k]);
     while (true) {
       const HostLevel& F = levels[k].back();
       if ((int)levels[k].size() >= kMaxLevels) break;
@@ -1915,7 +1963,7 @@ static bool tangent_setup(apic_sim* S) {
       for (int j = 0; j <= I.n2; ++j) {
         size_t nd = (size_t)i * I.N2 + j;
         D1h wd[kSt];
-        fine_row<D1h>(I, al, i, j, wd);
+        fine_row<D1h>(I, al, i, j, wd, V.data());
         for (int q = 0; q < kSt; ++q) hst[(size_t)q * I.nodes + nd] = wd[q].d[0];
       }
     grain_bbc(I, hbg);

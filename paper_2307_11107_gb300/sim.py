@@ -38,7 +38,8 @@ def make_config(d, precision="fp32"):
     c.precision = _abi.FP64 if prec in ("fp64", _abi.FP64) else _abi.FP32_REFINED
     c.flags = ((_abi.NO_INJECT if d.get("no_inject") else 0) | (_abi.NO_FIELD if d.get("no_field") else 0) |
                (_abi.CHORD_ABSORB if d.get("chord_absorb") else 0) |
-               (_abi.FLOATING if d.get("floating") else 0) | (_abi.BOLTZMANN if d.get("boltzmann") else 0))
+               (_abi.FLOATING if d.get("floating") else 0) | (_abi.BOLTZMANN if d.get("boltzmann") else 0) |
+               (_abi.FE_OPERATOR if d.get("fe_operator") else 0))
     c.poisson_tol = float(d.get("poisson_tol", 0.0))
     c.poisson_max_iter = int(d.get("poisson_max_iter", 0))
     c.sort_interval = int(d.get("sort_interval", 0))

@@ -45,13 +45,15 @@ def test_vacuum_sphere(apic, precision):
     assert np.all(J[[0, 2, 3]] == 0.0) and np.all(J[:, 2] == 0.0)
 
 
-@pytest.mark.parametrize("precision,alpha,B", [("fp64", 0.15, 0.5), ("fp64", -0.2, 1.0), ("fp32", 0.15, 0.5)])
-def test_window_against_oracle_differences(apic, precision, alpha, B):
+@pytest.mark.parametrize("precision,alpha,B,fe", [("fp64", 0.15, 0.5, False), ("fp64", -0.2, 1.0, False),
+                                                  ("fp32", 0.15, 0.5, False), ("fp64", 0.15, 0.5, True)])
+def test_window_against_oracle_differences(apic, precision, alpha, B, fe):
     """Window means and the 5 x 3 Jacobian against the oracle's central
-    differences with the decisions of its unperturbed run."""
+    differences with the decisions of its unperturbed run (also with the
+    conservative operator, whose alpha derivative includes the node volumes')."""
     n, K = 4000, 5
     cfg = workload(n1=32, n2=16, alpha=alpha, B=B, n_init=n, x1_out=-0.1, seed=3, poisson_tol=1e-13,
-                   poisson_max_iter=80)
+                   poisson_max_iter=80, fe_operator=fe)
     st = _states(n, cfg["x1_out"], 31)
     if precision == "fp32":
         st = [s.astype(np.float32).astype(np.float64) for s in st]
