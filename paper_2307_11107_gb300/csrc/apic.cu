@@ -1382,7 +1382,7 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
     case 1:
       // Boltzmann electrons: newton Newton iterations, each a linear solve
       for (int k = 0; k < (S->boltz ? S->newton : 1); ++k) {
-        if (S->boltz) launch_newton(d, -1, s);
+        if (S->boltz) launch_newton(d, -1, k == S->newton - 1, s);
         if (S->coop > 0) {
           if (solve_coop<Real>(S, d, s, kBcrRho | kBcrFields) != cudaSuccess) return false;
           continue;
@@ -1790,7 +1790,7 @@ static int solve_impl(apic_sim* S, int inst, const double* rho, double* phi_out)
   launch_b_from_rho(d, inst, S->stream);
   if (I.flags & APIC_BOLTZMANN) {  // Newton from the current phi
     for (int k = 0; k < S->newton; ++k) {
-      launch_newton(d, inst, S->stream);
+      launch_newton(d, inst, k == S->newton - 1, S->stream);
       if (!solve_instance<Real>(S, inst)) return S->status;
     }
     launch_newton_end(d, S->stream);

@@ -10,6 +10,10 @@ namespace apic {
 
 constexpr int kNT = APIC_NT;
 constexpr int kNH = APIC_NH;
+// Inexact Newton (Boltzmann electrons): every Newton iteration but the last
+// solves its linear system only until the residual has fallen by this factor
+// (or below the tolerance); quadratic convergence makes up for it.
+constexpr double kNewtonEta = 1e-3;
 constexpr int kMaxLevels = 12;
 constexpr int kMaxPop = 128;      // populations (instance x species) per batch
 constexpr int kTable = 4096;      // intervals of the inverse-CDF sampling tables
@@ -98,7 +102,7 @@ struct PopState {
 // Per-instance solver scalars (device).
 struct SolverState {
   double rho, alpha, omega, rho_old;
-  double bnorm2, rnorm2;
+  double eta2, rn0;         // inexact Newton: stop also at |r|^2 <= eta2 |r_0|^2 (0: the tolerance alone); |r_0|^2
   double res;              // relative residual of the last iterate
   int32_t iters, done;
   double pad[8];
@@ -234,7 +238,7 @@ void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s);
 void launch_b_vacuum(const DevPtrs& d, int inst, cudaStream_t s);
 void launch_store_vacuum(const DevPtrs& d, int inst, cudaStream_t s);
 void launch_float_phi(const DevPtrs& d, cudaStream_t s);
-void launch_newton(const DevPtrs& d, int only, cudaStream_t s);
+void launch_newton(const DevPtrs& d, int only, int last, cudaStream_t s);
 void launch_newton_end(const DevPtrs& d, cudaStream_t s);
 
 // Block cyclic reduction (bcr.cu) of the finest-level system of every

@@ -794,7 +794,8 @@ __global__ void __launch_bounds__(256) k_bicg_p(DevPtrs d, int final_check) {
   __shared__ double shp;
   double bn = cta_partials(d, inst, 0, &shp), rho = cta_partials(d, inst, 1, &shp), rn = cta_partials(d, inst, 2, &shp);
   double tol2 = I.tol * I.tol;
-  bool conv = rn <= tol2 * bn || !(rn == rn);
+  const double rn0 = S.iters == 0 ? rn : S.rn0;
+  bool conv = rn <= fmax(tol2 * bn, S.eta2 * rn0) || !(rn == rn);
   bool last = final_check || S.iters >= I.max_iter;
   if (conv || last) {
     __syncthreads();
@@ -820,7 +821,10 @@ __global__ void __launch_bounds__(256) k_bicg_p(DevPtrs d, int final_check) {
     e0[nd] = Real(0);
   }
   __syncthreads();
-  if (blockIdx.x == 0 && threadIdx.x == 0) S.rho = rho;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S.rho = rho;
+    if (S.iters == 0) S.rn0 = rn;
+  }
 }
 
 // ph = M^-1 p (from e0), v = A ph; partial (rh, v).  Same kernel for the
@@ -944,7 +948,7 @@ __global__ void k_bicg_check(DevPtrs d, cudaGraphConditionalHandle h, int use_ha
     const Inst& I = d.inst[inst];
     if (S.done) continue;
     double bn = sum_partials(d, inst, 0), rn = sum_partials(d, inst, 2);
-    bool conv = rn <= I.tol * I.tol * bn;
+    bool conv = rn <= fmax(I.tol * I.tol * bn, S.eta2 * S.rn0);
     bool bad = !(rn == rn);
     if (conv || bad || S.iters >= I.max_iter) {
       S.done = 1;
@@ -1055,6 +1059,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(DevPtrs d, SolvePlan
   __shared__ int done[kCoopMaxInst];
   __shared__ double s_rho[kCoopMaxInst], s_rho_old[kCoopMaxInst], s_alpha[kCoopMaxInst], s_omega[kCoopMaxInst];
   __shared__ double s_bn[kCoopMaxInst];
+  __shared__ double s_eta2[kCoopMaxInst], s_rn0[kCoopMaxInst];
   __shared__ int s_iters[kCoopMaxInst];
   const int nb = gridDim.x;
   const long long stride = (long long)nb * blockDim.x;
@@ -1077,6 +1082,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(DevPtrs d, SolvePlan
       s_alpha[inst] = 1.0;
       s_omega[inst] = 1.0;
       s_iters[inst] = 0;
+      s_eta2[inst] = d.sol[inst].eta2;
     }
     const double* st = d.st64 + (long long)kSt * I.node_off;
     const double* x = d.phi + I.node_off;
@@ -1115,7 +1121,9 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(DevPtrs d, SolvePlan
       if (done[inst]) continue;
       double rho = coop_sum(d, inst, 1, nb, sh), rn = coop_sum(d, inst, 2, nb, sh);
       double bn = s_bn[inst];
-      bool conv = rn <= I.tol * I.tol * bn;
+      if (it == 0 && threadIdx.x == 0) s_rn0[inst] = rn;
+      __syncthreads();
+      bool conv = rn <= fmax(I.tol * I.tol * bn, s_eta2[inst] * s_rn0[inst]);
       bool bad = !(rn == rn);
       __syncthreads();
       if (threadIdx.x == 0) {
