@@ -129,8 +129,9 @@ typedef struct {
   int32_t sort_interval; /* sort particles by cell every this many steps (0: never) */
   int32_t history_cap;   /* rows of the per-step history ring (0: 4096) */
   int32_t poisson_guess; /* start of each step's solve: 0 previous phi, 1 linear extrapolation 2 phi^n - phi^n-1 */
-  int32_t newton_iters;  /* APIC_BOLTZMANN: Newton iterations per solve (0: 8); once the nonlinear residual
-                            is below poisson_tol the remaining iterations do no solver work */
+  int32_t newton_iters;  /* APIC_BOLTZMANN: Newton iterations per solve (0: 8); the linear solve of each but
+                            the last stops once its residual has fallen 1000-fold (inexact Newton); once the
+                            nonlinear residual is below poisson_tol the remaining iterations do no solver work */
   int32_t reserved[3];
 } apic_config_t;
 
