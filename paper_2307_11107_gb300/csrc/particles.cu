@@ -952,17 +952,23 @@ __global__ void __launch_bounds__(256) k_sort_count(DevPtrs d) {
     const Real ih1 = (Real)(1.0 / I.h1);
     for (int r = threadIdx.x; r < nrows; r += blockDim.x) s_hist[r] = 0u;
     __syncthreads();
+    // all of the thread's loads first (kSortItems in flight), then the keys
+    Real xs[kSortItems];
+#pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-      long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
+      const long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
+      xs[it] = k < npop ? X1[P.base + k] : Real(1);
+    }
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      const long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
       int row = -1;
       if (k < npop) {
-        long long slot = P.base + k;
-        Real x1 = X1[slot];
-        if (x1 < Real(0)) {
-          row = (int)floor((x1 + Real(1)) * ih1);
+        if (xs[it] < Real(0)) {
+          row = (int)floor((xs[it] + Real(1)) * ih1);
           row = row < 0 ? 0 : (row > nrows - 1 ? nrows - 1 : row);
         }
-        d.keys[slot] = row;
+        d.keys[P.base + k] = row;
       }
       warp_count(s_hist, row);
     }
@@ -1049,11 +1055,15 @@ __global__ void __launch_bounds__(256) k_sort_scatter(DevPtrs d) {
     unsigned* cur = s_hist + nrows;
     for (int r = threadIdx.x; r < nrows; r += blockDim.x) cnt[r] = 0u;
     __syncthreads();
+    // the thread's keys, all loads in flight at once; kept for the placement
+    int rows[kSortItems];
+#pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-      long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
-      int row = k < npop ? d.keys[P.base + k] : -1;
-      warp_count(cnt, row);
+      const long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
+      rows[it] = k < npop ? d.keys[P.base + k] : -1;
     }
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) warp_count(cnt, rows[it]);
     __syncthreads();
     // reserve this chunk's range of every row it holds
     const unsigned long long first = d.cell_off[P.cell_off];
@@ -1062,35 +1072,38 @@ __global__ void __launch_bounds__(256) k_sort_scatter(DevPtrs d) {
       cur[r] = c ? (unsigned)(d.cell_off[P.cell_off + r] - first) + atomicAdd(d.cell_cnt + P.cell_off + r, c) : 0u;
     }
     __syncthreads();
-    // the key and state of the next item are loaded while the current one is placed
-    int nrow = -1;
-    Real n1v = Real(0), n2v = Real(0), nRv = Real(0), nZv = Real(0), nTv = Real(0);
-    auto fetch = [&](int it) {
-      long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
-      nrow = -1;
-      if (k < npop) {
-        long long slot = P.base + k;
-        nrow = d.keys[slot];
-        n1v = ((const Real*)d.x1)[slot];
-        n2v = ((const Real*)d.x2)[slot];
-        nRv = ((const Real*)d.vR)[slot];
-        nZv = ((const Real*)d.vZ)[slot];
-        nTv = ((const Real*)d.vT)[slot];
+    // the states of half the thread's items in flight at once while the
+    // other half is placed
+    constexpr int kHalf = kSortItems / 2;
+    static_assert(kSortItems % 2 == 0, "two halves");
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      Real v1[kHalf], v2[kHalf], vR[kHalf], vZ[kHalf], vT[kHalf];
+#pragma unroll
+      for (int u = 0; u < kHalf; ++u) {
+        const int it = h * kHalf + u;
+        const long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
+        if (rows[it] >= 0) {
+          const long long slot = P.base + k;
+          v1[u] = ((const Real*)d.x1)[slot];
+          v2[u] = ((const Real*)d.x2)[slot];
+          vR[u] = ((const Real*)d.vR)[slot];
+          vZ[u] = ((const Real*)d.vZ)[slot];
+          vT[u] = ((const Real*)d.vT)[slot];
+        }
       }
-    };
-    fetch(0);
-    for (int it = 0; it < kSortItems; ++it) {
-      const int row = nrow;
-      const Real v1 = n1v, v2 = n2v, vR = nRv, vZ = nZv, vT = nTv;
-      if (it + 1 < kSortItems) fetch(it + 1);
-      unsigned pos = warp_count(cur, row);
-      if (row >= 0) {
-        long long dst = P.base + (long long)pos;
-        ((Real*)d.y1)[dst] = v1;
-        ((Real*)d.y2)[dst] = v2;
-        ((Real*)d.yR)[dst] = vR;
-        ((Real*)d.yZ)[dst] = vZ;
-        ((Real*)d.yT)[dst] = vT;
+#pragma unroll
+      for (int u = 0; u < kHalf; ++u) {
+        const int row = rows[h * kHalf + u];
+        const unsigned pos = warp_count(cur, row);
+        if (row >= 0) {
+          const long long dst = P.base + (long long)pos;
+          ((Real*)d.y1)[dst] = v1[u];
+          ((Real*)d.y2)[dst] = v2[u];
+          ((Real*)d.yR)[dst] = vR[u];
+          ((Real*)d.yZ)[dst] = vZ[u];
+          ((Real*)d.yT)[dst] = vT[u];
+        }
       }
     }
     __syncthreads();
