@@ -11,6 +11,13 @@
  * numeric results (Figs. 1-3 are plots), so all dynamic quantities are pinned
  * only by invariants (round trips, closed forms, conservation laws); the tests
  * say which invariant pins which function.
+ *
+ * Options beside the paper's method, each off by default and pinned by its own
+ * tests: chord-intersection absorption of grazing orbits (OR_CHORD), the
+ * isolated grain whose potential follows the collected charge (OR_FLOATING),
+ * Boltzmann electrons solved by Newton (OR_BOLTZMANN; the paper mentions the
+ * option in Sec. 2), and the conservative finite-element form of Eqs. 6-7
+ * (OR_FE).
  */
 #include "apic_oracle.h"
 
