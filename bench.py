@@ -27,6 +27,12 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s (full PIC step) FP32+refined vs FP64 at stated error; % HBM roofline"
 UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE_STEP = 40  # FP32 state (x1, x2, vR, vZ, vTheta) read once and written once
+# FP32 operations of one particle update as the equations state them (Eq. 3
+# radius, cell and weights, bilinear gather of the two node gradients, the
+# metric of Eq. 10, the Boris step of Eq. 9, the chord and rotation, the
+# grain and escape tests, Eq. 2 and the new cell): 127, counted per
+# operation (a multiply-add as two, a square root or division as one)
+FLOPS_PER_PARTICLE_STEP = 127
 
 
 def parse():
@@ -341,6 +347,16 @@ def main():
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": "k_push",
             "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP, "peak_source": src,
             "push_ms": push_ms, "phase_ms_per_step": {k: v / kt for k, v in st["phase_ms"].items()}}
+    # the ALU ceiling beside it: the push's FP32 arithmetic against the measured
+    # FMA throughput of this GPU (the measured peaks hold no CUDA-core figure)
+    try:
+        fma_tflops = apic.probe_fp32_fma()
+        alu = FLOPS_PER_PARTICLE_STEP * n_avg / (push_ms / 1e3) / 1e12
+        roof["alu"] = {"flops_per_particle_step": FLOPS_PER_PARTICLE_STEP, "achieved": alu,
+                       "peak": fma_tflops, "unit": "TFLOP/s", "frac": alu / fma_tflops,
+                       "peak_source": "measured (apic_probe_fp32_fma)"}
+    except Exception as e:  # the probe is a side figure: its failure leaves the line intact
+        roof["alu"] = {"unavailable": str(e)}
 
     # end to end through the public API: initial state uploaded from pinned host
     # memory, then per step apic_step + apic_tallies (bins, counts, history row)

@@ -333,6 +333,15 @@ typedef struct {
 int apic_deposit_static(const apic_grid_t* grid, const double* x1, const double* x2, int64_t n, double qw,
                         const double* volume, double* rho, void* stream);
 
+/* FP32 CUDA-core throughput of the current device in TFLOP/s: independent fused
+ * multiply-add chains (2 FLOPs each) over every SM, reps iterations per chain,
+ * timed with CUDA events on `stream` (a cudaStream_t; NULL: the default stream)
+ * after one warm-up launch.  It is the ALU ceiling that the push's arithmetic
+ * is compared with (the measured peaks hold only memory bandwidth and tensor
+ * throughput).  Waits for the stream.
+ * Errors: INVALID_ARG (NULL tflops, reps < 1), CUDA. */
+int apic_probe_fp32_fma(void* stream, int32_t reps, double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

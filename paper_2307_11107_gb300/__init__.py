@@ -6,7 +6,7 @@
 from ._abi import (EXPLICIT, FLUX_SURFACE, FP32_REFINED, FP64, LOAD_VOLUME, NH, NO_FIELD, NO_INJECT, NT,
                    SYMBOLS, load)
 from .build import build
-from .sim import ApicError, Sim, make_config
+from .sim import ApicError, Sim, make_config, probe_fp32_fma
 
-__all__ = ["Sim", "ApicError", "make_config", "build", "load", "SYMBOLS", "FP64", "FP32_REFINED",
+__all__ = ["Sim", "ApicError", "make_config", "probe_fp32_fma", "build", "load", "SYMBOLS", "FP64", "FP32_REFINED",
            "LOAD_VOLUME", "FLUX_SURFACE", "EXPLICIT", "NO_INJECT", "NO_FIELD", "NT", "NH"]

@@ -35,6 +35,7 @@ UNITS = [
     ("tangent.cu", "tangent_f64.o", ["-DAPIC_REAL=double", "-DAPIC_TANGENT_COMMON", "-fmad=false"]),
     ("tangent.cu", "tangent_f32.o", ["-DAPIC_REAL=float"]),
     ("deposit_static.cu", "deposit_static.o", ["-fmad=false"]),
+    ("probe.cu", "probe.o", []),
 ]
 
 

@@ -19,6 +19,19 @@ class ApicError(RuntimeError):
         self.code = code
 
 
+def probe_fp32_fma(stream=None, reps=4096):
+    """FP32 CUDA-core throughput of the current GPU in TFLOP/s
+    (apic_probe_fp32_fma)."""
+    import torch
+    lib = _abi.load()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_double()
+    rc = lib.apic_probe_fp32_fma(C.c_void_p(s.cuda_stream), int(reps), C.byref(out))
+    if rc != 0:
+        raise ApicError(rc, "apic_probe_fp32_fma failed")
+    return out.value
+
+
 def make_config(d, precision="fp32"):
     """Workload dict (the keys used by tests and bench) -> apic_config_t."""
     c = _abi.Config()

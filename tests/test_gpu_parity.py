@@ -162,3 +162,11 @@ def test_sorting_does_not_change_results(apic, prec):
     for sp in (0, 1):
         assert t0["counts"][sp] == t1["counts"][sp]
     assert np.allclose(t0["bins"], t1["bins"], rtol=1e-12, atol=1e-300)
+
+
+def test_fp32_fma_probe(apic):
+    """The FP32 CUDA-core ceiling the push's arithmetic is compared with: the
+    probe runs and reports a plausible GB300 figure (152 SMs x 128 lanes x 2
+    FLOPs at up to 2.07 GHz is about 80 TFLOP/s)."""
+    t = apic.probe_fp32_fma()
+    assert 20.0 < t < 100.0, t
