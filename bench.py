@@ -185,6 +185,28 @@ def replica_throughput(advanced, seconds, pg=None, device="cpu"):
     return a / t, a, t
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the
+    architecture)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip() + " (" + platform.machine() + ")"
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
 def run_oracle(cfg, n_per_species, steps):
     """The FP64 CPU oracle as it stands, single thread, on `steps` steps of the
     same workload with n_per_species macro-particles per species (the macro
@@ -220,7 +242,7 @@ def reference_arm(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": cfg["name"], "alpha": cfg["alpha"], "grid": [cfg["n1"], cfg["n2"]],
                    "particles_per_species": n, "sample": "full steps with %d macro-particles per species" % n},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_model(),
                          "sample": "%d steps, %d macro-particles per species, 256x128 grid" % (steps, n)},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -399,7 +421,7 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu:
         n, k = 2_000_000, 50  # about 10-15 s of single-thread work
         val, secs = run_oracle(cfg, n, k)
-        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_model(),
                "sample": "%d full steps of the same workload with %.0e macro-particles per species (FP64, 1 thread)"
                          % (k, n),
                "seconds": secs}
