@@ -8,5 +8,14 @@ from ._abi import (EXPLICIT, FLUX_SURFACE, FP32_REFINED, FP64, LOAD_VOLUME, NH, 
 from .build import build
 from .sim import ApicError, Sim, make_config, probe_fp32_fma
 
-__all__ = ["Sim", "ApicError", "make_config", "probe_fp32_fma", "build", "load", "SYMBOLS", "FP64", "FP32_REFINED",
+
+def __getattr__(name):
+    # the torch.autograd binding is loaded on first use
+    if name == "AdjointWindow":
+        from .autograd import AdjointWindow
+        return AdjointWindow
+    raise AttributeError(name)
+
+
+__all__ = ["Sim", "ApicError", "make_config", "probe_fp32_fma", "AdjointWindow", "build", "load", "SYMBOLS", "FP64", "FP32_REFINED",
            "LOAD_VOLUME", "FLUX_SURFACE", "EXPLICIT", "NO_INJECT", "NO_FIELD", "NT", "NH"]

@@ -117,3 +117,31 @@ def test_batched_window_equals_single(apic):
         assert np.allclose(out["values"][k], v, rtol=1e-10, atol=1e-12)
         scale = np.abs(J).max(axis=1, keepdims=True) + 1e-30
         assert (np.abs(out["jacobian"][k] - J) / scale).max() < 1e-8
+
+
+def test_autograd_window(apic):
+    """apic.AdjointWindow as a torch.autograd.Function: on the vacuum sphere
+    the gradient of the grain charge is dQ/dphi_g = 4 pi/(1 + x1_out) along
+    phi_g and zero along B; with particles, backward equals the vector-Jacobian
+    product of apic_adjoint for the same window."""
+    import torch
+    cfg = workload(n1=64, n2=32, alpha=0.0, n_init=1000, no_inject=True, poisson_tol=1e-12, poisson_max_iter=60)
+    p = torch.tensor([[cfg["alpha"], cfg["phi_g"], cfg["B"]]], dtype=torch.float64, requires_grad=True)
+    v = apic.AdjointWindow.apply(p, [cfg], [[None, None]], 3, "fp64")
+    v[0, 4].backward()
+    x1o = cfg["x1_out"]
+    assert p.grad[0, 1].item() == pytest.approx(4 * np.pi / (1 + x1o), rel=1e-9)
+    assert p.grad[0, 2].item() == 0.0
+    n, K = 4000, 4
+    cfg = workload(n1=32, n2=16, alpha=0.15, B=0.5, n_init=n, x1_out=-0.1, seed=3, poisson_tol=1e-13,
+                   poisson_max_iter=80)
+    st = _states(n, cfg["x1_out"], 31)
+    w = np.array([0.3, -1.0, 2.0, 0.5, 1e-3])
+    p = torch.tensor([[cfg["alpha"], cfg["phi_g"], cfg["B"]]], dtype=torch.float64, requires_grad=True)
+    v = apic.AdjointWindow.apply(p, [cfg], [st], K, "fp64")
+    (v[0] * torch.as_tensor(w)).sum().backward()
+    s = apic.Sim(cfg, precision="fp64")
+    for sp, x in enumerate(st):
+        s.add_particles(sp, x)
+    g = s.adjoint(K, w)
+    assert np.allclose(p.grad.numpy(), g, rtol=1e-12, atol=0)
