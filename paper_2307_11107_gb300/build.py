@@ -3,12 +3,14 @@
 Translation units (compiled in parallel):
   particles.cu  twice: FP64 particles (-fmad=false, the parity build) and FP32
   poisson.cu    twice: FP64 and FP32 multigrid preconditioner
-  fields.cu     node fields and bookkeeping (FP64, -fmad=false)
+  fields.cu     node fields and bookkeeping, the isolated grain's correction and
+                the Newton linearisation of Boltzmann electrons (FP64, -fmad=false)
   bcr.cu        block cyclic reduction solve (FP32 blocks, FP64 refinement)
   apic.cu       host set-up and the C ABI
   tangent.cu    twice: the sensitivity window's particle kernels in FP64
                 (-fmad=false, with its node kernels) and FP32
   deposit_static.cu  the deposit entry point that uses no caller-side allocation
+  probe.cu      the FP32 fused-multiply-add throughput probe (the ALU ceiling)
 """
 import os
 import shutil
