@@ -84,7 +84,7 @@ extern "C" {
                                 apic_solve_poisson keeps using phi_grain. */
 #define APIC_FE_OPERATOR 32  /* the conservative form of Eqs. 6-7 instead of Eq. 7's finite differences: the
                                 bilinear finite-element weak form on the logical grid, sum_b K_ab phi_b =
-                                rho_a V_a with K_ab = int grad N_a . grad N_b dOmega (metric at cell centres),
+                                rho_a V_a with K_ab = int grad N_a . grad N_b dOmega (3 x 3 Gauss points per cell),
                                 symmetric after weighting by V, exact discrete Gauss law; same solvers */
 #define APIC_BOLTZMANN 16    /* electrons are not simulated: their density is n0 exp(phi) (Te = 1, potential
                                 zero at the outer surface) in Eq. 6, whose nonlinear problem is solved by

@@ -376,29 +376,51 @@ double or_sample_table(const or_sim* s, int which, double u) {
  *   K_ab = int grad N_a . grad N_b dOmega
  *        = int (J g^kl dN_a/dx_k dN_b/dx_l) dx1 dx2,
  * g^kl = grad x_k . grad x_l from the chain rule of Eq. 2 (or_metric) and
- * J = dOmega / (dx1 dx2) of Eq. 5, both taken at the cell centre (midpoint
- * rule per cell).  K is symmetric, and its rows over all nodes sum to zero
- * (the hat functions sum to one), so the discrete Gauss law holds exactly.
- * The cell matrix of cell (ci, cj), corners p = px + 2 py at node
- * (ci + px, cj + py): with s(0) = -1, s(1) = +1 and
- * int f_a f_b = 1/3 (a = b) or 1/6 over the unit interval (f_0 = 1 - t,
- * f_1 = t),
- *   K_pq = J g11 h2/h1 s(px)s(qx) F(py,qy) + J g22 h1/h2 s(py)s(qy) F(px,qx)
- *        + J g12 (s(px)s(qy) + s(qx)s(py)) / 4. */
+ * J = dOmega / (dx1 dx2) of Eq. 5, integrated per cell by quadrature.  K is
+ * symmetric, and its rows over all nodes sum to zero (the hat functions sum
+ * to one), so the discrete Gauss law holds exactly.  Cell (ci, cj) has the
+ * corners p = px + 2 py at nodes (ci + px, cj + py). */
 static void fe_cell(const or_sim* s, int ci, int cj, double K[4][4]) {
-  double x1c = 0.5 * (x1_node(s, ci) + x1_node(s, ci + 1));
-  double x2c = 0.5 * (x2_node(s, cj) + x2_node(s, cj + 1));
-  double m[4];
-  or_metric(s->c.alpha, or_r_of(s->c.alpha, x1c, x2c), x2c, m);
-  double g11 = m[0] * m[0] + m[1] * m[1], g22 = m[2] * m[2] + m[3] * m[3], g12 = m[0] * m[2] + m[1] * m[3];
-  double J = or_dOmega(s->c.alpha, x1c, x2c);
-  double a = J * g11 * s->h2 / s->h1, c = J * g22 * s->h1 / s->h2, b = J * g12;
-  for (int p = 0; p < 4; ++p)
-    for (int q = 0; q < 4; ++q) {
-      int px = p & 1, py = p >> 1, qx = q & 1, qy = q >> 1;
-      double sxp = px ? 1.0 : -1.0, syp = py ? 1.0 : -1.0, sxq = qx ? 1.0 : -1.0, syq = qy ? 1.0 : -1.0;
-      double fy = py == qy ? 1.0 / 3.0 : 1.0 / 6.0, fx = px == qx ? 1.0 / 3.0 : 1.0 / 6.0;
-      K[p][q] = a * sxp * sxq * fy + c * syp * syq * fx + b * 0.25 * (sxp * syq + sxq * syp);
+  /* 3 x 3 Gauss-Legendre points of the cell; in the two cells next to a pole
+   * the x2 points are placed in t = sqrt(distance to the pole), where J's
+   * sqrt(1 - x2^2) growth becomes smooth */
+  static const double gx[3] = {-0.7745966692414834, 0.0, 0.7745966692414834};
+  static const double gw[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+  double xa = x1_node(s, ci), xb = x1_node(s, ci + 1), ya = x2_node(s, cj), yb = x2_node(s, cj + 1);
+  memset(K, 0, sizeof(double) * 16);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double f1 = 0.5 * (gx[a] + 1.0), x1 = xa + f1 * (xb - xa);
+      double wq = 0.25 * gw[a] * gw[b] * (xb - xa) * (yb - ya);
+      double f2 = 0.5 * (gx[b] + 1.0), x2;
+      if (cj == 0) {          /* x2 = -1 + h2 t^2, dx2 = 2 h2 t dt */
+        x2 = ya + (yb - ya) * f2 * f2;
+        wq *= 2.0 * f2;
+        f2 = f2 * f2;
+      } else if (cj == s->c.n2 - 1) {  /* x2 = 1 - h2 t^2 */
+        double t = f2;
+        x2 = yb - (yb - ya) * t * t;
+        wq *= 2.0 * t;
+        f2 = 1.0 - t * t;
+      } else {
+        x2 = ya + f2 * (yb - ya);
+      }
+      double m[4];
+      or_metric(s->c.alpha, or_r_of(s->c.alpha, x1, x2), x2, m);
+      double g11 = m[0] * m[0] + m[1] * m[1], g22 = m[2] * m[2] + m[3] * m[3], g12 = m[0] * m[2] + m[1] * m[3];
+      double J = or_dOmega(s->c.alpha, x1, x2);
+      /* derivatives of the bilinear corner functions at (f1, f2) */
+      double d1[4], d2[4];
+      for (int p = 0; p < 4; ++p) {
+        int px = p & 1, py = p >> 1;
+        double sx = px ? 1.0 : -1.0, sy = py ? 1.0 : -1.0;
+        double ex = px ? f1 : 1.0 - f1, ey = py ? f2 : 1.0 - f2;
+        d1[p] = sx * ey / (xb - xa);
+        d2[p] = sy * ex / (yb - ya);
+      }
+      for (int p = 0; p < 4; ++p)
+        for (int q = 0; q < 4; ++q)
+          K[p][q] += wq * J * (g11 * d1[p] * d1[q] + g12 * (d1[p] * d2[q] + d2[p] * d1[q]) + g22 * d2[p] * d2[q]);
     }
 }
 

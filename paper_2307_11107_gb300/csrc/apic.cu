@@ -368,27 +368,50 @@ void build_volumes(const Inst& I, std::vector<double>& V) { volumes_t<double>(I,
 // node volume) with
 //   K_ab = int grad N_a . grad N_b dOmega = int J g^kl dN_a/dx_k dN_b/dx_l dx1 dx2,
 // g^kl = grad x_k . grad x_l (the chain rule of Eq. 2) and J = dOmega/(dx1 dx2)
-// (Eq. 5), both at the cell centre.  Cell (ci, cj), corner p = px + 2 py at
-// node (ci + px, cj + py); with s(0) = -1, s(1) = 1 and F = 1/3 on equal
-// corners' coordinates, 1/6 otherwise (products of the linear factors
-// integrated over a unit interval):
-//   K_pq = J g11 h2/h1 s(px) s(qx) F(py, qy) + J g22 h1/h2 s(py) s(qy) F(px, qx)
-//        + J g12 (s(px) s(qy) + s(qx) s(py)) / 4.
+// (Eq. 5).  Cell (ci, cj), corner p = px + 2 py at node (ci + px, cj + py),
+// integrated with 3 x 3 Gauss-Legendre points; in the two cells next to a
+// pole the x2 points are placed in t with x2 = pole -+ h2 t^2, where J's
+// sqrt(1 - x2^2) growth becomes smooth.
 template <class T>
 void fe_cell_h(const Inst& I, T alpha, int ci, int cj, T K[4][4]) {
-  const double x1c = 0.5 * (x1_node_h(I, ci) + x1_node_h(I, ci + 1));
-  const double x2c = 0.5 * (x2_node_h(I, cj) + x2_node_h(I, cj + 1));
-  const Metric<T> m = metric(alpha, radius(alpha, T(x1c), T(x2c)), T(x2c));
-  const T g11 = m.x1R * m.x1R + m.x1Z * m.x1Z, g22 = m.x2R * m.x2R + m.x2Z * m.x2Z;
-  const T g12 = m.x1R * m.x2R + m.x1Z * m.x2Z;
-  const T J = volume_density(alpha, T(x1c), T(x2c));
-  const T a = J * g11 * T(I.h2 / I.h1), c = J * g22 * T(I.h1 / I.h2), b = J * g12;
+  const double gx[3] = {-0.7745966692414834, 0.0, 0.7745966692414834};  // +-sqrt(3/5), 0
+  const double gw[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+  const double xa = x1_node_h(I, ci), xb = x1_node_h(I, ci + 1);
+  const double ya = x2_node_h(I, cj), yb = x2_node_h(I, cj + 1);
   for (int p = 0; p < 4; ++p)
-    for (int q = 0; q < 4; ++q) {
-      const int px = p & 1, py = p >> 1, qx = q & 1, qy = q >> 1;
-      const double sxp = px ? 1.0 : -1.0, syp = py ? 1.0 : -1.0, sxq = qx ? 1.0 : -1.0, syq = qy ? 1.0 : -1.0;
-      const double fy = py == qy ? 1.0 / 3.0 : 1.0 / 6.0, fx = px == qx ? 1.0 / 3.0 : 1.0 / 6.0;
-      K[p][q] = a * T(sxp * sxq * fy) + c * T(syp * syq * fx) + b * T(0.25 * (sxp * syq + sxq * syp));
+    for (int q = 0; q < 4; ++q) K[p][q] = T(0.0);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      const double f1 = 0.5 * (gx[a] + 1.0), x1 = xa + f1 * (xb - xa);
+      double wq = 0.25 * gw[a] * gw[b] * (xb - xa) * (yb - ya);
+      double f2 = 0.5 * (gx[b] + 1.0), x2;
+      if (cj == 0) {  // x2 = -1 + h2 t^2, dx2 = 2 h2 t dt
+        x2 = ya + (yb - ya) * f2 * f2;
+        wq *= 2.0 * f2;
+        f2 = f2 * f2;
+      } else if (cj == I.n2 - 1) {  // x2 = 1 - h2 t^2
+        const double t = f2;
+        x2 = yb - (yb - ya) * t * t;
+        wq *= 2.0 * t;
+        f2 = 1.0 - t * t;
+      } else {
+        x2 = ya + f2 * (yb - ya);
+      }
+      const Metric<T> m = metric(alpha, radius(alpha, T(x1), T(x2)), T(x2));
+      const T g11 = m.x1R * m.x1R + m.x1Z * m.x1Z, g22 = m.x2R * m.x2R + m.x2Z * m.x2Z;
+      const T g12 = m.x1R * m.x2R + m.x1Z * m.x2Z;
+      const T Jw = volume_density(alpha, T(x1), T(x2)) * T(wq);
+      double d1[4], d2[4];  // derivatives of the corner functions at (f1, f2)
+      for (int p = 0; p < 4; ++p) {
+        const int px = p & 1, py = p >> 1;
+        const double sx = px ? 1.0 : -1.0, sy = py ? 1.0 : -1.0;
+        const double ex = px ? f1 : 1.0 - f1, ey = py ? f2 : 1.0 - f2;
+        d1[p] = sx * ey / (xb - xa);
+        d2[p] = sy * ex / (yb - ya);
+      }
+      for (int p = 0; p < 4; ++p)
+        for (int q = 0; q < 4; ++q)
+          K[p][q] += Jw * (g11 * T(d1[p] * d1[q]) + g12 * T(d1[p] * d2[q] + d2[p] * d1[q]) + g22 * T(d2[p] * d2[q]));
     }
 }
 
