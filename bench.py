@@ -52,6 +52,8 @@ def parse():
                     help="batched48 only: the first N instances (smaller runs, e.g. under a profiler)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sort-interval", type=int, default=None,
+                    help="override the workload's sort interval (steps between particle sorts)")
     ap.add_argument("--autotune", action="store_true",
                     help="choose the sort interval with apic_autotune after the warm-up (untimed)")
     return ap.parse_args()
@@ -312,6 +314,9 @@ def main():
     import paper_2307_11107_gb300 as apic
     apic.build()
     cfgs = replica_configs(args.workload, args.particles, rank, max(4096, args.steps + args.warmup + 8), args.instances)
+    if args.sort_interval is not None:
+        for c in cfgs:
+            c["sort_interval"] = args.sort_interval
     cfg = cfgs[0]
     sim = apic.Sim(cfgs)
     for k, c in enumerate(cfgs):
