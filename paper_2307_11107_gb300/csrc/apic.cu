@@ -175,6 +175,7 @@ struct apic_sim {
   bool floating = false;              // some instance has an isolated grain (APIC_FLOATING)
   bool boltz = false;                 // some instance has Boltzmann electrons (APIC_BOLTZMANN)
   int newton = 0;                     // Newton iterations per solve (the largest of those instances)
+  double newton_eta = kNewtonEta;     // inexact-Newton reduction of every linear solve but the last
   size_t l2_persist = 0;              // bytes of L2 set aside for them (0: none)
   long long tab_total = 0;
   TanPtrs tan{};                      // sensitivity-window state (allocated on first use)
@@ -1086,6 +1087,7 @@ static int setup(apic_sim* S) {
       S->newton = std::max(S->newton, S->cfg[k].newton_iters > 0 ? S->cfg[k].newton_iters : 8);
     }
   if (S->boltz) d.diag0 = (double*)A(sizeof(double) * total_nodes);
+  if (const char* ne = std::getenv("APIC_NEWTON_ETA")) S->newton_eta = std::min(0.5, std::max(0.0, std::atof(ne)));
   S->phi_save = (double*)A(sizeof(double) * total_nodes);
   d.st64 = (double*)A(sizeof(double) * kSt * total_nodes);
   d.acc = (unsigned long long*)A(sizeof(unsigned long long) * 2 * total_nodes);
@@ -1405,7 +1407,7 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
     case 1:
       // Boltzmann electrons: newton Newton iterations, each a linear solve
       for (int k = 0; k < (S->boltz ? S->newton : 1); ++k) {
-        if (S->boltz) launch_newton(d, -1, k == S->newton - 1, s);
+        if (S->boltz) launch_newton(d, -1, k == S->newton - 1 ? 0.0 : S->newton_eta, s);
         if (S->coop > 0) {
           if (solve_coop<Real>(S, d, s, kBcrRho | kBcrFields) != cudaSuccess) return false;
           continue;
@@ -1813,7 +1815,7 @@ static int solve_impl(apic_sim* S, int inst, const double* rho, double* phi_out)
   launch_b_from_rho(d, inst, S->stream);
   if (I.flags & APIC_BOLTZMANN) {  // Newton from the current phi
     for (int k = 0; k < S->newton; ++k) {
-      launch_newton(d, inst, k == S->newton - 1, S->stream);
+      launch_newton(d, inst, k == S->newton - 1 ? 0.0 : S->newton_eta, S->stream);
       if (!solve_instance<Real>(S, inst)) return S->status;
     }
     launch_newton_end(d, S->stream);

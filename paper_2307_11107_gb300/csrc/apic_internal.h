@@ -12,7 +12,8 @@ constexpr int kNT = APIC_NT;
 constexpr int kNH = APIC_NH;
 // Inexact Newton (Boltzmann electrons): every Newton iteration but the last
 // solves its linear system only until the residual has fallen by this factor
-// (or below the tolerance); quadratic convergence makes up for it.
+// (or below the tolerance); quadratic convergence makes up for it.  The
+// environment knob APIC_NEWTON_ETA replaces it at creation.
 constexpr double kNewtonEta = 1e-3;
 constexpr int kMaxLevels = 12;
 constexpr int kMaxPop = 128;      // populations (instance x species) per batch
@@ -238,7 +239,7 @@ void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s);
 void launch_b_vacuum(const DevPtrs& d, int inst, cudaStream_t s);
 void launch_store_vacuum(const DevPtrs& d, int inst, cudaStream_t s);
 void launch_float_phi(const DevPtrs& d, cudaStream_t s);
-void launch_newton(const DevPtrs& d, int only, int last, cudaStream_t s);
+void launch_newton(const DevPtrs& d, int only, double eta, cudaStream_t s);
 void launch_newton_end(const DevPtrs& d, cudaStream_t s);
 
 // Block cyclic reduction (bcr.cu) of the finest-level system of every

@@ -111,15 +111,15 @@ __global__ void __launch_bounds__(256) k_float_phi(DevPtrs d) {
 // b = -rho_i rscale + (Dirichlet terms) + rscale exp(phi_k) (1 - phi_k); the
 // |b|^2 partials as k_rho, so that the BiCGSTAB solve that follows stops at
 // once when phi_k already satisfies the nonlinear equations to its
-// tolerance.  The solve of every iteration but the last (`last` = 0) may stop
-// once its residual has fallen by kNewtonEta (inexact Newton).  only >= 0:
-// that instance alone.
-__global__ void __launch_bounds__(256) k_newton(DevPtrs d, int only, int last) {
+// tolerance.  The solve may also stop once its residual has fallen by eta
+// (inexact Newton; eta = 0 for the last iteration).  only >= 0: that
+// instance alone.
+__global__ void __launch_bounds__(256) k_newton(DevPtrs d, int only, double eta) {
   __shared__ double sh[256];
   const int inst = blockIdx.y;
   const Inst& I = d.inst[inst];
   if (!(I.flags & APIC_BOLTZMANN) || (only >= 0 && inst != only)) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) d.sol[inst].eta2 = last ? 0.0 : kNewtonEta * kNewtonEta;
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.sol[inst].eta2 = eta * eta;
   double* dg = d.st64 + (long long)kSt * I.node_off + (long long)st_slot(0, 0) * I.nodes;
   double part = 0.0;
   for (long long nd = (long long)blockIdx.x * blockDim.x + threadIdx.x; nd < I.nodes;
@@ -249,8 +249,8 @@ void launch_b_from_rho(const DevPtrs& d, int inst, cudaStream_t s) { k_b_from_rh
 void launch_b_vacuum(const DevPtrs& d, int inst, cudaStream_t s) { k_b_vacuum<<<kRedBlocks, 256, 0, s>>>(d, inst); }
 void launch_store_vacuum(const DevPtrs& d, int inst, cudaStream_t s) { k_store_vacuum<<<kRedBlocks, 256, 0, s>>>(d, inst); }
 void launch_float_phi(const DevPtrs& d, cudaStream_t s) { k_float_phi<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d); }
-void launch_newton(const DevPtrs& d, int only, int last, cudaStream_t s) {
-  k_newton<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d, only, last);
+void launch_newton(const DevPtrs& d, int only, double eta, cudaStream_t s) {
+  k_newton<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d, only, eta);
 }
 void launch_newton_end(const DevPtrs& d, cudaStream_t s) { k_newton_end<<<dim3(kRedBlocks, d.n_inst), 256, 0, s>>>(d); }
 
