@@ -92,7 +92,9 @@ extern "C" {
                                 multigrid of the linear operator (the species given are the ions).  Forces the
                                 multigrid solver (one cooperative launch per Newton iteration for a single
                                 instance, per-phase kernels for a batch).  apic_solve_poisson solves the same
-                                nonlinear problem for the given ion density.  Not with APIC_NO_FIELD,
+                                nonlinear problem for the given ion density.  The grain collects the
+                                electrons' one-sided Maxwellian flux exp(phi_grain)/sqrt(2 pi) per unit area
+                                and time (history's current).  Not with APIC_NO_FIELD,
                                 APIC_FLOATING or apic_sensitivity (INVALID_ARG). */
 
 #define APIC_NT 7  /* tally components per (species, bin): hits, charge, p_R, p_Z, L_z, E_kin, E_kin + E_bind */

@@ -1098,6 +1098,12 @@ int or_step(or_sim* s, int n_steps) {
     memset(s->step_tally, 0, sizeof(s->step_tally));
     compact_push(s);
     if (!(s->c.flags & OR_NO_INJECT)) inject(s);
+    if (s->c.flags & OR_BOLTZMANN) {
+      /* Boltzmann electrons reach the grain as the one-sided flux of a
+       * Maxwellian of density n0 exp(phi_g) at the surface (Te = me = 1):
+       * exp(phi_g) sqrt(1 / 2 pi) per unit area and time, charge -1 each */
+      s->step_tally[0] -= exp(s->c.phi_g) * sqrt(1.0 / (2.0 * OR_PI)) * s->A_grain * s->c.dt;
+    }
     if (s->c.flags & OR_FLOATING) s->Qg += s->step_tally[0]; /* charge collected this step */
     record_history(s);
     s->step++;
@@ -1130,6 +1136,8 @@ or_sim* or_create(const or_config* cfg) {
   build_tables(s);
   if (!(cfg->flags & OR_NO_FIELD)) build_matrix(s);
   s->phig = cfg->phi_g;
+  /* an isolated grain's charge-restoring correction is a superposition,
+   * which the nonlinear Boltzmann problem does not allow */
   if (((cfg->flags & (OR_FLOATING | OR_BOLTZMANN)) && (cfg->flags & OR_NO_FIELD)) ||
       ((cfg->flags & OR_FLOATING) && (cfg->flags & OR_BOLTZMANN))) {
     or_destroy(s);

@@ -27,7 +27,8 @@ extern "C" {
 #define OR_CHORD 4       /* also absorb when the step's chord passes through the grain */
 #define OR_CHORD_SAMPLES 8 /* the chord is tested at s = k / OR_CHORD_SAMPLES, k = 1..7 */
 #define OR_FLOATING 8    /* isolated grain: its potential follows the charge it collects */
-#define OR_BOLTZMANN 16  /* electrons not simulated: n_e = exp(phi) in Eq. 6, solved by Newton */
+#define OR_BOLTZMANN 16  /* electrons not simulated: n_e = exp(phi) in Eq. 6, solved by Newton; the grain
+                            collects their Maxwellian flux exp(phi_g) sqrt(1/2pi) per unit area */
 #define OR_FE 32         /* conservative (bilinear finite-element) form of Eqs. 6-7 instead of Eq. 7's differences */
 
 #define OR_NT 7          /* tally components per bin */

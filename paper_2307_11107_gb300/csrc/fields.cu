@@ -205,6 +205,10 @@ __global__ void k_step_end(DevPtrs d) {
     res[s] = (double)(S.loaded + S.injected - S.absorbed - S.escaped - S.dropped);
   }
   double dt = I.dt;
+  // Boltzmann electrons reach the grain as the one-sided flux of a Maxwellian
+  // of density n0 exp(phi_g) at the surface (Te = me = 1): exp(phi_g)/sqrt(2 pi)
+  // per unit area and time, charge -1 each
+  if (I.flags & APIC_BOLTZMANN) T.tally[0] -= exp(I.phi_g) * (1.0 / sqrt(2.0 * kPi)) * I.A_grain * dt;
   double* h = d.hist + I.hist_off + (T.step % I.hist_cap) * kNH;
   h[0] = (double)(T.step + 1) * dt;
   h[1] = T.tally[0] / dt;

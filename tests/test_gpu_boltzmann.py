@@ -58,7 +58,8 @@ def test_single_step_fp64(apic):
     g, r = s.particles(0), o.particles(0)[0]
     assert g.shape == r.shape
     assert np.abs(g - r).max() < 1e-9
-    t = s.tallies()
+    t = s.tallies(history=True)
+    assert abs(t["history"][0, 1] - o.history()[0, 1]) < 1e-12 * abs(o.history()[0, 1])  # ions + electrons
     assert t["counts"][0]["absorbed"] == o.counts()[0]["absorbed"]
     assert t["counts"][0]["escaped"] == o.counts()[0]["escaped"]
     assert np.abs(t["bins"] - o.bins()).max() < 1e-9 * max(np.abs(o.bins()).max(), 1e-300)
@@ -123,3 +124,12 @@ def test_boltzmann_rejections(apic):
         s.sensitivity(2)
     with pytest.raises(apic.ApicError):
         apic.Sim(_cfg(floating=True))
+
+
+def test_boltzmann_electron_current(apic):
+    """With no ions, the grain current is the Boltzmann electrons' Maxwellian
+    flux alone: -4 pi exp(phi_g) / sqrt(2 pi) for the unit sphere."""
+    s = apic.Sim(_cfg(n1=32, n2=16, alpha=0.0, phi_g=-1.5))
+    s.step(2)
+    h = s.tallies(history=True)["history"]
+    assert np.allclose(h[:, 1], -4 * np.pi * np.exp(-1.5) / np.sqrt(2 * np.pi), rtol=1e-12, atol=0)

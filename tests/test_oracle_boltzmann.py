@@ -96,3 +96,15 @@ def test_boltzmann_rejects_field_free_and_isolated_grain():
         oracle.Sim(_cfg(32, 16, no_field=True))
     with pytest.raises(ValueError):
         oracle.Sim(_cfg(32, 16, floating=True))
+
+
+@pytest.mark.parametrize("phi_g", [-2.5, -0.5])
+def test_boltzmann_electron_current(phi_g):
+    """The grain collects the Boltzmann electrons' one-sided Maxwellian flux,
+    n0 exp(phi_g) sqrt(Te / 2 pi me) per unit area: with no ions the grain
+    current of a unit sphere (area 4 pi) is -4 pi exp(phi_g) / sqrt(2 pi) every
+    step."""
+    s = oracle.Sim(_cfg(32, 16, phi_g=phi_g))
+    s.step(3)
+    h = s.history()
+    assert np.allclose(h[:, 1], -4 * np.pi * np.exp(phi_g) / np.sqrt(2 * np.pi), rtol=1e-12, atol=0)
