@@ -65,6 +65,7 @@ def lib():
         L.or_newton_iterations.argtypes = [vp]
         L.or_apply_operator.argtypes = [vp, P(d), P(d)]
         L.or_gradients.argtypes = [vp]
+        L.or_set_phi.argtypes = [vp, P(d)]
         L.or_push_only.argtypes = [vp]
         L.or_count.restype = i64
         L.or_count.argtypes = [vp, C.c_int]
@@ -222,6 +223,11 @@ class Sim:
 
     def gradients(self):
         lib().or_gradients(self.h)
+
+    def set_phi(self, phi):
+        """Replace the potential by the given node values [n1+1][n2+1]."""
+        p = np.ascontiguousarray(phi, dtype=np.float64).reshape(self.n1 + 1, self.n2 + 1)
+        lib().or_set_phi(self.h, _dp(p))
 
     def count(self, sp):
         return lib().or_count(self.h, sp)

@@ -675,6 +675,14 @@ int or_solve_linear(or_sim* s, const double* rho, double* phi_out) {
   return 0;
 }
 
+/* Replace the simulation's potential by the caller's node values (pin tests:
+ * the gather, the push in a field and the surface quantities are then
+ * checked on potentials whose gradient and surface integrals are known in
+ * closed form). */
+void or_set_phi(or_sim* s, const double* phi) {
+  memcpy(s->phi, phi, sizeof(double) * (size_t)s->N1 * s->N2);
+}
+
 /* Node gradients dphi/dx1, dphi/dx2 (Sec. 2 after Eq. 10: derivatives taken
  * numerically at the grid nodes): central in the interior, one-sided second
  * order on the four edges. */

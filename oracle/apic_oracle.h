@@ -70,6 +70,7 @@ int or_solve(or_sim* s, const double* rho_or_null, double* phi_out);
 int or_solve_linear(or_sim* s, const double* rho, double* phi_out); /* Eqs. 6-7 with rho, any electron model */
 int or_newton_iterations(const or_sim* s);  /* Boltzmann electrons: Newton iterations of the last step's solve */
 void or_apply_operator(const or_sim* s, const double* phi, double* out); /* L phi per node (see apic_oracle.c) */
+void or_set_phi(or_sim* s, const double* phi); /* phi := caller values [n1+1][n2+1] (pin tests) */
 void or_gradients(or_sim* s);               /* G1, G2 from the current phi */
 int or_push_only(or_sim* s);                /* gather + push + absorb + escape, no inject */
 
