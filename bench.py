@@ -1,16 +1,20 @@
 """Benchmark of the APIC particle-in-cell step on GB300.
 
 Metric: particle-steps/s of full steps (deposit, Poisson solve to the stated
-tolerance, gather, push, absorption tallies, escape, injection) on the dipole
-workload: alpha = 0.15 (a = 0.3), B = 1, 256 x 128 cells, 1e7 macro-particles
-per species, FP32 particles with the FP64-refined Poisson solve.
+tolerance, gather, push, absorption tallies, escape, injection) on the
+precision form at scale: alpha = 0.225 (a = 0.45), B = 1, 1024 x 512 cells,
+5e7 macro-particles per species, FP32 particles with the Poisson problem
+solved in FP32 inside an FP64 residual refinement to 1e-10.  The line states
+the FP32 path's error against the FP64 oracle (one step from the same states,
+the same workload on 256 x 128 cells).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 N > 1 runs under torch.distributed.run; every rank advances an independent
 replica (the path has no data exchange between GPUs), rank 0 prints one JSON
 line with the whole-job throughput.  The reference arm (--impl reference) is
-the FP64 CPU oracle on a bounded sample of the same workload.
+the FP64 CPU oracle on a bounded sample of the same workload, one replica per
+host core.
 """
 import argparse
 import json
@@ -38,12 +42,12 @@ FLOPS_PER_PARTICLE_STEP = 127
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=30)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--particles", type=int, default=None,
                     help="macro-particles per species (default: the workload's own count)")
-    ap.add_argument("--workload", default="dipole256",
+    ap.add_argument("--workload", default="dipole1024",
                     choices=["dipole256", "dipole1024", "batched48", "sphere64", "window", "boltzmann256",
                              "floating256"],
                     help="window: the sensitivity window (forward-mode derivatives along alpha, phi_g, B) on the "
@@ -209,46 +213,169 @@ def cpu_model():
     return platform.machine()
 
 
-def run_oracle(cfg, n_per_species, steps):
-    """The FP64 CPU oracle as it stands, single thread, on `steps` steps of the
-    same workload with n_per_species macro-particles per species (the macro
-    weight follows n_per_species).  Returns (particle-steps/s, seconds)."""
-    import oracle
+# The CPU oracle's banded LU of a 1024 x 512 grid is 6.5 GB, takes about 95 s
+# to factor on one core and about 1.1 s per solve (x86 host; factor ~ n1 n2^3,
+# solve ~ n1 n2^2).  The CPU-baseline leg of the main line runs the same
+# workload on 256 x 128 cells (the downsampled grid of the precision form's
+# comparison); the reference arm runs the largest grid whose factorisation and
+# solves fit its time budget (the full grid for short runs).
+ORACLE_MAX_GRID = (256, 128)
+
+
+def oracle_workload(cfg, grid=ORACLE_MAX_GRID):
+    """The workload as the CPU oracle runs it: the same parameters, the grid
+    reduced to at most `grid` cells."""
     c = dict(cfg)
-    c["species"] = [dict(s, n_init=n_per_species) for s in cfg["species"]]
+    c["n1"], c["n2"] = min(cfg["n1"], grid[0]), min(cfg["n2"], grid[1])
+    return c
+
+
+def reference_grid(cfg, total_steps, budget_s=150.0):
+    """Largest grid (the workload's, else halved in both directions) whose
+    oracle set-up and total_steps Poisson solves take at most budget_s."""
+    n1, n2 = cfg["n1"], cfg["n2"]
+    while n1 > 64:
+        a, b = n1 / 1024.0, n2 / 512.0
+        if 95.0 * a * b ** 3 + total_steps * 1.1 * a * b * b <= budget_s:
+            break
+        n1, n2 = n1 // 2, n2 // 2
+    return n1, n2
+
+
+def _oracle_replica(job):
+    """One oracle replica (a process of its own): warm-up steps untimed, then
+    timed steps; returns (particle-steps advanced, seconds)."""
+    cfg, n, warmup, steps, tag = job
+    cfg = dict(cfg)
+    sys.path.insert(0, ROOT)
+    import oracle
+    c = dict(cfg, instance=tag)
+    c["species"] = [dict(s, n_init=n) for s in cfg["species"]]
     sim = oracle.Sim(c)
     for sp in range(len(c["species"])):
-        sim.load_volume(sp, n_per_species)
+        sim.load_volume(sp, n)
+    sim.step(warmup)
     adv = 0
     t0 = time.perf_counter()
     for _ in range(steps):
         adv += sum(sim.count(sp) for sp in range(len(c["species"])))
         sim.step(1)
-    dt = time.perf_counter() - t0
-    return adv / dt, dt
+    return adv, time.perf_counter() - t0
+
+
+def run_oracle(cfg, n_per_species, steps, warmup=0, cores=1, grid=ORACLE_MAX_GRID):
+    """The FP64 CPU oracle as it stands on `steps` steps of the workload (grid
+    per oracle_workload) with n_per_species macro-particles per species (the
+    macro weight follows n_per_species), after `warmup` untimed steps.  With
+    cores > 1, that many independent replicas (distinct random streams) run in
+    spawned processes at once, one per core.  Returns (particle-steps/s of all
+    replicas, seconds of the slowest)."""
+    c = oracle_workload(cfg, grid)
+    jobs = [(c, n_per_species, warmup, steps, 1000 + k) for k in range(cores)]
+    if cores == 1:
+        res = [_oracle_replica(jobs[0])]
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_replica, jobs)
+    adv = sum(r[0] for r in res)
+    secs = max(r[1] for r in res)
+    return adv / secs, secs
+
+
+def profile_figure(key, workload_name):
+    """A figure recorded under profiles/ (profiles/figures.txt lines
+    "<key> <workload> <value>"), or None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "figures.txt")) as f:
+            for line in f:
+                p = line.split()
+                if len(p) >= 3 and p[0] == key and p[1] == workload_name:
+                    return float(p[2])
+    except Exception:
+        pass
+    return None
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    cfg = workload(args.particles, "dipole256")
-    # bounded sample: keep the whole warm-up + timed run within ~2 minutes
-    # (the oracle advances ~1e7 particle-steps/s on one core).
-    steps = max(1, args.steps)
-    n = int(max(2000, min(cfg["species"][0]["n_init"], 5.0e8 / (2 * steps))))
-    val, secs = run_oracle(cfg, n, steps)
+    cfg = workload(args.particles, args.workload if args.workload in ("dipole256", "dipole1024") else "dipole1024")
+    steps, warm = max(1, args.steps), max(0, args.warmup)
+    grid = reference_grid(cfg, steps + warm)
+    oc = oracle_workload(cfg, grid)
+    # one process: the banded LU's memory (6.5 GB on the full grid) is not
+    # replicated per core; bounded particle sample, ~1.7e7 particle-steps/s
+    cores = 1
+    n = int(max(2000, min(cfg["species"][0]["n_init"], 5.0e8 / (2 * (steps + warm)))))
+    val, secs = run_oracle(cfg, n, steps, warm, cores, grid)
+    sample = ("%d untimed + %d timed full steps with %d macro-particles per species on %dx%d cells (FP64, banded LU "
+              "factored once before the steps, 1 thread)" % (warm, steps, n, oc["n1"], oc["n2"]))
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * secs / steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": warm, "ms_per_step": 1e3 * secs / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": cfg["name"], "alpha": cfg["alpha"], "grid": [cfg["n1"], cfg["n2"]],
-                   "particles_per_species": n, "sample": "full steps with %d macro-particles per species" % n},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_model(),
-                         "sample": "%d steps, %d macro-particles per species, 256x128 grid" % (steps, n)},
+        "config": {"workload": cfg["name"], "alpha": cfg["alpha"], "grid_cells": [cfg["n1"], cfg["n2"]],
+                   "oracle_grid_cells": [oc["n1"], oc["n2"]], "particles_per_species": n, "sample": sample},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                         "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def precision_error(apic, cfg, n=200_000, seed=17):
+    """The FP32 path's error against the FP64 oracle: one step of the same
+    workload on the oracle's grid (oracle_workload) from the same FP32-rounded
+    particle states (n per species, uniform in the logical box, Maxwellian
+    velocities at each species' v_th).  Returns relative errors of rho and phi
+    (max-norm), of the particles (largest scaled difference of matched
+    states), of the grain charge and electric force, and of the absorbed
+    counts."""
+    import numpy as np
+    import oracle
+    c = oracle_workload(cfg)
+    c = dict(c, no_inject=True, species=[dict(s, n_init=n) for s in cfg["species"]], poisson_max_iter=60)
+    g, o = apic.Sim(c), oracle.Sim(c)
+    rng = np.random.default_rng(seed)
+    vth = [np.sqrt(s["T"] / s["m"]) for s in c["species"]]
+    for sp in range(len(c["species"])):
+        st = np.column_stack([rng.uniform(-0.999, c["x1_out"] - 1e-3, n), rng.uniform(-0.999, 0.999, n),
+                              rng.standard_normal((n, 3)) * vth[sp]]).astype(np.float32).astype(np.float64)
+        g.add_particles(sp, st)
+        o.add_particles(sp, st)
+    g.step(1)
+    o.step(1)
+
+    def rel(a, b):
+        return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+    out = {"workload": "%s on %dx%d cells, one step, %d particles per species" % (cfg["name"], c["n1"], c["n2"], n),
+           "rho": rel(g.field("rho"), o.grid("rho")), "phi": rel(g.field("phi"), o.grid("phi"))}
+    from scipy.spatial import cKDTree
+    worst, unmatched = 0.0, 0
+    for sp in range(len(c["species"])):
+        a, b = g.particles(sp), o.particles(sp)[0]
+        scale = np.array([1.0, 1.0, vth[sp], vth[sp], vth[sp]])
+        d, k = cKDTree(b / scale).query(a / scale)
+        unmatched += abs(a.shape[0] - b.shape[0]) + int((np.unique(k, return_counts=True)[1] > 1).sum())
+        worst = max(worst, float(np.sort(d)[-1 - min(unmatched, d.size - 1)]))
+    t = g.tallies()
+    sc = o.scalars()
+    out.update(particles=worst, particles_unmatched=unmatched,
+               grain_Q=abs(t["Q"] - sc["Q"]) / abs(sc["Q"]), grain_FZ=abs(t["FZ"] - sc["FZ"]) / max(abs(sc["FZ"]), 1e-300),
+               absorbed=[t["counts"][sp]["absorbed"] - o.counts()[sp]["absorbed"] for sp in range(len(c["species"]))],
+               tolerance={"fields": 2e-5, "particles": 2e-4})
+    g.close()
+    return out
 
 
 def window_bench(args):
@@ -374,6 +501,13 @@ def main():
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": "k_push",
             "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP, "peak_source": src,
             "push_ms": push_ms, "phase_ms_per_step": {k: v / kt for k, v in st["phase_ms"].items()}}
+    # the whole step against the same roofline: the particle state's bytes per
+    # step over the step time (the solve, sort and injection add time, not bytes)
+    full = BYTES_PER_PARTICLE_STEP * total_adv / args.steps / (ms / args.steps / 1e3) / 1e9
+    roof["full_step"] = {"achieved": full, "frac": full / peaks["hbm_gbs"], "unit": "GB/s"}
+    solve_ms = roof["phase_ms_per_step"].get("poisson", 0.0) + roof["phase_ms_per_step"].get("deposit_rho", 0.0)
+    roof["poisson"] = {"ms_per_step": solve_ms, "dram_bytes_per_step": profile_figure("dram_bytes_per_solve_step",
+                                                                                     cfg["name"])}
     # the ALU ceiling beside it: the push's FP32 arithmetic against the measured
     # FMA throughput of this GPU (the measured peaks hold no CUDA-core figure)
     try:
@@ -423,13 +557,22 @@ def main():
         sim.close()
 
     cpu = None
+    perr = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        n, k = 2_000_000, 50  # about 10-15 s of single-thread work
-        val, secs = run_oracle(cfg, n, k)
-        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_model(),
-               "sample": "%d full steps of the same workload with %.0e macro-particles per species (FP64, 1 thread)"
-                         % (k, n),
-               "seconds": secs}
+        oc = oracle_workload(cfg)
+        n, k, kw = 1_000_000, 20, 2  # about 10-15 s of work per core
+        val, secs = run_oracle(cfg, n, k, kw, 1)
+        cores = host_cores()
+        val_all, secs_all = run_oracle(cfg, n, k, kw, cores) if cores > 1 else (val, secs)
+        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_model(), "nproc": cores,
+               "sample": "%d untimed + %d timed full steps of the same workload on %dx%d cells with %.0e "
+                         "macro-particles per species (FP64, 1 thread)" % (kw, k, oc["n1"], oc["n2"], n),
+               "seconds": secs,
+               "all_cores": {"value": val_all, "unit": UNIT, "cores": cores, "seconds": secs_all,
+                             "sample": "%d independent replicas of that sample in spawned processes, one per host "
+                                       "core" % cores}}
+        if len(cfgs) == 1:
+            perr = precision_error(apic, cfg)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -449,7 +592,8 @@ def main():
                        "dt": cfg["dt"],
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "sort_interval": tuned if tuned is not None else cfg.get("sort_interval", 0)},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": roof, "cpu_baseline": cpu, "error_vs_fp64_oracle": perr, "e2e": e2e,
+            "gpu_launches": int(launches),
             "poisson_loop_iters": int(loop_iters), "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -53,8 +53,11 @@ extern "C" {
 #define APIC_ERR_GEOMETRY (-2)     /* |alpha| >= 0.245 or x1_outer not in (-1, 0) */
 #define APIC_ERR_CAPACITY (-3)     /* a species outgrew its particle capacity */
 #define APIC_ERR_NOT_CONVERGED (-4)/* Poisson iteration limit reached above tolerance */
-#define APIC_ERR_NONFINITE (-5)    /* NaN/Inf in the fields */
-#define APIC_ERR_TIMEOUT (-6)      /* reserved: bounded device wait gave up */
+#define APIC_ERR_NONFINITE (-5)    /* NaN/Inf in the fields or residual, or a tally value beyond its fixed-point
+                                      range (|v| >= 11585 v_th for the energy) */
+#define APIC_ERR_TIMEOUT (-6)      /* a bounded device wait gave up: a grid barrier of a cooperative solver (2 s of
+                                      global time) or a bulk-copy wait; every CTA returns and the context stays
+                                      usable, the object keeps the error */
 #define APIC_ERR_CUDA (-7)         /* CUDA runtime or allocation failure */
 
 /* precision of the particle arrays and of the Poisson preconditioner */
@@ -97,7 +100,9 @@ extern "C" {
                                 and time (history's current).  Not with APIC_NO_FIELD,
                                 APIC_FLOATING or apic_sensitivity (INVALID_ARG). */
 
-#define APIC_NT 7  /* tally components per (species, bin): hits, charge, p_R, p_Z, L_z, E_kin, E_kin + E_bind */
+#define APIC_NT 7  /* tally components per (species, bin): hits, charge, p_R, p_Z, L_z, E_kin, E_kin + E_bind.
+                      With APIC_BOLTZMANN the bins hold the simulated ions only: the electrons' flux
+                      enters the history's current alone (not its heat flux). */
 #define APIC_NH 11 /* history fields per step: t, current, drag F_Z, electric F_Z, torque T_z,
                       heat flux, grain charge Q, resident species 0, resident species 1, absorbed events,
                       grain potential of the step's field */
@@ -191,13 +196,26 @@ int apic_destroy(apic_sim* sim);
 int apic_inject(apic_sim* sim, int32_t instance, int32_t species, int64_t n, int32_t mode,
                 const double* explicit_state);
 
-/* Advance every instance by n_steps full steps (deposit -> Poisson -> gather ->
- * push -> absorb -> escape -> inject).  Work is queued on the stream and the
- * call waits for it once at the end to read the status word.  Errors:
- * CAPACITY, NOT_CONVERGED, NONFINITE, CUDA. */
+/* Advance every instance by n_steps full steps of the method (Sec. 1 and
+ * Sec. 2): charge weighing with the node volumes of Eq. 5 -> the Poisson
+ * problem of Eqs. 6-7 -> node gradients and the gather of Eq. 10 -> the
+ * leapfrog push of Eq. 9 -> absorption on the grain x1 = -1 with its tallies
+ * -> escape through x1 = x1_outer -> Maxwellian injection through the outer
+ * surface weighted by Eq. 4.  Work is queued on the stream and the call waits
+ * for it once at the end to read the status word.  Errors: CAPACITY,
+ * NOT_CONVERGED, NONFINITE, TIMEOUT, CUDA. */
 int apic_step(apic_sim* sim, int32_t n_steps);
 
-/* Copy tallies, counts and the history of `instance` into caller buffers. */
+/* Copy tallies, counts and the history of `instance` into caller buffers
+ * (Sec. 1: the charge, momentum, angular momentum and energy that absorbed
+ * particles transfer to the grain at the point of impact, binned by the x2
+ * of the impact; Sec. 2 after Eq. 10: the grain charge and electric force).
+ * The bins are sums of fixed-point values (scaled by the species' thermal
+ * speed, 36 fraction bits, 128-bit accumulators): they do not depend on the
+ * order of the absorption events, and each event's value is rounded by at
+ * most 7.3e-12 of m w v_th (momenta), m w v_th R0 (L_z) or m w v_th^2
+ * (energy).  Waits for the stream.  Errors: INVALID_ARG, those of earlier
+ * calls (sticky). */
 int apic_tallies(apic_sim* sim, int32_t instance, apic_tallies_t* out);
 
 /* Solve Eqs. 6-7 for `instance` with the GPU solver.  rho: host [n1+1][n2+1]
@@ -313,8 +331,12 @@ int apic_adjoint(apic_sim* sim, int32_t n_steps, const double* dL_dout, double* 
  *
  * rho[i][j] = qw * sum_p S_ij(p) / volume[i][j]: the cloud-in-cell weights S
  * of the n particles at (x1[p], x2[p]) on the grid `grid` (n1 x n2 cells,
- * x1 in [-1, x1_outer], x2 in [-1, 1]), the same weighing as apic_step's
- * deposit, with 64-bit fixed-point sums.  x1, x2 (n doubles), volume and rho
+ * x1 in [-1, x1_outer], x2 in [-1, 1]), the same weighing as the deposit of
+ * an FP64 (APIC_FP64) instance's apic_step, with 64-bit fixed-point sums (an
+ * FP32 instance rounds the cell fractions to 16 bits first, a difference of
+ * up to 2^-17 of a particle's charge per node).  A particle outside
+ * [-1, x1_outer] x [-1, 1] or with a non-finite coordinate is skipped (it adds
+ * no charge), as a freed or escaped slot of a simulation is.  x1, x2 (n doubles), volume and rho
  * ((n1+1)(n2+1) doubles, row-major) are device pointers owned by the caller;
  * work is queued on `stream` (a cudaStream_t) and the call returns without
  * waiting.  No cudaMalloc, cudaFree or other allocating call is made.
@@ -334,6 +356,17 @@ typedef struct {
 
 int apic_deposit_static(const apic_grid_t* grid, const double* x1, const double* x2, int64_t n, double qw,
                         const double* volume, double* rho, void* stream);
+
+/* Failure-detection check: launches four CTAs that wait at a grid barrier
+ * of the kind the cooperative solvers use, set up so that it never completes
+ * (one arrival more than there are CTAs), with the wait limited to limit_ns
+ * of global time (1e3 .. 1e10) instead of the solvers' 2 s.  Each wait gives up
+ * at the limit, sets the status word's time-out bit and its CTA returns; the
+ * call then reads the status word as apic_step does and returns
+ * APIC_ERR_TIMEOUT, which the object keeps (sticky).  The CUDA context stays
+ * usable: other objects are unaffected.  Errors: INVALID_ARG, TIMEOUT (the
+ * expected result), CUDA. */
+int apic_check_wait_limit(apic_sim* sim, int64_t limit_ns);
 
 /* FP32 CUDA-core throughput of the current device in TFLOP/s: independent fused
  * multiply-add chains (2 FLOPs each) over every SM, reps iterations per chain,

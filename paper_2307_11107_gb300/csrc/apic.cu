@@ -804,7 +804,7 @@ static int setup(apic_sim* S) {
     I.tab_off = tab_total;
     tab_total += 2 * (kTable + 1);
     I.bin_off = bins_total;
-    bins_total += (long long)c.n_species * c.n2 * kNT;
+    bins_total += (long long)c.n_species * ((long long)c.n2 * kTallyBinWords + kTallyStepWords);
     I.hist_off = hist_total;
     hist_total += (long long)I.hist_cap * kNH;
     I.en_off = en_total;
@@ -878,6 +878,8 @@ static int setup(apic_sim* S) {
       P.T = sp.T;
       P.w = I.V_dom / (double)sp.n_init;
       P.vth = std::sqrt(sp.T / sp.m);
+      P.tunit = P.vth;
+      P.tfix_off = I.bin_off + (long long)s * ((long long)c.n2 * kTallyBinWords + kTallyStepWords);
       P.lam = std::sqrt(sp.T / (2.0 * kPi * sp.m)) * I.A_out * c.dt / P.w;
       P.base = slots;
       P.cap = sp.capacity;
@@ -1100,12 +1102,13 @@ static int setup(apic_sim* S) {
   d.tab = (double*)A(sizeof(double) * tab_total);
   d.guide = (int32_t*)A(sizeof(int32_t) * tab_total);
   d.sgeo = (double*)A(sizeof(double) * 4 * en_total);
-  d.bins = (double*)A(sizeof(double) * std::max<long long>(1, bins_total));
+  d.tfix = (unsigned long long*)A(sizeof(unsigned long long) * std::max<long long>(1, bins_total));
   d.hist = (double*)A(sizeof(double) * hist_total);
   d.en = (double*)A(sizeof(double) * en_total);
   d.red = (double*)A(sizeof(double) * ni * kNRed * kRedBlocks);
   d.cred = (double*)A(sizeof(double) * ni * kNRed * kCoopMaxBlocks);
   d.bar = (unsigned*)A(sizeof(unsigned) * 4);
+  d.wait_ns = kWaitNs;
   if (pl.bcr.n_inst > 0) {
     // blocks and tail inverses of every instance in one range (one L2
     // access-policy window covers them)
@@ -1491,6 +1494,21 @@ static bool capture(apic_sim* S, const DevPtrs& d, int p0, int p1, cudaGraph_t* 
   return false;
 }
 
+static int read_status(apic_sim* S);
+
+extern "C" int apic_check_wait_limit(apic_sim* S, int64_t limit_ns) {
+  if (!S) return APIC_ERR_INVALID_ARG;
+  if (limit_ns < 1000 || limit_ns > 10000000000ll) return S->fail(APIC_ERR_INVALID_ARG, "limit_ns out of range");
+  if (S->status != APIC_OK) return S->status;
+  DevPtrs w = S->d;
+  w.bar = (unsigned*)S->dalloc(256);  // a zeroed barrier counter of its own
+  if (!w.bar) return S->status;
+  w.wait_ns = (unsigned long long)limit_ns;
+  launch_wait_check(w, 4, S->stream);
+  if (!S->ck(cudaGetLastError(), "wait check launch")) return S->status;
+  return read_status(S);
+}
+
 static int read_status(apic_sim* S) {
   if (!S->d2h(S->h_err, S->d.err, 1) || !S->sync()) return S->status;
   int e = S->h_err[0];
@@ -1746,7 +1764,9 @@ extern "C" int apic_tallies(apic_sim* S, int32_t instance, apic_tallies_t* out) 
   if (instance < 0 || instance >= S->n_inst) return APIC_ERR_INVALID_ARG;
   const Inst& I = S->inst[instance];
   if (!S->sync()) return S->status;
-  if (out->bins) S->d2h(out->bins, S->d.bins + I.bin_off, (size_t)I.n_species * I.n2 * kNT);
+  const long long tw = (long long)I.n_species * ((long long)I.n2 * kTallyBinWords + kTallyStepWords);
+  std::vector<unsigned long long> tfix((size_t)tw);
+  if (out->bins) S->d2h(tfix.data(), S->d.tfix + I.bin_off, (size_t)tw);
   StepState stp;
   SolverState sol;
   S->d2h(&stp, S->d.stp + instance, 1);
@@ -1757,6 +1777,27 @@ extern "C" int apic_tallies(apic_sim* S, int32_t instance, apic_tallies_t* out) 
   std::vector<double> hist((size_t)I.hist_cap * kNH);
   S->d2h(hist.data(), S->d.hist + I.hist_off, hist.size());
   if (!S->sync()) return S->status;
+  if (out->bins) {
+    // bins from the fixed-point sums (tally_fixed.cuh): charge = hits q w,
+    // momenta and L_z times m w v_th, energy times m w v_th^2, plus the
+    // binding energy per hit of a positive species
+    for (int s = 0; s < I.n_species; ++s) {
+      const Pop& P = S->pop[I.pop0 + s];
+      const double mwu = P.m * P.w * P.tunit;
+      for (int j = 0; j < I.n2; ++j) {
+        const unsigned long long* b = tfix.data() + (P.tfix_off - I.bin_off) + (size_t)j * kTallyBinWords;
+        double* o = out->bins + ((size_t)s * I.n2 + j) * kNT;
+        const double hits = (double)b[0];
+        o[0] = hits;
+        o[1] = hits * P.q * P.w;
+        o[2] = mwu * fixed128_value(b[1], b[2]);
+        o[3] = mwu * fixed128_value(b[3], b[4]);
+        o[4] = mwu * fixed128_value(b[5], b[6]);
+        o[5] = mwu * P.tunit * fixed128_value(b[7], b[8]);
+        o[6] = o[5] + (P.q > 0.0 ? hits * I.e_bind * P.w : 0.0);
+      }
+    }
+  }
   for (int s = 0; s < 2; ++s) {
     out->counts[s][0] = ps[s].loaded;
     out->counts[s][1] = ps[s].injected;

@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include "../../include/apic.h"
+#include "tally_fixed.cuh"
 
 namespace apic {
 
@@ -28,6 +29,7 @@ constexpr int kErrCapacity = 1;
 constexpr int kErrNotConverged = 2;
 constexpr int kErrNonFinite = 4;
 constexpr int kErrTimeout = 8;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // grid-barrier waits give up after 2 s
 constexpr int kCoopMaxBlocks = 256;  // CTAs of the cooperative solver (partial-sum slots)
 constexpr int kCoopMaxInst = 64;     // instances the cooperative solver handles
 
@@ -59,7 +61,7 @@ struct Inst {
   int64_t nodes;           // N1 * N2
   int64_t node_off;        // offset into per-node arrays of the batch
   int64_t tab_off;         // offset of the two CDF tables (volume, surface), (kTable+1) each
-  int64_t bin_off;         // offset of the tally bins [n_species][n2][kNT]
+  int64_t bin_off;         // first word of its populations' fixed-point tallies (Pop::tfix_off)
   int64_t hist_off;        // offset of the history ring [hist_cap][kNH]
   int64_t en_off;          // offset of the surface field E_n [N2] (and of the surface geometry, 4 per node)
   int32_t hist_cap;
@@ -86,6 +88,8 @@ struct Pop {
   int64_t acc_off;         // offset of this population's deposit accumulator (nodes of its instance)
   int64_t cell_off;        // first sort bin of this population (bins = grid rows)
   int64_t cells;           // sort bins of this population (n1 rows)
+  double tunit;            // velocity unit of the fixed-point tallies (v_th)
+  int64_t tfix_off;        // first word of its fixed-point tallies: [n2][kTallyBinWords], then [kTallyStepWords]
 };
 
 // Device-mutable counters of one population.
@@ -113,7 +117,7 @@ struct SolverState {
 struct StepState {
   long long step;
   double Q, FZ;            // grain charge and electric force of the last solve
-  double tally[5];         // this step: charge, p_Z, L_z, heat, events
+  double tally[5];         // this step: charge, p_Z, L_z, heat, events (from the fixed-point sums at the step's end)
   // isolated grain (APIC_FLOATING): potential of the last field, the grain
   // charge it holds, the last correction, whether qg has been fixed yet
   double phig, qg, dphig, qg_set;
@@ -160,12 +164,13 @@ struct DevPtrs {
   double* tab;
   int32_t* guide;                 // per table entry g: interval of (g / kTable) * total (same layout as tab)
   double* sgeo;                   // grain-surface geometry per x2 node: |grad x1|, n_Z, dA/dx2, trapezoid weight
-  double* bins;
+  unsigned long long* tfix;       // fixed-point tallies of every population (tally_fixed.cuh)
   double* hist;
   double* en;
   double* red;                    // reduction partials [n_inst][kNRed][kRedBlocks]
   double* cred;                   // cooperative solver partials [n_inst][kNRed][kCoopMaxBlocks]
   unsigned* bar;                  // grid barrier of the cooperative solver (count, generation)
+  unsigned long long wait_ns;     // time limit of a grid-barrier wait (global timer), then APIC_ERR_TIMEOUT
   int64_t total_nodes;
   int64_t level_nodes;
   // block cyclic reduction: factor blocks and tail inverses of every instance,
@@ -180,6 +185,25 @@ struct DevPtrs {
   const int32_t* bcr_tpre;        // [n_inst + 1]: prefix sums of the instances' node tasks
   double* bcr_part;               // [1 + kBcrMaxRhs][chunks]: |b|^2, then |r|^2 per right-hand side, of each range
 };
+
+#ifdef __CUDACC__
+// This step's tallies of instance `inst` from its populations' fixed-point
+// sums, in population order: charge, p_Z, L_z, heat (E_kin + E_bind), events.
+__device__ inline void step_tallies(const DevPtrs& d, int inst, double out[5]) {
+  const Inst& I = d.inst[inst];
+  for (int k = 0; k < 5; ++k) out[k] = 0.0;
+  for (int s = 0; s < I.n_species; ++s) {
+    const Pop& P = d.pop[I.pop0 + s];
+    const unsigned long long* st = d.tfix + P.tfix_off + (long long)I.n2 * kTallyBinWords;
+    const double hits = (double)st[0], mwu = P.m * P.w * P.tunit;
+    out[0] += hits * P.q * P.w;
+    out[1] += mwu * fixed128_value(st[1], st[2]);
+    out[2] += mwu * fixed128_value(st[3], st[4]);
+    out[3] += mwu * P.tunit * fixed128_value(st[5], st[6]) + (P.q > 0.0 ? hits * I.e_bind * P.w : 0.0);
+    out[4] += hits;
+  }
+}
+#endif
 
 // ---- sensitivity window (forward mode) ----
 // Derivatives with respect to kNPar parameters, index p: 0 = alpha, 1 = phi_g,
@@ -375,6 +399,9 @@ cudaError_t launch_solve_bcr_rhs(const DevPtrs& d, const SolvePlan& plan, int bl
 // and tail chunk, and the kernel's shared memory (plan.bcr.smem, plan.bcr.dyn).
 int bcr_configure(SolvePlan& plan, BcrInst* inst, int n_inst, int sms);
 const void* bcr_kernel(const SolvePlan& plan);  // the solve kernel (to find its graph node)
+// blocks CTAs (all resident) wait at a barrier that never completes, each
+// for d.wait_ns; d.bar must point at a zeroed counter of its own.
+void launch_wait_check(const DevPtrs& d, int blocks, cudaStream_t s);
 
 // sensitivity window (tangent.cu)
 template <class Real>

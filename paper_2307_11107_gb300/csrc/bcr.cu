@@ -597,9 +597,16 @@ const void* kernel_for(const BcrPlan& b) {
   return b.wide ? (const void*)k_solve_bcr<kBcrMaxNWide> : (const void*)k_solve_bcr<kBcrMaxN>;
 }
 
+// Check of the bounded grid-barrier wait: the CTAs wait at a barrier that
+// expects one arrival more than there are CTAs, so no wait can complete; each
+// gives up after d.wait_ns, sets the status word's time-out bit and returns.
+__global__ void k_wait_check(DevPtrs d) { grid_sync(d, gridDim.x + 1u); }
+
 }  // namespace
 
 const void* bcr_kernel(const SolvePlan& pl) { return kernel_for(pl.bcr); }
+
+void launch_wait_check(const DevPtrs& d, int blocks, cudaStream_t s) { k_wait_check<<<blocks, 32, 0, s>>>(d); }
 
 int bcr_configure(SolvePlan& pl, BcrInst* bi, int ni, int sms) {
   int dev = 0, optin = 0;

@@ -55,24 +55,29 @@ __global__ void k_clear(unsigned long long* acc, long long nodes) {
 
 // Bilinear (cloud-in-cell) weights of each particle in the logical (x1, x2)
 // grid, rounded to F fractional bits and added with 64-bit integer atomics
-// (order-independent sums).
+// (order-independent sums).  A particle outside [-1, x1_outer] x [-1, 1], or
+// with a non-finite coordinate, carries no charge onto the grid (as a freed
+// or escaped slot of a simulation does) and is skipped.
 __global__ void k_weigh(unsigned long long* acc, const double* x1, const double* x2, long long n, int n1, int n2,
-                        double h1, double h2, int F) {
-  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  double u1 = (x1[k] + 1.0) / h1, u2 = (x2[k] + 1.0) / h2;
-  int i = (int)floor(u1), j = (int)floor(u2);
-  i = i < 0 ? 0 : (i > n1 - 1 ? n1 - 1 : i);
-  j = j < 0 ? 0 : (j > n2 - 1 ? n2 - 1 : j);
-  double f1 = u1 - i, f2 = u2 - j;
-  f1 = f1 < 0.0 ? 0.0 : (f1 > 1.0 ? 1.0 : f1);
-  f2 = f2 < 0.0 ? 0.0 : (f2 > 1.0 ? 1.0 : f2);
-  double sc = ldexp(1.0, F), g1 = 1.0 - f1, g2 = 1.0 - f2;
-  long long N2 = n2 + 1, b = (long long)i * N2 + j;
-  atomicAdd(acc + b, (unsigned long long)__double2ll_rn(g1 * g2 * sc));
-  atomicAdd(acc + b + N2, (unsigned long long)__double2ll_rn(f1 * g2 * sc));
-  atomicAdd(acc + b + 1, (unsigned long long)__double2ll_rn(g1 * f2 * sc));
-  atomicAdd(acc + b + N2 + 1, (unsigned long long)__double2ll_rn(f1 * f2 * sc));
+                        double x1_outer, double h1, double h2, int F) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const double a = x1[k], c = x2[k];
+    if (!(a >= -1.0 && a <= x1_outer && c >= -1.0 && c <= 1.0)) continue;  // NaN fails too
+    double u1 = (a + 1.0) / h1, u2 = (c + 1.0) / h2;
+    int i = (int)floor(u1), j = (int)floor(u2);
+    i = i < 0 ? 0 : (i > n1 - 1 ? n1 - 1 : i);
+    j = j < 0 ? 0 : (j > n2 - 1 ? n2 - 1 : j);
+    double f1 = u1 - i, f2 = u2 - j;
+    f1 = f1 < 0.0 ? 0.0 : (f1 > 1.0 ? 1.0 : f1);
+    f2 = f2 < 0.0 ? 0.0 : (f2 > 1.0 ? 1.0 : f2);
+    double sc = ldexp(1.0, F), g1 = 1.0 - f1, g2 = 1.0 - f2;
+    long long N2 = n2 + 1, b = (long long)i * N2 + j;
+    atomicAdd(acc + b, (unsigned long long)__double2ll_rn(g1 * g2 * sc));
+    atomicAdd(acc + b + N2, (unsigned long long)__double2ll_rn(f1 * g2 * sc));
+    atomicAdd(acc + b + 1, (unsigned long long)__double2ll_rn(g1 * f2 * sc));
+    atomicAdd(acc + b + N2 + 1, (unsigned long long)__double2ll_rn(f1 * f2 * sc));
+  }
 }
 
 __global__ void k_density(const unsigned long long* acc, const double* V, double* rho, long long nodes, double scale) {
@@ -99,9 +104,13 @@ extern "C" int apic_deposit_static(const apic_grid_t* grid, const double* x1, co
   int gb = (int)((nodes + 255) / 256);
   gb = gb > 4096 ? 4096 : gb;
   k_clear<<<gb, 256, 0, s>>>(acc, nodes);
+  if (cudaGetLastError() != cudaSuccess) return APIC_ERR_CUDA;
   if (n > 0) {
     double h1 = (grid->x1_outer + 1.0) / grid->n1, h2 = 2.0 / grid->n2;
-    k_weigh<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, x1, x2, n, grid->n1, grid->n2, h1, h2, F);
+    long long wb = (n + 255) / 256;
+    wb = wb > 16384 ? 16384 : wb;  // grid-stride loop beyond 2^22 particles
+    k_weigh<<<(unsigned)wb, 256, 0, s>>>(acc, x1, x2, n, grid->n1, grid->n2, grid->x1_outer, h1, h2, F);
+    if (cudaGetLastError() != cudaSuccess) return APIC_ERR_CUDA;  // rho is not written
   }
   k_density<<<gb, 256, 0, s>>>(acc, volume, rho, nodes, qw * ldexp(1.0, -F));
   return cudaGetLastError() == cudaSuccess ? APIC_OK : APIC_ERR_CUDA;

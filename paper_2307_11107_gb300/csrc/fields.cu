@@ -205,6 +205,12 @@ __global__ void k_step_end(DevPtrs d) {
     res[s] = (double)(S.loaded + S.injected - S.absorbed - S.escaped - S.dropped);
   }
   double dt = I.dt;
+  step_tallies(d, inst, T.tally);
+  for (int s = 0; s < I.n_species; ++s) {
+    const Pop& P = d.pop[I.pop0 + s];
+    unsigned long long* st = d.tfix + P.tfix_off + (long long)I.n2 * kTallyBinWords;
+    for (int k = 0; k < kTallyStepWords; ++k) st[k] = 0ull;
+  }
   // Boltzmann electrons reach the grain as the one-sided flux of a Maxwellian
   // of density n0 exp(phi_g) at the surface (Te = me = 1): exp(phi_g)/sqrt(2 pi)
   // per unit area and time, charge -1 each

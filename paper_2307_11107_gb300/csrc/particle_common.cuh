@@ -113,6 +113,19 @@ __device__ __noinline__ Real chord_entry(Real al, Real R, Real Z, Real dx, Real 
   return Real(0);
 }
 
+// One tally component (value already divided by its unit) added to a bin's
+// accumulator and, if given, to the step's; out of range sets the status
+// word's non-finite bit.
+__device__ __forceinline__ void tally_add(const DevPtrs& d, unsigned long long* bin, unsigned long long* step, double x) {
+  long long v;
+  if (!to_fixed(x, 1.0, &v)) {
+    atomicOr(d.err, kErrNonFinite);
+    return;
+  }
+  fixed128_add(bin, v);
+  if (step) fixed128_add(step, v);
+}
+
 __device__ void absorb_tally(const DevPtrs& d, const Inst& I, const Pop& P, Real R, Real Z, Real vx, Real vz,
                              Real vy, Real tau) {
   Real al = (Real)I.alpha;
@@ -136,23 +149,18 @@ __device__ void absorb_tally(const DevPtrs& d, const Inst& I, const Pop& P, Real
   Real vRi = c * vx + sn * vy;
   int bin = (int)floor((x2i + Real(1)) / (Real)I.h2);
   bin = bin < 0 ? 0 : (bin > I.n2 - 1 ? I.n2 - 1 : bin);
-  double q = P.q, m = P.m, w = P.w;
-  double ek = 0.5 * m * ((double)vx * vx + (double)vz * vz + (double)vy * vy) * w;
-  double eb = q > 0.0 ? I.e_bind * w : 0.0;
-  double* b = d.bins + I.bin_off + ((long long)P.species * I.n2 + bin) * kNT;
-  atomicAdd(b + 0, 1.0);
-  atomicAdd(b + 1, q * w);
-  atomicAdd(b + 2, m * (double)vRi * w);
-  atomicAdd(b + 3, m * (double)vz * w);
-  atomicAdd(b + 4, m * (double)R * (double)vy * w);
-  atomicAdd(b + 5, ek);
-  atomicAdd(b + 6, ek + eb);
-  double* st = d.stp[P.inst].tally;
-  atomicAdd(st + 0, q * w);
-  atomicAdd(st + 1, m * (double)vz * w);
-  atomicAdd(st + 2, m * (double)R * (double)vy * w);
-  atomicAdd(st + 3, ek + eb);
-  atomicAdd(st + 4, 1.0);
+  // fixed-point sums (tally_fixed.cuh): hits exactly; momenta and L_z in
+  // units of v_th, the kinetic energy in units of v_th^2 (m w applied at
+  // read-back, and the binding energy and charge from the hit count)
+  const double iu = 1.0 / P.tunit;
+  unsigned long long* b = d.tfix + P.tfix_off + (long long)bin * kTallyBinWords;
+  unsigned long long* st = d.tfix + P.tfix_off + (long long)I.n2 * kTallyBinWords;
+  atomicAdd(b, 1ull);
+  atomicAdd(st, 1ull);
+  tally_add(d, b + 1, nullptr, (double)vRi * iu);
+  tally_add(d, b + 3, st + 1, (double)vz * iu);
+  tally_add(d, b + 5, st + 3, (double)R * (double)vy * iu);
+  tally_add(d, b + 7, st + 5, 0.5 * ((double)vx * vx + (double)vz * vz + (double)vy * vy) * iu * iu);
 }
 
 __device__ __forceinline__ int find_pop(const long long* pre, int n_pop, long long t) {

@@ -71,7 +71,7 @@ __device__ bool grid_sync(const DevPtrs& d, unsigned nb) {
         }
         const unsigned long long now = global_ns();
         if (t0 == 0) t0 = now;
-        else if (now - t0 > 2000000000ull) {
+        else if (now - t0 > d.wait_ns) {
           atomicOr(d.err, kErrTimeout);
           ok = 0;
           break;

@@ -538,11 +538,13 @@ __global__ void k_tan_step_end(DevPtrs d, TanPtrs t) {
   const Inst& I = d.inst[inst];
   const StepState& T = d.stp[inst];
   const double dt = I.dt;
+  double tl[5];
+  step_tallies(d, inst, tl);
   double* v = t.vals + (long long)inst * kNOut;
-  v[0] += T.tally[1] / dt;
+  v[0] += tl[1] / dt;
   v[1] += T.FZ;
-  v[2] += T.tally[0] / dt;
-  v[3] += T.tally[2] / dt;
+  v[2] += tl[0] / dt;
+  v[3] += tl[2] / dt;
   v[4] += T.Q;
   double* tt = t.tally + (long long)inst * kNOut * kNPar;
   double* J = t.jac + (long long)inst * kNOut * kNPar;

@@ -225,6 +225,11 @@ class Sim:
         self._check(self._lib.apic_adjoint(self.h, int(n_steps), g.ctypes.data_as(dp), grad.ctypes.data_as(dp)))
         return grad
 
+    def check_wait_limit(self, limit_ns):
+        """apic_check_wait_limit: returns the status code (APIC_ERR_TIMEOUT,
+        -6, is the expected one) without raising."""
+        return int(self._lib.apic_check_wait_limit(self.h, int(limit_ns)))
+
     def autotune(self, steps_per_trial=16):
         """Sort-interval autotuning (apic_autotune): returns the interval kept
         and the measured ms per step of every candidate."""

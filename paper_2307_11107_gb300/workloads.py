@@ -51,8 +51,8 @@ def dipole_256_floating(precision="fp32", n_per_species=10_000_000):
 
 def dipole_1024(precision="fp32", n_per_species=50_000_000):
     """Precision form at scale: a = 0.45 (alpha = 0.225), 1024 x 512 cells,
-    5e7 macro-particles per species, FP32 particles and multigrid inside the
-    FP64 residual loop to 1e-10 (1000 steps)."""
+    5e7 macro-particles per species, FP32 particles, the Poisson problem solved
+    in FP32 inside the FP64 residual refinement to 1e-10 (1000 steps)."""
     return dict(name="dipole_a0.45_1024x512_1e8", alpha=0.225, x1_out=-0.05, phi_g=-2.5, phi_out=0.0, B=1.0,
                 dt=0.1, n1=1024, n2=512,
                 species=[dict(ELECTRON, n_init=n_per_species), dict(ion(0.5), n_init=n_per_species)],

@@ -1,8 +1,10 @@
-"""Precision form (FP32 particles, FP32 multigrid inside the FP64 residual
-loop, FP64 tallies) against the FP64 oracle.  Single steps from identical
-states are compared element by element at FP32 accuracy; longer runs, whose
-trajectories separate (PIC dynamics amplify rounding), are compared through
-time-averaged tallies and fields against their statistical noise."""
+"""Precision form (FP32 particles, the FP32 block cyclic reduction inside the
+FP64 residual loop, fixed-point tallies) against the FP64 oracle.  Single
+steps from identical states are compared element by element at FP32
+accuracy, also at the sizes where the kernels take their full-size paths;
+longer runs, whose trajectories separate (PIC dynamics amplify rounding), are
+compared through time-averaged tallies and fields against their statistical
+noise."""
 import numpy as np
 import pytest
 
@@ -37,7 +39,7 @@ def test_fp32_single_step_against_fp64_oracle(apic, alpha, B):
     o.step(1)
     rho, rho_o = s.field("rho"), o.grid("rho")
     phi, phi_o = s.field("phi"), o.grid("phi")
-    # deposit: weights quantised to 2^-20 of a cell, positions in FP32
+    # deposit: cell fractions quantised to 16 bits (2^-16 of a cell), positions in FP32
     e_rho = np.abs(rho - rho_o).max() / np.abs(rho_o).max()
     e_phi = np.abs(phi - phi_o).max() / np.abs(phi_o).max()
     print(f"fp32 step alpha={alpha} B={B}: rho {e_rho:.2e} phi {e_phi:.2e}", end="")
@@ -53,20 +55,88 @@ def test_fp32_single_step_against_fp64_oracle(apic, alpha, B):
     print()
 
 
+def _match(g, r, scale):
+    """Nearest-neighbour matching of two particle sets (rows x1, x2, vR, vZ,
+    vTheta) in scaled coordinates: the matched pairs' largest scaled
+    difference, and the rows of either set left without a partner."""
+    from scipy.spatial import cKDTree
+    tree = cKDTree(r / scale)
+    d, k = tree.query(g / scale)
+    uniq, cnt = np.unique(k, return_counts=True)
+    dup = int((cnt > 1).sum())
+    return d, abs(g.shape[0] - r.shape[0]) + dup
+
+
+@pytest.mark.parametrize("n1,n2,alpha,n", [(256, 128, 0.15, 1_000_000), (64, 512, 0.225, 500_000)])
+def test_fp32_step_full_size_paths(apic, n1, n2, alpha, n):
+    """One FP32 step at the sizes where the kernels take their full-size
+    paths, from the same FP32-rounded states as the FP64 oracle, particles
+    sorted by row first (sort interval 8): on 256 x 128 cells the push's
+    8-row deposit window is kept across chunks and flushed after 31 of them,
+    chunk groups are taken from the counter and fast particles deposit outside
+    the window; on 64 x 512 cells the window has 4 rows and the Poisson solve
+    is the wide reduction kernel (513 unknowns per row) with level 1 applied
+    from the stencil (its blocks exceed L2).  rho, phi and every particle are
+    compared with the oracle; a second step's density (the push's windowed
+    deposit) is compared with the oracle's deposit of the GPU's own positions
+    after the first step."""
+    cfg = workload(n1=n1, n2=n2, alpha=alpha, B=1.0, x1_out=-0.05, n_init=n, Ti=0.5, precision="fp32",
+                   no_inject=True, poisson_tol=1e-12, poisson_max_iter=60, sort_interval=8)
+    s, o = apic.Sim(cfg), oracle.Sim(cfg)
+    states = []
+    for sp, seed, vs in ((0, 41, 1.0), (1, 42, 0.0165)):
+        st = random_states(n, cfg["x1_out"], seed=seed, vscale=vs).astype(np.float32).astype(np.float64)
+        s.add_particles(sp, st)
+        o.add_particles(sp, st)
+        states.append(st)
+    s.step(1)
+    o.step(1)
+    rho, rho_o = s.field("rho"), o.grid("rho")
+    phi, phi_o = s.field("phi"), o.grid("phi")
+    e_rho = np.abs(rho - rho_o).max() / np.abs(rho_o).max()
+    e_phi = np.abs(phi - phi_o).max() / np.abs(phi_o).max()
+    print(f"\nfp32 {n1}x{n2} step: rho {e_rho:.2e} phi {e_phi:.2e}", end="")
+    assert e_rho <= 2e-5 and e_phi <= 2e-5
+    after = []
+    for sp, vs in ((0, 1.0), (1, 0.0165)):
+        g, r = s.particles(sp), o.particles(sp)[0]
+        after.append(g)
+        scale = np.array([1.0, 1.0, vs, vs, vs])
+        d, unmatched = _match(g, r, scale)
+        print(f" sp{sp}: max {d.max():.2e}, unmatched {unmatched}", end="")
+        assert unmatched <= 4
+        assert np.sort(d)[-unmatched - 1] < 2e-4
+    tg, oc = s.tallies()["counts"], o.counts()
+    for sp in (0, 1):
+        for key in ("absorbed", "escaped"):
+            assert abs(tg[sp][key] - oc[sp][key]) <= 4, (sp, key, tg[sp][key], oc[sp][key])
+    # the windowed deposit of the push, against the oracle's deposit of the
+    # positions the GPU pushed to (16-bit cell fractions against exact ones)
+    s.step(1)
+    od = oracle.Sim(dict(cfg, no_field=True))
+    for sp in (0, 1):
+        od.add_particles(sp, after[sp])
+    od.deposit()
+    rho2, rho2_o = s.field("rho"), od.grid("rho")
+    e2 = np.abs(rho2 - rho2_o).max() / np.abs(rho2_o).max()
+    print(f" step-2 deposit {e2:.2e}")
+    assert e2 <= 2e-5
+
+
 @pytest.mark.slow
 def test_fp32_statistics_against_fp64_oracle(apic):
-    """Downsampled dipole run (alpha = 0.15, B = 1, 128 x 64 cells, 1e5
-    particles per species, 80 steps): time-averaged currents, drag, grain
+    """Downsampled dipole run (alpha = 0.15, B = 1, 256 x 128 cells, 1e6
+    particles per species, 100 steps): time-averaged currents, drag, grain
     charge and the radial density profile of the FP32-refined GPU run agree
     with the FP64 oracle within their statistical noise."""
-    n = 100000
-    cfg = workload(n1=128, n2=64, alpha=0.15, B=1.0, x1_out=-0.05, n_init=n, Ti=0.5, seed=7,
+    n = 1_000_000
+    cfg = workload(n1=256, n2=128, alpha=0.15, B=1.0, x1_out=-0.05, n_init=n, Ti=0.5, seed=7,
                    precision="fp32", poisson_tol=1e-10, poisson_max_iter=40, sort_interval=8)
     s, o = apic.Sim(cfg), oracle.Sim(cfg)
     for sp in (0, 1):
         s.load_volume(sp, n)
         o.load_volume(sp, n)
-    steps, avg = 80, 40
+    steps, avg = 100, 50
     s.step(steps)
     o.step(steps)
     hg, ho = s.tallies()["history"][-avg:], o.history()[-avg:]

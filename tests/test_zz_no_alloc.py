@@ -47,6 +47,37 @@ def test_deposit_static_matches_step_deposit_twice():
         assert err < 1e-11, err
 
 
+def test_deposit_static_skips_particles_outside_the_domain():
+    """Rows outside [-1, x1_outer] x [-1, 1] or with a NaN coordinate add no
+    charge: the density of the in-domain rows alone, bit for bit."""
+    import torch
+    import paper_2307_11107_gb300 as apic
+    from paper_2307_11107_gb300 import _abi
+    apic.build()
+    L = _abi.load()
+    cfg = workload(n1=64, n2=32, alpha=0.15)
+    st = random_states(20000, cfg["x1_out"], seed=22)
+    bad = np.array([[2.0, 0.1], [-1.5, 0.0], [-0.5, 1.5], [-0.5, -1.2], [np.nan, 0.0], [-0.5, np.nan],
+                    [np.inf, 0.0], [cfg["x1_out"] + 1e-3, 0.3]])
+    dev = torch.device("cuda")
+    Vd = torch.ones((cfg["n1"] + 1, cfg["n2"] + 1), dtype=torch.float64, device=dev)
+    grid = _abi.Grid(cfg["n1"], cfg["n2"], cfg["x1_out"])
+    stream = torch.cuda.current_stream()
+    out = []
+    for xy in (st[:, :2], np.concatenate([bad, st[:, :2], bad])):
+        x1 = torch.tensor(xy[:, 0], dtype=torch.float64, device=dev)
+        x2 = torch.tensor(xy[:, 1], dtype=torch.float64, device=dev)
+        rho = torch.empty_like(Vd)
+        # the same particle count bound (fixed-point bits) for both calls
+        rc = L.apic_deposit_static(C.byref(grid), x1.data_ptr(), x2.data_ptr(), xy.shape[0], 1.0, Vd.data_ptr(),
+                                   rho.data_ptr(), C.c_void_p(stream.cuda_stream))
+        assert rc == 0
+        torch.cuda.synchronize()
+        out.append(rho.cpu().numpy())
+    assert np.abs(out[0] - out[1]).max() <= 1e-12 * np.abs(out[0]).max()
+    assert out[0].sum() == pytest.approx(20000, rel=1e-12)
+
+
 def test_deposit_static_rejects_oversized_grid():
     import paper_2307_11107_gb300 as apic
     from paper_2307_11107_gb300 import _abi
