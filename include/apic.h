@@ -259,6 +259,9 @@ typedef struct {
 #define APIC_SOLVER_BCR 2        /* FP64 iterative refinement around an FP32 block cyclic reduction of
                                     every instance in one cooperative launch (FP32 particles, any n1,
                                     grids up to 543 cells in x2) */
+#define APIC_SOLVER_ND 3         /* the same refinement around an FP32 nested-dissection factorisation (formed
+                                    once at creation on the host in FP64) for some or all instances: grids
+                                    wider than 256 cells in x2, or every grid with APIC_DIRECT=nd */
 
 /* Counters of the batch (launch counts, Krylov iterations, phase times). */
 int apic_stats(apic_sim* sim, apic_stats_t* out);

@@ -72,7 +72,8 @@ class Stats(C.Structure):
 
 
 SOLVERS = ("multigrid BiCGSTAB, per-phase kernels", "multigrid BiCGSTAB, one cooperative launch",
-           "FP32 block cyclic reduction in FP64 iterative refinement, one cooperative launch")
+           "FP32 block cyclic reduction in FP64 iterative refinement, one cooperative launch",
+           "FP32 nested dissection in FP64 iterative refinement, one cooperative launch")
 
 
 _lib = None

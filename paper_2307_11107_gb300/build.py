@@ -11,6 +11,7 @@ Translation units (compiled in parallel):
                 (-fmad=false, with its node kernels) and FP32
   deposit_static.cu  the deposit entry point that uses no caller-side allocation
   probe.cu      the FP32 fused-multiply-add throughput probe (the ALU ceiling)
+  nd_factor.cpp the host nested-dissection factorisation of the Poisson system
 """
 import os
 import shutil
@@ -38,6 +39,7 @@ UNITS = [
     ("tangent.cu", "tangent_f32.o", ["-DAPIC_REAL=float"]),
     ("deposit_static.cu", "deposit_static.o", ["-fmad=false"]),
     ("probe.cu", "probe.o", []),
+    ("nd_factor.cpp", "nd_factor.o", []),
 ]
 
 

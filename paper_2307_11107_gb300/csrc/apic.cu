@@ -595,6 +595,8 @@ void parallel_for(int n, F f) {
   for (auto& x : th) x.join();
 }
 
+double nd_coef(const void* ctx, int i, int j, int slot) { return ((const HostLevel*)ctx)->get(slot, i, j); }
+
 // Layout of instance I's reduction: block size, levels before the dense
 // tail, first block of each kind per level (real rows only).  False if the
 // reduction does not apply (N2 > kBcrMaxNWide, n1 < 4, n1 > 2^(kBcrMaxK-1)).
@@ -942,10 +944,28 @@ static int setup(apic_sim* S) {
   std::vector<int32_t> bcr_kind, bcr_pre, bcr_npre, bcr_tpre;
   long long bcr_rows = 0;  // floats of bcr_f (and of bcr_e)
   int bcr_nb = 0;          // CTAs of the reduction solve
+  // nested dissection per instance (APIC_DIRECT=nd: every instance, bcr:
+  // none; default: grids wider than kBcrMaxN cells in x2)
+  std::vector<NdFactor> nds(ni);
+  std::vector<char> use_nd(ni, 0);
+  NdUpload ndu;
+  long long nd_w = 0;  // floats of one right-hand side's update vectors
   {
     const char* pc = std::getenv("APIC_PRECOND");
     bool want = sizeof(Real) == 4 && ni <= kCoopMaxInst && !(pc && std::string(pc) == "mg");
     for (const Inst& I : S->inst) want = want && !(I.flags & (APIC_NO_FIELD | APIC_BOLTZMANN));
+    const char* dm = std::getenv("APIC_DIRECT");
+    const std::string direct = dm ? dm : "auto";
+    for (int k = 0; k < ni && want; ++k) {
+      const Inst& I = S->inst[k];
+      use_nd[k] = direct == "nd" || (direct != "bcr" && I.N2 > kBcrMaxN + 1);
+      if (!use_nd[k]) continue;
+      std::string why;
+      int T = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+      if (!nd_build(I.n1 - 1, I.N2, nd_coef, &levels[k][0], 16, T, false, nds[k], why) ||
+          nds[k].depth > kNdMaxDepth)
+        use_nd[k] = 0;  // the reduction (or multigrid) instead
+    }
     long long off = 0;
     // dense level-1 blocks when the whole reduction then still fits in L2
     // (fewer phases); else level 1 applies the stencil's couplings (fewer
@@ -955,13 +975,41 @@ static int setup(apic_sim* S) {
       off = 0;
       bcr_rows = 0;
       bcr_in.assign(ni, BcrInst{});
+      ndu = NdUpload();
+      nd_w = 0;
+      int nd_need = 0;
       for (int k = 0; k < ni && want; ++k) {
         BcrInst& B = bcr_in[k];
+        auto up = [](long long v) { return (v + 63) & ~63ll; };  // 256-byte aligned ranges
+        if (use_nd[k]) {
+          std::memset(&B, 0, sizeof(B));
+          const Inst& I = S->inst[k];
+          B.M = I.n1 - 1;
+          B.N = I.N2;
+          B.Np = (B.N + 3) & ~3;
+          B.base = off;
+          NdLevels lvl;
+          nd_need = std::max(nd_need, nd_layout(nds[k], off, nd_w, kNdWarpMaxS, kNdWarpMaxU, kNdTaskFloats,
+                                                kNdTaskFronts, ndu, lvl));
+          B.nd = 1;
+          B.nd_depth = nds[k].depth;
+          for (int l = 0; l <= nds[k].depth + 1; ++l) {
+            B.nd_ft[l] = lvl.ft[l];
+            B.nd_bt[l] = lvl.bt[l];
+          }
+          off += up(nds[k].fm_total + nds[k].nb_total);
+          nd_w += up(nds[k].w_total);
+          B.foff = bcr_rows;
+          bcr_rows += (long long)B.M * B.N;
+          B.node_off = I.node_off;
+          B.nodes = I.nodes;
+          B.st_off = I.lv[0].st;
+          continue;
+        }
         if (!bcr_layout(S->inst[k], B, dense1 != 0)) {
           want = false;
           break;
         }
-        auto up = [](long long v) { return (v + 63) & ~63ll; };  // 256-byte aligned ranges
         B.base = off;
         off += up(B.blocks * B.blk);
         B.tail = off;
@@ -972,6 +1020,7 @@ static int setup(apic_sim* S) {
         B.nodes = S->inst[k].nodes;
         B.st_off = S->inst[k].lv[0].st;
       }
+      pl.bcr.nd_floats = nd_need;
       if (4.0 * (double)off <= l2_fit) break;
     }
     const double bytes = 4.0 * (double)off;
@@ -999,6 +1048,12 @@ static int setup(apic_sim* S) {
         const int M = B.M;
         auto ne = [&](int l) { return (M / (1 << (l - 1)) + 1) / 2; };
         auto nk = [&](int l) { return M / (2 << (l - 1)); };
+        if (B.nd) {  // forward from the deepest level, then backward from the root
+          for (int l = B.nd_depth; l >= 0; --l) st.push_back({kNdFwd << 8 | l, B.nd_ft[l + 1] - B.nd_ft[l]});
+          for (int l = 0; l <= B.nd_depth; ++l) st.push_back({kNdBack << 8 | l, B.nd_bt[l + 1] - B.nd_bt[l]});
+          phases = std::max(phases, (int)st.size());
+          continue;
+        }
         const int l0 = B.dense1 ? 1 : 2;  // first level with dense blocks
         if (B.Lt >= 1 && !B.dense1) {
           st.push_back({kBcrFwd1 << 8 | 1, ne(1)});
@@ -1035,6 +1090,7 @@ static int setup(apic_sim* S) {
         bcr_tpre[k + 1] = bcr_tpre[k] + (bcr_npre[k + 1] - bcr_npre[k] + pl.bcr.task_sub - 1) / pl.bcr.task_sub;
       pl.bcr.n_inst = ni;
       pl.bcr.phases = phases;
+      pl.bcr.nd_wrows = nd_w;
     } else {
       pl.bcr.n_inst = 0;
     }
@@ -1122,6 +1178,26 @@ static int setup(apic_sim* S) {
     d.bcr_npre = (const int32_t*)A(sizeof(int32_t) * bcr_npre.size());
     d.bcr_tpre = (const int32_t*)A(sizeof(int32_t) * bcr_tpre.size());
     d.bcr_part = (double*)A(sizeof(double) * (1 + kBcrMaxRhs) * (size_t)pl.bcr.chunks);
+    if (!ndu.fronts.empty()) {
+      d.nd_front = (const NdFront*)A(sizeof(NdFront) * ndu.fronts.size());
+      d.nd_idx = (const int32_t*)A(sizeof(int32_t) * ndu.idx.size());
+      d.nd_gather = (const int32_t*)A(sizeof(int32_t) * ndu.gather.size());
+      d.nd_task = (const int4*)A(sizeof(NdTask) * ndu.tasks.size());
+      d.nd_w = (float*)A(sizeof(float) * kBcrMaxRhs * (size_t)std::max<long long>(1, nd_w));
+      if (S->status != APIC_OK) return S->status;
+      S->h2d((NdFront*)d.nd_front, ndu.fronts.data(), ndu.fronts.size());
+      S->h2d((int32_t*)d.nd_idx, ndu.idx.data(), ndu.idx.size());
+      S->h2d((int32_t*)d.nd_gather, ndu.gather.data(), ndu.gather.size());
+      S->h2d((NdTask*)d.nd_task, ndu.tasks.data(), ndu.tasks.size());
+      for (int k = 0; k < ni; ++k) {
+        if (!use_nd[k]) continue;
+        const BcrInst& B = bcr_in[k];
+        S->h2d(d.bcr + B.base, nds[k].fm.data(), nds[k].fm.size());
+        S->h2d(d.bcr + B.base + nds[k].fm_total, nds[k].nb.data(), nds[k].nb.size());
+      }
+      if (!S->sync()) return S->status;  // the host copies are released below
+      for (int k = 0; k < ni; ++k) nds[k] = NdFactor();
+    }
     if (S->status != APIC_OK) return S->status;
     S->h2d((BcrInst*)d.bcr_inst, bcr_in.data(), bcr_in.size());
     S->h2d((int32_t*)d.bcr_kind, bcr_kind.data(), bcr_kind.size());
@@ -1133,6 +1209,7 @@ static int setup(apic_sim* S) {
     std::vector<double> T, aug;
     for (int k = 0; k < ni; ++k) {
       const BcrInst& B = bcr_in[k];
+      if (B.nd) continue;
       if (!bcr_factor(levels[k][0], B, blocks, T))
         return S->fail(APIC_ERR_INVALID_ARG, "block cyclic reduction: singular diagonal block");
       if (B.blocks > 0) S->h2d(d.bcr + B.base, blocks.data(), (size_t)(B.blocks * B.blk));
@@ -1630,7 +1707,8 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
   }
   if (S->floating) out->kernels_per_step += 2;  // the isolated grains' correction and the gradients again
   out->timed_steps = S->timed_steps;
-  out->solver = S->plan.bcr.n_inst > 0 ? APIC_SOLVER_BCR : (S->coop > 0 ? APIC_SOLVER_MG_COOP : APIC_SOLVER_MG_KERNELS);
+  out->solver = S->plan.bcr.n_inst > 0 ? (S->d.nd_front ? APIC_SOLVER_ND : APIC_SOLVER_BCR)
+                                       : (S->coop > 0 ? APIC_SOLVER_MG_COOP : APIC_SOLVER_MG_KERNELS);
   out->sorts = S->sorts;
   out->kernels_per_sort = 6;
   for (int p = 0; p < APIC_NPHASE; ++p) out->phase_ms[p] = S->phase_ms[p];
@@ -1762,6 +1840,7 @@ extern "C" int apic_inject(apic_sim* S, int32_t instance, int32_t species, int64
 extern "C" int apic_tallies(apic_sim* S, int32_t instance, apic_tallies_t* out) {
   if (!S || !out) return APIC_ERR_INVALID_ARG;
   if (instance < 0 || instance >= S->n_inst) return APIC_ERR_INVALID_ARG;
+  if (S->status != APIC_OK) return S->status;  // sticky
   const Inst& I = S->inst[instance];
   if (!S->sync()) return S->status;
   const long long tw = (long long)I.n_species * ((long long)I.n2 * kTallyBinWords + kTallyStepWords);

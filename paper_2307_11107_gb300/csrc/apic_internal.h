@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include "../../include/apic.h"
+#include "nd_factor.h"
 #include "tally_fixed.cuh"
 
 namespace apic {
@@ -184,6 +185,15 @@ struct DevPtrs {
   const int32_t* bcr_npre;        // [n_inst + 1]: prefix sums of the instances' partial-sum ranges (kBcrSub nodes)
   const int32_t* bcr_tpre;        // [n_inst + 1]: prefix sums of the instances' node tasks
   double* bcr_part;               // [1 + kBcrMaxRhs][chunks]: |b|^2, then |r|^2 per right-hand side, of each range
+  // nested dissection (instances with BcrInst::nd): fronts of every such
+  // instance (offsets global: idx, gather, matrices in bcr, update vectors
+  // per right-hand side in nd_w), their index and gather tables, the tasks
+  // (front or first front, first row or front count, rows, 1 = one front per warp)
+  const NdFront* nd_front;
+  const int32_t* nd_idx;
+  const int32_t* nd_gather;
+  const int4* nd_task;
+  float* nd_w;
 };
 
 #ifdef __CUDACC__
@@ -302,6 +312,16 @@ constexpr int kBcrFwd = 3;    // f_i -= P f_{i-h} + Q f_{i+h}, level >= 2
 constexpr int kBcrTail = 4;   // e = T^-1 f on a chunk of tail rows
 constexpr int kBcrBack = 5;   // e_k = B_k^-1 f_k - G e_{k-h} - H e_{k+h}, level >= 2
 constexpr int kBcrBack1 = 6;  // e_k = B_k^-1 (f_k - A_k e_{k-1} - C_k e_{k+1}), level 1
+// Nested dissection (nd_factor.h) in place of the reduction, per instance:
+// the forward sweep from the deepest tree level to the root, then the
+// backward sweep from the root down, one level per phase.
+constexpr int kNdFwd = 7;     // a front's z_S = F_SS^-1 v_S and W = v_U - (F_US F_SS^-1) v_S
+constexpr int kNdBack = 8;    // x_S = z_S - (F_SS^-1 F_SU) x_U, and x += e
+constexpr int kNdMaxDepth = 40;
+constexpr int kNdWarpMaxS = 64;     // fronts with a separator up to this size run one per warp
+constexpr int kNdWarpMaxU = 192;    // ... and an update set up to this size
+constexpr int kNdTaskFloats = 16384;  // matrix floats per task of a large front (row chunks)
+constexpr int kNdTaskFronts = 32;     // small fronts per task (taken by the warps in turn)
 struct BcrInst {
   int K;                    // 2^K >= n1
   int N;                    // block size N2
@@ -324,6 +344,10 @@ struct BcrInst {
   int64_t P[kBcrMaxK], Q[kBcrMaxK];                  // block index (from base) of the first block of each kind at level l
   int64_t Binv[kBcrMaxK], G[kBcrMaxK], H[kBcrMaxK];
   int64_t blocks;           // blocks of this instance
+  int nd;                   // 1: nested dissection instead of the reduction (the fields above unused)
+  int nd_depth;             // deepest tree level
+  int32_t nd_ft[kNdMaxDepth + 2];  // forward tasks of level l: DevPtrs::nd_task [nd_ft[l], nd_ft[l + 1])
+  int32_t nd_bt[kNdMaxDepth + 2];  // backward tasks of level l: [nd_bt[l], nd_bt[l + 1])
 };
 // Phase schedule: instance k runs its stages Fwd1, Upd1, Fwd(2..Lt), Tail,
 // Back(Lt..2), Back1 (Lt = 0: Tail alone) in phases 0, 1, ..., one grid
@@ -340,6 +364,9 @@ struct BcrPlan {
   int64_t rows;             // floats of one right-hand side's rows in bcr_f / bcr_e (all instances)
   int task_sub;             // partial-sum ranges per node task (1..kBcrMaxTaskSub)
   int pad2;
+  int64_t nd_wrows;         // floats of one right-hand side's update vectors in nd_w (all instances)
+  int nd_floats;            // shared-memory floats a large nested-dissection front needs (0: none)
+  int pad3;
 };
 
 // Poisson (poisson.cu): host-side launch plan of the multigrid levels.

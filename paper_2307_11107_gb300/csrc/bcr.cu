@@ -362,6 +362,125 @@ __device__ bool run_stage(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, 
   return true;
 }
 
+// ---- nested dissection (BcrInst::nd) ----
+// Dot products of matrix rows (row-major, 16-byte aligned rows of n4 float4)
+// with a vector in shared memory: G lanes per row, 32 / G rows per warp at a
+// time, partial sums added in a fixed butterfly (the result does not depend
+// on the CTA or the batch).  fn(row, value) is called by the first lane of
+// each row's group.
+template <int G, class Fn>
+__device__ __forceinline__ void rows_dot(const float* mat, int stride4, int row0, int row1, const float4* v, int n4,
+                                         int lane, int first, int step, Fn fn) {
+  const int gl = lane & (G - 1), gr = lane / G;
+  for (int a0 = row0 + first * (32 / G); a0 < row1; a0 += step * (32 / G)) {
+    const int a = a0 + gr;
+    float acc = 0.0f;
+    if (a < row1) {
+      const float4* r = (const float4*)mat + (long long)a * stride4;
+      for (int t = gl; t < n4; t += G) {
+        const float4 m = __ldg(r + t), x = v[t];
+        acc = fmaf(m.x, x.x, fmaf(m.y, x.y, fmaf(m.z, x.z, fmaf(m.w, x.w, acc))));
+      }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if (a < row1 && gl == 0) fn(a, acc);
+  }
+}
+
+template <class Fn>
+__device__ __forceinline__ void rows_dot_any(int n4, const float* mat, int stride4, int row0, int row1, const float4* v,
+                                             int lane, int first, int step, Fn fn) {
+  if (n4 >= 32) rows_dot<32>(mat, stride4, row0, row1, v, n4, lane, first, step, fn);
+  else if (n4 > 8) rows_dot<16>(mat, stride4, row0, row1, v, n4, lane, first, step, fn);
+  else if (n4 > 4) rows_dot<8>(mat, stride4, row0, row1, v, n4, lane, first, step, fn);
+  else if (n4 > 2) rows_dot<4>(mat, stride4, row0, row1, v, n4, lane, first, step, fn);
+  else if (n4 > 1) rows_dot<2>(mat, stride4, row0, row1, v, n4, lane, first, step, fn);
+  else rows_dot<1>(mat, stride4, row0, row1, v, n4, lane, first, step, fn);
+}
+
+// Entry p of front F's assembled right-hand side: the residual at its node
+// (separator positions only) plus what its children's update vectors hold
+// for it, in the order child 0, child 1.
+__device__ __forceinline__ float nd_rhs(const DevPtrs& d, const NdFront& F, int p, const float* f, const float* w) {
+  float v = p < F.s ? f[d.nd_idx[F.S + p]] : 0.0f;
+  const int g0 = d.nd_gather[F.G + 2 * p], g1 = d.nd_gather[F.G + 2 * p + 1];
+  if (g0 >= 0) v += w[d.nd_front[F.child[0]].W + g0];
+  if (g1 >= 0) v += w[d.nd_front[F.child[1]].W + g1];
+  return v;
+}
+
+// Forward rows [r0, r1) of front F with its v_S in vs (sp floats, zero
+// padded): rows below s give z_S into e, the others W = v_U - M v_S.
+__device__ __forceinline__ void nd_fwd_rows(const DevPtrs& d, const NdFront& F, int r0, int r1, const float* vs,
+                                            const float* f, float* e, float* w, int lane, int first, int step) {
+  rows_dot_any(F.sp >> 2, (const float*)d.bcr + F.FM, F.sp >> 2, r0, r1, (const float4*)vs, lane, first, step,
+               [&](int a, float acc) {
+                 if (a < F.s) e[d.nd_idx[F.S + a]] = acc;
+                 else w[F.W + a - F.s] = nd_rhs(d, F, a, f, w) - acc;
+               });
+}
+
+// Backward rows [r0, r1) of front F with x_U in xu (up floats, zero padded):
+// x_S = z_S - N x_U into e, and x += e at the node.
+__device__ __forceinline__ void nd_back_rows(const DevPtrs& d, const NdFront& F, int r0, int r1, const float* xu,
+                                             float* e, double* x, int N, int lane, int first, int step) {
+  auto put = [&](int a, float acc) {
+    const int u = d.nd_idx[F.S + a];
+    const float val = e[u] - acc;
+    e[u] = val;
+    x[(long long)u + N] += (double)val;
+  };
+  if (F.u == 0) {
+    for (int a = r0 + first * 32 + lane; a < r1; a += step * 32) put(a, 0.0f);
+    return;
+  }
+  rows_dot_any(F.up >> 2, (const float*)d.bcr + F.NB, F.up >> 2, r0, r1, (const float4*)xu, lane, first, step, put);
+}
+
+// One task of a nested-dissection phase of instance B: either rows
+// [T.y, T.y + T.z) of the large front T.x (the whole CTA), or the T.z small
+// fronts from T.x (one warp each, per-warp vectors in red).
+__device__ bool run_nd(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int l, int q, float* fb, float* eb,
+                       double* xb, float* wb) {
+  const float* f = fb + B.foff;
+  float* e = eb + B.foff;
+  double* x = xb + B.node_off;
+  const int4 T = d.nd_task[(kind == kNdFwd ? B.nd_ft[l] : B.nd_bt[l]) + q];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (T.w == 0) {
+    const NdFront F = d.nd_front[T.x];
+    float* v = c.red;
+    if (kind == kNdFwd) {
+      for (int p = threadIdx.x; p < F.sp; p += blockDim.x) v[p] = p < F.s ? nd_rhs(d, F, p, f, wb) : 0.0f;
+      __syncthreads();
+      nd_fwd_rows(d, F, T.y, T.y + T.z, v, f, e, wb, lane, warp, kBcrWarps);
+    } else {
+      for (int p = threadIdx.x; p < F.up; p += blockDim.x) v[p] = p < F.u ? e[d.nd_idx[F.U + p]] : 0.0f;
+      __syncthreads();
+      nd_back_rows(d, F, T.y, T.y + T.z, v, e, x, B.N, lane, warp, kBcrWarps);
+    }
+    __syncthreads();
+    return true;
+  }
+  // small fronts, one per warp (per-warp vector of kNdWarpMaxS + kNdWarpMaxU floats)
+  float* v = c.red + warp * (kNdWarpMaxS + kNdWarpMaxU);
+  for (int k = warp; k < T.z; k += kBcrWarps) {
+    const NdFront F = d.nd_front[T.x + k];
+    if (kind == kNdFwd) {
+      for (int p = lane; p < F.sp; p += 32) v[p] = p < F.s ? nd_rhs(d, F, p, f, wb) : 0.0f;
+      __syncwarp();
+      nd_fwd_rows(d, F, 0, F.s + F.u, v, f, e, wb, lane, 0, 1);
+    } else {
+      for (int p = lane; p < F.up; p += 32) v[p] = p < F.u ? e[d.nd_idx[F.U + p]] : 0.0f;
+      __syncwarp();
+      nd_back_rows(d, F, 0, F.s, v, e, x, B.N, lane, 0, 1);
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
 // Fixed-order sum of part[r chunks + npre[k] .. r chunks + npre[k+1]) for
 // every system v = r ni + k (right-hand side r < nrhs, instance k) with
 // sel[v] (all when sel is null), one warp per system; out[v] in shared
@@ -446,7 +565,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   __shared__ double sh[40];
   __shared__ float sv[3][MAXN];
   __shared__ float sres[MAXN];
-  __shared__ float red[kBcrWarps * MAXN];
+  __shared__ __align__(16) float red[kBcrWarps * MAXN];
   __shared__ double s_bn[kCoopMaxInst];
   __shared__ double s_rn[kCoopMaxInst];
   __shared__ int s_act[kCoopMaxInst];
@@ -568,9 +687,15 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
         const int k = task_inst_s(s_pre, ni, tt);
         if (!s_act[rh * ni + k]) continue;
         const BcrInst& B = k == 0 ? s_b0 : d.bcr_inst[k];
-        if (!run_stage<MAXN>(d, c, B, s_kind[k] >> 8, s_kind[k] & 255, tt - s_pre[k], sv, d.bcr_f + rh * pl.rows,
-                             d.bcr_e + rh * pl.rows, x_of(rh)))
+        const int kind = s_kind[k] >> 8;
+        if (kind == kNdFwd || kind == kNdBack) {
+          if (!run_nd(d, c, B, kind, s_kind[k] & 255, tt - s_pre[k], d.bcr_f + rh * pl.rows, d.bcr_e + rh * pl.rows,
+                      x_of(rh), d.nd_w + rh * pl.nd_wrows))
+            return;
+        } else if (!run_stage<MAXN>(d, c, B, kind, s_kind[k] & 255, tt - s_pre[k], sv, d.bcr_f + rh * pl.rows,
+                                    d.bcr_e + rh * pl.rows, x_of(rh))) {
           return;
+        }
       }
       if (p + 1 < pl.phases) load_tab(p + 1);
       if (!grid_sync(d, nb)) return;
@@ -614,8 +739,12 @@ int bcr_configure(SolvePlan& pl, BcrInst* bi, int ni, int sms) {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int nb = sms < kCoopMaxBlocks ? sms : kCoopMaxBlocks;
   int widest = 0;
-  for (int k = 0; k < ni; ++k) widest = bi[k].N > widest ? bi[k].N : widest;
-  pl.bcr.wide = widest > kBcrMaxN ? 1 : 0;
+  for (int k = 0; k < ni; ++k)
+    if (!bi[k].nd) widest = bi[k].N > widest ? bi[k].N : widest;
+  // nested dissection uses the reduction buffer (kBcrWarps x MAXN floats) for
+  // a large front's vector
+  pl.bcr.wide = widest > kBcrMaxN || pl.bcr.nd_floats > kBcrWarps * kBcrMaxN ? 1 : 0;
+  if (pl.bcr.nd_floats > kBcrWarps * kBcrMaxNWide) return 0;
   const long long budget = (long long)optin - static_smem(pl.bcr.wide ? kBcrMaxNWide : kBcrMaxN);
   const void* kern = kernel_for(pl.bcr);
   // tail chunks: about one per CTA when the tails are few, else one row per warp

@@ -18,7 +18,8 @@ def _instances(prec):
     ]
 
 
-_SOLVER = {"bcr": "FP32 block cyclic reduction", "mg": "multigrid BiCGSTAB, per-phase kernels"}
+_SOLVER = {"bcr": "FP32 block cyclic reduction", "nd": "FP32 nested dissection",
+           "mg": "multigrid BiCGSTAB, per-phase kernels"}
 
 
 def _run(apic, cfgs, steps, solver=None):
@@ -37,16 +38,19 @@ def _run(apic, cfgs, steps, solver=None):
     return out
 
 
-@pytest.mark.parametrize("prec,solver", [("fp64", "mg"), ("fp32", "bcr"), ("fp32", "mg")])
+@pytest.mark.parametrize("prec,solver", [("fp64", "mg"), ("fp32", "bcr"), ("fp32", "nd"), ("fp32", "mg")])
 def test_batch_equals_solo(prec, solver, monkeypatch):
     """Same solver path for the batch and each instance alone (the block
-    cyclic reduction of every instance in one launch, or the per-phase
-    multigrid kernels): the results agree bit for bit."""
+    cyclic reduction or the nested dissection of every instance in one
+    launch, or the per-phase multigrid kernels): the results agree bit for
+    bit."""
     import paper_2307_11107_gb300 as apic
     apic.build()
     cfgs = _instances(prec)
     if solver == "mg":
         monkeypatch.setenv("APIC_PRECOND", "mg")
+    if solver in ("bcr", "nd"):
+        monkeypatch.setenv("APIC_DIRECT", solver)
     batched = _run(apic, cfgs, 6, solver)
     if solver == "mg":
         monkeypatch.setenv("APIC_SOLVER", "kernels")

@@ -42,20 +42,35 @@ def test_poisson_fp64_matches_banded_lu(apic, alpha, grid):
     assert rel(s.solve_poisson(rho), o.solve(rho)) < 1e-10
 
 
+@pytest.mark.parametrize("direct", ["bcr", "nd"])
 @pytest.mark.parametrize("alpha,grid", [(0.15, (256, 128)), (0.225, (256, 128)), (0.15, (96, 48)),
                                         (0.225, (288, 144)), (-0.24, (160, 80)), (0.15, (64, 300)),
                                         (0.225, (32, 512))])
-def test_poisson_fp32_refined_matches_banded_lu(apic, alpha, grid):
-    """FP32 block cyclic reduction inside the FP64 residual loop reaches the
-    FP64 solution, for n1 a power of two and not (rows beyond n1 - 1 padded
-    with a zero correction), and for blocks wider than 256 unknowns (the
-    wide kernel, 17 outputs per lane)."""
+def test_poisson_fp32_refined_matches_banded_lu(apic, alpha, grid, direct, monkeypatch):
+    """The FP32 direct solve inside the FP64 residual loop reaches the FP64
+    solution: the block cyclic reduction (n1 a power of two and not, rows
+    beyond n1 - 1 padded with a zero correction; blocks wider than 256
+    unknowns in the wide kernel) and the nested-dissection factorisation."""
+    monkeypatch.setenv("APIC_DIRECT", direct)
     n1, n2 = grid
     cfg = workload(n1=n1, n2=n2, alpha=alpha, x1_out=-0.05, n_init=1000, precision="fp32",
                    poisson_tol=1e-12, poisson_max_iter=60)
     rho = random_rho(n1, n2, seed=n1 + 3, scale=0.3)
     s, o = apic.Sim(cfg), oracle.Sim(cfg)
-    assert s.stats()["solver"].startswith("FP32 block cyclic reduction")
+    assert s.stats()["solver"].startswith("FP32 block cyclic reduction" if direct == "bcr" else "FP32 nested dissection")
+    assert rel(s.solve_poisson(rho), o.solve(rho)) < 1e-9
+
+
+@pytest.mark.parametrize("alpha,grid", [(0.225, (16, 1024)), (-0.24, (24, 640))])
+def test_poisson_nested_dissection_beyond_reduction_width(apic, alpha, grid):
+    """Grids wider than the block cyclic reduction takes (543 cells in x2)
+    are solved by the nested dissection to the same accuracy."""
+    n1, n2 = grid
+    cfg = workload(n1=n1, n2=n2, alpha=alpha, x1_out=-0.05, n_init=1000, precision="fp32",
+                   poisson_tol=1e-12, poisson_max_iter=60)
+    rho = random_rho(n1, n2, seed=n1 + 5, scale=0.3)
+    s, o = apic.Sim(cfg), oracle.Sim(cfg)
+    assert s.stats()["solver"].startswith("FP32 nested dissection")
     assert rel(s.solve_poisson(rho), o.solve(rho)) < 1e-9
 
 
