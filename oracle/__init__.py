@@ -84,6 +84,9 @@ def lib():
         L.or_tape_get.argtypes = [vp, vp, P(i64), P(i64)]
         L.or_tape_set.argtypes = [vp, vp, i64, P(i64), i64]
         L.or_tape_status.argtypes = [vp]
+        L.or_tape_ix_get.restype = i64
+        L.or_tape_ix_get.argtypes = [vp, vp]
+        L.or_tape_ix_set.argtypes = [vp, vp, i64]
         _lib = L
     return _lib
 
@@ -285,21 +288,27 @@ class Sim:
         lib().or_tape_mode(self.h, int(mode))
 
     def tape(self):
-        """(status bytes, injection counts) recorded so far."""
+        """(status bytes, injection counts, cells and table intervals) recorded so far."""
         n_nk = C.c_int64()
         n = lib().or_tape_get(self.h, None, None, C.byref(n_nk))
         st = np.zeros(max(n, 1), dtype=np.uint8)
         nk = np.zeros(max(n_nk.value, 1), dtype=np.int64)
         lib().or_tape_get(self.h, st.ctypes.data_as(C.c_void_p), nk.ctypes.data_as(C.POINTER(C.c_int64)),
                           C.byref(n_nk))
-        return st[:n].copy(), nk[: n_nk.value].copy()
+        ni = lib().or_tape_ix_get(self.h, None)
+        ix = np.zeros(max(ni, 1), dtype=np.int32)
+        lib().or_tape_ix_get(self.h, ix.ctypes.data_as(C.c_void_p))
+        return st[:n].copy(), nk[: n_nk.value].copy(), ix[:ni].copy()
 
     def set_tape(self, tape):
-        st, nk = (np.ascontiguousarray(a) for a in tape)
+        st, nk = (np.ascontiguousarray(a) for a in tape[:2])
         st = st.astype(np.uint8)
         nk = nk.astype(np.int64)
         lib().or_tape_set(self.h, st.ctypes.data_as(C.c_void_p), st.size,
                           nk.ctypes.data_as(C.POINTER(C.c_int64)), nk.size)
+        if len(tape) > 2:
+            ix = np.ascontiguousarray(tape[2], dtype=np.int32)
+            lib().or_tape_ix_set(self.h, ix.ctypes.data_as(C.c_void_p), ix.size)
 
     def tape_ok(self):
         return lib().or_tape_status(self.h) == 0

@@ -227,6 +227,10 @@ struct or_sim {
   int64_t tape_n, tape_cap, tape_pos;
   int64_t* tape_nk;
   int64_t tape_nk_n, tape_nk_cap, tape_nk_pos;
+  /* cells and table intervals: every locate (packed i (n2+1) + j) and every
+   * injection's table interval, in the order they are taken */
+  int32_t* tape_ix;
+  int64_t tape_ix_n, tape_ix_cap, tape_ix_pos;
 };
 
 /* Decision of one particle update or injection draw under the tape: the
@@ -242,6 +246,24 @@ static int tape_status(or_sim* s, int natural) {
   }
   if (s->tape_mode == OR_TAPE_REPLAY) {
     if (s->tape_pos < s->tape_n) return s->tape_st[s->tape_pos++];
+    s->tape_short = 1;
+  }
+  return natural;
+}
+
+/* An integer choice (a particle's cell, a table interval) under the tape:
+ * record mode stores the natural one, replay returns the recorded one. */
+static int tape_int(or_sim* s, int natural) {
+  if (s->tape_mode == OR_TAPE_RECORD) {
+    if (s->tape_ix_n == s->tape_ix_cap) {
+      s->tape_ix_cap = s->tape_ix_cap ? 2 * s->tape_ix_cap : 65536;
+      s->tape_ix = (int32_t*)realloc(s->tape_ix, sizeof(int32_t) * (size_t)s->tape_ix_cap);
+    }
+    s->tape_ix[s->tape_ix_n++] = natural;
+    return natural;
+  }
+  if (s->tape_mode == OR_TAPE_REPLAY) {
+    if (s->tape_ix_pos < s->tape_ix_n) return s->tape_ix[s->tape_ix_pos++];
     s->tape_short = 1;
   }
   return natural;
@@ -336,19 +358,24 @@ static void build_tables(or_sim* s) {
   s->A_grain = ag;
 }
 
-/* Inverse CDF with linear interpolation inside the table interval. */
-static double sample_table(const double* cdf, double u) {
+/* Inverse CDF with linear interpolation inside the table interval (under a
+ * decision tape the interval is recorded or replayed, the interpolation
+ * follows the parameters). */
+static double sample_table_in(or_sim* s, const double* cdf, double u) {
   double t = u * cdf[TABLE_M];
   int lo = 0, hi = TABLE_M;
   while (hi - lo > 1) {
     int mid = (lo + hi) / 2;
     if (cdf[mid] <= t) lo = mid; else hi = mid;
   }
+  if (s) lo = tape_int(s, lo);
   double ht = 2.0 / TABLE_M;
   double d = cdf[lo + 1] - cdf[lo];
   double f = d > 0.0 ? (t - cdf[lo]) / d : 0.5;
   return -1.0 + lo * ht + f * ht;
 }
+
+static double sample_table(const double* cdf, double u) { return sample_table_in(NULL, cdf, u); }
 
 double or_sample_table(const or_sim* s, int which, double u) {
   return sample_table(which == 0 ? s->cdf_vol : s->cdf_surf, u);
@@ -812,19 +839,29 @@ int or_add_particles(or_sim* s, int spi, int64_t n, const double* st) {
 }
 
 /* Cell and bilinear fractions of a point; the same weights serve charge
- * weighing and field interpolation (Sec. 1). */
-static void locate(const or_sim* s, double x1, double x2, int* i, int* j, double* f1, double* f2) {
+ * weighing and field interpolation (Sec. 1).  Under a decision tape the cell
+ * is recorded, or replayed with the fractions left unclamped, so that a
+ * replayed run's weights are the same bilinear functions of the position
+ * (the frozen-decision map is then smooth in the parameters). */
+static void locate(or_sim* s, double x1, double x2, int* i, int* j, double* f1, double* f2) {
   double u1 = (x1 + 1.0) / s->h1, u2 = (x2 + 1.0) / s->h2;
   int a = (int)floor(u1), b = (int)floor(u2);
   if (a < 0) a = 0;
   if (a > s->c.n1 - 1) a = s->c.n1 - 1;
   if (b < 0) b = 0;
   if (b > s->c.n2 - 1) b = s->c.n2 - 1;
+  if (s->tape_mode != OR_TAPE_OFF) {
+    int packed = tape_int(s, a * s->N2 + b);
+    a = packed / s->N2;
+    b = packed % s->N2;
+  }
   double g1 = u1 - a, g2 = u2 - b;
-  if (g1 < 0.0) g1 = 0.0;
-  if (g1 > 1.0) g1 = 1.0;
-  if (g2 < 0.0) g2 = 0.0;
-  if (g2 > 1.0) g2 = 1.0;
+  if (s->tape_mode != OR_TAPE_REPLAY) {
+    if (g1 < 0.0) g1 = 0.0;
+    if (g1 > 1.0) g1 = 1.0;
+    if (g2 < 0.0) g2 = 0.0;
+    if (g2 > 1.0) g2 = 1.0;
+  }
   *i = a; *j = b; *f1 = g1; *f2 = g2;
 }
 
@@ -994,7 +1031,7 @@ static void inject(or_sim* s) {
       double a[4], b[4];
       draw(s, spi, g, 2u, 0u, a);
       draw(s, spi, g, 2u, 1u, b);
-      double x2 = sample_table(s->cdf_surf, a[0]);
+      double x2 = sample_table_in(s, s->cdf_surf, a[0]);
       double vn = vth * sqrt(-2.0 * log(a[1]));
       double z0, z1;
       box_muller(a[2], a[3], &z0, &z1);
@@ -1173,7 +1210,7 @@ void or_destroy(or_sim* s) {
   }
   free(s->rho); free(s->phi); free(s->G1); free(s->G2); free(s->V);
   free(s->band); free(s->piv); free(s->bins); free(s->hist); free(s->phi_vac);
-  free(s->tape_st); free(s->tape_nk);
+  free(s->tape_st); free(s->tape_nk); free(s->tape_ix);
   free(s);
 }
 
@@ -1234,17 +1271,34 @@ void or_get_scalars(const or_sim* s, double* out) {
 /* ---- decision tape (frozen-decision runs) ----
  * Finite-difference derivatives of a PIC window are only meaningful with the
  * discrete decisions held fixed: a particle absorbed in one run and not in a
- * neighbouring one changes a tally by a whole particle.  A run in record mode
- * stores every decision; runs of perturbed parameters replay them. */
+ * neighbouring one changes a tally by a whole particle, and a particle that
+ * crosses a cell boundary moves onto a different piece of the piecewise
+ * bilinear weights.  A run in record mode stores every decision (fates,
+ * injection counts, cells, table intervals); runs of perturbed parameters
+ * replay them. */
 void or_tape_mode(or_sim* s, int mode) {
   s->tape_mode = mode;
   s->tape_pos = 0;
   s->tape_nk_pos = 0;
+  s->tape_ix_pos = 0;
   s->tape_short = 0;
   if (mode == OR_TAPE_RECORD) {
     s->tape_n = 0;
     s->tape_nk_n = 0;
+    s->tape_ix_n = 0;
   }
+}
+
+int64_t or_tape_ix_get(const or_sim* s, int32_t* out) {
+  if (out) memcpy(out, s->tape_ix, sizeof(int32_t) * (size_t)s->tape_ix_n);
+  return s->tape_ix_n;
+}
+
+void or_tape_ix_set(or_sim* s, const int32_t* ix, int64_t n) {
+  s->tape_ix = (int32_t*)realloc(s->tape_ix, sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  if (n > 0) memcpy(s->tape_ix, ix, sizeof(int32_t) * (size_t)n);
+  s->tape_ix_n = s->tape_ix_cap = n;
+  s->tape_ix_pos = 0;
 }
 
 int64_t or_tape_get(const or_sim* s, uint8_t* st, int64_t* nk, int64_t* n_nk) {

@@ -87,12 +87,14 @@ double or_sample_table(const or_sim* s, int which, double u); /* 0 volume, 1 sur
 
 /* ---- decision tape: frozen-decision runs for finite-difference derivatives ---- */
 #define OR_TAPE_OFF 0
-#define OR_TAPE_RECORD 1  /* store every absorb/escape/keep decision and injection count */
+#define OR_TAPE_RECORD 1  /* store every absorb/escape/keep decision, injection count, cell and table interval */
 #define OR_TAPE_REPLAY 2  /* take them from the tape instead of the geometry */
 void or_tape_mode(or_sim* s, int mode);
 int64_t or_tape_get(const or_sim* s, uint8_t* st, int64_t* nk, int64_t* n_nk); /* returns status count */
 void or_tape_set(or_sim* s, const uint8_t* st, int64_t n, const int64_t* nk, int64_t n_nk);
 int or_tape_status(const or_sim* s); /* -1 if a replay ran past the end of its tape */
+int64_t or_tape_ix_get(const or_sim* s, int32_t* out);          /* cells and table intervals; returns the count */
+void or_tape_ix_set(or_sim* s, const int32_t* ix, int64_t n);
 
 #ifdef __cplusplus
 }

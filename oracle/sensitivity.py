@@ -5,10 +5,15 @@ electric F_Z on the grain, current = absorbed charge per time, torque T_z =
 absorbed L_z per time, grain charge Q; history columns 2, 3, 1, 4, 6 of the
 oracle) are averaged over a window of K steps that starts from a given
 particle state.  Their derivatives with respect to alpha, phi_g and B are
-central differences of runs at p +- h that replay the decisions (absorbed,
-escaped or kept, per update and per injection draw; injection counts) of the
-run at p, so that no particle changes fate between the runs.  Random numbers
-are the same in every run (same seed and draw counters).
+central differences of runs at p +- h that replay the decisions of the run at
+p (absorbed, escaped or kept, per update and per injection draw; injection
+counts; every particle's cell at every weighing and gather, whose bilinear
+weights are then taken unclamped; every injection's sampling-table
+interval), so that no particle changes fate or piece of the piecewise
+bilinear weights between the runs: the replayed map is smooth in the
+parameters and its central differences converge at O(h^2) to the
+frozen-decision derivative.  Random numbers are the same in every run (same
+seed and draw counters).
 """
 import numpy as np
 
