@@ -885,7 +885,7 @@ static int setup(apic_sim* S) {
       P.lam = std::sqrt(sp.T / (2.0 * kPi * sp.m)) * I.A_out * c.dt / P.w;
       P.base = slots;
       P.cap = sp.capacity;
-      slots += sp.capacity;
+      slots += (sp.capacity + 3) & ~3ll;  // slot ranges on 16-byte boundaries (the FP32 push's vector loads)
       P.inst = k;
       P.species = s;
       int lg = bits_for(sp.capacity);
@@ -978,6 +978,12 @@ static int setup(apic_sim* S) {
       ndu = NdUpload();
       nd_w = 0;
       int nd_need = 0;
+      int nd_ctas = 0;  // CTAs of the solve (small fronts are spread over them)
+      {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nd_ctas, cudaDevAttrMultiProcessorCount, dev);
+      }
       for (int k = 0; k < ni && want; ++k) {
         BcrInst& B = bcr_in[k];
         auto up = [](long long v) { return (v + 63) & ~63ll; };  // 256-byte aligned ranges
@@ -990,7 +996,7 @@ static int setup(apic_sim* S) {
           B.base = off;
           NdLevels lvl;
           nd_need = std::max(nd_need, nd_layout(nds[k], off, nd_w, kNdWarpMaxS, kNdWarpMaxU, kNdTaskFloats,
-                                                kNdTaskFronts, ndu, lvl));
+                                                kNdTaskFronts, nd_ctas, ndu, lvl));
           B.nd = 1;
           B.nd_depth = nds[k].depth;
           for (int l = 0; l <= nds[k].depth + 1; ++l) {

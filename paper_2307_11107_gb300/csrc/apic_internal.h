@@ -321,7 +321,7 @@ constexpr int kNdMaxDepth = 40;
 constexpr int kNdWarpMaxS = 64;     // fronts with a separator up to this size run one per warp
 constexpr int kNdWarpMaxU = 192;    // ... and an update set up to this size
 constexpr int kNdTaskFloats = 16384;  // matrix floats per task of a large front (row chunks)
-constexpr int kNdTaskFronts = 32;     // small fronts per task (taken by the warps in turn)
+constexpr int kNdTaskFronts = 16;     // small fronts per task at most (one per warp)
 struct BcrInst {
   int K;                    // 2^K >= n1
   int N;                    // block size N2

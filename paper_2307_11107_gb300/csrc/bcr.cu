@@ -403,10 +403,10 @@ __device__ __forceinline__ void rows_dot_any(int n4, const float* mat, int strid
 // (separator positions only) plus what its children's update vectors hold
 // for it, in the order child 0, child 1.
 __device__ __forceinline__ float nd_rhs(const DevPtrs& d, const NdFront& F, int p, const float* f, const float* w) {
+  const int2 g = *(const int2*)(d.nd_gather + F.G + 2 * p);  // absolute offsets into w (-1: none)
   float v = p < F.s ? f[d.nd_idx[F.S + p]] : 0.0f;
-  const int g0 = d.nd_gather[F.G + 2 * p], g1 = d.nd_gather[F.G + 2 * p + 1];
-  if (g0 >= 0) v += w[d.nd_front[F.child[0]].W + g0];
-  if (g1 >= 0) v += w[d.nd_front[F.child[1]].W + g1];
+  if (g.x >= 0) v += w[g.x];
+  if (g.y >= 0) v += w[g.y];
   return v;
 }
 
@@ -478,6 +478,9 @@ __device__ bool run_nd(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int
     }
     __syncwarp();
   }
+  // the next task may be a large front's, whose vector overwrites the
+  // per-warp areas: every warp finishes here first
+  __syncthreads();
   return true;
 }
 

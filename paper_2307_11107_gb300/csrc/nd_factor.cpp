@@ -473,7 +473,7 @@ void nd_solve_host(const NdFactor& f, const double* r, double* e, bool fp64) {
 }
 
 int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u, int task_floats, int task_fronts,
-              NdUpload& up, NdLevels& lv) {
+              int ctas, NdUpload& up, NdLevels& lv) {
   const int nf = (int)f.fronts.size();
   const int64_t front0 = (int64_t)up.fronts.size(), idx0 = (int64_t)up.idx.size(), g0 = (int64_t)up.gather.size();
   std::vector<int> order;  // deepest level first
@@ -499,9 +499,20 @@ int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u
   }
   up.idx.insert(up.idx.end(), f.idx.begin(), f.idx.end());
   up.gather.insert(up.gather.end(), f.gather.begin(), f.gather.end());
+  for (int q = 0; q < nf; ++q) {  // child-relative gather entries -> absolute update-vector offsets
+    const NdFront& F = up.fronts[front0 + q];
+    for (int p = 0; p < F.s + F.u; ++p)
+      for (int c = 0; c < 2; ++c) {
+        int32_t& g = up.gather[F.G + 2 * p + c];
+        if (g >= 0) g = (int32_t)(up.fronts[F.child[c]].W + g);
+      }
+  }
   auto level_tasks = [&](int l, bool fwd) {
     int q = 0;
     while (q < nf && up.fronts[front0 + q].level != l) ++q;
+    int small = 0;
+    for (int z = q; z < nf && up.fronts[front0 + z].level == l; ++z) small += !large(up.fronts[front0 + z]);
+    const int per = std::max(1, std::min(task_fronts, (small + std::max(1, ctas) - 1) / std::max(1, ctas)));
     while (q < nf && up.fronts[front0 + q].level == l) {
       const NdFront& F = up.fronts[front0 + q];
       if (large(F)) {
@@ -513,7 +524,7 @@ int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u
         continue;
       }
       int n = 0;
-      while (q + n < nf && n < task_fronts) {
+      while (q + n < nf && n < per) {
         const NdFront& G = up.fronts[front0 + q + n];
         if (G.level != l || large(G)) break;
         ++n;
@@ -543,8 +554,8 @@ void nd_solve_tables(const NdUpload& up, const NdLevels& lv, int depth, const st
   auto rhs = [&](const NdFront& F, int p) {
     float v = p < F.s ? r[up.idx[F.S + p]] : 0.0f;
     const int g0 = up.gather[F.G + 2 * p], g1 = up.gather[F.G + 2 * p + 1];
-    if (g0 >= 0) v += w[up.fronts[F.child[0]].W + g0];
-    if (g1 >= 0) v += w[up.fronts[F.child[1]].W + g1];
+    if (g0 >= 0) v += w[g0];
+    if (g1 >= 0) v += w[g1];
     return v;
   };
   auto fwd = [&](const NdFront& F, int r0, int r1) {

@@ -620,6 +620,326 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
   if (s_wpop >= 0) flush(s_wpop, s_row0);
 }
 
+// FP32 push with four consecutive particles per thread: the state arrays are
+// read and written as 128-bit vectors (five loads and five stores per four
+// particles instead of twenty each), the chunk's first live row comes from
+// loads already in flight, and absorbed or escaped particles are counted on a
+// path taken only by warps that lost one.  Same chunks (2048 consecutive
+// particles of one population, taken in groups from the counter), deposit
+// window and per-particle arithmetic as k_push.  Population slot ranges start
+// on multiples of four slots and extend to one (apic_create), so every vector
+// lies inside its population's range; slots beyond the population's count
+// are read and written back unchanged.
+struct P4 {
+  float4 x1, x2, vR, vZ, vT;
+};
+
+__device__ __forceinline__ float& lane4(float4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); }
+
+#ifndef APIC_PUSH4_MIN_BLOCKS
+#define APIC_PUSH4_MIN_BLOCKS 3  // 85 registers: the four particles' state stays in registers
+#endif
+template <bool kChord>
+__global__ void __launch_bounds__(256, APIC_PUSH4_MIN_BLOCKS) k_push4(DevPtrs d, int win_n2, int win_rows, int group) {
+  extern __shared__ unsigned long long s_win[];
+  const int win_words = 2 * win_rows * win_n2;
+  long long* s_pre = (long long*)(s_win + win_words);
+  PushConst* s_pc = (PushConst*)(s_pre + d.n_pop + 1);
+  __shared__ int s_row0, s_wpop, s_nsince, s_newrow0, s_flush, s_gi;
+  __shared__ unsigned s_rowmask;
+  constexpr int kPer = 4;                 // particles per thread and item
+  const long long CH = (long long)kPushItems * blockDim.x;  // 2048 particles per chunk
+  const int items = kPushItems / kPer;     // 2 items of 1024 particles
+  if (threadIdx.x == 0) {
+    long long a = 0;
+    for (int p = 0; p < d.n_pop; ++p) {
+      s_pre[p] = a;
+      a += (d.ps[p].n + CH - 1) / CH;
+    }
+    s_pre[d.n_pop] = a;
+  }
+  for (int p = threadIdx.x; p < d.n_pop; p += blockDim.x) {
+    const Pop& P = d.pop[p];
+    const Inst& I = d.inst[P.inst];
+    PushConst C;
+    C.al = (Real)I.alpha;
+    C.h1 = (Real)I.h1;
+    C.h2 = (Real)I.h2;
+    C.x1_out = (Real)I.x1_out;
+    C.dt = (Real)I.dt;
+    C.B = (Real)I.B;
+    C.h = Real(0.5) * (Real)(P.q / P.m) * (Real)I.dt;
+    C.ih1 = (Real)(1.0 / I.h1);
+    C.ih2 = (Real)(1.0 / I.h2);
+    C.tz = C.h * (-(Real)I.B);
+    C.sz = Real(2) * C.tz / (Real(1) + C.tz * C.tz);
+    C.n1 = I.n1;
+    C.n2 = I.n2;
+    C.N2 = I.N2;
+    C.fbits = P.fbits;
+    C.node_off = I.node_off;
+    C.acc_off = P.acc_off;
+    s_pc[p] = C;
+  }
+  for (int k = threadIdx.x; k < win_words; k += blockDim.x) s_win[k] = 0ull;
+  __syncthreads();
+  const long long total_chunks = s_pre[d.n_pop];
+  float4* X1 = (float4*)d.x1;
+  float4* X2 = (float4*)d.x2;
+  float4* VR = (float4*)d.vR;
+  float4* VZ = (float4*)d.vZ;
+  float4* VT = (float4*)d.vT;
+  const float2* G = (const float2*)d.G;
+  auto flush = [&](int wp, int row0) {
+    const PushConst& Cw = s_pc[wp];
+    const int rows = Cw.n2 <= win_n2 ? win_rows : 0;
+    unsigned long long* g = d.acc + Cw.acc_off;
+    const unsigned S = 1u << (Cw.fbits >> 1);
+    const unsigned cm = s_rowmask;
+    const unsigned nm = cm | (cm << 1);
+    const int nrows = __popc(nm);
+    for (int e = threadIdx.x; e < nrows * Cw.N2; e += blockDim.x) {
+      const int q = e / Cw.N2, nj = e - q * Cw.N2;
+      unsigned mm = nm;
+      for (int z = 0; z < q; ++z) mm &= mm - 1u;
+      const int rr = __ffs(mm) - 1;
+      unsigned long long v = 0, w[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int cr = rr - (t & 1), cj = nj - (t >> 1);
+        if (cr < 0 || cr >= rows || !((cm >> cr) & 1u) || cj < 0 || cj >= Cw.n2) continue;
+        const unsigned long long* c = s_win + 2 * (cr * Cw.n2 + cj);
+        if (c[1] == 0ull) continue;
+        corner_weights(c[0], c[1], S, w);
+        v += w[t];
+      }
+      if (v) atomicAdd(g + (long long)(row0 + rr) * Cw.N2 + nj, v);
+    }
+    __syncthreads();
+    const int crows = __popc(cm);
+    for (int e = threadIdx.x; e < 2 * crows * Cw.n2; e += blockDim.x) {
+      const int q = e / (2 * Cw.n2), o = e - q * 2 * Cw.n2;
+      unsigned mm = cm;
+      for (int z = 0; z < q; ++z) mm &= mm - 1u;
+      s_win[2 * (__ffs(mm) - 1) * Cw.n2 + o] = 0ull;
+    }
+    __syncthreads();
+  };
+  const int nch = (int)total_chunks;
+  const int GS = group > 0 ? group : 1;
+  const int ngroups = (nch + GS - 1) / GS;
+  if (threadIdx.x == 0) {
+    s_wpop = -1;
+    s_nsince = 0;
+    s_rowmask = 0u;
+  }
+  __syncthreads();
+  const unsigned lane = threadIdx.x & 31;
+  for (int q = 0;; ++q) {
+    if (q % GS == 0) {
+      if (threadIdx.x == 0) s_gi = (int)atomicAdd((unsigned long long*)(d.cnt + 1), 1ull);
+      __syncthreads();
+    }
+    const int gi = s_gi;
+    if (gi >= ngroups) break;
+    const long long chunk = (long long)gi * GS + q % GS;
+    if (chunk >= nch) continue;
+    const int pop = find_pop(s_pre, d.n_pop, chunk);
+    const PushConst C = s_pc[pop];
+    const long long npop = d.ps[pop].n, pbase = d.pop[pop].base;
+    const long long c0 = (chunk - s_pre[pop]) * CH;
+    const long long v0 = (pbase + c0) / kPer + threadIdx.x;  // vector of item 0 (pbase, c0: multiples of 4)
+    const int nleft = npop - c0 > CH ? (int)CH : (int)(npop - c0);  // particles of the chunk in the population
+    P4 st;
+    auto load = [&](int it) {
+      const long long v = v0 + (long long)it * blockDim.x;
+      if ((it * (int)blockDim.x + (int)threadIdx.x) * kPer < nleft) {
+        st.x1 = X1[v];
+        st.x2 = X2[v];
+        st.vR = VR[v];
+        st.vZ = VZ[v];
+        st.vT = VT[v];
+      } else {
+        st.x1 = make_float4(2.0f, 2.0f, 2.0f, 2.0f);
+      }
+    };
+    load(0);
+    if (threadIdx.x == 0) {
+      // window rows from the chunk's first live particle (this thread holds the first four)
+      int row = -1;
+      for (int k = 0; k < kPer && row < 0; ++k) {
+        const float xq = lane4(st.x1, k);
+        if (k < nleft && xq < 0.0f) row = (int)floor((double)((xq + 1.0f) * C.ih1));
+      }
+      for (int qq = kPer; row < 0 && qq < 64 && c0 + qq < npop; ++qq) {
+        const float xq = ((const float*)d.x1)[pbase + c0 + qq];
+        if (xq < 0.0f) row = (int)floor((double)((xq + 1.0f) * C.ih1));
+      }
+      row = row < 0 ? 0 : row;
+      const int r0 = row > 0 ? row - 1 : 0;
+      const int rows = C.n2 <= win_n2 ? win_rows : 0;
+      const bool keep = s_wpop == pop && s_nsince < kFlushChunks && r0 >= s_row0 && r0 + 2 < s_row0 + rows;
+      s_flush = s_wpop >= 0 && !keep;
+      s_newrow0 = keep ? s_row0 : r0;
+    }
+    __syncthreads();
+    if (s_flush) flush(s_wpop, s_row0);
+    if (threadIdx.x == 0) {
+      if (s_row0 != s_newrow0 || s_wpop != pop || s_flush) {
+        s_row0 = s_newrow0;
+        s_wpop = pop;
+        s_rowmask = 0u;
+        s_nsince = 0;
+      }
+      s_nsince += 1;
+    }
+    __syncthreads();
+    CellWin CW;
+    CW.s = s_win;
+    CW.g = d.acc + C.acc_off;
+    CW.row0 = s_row0;
+    CW.rows = C.n2 <= win_n2 ? win_rows : 0;
+    CW.n2 = C.n2;
+    CW.N2 = C.N2;
+    const float2* Gi = G + C.node_off;
+    const int bits = C.fbits >> 1;
+    for (int it = 0; it < items; ++it) {
+      if (it > 0) load(it);
+      const int base_local = it * (int)blockDim.x * kPer + (int)threadIdx.x * kPer;  // chunk-local index of particle 0
+      unsigned deadm = 0u, absm = 0u, rows_hit = 0u;
+#pragma unroll 1
+      for (int k = 0; k < kPer; ++k) {
+        const bool active = base_local + k < nleft;
+        const float x1 = lane4(st.x1, k);
+        const bool alive = active && x1 < 0.0f;
+        int fate = 0;
+        int key = -1, di = 0, dj = 0;
+        unsigned q1 = 0, q2 = 0;
+        if (alive) {
+          float x2 = lane4(st.x2, k), vR = lane4(st.vR, k), vZ = lane4(st.vZ, k), vT = lane4(st.vT, k);
+          const float al = C.al, dt = C.dt;
+          float x1f = x1;
+          float disc = 1.0f - 4.0f * al * x1f * x2;
+          float ir = __fdividef(-2.0f * x1f, 1.0f + sqrtf(disc));  // 1/r (Eq. 3)
+          float r = __fdividef(1.0f, ir);
+          float s2 = (1.0f - x2) * (1.0f + x2);
+          float sn = sqrtf(s2);
+          float R = r * sn, Z = r * x2;
+          float u1 = (x1f + 1.0f) * C.ih1, u2 = (x2 + 1.0f) * C.ih2;
+          int ci = min(max((int)floorf(u1), 0), C.n1 - 1), cj = min(max((int)floorf(u2), 0), C.n2 - 1);
+          float f1 = fminf(fmaxf(u1 - (float)ci, 0.0f), 1.0f), f2 = fminf(fmaxf(u2 - (float)cj, 0.0f), 1.0f);
+          const int n00 = ci * C.N2 + cj;
+          float2 a00 = Gi[n00], a10 = Gi[n00 + C.N2], a01 = Gi[n00 + 1], a11 = Gi[n00 + C.N2 + 1];
+          float g1 = (1.0f - f2) * ((1.0f - f1) * a00.x + f1 * a10.x) + f2 * ((1.0f - f1) * a01.x + f1 * a11.x);
+          float g2 = (1.0f - f2) * ((1.0f - f1) * a00.y + f1 * a10.y) + f2 * ((1.0f - f1) * a01.y + f1 * a11.y);
+          float ir3 = ir * ir * ir;
+          float x1R = sn * (r + 3.0f * al * x2) * ir3, x1Z = (r * x2 + al * (3.0f * x2 * x2 - 1.0f)) * ir3;
+          float x2R = -x2 * sn * ir, x2Z = s2 * ir;
+          float ER = -(x1R * g1 + x2R * g2), EZ = -(x1Z * g1 + x2Z * g2);
+          float h = C.h, tz = C.tz, sz = C.sz;
+          float vx = vR + h * ER, vy = vT, vz = vZ + h * EZ;
+          float px_ = vx + vy * tz, py_ = vy - vx * tz;
+          vx = vx + py_ * sz + h * ER;
+          vy = vy - px_ * sz;
+          vz = vz + h * EZ;
+          float Xc = R + vx * dt, Yc = vy * dt, Zn = Z + vz * dt;
+          float Rn2 = Xc * Xc + Yc * Yc;
+          float cr = 1.0f, sr = 0.0f;
+          if (Rn2 > 0.0f) {
+            float iR = rsqrtf(Rn2);
+            cr = Xc * iR;
+            sr = Yc * iR;
+          }
+          float vRn = cr * vx + sr * vy, vTn = -sr * vx + cr * vy;
+          float rn2 = Rn2 + Zn * Zn;
+          float irn = rsqrtf(rn2);
+          float rn = rn2 * irn;
+          float x2n = Zn * irn;
+          float tr = 2.0f * rn - 1.0f;
+          bool hit = tr < 0.0f || tr * tr < 1.0f + 4.0f * al * x2n;
+          float tau = dt;
+          if (kChord && !hit && (d.inst[d.pop[pop].inst].flags & APIC_CHORD_ABSORB)) {
+            const float se = chord_entry(al, R, Z, vx * dt, vy * dt, vz * dt);
+            if (se > 0.0f) {
+              hit = true;
+              tau = dt * se;
+            }
+          }
+          if (hit) {
+            const Pop& P = d.pop[pop];
+            absorb_tally(d, d.inst[P.inst], P, R, Z, vx, vz, vy, tau);
+            lane4(st.x1, k) = 2.0f;
+            fate = 1;
+          } else {
+            float x1n = -irn * (1.0f + al * x2n * irn);
+            if (x1n > C.x1_out) {
+              lane4(st.x1, k) = 2.0f;
+              fate = 2;
+            } else {
+              lane4(st.x1, k) = x1n;
+              lane4(st.x2, k) = x2n;
+              lane4(st.vR, k) = vRn;
+              lane4(st.vZ, k) = vz;
+              lane4(st.vT, k) = vTn;
+              float v1 = (x1n + 1.0f) * C.ih1, v2 = (x2n + 1.0f) * C.ih2;
+              int ni = min(max((int)floorf(v1), 0), C.n1 - 1), nj = min(max((int)floorf(v2), 0), C.n2 - 1);
+              float e1 = fminf(fmaxf(v1 - (float)ni, 0.0f), 1.0f), e2 = fminf(fmaxf(v2 - (float)nj, 0.0f), 1.0f);
+              const float one = (float)(1u << bits);
+              q1 = min((unsigned)(e1 * one + 0.5f), 1u << bits);
+              q2 = min((unsigned)(e2 * one + 0.5f), 1u << bits);
+              key = ni * C.N2 + nj;
+              di = ni;
+              dj = nj;
+            }
+          }
+        }
+        if (fate) {
+          deadm |= 1u << k;
+          if (fate == 1) absm |= 1u << k;
+        }
+        deposit_moments(CW, key, di, dj, q1, q2, bits, key >= 0);
+        const int rr = di - CW.row0;
+        if (key >= 0 && rr >= 0 && rr < CW.rows) rows_hit |= 1u << rr;
+      }
+      if ((it * (int)blockDim.x + (int)threadIdx.x) * kPer < nleft) {
+        const long long v = v0 + (long long)it * blockDim.x;
+        X1[v] = st.x1;
+        X2[v] = st.x2;
+        VR[v] = st.vR;
+        VZ[v] = st.vZ;
+        VT[v] = st.vT;
+      }
+      const unsigned rh = __reduce_or_sync(kFull, rows_hit);
+      if (lane == 0 && rh) atomicOr(&s_rowmask, rh);
+      // absorbed or escaped particles: counters and freed slots (rare)
+      if (__any_sync(kFull, deadm != 0u)) {
+        const unsigned nd = __popc(deadm);
+        unsigned incl = nd;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned y = __shfl_up_sync(kFull, incl, o);
+          if ((int)lane >= o) incl += y;
+        }
+        const unsigned tot = __shfl_sync(kFull, incl, 31);
+        const unsigned tabs = __reduce_add_sync(kFull, __popc(absm));
+        long long h0 = 0;
+        if (lane == 0) {
+          PopState& S = d.ps[pop];
+          if (tabs) atomicAdd((unsigned long long*)&S.absorbed, (unsigned long long)tabs);
+          if (tot - tabs) atomicAdd((unsigned long long*)&S.escaped, (unsigned long long)(tot - tabs));
+          h0 = (long long)atomicAdd((unsigned long long*)&S.n_holes, (unsigned long long)tot);
+        }
+        h0 = __shfl_sync(kFull, h0, 0);
+        long long hpos = h0 + (long long)(incl - nd);
+        for (int k = 0; k < kPer; ++k)
+          if ((deadm >> k) & 1u) d.holes[d.pop[pop].base + hpos++] = (int32_t)(c0 + base_local + k);
+      }
+    }
+    __syncthreads();
+  }
+  if (s_wpop >= 0) flush(s_wpop, s_row0);
+}
+
 // Deposit every live particle (after external changes to the particle set,
 // and in every step of the sensitivity window).  Each CTA takes a contiguous
 // range of the (row-sorted) particles in chunks of kDepItems x blockDim and
@@ -1160,6 +1480,18 @@ void launch_deposit_all<Real>(const DevPtrs& d, int max_grid, int max_n2, cudaSt
 }
 
 // Dynamic shared memory of the push: window, chunk prefix, population constants.
+// FP32 particles take the four-particle vector push (APIC_PUSH4=0: the
+// one-particle push, for comparison).
+static bool push4() {
+  if (kF64) return false;
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("APIC_PUSH4");
+    on = e ? (std::atoi(e) != 0) : 1;
+  }
+  return on != 0;
+}
+
 static int push_smem(int rows, int win_n2, int n_pop) {
   const int words = kF64 ? rows * (win_n2 + 1) : 2 * rows * win_n2;
   return words * (int)sizeof(unsigned long long) + (n_pop + 1) * (int)sizeof(long long) +
@@ -1183,13 +1515,13 @@ int push_window_rows<Real>(int max_n2) {
     rows = std::max(2, std::min(kWinRows, 32768 / std::max(1, row_bytes)));
     const char* e = std::getenv("APIC_WIN_ROWS");  // tuning: a fixed row count
     if (e) rows = std::max(2, std::min(kWinRows, std::atoi(e)));
+    const void* kern = push4() ? (const void*)k_push4<false> : (const void*)k_push<false>;
+    const int want = push4() ? (int)APIC_PUSH4_MIN_BLOCKS : (int)APIC_PUSH_MIN_BLOCKS;
     for (; !e && rows > 2; --rows) {
       const int sm = push_smem(rows, win_n2, kMaxPop);
-      cudaFuncSetAttribute(k_push<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
       int per = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_push<false>, 256, sm) == cudaSuccess &&
-          per >= (int)APIC_PUSH_MIN_BLOCKS)
-        break;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, sm) == cudaSuccess && per >= want) break;
     }
     cudaGetLastError();
     rows_for[win_n2] = rows;
@@ -1202,7 +1534,9 @@ void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, bool chord, cudaS
   const int win_n2 = max_n2 < kWinMaxN2 - 1 ? max_n2 : kWinMaxN2 - 1;
   const int rows = push_window_rows<Real>(max_n2);
   const int sm = push_smem(rows, win_n2, d.n_pop);
-  const void* kern = chord ? (const void*)k_push<true> : (const void*)k_push<false>;
+  const bool v4 = push4();
+  const void* kern = v4 ? (chord ? (const void*)k_push4<true> : (const void*)k_push4<false>)
+                        : (chord ? (const void*)k_push<true> : (const void*)k_push<false>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   static int group = -1;  // chunks per group (APIC_PUSH_GROUP, default 4: the fastest of 1, 2, 4, 8 measured)
   if (group < 0) {
@@ -1210,8 +1544,15 @@ void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, bool chord, cudaS
     group = e ? std::max(1, std::atoi(e)) : 4;
   }
   cudaMemsetAsync(d.cnt + 1, 0, sizeof(long long), s);  // the group counter
-  if (chord) k_push<true><<<grid, 256, sm, s>>>(d, win_n2, rows, group);
-  else k_push<false><<<grid, 256, sm, s>>>(d, win_n2, rows, group);
+  if (v4) {
+    grid = std::max(1, grid / 4 * (int)APIC_PUSH4_MIN_BLOCKS);  // the caller's grid is 4 CTAs per SM
+    if (chord) k_push4<true><<<grid, 256, sm, s>>>(d, win_n2, rows, group);
+    else k_push4<false><<<grid, 256, sm, s>>>(d, win_n2, rows, group);
+  } else if (chord) {
+    k_push<true><<<grid, 256, sm, s>>>(d, win_n2, rows, group);
+  } else {
+    k_push<false><<<grid, 256, sm, s>>>(d, win_n2, rows, group);
+  }
 }
 
 template <>

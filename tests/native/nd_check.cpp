@@ -94,8 +94,8 @@ int main(int argc, char** argv) {
   apic::NdUpload up;
   apic::NdLevels l0, l1;
   const int64_t mat1 = ((f.fm_total + f.nb_total + 63) / 64) * 64, w1 = ((f.w_total + 63) / 64) * 64;
-  apic::nd_layout(f, 0, 0, 64, 192, 16384, 32, up, l0);
-  apic::nd_layout(f, mat1, w1, 64, 192, 16384, 32, up, l1);
+  apic::nd_layout(f, 0, 0, 64, 192, 16384, 16, 152, up, l0);
+  apic::nd_layout(f, mat1, w1, 64, 192, 16384, 16, 152, up, l1);
   std::vector<float> matbuf((size_t)(2 * mat1), 0.0f);
   for (int k = 0; k < 2; ++k) {
     std::copy(f.fm.begin(), f.fm.end(), matbuf.begin() + k * mat1);

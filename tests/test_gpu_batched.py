@@ -68,21 +68,24 @@ def test_batch_equals_solo(prec, solver, monkeypatch):
         assert np.allclose(tb["history"], ts["history"], rtol=1e-12, atol=1e-12)
 
 
-def test_batched_reduction_poisson_matches_banded_lu():
+@pytest.mark.parametrize("direct", ["bcr", "auto"])
+def test_batched_reduction_poisson_matches_banded_lu(direct, monkeypatch):
     """Every instance of an uneven FP32 batch (different alpha and grid, n1
     a power of two or not, one instance wider than 256 unknowns per row, so
     the wide kernel runs the narrow ones too) solved by the batched block
-    cyclic reduction against the oracle's banded LU; solving one instance
-    leaves the others' potential alone."""
+    cyclic reduction against the oracle's banded LU; by default the wide
+    instance takes the nested dissection in the same launch as the others'
+    reduction.  Solving one instance leaves the others' potential alone."""
     import oracle
     import paper_2307_11107_gb300 as apic
     from tests.inputs import random_rho
     apic.build()
+    monkeypatch.setenv("APIC_DIRECT", direct)
     grids = [(64, 32, 0.1), (96, 48, 0.2), (160, 80, -0.24), (256, 128, 0.15), (32, 300, 0.05)]
     cfgs = [workload(n1=a, n2=b, alpha=al, x1_out=-0.05, n_init=1000, precision="fp32", poisson_tol=1e-12,
                      poisson_max_iter=60, instance=k) for k, (a, b, al) in enumerate(grids)]
     s = apic.Sim(cfgs)
-    assert s.stats()["solver"].startswith(_SOLVER["bcr"])
+    assert s.stats()["solver"].startswith(_SOLVER["bcr" if direct == "bcr" else "nd"])
     before = [s.field("phi", k) for k in range(len(cfgs))]
     for k, c in enumerate(cfgs):
         rho = random_rho(c["n1"], c["n2"], seed=40 + k, scale=0.3)

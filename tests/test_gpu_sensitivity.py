@@ -90,24 +90,39 @@ def test_window_against_oracle_differences(apic, precision, alpha, B, fe):
 def test_adjoint_form_configuration_against_oracle_differences(apic):
     """The adjoint form's configuration: alpha = 0.15 (a = 0.3), B = 1,
     256 x 128 cells, 1e6 particles per species, a window of K = 10 steps with
-    injection, FP32 on the GPU.  Window means and Jacobian against the FP64
-    oracle's frozen-decision central differences at h = 1e-4, within 1e-3 of
-    each row's scale (the current row, I d ln w / d alpha, is below the
-    differences' rounding and is checked in the test above)."""
+    injection.  The oracle's central differences replay every decision of its
+    unperturbed run, each particle's cell included, so they converge at
+    O(h^2) to the frozen-decision derivative.  FP64 tangents: all rows but the
+    current (whose differences are rounding-limited; checked above) within
+    1e-3 of each row's scale, against differences at h = 1e-5 for every
+    column and at the configuration's h = 1e-4 for phi_g and B (at 1e-4 the
+    alpha column still carries an O(h^2) error of up to 10 %: the geometry's
+    second derivatives are large).  FP32 tangents: an FP32 trajectory holds
+    other cells than the FP64 one for some 1e4 particle-steps, and each such
+    particle's derivative moves by the jump of the bilinear weights' slope,
+    so only the rows that no field derivative dominates, drag and torque, are
+    held to the FP64 derivative (within 5e-3)."""
     n, K = 1_000_000, 10
     cfg = workload(n1=256, n2=128, alpha=0.15, B=1.0, x1_out=-0.05, n_init=n, Ti=0.5, seed=5,
                    poisson_tol=1e-12, poisson_max_iter=60)
     st = [random_states(n, cfg["x1_out"], seed=71), random_states(n, cfg["x1_out"], seed=72, vscale=0.0165)]
     st = [x.astype(np.float32).astype(np.float64) for x in st]
-    vo, Jo, _ = window_sensitivity(cfg, st, K, h=dict(alpha=1e-4, phi_g=1e-4, B=1e-4))
-    _, vg, Jg = _gpu_window(apic, cfg, st, K, "fp32")
+    vo, J5, _ = window_sensitivity(cfg, st, K, h=dict(alpha=1e-5, phi_g=1e-5, B=1e-5))
+    _, J4, _ = window_sensitivity(cfg, st, K, h=dict(alpha=1e-5, phi_g=1e-4, B=1e-4))
+    rows = [0, 1, 3, 4]
+    scale = np.abs(J5).max(axis=1, keepdims=True) + 1e-30
+    _, vg, Jg = _gpu_window(apic, cfg, st, K, "fp64")
+    e5 = (np.abs(Jg - J5) / scale)[rows]
+    e4 = (np.abs(Jg - J4) / scale)[rows][:, 1:]
     ev = np.abs(vg - vo) / (np.abs(vo) + 1e-12)
-    scale = np.abs(Jo).max(axis=1, keepdims=True) + 1e-30
-    eJ = np.abs(Jg - Jo) / scale
-    print(f"\nadjoint-form configuration: values rel err {ev.max():.2e}, jacobian rel err {eJ[[0, 1, 3, 4]].max():.2e}"
-          f"\n oracle J =\n{Jo}\n gpu J =\n{Jg}")
-    assert ev.max() < 1e-3
-    assert eJ[[0, 1, 3, 4]].max() < 1e-3
+    _, vf, Jf = _gpu_window(apic, cfg, st, K, "fp32")
+    ef = (np.abs(Jf - Jg) / (np.abs(Jg).max(axis=1, keepdims=True) + 1e-30))[[0, 3]]
+    print(f"\nadjoint-form configuration: values {ev.max():.2e}, fp64 vs h=1e-5 {e5.max():.2e}, vs h=1e-4 "
+          f"(phi_g, B) {e4.max():.2e}, fp32 drag/torque vs fp64 {ef.max():.2e}\n oracle J (h=1e-5) =\n{J5}"
+          f"\n gpu fp64 J =\n{Jg}\n gpu fp32 J =\n{Jf}")
+    assert ev.max() < 1e-9
+    assert e5.max() < 1e-3 and e4.max() < 1e-3
+    assert ef.max() < 5e-3
 
 
 def test_adjoint_is_the_vector_jacobian_product(apic):
