@@ -289,7 +289,7 @@ int apic_step_timed(apic_sim* sim, int32_t n_steps);
 #define APIC_TUNE_CANDIDATES 7
 int apic_autotune(apic_sim* sim, int32_t steps_per_trial, int32_t* sort_interval, double* ms_per_step);
 
-/* ---- Sensitivity window (forward mode) -----------------------------------
+/* ---- Sensitivity window (forward mode) and its adjoint (reverse mode) ------
  * Derivatives of window-averaged grain outputs with respect to the grain
  * shape alpha (Eqs. 2-5, 7), the grain potential phi_g (boundary value of
  * Eq. 6) and the axial magnetic field B (Eq. 9).
@@ -318,12 +318,27 @@ int apic_autotune(apic_sim* sim, int32_t steps_per_trial, int32_t* sort_interval
                         current (absorbed charge / dt), torque T_z (absorbed L_z / dt), grain charge Q */
 int apic_sensitivity(apic_sim* sim, int32_t n_steps, double* values, double* jacobian);
 
-/* Gradient of L = sum_o dL_dout[o] * output_o (window means) with respect to
- * (alpha, phi_g, B): the vector-Jacobian product of apic_sensitivity's
- * Jacobian (three parameters, so the forward sweep costs what a reverse one
- * would and needs no checkpoints).  dL_dout: [n_instances][APIC_NOUT];
- * grad: [n_instances][APIC_NPAR]; host arrays owned by the caller.
- * Errors: as apic_sensitivity; INVALID_ARG for NULL arrays. */
+/* Gradient of L = sum_o dL_dout[o] * output_o (window means over n_steps
+ * steps from the current state) with respect to (alpha, phi_g, B), by a
+ * reverse sweep with per-step checkpoints: a forward pass of the window keeps,
+ * for every step, the particle state at its start, rho and phi, each slot's
+ * fate and each injection draw's slot; the backward pass then transposes the
+ * step's operations from the last step to the first (injection of Eq. 4,
+ * the push of Eqs. 10, 9 and 2 with each particle's local Jacobian, the
+ * surface charge and force, the node gradients, the Poisson problem of
+ * Eqs. 6-7 solved transposed by a nested-dissection factorisation of the
+ * operator in FP64, and the charge weighing with the node volumes of Eq. 5).
+ * Decisions are frozen as in apic_sensitivity (the same derivative: this is
+ * the transpose of its Jacobian).  The window advances the simulation by
+ * n_steps steps.  Memory: 5 n_steps particle arrays of checkpoints, 2 n_steps
+ * FP64 node arrays and a factorisation of each instance's operator (formed at
+ * the first call, a few seconds for 1024 x 512 cells).
+ * dL_dout: [n_instances][APIC_NOUT]; values (or NULL): [n_instances][APIC_NOUT]
+ * window means; grad: [n_instances][APIC_NPAR]; host arrays owned by the
+ * caller.  Errors: as apic_sensitivity; INVALID_ARG for NULL dL_dout or grad. */
+int apic_adjoint_window(apic_sim* sim, int32_t n_steps, const double* dL_dout, double* values, double* grad);
+
+/* apic_adjoint_window without the window means. */
 int apic_adjoint(apic_sim* sim, int32_t n_steps, const double* dL_dout, double* grad);
 
 /* ---- Charge deposit without device allocation --------------------------

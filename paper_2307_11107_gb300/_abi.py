@@ -22,7 +22,7 @@ NT, NH = 7, 11
 SYMBOLS = ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
            "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_last_error",
            "apic_num_instances", "apic_stats", "apic_step_timed", "apic_deposit_static", "apic_sensitivity",
-           "apic_adjoint", "apic_autotune", "apic_probe_fp32_fma", "apic_check_wait_limit")
+           "apic_adjoint", "apic_adjoint_window", "apic_autotune", "apic_probe_fp32_fma", "apic_check_wait_limit")
 TUNE_INTERVALS = (2, 4, 6, 8, 12, 16, 24)
 NPAR, NOUT = 3, 5
 PARAMS = ("alpha", "phi_g", "B")
@@ -106,13 +106,14 @@ def load():
     L.apic_deposit_static.argtypes = [C.POINTER(Grid), vp, vp, i64, C.c_double, vp, vp, vp]
     L.apic_sensitivity.argtypes = [vp, i32, dp, dp]
     L.apic_adjoint.argtypes = [vp, i32, dp, dp]
+    L.apic_adjoint_window.argtypes = [vp, i32, dp, dp, dp]
     L.apic_autotune.argtypes = [vp, i32, C.POINTER(i32), dp]
     L.apic_probe_fp32_fma.argtypes = [vp, i32, dp]
     L.apic_check_wait_limit.argtypes = [vp, i64]
     for name in ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
                  "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_stats", "apic_step_timed",
                  "apic_deposit_static", "apic_sensitivity", "apic_adjoint", "apic_autotune", "apic_probe_fp32_fma",
-                 "apic_check_wait_limit"):
+                 "apic_check_wait_limit", "apic_adjoint_window"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

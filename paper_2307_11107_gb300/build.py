@@ -12,6 +12,8 @@ Translation units (compiled in parallel):
   deposit_static.cu  the deposit entry point that uses no caller-side allocation
   probe.cu      the FP32 fused-multiply-add throughput probe (the ALU ceiling)
   nd_factor.cpp the host nested-dissection factorisation of the Poisson system
+  adjoint.cu    twice: the reverse sweep of the sensitivity window in FP64 (-fmad=false,
+                with its node kernels) and FP32
 """
 import os
 import shutil
@@ -40,6 +42,8 @@ UNITS = [
     ("deposit_static.cu", "deposit_static.o", ["-fmad=false"]),
     ("probe.cu", "probe.o", []),
     ("nd_factor.cpp", "nd_factor.o", []),
+    ("adjoint.cu", "adjoint_f64.o", ["-DAPIC_REAL=double", "-DAPIC_ADJOINT_COMMON", "-fmad=false"]),
+    ("adjoint.cu", "adjoint_f32.o", ["-DAPIC_REAL=float"]),
 ]
 
 

@@ -180,6 +180,10 @@ struct apic_sim {
   long long tab_total = 0;
   TanPtrs tan{};                      // sensitivity-window state (allocated on first use)
   bool tan_ready = false;
+  AdjPtrs adj{};                      // reverse-sweep state (allocated on first use, for up to adj_K steps)
+  int adj_K = 0;
+  std::vector<std::vector<std::pair<int, int>>> adj_levels;  // per instance, per tree level: fronts [f0, f1)
+  std::vector<int> adj_smem;                                  // per instance: doubles of a front's vector
 
   int fail(int code, const std::string& m) {
     if (status == APIC_OK) {
@@ -2227,18 +2231,206 @@ extern "C" int apic_sensitivity(apic_sim* S, int32_t n_steps, double* values, do
                                    : sensitivity_impl<float>(S, n_steps, values, jacobian);
 }
 
-extern "C" int apic_adjoint(apic_sim* S, int32_t n_steps, const double* dL_dout, double* grad) {
+// Reverse-sweep state for windows of up to K steps: checkpoints, fates,
+// injection records, adjoint vectors, and a nested-dissection factorisation
+// of every instance's solved operator in FP64 for the transposed solve.
+template <class Real>
+static bool adjoint_setup(apic_sim* S, int K) {
+  if (!tangent_setup<Real>(S)) return false;
+  AdjPtrs& a = S->adj;
+  const DevPtrs& d = S->d;
+  const long long tn = d.total_nodes;
+  const int ni = S->n_inst;
+  const size_t R = sizeof(Real);
+  if (S->adj_K < K) {
+    // (a smaller earlier allocation stays in the pool until apic_destroy)
+    a.K = K;
+    a.stride = S->slots;
+    a.ck = S->dalloc(R * 5 * (size_t)K * (size_t)S->slots);
+    a.ck_ps = (PopState*)S->dalloc(sizeof(PopState) * (size_t)(K + 1) * S->n_pop);
+    a.ck_rho = (double*)S->dalloc(sizeof(double) * (size_t)K * tn);
+    a.ck_phi = (double*)S->dalloc(sizeof(double) * (size_t)K * tn);
+    a.fate = (uint8_t*)S->dalloc((size_t)K * (size_t)S->slots);
+    a.inj_cap = std::max<long long>(1, S->max_inj);
+    a.inj = (int64_t*)S->dalloc(sizeof(int64_t) * (size_t)K * S->n_pop * (size_t)a.inj_cap);
+    if (!a.lam) {
+      a.lam = (double*)S->dalloc(sizeof(double) * 5 * (size_t)S->slots);
+      a.lG = (double*)S->dalloc(sizeof(double) * 2 * tn);
+      a.lphi = (double*)S->dalloc(sizeof(double) * tn);
+      a.lrho = (double*)S->dalloc(sizeof(double) * tn);
+      a.Gk = S->dalloc(2 * R * tn);
+      a.seed = (double*)S->dalloc(sizeof(double) * ni * kNOut);
+      a.grad = (double*)S->dalloc(sizeof(double) * ni * kNPar);
+      a.vals = (double*)S->dalloc(sizeof(double) * ni * kNOut);
+    }
+    if (S->status != APIC_OK) return false;
+    S->adj_K = K;
+  }
+  if (a.nd_front) return true;
+  // the transposed solve: every instance's operator (rows scaled as solved)
+  // factored by nested dissection, FP64 fronts
+  NdUpload up;
+  std::vector<NdFactor> fs(ni);
+  std::vector<int64_t> mat0(ni);
+  int64_t mat = 0, w = 0, unk = 0;
+  int T = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+  S->adj_levels.assign(ni, {});
+  S->adj_smem.assign(ni, 1);
+  for (int k = 0; k < ni; ++k) {
+    const Inst& I = S->inst[k];
+    if (ni > kCoopMaxInst) {
+      S->fail(APIC_ERR_INVALID_ARG, "too many instances for the reverse sweep");
+      return false;
+    }
+    a.unk_off[k] = unk;
+    unk += (long long)(I.n1 - 1) * I.N2;
+    if (I.flags & APIC_NO_FIELD) continue;
+    std::vector<double> V, rsc, bbc;
+    build_volumes(I, V);
+    HostLevel L;
+    build_fine(I, V, L, rsc, bbc);
+    std::string why;
+    if (!nd_build(I.n1 - 1, I.N2, nd_coef, &L, 16, T, true, fs[k], why)) {
+      S->fail(APIC_ERR_INVALID_ARG, "reverse sweep: " + why);
+      return false;
+    }
+    const int f0 = (int)up.fronts.size();
+    NdLevels lv;
+    nd_layout(fs[k], mat, w, kNdWarpMaxS, kNdWarpMaxU, kNdTaskFloats, kNdTaskFronts, 1, up, lv);
+    mat0[k] = mat;
+    mat += fs[k].fm_total + fs[k].nb_total;
+    w += fs[k].w_total;
+    auto& lvs = S->adj_levels[k];
+    lvs.assign(fs[k].depth + 1, {0, 0});
+    for (int q = f0; q < (int)up.fronts.size(); ++q) {
+      const NdFront& F = up.fronts[q];
+      auto& r = lvs[F.level];
+      if (r.second == 0) r.first = q;
+      r.second = q + 1;
+      S->adj_smem[k] = std::max(S->adj_smem[k], F.s + F.u);
+    }
+  }
+  a.unk_off[ni] = unk;
+  a.rhs = (double*)S->dalloc(sizeof(double) * (size_t)std::max<int64_t>(1, unk));
+  a.ndw = (double*)S->dalloc(sizeof(double) * (size_t)std::max<int64_t>(1, w));
+  double* mbuf = (double*)S->dalloc(sizeof(double) * (size_t)std::max<int64_t>(1, mat));
+  a.nd_front = (const NdFront*)S->dalloc(sizeof(NdFront) * std::max<size_t>(1, up.fronts.size()));
+  a.nd_idx = (const int32_t*)S->dalloc(sizeof(int32_t) * std::max<size_t>(1, up.idx.size()));
+  a.nd_gather = (const int32_t*)S->dalloc(sizeof(int32_t) * std::max<size_t>(1, up.gather.size()));
+  if (S->status != APIC_OK) return false;
+  a.nd_mat = mbuf;
+  S->h2d((NdFront*)a.nd_front, up.fronts.data(), up.fronts.size());
+  S->h2d((int32_t*)a.nd_idx, up.idx.data(), up.idx.size());
+  S->h2d((int32_t*)a.nd_gather, up.gather.data(), up.gather.size());
+  for (int k = 0; k < ni; ++k) {
+    if (fs[k].fm64.empty()) continue;
+    S->h2d(mbuf + mat0[k], fs[k].fm64.data(), fs[k].fm64.size());
+    S->h2d(mbuf + mat0[k] + fs[k].fm_total, fs[k].nb64.data(), fs[k].nb64.size());
+  }
+  for (int k = 0; k < ni; ++k) {
+    int need = S->adj_smem[k] * (int)sizeof(double);
+    if (need > 48 * 1024 &&
+        !S->ck(cudaFuncSetAttribute(adj_ndT_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize, need), "smem"))
+      return false;
+  }
+  return S->sync();
+}
+
+// The reverse sweep of an n-step window: forward pass with checkpoints,
+// then the steps backwards (adjoint.cu).
+template <class Real>
+static int adjoint_impl(apic_sim* S, int n, const double* dL_dout, double* values, double* grad) {
+  if (S->chord) return S->fail(APIC_ERR_INVALID_ARG, "the adjoint window does not take APIC_CHORD_ABSORB");
+  if (S->floating) return S->fail(APIC_ERR_INVALID_ARG, "the adjoint window does not take APIC_FLOATING");
+  if (S->boltz) return S->fail(APIC_ERR_INVALID_ARG, "the adjoint window does not take APIC_BOLTZMANN");
+  if (!adjoint_setup<Real>(S, n)) return S->status;
+  const TanPtrs& t = S->tan;
+  AdjPtrs a = S->adj;
+  a.K = n;
+  const DevPtrs d = S->view(S->par);
+  const long long tn = d.total_nodes;
+  const int ni = S->n_inst;
+  cudaStream_t s = S->stream;
+  const size_t R = sizeof(Real);
+  const size_t pbytes = R * (size_t)S->slots;
+  std::vector<double> seed((size_t)ni * kNOut);
+  for (size_t q = 0; q < seed.size(); ++q) seed[q] = dL_dout[q] / n;
+  S->h2d(a.seed, seed.data(), seed.size());
+  S->ck(cudaMemsetAsync(a.grad, 0, sizeof(double) * ni * kNPar, s), "memset");
+  S->ck(cudaMemsetAsync(a.vals, 0, sizeof(double) * ni * kNOut, s), "memset");
+  S->ck(cudaMemsetAsync(a.inj, 0xff, sizeof(int64_t) * (size_t)n * S->n_pop * a.inj_cap, s), "memset");
+  void* arr[5] = {d.x1, d.x2, d.vR, d.vZ, d.vT};
+  // forward pass, checkpoint k holding the state at the start of step k
+  for (int k = 0; k < n && S->status == APIC_OK; ++k) {
+    for (int c = 0; c < 5; ++c)
+      S->ck(cudaMemcpyAsync((char*)a.ck + ((size_t)k * 5 + c) * pbytes, arr[c], pbytes, cudaMemcpyDeviceToDevice, s),
+            "checkpoint");
+    S->ck(cudaMemcpyAsync(a.ck_ps + (size_t)k * S->n_pop, d.ps, sizeof(PopState) * S->n_pop, cudaMemcpyDeviceToDevice,
+                          s),
+          "checkpoint");
+    S->ck(cudaMemsetAsync(d.acc, 0, sizeof(unsigned long long) * 2 * tn, s), "memset");
+    launch_deposit_all<Real>(d, S->push_grid, S->max_n2, s);
+    launch_rho<Real>(d, s);
+    S->ck(cudaMemcpyAsync(a.ck_rho + (size_t)k * tn, d.rho, sizeof(double) * tn, cudaMemcpyDeviceToDevice, s), "ck");
+    if (!solve_now<Real>(S, d)) break;
+    S->ck(cudaMemcpyAsync(a.ck_phi + (size_t)k * tn, d.phi, sizeof(double) * tn, cudaMemcpyDeviceToDevice, s), "ck");
+    launch_gradients<Real>(d, s);
+    launch_surface(d, s);
+    launch_adj_fwd_push<Real>(d, a, k, s);
+    launch_adj_fwd_inject<Real>(d, a, t, k, S->max_inj, s);
+    launch_adj_values(d, a, s);
+    launch_step_end(d, s);
+    S->host_step += 1;
+  }
+  S->ck(cudaMemcpyAsync(a.ck_ps + (size_t)n * S->n_pop, d.ps, sizeof(PopState) * S->n_pop, cudaMemcpyDeviceToDevice, s),
+        "checkpoint");
+  S->dirty = true;  // the accumulators no longer hold the current particles
+  // reverse pass
+  S->ck(cudaMemsetAsync(a.lam, 0, sizeof(double) * 5 * (size_t)S->slots, s), "memset");
+  for (int k = n - 1; k >= 0 && S->status == APIC_OK; --k) {
+    DevPtrs dg = d;  // the node gradients of step k from its potential
+    dg.phi = a.ck_phi + (size_t)k * tn;
+    dg.G = a.Gk;
+    launch_gradients<Real>(dg, s);
+    S->ck(cudaMemsetAsync(a.lG, 0, sizeof(double) * 2 * tn, s), "memset");
+    S->ck(cudaMemsetAsync(a.lphi, 0, sizeof(double) * tn, s), "memset");
+    launch_adj_rev_inject<Real>(d, a, t, k, S->max_inj, s);
+    launch_adj_rev_push<Real>(d, a, t, k, s);
+    launch_adj_surface(d, a, t, k, s);
+    launch_adj_gradT(d, a, s);
+    launch_adj_to_unknowns(d, a, s);
+    for (int q = 0; q < ni; ++q) {
+      const auto& lv = S->adj_levels[q];
+      for (int l = (int)lv.size() - 1; l >= 0; --l)
+        launch_adj_ndT(a, lv[l].first, lv[l].second, a.unk_off[q], S->adj_smem[q], true, s);
+      for (int l = 0; l < (int)lv.size(); ++l)
+        launch_adj_ndT(a, lv[l].first, lv[l].second, a.unk_off[q], S->adj_smem[q], false, s);
+    }
+    launch_adj_after_solve(d, a, t, k, s);
+    launch_adj_rev_deposit<Real>(d, a, k, s);
+  }
+  if (!S->ck(cudaGetLastError(), "adjoint launch")) return S->status;
+  std::vector<double> hv((size_t)ni * kNOut), hg((size_t)ni * kNPar);
+  S->d2h(hv.data(), a.vals, hv.size());
+  S->d2h(hg.data(), a.grad, hg.size());
+  int rc = read_status(S);
+  if (rc != APIC_OK) return rc;
+  for (size_t q = 0; q < hv.size(); ++q)
+    if (values) values[q] = hv[q] / n;
+  for (size_t q = 0; q < hg.size(); ++q)
+    if (grad) grad[q] = hg[q];
+  return APIC_OK;
+}
+
+extern "C" int apic_adjoint_window(apic_sim* S, int32_t n_steps, const double* dL_dout, double* values,
+                                   double* grad) {
   if (!S || !dL_dout || !grad) return APIC_ERR_INVALID_ARG;
   if (S->status != APIC_OK) return S->status;
   if (n_steps < 1) return APIC_ERR_INVALID_ARG;
-  std::vector<double> J((size_t)S->n_inst * kNOut * kNPar);
-  int rc = apic_sensitivity(S, n_steps, nullptr, J.data());
-  if (rc != APIC_OK) return rc;
-  for (int k = 0; k < S->n_inst; ++k)
-    for (int p = 0; p < kNPar; ++p) {
-      double g = 0.0;
-      for (int o = 0; o < kNOut; ++o) g += dL_dout[k * kNOut + o] * J[((size_t)k * kNOut + o) * kNPar + p];
-      grad[k * kNPar + p] = g;
-    }
-  return APIC_OK;
+  return S->precision == APIC_FP64 ? adjoint_impl<double>(S, n_steps, dL_dout, values, grad)
+                                   : adjoint_impl<float>(S, n_steps, dL_dout, values, grad);
+}
+
+extern "C" int apic_adjoint(apic_sim* S, int32_t n_steps, const double* dL_dout, double* grad) {
+  return apic_adjoint_window(S, n_steps, dL_dout, nullptr, grad);
 }

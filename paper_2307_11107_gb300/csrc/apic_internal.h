@@ -240,6 +240,42 @@ struct TanPtrs {
   double* vals;            // per instance [kNOut]: sums of the outputs over the window
 };
 
+// ---- reverse sweep (adjoint window) ----
+// The forward pass of a K-step window keeps, per step k, the particle state
+// and population counters at the start of the step, the step's rho and phi,
+// each slot's fate in the push and each injection draw's slot; the reverse
+// pass then runs the step's operations backwards, from step K-1 to 0.
+struct AdjPtrs {
+  int K;                   // window steps
+  int pad;
+  int64_t stride;          // particle slots of one component (all populations)
+  void* ck;                // [K][5][stride] particle state at the start of step k (particle precision)
+  PopState* ck_ps;         // [K + 1][n_pop] population counters at the start of step k (k = K: after the window)
+  double* ck_rho;          // [K][total_nodes]
+  double* ck_phi;          // [K][total_nodes]
+  uint8_t* fate;           // [K][stride]: 0 kept, 1 absorbed, 2 escaped, 3 no live particle at the start of the step
+  int64_t* inj;            // [K][n_pop][inj_cap]: slot (from the population's base) of injection draw q of step k;
+                           // -1 absorbed during its first flight, -2 escaped
+  int64_t inj_cap;
+  double* lam;             // [5][stride] adjoint of the particle state
+  double* lG;              // [2][total_nodes] adjoint of the node gradients
+  double* lphi;            // [total_nodes] adjoint of phi
+  double* lrho;            // [total_nodes] adjoint of rho
+  double* rhs;             // transposed solve: right-hand side / solution over every instance's unknowns
+  double* ndw;             // its update vectors
+  void* Gk;                // node gradients of step k (pairs of the particle type)
+  double* seed;            // [n_inst][kNOut] dL / d(output of one step) = dL_dout / K
+  double* grad;            // [n_inst][kNPar] parameter adjoints
+  double* vals;            // [n_inst][kNOut] window sums of the outputs
+  // transposed nested-dissection solve: FP64 fronts of every instance
+  const NdFront* nd_front;
+  const int32_t* nd_idx;
+  const int32_t* nd_gather;
+  const double* nd_mat;
+  int64_t unk_off[kCoopMaxInst + 1];  // first unknown of each instance in rhs
+};
+constexpr int kAdjBlocks = 256;  // CTAs of the reverse particle kernels (fixed: deterministic partial sums)
+
 // ---- launchers (defined in the kernel translation units) ----
 template <class Real>
 void launch_load(const DevPtrs& d, int pop, long long n0, long long count, long long draw0, int kind,
@@ -448,5 +484,28 @@ void launch_tan_b(const DevPtrs& d, const TanPtrs& t, int p, int direct, cudaStr
 void launch_tan_store(const DevPtrs& d, const TanPtrs& t, int p, int direct, cudaStream_t s);
 void launch_tan_surface(const DevPtrs& d, const TanPtrs& t, cudaStream_t s);
 void launch_tan_step_end(const DevPtrs& d, const TanPtrs& t, cudaStream_t s);
+
+// reverse sweep (adjoint.cu)
+template <class Real>
+void launch_adj_fwd_push(const DevPtrs& d, const AdjPtrs& a, int k, cudaStream_t s);
+template <class Real>
+void launch_adj_fwd_inject(const DevPtrs& d, const AdjPtrs& a, const TanPtrs& t, int k, long long max_inj,
+                           cudaStream_t s);
+template <class Real>
+void launch_adj_rev_inject(const DevPtrs& d, const AdjPtrs& a, const TanPtrs& t, int k, long long max_inj,
+                           cudaStream_t s);
+template <class Real>
+void launch_adj_rev_push(const DevPtrs& d, const AdjPtrs& a, const TanPtrs& t, int k, cudaStream_t s);
+template <class Real>
+void launch_adj_rev_deposit(const DevPtrs& d, const AdjPtrs& a, int k, cudaStream_t s);
+void launch_adj_values(const DevPtrs& d, const AdjPtrs& a, cudaStream_t s);
+void launch_adj_surface(const DevPtrs& d, const AdjPtrs& a, const TanPtrs& t, int k, cudaStream_t s);
+void launch_adj_gradT(const DevPtrs& d, const AdjPtrs& a, cudaStream_t s);
+void launch_adj_to_unknowns(const DevPtrs& d, const AdjPtrs& a, cudaStream_t s);
+// the transposed sweeps over one tree level's fronts [f0, f1) of the instance
+// whose unknowns start at unk0 (smem_doubles: its largest s + u)
+void launch_adj_ndT(const AdjPtrs& a, int f0, int f1, long long unk0, int smem_doubles, bool forward, cudaStream_t s);
+void launch_adj_after_solve(const DevPtrs& d, const AdjPtrs& a, const TanPtrs& t, int k, cudaStream_t s);
+const void* adj_ndT_kernel();  // the transposed-sweep kernel (its shared-memory limit is raised at set-up)
 
 }  // namespace apic

@@ -507,12 +507,19 @@ int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u
         if (g >= 0) g = (int32_t)(up.fronts[F.child[c]].W + g);
       }
   }
+  // tiny fronts (s <= 16, u <= 48) go four to a warp, one per 8-lane group
+  auto tiny = [&](const NdFront& F) { return F.s <= kNdTinyS && F.u <= kNdTinyU; };
   auto level_tasks = [&](int l, bool fwd) {
     int q = 0;
     while (q < nf && up.fronts[front0 + q].level != l) ++q;
-    int small = 0;
-    for (int z = q; z < nf && up.fronts[front0 + z].level == l; ++z) small += !large(up.fronts[front0 + z]);
-    const int per = std::max(1, std::min(task_fronts, (small + std::max(1, ctas) - 1) / std::max(1, ctas)));
+    int small = 0, nt = 0;
+    for (int z = q; z < nf && up.fronts[front0 + z].level == l; ++z) {
+      small += !large(up.fronts[front0 + z]);
+      nt += tiny(up.fronts[front0 + z]);
+    }
+    const int c = std::max(1, ctas);
+    const int per = std::max(1, std::min(task_fronts, (small + c - 1) / c));
+    const int per_tiny = std::max(1, std::min(4 * task_fronts, (nt + c - 1) / c));
     while (q < nf && up.fronts[front0 + q].level == l) {
       const NdFront& F = up.fronts[front0 + q];
       if (large(F)) {
@@ -523,13 +530,15 @@ int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u
         ++q;
         continue;
       }
+      const bool t = tiny(F);
+      const int cap = t ? per_tiny : per;
       int n = 0;
-      while (q + n < nf && n < per) {
+      while (q + n < nf && n < cap) {
         const NdFront& G = up.fronts[front0 + q + n];
-        if (G.level != l || large(G)) break;
+        if (G.level != l || large(G) || tiny(G) != t) break;
         ++n;
       }
-      up.tasks.push_back(NdTask{(int)(front0 + q), 0, n, 1});
+      up.tasks.push_back(NdTask{(int)(front0 + q), 0, n, t ? 2 : 1});
       q += n;
     }
   };
@@ -580,14 +589,14 @@ void nd_solve_tables(const NdUpload& up, const NdLevels& lv, int depth, const st
   for (int l = depth; l >= 0; --l)
     for (int t = lv.ft[l]; t < lv.ft[l + 1]; ++t) {
       const NdTask& T = up.tasks[t];
-      if (!T.warp) fwd(up.fronts[T.front], T.r0, T.r0 + T.n);
+      if (T.warp == 0) fwd(up.fronts[T.front], T.r0, T.r0 + T.n);
       else
         for (int k = 0; k < T.n; ++k) fwd(up.fronts[T.front + k], 0, up.fronts[T.front + k].s + up.fronts[T.front + k].u);
     }
   for (int l = 0; l <= depth; ++l)
     for (int t = lv.bt[l]; t < lv.bt[l + 1]; ++t) {
       const NdTask& T = up.tasks[t];
-      if (!T.warp) back(up.fronts[T.front], T.r0, T.r0 + T.n);
+      if (T.warp == 0) back(up.fronts[T.front], T.r0, T.r0 + T.n);
       else
         for (int k = 0; k < T.n; ++k) back(up.fronts[T.front + k], 0, up.fronts[T.front + k].s);
     }

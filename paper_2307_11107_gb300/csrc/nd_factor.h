@@ -73,11 +73,14 @@ void nd_solve_host(const NdFactor& f, const double* r, double* e, bool fp64);
 
 // ---- device tables (what the GPU's nested-dissection tasks read) ----
 // A task of one tree level: rows [r0, r0 + n) of the large front `front`
-// (warp = 0, the whole CTA), or the n small fronts from `front` (warp = 1,
-// one warp each).  Same layout as CUDA's int4.
+// (warp = 0, the whole CTA), the n small fronts from `front` (warp = 1, one
+// warp each), or the n tiny fronts from `front` (warp = 2, four per warp, one
+// per 8-lane group).  Same layout as CUDA's int4.
 struct NdTask {
   int front, r0, n, warp;
 };
+constexpr int kNdTinyS = 16;  // tiny fronts: separator and update set within these sizes
+constexpr int kNdTinyU = 48;
 // Fronts of a batch's instances, sorted by level within each instance, with
 // offsets made global: S, U into idx; G into gather; W into one right-hand
 // side's update vectors; FM, NB into the batch's matrix buffer.

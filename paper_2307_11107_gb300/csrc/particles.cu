@@ -350,6 +350,9 @@ __global__ void __launch_bounds__(256, APIC_PUSH_MIN_BLOCKS) k_push(DevPtrs d, i
   __syncthreads();
   for (int q = 0;; ++q) {
    if (q % GS == 0) {
+     // every warp has read the previous group's index (chunks past the last
+     // one are skipped without a barrier, so warps may drift apart there)
+     __syncthreads();
      if (threadIdx.x == 0) s_gi = (int)atomicAdd((unsigned long long*)(d.cnt + 1), 1ull);
      __syncthreads();
    }
@@ -737,6 +740,7 @@ __global__ void __launch_bounds__(256, APIC_PUSH4_MIN_BLOCKS) k_push4(DevPtrs d,
   const unsigned lane = threadIdx.x & 31;
   for (int q = 0;; ++q) {
     if (q % GS == 0) {
+      __syncthreads();  // every warp has read the previous group's index
       if (threadIdx.x == 0) s_gi = (int)atomicAdd((unsigned long long*)(d.cnt + 1), 1ull);
       __syncthreads();
     }
@@ -807,7 +811,7 @@ __global__ void __launch_bounds__(256, APIC_PUSH4_MIN_BLOCKS) k_push4(DevPtrs d,
       if (it > 0) load(it);
       const int base_local = it * (int)blockDim.x * kPer + (int)threadIdx.x * kPer;  // chunk-local index of particle 0
       unsigned deadm = 0u, absm = 0u, rows_hit = 0u;
-#pragma unroll 1
+#pragma unroll
       for (int k = 0; k < kPer; ++k) {
         const bool active = base_local + k < nleft;
         const float x1 = lane4(st.x1, k);

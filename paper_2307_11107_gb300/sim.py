@@ -215,15 +215,18 @@ class Sim:
         self._check(self._lib.apic_sensitivity(self.h, int(n_steps), vals.ctypes.data_as(dp), jac.ctypes.data_as(dp)))
         return dict(values=vals, jacobian=jac)
 
-    def adjoint(self, n_steps, dL_dout):
+    def adjoint(self, n_steps, dL_dout, values=False):
         """Gradient [instances, 3] of sum(dL_dout * window means) along
-        (alpha, phi_g, B) (apic_adjoint)."""
+        (alpha, phi_g, B) by the reverse sweep (apic_adjoint_window); with
+        values=True also the window means [instances, 5]."""
         ni = len(self.cfgs)
         g = np.ascontiguousarray(np.broadcast_to(np.asarray(dL_dout, dtype=np.float64), (ni, _abi.NOUT)))
         grad = np.zeros((ni, _abi.NPAR))
+        vals = np.zeros((ni, _abi.NOUT))
         dp = C.POINTER(C.c_double)
-        self._check(self._lib.apic_adjoint(self.h, int(n_steps), g.ctypes.data_as(dp), grad.ctypes.data_as(dp)))
-        return grad
+        self._check(self._lib.apic_adjoint_window(self.h, int(n_steps), g.ctypes.data_as(dp), vals.ctypes.data_as(dp),
+                                                  grad.ctypes.data_as(dp)))
+        return (grad, vals) if values else grad
 
     def check_wait_limit(self, limit_ns):
         """apic_check_wait_limit: returns the status code (APIC_ERR_TIMEOUT,
