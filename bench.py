@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--sort-interval", type=int, default=None,
                     help="override the workload's sort interval (steps between particle sorts)")
     ap.add_argument("--autotune", action="store_true",
-                    help="choose the sort interval with apic_autotune after the warm-up (untimed)")
+                    help="choose the sort interval and the push's tiles with apic_autotune after the "
+                         "warm-up (untimed; on by default for batched48)")
     return ap.parse_args()
 
 
@@ -451,8 +452,9 @@ def main():
             sim.load_volume(sp, c["species"][sp]["n_init"], instance=k)
     sim.step(args.warmup)
     tuned = None
-    if args.autotune:
-        tuned = sim.autotune(max(2, args.warmup // 7))[0]
+    if args.autotune or (args.workload == "batched48" and args.sort_interval is None):
+        tuned = sim.autotune(max(8, args.warmup // 4))[0]
+    tiles = sim.stats()
 
     def barrier():
         if pg is not None:
@@ -591,7 +593,8 @@ def main():
                        "grain": "isolated (floating potential)" if cfg.get("floating") else "fixed potential",
                        "dt": cfg["dt"],
                        "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "sort_interval": tuned if tuned is not None else cfg.get("sort_interval", 0)},
+                       "sort_interval": tiles["sort_interval"], "autotuned": tuned is not None,
+                       "push_window_rows": tiles["win_rows"], "push_chunk_group": tiles["chunk_group"]},
             "roofline": roof, "cpu_baseline": cpu, "error_vs_fp64_oracle": perr, "e2e": e2e,
             "gpu_launches": int(launches),
             "poisson_loop_iters": int(loop_iters), "clocks": clk.summary(),

@@ -180,6 +180,8 @@ struct apic_sim {
   long long tab_total = 0;
   TanPtrs tan{};                      // sensitivity-window state (allocated on first use)
   bool tan_ready = false;
+  int win_rows = 0;                   // push deposit window rows (0: default for the grid), set by apic_autotune
+  int chunk_group = 0;                // push chunks per group (0: default), set by apic_autotune
   AdjPtrs adj{};                      // reverse-sweep state (allocated on first use, for up to adj_K steps)
   int adj_K = 0;
   std::vector<std::vector<std::pair<int, int>>> adj_levels;  // per instance, per tree level: fronts [f0, f1)
@@ -1413,19 +1415,30 @@ extern "C" int apic_create(const apic_config_t* cfg, void* stream, const apic_al
   return apic_create_batch(cfg, 1, stream, allocator, out);
 }
 
-extern "C" int apic_destroy(apic_sim* S) {
-  if (!S) return APIC_OK;
-  if (S->stream || S->cap) cudaStreamSynchronize(S->stream);
+// Drop the captured step graphs (the next step captures them again).
+static void drop_graphs(apic_sim* S) {
   for (int q = 0; q < 2; ++q) {
     if (S->exec[q]) cudaGraphExecDestroy(S->exec[q]);
     if (S->graph[q]) cudaGraphDestroy(S->graph[q]);
     if (S->sort_exec[q]) cudaGraphExecDestroy(S->sort_exec[q]);
     if (S->sort_graph[q]) cudaGraphDestroy(S->sort_graph[q]);
+    S->exec[q] = nullptr;
+    S->graph[q] = nullptr;
+    S->sort_exec[q] = nullptr;
+    S->sort_graph[q] = nullptr;
     for (int p = 0; p < APIC_NPHASE; ++p) {
       if (S->phase_exec[q][p]) cudaGraphExecDestroy(S->phase_exec[q][p]);
       if (S->phase_graph[q][p]) cudaGraphDestroy(S->phase_graph[q][p]);
+      S->phase_exec[q][p] = nullptr;
+      S->phase_graph[q][p] = nullptr;
     }
   }
+}
+
+extern "C" int apic_destroy(apic_sim* S) {
+  if (!S) return APIC_OK;
+  if (S->stream || S->cap) cudaStreamSynchronize(S->stream);
+  drop_graphs(S);
   for (int p = 0; p <= APIC_NPHASE; ++p)
     if (S->ev[p]) cudaEventDestroy(S->ev[p]);
   S->dfree_all();
@@ -1521,7 +1534,7 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
         launch_gradients<Real>(d, s);
       }
       break;
-    case 3: launch_push<Real>(d, S->push_grid, S->max_n2, S->chord, s); break;
+    case 3: launch_push<Real>(d, S->push_grid, S->max_n2, S->chord, S->win_rows, S->chunk_group, s); break;
     case 4: launch_inject<Real>(d, S->max_inj, s); break;
     case 5: launch_step_end(d, s); break;
     case 6: launch_sort<Real>(d, S->push_grid, s); break;  // not a step phase: the particle sort
@@ -1661,7 +1674,7 @@ static int step_timed_impl(apic_sim* S, int n) {
       for (int p = 0; p < APIC_NPHASE; ++p)
         if (!capture<Real>(S, S->view(q), p, p + 1, &S->phase_graph[q][p], &S->phase_exec[q][p])) return S->status;
     for (int p = 0; p <= APIC_NPHASE; ++p)
-      if (!S->ck(cudaEventCreate(&S->ev[p]), "event create")) return S->status;
+      if (!S->ev[p] && !S->ck(cudaEventCreate(&S->ev[p]), "event create")) return S->status;
   }
   for (int k = 0; k < n; ++k) {
     if (!launch_step<Real>(S, nullptr)) return S->status;  // sort when due (not timed)
@@ -1717,6 +1730,11 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
   }
   if (S->floating) out->kernels_per_step += 2;  // the isolated grains' correction and the gradients again
   out->timed_steps = S->timed_steps;
+  out->sort_interval = S->sort_interval;
+  out->win_rows = S->win_rows > 0 ? S->win_rows
+                                  : (S->precision == APIC_FP64 ? push_window_rows<double>(S->max_n2)
+                                                               : push_window_rows<float>(S->max_n2));
+  out->chunk_group = S->chunk_group > 0 ? S->chunk_group : 4;
   out->solver = S->plan.bcr.n_inst > 0 ? (S->d.nd_front ? APIC_SOLVER_ND : APIC_SOLVER_BCR)
                                        : (S->coop > 0 ? APIC_SOLVER_MG_COOP : APIC_SOLVER_MG_KERNELS);
   out->sorts = S->sorts;
@@ -1725,9 +1743,11 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
   return APIC_OK;
 }
 
-// Sort-interval autotuning: `trial` steps with each candidate interval (each
-// trial starts with a sort), CUDA events on the simulation's stream; the
-// fastest interval is kept.  Advances the simulation by 7 * trial steps.
+// Autotuning: `trial` steps (whole sort intervals) with each candidate sort
+// interval (each trial starts with a sort), CUDA events on the simulation's
+// stream, the fastest interval kept; then at that interval the push's chunk
+// group and deposit-window rows, one warm-up interval and the timed steps per
+// candidate with the step graphs recaptured.
 static const int kTuneIntervals[APIC_TUNE_CANDIDATES] = {2, 4, 6, 8, 12, 16, 24};
 
 template <class Real>
@@ -1767,11 +1787,55 @@ static int autotune_impl(apic_sim* S, int trial, int32_t* chosen, double* ms_out
       best_c = c;
     }
   }
+  if (S->status != APIC_OK) {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return S->status;
+  }
+  S->sort_interval = best_c;
+  *chosen = best_c;
+  // the push's tiles at that interval: chunks per group, then deposit-window
+  // rows; each candidate recaptures the step graphs and runs whole intervals
+  auto time_steps = [&]() -> double {
+    if (!S->sync() || !ensure_graphs<Real>(S)) return 1e300;
+    const int n = best_c * ((trial + best_c - 1) / best_c);
+    for (int k = 0; k < best_c && S->status == APIC_OK; ++k) launch_step<Real>(S, S->exec);  // warm-up interval
+    S->ck(cudaEventRecord(a, S->stream), "event record");
+    for (int k = 0; k < n && S->status == APIC_OK; ++k) launch_step<Real>(S, S->exec);
+    S->ck(cudaEventRecord(b, S->stream), "event record");
+    if (!S->ck(cudaEventSynchronize(b), "event sync")) return 1e300;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    return (double)ms / n;
+  };
+  const int groups[] = {2, 4, 8};
+  double best_t = 1e300;
+  int best_g = S->chunk_group, best_r = S->win_rows;
+  for (int g : groups) {
+    S->chunk_group = g;
+    drop_graphs(S);
+    const double t = time_steps();
+    if (t < best_t) {
+      best_t = t;
+      best_g = g;
+    }
+  }
+  S->chunk_group = best_g;
+  const int rows_cand[] = {2, 4, 6, 8};
+  for (int r : rows_cand) {
+    S->win_rows = r;
+    drop_graphs(S);
+    const double t = time_steps();
+    if (t < best_t) {
+      best_t = t;
+      best_r = r;
+    }
+  }
+  S->win_rows = best_r;
+  drop_graphs(S);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (S->status != APIC_OK) return S->status;
-  S->sort_interval = best_c;
-  *chosen = best_c;
   return read_status(S);
 }
 

@@ -399,6 +399,45 @@ __device__ __forceinline__ void rows_dot_any(int n4, const float* mat, int strid
   else rows_dot<1>(mat, stride4, row0, row1, v, n4, lane, first, step, fn);
 }
 
+// Rows of a tiny front by the 8-lane group that holds it (four fronts per
+// warp): G lanes per row (G <= 8), 8 / G rows at a time, butterflies inside
+// the group.  Every lane of the warp runs the same trip count (the largest
+// row count of the warp's fronts, nrows_max) so the shuffles stay converged.
+template <int G, class Fn>
+__device__ __forceinline__ void rows_dot_grp(const float* mat, int stride4, int nrows, int nrows_max, const float4* v,
+                                             int n4, int gl, Fn fn) {
+  const int sl = gl & (G - 1), sr = gl / G;
+  for (int a0 = 0; a0 < nrows_max; a0 += 8 / G) {
+    const int a = a0 + sr;
+    float acc = 0.0f;
+    if (a < nrows) {
+      const float4* r = (const float4*)mat + (long long)a * stride4;
+      for (int t = sl; t < n4; t += G) {
+        const float4 m = __ldg(r + t), x = v[t];
+        acc = fmaf(m.x, x.x, fmaf(m.y, x.y, fmaf(m.z, x.z, fmaf(m.w, x.w, acc))));
+      }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if (a < nrows && sl == 0) fn(a, acc);
+  }
+}
+
+template <class Fn>
+__device__ __forceinline__ void rows_dot_grp_any(int Gw, const float* mat, int stride4, int nrows, int nrows_max,
+                                                 const float4* v, int n4, int gl, Fn fn) {
+  if (Gw >= 8) rows_dot_grp<8>(mat, stride4, nrows, nrows_max, v, n4, gl, fn);
+  else if (Gw >= 4) rows_dot_grp<4>(mat, stride4, nrows, nrows_max, v, n4, gl, fn);
+  else if (Gw >= 2) rows_dot_grp<2>(mat, stride4, nrows, nrows_max, v, n4, gl, fn);
+  else rows_dot_grp<1>(mat, stride4, nrows, nrows_max, v, n4, gl, fn);
+}
+
+__device__ __forceinline__ int warp_max(int x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(kFull, x, o));
+  return x;
+}
+
 // Entry p of front F's assembled right-hand side: the residual at its node
 // (separator positions only) plus what its children's update vectors hold
 // for it, in the order child 0, child 1.
@@ -459,6 +498,55 @@ __device__ bool run_nd(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int
       for (int p = threadIdx.x; p < F.up; p += blockDim.x) v[p] = p < F.u ? e[d.nd_idx[F.U + p]] : 0.0f;
       __syncthreads();
       nd_back_rows(d, F, T.y, T.y + T.z, v, e, x, B.N, lane, warp, kBcrWarps);
+    }
+    __syncthreads();
+    return true;
+  }
+  if (T.w == 2) {
+    // tiny fronts, four per warp: group g = lane / 8 takes front
+    // T.x + 4 (warp + kBcrWarps i) + g, its vector at kNdTinyU floats of the
+    // warp's area
+    const int g = lane >> 3, gl = lane & 7;
+    float* vg = c.red + warp * (kNdWarpMaxS + kNdWarpMaxU) + g * kNdTinyU;
+    for (int k0 = 4 * warp; k0 < T.z; k0 += 4 * kBcrWarps) {
+      const int k = k0 + g;
+      const bool has = k < T.z;
+      NdFront F;
+      if (has) F = d.nd_front[T.x + k];
+      const int len = !has ? 0 : (kind == kNdFwd ? F.sp : F.up);
+      for (int p = gl; p < len; p += 8) {
+        if (kind == kNdFwd) vg[p] = p < F.s ? nd_rhs(d, F, p, f, wb) : 0.0f;
+        else vg[p] = p < F.u ? e[d.nd_idx[F.U + p]] : 0.0f;
+      }
+      __syncwarp();
+      const int n4 = len >> 2;
+      const int Gf = n4 <= 1 ? 1 : (n4 <= 2 ? 2 : (n4 <= 4 ? 4 : 8));
+      const int Gw = warp_max(has ? Gf : 1);
+      if (kind == kNdFwd) {
+        const int nrows = has ? F.s + F.u : 0;
+        rows_dot_grp_any(Gw, has ? (const float*)d.bcr + F.FM : (const float*)d.bcr, n4, nrows, warp_max(nrows),
+                         (const float4*)vg, n4, gl, [&](int a, float acc) {
+                           if (a < F.s) e[d.nd_idx[F.S + a]] = acc;
+                           else wb[F.W + a - F.s] = nd_rhs(d, F, a, f, wb) - acc;
+                         });
+      } else {
+        const int nrows = has ? F.s : 0;
+        if (warp_max(has && F.u > 0 ? 1 : 0)) {
+          rows_dot_grp_any(Gw, has ? (const float*)d.bcr + F.NB : (const float*)d.bcr, n4, nrows, warp_max(nrows),
+                           (const float4*)vg, n4, gl, [&](int a, float acc) {
+                             const int u = d.nd_idx[F.S + a];
+                             const float val = e[u] - (F.u > 0 ? acc : 0.0f);
+                             e[u] = val;
+                             x[(long long)u + B.N] += (double)val;
+                           });
+        } else {
+          for (int a = gl; a < nrows; a += 8) {
+            const int u = d.nd_idx[F.S + a];
+            x[(long long)u + B.N] += (double)e[u];
+          }
+        }
+      }
+      __syncwarp();
     }
     __syncthreads();
     return true;

@@ -1534,19 +1534,21 @@ int push_window_rows<Real>(int max_n2) {
 }
 
 template <>
-void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, bool chord, cudaStream_t s) {
+void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, bool chord, int win_rows, int chunk_group,
+                       cudaStream_t s) {
   const int win_n2 = max_n2 < kWinMaxN2 - 1 ? max_n2 : kWinMaxN2 - 1;
-  const int rows = push_window_rows<Real>(max_n2);
+  const int rows = win_rows > 0 ? std::max(2, std::min(kWinRows, win_rows)) : push_window_rows<Real>(max_n2);
   const int sm = push_smem(rows, win_n2, d.n_pop);
   const bool v4 = push4();
   const void* kern = v4 ? (chord ? (const void*)k_push4<true> : (const void*)k_push4<false>)
                         : (chord ? (const void*)k_push<true> : (const void*)k_push<false>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  static int group = -1;  // chunks per group (APIC_PUSH_GROUP, default 4: the fastest of 1, 2, 4, 8 measured)
-  if (group < 0) {
+  static int group_env = -1;  // chunks per group (APIC_PUSH_GROUP, default 4: the fastest of 1, 2, 4, 8 measured)
+  if (group_env < 0) {
     const char* e = std::getenv("APIC_PUSH_GROUP");
-    group = e ? std::max(1, std::atoi(e)) : 4;
+    group_env = e ? std::max(1, std::atoi(e)) : 4;
   }
+  const int group = chunk_group > 0 ? chunk_group : group_env;
   cudaMemsetAsync(d.cnt + 1, 0, sizeof(long long), s);  // the group counter
   if (v4) {
     grid = std::max(1, grid / 4 * (int)APIC_PUSH4_MIN_BLOCKS);  // the caller's grid is 4 CTAs per SM

@@ -34,8 +34,9 @@ def test_struct_layout_matches_header():
     #include <stddef.h>
     #include "apic.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu %zu\n", sizeof(apic_config_t), sizeof(apic_tallies_t), sizeof(apic_species_t),
-             offsetof(apic_config_t, seed), offsetof(apic_config_t, poisson_tol), offsetof(apic_tallies_t, step));
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(apic_config_t), sizeof(apic_tallies_t), sizeof(apic_species_t),
+             offsetof(apic_config_t, seed), offsetof(apic_config_t, poisson_tol), offsetof(apic_tallies_t, step),
+             sizeof(apic_stats_t), offsetof(apic_stats_t, chunk_group));
       return 0;
     }'''
     with tempfile.TemporaryDirectory() as td:
@@ -45,7 +46,8 @@ def test_struct_layout_matches_header():
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         vals = list(map(int, subprocess.check_output([exe]).split()))
     exp = [ctypes.sizeof(_abi.Config), ctypes.sizeof(_abi.Tallies), ctypes.sizeof(_abi.Species),
-           _abi.Config.seed.offset, _abi.Config.poisson_tol.offset, _abi.Tallies.step.offset]
+           _abi.Config.seed.offset, _abi.Config.poisson_tol.offset, _abi.Tallies.step.offset,
+           ctypes.sizeof(_abi.Stats), _abi.Stats.chunk_group.offset]
     assert vals == exp
 
 

@@ -98,8 +98,9 @@ def test_batched_reduction_poisson_matches_banded_lu(direct, monkeypatch):
 
 
 def test_autotune_keeps_a_candidate_and_stepping_stays_valid():
-    """The sort-interval autotuner times every candidate, keeps the fastest
-    and leaves a simulation that steps on with consistent counts."""
+    """The autotuner times every sort interval, keeps the fastest, tunes the
+    push's tiles at it and leaves a simulation that steps on with consistent
+    counts."""
     import paper_2307_11107_gb300 as apic
     apic.build()
     cfgs = _instances("fp32")
@@ -111,11 +112,16 @@ def test_autotune_keeps_a_candidate_and_stepping_stays_valid():
     chosen, ms = s.autotune(4)
     assert chosen in ms and all(v > 0.0 for v in ms.values())
     assert ms[chosen] == min(ms.values())
+    st = s.stats()
+    assert st["sort_interval"] == chosen
+    assert st["chunk_group"] in (2, 4, 8) and st["win_rows"] in (2, 4, 6, 8)
     s.step(5)
     for k in range(len(cfgs)):
         t = s.tallies(k)
-        # each candidate runs whole intervals: c * ceil(4 / c) steps
-        assert t["step"] == 4 + sum(c * -(-4 // c) for c in ms) + 5
+        # each interval candidate runs whole intervals, c * ceil(4 / c) steps;
+        # each of the 3 + 4 tile candidates one warm-up interval and as many
+        tiles = 7 * (chosen + chosen * -(-4 // chosen))
+        assert t["step"] == 4 + sum(c * -(-4 // c) for c in ms) + tiles + 5
         for sp in (0, 1):
             cnt = t["counts"][sp]
             assert cnt["resident"] == s.particles(sp, instance=k).shape[0]
