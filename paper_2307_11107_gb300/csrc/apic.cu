@@ -984,12 +984,15 @@ static int setup(apic_sim* S) {
       ndu = NdUpload();
       nd_w = 0;
       int nd_need = 0;
-      int nd_ctas = 0;  // CTAs of the solve (small fronts are spread over them)
+      int sms = 0;  // CTAs of the solve: an instance's small fronts are spread over its share
       {
         int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nd_ctas, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       }
+      double nd_nodes = 0.0;
+      for (int k = 0; k < ni; ++k)
+        if (use_nd[k]) nd_nodes += (double)S->inst[k].nodes;
       for (int k = 0; k < ni && want; ++k) {
         BcrInst& B = bcr_in[k];
         auto up = [](long long v) { return (v + 63) & ~63ll; };  // 256-byte aligned ranges
@@ -1001,8 +1004,11 @@ static int setup(apic_sim* S) {
           B.Np = (B.N + 3) & ~3;
           B.base = off;
           NdLevels lvl;
-          nd_need = std::max(nd_need, nd_layout(nds[k], off, nd_w, kNdWarpMaxS, kNdWarpMaxU, kNdTaskFloats,
-                                                kNdTaskFronts, nd_ctas, ndu, lvl));
+          // the share of the CTAs by nodes (the sums do not depend on the
+          // task layout: an instance computes the same alone or in a batch)
+          const int nd_ctas = std::max(1, (int)std::lround(sms * (double)I.nodes / nd_nodes));
+          nd_need = std::max(nd_need, nd_layout(nds[k], off, nd_w, kNdWarpMaxS, kNdWarpMaxU, kNdWarpStage, kNdTaskFloats,
+                                                kNdTaskFronts, kNdStageFloats, nd_ctas, ndu, lvl));
           B.nd = 1;
           B.nd_depth = nds[k].depth;
           for (int l = 0; l <= nds[k].depth + 1; ++l) {
@@ -2360,7 +2366,8 @@ static bool adjoint_setup(apic_sim* S, int K) {
     }
     const int f0 = (int)up.fronts.size();
     NdLevels lv;
-    nd_layout(fs[k], mat, w, kNdWarpMaxS, kNdWarpMaxU, kNdTaskFloats, kNdTaskFronts, 1, up, lv);
+    nd_layout(fs[k], mat, w, kNdWarpMaxS, kNdWarpMaxU, kNdWarpStage, kNdTaskFloats, kNdTaskFronts, kNdStageFloats, 1, up,
+              lv);
     mat0[k] = mat;
     mat += fs[k].fm_total + fs[k].nb_total;
     w += fs[k].w_total;

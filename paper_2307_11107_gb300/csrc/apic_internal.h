@@ -360,6 +360,11 @@ constexpr int kNdWarpMaxS = 64;     // fronts with a separator up to this size r
 constexpr int kNdWarpMaxU = 192;    // ... and an update set up to this size
 constexpr int kNdTaskFloats = 16384;  // matrix floats per task of a large front (row chunks)
 constexpr int kNdTaskFronts = 16;     // small fronts per task at most (one per warp)
+constexpr int kNdTaskRows = 4096;     // rows per task of a large front at most (kNdTaskFloats / 4)
+constexpr int kNdWarpStage = 2048;    // matrix floats of a warp's front (staged in shared memory) at most
+constexpr int kNdStageFloats = 16 * kNdWarpStage;  // a task's staged matrix rows at most (16 warps per CTA)
+static_assert(kNdTaskFloats <= kNdStageFloats && kNdWarpStage * kNdTaskFronts <= kNdStageFloats, "tasks stage whole");
+static_assert(kNdTaskFloats / 4 <= kNdTaskRows, "a task of 4-float rows fits");
 struct BcrInst {
   int K;                    // 2^K >= n1
   int N;                    // block size N2
@@ -396,7 +401,8 @@ struct BcrPlan {
   int smem;                 // 1: dynamic shared memory holds staged blocks
   int resident;             // 1: the whole reduction fits in L2 (dense level 1, blocks staged in shared memory)
   int dyn;                  // dynamic shared memory bytes of the solve kernel
-  int wide;                 // 1: some block is larger than kBcrMaxN (the wide kernel)
+  int wide;                 // solve kernel: 0 narrow reduction, 1 wide reduction (some block larger than
+                            // kBcrMaxN, or reduction and nested dissection), 2 nested dissection alone
   int64_t bytes;            // device bytes of all blocks and tail inverses
   int64_t chunks;           // partial-sum ranges of all instances (kBcrSub nodes each)
   int64_t rows;             // floats of one right-hand side's rows in bcr_f / bcr_e (all instances)

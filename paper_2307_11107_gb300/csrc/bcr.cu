@@ -34,6 +34,16 @@ constexpr int kBcrWarps = kBcrThreads / 32;
 constexpr int kTailChunk = 16;      // tail rows per task at most (one per warp)
 constexpr int kUpdRows = kBcrUpdRows;
 constexpr int kRangesPerPass = kBcrThreads / kBcrSub;  // partial-sum ranges a CTA covers at once
+// shared memory of the nested-dissection tasks (the wide kernel's reduction
+// buffer, kBcrWarps x kBcrMaxNWide floats): a large front's vector
+// (kNdVecCap floats) and its task's rows after it; a small front's v_S, z_S
+// and U rows (kNdWarpArea floats per warp); a tiny front's (kNdTinyArea per
+// 8-lane group, four groups per warp)
+constexpr int kNdVecCap = kBcrWarps * kBcrMaxNWide - kNdTaskRows;
+static_assert(kNdStageFloats == kBcrWarps * kNdWarpStage && kNdTaskFronts <= kBcrWarps, "one front per warp");
+constexpr int kNdWarpArea = 2 * kNdWarpMaxS + kNdWarpMaxU;
+constexpr int kNdTinyArea = 2 * kNdTinyS + kNdTinyU;
+static_assert(kNdWarpArea <= kBcrMaxNWide && 4 * kNdTinyArea <= kNdWarpArea && kNdTinyArea % 4 == 0, "areas");
 static_assert(kRangesPerPass * kBcrSub == kBcrThreads, "whole ranges per pass");
 
 // ---- bulk asynchronous copies (global -> shared, completion on an mbarrier) ----
@@ -363,73 +373,91 @@ __device__ bool run_stage(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, 
 }
 
 // ---- nested dissection (BcrInst::nd) ----
-// Dot products of matrix rows (row-major, 16-byte aligned rows of n4 float4)
-// with a vector in shared memory: G lanes per row, 32 / G rows per warp at a
-// time, partial sums added in a fixed butterfly (the result does not depend
-// on the CTA or the batch).  fn(row, value) is called by the first lane of
-// each row's group.
+// Every task runs in three stages, each a round of independent loads: (1) the
+// vectors (v_S and the U rows' right-hand sides forward, x_U backward) into
+// shared memory; (2) the matrix rows' dot products into shared memory; (3)
+// the results scattered to their nodes.  No load waits on another except the
+// index-then-value pairs of the gathers, which are issued in batches.
+
+// Dot products of matrix rows staged in shared memory (row-major, 16-byte
+// aligned rows of n4 float4; row a at mat + (a - base) stride4 float4) with a
+// vector in shared memory: G lanes per row, 32 / G rows per warp pass and U
+// passes in flight, partial sums added in a fixed butterfly (the result does
+// not depend on the CTA or the batch).  Rows past row1 load the last row
+// (branch-free loads) and are not reported.  fn(row, value) is called by the
+// first lane of each row's group.
 template <int G, class Fn>
-__device__ __forceinline__ void rows_dot(const float* mat, int stride4, int row0, int row1, const float4* v, int n4,
-                                         int lane, int first, int step, Fn fn) {
+__device__ __forceinline__ void rows_dot(const float* mat, int stride4, int row0, int row1, int base, const float4* v,
+                                         int n4, int lane, int first, int step, Fn fn) {
+  constexpr int R = 32 / G, U = G >= 16 ? 2 : 4;
   const int gl = lane & (G - 1), gr = lane / G;
-  for (int a0 = row0 + first * (32 / G); a0 < row1; a0 += step * (32 / G)) {
-    const int a = a0 + gr;
-    float acc = 0.0f;
-    if (a < row1) {
-      const float4* r = (const float4*)mat + (long long)a * stride4;
-      for (int t = gl; t < n4; t += G) {
-        const float4 m = __ldg(r + t), x = v[t];
-        acc = fmaf(m.x, x.x, fmaf(m.y, x.y, fmaf(m.z, x.z, fmaf(m.w, x.w, acc))));
-      }
+  const int pass = step * R;
+  const float4* m4 = (const float4*)mat;
+  for (int a0 = row0 + first * R; a0 < row1; a0 += U * pass) {
+    float acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = 0.0f;
+    for (int t = gl; t < n4; t += G) {
+      const float4 x = v[t];
+      float4 m[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) m[u] = m4[(long long)(min(a0 + u * pass + gr, row1 - 1) - base) * stride4 + t];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        acc[u] = fmaf(m[u].x, x.x, fmaf(m[u].y, x.y, fmaf(m[u].z, x.z, fmaf(m[u].w, x.w, acc[u]))));
     }
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    if (a < row1 && gl == 0) fn(a, acc);
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(kFull, acc[u], o);
+      const int a = a0 + u * pass + gr;
+      if (a < row1 && gl == 0) fn(a, acc[u]);
+    }
   }
 }
 
 template <class Fn>
-__device__ __forceinline__ void rows_dot_any(int n4, const float* mat, int stride4, int row0, int row1, const float4* v,
-                                             int lane, int first, int step, Fn fn) {
-  if (n4 >= 32) rows_dot<32>(mat, stride4, row0, row1, v, n4, lane, first, step, fn);
-  else if (n4 > 8) rows_dot<16>(mat, stride4, row0, row1, v, n4, lane, first, step, fn);
-  else if (n4 > 4) rows_dot<8>(mat, stride4, row0, row1, v, n4, lane, first, step, fn);
-  else if (n4 > 2) rows_dot<4>(mat, stride4, row0, row1, v, n4, lane, first, step, fn);
-  else if (n4 > 1) rows_dot<2>(mat, stride4, row0, row1, v, n4, lane, first, step, fn);
-  else rows_dot<1>(mat, stride4, row0, row1, v, n4, lane, first, step, fn);
+__device__ __forceinline__ void rows_dot_any(int n4, const float* mat, int stride4, int row0, int row1, int base,
+                                             const float4* v, int lane, int first, int step, Fn fn) {
+  if (n4 > 16) rows_dot<32>(mat, stride4, row0, row1, base, v, n4, lane, first, step, fn);
+  else if (n4 > 8) rows_dot<16>(mat, stride4, row0, row1, base, v, n4, lane, first, step, fn);
+  else if (n4 > 4) rows_dot<8>(mat, stride4, row0, row1, base, v, n4, lane, first, step, fn);
+  else rows_dot<4>(mat, stride4, row0, row1, base, v, n4, lane, first, step, fn);
 }
 
 // Rows of a tiny front by the 8-lane group that holds it (four fronts per
-// warp): G lanes per row (G <= 8), 8 / G rows at a time, butterflies inside
-// the group.  Every lane of the warp runs the same trip count (the largest
-// row count of the warp's fronts, nrows_max) so the shuffles stay converged.
+// warp): G lanes per row (G <= 8), 8 / G rows per group pass, four passes in
+// flight, butterflies inside the group.  Every lane of the warp runs the same
+// trip count (the largest row count of the warp's fronts, nrows_max) so the
+// shuffles stay converged; a group without rows (nrows = 0) loads nothing.
 template <int G, class Fn>
 __device__ __forceinline__ void rows_dot_grp(const float* mat, int stride4, int nrows, int nrows_max, const float4* v,
                                              int n4, int gl, Fn fn) {
+  constexpr int R = 8 / G, U = 4;
   const int sl = gl & (G - 1), sr = gl / G;
-  for (int a0 = 0; a0 < nrows_max; a0 += 8 / G) {
-    const int a = a0 + sr;
-    float acc = 0.0f;
-    if (a < nrows) {
-      const float4* r = (const float4*)mat + (long long)a * stride4;
-      for (int t = sl; t < n4; t += G) {
-        const float4 m = __ldg(r + t), x = v[t];
-        acc = fmaf(m.x, x.x, fmaf(m.y, x.y, fmaf(m.z, x.z, fmaf(m.w, x.w, acc))));
-      }
+  const float4* m4 = (const float4*)mat;
+  const int n4g = nrows > 0 ? n4 : 0;
+  for (int a0 = 0; a0 < nrows_max; a0 += U * R) {
+    float acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = 0.0f;
+    for (int t = sl; t < n4g; t += G) {
+      const float4 x = v[t];
+      float4 m[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) m[u] = m4[(long long)min(a0 + u * R + sr, nrows - 1) * stride4 + t];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        acc[u] = fmaf(m[u].x, x.x, fmaf(m[u].y, x.y, fmaf(m[u].z, x.z, fmaf(m[u].w, x.w, acc[u]))));
     }
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    if (a < nrows && sl == 0) fn(a, acc);
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(kFull, acc[u], o);
+      const int a = a0 + u * R + sr;
+      if (a < nrows && sl == 0) fn(a, acc[u]);
+    }
   }
-}
-
-template <class Fn>
-__device__ __forceinline__ void rows_dot_grp_any(int Gw, const float* mat, int stride4, int nrows, int nrows_max,
-                                                 const float4* v, int n4, int gl, Fn fn) {
-  if (Gw >= 8) rows_dot_grp<8>(mat, stride4, nrows, nrows_max, v, n4, gl, fn);
-  else if (Gw >= 4) rows_dot_grp<4>(mat, stride4, nrows, nrows_max, v, n4, gl, fn);
-  else if (Gw >= 2) rows_dot_grp<2>(mat, stride4, nrows, nrows_max, v, n4, gl, fn);
-  else rows_dot_grp<1>(mat, stride4, nrows, nrows_max, v, n4, gl, fn);
 }
 
 __device__ __forceinline__ int warp_max(int x) {
@@ -438,48 +466,110 @@ __device__ __forceinline__ int warp_max(int x) {
   return x;
 }
 
-// Entry p of front F's assembled right-hand side: the residual at its node
-// (separator positions only) plus what its children's update vectors hold
-// for it, in the order child 0, child 1.
-__device__ __forceinline__ float nd_rhs(const DevPtrs& d, const NdFront& F, int p, const float* f, const float* w) {
-  const int2 g = *(const int2*)(d.nd_gather + F.G + 2 * p);  // absolute offsets into w (-1: none)
-  float v = p < F.s ? f[d.nd_idx[F.S + p]] : 0.0f;
-  if (g.x >= 0) v += w[g.x];
-  if (g.y >= 0) v += w[g.y];
-  return v;
-}
-
-// Forward rows [r0, r1) of front F with its v_S in vs (sp floats, zero
-// padded): rows below s give z_S into e, the others W = v_U - M v_S.
-__device__ __forceinline__ void nd_fwd_rows(const DevPtrs& d, const NdFront& F, int r0, int r1, const float* vs,
-                                            const float* f, float* e, float* w, int lane, int first, int step) {
-  rows_dot_any(F.sp >> 2, (const float*)d.bcr + F.FM, F.sp >> 2, r0, r1, (const float4*)vs, lane, first, step,
-               [&](int a, float acc) {
-                 if (a < F.s) e[d.nd_idx[F.S + a]] = acc;
-                 else w[F.W + a - F.s] = nd_rhs(d, F, a, f, w) - acc;
-               });
-}
-
-// Backward rows [r0, r1) of front F with x_U in xu (up floats, zero padded):
-// x_S = z_S - N x_U into e, and x += e at the node.
-__device__ __forceinline__ void nd_back_rows(const DevPtrs& d, const NdFront& F, int r0, int r1, const float* xu,
-                                             float* e, double* x, int N, int lane, int first, int step) {
-  auto put = [&](int a, float acc) {
-    const int u = d.nd_idx[F.S + a];
-    const float val = e[u] - acc;
-    e[u] = val;
-    x[(long long)u + N] += (double)val;
-  };
-  if (F.u == 0) {
-    for (int a = r0 + first * 32 + lane; a < r1; a += step * 32) put(a, 0.0f);
-    return;
+// out[k] = entry p0 + k of front F's assembled right-hand side for k < n
+// (pad: zeros up to n_pad), by the threads `lane` + multiples of `stride`:
+// the residual at its node (separator positions p < s only) plus what its
+// children's update vectors hold for it, child 0 then child 1.  Four
+// entries per thread in flight: their table entries first, then the values.
+__device__ __forceinline__ void nd_rhs_into(const DevPtrs& d, const NdFront& F, int p0, int n, int n_pad, float* out,
+                                            const float* f, const float* w, int lane, int stride) {
+  constexpr int U = 4;
+  for (int b = lane; b < n_pad; b += U * stride) {
+    int2 g[U];
+    int ix[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = b + u * stride, p = p0 + k;
+      g[u] = k < n ? *(const int2*)(d.nd_gather + F.G + 2 * p) : make_int2(-1, -1);  // absolute offsets into w
+      ix[u] = k < n && p < F.s ? d.nd_idx[F.S + p] : -1;
+    }
+    float val[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      float x = ix[u] >= 0 ? f[ix[u]] : 0.0f;
+      if (g[u].x >= 0) x += w[g[u].x];
+      if (g[u].y >= 0) x += w[g[u].y];
+      val[u] = x;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (b + u * stride < n_pad) out[b + u * stride] = val[u];
   }
-  rows_dot_any(F.up >> 2, (const float*)d.bcr + F.NB, F.up >> 2, r0, r1, (const float4*)xu, lane, first, step, put);
 }
 
-// One task of a nested-dissection phase of instance B: either rows
-// [T.y, T.y + T.z) of the large front T.x (the whole CTA), or the T.z small
-// fronts from T.x (one warp each, per-warp vectors in red).
+// out[k] = e at update-set node k of F (k < u; zeros up to n_pad).
+__device__ __forceinline__ void nd_xu_into(const DevPtrs& d, const NdFront& F, int n_pad, float* out, const float* e,
+                                           int lane, int stride) {
+  constexpr int U = 4;
+  for (int b = lane; b < n_pad; b += U * stride) {
+    int ix[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) ix[u] = b + u * stride < F.u ? d.nd_idx[F.U + b + u * stride] : -1;
+    float val[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) val[u] = ix[u] >= 0 ? e[ix[u]] : 0.0f;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (b + u * stride < n_pad) out[b + u * stride] = val[u];
+  }
+}
+
+// Forward results of F's rows [r0, r1) held in res (row a at res[a - r0]):
+// z_S into e at the separator's nodes, W = v_U - M v_S into F's update vector.
+__device__ __forceinline__ void nd_fwd_store(const DevPtrs& d, const NdFront& F, int r0, int r1, const float* res,
+                                             float* e, float* w, int lane, int stride) {
+  constexpr int U = 4;
+  for (int b = r0 + lane; b < r1; b += U * stride) {
+    int ix[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int a = b + u * stride;
+      ix[u] = a < r1 && a < F.s ? d.nd_idx[F.S + a] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int a = b + u * stride;
+      if (ix[u] >= 0) e[ix[u]] = res[a - r0];
+      else if (a < r1) w[F.W + a - F.s] = res[a - r0];
+    }
+  }
+}
+
+// Backward results for F's separator rows [r0, r1), res[a - r0] = (N x_U)_a
+// (null when u = 0): x_S = z_S - N x_U into e, and x += x_S at the node.
+__device__ __forceinline__ void nd_back_store(const DevPtrs& d, const NdFront& F, int r0, int r1, const float* res,
+                                              float* e, double* x, int N, int lane, int stride) {
+  constexpr int U = 4;
+  for (int b = r0 + lane; b < r1; b += U * stride) {
+    int ix[U];
+    float z[U];
+    double xo[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) ix[u] = b + u * stride < r1 ? d.nd_idx[F.S + b + u * stride] : -1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      z[u] = ix[u] >= 0 ? e[ix[u]] : 0.0f;
+      xo[u] = ix[u] >= 0 ? x[(long long)ix[u] + N] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (ix[u] < 0) continue;
+      const float val = z[u] - (res ? res[b + u * stride - r0] : 0.0f);
+      e[ix[u]] = val;
+      x[(long long)ix[u] + N] = xo[u] + (double)val;
+    }
+  }
+}
+
+// One task of a nested-dissection phase of instance B: rows [T.y, T.y + T.z)
+// of the large front T.x (T.w = 0, the whole CTA), the T.z <= kBcrWarps small
+// fronts from T.x (T.w = 1, one per warp) or the T.z <= 4 kBcrWarps tiny
+// fronts from T.x (T.w = 2, one per 8-lane group).  A task's matrix rows are
+// one contiguous range (the fronts' matrices are stored level by level in
+// task order, within kNdStageFloats), staged into the dynamic shared memory
+// by one bulk copy issued before the vectors are gathered; the vectors live in the wide kernel's
+// reduction buffer (a large front's at [0, kNdVecCap) and its task rows'
+// values after it; kNdWarpArea floats per warp, kNdTinyArea per 8-lane group).
 __device__ bool run_nd(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int l, int q, float* fb, float* eb,
                        double* xb, float* wb) {
   const float* f = fb + B.foff;
@@ -487,86 +577,167 @@ __device__ bool run_nd(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int
   double* x = xb + B.node_off;
   const int4 T = d.nd_task[(kind == kNdFwd ? B.nd_ft[l] : B.nd_bt[l]) + q];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool fwd = kind == kNdFwd;
+  const float* mat = (const float*)d.bcr;
+  // the task's matrix range [m0, m1)
+  long long m0, m1;
+  {
+    const NdFront F0 = d.nd_front[T.x];
+    if (T.w == 0) {
+      const int width = fwd ? F0.sp : F0.up;
+      m0 = (fwd ? F0.FM : F0.NB) + (long long)T.y * width;
+      m1 = m0 + (fwd || F0.u > 0 ? (long long)T.z * width : 0);
+    } else {
+      const NdFront FL = d.nd_front[T.x + T.z - 1];
+      m0 = fwd ? F0.FM : F0.NB;
+      m1 = fwd ? FL.FM + (long long)(FL.s + FL.u) * FL.sp : FL.NB + (long long)FL.s * FL.up;
+    }
+  }
+  // the layout keeps every task within the stage (kNdStageFloats): a larger
+  // one is a table fault, reported as a capacity error and not computed
+  if (m1 - m0 > kNdStageFloats) {
+    if (threadIdx.x == 0) atomicOr(c.err, kErrCapacity);
+    return true;
+  }
+  const bool staged = m1 > m0;
+  if (staged && threadIdx.x == 0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the earlier tasks' reads
+    mbar_expect_tx(c.bar, (unsigned)(m1 - m0) * 4u);
+    bulk_g2s(c.sbuf, mat + m0, (unsigned)(m1 - m0) * 4u, c.bar);
+  }
+  // matrix float o of the buffer in the stage
+  auto at = [&](long long o) { return c.sbuf + (o - m0); };
+  auto wait = [&]() {
+    if (!staged) return true;
+    if (!mbar_wait(c.bar, c.parity, c.err)) return false;
+    c.parity ^= 1u;
+    return true;
+  };
   if (T.w == 0) {
     const NdFront F = d.nd_front[T.x];
     float* v = c.red;
-    if (kind == kNdFwd) {
-      for (int p = threadIdx.x; p < F.sp; p += blockDim.x) v[p] = p < F.s ? nd_rhs(d, F, p, f, wb) : 0.0f;
+    float* res = c.red + kNdVecCap;
+    const int r0 = T.y, r1 = T.y + T.z;
+    if (fwd) {
+      nd_rhs_into(d, F, 0, F.s, F.sp, v, f, wb, threadIdx.x, blockDim.x);
+      const int u0 = max(r0, F.s);  // the task's U rows start with their right-hand sides
+      if (u0 < r1) nd_rhs_into(d, F, u0, r1 - u0, r1 - u0, res + (u0 - r0), f, wb, threadIdx.x, blockDim.x);
       __syncthreads();
-      nd_fwd_rows(d, F, T.y, T.y + T.z, v, f, e, wb, lane, warp, kBcrWarps);
+      if (!wait()) return false;
+      const int fs = F.s;
+      rows_dot_any(F.sp >> 2, at(m0), F.sp >> 2, r0, r1, r0, (const float4*)v, lane, warp, kBcrWarps,
+                  [=](int a, float acc) { res[a - r0] = a < fs ? acc : res[a - r0] - acc; });
+      __syncthreads();
+      nd_fwd_store(d, F, r0, r1, res, e, wb, threadIdx.x, blockDim.x);
     } else {
-      for (int p = threadIdx.x; p < F.up; p += blockDim.x) v[p] = p < F.u ? e[d.nd_idx[F.U + p]] : 0.0f;
+      nd_xu_into(d, F, F.up, v, e, threadIdx.x, blockDim.x);
       __syncthreads();
-      nd_back_rows(d, F, T.y, T.y + T.z, v, e, x, B.N, lane, warp, kBcrWarps);
+      if (!wait()) return false;
+      if (F.u > 0)
+        rows_dot_any(F.up >> 2, at(m0), F.up >> 2, r0, r1, r0, (const float4*)v, lane, warp, kBcrWarps,
+                    [=](int a, float acc) { res[a - r0] = acc; });
+      __syncthreads();
+      nd_back_store(d, F, r0, r1, F.u > 0 ? res : nullptr, e, x, B.N, threadIdx.x, blockDim.x);
     }
     __syncthreads();
     return true;
   }
   if (T.w == 2) {
-    // tiny fronts, four per warp: group g = lane / 8 takes front
-    // T.x + 4 (warp + kBcrWarps i) + g, its vector at kNdTinyU floats of the
-    // warp's area
+    // tiny fronts: group g = lane / 8 of warp w takes front T.x + 4 w + g.
+    // Its rows go G = 4 lanes to a row forward (sp <= kNdTinyS = 16: at most
+    // four float4), 8 backward (up <= kNdTinyU = 48): the sums do not depend
+    // on the other fronts of the warp
     const int g = lane >> 3, gl = lane & 7;
-    float* vg = c.red + warp * (kNdWarpMaxS + kNdWarpMaxU) + g * kNdTinyU;
-    for (int k0 = 4 * warp; k0 < T.z; k0 += 4 * kBcrWarps) {
-      const int k = k0 + g;
-      const bool has = k < T.z;
-      NdFront F;
-      if (has) F = d.nd_front[T.x + k];
-      const int len = !has ? 0 : (kind == kNdFwd ? F.sp : F.up);
-      for (int p = gl; p < len; p += 8) {
-        if (kind == kNdFwd) vg[p] = p < F.s ? nd_rhs(d, F, p, f, wb) : 0.0f;
-        else vg[p] = p < F.u ? e[d.nd_idx[F.U + p]] : 0.0f;
+    float* a0 = c.red + warp * kNdWarpArea + g * kNdTinyArea;
+    const int k = 4 * warp + g;
+    const bool has = k < T.z;
+    NdFront F;
+    if (has) F = d.nd_front[T.x + k];
+    const int n4 = has ? (fwd ? F.sp : F.up) >> 2 : 0;
+    const int nrows = !has ? 0 : (fwd ? F.s + F.u : (F.u > 0 ? F.s : 0));
+    const int nmax = warp_max(nrows);
+    if (fwd) {
+      float* vs = a0;                    // v_S, kNdTinyS floats
+      float* rs = a0 + kNdTinyS;         // z_S
+      float* ru = a0 + 2 * kNdTinyS;     // the U rows' right-hand sides, then W
+      if (has) {
+        nd_rhs_into(d, F, 0, F.s, F.sp, vs, f, wb, gl, 8);
+        nd_rhs_into(d, F, F.s, F.u, F.u, ru, f, wb, gl, 8);
+      }
+      __syncthreads();
+      if (!wait()) return false;
+      if (nmax > 0) {
+        const float* m = has ? at(F.FM) : c.sbuf;
+        const int fs = has ? F.s : 0;
+        auto put = [=](int a, float acc) {
+          if (a < fs) rs[a] = acc;
+          else ru[a - fs] -= acc;
+        };
+        rows_dot_grp<4>(m, n4, nrows, nmax, (const float4*)vs, n4, gl, put);
       }
       __syncwarp();
-      const int n4 = len >> 2;
-      const int Gf = n4 <= 1 ? 1 : (n4 <= 2 ? 2 : (n4 <= 4 ? 4 : 8));
-      const int Gw = warp_max(has ? Gf : 1);
-      if (kind == kNdFwd) {
-        const int nrows = has ? F.s + F.u : 0;
-        rows_dot_grp_any(Gw, has ? (const float*)d.bcr + F.FM : (const float*)d.bcr, n4, nrows, warp_max(nrows),
-                         (const float4*)vg, n4, gl, [&](int a, float acc) {
-                           if (a < F.s) e[d.nd_idx[F.S + a]] = acc;
-                           else wb[F.W + a - F.s] = nd_rhs(d, F, a, f, wb) - acc;
-                         });
-      } else {
-        const int nrows = has ? F.s : 0;
-        if (warp_max(has && F.u > 0 ? 1 : 0)) {
-          rows_dot_grp_any(Gw, has ? (const float*)d.bcr + F.NB : (const float*)d.bcr, n4, nrows, warp_max(nrows),
-                           (const float4*)vg, n4, gl, [&](int a, float acc) {
-                             const int u = d.nd_idx[F.S + a];
-                             const float val = e[u] - (F.u > 0 ? acc : 0.0f);
-                             e[u] = val;
-                             x[(long long)u + B.N] += (double)val;
-                           });
-        } else {
-          for (int a = gl; a < nrows; a += 8) {
-            const int u = d.nd_idx[F.S + a];
-            x[(long long)u + B.N] += (double)e[u];
-          }
-        }
+      if (has) {
+        for (int a = gl; a < F.s; a += 8) e[d.nd_idx[F.S + a]] = rs[a];
+        for (int a = gl; a < F.u; a += 8) wb[F.W + a] = ru[a];
+      }
+    } else {
+      float* vu = a0;                    // x_U, kNdTinyU floats
+      float* rs = a0 + kNdTinyU;         // N x_U
+      if (has) nd_xu_into(d, F, F.up, vu, e, gl, 8);
+      __syncthreads();
+      if (!wait()) return false;
+      if (nmax > 0) {
+        const float* m = has ? at(F.NB) : c.sbuf;
+        auto put = [=](int a, float acc) { rs[a] = acc; };
+        rows_dot_grp<8>(m, n4, nrows, nmax, (const float4*)vu, n4, gl, put);
       }
       __syncwarp();
+      if (has) nd_back_store(d, F, 0, F.s, F.u > 0 ? rs : nullptr, e, x, B.N, gl, 8);
     }
     __syncthreads();
     return true;
   }
-  // small fronts, one per warp (per-warp vector of kNdWarpMaxS + kNdWarpMaxU floats)
-  float* v = c.red + warp * (kNdWarpMaxS + kNdWarpMaxU);
-  for (int k = warp; k < T.z; k += kBcrWarps) {
-    const NdFront F = d.nd_front[T.x + k];
-    if (kind == kNdFwd) {
-      for (int p = lane; p < F.sp; p += 32) v[p] = p < F.s ? nd_rhs(d, F, p, f, wb) : 0.0f;
-      __syncwarp();
-      nd_fwd_rows(d, F, 0, F.s + F.u, v, f, e, wb, lane, 0, 1);
-    } else {
-      for (int p = lane; p < F.up; p += 32) v[p] = p < F.u ? e[d.nd_idx[F.U + p]] : 0.0f;
-      __syncwarp();
-      nd_back_rows(d, F, 0, F.s, v, e, x, B.N, lane, 0, 1);
+  // small fronts, one per warp
+  float* a0 = c.red + warp * kNdWarpArea;
+  const bool has = warp < T.z;
+  NdFront F;
+  if (has) F = d.nd_front[T.x + warp];
+  if (fwd) {
+    float* vs = a0;                      // v_S, kNdWarpMaxS floats
+    float* rs = a0 + kNdWarpMaxS;        // z_S
+    float* ru = a0 + 2 * kNdWarpMaxS;    // the U rows' right-hand sides, then W
+    if (has) {
+      nd_rhs_into(d, F, 0, F.s, F.sp, vs, f, wb, lane, 32);
+      nd_rhs_into(d, F, F.s, F.u, F.u, ru, f, wb, lane, 32);
     }
-    __syncwarp();
+    __syncthreads();
+    if (!wait()) return false;
+    if (has) {
+      const int fs = F.s;
+      rows_dot_any(F.sp >> 2, at(F.FM), F.sp >> 2, 0, F.s + F.u, 0, (const float4*)vs, lane, 0, 1,
+                  [=](int a, float acc) {
+                    if (a < fs) rs[a] = acc;
+                    else ru[a - fs] -= acc;
+                  });
+      __syncwarp();
+      nd_fwd_store(d, F, 0, F.s, rs, e, wb, lane, 32);
+      for (int a = lane; a < F.u; a += 32) wb[F.W + a] = ru[a];
+    }
+  } else {
+    float* vu = a0;                      // x_U, kNdWarpMaxU floats
+    float* rs = a0 + kNdWarpMaxU;        // N x_U
+    if (has) nd_xu_into(d, F, F.up, vu, e, lane, 32);
+    __syncthreads();
+    if (!wait()) return false;
+    if (has) {
+      if (F.u > 0)
+        rows_dot_any(F.up >> 2, at(F.NB), F.up >> 2, 0, F.s, 0, (const float4*)vu, lane, 0, 1,
+                    [=](int a, float acc) { rs[a] = acc; });
+      __syncwarp();
+      nd_back_store(d, F, 0, F.s, F.u > 0 ? rs : nullptr, e, x, B.N, lane, 32);
+    }
   }
-  // the next task may be a large front's, whose vector overwrites the
+  // the next task's copy overwrites the staged rows and its vectors the
   // per-warp areas: every warp finishes here first
   __syncthreads();
   return true;
@@ -650,7 +821,10 @@ __device__ void node_tasks(const DevPtrs& d, const int* npre, const int* tpre, i
 // b = DevPtrs::b).  An instance computes the same values alone or in a batch.
 // MAXN: the largest block size of the batch this instantiation handles (256
 // or 544 = 17 x 32, for grids up to 543 cells in x2).
-template <int MAXN>
+// kParts: 1 = reduction stages, 2 = nested-dissection tasks, 3 = both (a
+// batch of both kinds); each instantiation compiles only what it runs, so
+// the registers of one path do not spill the other's.
+template <int MAXN, int kParts>
 __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan pl, int mode, int only, BcrRhs rhs) {
   extern __shared__ __align__(128) float s_dyn[];
   __shared__ double sh[40];
@@ -780,12 +954,15 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
         const BcrInst& B = k == 0 ? s_b0 : d.bcr_inst[k];
         const int kind = s_kind[k] >> 8;
         if (kind == kNdFwd || kind == kNdBack) {
-          if (!run_nd(d, c, B, kind, s_kind[k] & 255, tt - s_pre[k], d.bcr_f + rh * pl.rows, d.bcr_e + rh * pl.rows,
-                      x_of(rh), d.nd_w + rh * pl.nd_wrows))
+          if constexpr ((kParts & 2) != 0) {
+            if (!run_nd(d, c, B, kind, s_kind[k] & 255, tt - s_pre[k], d.bcr_f + rh * pl.rows,
+                        d.bcr_e + rh * pl.rows, x_of(rh), d.nd_w + rh * pl.nd_wrows))
+              return;
+          }
+        } else if constexpr ((kParts & 1) != 0) {
+          if (!run_stage<MAXN>(d, c, B, kind, s_kind[k] & 255, tt - s_pre[k], sv, d.bcr_f + rh * pl.rows,
+                               d.bcr_e + rh * pl.rows, x_of(rh)))
             return;
-        } else if (!run_stage<MAXN>(d, c, B, kind, s_kind[k] & 255, tt - s_pre[k], sv, d.bcr_f + rh * pl.rows,
-                                    d.bcr_e + rh * pl.rows, x_of(rh))) {
-          return;
         }
       }
       if (p + 1 < pl.phases) load_tab(p + 1);
@@ -810,7 +987,11 @@ constexpr int static_smem(int maxn) {
 }
 
 const void* kernel_for(const BcrPlan& b) {
-  return b.wide ? (const void*)k_solve_bcr<kBcrMaxNWide> : (const void*)k_solve_bcr<kBcrMaxN>;
+  // wide: 0 the narrow reduction, 1 the wide reduction (and nested
+  // dissection, if some instance uses it), 2 nested dissection alone
+  return b.wide == 2   ? (const void*)k_solve_bcr<kBcrMaxNWide, 2>
+         : b.wide == 1 ? (const void*)k_solve_bcr<kBcrMaxNWide, 3>
+                       : (const void*)k_solve_bcr<kBcrMaxN, 1>;
 }
 
 // Check of the bounded grid-barrier wait: the CTAs wait at a barrier that
@@ -832,10 +1013,14 @@ int bcr_configure(SolvePlan& pl, BcrInst* bi, int ni, int sms) {
   int widest = 0;
   for (int k = 0; k < ni; ++k)
     if (!bi[k].nd) widest = bi[k].N > widest ? bi[k].N : widest;
-  // nested dissection uses the reduction buffer (kBcrWarps x MAXN floats) for
-  // a large front's vector
-  pl.bcr.wide = widest > kBcrMaxN || pl.bcr.nd_floats > kBcrWarps * kBcrMaxN ? 1 : 0;
-  if (pl.bcr.nd_floats > kBcrWarps * kBcrMaxNWide) return 0;
+  // nested dissection keeps its vectors in the wide kernel's reduction
+  // buffer (kBcrWarps x kBcrMaxNWide floats)
+  int any_nd = 0;
+  for (int k = 0; k < ni; ++k) any_nd |= bi[k].nd;
+  int any_bcr = 0;
+  for (int k = 0; k < ni; ++k) any_bcr |= !bi[k].nd;
+  pl.bcr.wide = !any_bcr ? 2 : (widest > kBcrMaxN || any_nd ? 1 : 0);
+  if (pl.bcr.nd_floats > kNdVecCap) return 0;
   const long long budget = (long long)optin - static_smem(pl.bcr.wide ? kBcrMaxNWide : kBcrMaxN);
   const void* kern = kernel_for(pl.bcr);
   // tail chunks: about one per CTA when the tails are few, else one row per warp
@@ -862,6 +1047,11 @@ int bcr_configure(SolvePlan& pl, BcrInst* bi, int ni, int sms) {
       any = 1;
       dyn = staged > dyn ? staged : dyn;
     }
+  }
+  if (any_nd) {  // the nested-dissection tasks stage their matrix rows
+    const long long nd_stage_bytes = (long long)kNdStageFloats * (long long)sizeof(float);
+    if (nd_stage_bytes > budget) return 0;
+    dyn = nd_stage_bytes > dyn ? nd_stage_bytes : dyn;
   }
   pl.bcr.smem = any;
   pl.bcr.dyn = (int)dyn;

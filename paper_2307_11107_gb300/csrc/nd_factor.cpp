@@ -268,14 +268,21 @@ bool nd_build(int M, int N, NdCoef coef, const void* ctx, int leaf, int threads,
     g += 2 * (int64_t)(F.s + F.u);
     F.W = w;
     w += (F.u + 3) & ~3;
-    F.FM = fm;
-    fm += (int64_t)(F.s + F.u) * F.sp;
-    F.NB = nb;
-    nb += (int64_t)F.s * F.up;
     f.depth = std::max(f.depth, F.level);
     f.max_s = std::max(f.max_s, F.s);
     f.max_u = std::max(f.max_u, F.u);
   }
+  // matrices level by level, deepest first (the order of the device's task
+  // tables: a task's fronts hold one contiguous range, staged by one copy)
+  for (int l = f.depth; l >= 0; --l)
+    for (int k = 0; k < nf; ++k) {
+      NdFront& F = f.fronts[k];
+      if (F.level != l) continue;
+      F.FM = fm;
+      fm += (int64_t)(F.s + F.u) * F.sp;
+      F.NB = nb;
+      nb += (int64_t)F.s * F.up;
+    }
   f.w_total = w;
   f.fm_total = fm;
   f.nb_total = nb;
@@ -472,8 +479,8 @@ void nd_solve_host(const NdFactor& f, const double* r, double* e, bool fp64) {
     }
 }
 
-int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u, int task_floats, int task_fronts,
-              int ctas, NdUpload& up, NdLevels& lv) {
+int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u, int warp_floats, int task_floats,
+              int task_fronts, int stage_floats, int ctas, NdUpload& up, NdLevels& lv) {
   const int nf = (int)f.fronts.size();
   const int64_t front0 = (int64_t)up.fronts.size(), idx0 = (int64_t)up.idx.size(), g0 = (int64_t)up.gather.size();
   std::vector<int> order;  // deepest level first
@@ -481,7 +488,13 @@ int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u
     for (int k : f.by_level[l]) order.push_back(k);
   std::vector<int> where(nf);
   for (int q = 0; q < nf; ++q) where[order[q]] = q;
-  auto large = [&](const NdFront& F) { return F.s > warp_s || F.u > warp_u; };
+  // large in a sweep: beyond a warp's vector areas, or a matrix beyond what a
+  // warp stages in shared memory
+  auto large_in = [&](const NdFront& F, bool fwd) {
+    const int64_t floats = fwd ? (int64_t)(F.s + F.u) * F.sp : (int64_t)F.s * F.up;
+    return F.s > warp_s || F.u > warp_u || floats > warp_floats;
+  };
+  auto large = [&](const NdFront& F) { return large_in(F, true) || large_in(F, false); };
   int need = 0;
   for (int q = 0; q < nf; ++q) {
     NdFront F = f.fronts[order[q]];
@@ -508,16 +521,25 @@ int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u
       }
   }
   // tiny fronts (s <= 16, u <= 48) go four to a warp, one per 8-lane group
-  auto tiny = [&](const NdFront& F) { return F.s <= kNdTinyS && F.u <= kNdTinyU; };
+  // every task's matrix rows fit the device's staging buffer (stage_floats)
+  auto floats_in = [&](const NdFront& F, bool fwd) {
+    return fwd ? (int64_t)(F.s + F.u) * F.sp : (int64_t)F.s * F.up;
+  };
   auto level_tasks = [&](int l, bool fwd) {
+    auto large = [&](const NdFront& F) { return large_in(F, fwd); };
+    auto tiny0 = [&](const NdFront& F) { return F.s <= kNdTinyS && F.u <= kNdTinyU && !large(F); };
     int q = 0;
     while (q < nf && up.fronts[front0 + q].level != l) ++q;
     int small = 0, nt = 0;
     for (int z = q; z < nf && up.fronts[front0 + z].level == l; ++z) {
       small += !large(up.fronts[front0 + z]);
-      nt += tiny(up.fronts[front0 + z]);
+      nt += tiny0(up.fronts[front0 + z]);
     }
     const int c = std::max(1, ctas);
+    // tiny fronts go four to a warp when there are at least four per CTA,
+    // else one to a warp like the small ones
+    const bool use_tiny = nt >= 4 * c;
+    auto tiny = [&](const NdFront& F) { return use_tiny && tiny0(F); };
     const int per = std::max(1, std::min(task_fronts, (small + c - 1) / c));
     const int per_tiny = std::max(1, std::min(4 * task_fronts, (nt + c - 1) / c));
     while (q < nf && up.fronts[front0 + q].level == l) {
@@ -525,7 +547,7 @@ int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u
       if (large(F)) {
         const int rows = fwd ? F.s + F.u : F.s;
         const int width = fwd ? F.sp : std::max(4, F.up);
-        const int nr = std::max(16, task_floats / width);
+        const int nr = std::max(1, task_floats / width);
         for (int r = 0; r < rows; r += nr) up.tasks.push_back(NdTask{(int)(front0 + q), r, std::min(nr, rows - r), 0});
         ++q;
         continue;
@@ -533,9 +555,11 @@ int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u
       const bool t = tiny(F);
       const int cap = t ? per_tiny : per;
       int n = 0;
+      int64_t floats = 0;
       while (q + n < nf && n < cap) {
         const NdFront& G = up.fronts[front0 + q + n];
-        if (G.level != l || large(G) || tiny(G) != t) break;
+        if (G.level != l || large(G) || tiny(G) != t || floats + floats_in(G, fwd) > stage_floats) break;
+        floats += floats_in(G, fwd);
         ++n;
       }
       up.tasks.push_back(NdTask{(int)(front0 + q), 0, n, t ? 2 : 1});

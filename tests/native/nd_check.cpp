@@ -94,12 +94,40 @@ int main(int argc, char** argv) {
   apic::NdUpload up;
   apic::NdLevels l0, l1;
   const int64_t mat1 = ((f.fm_total + f.nb_total + 63) / 64) * 64, w1 = ((f.w_total + 63) / 64) * 64;
-  apic::nd_layout(f, 0, 0, 64, 192, 16384, 16, 152, up, l0);
-  apic::nd_layout(f, mat1, w1, 64, 192, 16384, 16, 152, up, l1);
+  apic::nd_layout(f, 0, 0, 64, 192, 2048, 16384, 16, 32768, 152, up, l0);
+  apic::nd_layout(f, mat1, w1, 64, 192, 2048, 16384, 16, 32768, 152, up, l1);
   std::vector<float> matbuf((size_t)(2 * mat1), 0.0f);
   for (int k = 0; k < 2; ++k) {
     std::copy(f.fm.begin(), f.fm.end(), matbuf.begin() + k * mat1);
     std::copy(f.nb.begin(), f.nb.end(), matbuf.begin() + k * mat1 + f.fm_total);
+  }
+  // every task's matrix rows are one contiguous range in each sweep (the
+  // device stages a task by one copy): consecutive fronts of a task follow
+  // one another
+  long long gaps = 0, big = 0;
+  for (size_t i = 0; i < up.tasks.size(); ++i) {
+    const apic::NdTask& t = up.tasks[i];
+    const bool fwd = (int)i < l0.bt[0] || ((int)i >= l1.ft[0] && (int)i < l1.bt[0]);
+    int64_t fw = 0, bw = 0;
+    for (int q = t.front; t.warp != 0 && q < t.front + t.n; ++q) {
+      const apic::NdFront &A = up.fronts[q];
+      fw += (int64_t)(A.s + A.u) * A.sp;
+      bw += (int64_t)A.s * A.up;
+      if (q + 1 == t.front + t.n) break;
+      const apic::NdFront &C = up.fronts[q + 1];
+      gaps += A.FM + (int64_t)(A.s + A.u) * A.sp != C.FM;
+      gaps += A.NB + (int64_t)A.s * A.up != C.NB;
+    }
+    if (t.warp == 0) {
+      const apic::NdFront &A = up.fronts[t.front];
+      fw = (int64_t)t.n * A.sp;
+      bw = (int64_t)t.n * A.up;
+    }
+    big += (fwd ? fw : bw) > 32768;  // the task's matrix rows fit the device's stage
+  }
+  if (gaps || big) {
+    std::printf("FAIL %lld task fronts not contiguous, %lld tasks beyond the stage\n", gaps, big);
+    return 1;
   }
   std::vector<float> r32(r.begin(), r.end()), e32((size_t)M * N, 0.0f), w((size_t)(2 * w1), 0.0f);
   apic::nd_solve_tables(up, l1, f.depth, matbuf, N, r32.data(), e32.data(), w);
