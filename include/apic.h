@@ -262,10 +262,12 @@ typedef struct {
 #define APIC_SOLVER_MG_COOP 1    /* the same in one cooperative launch per solve (FP64, one instance) */
 #define APIC_SOLVER_BCR 2        /* FP64 iterative refinement around an FP32 block cyclic reduction of
                                     every instance in one cooperative launch (FP32 particles, any n1,
-                                    grids up to 543 cells in x2) */
+                                    grids up to 543 cells in x2): the default when the whole batch's
+                                    reduction blocks fit in L2 (e.g. one 256 x 128 grid) */
 #define APIC_SOLVER_ND 3         /* the same refinement around an FP32 nested-dissection factorisation (formed
-                                    once at creation on the host in FP64) for some or all instances: grids
-                                    wider than 256 cells in x2, or every grid with APIC_DIRECT=nd */
+                                    once at creation on the host in FP64) for some or all instances: the
+                                    default otherwise (larger grids, batches); APIC_DIRECT=bcr / nd / wide
+                                    (nested dissection only for grids wider than 256 cells) override */
 
 /* Counters of the batch (launch counts, Krylov iterations, phase times). */
 int apic_stats(apic_sim* sim, apic_stats_t* out);

@@ -951,7 +951,8 @@ static int setup(apic_sim* S) {
   long long bcr_rows = 0;  // floats of bcr_f (and of bcr_e)
   int bcr_nb = 0;          // CTAs of the reduction solve
   // nested dissection per instance (APIC_DIRECT=nd: every instance, bcr:
-  // none; default: grids wider than kBcrMaxN cells in x2)
+  // none, wide: grids wider than kBcrMaxN cells in x2; default: every
+  // instance unless the whole reduction fits in L2)
   std::vector<NdFactor> nds(ni);
   std::vector<char> use_nd(ni, 0);
   NdUpload ndu;
@@ -962,9 +963,25 @@ static int setup(apic_sim* S) {
     for (const Inst& I : S->inst) want = want && !(I.flags & (APIC_NO_FIELD | APIC_BOLTZMANN));
     const char* dm = std::getenv("APIC_DIRECT");
     const std::string direct = dm ? dm : "auto";
+    // auto: the reduction where all its blocks (dense level 1) fit in L2
+    // (fewer, shorter phases), else nested dissection (its fronts stream
+    // about a tenth of the reduction's bytes from DRAM)
+    bool red_fits = false;
+    if (want && direct == "auto") {
+      double b = 0.0;
+      bool ok = true;
+      for (int k = 0; k < ni && ok; ++k) {
+        BcrInst B{};
+        ok = bcr_layout(S->inst[k], B, true);
+        b += 4.0 * ((double)B.blocks * (double)B.blk + (double)B.tail_n * (double)B.tail_np);
+      }
+      red_fits = ok && b <= 112.0 * 1024 * 1024;
+    }
     for (int k = 0; k < ni && want; ++k) {
       const Inst& I = S->inst[k];
-      use_nd[k] = direct == "nd" || (direct != "bcr" && I.N2 > kBcrMaxN + 1);
+      // wide: nested dissection only where the narrow reduction does not
+      // apply (a batch may then mix both in one launch)
+      use_nd[k] = direct == "nd" || (direct == "auto" && !red_fits) || (direct == "wide" && I.N2 > kBcrMaxN + 1);
       if (!use_nd[k]) continue;
       std::string why;
       int T = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));

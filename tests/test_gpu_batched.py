@@ -68,14 +68,16 @@ def test_batch_equals_solo(prec, solver, monkeypatch):
         assert np.allclose(tb["history"], ts["history"], rtol=1e-12, atol=1e-12)
 
 
-@pytest.mark.parametrize("direct", ["bcr", "auto"])
+@pytest.mark.parametrize("direct", ["bcr", "auto", "wide"])
 def test_batched_reduction_poisson_matches_banded_lu(direct, monkeypatch):
     """Every instance of an uneven FP32 batch (different alpha and grid, n1
     a power of two or not, one instance wider than 256 unknowns per row, so
     the wide kernel runs the narrow ones too) solved by the batched block
-    cyclic reduction against the oracle's banded LU; by default the wide
-    instance takes the nested dissection in the same launch as the others'
-    reduction.  Solving one instance leaves the others' potential alone."""
+    cyclic reduction against the oracle's banded LU; by default (the
+    reduction would not fit in L2) every instance takes the nested
+    dissection; with APIC_DIRECT=wide the wide instance takes it in the same
+    launch as the others' reduction.  Solving one instance leaves the
+    others' potential alone."""
     import oracle
     import paper_2307_11107_gb300 as apic
     from tests.inputs import random_rho
