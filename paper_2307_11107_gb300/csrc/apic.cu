@@ -1185,6 +1185,7 @@ static int setup(apic_sim* S) {
   d.st64 = (double*)A(sizeof(double) * kSt * total_nodes);
   d.acc = (unsigned long long*)A(sizeof(unsigned long long) * 2 * total_nodes);
   d.G = A(2 * R * total_nodes);
+  d.H = R == sizeof(float) ? (float*)A(4 * sizeof(float) * total_nodes) : nullptr;
   d.st = A(R * kSt * level_nodes);
   d.e = A(R * level_nodes);
   d.f = A(R * level_nodes);

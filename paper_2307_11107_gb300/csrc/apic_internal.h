@@ -156,6 +156,8 @@ struct DevPtrs {
   double* st64;                   // finest-level stencil, FP64 [kSt][nodes] per instance (same offsets)
   unsigned long long* acc;        // deposit accumulators
   void* G;                        // node gradients (dphi/dx1, dphi/dx2) as pairs of the particle type
+  float* H;                       // FP32: (G[n], G[n + 1]) per node n, four floats (the vector push's
+                                  // gather reads a cell's four corners in two loads); null in FP64
   // multigrid (particle type)
   void* st;                       // stencils of all levels
   void *e, *f;                    // level vectors

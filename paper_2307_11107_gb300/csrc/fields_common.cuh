@@ -77,6 +77,14 @@ __device__ __forceinline__ void grad_node(const DevPtrs& d, const Inst& I, long 
   v.x = (Real)g1;
   v.y = (Real)g2;
   ((R2*)d.G)[I.node_off + nd] = v;
+  if constexpr (sizeof(Real) == sizeof(float)) {
+    if (d.H) {  // the pair table: this node's half of its own entry and of its left neighbour's
+      float2* H2 = (float2*)d.H;
+      const float2 w = make_float2((float)v.x, (float)v.y);
+      H2[2 * (I.node_off + nd)] = w;
+      if (j > 0) H2[2 * (I.node_off + nd) - 1] = w;
+    }
+  }
 }
 
 // Fixed-order block sum (warp shuffles, then warp 0 over the warp sums); any

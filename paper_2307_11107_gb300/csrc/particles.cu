@@ -27,6 +27,8 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPushItems = 8;    // particles per thread per chunk
 constexpr int kFlushChunks = 31;  // chunks (of 2048 particles) between window flushes at most
+constexpr int kPush4Items = 16;   // the vector push: particles per thread per chunk (4096 per chunk)
+constexpr int kFlushChunks4 = 15; // its chunks between window flushes at most (15 x 4096 < 2^16)
 constexpr int kWinRows = 8;      // node rows of the shared-memory deposit window at most
 constexpr int kWinMaxN2 = 513;   // widest grid row the window holds (larger grids deposit globally)
 constexpr int kInjRows = 3;      // node rows of the injection window (the last two cell rows)
@@ -651,8 +653,8 @@ __global__ void __launch_bounds__(256, APIC_PUSH4_MIN_BLOCKS) k_push4(DevPtrs d,
   __shared__ int s_row0, s_wpop, s_nsince, s_newrow0, s_flush, s_gi;
   __shared__ unsigned s_rowmask;
   constexpr int kPer = 4;                 // particles per thread and item
-  const long long CH = (long long)kPushItems * blockDim.x;  // 2048 particles per chunk
-  const int items = kPushItems / kPer;     // 2 items of 1024 particles
+  const long long CH = (long long)kPush4Items * blockDim.x;  // 4096 particles per chunk
+  const int items = kPush4Items / kPer;     // 4 items of 1024 particles
   if (threadIdx.x == 0) {
     long long a = 0;
     for (int p = 0; p < d.n_pop; ++p) {
@@ -692,7 +694,7 @@ __global__ void __launch_bounds__(256, APIC_PUSH4_MIN_BLOCKS) k_push4(DevPtrs d,
   float4* VR = (float4*)d.vR;
   float4* VZ = (float4*)d.vZ;
   float4* VT = (float4*)d.vT;
-  const float2* G = (const float2*)d.G;
+  const float4* H = (const float4*)d.H;
   auto flush = [&](int wp, int row0) {
     const PushConst& Cw = s_pc[wp];
     const int rows = Cw.n2 <= win_n2 ? win_rows : 0;
@@ -771,18 +773,20 @@ __global__ void __launch_bounds__(256, APIC_PUSH4_MIN_BLOCKS) k_push4(DevPtrs d,
     if (threadIdx.x == 0) {
       // window rows from the chunk's first live particle (this thread holds the first four)
       int row = -1;
+      // (the window's place changes no result: deposits outside it go to
+      // the global accumulator)
       for (int k = 0; k < kPer && row < 0; ++k) {
         const float xq = lane4(st.x1, k);
-        if (k < nleft && xq < 0.0f) row = (int)floor((double)((xq + 1.0f) * C.ih1));
+        if (k < nleft && xq < 0.0f) row = (int)floorf((xq + 1.0f) * C.ih1);
       }
       for (int qq = kPer; row < 0 && qq < 64 && c0 + qq < npop; ++qq) {
         const float xq = ((const float*)d.x1)[pbase + c0 + qq];
-        if (xq < 0.0f) row = (int)floor((double)((xq + 1.0f) * C.ih1));
+        if (xq < 0.0f) row = (int)floorf((xq + 1.0f) * C.ih1);
       }
       row = row < 0 ? 0 : row;
       const int r0 = row > 0 ? row - 1 : 0;
       const int rows = C.n2 <= win_n2 ? win_rows : 0;
-      const bool keep = s_wpop == pop && s_nsince < kFlushChunks && r0 >= s_row0 && r0 + 2 < s_row0 + rows;
+      const bool keep = s_wpop == pop && s_nsince < kFlushChunks4 && r0 >= s_row0 && r0 + 2 < s_row0 + rows;
       s_flush = s_wpop >= 0 && !keep;
       s_newrow0 = keep ? s_row0 : r0;
     }
@@ -805,7 +809,7 @@ __global__ void __launch_bounds__(256, APIC_PUSH4_MIN_BLOCKS) k_push4(DevPtrs d,
     CW.rows = C.n2 <= win_n2 ? win_rows : 0;
     CW.n2 = C.n2;
     CW.N2 = C.N2;
-    const float2* Gi = G + C.node_off;
+    const float4* Hi = H + C.node_off;
     const int bits = C.fbits >> 1;
     for (int it = 0; it < items; ++it) {
       if (it > 0) load(it);
@@ -833,9 +837,9 @@ __global__ void __launch_bounds__(256, APIC_PUSH4_MIN_BLOCKS) k_push4(DevPtrs d,
           int ci = min(max((int)floorf(u1), 0), C.n1 - 1), cj = min(max((int)floorf(u2), 0), C.n2 - 1);
           float f1 = fminf(fmaxf(u1 - (float)ci, 0.0f), 1.0f), f2 = fminf(fmaxf(u2 - (float)cj, 0.0f), 1.0f);
           const int n00 = ci * C.N2 + cj;
-          float2 a00 = Gi[n00], a10 = Gi[n00 + C.N2], a01 = Gi[n00 + 1], a11 = Gi[n00 + C.N2 + 1];
-          float g1 = (1.0f - f2) * ((1.0f - f1) * a00.x + f1 * a10.x) + f2 * ((1.0f - f1) * a01.x + f1 * a11.x);
-          float g2 = (1.0f - f2) * ((1.0f - f1) * a00.y + f1 * a10.y) + f2 * ((1.0f - f1) * a01.y + f1 * a11.y);
+          const float4 b0 = Hi[n00], b1 = Hi[n00 + C.N2];  // (G00, G01), (G10, G11)
+          float g1 = (1.0f - f2) * ((1.0f - f1) * b0.x + f1 * b1.x) + f2 * ((1.0f - f1) * b0.z + f1 * b1.z);
+          float g2 = (1.0f - f2) * ((1.0f - f1) * b0.y + f1 * b1.y) + f2 * ((1.0f - f1) * b0.w + f1 * b1.w);
           float ir3 = ir * ir * ir;
           float x1R = sn * (r + 3.0f * al * x2) * ir3, x1Z = (r * x2 + al * (3.0f * x2 * x2 - 1.0f)) * ir3;
           float x2R = -x2 * sn * ir, x2Z = s2 * ir;
