@@ -594,7 +594,8 @@ def main():
                        "dt": cfg["dt"],
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "sort_interval": tiles["sort_interval"], "autotuned": tuned is not None,
-                       "push_window_rows": tiles["win_rows"], "push_chunk_group": tiles["chunk_group"]},
+                       "push_window_rows": tiles["win_rows"], "push_chunk_group": tiles["chunk_group"],
+                       "push_chunk_particles": 256 * tiles["chunk_items"]},
             "roofline": roof, "cpu_baseline": cpu, "error_vs_fp64_oracle": perr, "e2e": e2e,
             "gpu_launches": int(launches),
             "poisson_loop_iters": int(loop_iters), "clocks": clk.summary(),

@@ -253,8 +253,8 @@ typedef struct {
   int64_t sorts;                /* particle sorts launched (every sort_interval steps) */
   int32_t sort_interval;        /* steps between particle sorts in use (0: none) */
   int32_t win_rows;             /* node rows of the push's shared-memory deposit window in use */
-  int32_t chunk_group;          /* consecutive 2048-particle chunks a push CTA takes at a time */
-  int32_t pad;
+  int32_t chunk_group;          /* consecutive particle chunks a push CTA takes at a time */
+  int32_t chunk_items;          /* FP32 push: particles per thread of a chunk (16: 4096 per chunk, 32: 8192) */
 } apic_stats_t;
 
 /* Poisson solvers (chosen at creation) */
@@ -279,21 +279,24 @@ int apic_stats(apic_sim* sim, apic_stats_t* out);
 int apic_step_timed(apic_sim* sim, int32_t n_steps);
 
 /* ---- Autotuning ------------------------------------------------------------
- * Three schedules of the step trade against each other: the particle sort's
+ * Four schedules of the step trade against each other: the particle sort's
  * interval (the sort's cost against the push's locality: the push deposits
  * through a shared-memory window of grid rows, which works best on recently
  * sorted particles), the node rows of that window (a wider window catches
  * more of a chunk's deposits, a narrower one leaves more L1 to the field
- * gather) and the chunks a push CTA takes from the shared counter at a time.
- * apic_autotune first runs, for each of APIC_TUNE_CANDIDATES intervals c
- * (2, 4, 6, 8, 12, 16, 24), whole sort intervals, c * ceil(steps_per_trial /
- * c) full steps each starting with a sort, timed with CUDA events on the
- * simulation's stream, and keeps the fastest; then, at that interval, chunk
- * groups 2, 4, 8 and window rows 2, 4, 6, 8 (the step graphs recaptured for
+ * gather), the chunks a push CTA takes from the shared counter at a time and
+ * the size of a chunk (fewer barriers per particle against a coarser load
+ * balance).  apic_autotune first runs, for each of APIC_TUNE_CANDIDATES
+ * intervals c (2, 4, 6, 8, 12, 16, 24), whole sort intervals, c *
+ * ceil(steps_per_trial / c) full steps each starting with a sort, timed with
+ * CUDA events on the simulation's stream, and keeps the fastest; then, at
+ * that interval, chunk groups 2, 4, 8, window rows 2, 4, 6, 8 and (FP32)
+ * chunks of 16 or 32 particles per thread (the step graphs recaptured for
  * each, one warm-up interval and then the same timed steps), keeping the
- * fastest of each.  apic_stats reports the choices.  The simulation advances
- * by the steps run (results as apic_step).  Without sorting (sort_interval = 0
- * at creation) nothing runs and 0 is returned in *sort_interval.
+ * fastest of each.  apic_stats reports the choices.  The simulation
+ * advances by the steps run (results as apic_step).  Without sorting
+ * (sort_interval = 0 at creation) nothing runs and 0 is returned in
+ * *sort_interval.
  * ms_per_step: [APIC_TUNE_CANDIDATES] host array (or NULL) for the sort
  * intervals' measured times.  Errors: INVALID_ARG (NULL sort_interval,
  * steps_per_trial < 1), those of apic_step. */

@@ -69,7 +69,8 @@ class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("poisson_loop_iters", C.c_int64), ("kernels_per_step", C.c_int32),
                 ("kernels_per_iter", C.c_int32), ("timed_steps", C.c_int64), ("phase_ms", C.c_double * NPHASE),
                 ("solver", C.c_int32), ("kernels_per_sort", C.c_int32), ("sorts", C.c_int64),
-                ("sort_interval", C.c_int32), ("win_rows", C.c_int32), ("chunk_group", C.c_int32), ("pad", C.c_int32)]
+                ("sort_interval", C.c_int32), ("win_rows", C.c_int32), ("chunk_group", C.c_int32),
+                ("chunk_items", C.c_int32)]
 
 
 SOLVERS = ("multigrid BiCGSTAB, per-phase kernels", "multigrid BiCGSTAB, one cooperative launch",

@@ -182,6 +182,7 @@ struct apic_sim {
   bool tan_ready = false;
   int win_rows = 0;                   // push deposit window rows (0: default for the grid), set by apic_autotune
   int chunk_group = 0;                // push chunks per group (0: default), set by apic_autotune
+  int chunk_items = 0;                // vector push particles per thread of a chunk (0: default), apic_autotune
   AdjPtrs adj{};                      // reverse-sweep state (allocated on first use, for up to adj_K steps)
   int adj_K = 0;
   std::vector<std::vector<std::pair<int, int>>> adj_levels;  // per instance, per tree level: fronts [f0, f1)
@@ -1558,7 +1559,9 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
         launch_gradients<Real>(d, s);
       }
       break;
-    case 3: launch_push<Real>(d, S->push_grid, S->max_n2, S->chord, S->win_rows, S->chunk_group, s); break;
+    case 3:
+      launch_push<Real>(d, S->push_grid, S->max_n2, S->chord, S->win_rows, S->chunk_group, S->chunk_items, S->slots, s);
+      break;
     case 4: launch_inject<Real>(d, S->max_inj, s); break;
     case 5: launch_step_end(d, s); break;
     case 6: launch_sort<Real>(d, S->push_grid, s); break;  // not a step phase: the particle sort
@@ -1728,6 +1731,13 @@ extern "C" int apic_step_timed(apic_sim* S, int32_t n_steps) {
   return S->precision == APIC_FP64 ? step_timed_impl<double>(S, n_steps) : step_timed_impl<float>(S, n_steps);
 }
 
+// The vector push's default chunk (launch_push): 32 particles per thread when
+// the batch's slots give every CTA two dozen 8192-particle chunks.
+static int push4_default_items(const apic_sim* S) {
+  const int grid = std::max(1, S->push_grid / 4 * (int)APIC_PUSH4_MIN_BLOCKS);
+  return S->slots >= 24ll * 8192 * grid ? 32 : 16;
+}
+
 extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
   if (!S || !out) return APIC_ERR_INVALID_ARG;
   long long cnt = 0;
@@ -1759,6 +1769,7 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
                                   : (S->precision == APIC_FP64 ? push_window_rows<double>(S->max_n2)
                                                                : push_window_rows<float>(S->max_n2));
   out->chunk_group = S->chunk_group > 0 ? S->chunk_group : 4;
+  out->chunk_items = S->precision == APIC_FP64 ? 0 : (S->chunk_items > 0 ? S->chunk_items : push4_default_items(S));
   out->solver = S->plan.bcr.n_inst > 0 ? (S->d.nd_front ? APIC_SOLVER_ND : APIC_SOLVER_BCR)
                                        : (S->coop > 0 ? APIC_SOLVER_MG_COOP : APIC_SOLVER_MG_KERNELS);
   out->sorts = S->sorts;
@@ -1856,6 +1867,20 @@ static int autotune_impl(apic_sim* S, int trial, int32_t* chosen, double* ms_out
     }
   }
   S->win_rows = best_r;
+  int best_i = S->chunk_items;
+  if (S->precision != APIC_FP64) {  // the vector push's chunk size
+    const int items_cand[] = {16, 32};
+    for (int c : items_cand) {
+      S->chunk_items = c;
+      drop_graphs(S);
+      const double t = time_steps();
+      if (t < best_t) {
+        best_t = t;
+        best_i = c;
+      }
+    }
+  }
+  S->chunk_items = best_i;
   drop_graphs(S);
   cudaEventDestroy(a);
   cudaEventDestroy(b);

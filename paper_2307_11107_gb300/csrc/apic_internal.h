@@ -287,10 +287,16 @@ void launch_explicit(const DevPtrs& d, int pop, long long n0, long long count, c
                      cudaStream_t s);
 template <class Real>
 void launch_deposit_all(const DevPtrs& d, int max_grid, int max_n2, cudaStream_t s);
-// win_rows, chunk_group: the deposit window's node rows and the chunks a CTA
-// takes per group (0: the defaults, push_window_rows and 4)
+#ifndef APIC_PUSH4_MIN_BLOCKS
+#define APIC_PUSH4_MIN_BLOCKS 3  // CTAs of the vector push per SM (80 registers: the four particles stay in registers)
+#endif
+// win_rows, chunk_group, chunk_items: the deposit window's node rows, the
+// chunks a CTA takes per group and the particles per thread of a chunk of the
+// vector push (16 or 32; 0: the defaults, push_window_rows, 4 and 32 when
+// `particles` (the batch's particle slots) give every CTA two dozen chunks)
 template <class Real>
-void launch_push(const DevPtrs& d, int grid, int max_n2, bool chord, int win_rows, int chunk_group, cudaStream_t s);
+void launch_push(const DevPtrs& d, int grid, int max_n2, bool chord, int win_rows, int chunk_group, int chunk_items,
+                 long long particles, cudaStream_t s);
 // Node rows of the push's shared-memory deposit window for grids up to max_n2
 // cells in x2 (queried once per width; call at set-up, before any capture).
 template <class Real>

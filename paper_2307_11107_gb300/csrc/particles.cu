@@ -27,8 +27,10 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPushItems = 8;    // particles per thread per chunk
 constexpr int kFlushChunks = 31;  // chunks (of 2048 particles) between window flushes at most
-constexpr int kPush4Items = 16;   // the vector push: particles per thread per chunk (4096 per chunk)
-constexpr int kFlushChunks4 = 15; // its chunks between window flushes at most (15 x 4096 < 2^16)
+// the vector push: particles per thread per chunk, 16 (4096 per chunk) or 32
+// (8192: fewer barriers per particle, coarser load balance); a window is
+// flushed before a cell's packed moments could hold 2^16 particles
+constexpr int kPush4ItemsMax = 32;
 constexpr int kWinRows = 8;      // node rows of the shared-memory deposit window at most
 constexpr int kWinMaxN2 = 513;   // widest grid row the window holds (larger grids deposit globally)
 constexpr int kInjRows = 3;      // node rows of the injection window (the last two cell rows)
@@ -170,23 +172,15 @@ __device__ __forceinline__ void cell_add(const CellWin& W, int ci, int cj, unsig
   }
 }
 
-// One particle per lane; when all 32 lanes share one cell the sums of the
-// moments are taken with the hardware warp reduction and one lane adds them.
+// One particle per lane.  (Summing a warp's moments first when all its lanes
+// share one cell measured slower on row-sorted particles: the warp-wide test
+// costs more than the rare shared atomics it saves.)
 __device__ __forceinline__ void deposit_moments(const CellWin& W, int key, int ci, int cj, unsigned q1, unsigned q2,
                                                 int b, bool active) {
   const unsigned S = 1u << b;
   const unsigned long long p12 = (unsigned long long)q1 * q2;
-  const int k0 = __shfl_sync(kFull, key, 0);
-  if (__all_sync(kFull, active && key == k0)) {
-    unsigned long long s1 = __reduce_add_sync(kFull, q1);
-    unsigned long long s2 = __reduce_add_sync(kFull, q2);
-    unsigned lo = __reduce_add_sync(kFull, (unsigned)(p12 & 0xffffffu));
-    unsigned hi = __reduce_add_sync(kFull, (unsigned)(p12 >> 24));
-    if ((threadIdx.x & 31) == 0)
-      cell_add(W, ci, cj, (s1 << 32) | s2, ((unsigned long long)hi << 24) + lo + (32ull << 48), S);
-  } else if (active) {
-    cell_add(W, ci, cj, ((unsigned long long)q1 << 32) | q2, p12 + (1ull << 48), S);
-  }
+  (void)key;
+  if (active) cell_add(W, ci, cj, ((unsigned long long)q1 << 32) | q2, p12 + (1ull << 48), S);
 }
 
 __device__ __forceinline__ long long dep_key(const Inst& I, const Pop& P, const Cell& c) {
@@ -641,11 +635,9 @@ struct P4 {
 
 __device__ __forceinline__ float& lane4(float4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); }
 
-#ifndef APIC_PUSH4_MIN_BLOCKS
-#define APIC_PUSH4_MIN_BLOCKS 3  // 85 registers: the four particles' state stays in registers
-#endif
 template <bool kChord>
-__global__ void __launch_bounds__(256, APIC_PUSH4_MIN_BLOCKS) k_push4(DevPtrs d, int win_n2, int win_rows, int group) {
+__global__ void __launch_bounds__(256, APIC_PUSH4_MIN_BLOCKS) k_push4(DevPtrs d, int win_n2, int win_rows, int group,
+                                                                      int chunk_items) {
   extern __shared__ unsigned long long s_win[];
   const int win_words = 2 * win_rows * win_n2;
   long long* s_pre = (long long*)(s_win + win_words);
@@ -653,8 +645,9 @@ __global__ void __launch_bounds__(256, APIC_PUSH4_MIN_BLOCKS) k_push4(DevPtrs d,
   __shared__ int s_row0, s_wpop, s_nsince, s_newrow0, s_flush, s_gi;
   __shared__ unsigned s_rowmask;
   constexpr int kPer = 4;                 // particles per thread and item
-  const long long CH = (long long)kPush4Items * blockDim.x;  // 4096 particles per chunk
-  const int items = kPush4Items / kPer;     // 4 items of 1024 particles
+  const long long CH = (long long)chunk_items * blockDim.x;  // particles per chunk
+  const int items = chunk_items / kPer;     // items of kPer x blockDim particles
+  const int flush_chunks = (int)(65535 / CH);  // chunks between window flushes at most
   if (threadIdx.x == 0) {
     long long a = 0;
     for (int p = 0; p < d.n_pop; ++p) {
@@ -786,7 +779,7 @@ __global__ void __launch_bounds__(256, APIC_PUSH4_MIN_BLOCKS) k_push4(DevPtrs d,
       row = row < 0 ? 0 : row;
       const int r0 = row > 0 ? row - 1 : 0;
       const int rows = C.n2 <= win_n2 ? win_rows : 0;
-      const bool keep = s_wpop == pop && s_nsince < kFlushChunks4 && r0 >= s_row0 && r0 + 2 < s_row0 + rows;
+      const bool keep = s_wpop == pop && s_nsince < flush_chunks && r0 >= s_row0 && r0 + 2 < s_row0 + rows;
       s_flush = s_wpop >= 0 && !keep;
       s_newrow0 = keep ? s_row0 : r0;
     }
@@ -1539,7 +1532,7 @@ int push_window_rows<Real>(int max_n2) {
 
 template <>
 void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, bool chord, int win_rows, int chunk_group,
-                       cudaStream_t s) {
+                       int chunk_items, long long particles, cudaStream_t s) {
   const int win_n2 = max_n2 < kWinMaxN2 - 1 ? max_n2 : kWinMaxN2 - 1;
   const int rows = win_rows > 0 ? std::max(2, std::min(kWinRows, win_rows)) : push_window_rows<Real>(max_n2);
   const int sm = push_smem(rows, win_n2, d.n_pop);
@@ -1556,8 +1549,11 @@ void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, bool chord, int w
   cudaMemsetAsync(d.cnt + 1, 0, sizeof(long long), s);  // the group counter
   if (v4) {
     grid = std::max(1, grid / 4 * (int)APIC_PUSH4_MIN_BLOCKS);  // the caller's grid is 4 CTAs per SM
-    if (chord) k_push4<true><<<grid, 256, sm, s>>>(d, win_n2, rows, group);
-    else k_push4<false><<<grid, 256, sm, s>>>(d, win_n2, rows, group);
+    // 8192-particle chunks when every CTA still gets two dozen of them
+    int ci = chunk_items == 16 || chunk_items == 32 ? chunk_items
+                                                    : (particles >= 24ll * 8192 * grid ? kPush4ItemsMax : 16);
+    if (chord) k_push4<true><<<grid, 256, sm, s>>>(d, win_n2, rows, group, ci);
+    else k_push4<false><<<grid, 256, sm, s>>>(d, win_n2, rows, group, ci);
   } else if (chord) {
     k_push<true><<<grid, 256, sm, s>>>(d, win_n2, rows, group);
   } else {

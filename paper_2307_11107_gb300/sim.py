@@ -154,7 +154,7 @@ class Sim:
                     phase_ms=dict(zip(_abi.PHASES, [float(v) for v in st.phase_ms])),
                     solver=_abi.SOLVERS[int(st.solver)], sorts=int(st.sorts),
                     kernels_per_sort=int(st.kernels_per_sort), sort_interval=int(st.sort_interval),
-                    win_rows=int(st.win_rows), chunk_group=int(st.chunk_group))
+                    win_rows=int(st.win_rows), chunk_group=int(st.chunk_group), chunk_items=int(st.chunk_items))
 
     def tallies(self, instance=0, history=True):
         c = self.cfgs[instance]
