@@ -247,6 +247,17 @@ struct apic_sim {
   }
 };
 
+// After a set-up kernel with grid barriers: false (and APIC_ERR_TIMEOUT) if a
+// barrier wait gave up.  Call after a synchronisation.
+static bool setup_wait_ok(apic_sim* S, const char* what) {
+  if (!S->d2h(S->h_err, S->d.err, 1) || !S->sync()) return false;
+  if (*S->h_err & kErrTimeout) {
+    S->fail(APIC_ERR_TIMEOUT, std::string(what) + ": grid barrier wait timed out");
+    return false;
+  }
+  return true;
+}
+
 namespace {
 
 int validate(const apic_config_t& c, std::string& why) {
@@ -1253,7 +1264,7 @@ static int setup(apic_sim* S) {
       // dense inverse of the tail system: Gauss-Jordan on the GPU (FP64), stored in FP32
       const int n = B.tail_n;
       double* work = (double*)S->dalloc(sizeof(double) * 2 * (size_t)n * n);
-      double* fbuf = (double*)S->dalloc(sizeof(double) * (size_t)n);
+      double* fbuf = (double*)S->dalloc(sizeof(double) * ((size_t)n + 1));  // + the barrier counter
       float* dense = (float*)S->dalloc(sizeof(float) * (size_t)n * n);
       if (!work || !fbuf || !dense) return S->status;
       aug.assign((size_t)n * 2 * n, 0.0);
@@ -1262,14 +1273,17 @@ static int setup(apic_sim* S) {
         aug[(size_t)r * 2 * n + n + r] = 1.0;
       }
       S->h2d(work, aug.data(), aug.size());
-      if (!S->ck(launch_dense_inverse<float>(work, fbuf, n, dense, S->stream), "dense inverse (tail)"))
+      if (!S->ck(launch_dense_inverse<float>(work, fbuf, n, dense, (unsigned long long*)(fbuf + n), d.err, d.wait_ns,
+                                             S->stream),
+                 "dense inverse (tail)"))
         return S->status;
       // rows padded to 16 bytes (bulk copies of row chunks)
       if (!S->ck(cudaMemcpy2DAsync(d.bcr + B.tail, sizeof(float) * B.tail_np, dense, sizeof(float) * n,
                                    sizeof(float) * n, n, cudaMemcpyDeviceToDevice, S->stream),
                  "tail copy"))
         return S->status;
-      if (!S->sync()) return S->status;  // the host vectors are refilled for the next instance
+      // the host vectors are refilled for the next instance
+      if (!S->sync() || !setup_wait_ok(S, "dense inverse (tail)")) return S->status;
       for (void* q : {(void*)dense, (void*)fbuf, (void*)work}) {
         auto it = std::find(S->blocks.begin(), S->blocks.end(), q);
         if (it != S->blocks.end()) S->blocks.erase(it);
@@ -1310,7 +1324,7 @@ static int setup(apic_sim* S) {
       // Gauss-Jordan on the GPU: n x 2n FP64 workspace, result stored in the particle precision
       int nu = I.coarse_n;
       double* work = (double*)S->dalloc(sizeof(double) * 2 * (size_t)nu * nu);
-      double* fbuf = (double*)S->dalloc(sizeof(double) * (size_t)nu);
+      double* fbuf = (double*)S->dalloc(sizeof(double) * ((size_t)nu + 1));  // + the barrier counter
       if (!work || !fbuf) return S->status;
       std::vector<double> aug((size_t)nu * 2 * nu, 0.0);
       for (int r = 0; r < nu; ++r) {
@@ -1318,9 +1332,11 @@ static int setup(apic_sim* S) {
         aug[(size_t)r * 2 * nu + nu + r] = 1.0;
       }
       S->h2d(work, aug.data(), aug.size());
-      if (!S->ck(launch_dense_inverse<Real>(work, fbuf, nu, (Real*)d.cinv + I.cinv_off, S->stream), "dense inverse"))
+      if (!S->ck(launch_dense_inverse<Real>(work, fbuf, nu, (Real*)d.cinv + I.cinv_off,
+                                            (unsigned long long*)(fbuf + nu), d.err, d.wait_ns, S->stream),
+                 "dense inverse"))
         return S->status;
-      if (!S->sync()) return S->status;
+      if (!S->sync() || !setup_wait_ok(S, "dense inverse")) return S->status;
       // release the workspace
       for (void* q : {(void*)fbuf, (void*)work}) {
         auto it = std::find(S->blocks.begin(), S->blocks.end(), q);

@@ -451,9 +451,12 @@ cudaError_t launch_solve_coop(const DevPtrs& d, const SolvePlan& plan, int block
 template <class Real>
 int coop_blocks(const SolvePlan& plan, int sms);
 // Dense inverse of an n x n FP64 matrix on the GPU (Gauss-Jordan, partial
-// pivoting); work: n x 2n doubles, a[n][n] row-major on entry; out: Real[n][n].
+// pivoting, one cooperative launch); work: n x 2n doubles, a[n][n] row-major
+// on entry; out: Real[n][n]; cnt: the launch's grid-barrier counter (zeroed
+// here); a barrier wait beyond wait_ns sets kErrTimeout in *err.
 template <class Real>
-cudaError_t launch_dense_inverse(double* work, double* fbuf, int n, Real* out, cudaStream_t s);
+cudaError_t launch_dense_inverse(double* work, double* fbuf, int n, Real* out, unsigned long long* cnt, int32_t* err,
+                                 unsigned long long wait_ns, cudaStream_t s);
 void launch_finish_injection(const DevPtrs& d, int pop, cudaStream_t s);
 
 // Block cyclic reduction solve (bcr.cu): iterative refinement with an FP64

@@ -683,57 +683,96 @@ __global__ void __launch_bounds__(256) k_coarse(DevPtrs d) {
   coarse_rows<Real>(d, I, (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), warps);
 }
 
-// Set-up: Gauss-Jordan with partial pivoting on an n x 2n FP64 matrix [A | I].
-// One CTA picks the pivot of column c, swaps it into row c, scales row c and
-// records the elimination factors; then every other row is updated.
-__global__ void __launch_bounds__(1024) k_gj_pivot(double* M, double* fb, int n, int c) {
+// Set-up: Gauss-Jordan with partial pivoting on an n x 2n FP64 matrix [A | I]
+// in one cooperative launch.  Per column c: CTA 0 picks the pivot, swaps it
+// into row c, scales row c and records the elimination factors fb; after a
+// grid barrier every warp updates its rows; a second barrier ends the column.
+// The barrier counts on *cnt (zeroed before the launch), each wait bounded by
+// wait_ns of global time (then kErrTimeout in *err and every CTA returns).
+__device__ bool gj_sync(unsigned long long* cnt, unsigned nb, int32_t* err, unsigned long long wait_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long old = atom_add_release_u64(cnt, 1ull);
+    const unsigned long long target = (old / nb + 1ull) * nb;
+    int ok = 1;
+    unsigned long long t0 = 0;
+    for (long long spins = 0; ld_acquire_u64(cnt) < target; ++spins) {
+      if ((spins & 255) == 255) {
+        if ((*(volatile int*)err) & kErrTimeout) {
+          ok = 0;
+          break;
+        }
+        const unsigned long long now = global_ns();
+        if (t0 == 0) t0 = now;
+        else if (now - t0 > wait_ns) {
+          atomicOr(err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(1024) k_gj(double* M, double* fb, int n, unsigned long long* cnt, int32_t* err,
+                                             unsigned long long wait_ns) {
   __shared__ double sv[1024];
   __shared__ int si[1024];
   const long long w = 2LL * n;
-  double best = -1.0;
-  int arg = c;
-  for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
-    double v = fabs(M[(long long)r * w + c]);
-    if (v > best) {
-      best = v;
-      arg = r;
-    }
-  }
-  sv[threadIdx.x] = best;
-  si[threadIdx.x] = arg;
-  __syncthreads();
-  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      double a = sv[threadIdx.x], b = sv[threadIdx.x + o];
-      int ia = si[threadIdx.x], ib = si[threadIdx.x + o];
-      if (b > a || (b == a && ib < ia)) {
-        sv[threadIdx.x] = b;
-        si[threadIdx.x] = ib;
+  const unsigned nb = gridDim.x;
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (int c = 0; c < n; ++c) {
+    if (blockIdx.x == 0) {
+      double best = -1.0;
+      int arg = c;
+      for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
+        const double v = fabs(M[(long long)r * w + c]);
+        if (v > best) {
+          best = v;
+          arg = r;
+        }
       }
+      sv[threadIdx.x] = best;
+      si[threadIdx.x] = arg;
+      __syncthreads();
+      for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+          const double x = sv[threadIdx.x], y = sv[threadIdx.x + o];
+          const int ix = si[threadIdx.x], iy = si[threadIdx.x + o];
+          if (y > x || (y == x && iy < ix)) {
+            sv[threadIdx.x] = y;
+            si[threadIdx.x] = iy;
+          }
+        }
+        __syncthreads();
+      }
+      const int p = si[0];
+      if (p != c)
+        for (long long k = threadIdx.x; k < w; k += blockDim.x) {
+          const double t = M[(long long)c * w + k];
+          M[(long long)c * w + k] = M[(long long)p * w + k];
+          M[(long long)p * w + k] = t;
+        }
+      __syncthreads();
+      const double inv = 1.0 / M[(long long)c * w + c];
+      __syncthreads();
+      for (long long k = threadIdx.x; k < w; k += blockDim.x) M[(long long)c * w + k] *= inv;
+      for (int r = threadIdx.x; r < n; r += blockDim.x) fb[r] = r == c ? 0.0 : M[(long long)r * w + c];
     }
-    __syncthreads();
+    if (!gj_sync(cnt, nb, err, wait_ns)) return;
+    for (long long r = gw; r < n; r += warps) {
+      const double f = fb[r];
+      if (f == 0.0) continue;
+      for (long long k = c + lane; k < w; k += 32) M[r * w + k] -= f * M[(long long)c * w + k];
+    }
+    if (!gj_sync(cnt, nb, err, wait_ns)) return;
   }
-  const int p = si[0];
-  if (p != c)
-    for (long long k = threadIdx.x; k < w; k += blockDim.x) {
-      double t = M[(long long)c * w + k];
-      M[(long long)c * w + k] = M[(long long)p * w + k];
-      M[(long long)p * w + k] = t;
-    }
-  __syncthreads();
-  const double inv = 1.0 / M[(long long)c * w + c];
-  __syncthreads();
-  for (long long k = threadIdx.x; k < w; k += blockDim.x) M[(long long)c * w + k] *= inv;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) fb[r] = r == c ? 0.0 : M[(long long)r * w + c];
-}
-
-__global__ void __launch_bounds__(256) k_gj_elim(double* M, const double* fb, int n, int c) {
-  const long long w = 2LL * n;
-  const int r = blockIdx.y;
-  const double f = fb[r];
-  if (f == 0.0) return;
-  for (long long k = c + (long long)blockIdx.x * blockDim.x + threadIdx.x; k < w; k += (long long)gridDim.x * blockDim.x)
-    M[(long long)r * w + k] -= f * M[(long long)c * w + k];
 }
 
 template <class Real>
@@ -1318,13 +1357,19 @@ cudaError_t launch_solve_coop<APIC_POISSON_REAL>(const DevPtrs& d, const SolvePl
 
 template <>
 cudaError_t launch_dense_inverse<APIC_POISSON_REAL>(double* work, double* fbuf, int n, APIC_POISSON_REAL* out,
-                                                    cudaStream_t s) {
-  for (int c = 0; c < n; ++c) {
-    k_gj_pivot<<<1, 1024, 0, s>>>(work, fbuf, n, c);
-    int bx = (int)((2LL * n - c + 255) / 256);
-    bx = bx > 16 ? 16 : bx;
-    k_gj_elim<<<dim3(bx, n), 256, 0, s>>>(work, fbuf, n, c);
-  }
+                                                    unsigned long long* cnt, int32_t* err,
+                                                    unsigned long long wait_ns, cudaStream_t s) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gj, 1024, 0);
+  if (e != cudaSuccess) return e;
+  if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
+  e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&work, &fbuf, &n, &cnt, &err, &wait_ns};
+  e = cudaLaunchCooperativeKernel((const void*)k_gj, dim3(sms), dim3(1024), args, 0, s);
+  if (e != cudaSuccess) return e;
   k_gj_store<APIC_POISSON_REAL><<<256, 256, 0, s>>>(work, n, out);
   return cudaGetLastError();
 }
