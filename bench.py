@@ -58,9 +58,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sort-interval", type=int, default=None,
                     help="override the workload's sort interval (steps between particle sorts)")
-    ap.add_argument("--autotune", action="store_true",
-                    help="choose the sort interval and the push's tiles with apic_autotune after the "
-                         "warm-up (untimed; on by default for batched48)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the workload's sort interval and the default tiles (by default apic_autotune "
+                         "chooses the sort interval and the push's tiles after the warm-up, untimed)")
     return ap.parse_args()
 
 
@@ -452,7 +452,7 @@ def main():
             sim.load_volume(sp, c["species"][sp]["n_init"], instance=k)
     sim.step(args.warmup)
     tuned = None
-    if args.autotune or (args.workload == "batched48" and args.sort_interval is None):
+    if not args.no_autotune and args.sort_interval is None:
         tuned = sim.autotune(max(8, args.warmup // 4))[0]
     tiles = sim.stats()
 

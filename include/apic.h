@@ -290,7 +290,7 @@ int apic_step_timed(apic_sim* sim, int32_t n_steps);
  * intervals c (2, 4, 6, 8, 12, 16, 24), whole sort intervals, c *
  * ceil(steps_per_trial / c) full steps each starting with a sort, timed with
  * CUDA events on the simulation's stream, and keeps the fastest; then, at
- * that interval, chunk groups 2, 4, 8, window rows 2, 4, 6, 8 and (FP32)
+ * that interval, chunk groups 2, 4, 8, window rows 2, 4, 6, 8, 12, 16 and (FP32)
  * chunks of 16 or 32 particles per thread (the step graphs recaptured for
  * each, one warm-up interval and then the same timed steps), keeping the
  * fastest of each.  apic_stats reports the choices.  The simulation

@@ -1872,7 +1872,7 @@ static int autotune_impl(apic_sim* S, int trial, int32_t* chosen, double* ms_out
     }
   }
   S->chunk_group = best_g;
-  const int rows_cand[] = {2, 4, 6, 8};
+  const int rows_cand[] = {2, 4, 6, 8, 12, 16};
   for (int r : rows_cand) {
     S->win_rows = r;
     drop_graphs(S);

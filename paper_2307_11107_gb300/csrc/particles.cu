@@ -31,7 +31,8 @@ constexpr int kFlushChunks = 31;  // chunks (of 2048 particles) between window f
 // (8192: fewer barriers per particle, coarser load balance); a window is
 // flushed before a cell's packed moments could hold 2^16 particles
 constexpr int kPush4ItemsMax = 32;
-constexpr int kWinRows = 8;      // node rows of the shared-memory deposit window at most
+constexpr int kWinRows = 8;      // node rows of the initial deposit's shared-memory window
+constexpr int kPushWinRows = 16; // node rows of the push's shared-memory deposit window at most
 constexpr int kWinMaxN2 = 513;   // widest grid row the window holds (larger grids deposit globally)
 constexpr int kInjRows = 3;      // node rows of the injection window (the last two cell rows)
 constexpr int kInjMaxN2 = 512;   // widest grid (cells in x2) the injection window holds
@@ -1503,19 +1504,20 @@ template <>
 int push_window_rows<Real>(int max_n2) {
   // window capacity: the widest grid of the batch, up to kWinMaxN2 - 1 cells
   // (wider grids deposit straight to global memory); node rows up to
-  // kWinRows within 32 KB (a 512-cell row of FP32 cell moments takes 8 KB;
-  // a smaller window leaves more L1 for the gather: on the 1024 x 512 grid 4
-  // rows pushed in 2.47 ms, 5 in 2.75, 8 in 3.67) and as many as keep
-  // APIC_PUSH_MIN_BLOCKS CTAs per SM resident.  Cached per width: the first
-  // call (at set-up, before any capture) queries the occupancy.
+  // kWinRows within 48 KB (a 512-cell row of FP32 cell moments takes 8 KB;
+  // on the 1024 x 512 grid with 1e8 particles the vector push took 1.55 ms
+  // with 4 rows, 1.47 with 6, 1.51 with 8, 1.75 with 10: wider windows leave
+  // less L1 to the gather) and as many as keep the push's CTAs per SM
+  // resident.  Cached per width: the first call (at set-up, before any
+  // capture) queries the occupancy.  apic_autotune tries 2 to 16 rows.
   const int win_n2 = max_n2 < kWinMaxN2 - 1 ? max_n2 : kWinMaxN2 - 1;
   static int rows_for[kWinMaxN2 + 1] = {};
   int rows = rows_for[win_n2];
   if (rows == 0) {
     const int row_bytes = (kF64 ? (win_n2 + 1) : 2 * win_n2) * (int)sizeof(unsigned long long);
-    rows = std::max(2, std::min(kWinRows, 32768 / std::max(1, row_bytes)));
+    rows = std::max(2, std::min(kWinRows, 49152 / std::max(1, row_bytes)));
     const char* e = std::getenv("APIC_WIN_ROWS");  // tuning: a fixed row count
-    if (e) rows = std::max(2, std::min(kWinRows, std::atoi(e)));
+    if (e) rows = std::max(2, std::min(kPushWinRows, std::atoi(e)));
     const void* kern = push4() ? (const void*)k_push4<false> : (const void*)k_push<false>;
     const int want = push4() ? (int)APIC_PUSH4_MIN_BLOCKS : (int)APIC_PUSH_MIN_BLOCKS;
     for (; !e && rows > 2; --rows) {
@@ -1534,7 +1536,7 @@ template <>
 void launch_push<Real>(const DevPtrs& d, int grid, int max_n2, bool chord, int win_rows, int chunk_group,
                        int chunk_items, long long particles, cudaStream_t s) {
   const int win_n2 = max_n2 < kWinMaxN2 - 1 ? max_n2 : kWinMaxN2 - 1;
-  const int rows = win_rows > 0 ? std::max(2, std::min(kWinRows, win_rows)) : push_window_rows<Real>(max_n2);
+  const int rows = win_rows > 0 ? std::max(2, std::min(kPushWinRows, win_rows)) : push_window_rows<Real>(max_n2);
   const int sm = push_smem(rows, win_n2, d.n_pop);
   const bool v4 = push4();
   const void* kern = v4 ? (chord ? (const void*)k_push4<true> : (const void*)k_push4<false>)

@@ -116,13 +116,13 @@ def test_autotune_keeps_a_candidate_and_stepping_stays_valid():
     assert ms[chosen] == min(ms.values())
     st = s.stats()
     assert st["sort_interval"] == chosen
-    assert st["chunk_group"] in (2, 4, 8) and st["win_rows"] in (2, 4, 6, 8) and st["chunk_items"] in (16, 32)
+    assert st["chunk_group"] in (2, 4, 8) and st["win_rows"] in (2, 4, 6, 8, 12, 16) and st["chunk_items"] in (16, 32)
     s.step(5)
     for k in range(len(cfgs)):
         t = s.tallies(k)
         # each interval candidate runs whole intervals, c * ceil(4 / c) steps;
-        # each of the 3 + 4 + 2 tile candidates one warm-up interval and as many
-        tiles = 9 * (chosen + chosen * -(-4 // chosen))
+        # each of the 3 + 6 + 2 tile candidates one warm-up interval and as many
+        tiles = 11 * (chosen + chosen * -(-4 // chosen))
         assert t["step"] == 4 + sum(c * -(-4 // c) for c in ms) + tiles + 5
         for sp in (0, 1):
             cnt = t["counts"][sp]
