@@ -1,5 +1,6 @@
-"""Precision form (FP32 particles, the FP32 block cyclic reduction inside the
-FP64 residual loop, fixed-point tallies) against the FP64 oracle.  Single
+"""Precision form (FP32 particles, the FP32 direct solve (block cyclic
+reduction or nested dissection) inside the FP64 residual loop, fixed-point
+tallies) against the FP64 oracle.  Single
 steps from identical states are compared element by element at FP32
 accuracy, also at the sizes where the kernels take their full-size paths;
 longer runs, whose trajectories separate (PIC dynamics amplify rounding), are
@@ -71,12 +72,13 @@ def _match(g, r, scale):
 def test_fp32_step_full_size_paths(apic, n1, n2, alpha, n):
     """One FP32 step at the sizes where the kernels take their full-size
     paths, from the same FP32-rounded states as the FP64 oracle, particles
-    sorted by row first (sort interval 8): on 256 x 128 cells the push's
-    8-row deposit window is kept across chunks and flushed after 31 of them,
-    chunk groups are taken from the counter and fast particles deposit outside
-    the window; on 64 x 512 cells the window has 4 rows and the Poisson solve
-    is the wide reduction kernel (513 unknowns per row) with level 1 applied
-    from the stencil (its blocks exceed L2).  rho, phi and every particle are
+    sorted by row first (sort interval 8): on 256 x 128 cells the vector
+    push's 8-row deposit window is kept across 4096-particle chunks and
+    flushed after 15 of them, chunk groups are taken from the counter, fast
+    particles deposit outside the window and the Poisson solve is the block
+    cyclic reduction (its blocks fit in L2); on 64 x 512 cells the window has
+    6 rows of 512 cells and the solve is the nested dissection (the
+    reduction's blocks would exceed L2).  rho, phi and every particle are
     compared with the oracle; a second step's density (the push's windowed
     deposit) is compared with the oracle's deposit of the GPU's own positions
     after the first step."""
