@@ -997,7 +997,12 @@ static int setup(apic_sim* S) {
       if (!use_nd[k]) continue;
       std::string why;
       int T = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
-      if (!nd_build(I.n1 - 1, I.N2, nd_coef, &levels[k][0], 16, T, false, nds[k], why) ||
+      static int leaf = -1;  // nodes per leaf piece at most (APIC_ND_LEAF, default 16)
+      if (leaf < 0) {
+        const char* e = std::getenv("APIC_ND_LEAF");
+        leaf = e ? std::max(1, std::min(256, std::atoi(e))) : 16;
+      }
+      if (!nd_build(I.n1 - 1, I.N2, nd_coef, &levels[k][0], leaf, T, false, nds[k], why) ||
           nds[k].depth > kNdMaxDepth)
         use_nd[k] = 0;  // the reduction (or multigrid) instead
     }
