@@ -968,6 +968,8 @@ static int setup(apic_sim* S) {
   std::vector<NdFactor> nds(ni);
   std::vector<char> use_nd(ni, 0);
   NdUpload ndu;
+  std::vector<int2> nd_flow;      // the dataflow sweeps' task orders
+  std::vector<int32_t> nd_need;   // tasks per front and sweep
   long long nd_w = 0;  // floats of one right-hand side's update vectors
   {
     const char* pc = std::getenv("APIC_PRECOND");
@@ -1143,6 +1145,44 @@ static int setup(apic_sim* S) {
       pl.bcr.n_inst = ni;
       pl.bcr.phases = phases;
       pl.bcr.nd_wrows = nd_w;
+      // dataflow sweeps when every instance is solved by nested dissection
+      // (APIC_ND_FLOW=0: one grid barrier per tree level instead): a task
+      // waits only for the fronts it reads (forward: its fronts' children,
+      // backward: their parents), every front counting its finished tasks
+      bool all_nd = true;
+      for (int k = 0; k < ni; ++k) all_nd = all_nd && use_nd[k];
+      if (const char* e = std::getenv("APIC_ND_FLOW")) all_nd = all_nd && std::atoi(e) != 0;
+      pl.bcr.nd_flow = all_nd ? 1 : 0;
+      nd_flow.clear();
+      nd_need.clear();
+      if (all_nd) {
+        const int nf = (int)ndu.fronts.size();
+        nd_need.assign(2 * (size_t)nf, 0);
+        std::vector<std::pair<std::pair<int, int>, int2>> fe, be;  // ((key, instance), (task, instance))
+        for (int k = 0; k < ni; ++k) {
+          const BcrInst& B = bcr_in[k];
+          for (int l = 0; l <= B.nd_depth; ++l) {
+            for (int t = B.nd_ft[l]; t < B.nd_ft[l + 1]; ++t) fe.push_back({{B.nd_depth - l, k}, make_int2(t, k)});
+            for (int t = B.nd_bt[l]; t < B.nd_bt[l + 1]; ++t) be.push_back({{l, k}, make_int2(t, k)});
+          }
+        }
+        auto by_key = [](const std::pair<std::pair<int, int>, int2>& a, const std::pair<std::pair<int, int>, int2>& b) {
+          return a.first < b.first || (a.first == b.first && a.second.x < b.second.x);
+        };
+        std::stable_sort(fe.begin(), fe.end(), by_key);
+        std::stable_sort(be.begin(), be.end(), by_key);
+        for (int sw = 0; sw < 2; ++sw)
+          for (const auto& x : sw == 0 ? fe : be) {
+            nd_flow.push_back(x.second);
+            const NdTask& T = ndu.tasks[x.second.x];
+            if (T.warp == 0) nd_need[(size_t)sw * nf + T.front] += 1;
+            else
+              for (int q = 0; q < T.n; ++q) nd_need[(size_t)sw * nf + T.front + q] += 1;
+          }
+        pl.bcr.nd_nf = (int)fe.size();
+        pl.bcr.nd_nb = (int)be.size();
+        pl.bcr.nd_fronts = nf;
+      }
     } else {
       pl.bcr.n_inst = 0;
     }
@@ -1237,7 +1277,17 @@ static int setup(apic_sim* S) {
       d.nd_gather = (const int32_t*)A(sizeof(int32_t) * ndu.gather.size());
       d.nd_task = (const int4*)A(sizeof(NdTask) * ndu.tasks.size());
       d.nd_w = (float*)A(sizeof(float) * kBcrMaxRhs * (size_t)std::max<long long>(1, nd_w));
+      if (pl.bcr.nd_flow) {
+        d.nd_flow = (const int2*)A(sizeof(int2) * nd_flow.size());
+        d.nd_need = (const int32_t*)A(sizeof(int32_t) * nd_need.size());
+        d.nd_done = (unsigned*)A(sizeof(unsigned) * 2 * kBcrMaxRhs * (size_t)pl.bcr.nd_fronts);
+        d.nd_next = (unsigned long long*)A(sizeof(unsigned long long) * 2);
+      }
       if (S->status != APIC_OK) return S->status;
+      if (pl.bcr.nd_flow) {
+        S->h2d((int2*)d.nd_flow, nd_flow.data(), nd_flow.size());
+        S->h2d((int32_t*)d.nd_need, nd_need.data(), nd_need.size());
+      }
       S->h2d((NdFront*)d.nd_front, ndu.fronts.data(), ndu.fronts.size());
       S->h2d((int32_t*)d.nd_idx, ndu.idx.data(), ndu.idx.size());
       S->h2d((int32_t*)d.nd_gather, ndu.gather.data(), ndu.gather.size());

@@ -196,6 +196,14 @@ struct DevPtrs {
   const int32_t* nd_gather;
   const int4* nd_task;
   float* nd_w;
+  // dataflow sweeps (BcrPlan::nd_flow): the forward then the backward task
+  // order (task, instance; every task after the tasks it depends on), the
+  // tasks each front takes per sweep [2][fronts], the done counters
+  // [2][kBcrMaxRhs][fronts] and the two sweeps' task counters
+  const int2* nd_flow;
+  const int32_t* nd_need;
+  unsigned* nd_done;
+  unsigned long long* nd_next;
 };
 
 #ifdef __CUDACC__
@@ -418,6 +426,9 @@ struct BcrPlan {
   int pad2;
   int64_t nd_wrows;         // floats of one right-hand side's update vectors in nd_w (all instances)
   int nd_floats;            // shared-memory floats a large nested-dissection front needs (0: none)
+  int nd_flow;              // 1: every instance by nested dissection, each sweep one dataflow phase
+  int nd_nf, nd_nb;         // entries of the forward and backward task orders
+  int nd_fronts;            // fronts of all instances
   int pad3;
 };
 

@@ -570,12 +570,11 @@ __device__ __forceinline__ void nd_back_store(const DevPtrs& d, const NdFront& F
 // by one bulk copy issued before the vectors are gathered; the vectors live in the wide kernel's
 // reduction buffer (a large front's at [0, kNdVecCap) and its task rows'
 // values after it; kNdWarpArea floats per warp, kNdTinyArea per 8-lane group).
-__device__ bool run_nd(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int l, int q, float* fb, float* eb,
-                       double* xb, float* wb) {
+__device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, const int4 T, float* fb, float* eb,
+                            double* xb, float* wb) {
   const float* f = fb + B.foff;
   float* e = eb + B.foff;
   double* x = xb + B.node_off;
-  const int4 T = d.nd_task[(kind == kNdFwd ? B.nd_ft[l] : B.nd_bt[l]) + q];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool fwd = kind == kNdFwd;
   const float* mat = (const float*)d.bcr;
@@ -743,6 +742,79 @@ __device__ bool run_nd(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int
   return true;
 }
 
+// Task q of level l of instance B's sweep `kind`.
+__device__ __forceinline__ bool run_nd(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int l, int q, float* fb,
+                                       float* eb, double* xb, float* wb) {
+  const int4 T = d.nd_task[(kind == kNdFwd ? B.nd_ft[l] : B.nd_bt[l]) + q];
+  return run_nd_task(d, c, B, kind, T, fb, eb, xb, wb);
+}
+
+// ---- dataflow sweeps (BcrPlan::nd_flow) ----
+// The CTAs take the sweep's tasks in the task order (right-hand side by
+// right-hand side) from a counter.  Before a task runs, thread f of the CTA
+// waits until front f of the task has what it reads: forward, both children
+// have finished all their tasks; backward, the parent has.  After the task,
+// each of its fronts counts one finished task (release; the waits acquire).
+// The order puts every task after those it waits for, and every CTA is
+// resident (cooperative launch), so the earliest unfinished task always
+// runs.  A wait gives up after d.wait_ns (kErrTimeout): false.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ bool nd_wait_deps(const DevPtrs& d, const BcrPlan& pl, int kind, int rh, const int4 T) {
+  const int nfr = T.w == 0 ? 1 : T.z;
+  const int sw = kind == kNdFwd ? 0 : 1;
+  const unsigned* done = d.nd_done + ((long long)sw * kBcrMaxRhs + rh) * pl.nd_fronts;
+  const int32_t* need = d.nd_need + (long long)sw * pl.nd_fronts;
+  bool ok = true;
+  if ((int)threadIdx.x < nfr) {
+    const NdFront& F = d.nd_front[T.x + threadIdx.x];
+    int dep[2] = {-1, -1};
+    if (kind == kNdFwd) {
+      dep[0] = F.child[0];
+      dep[1] = F.child[1];
+    } else {
+      dep[0] = F.parent;
+    }
+    unsigned long long t0 = 0;
+    for (int q = 0; q < 2 && ok; ++q) {
+      if (dep[q] < 0) continue;
+      const unsigned want = (unsigned)need[dep[q]];
+      for (long long spins = 0; ld_acquire_u32(done + dep[q]) < want; ++spins) {
+        if ((spins & 63) == 63) {
+          if ((*(volatile int*)d.err) & kErrTimeout) {
+            ok = false;
+            break;
+          }
+          const unsigned long long now = global_ns();
+          if (t0 == 0) t0 = now;
+          else if (now - t0 > d.wait_ns) {
+            atomicOr(d.err, kErrTimeout);
+            ok = false;
+            break;
+          }
+        }
+        __nanosleep(64);
+      }
+    }
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// After a task (its last __syncthreads behind it): each front counts one.
+__device__ __forceinline__ void nd_signal(const DevPtrs& d, const BcrPlan& pl, int kind, int rh, const int4 T) {
+  const int nfr = T.w == 0 ? 1 : T.z;
+  const int sw = kind == kNdFwd ? 0 : 1;
+  if ((int)threadIdx.x < nfr) {
+    unsigned* p = d.nd_done + ((long long)sw * kBcrMaxRhs + rh) * pl.nd_fronts + T.x + threadIdx.x;
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
+  }
+}
+
 // Fixed-order sum of part[r chunks + npre[k] .. r chunks + npre[k+1]) for
 // every system v = r ni + k (right-hand side r < nrhs, instance k) with
 // sel[v] (all when sel is null), one warp per system; out[v] in shared
@@ -840,6 +912,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   __shared__ int s_pre[kCoopMaxInst + 1];
   __shared__ int s_kind[kCoopMaxInst];
   __shared__ __align__(8) uint64_t s_bar;
+  __shared__ long long s_task;  // dataflow sweeps: the task this CTA takes
   __shared__ __align__(16) BcrInst s_b0;  // instance 0's table (one load per kernel instead of one per task)
   const int nb = gridDim.x, ni = d.n_inst, R = rhs.n, nv = R * ni;
   static_assert(kBcrMaxRhs == 3, "selections below");
@@ -913,6 +986,17 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
                  }
                  return rr;
                });
+    if constexpr ((kParts & 2) != 0) {
+      if (pl.nd_flow) {  // the dataflow sweeps' counters, for this pass
+        const long long nz = 2ll * kBcrMaxRhs * pl.nd_fronts;
+        for (long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x; z < nz; z += (long long)nb * blockDim.x)
+          d.nd_done[z] = 0u;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+          d.nd_next[0] = 0ull;
+          d.nd_next[1] = 0ull;
+        }
+      }
+    }
     load_tab(0);
     if (!grid_sync(d, nb)) return;
     store_tab();  // read after the synchronisation that ends inst_sums
@@ -940,6 +1024,36 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
       }
     }
     if (!__syncthreads_or(more)) break;
+    if constexpr (kParts == 2) {
+      if (pl.nd_flow) {  // nested dissection of every instance: one dataflow phase per sweep
+        for (int sw = 0; sw < 2; ++sw) {
+          const int kind = sw == 0 ? kNdFwd : kNdBack;
+          const int n = sw == 0 ? pl.nd_nf : pl.nd_nb;
+          const int2* list = d.nd_flow + (sw == 0 ? 0 : pl.nd_nf);
+          const long long total = (long long)R * n;
+          for (;;) {
+            if (threadIdx.x == 0) s_task = (long long)atomicAdd(d.nd_next + sw, 1ull);
+            __syncthreads();
+            const long long t = s_task;
+            __syncthreads();
+            if (t >= total) break;
+            const int rh = (int)(t / n);
+            const int2 en = list[t - (long long)rh * n];
+            if (!s_act[rh * ni + en.y]) continue;
+            const int4 T = d.nd_task[en.x];
+            if (!nd_wait_deps(d, pl, kind, rh, T)) return;
+            const BcrInst& B = en.y == 0 ? s_b0 : d.bcr_inst[en.y];
+            if (!run_nd_task(d, c, B, kind, T, d.bcr_f + rh * pl.rows, d.bcr_e + rh * pl.rows, x_of(rh),
+                             d.nd_w + rh * pl.nd_wrows))
+              return;
+            nd_signal(d, pl, kind, rh, T);
+          }
+          if (!grid_sync(d, nb)) return;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt[0] += 1;
+        continue;
+      }
+    }
     // the reduction passes: phase p runs the p-th stage of every instance
     for (int p = 0; p < pl.phases; ++p) {
       if (p > 0) {  // the phase's task tables (loaded before the last barrier)
