@@ -1281,7 +1281,6 @@ static int setup(apic_sim* S) {
         d.nd_flow = (const int2*)A(sizeof(int2) * nd_flow.size());
         d.nd_need = (const int32_t*)A(sizeof(int32_t) * nd_need.size());
         d.nd_done = (unsigned*)A(sizeof(unsigned) * 2 * kBcrMaxRhs * (size_t)pl.bcr.nd_fronts);
-        d.nd_next = (unsigned long long*)A(sizeof(unsigned long long) * 2);
       }
       if (S->status != APIC_OK) return S->status;
       if (pl.bcr.nd_flow) {

@@ -198,12 +198,11 @@ struct DevPtrs {
   float* nd_w;
   // dataflow sweeps (BcrPlan::nd_flow): the forward then the backward task
   // order (task, instance; every task after the tasks it depends on), the
-  // tasks each front takes per sweep [2][fronts], the done counters
-  // [2][kBcrMaxRhs][fronts] and the two sweeps' task counters
+  // tasks each front takes per sweep [2][fronts] and the done counters
+  // [2][kBcrMaxRhs][fronts]
   const int2* nd_flow;
   const int32_t* nd_need;
   unsigned* nd_done;
-  unsigned long long* nd_next;
 };
 
 #ifdef __CUDACC__

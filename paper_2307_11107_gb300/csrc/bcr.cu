@@ -41,8 +41,11 @@ constexpr int kRangesPerPass = kBcrThreads / kBcrSub;  // partial-sum ranges a C
 // 8-lane group, four groups per warp)
 constexpr int kNdVecCap = kBcrWarps * kBcrMaxNWide - kNdTaskRows;
 static_assert(kNdStageFloats == kBcrWarps * kNdWarpStage && kNdTaskFronts <= kBcrWarps, "one front per warp");
-constexpr int kNdWarpArea = 2 * kNdWarpMaxS + kNdWarpMaxU;
-constexpr int kNdTinyArea = 2 * kNdTinyS + kNdTinyU;
+// per-warp area, forward: v_S, z_S, the U rows, the separator's node indices;
+// backward: x_U, N x_U, the separator's node indices, z_S, x (doubles)
+constexpr int kNdWarpArea = 8 * kNdWarpMaxS;   // 512 floats
+constexpr int kNdTinyArea = 8 * kNdTinyS;      // 128 floats, four groups per warp
+static_assert(kNdWarpMaxU == 3 * kNdWarpMaxS && kNdTinyU == 3 * kNdTinyS, "area layout");
 static_assert(kNdWarpArea <= kBcrMaxNWide && 4 * kNdTinyArea <= kNdWarpArea && kNdTinyArea % 4 == 0, "areas");
 static_assert(kRangesPerPass * kBcrSub == kBcrThreads, "whole ranges per pass");
 
@@ -472,7 +475,8 @@ __device__ __forceinline__ int warp_max(int x) {
 // children's update vectors hold for it, child 0 then child 1.  Four
 // entries per thread in flight: their table entries first, then the values.
 __device__ __forceinline__ void nd_rhs_into(const DevPtrs& d, const NdFront& F, int p0, int n, int n_pad, float* out,
-                                            const float* f, const float* w, int lane, int stride) {
+                                            const float* f, const float* w, int lane, int stride,
+                                            int* sidx = nullptr) {
   constexpr int U = 4;
   for (int b = lane; b < n_pad; b += U * stride) {
     int2 g[U];
@@ -492,8 +496,29 @@ __device__ __forceinline__ void nd_rhs_into(const DevPtrs& d, const NdFront& F, 
       val[u] = x;
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+    for (int u = 0; u < U; ++u) {
       if (b + u * stride < n_pad) out[b + u * stride] = val[u];
+      if (sidx && ix[u] >= 0) sidx[b + u * stride] = ix[u];  // the separator's node (p0 = 0)
+    }
+  }
+}
+
+// The separator's node indices, z_S (e) and x there, for F's backward rows
+// (all loads of a thread in flight at once).
+__device__ __forceinline__ void nd_sx_into(const DevPtrs& d, const NdFront& F, int* sidx, float* sz, double* sx,
+                                           const float* e, const double* x, int N, int lane, int stride) {
+  constexpr int U = 4;
+  for (int b = lane; b < F.s; b += U * stride) {
+    int ix[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) ix[u] = b + u * stride < F.s ? d.nd_idx[F.S + b + u * stride] : -1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (ix[u] < 0) continue;
+      sidx[b + u * stride] = ix[u];
+      sz[b + u * stride] = e[ix[u]];
+      sx[b + u * stride] = x[(long long)ix[u] + N];
+    }
   }
 }
 
@@ -659,8 +684,9 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
       float* vs = a0;                    // v_S, kNdTinyS floats
       float* rs = a0 + kNdTinyS;         // z_S
       float* ru = a0 + 2 * kNdTinyS;     // the U rows' right-hand sides, then W
+      int* si = (int*)(a0 + 5 * kNdTinyS);  // the separator's nodes
       if (has) {
-        nd_rhs_into(d, F, 0, F.s, F.sp, vs, f, wb, gl, 8);
+        nd_rhs_into(d, F, 0, F.s, F.sp, vs, f, wb, gl, 8, si);
         nd_rhs_into(d, F, F.s, F.u, F.u, ru, f, wb, gl, 8);
       }
       __syncthreads();
@@ -676,13 +702,19 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
       }
       __syncwarp();
       if (has) {
-        for (int a = gl; a < F.s; a += 8) e[d.nd_idx[F.S + a]] = rs[a];
+        for (int a = gl; a < F.s; a += 8) e[si[a]] = rs[a];
         for (int a = gl; a < F.u; a += 8) wb[F.W + a] = ru[a];
       }
     } else {
       float* vu = a0;                    // x_U, kNdTinyU floats
       float* rs = a0 + kNdTinyU;         // N x_U
-      if (has) nd_xu_into(d, F, F.up, vu, e, gl, 8);
+      int* si = (int*)(a0 + 4 * kNdTinyS);
+      float* sz = a0 + 5 * kNdTinyS;
+      double* sx = (double*)(a0 + 6 * kNdTinyS);
+      if (has) {
+        nd_xu_into(d, F, F.up, vu, e, gl, 8);
+        nd_sx_into(d, F, si, sz, sx, e, x, B.N, gl, 8);
+      }
       __syncthreads();
       if (!wait()) return false;
       if (nmax > 0) {
@@ -691,7 +723,12 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
         rows_dot_grp<8>(m, n4, nrows, nmax, (const float4*)vu, n4, gl, put);
       }
       __syncwarp();
-      if (has) nd_back_store(d, F, 0, F.s, F.u > 0 ? rs : nullptr, e, x, B.N, gl, 8);
+      if (has)
+        for (int a = gl; a < F.s; a += 8) {
+          const float val = sz[a] - (F.u > 0 ? rs[a] : 0.0f);
+          e[si[a]] = val;
+          x[(long long)si[a] + B.N] = sx[a] + (double)val;
+        }
     }
     __syncthreads();
     return true;
@@ -705,8 +742,9 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
     float* vs = a0;                      // v_S, kNdWarpMaxS floats
     float* rs = a0 + kNdWarpMaxS;        // z_S
     float* ru = a0 + 2 * kNdWarpMaxS;    // the U rows' right-hand sides, then W
+    int* si = (int*)(a0 + 5 * kNdWarpMaxS);  // the separator's nodes
     if (has) {
-      nd_rhs_into(d, F, 0, F.s, F.sp, vs, f, wb, lane, 32);
+      nd_rhs_into(d, F, 0, F.s, F.sp, vs, f, wb, lane, 32, si);
       nd_rhs_into(d, F, F.s, F.u, F.u, ru, f, wb, lane, 32);
     }
     __syncthreads();
@@ -714,26 +752,36 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
     if (has) {
       const int fs = F.s;
       rows_dot_any(F.sp >> 2, at(F.FM), F.sp >> 2, 0, F.s + F.u, 0, (const float4*)vs, lane, 0, 1,
-                  [=](int a, float acc) {
-                    if (a < fs) rs[a] = acc;
-                    else ru[a - fs] -= acc;
-                  });
+                   [=](int a, float acc) {
+                     if (a < fs) rs[a] = acc;
+                     else ru[a - fs] -= acc;
+                   });
       __syncwarp();
-      nd_fwd_store(d, F, 0, F.s, rs, e, wb, lane, 32);
+      for (int a = lane; a < F.s; a += 32) e[si[a]] = rs[a];
       for (int a = lane; a < F.u; a += 32) wb[F.W + a] = ru[a];
     }
   } else {
     float* vu = a0;                      // x_U, kNdWarpMaxU floats
     float* rs = a0 + kNdWarpMaxU;        // N x_U
-    if (has) nd_xu_into(d, F, F.up, vu, e, lane, 32);
+    int* si = (int*)(a0 + 4 * kNdWarpMaxS);
+    float* sz = a0 + 5 * kNdWarpMaxS;
+    double* sx = (double*)(a0 + 6 * kNdWarpMaxS);
+    if (has) {
+      nd_xu_into(d, F, F.up, vu, e, lane, 32);
+      nd_sx_into(d, F, si, sz, sx, e, x, B.N, lane, 32);
+    }
     __syncthreads();
     if (!wait()) return false;
     if (has) {
       if (F.u > 0)
         rows_dot_any(F.up >> 2, at(F.NB), F.up >> 2, 0, F.s, 0, (const float4*)vu, lane, 0, 1,
-                    [=](int a, float acc) { rs[a] = acc; });
+                     [=](int a, float acc) { rs[a] = acc; });
       __syncwarp();
-      nd_back_store(d, F, 0, F.s, F.u > 0 ? rs : nullptr, e, x, B.N, lane, 32);
+      for (int a = lane; a < F.s; a += 32) {
+        const float val = sz[a] - (F.u > 0 ? rs[a] : 0.0f);
+        e[si[a]] = val;
+        x[(long long)si[a] + B.N] = sx[a] + (double)val;
+      }
     }
   }
   // the next task's copy overwrites the staged rows and its vectors the
@@ -750,14 +798,14 @@ __device__ __forceinline__ bool run_nd(const DevPtrs& d, Ctx& c, const BcrInst& 
 }
 
 // ---- dataflow sweeps (BcrPlan::nd_flow) ----
-// The CTAs take the sweep's tasks in the task order (right-hand side by
-// right-hand side) from a counter.  Before a task runs, thread f of the CTA
+// CTA b takes the sweep's tasks b, b + nb, ... of the task order (right-hand
+// side by right-hand side).  Before a task runs, thread f of the CTA
 // waits until front f of the task has what it reads: forward, both children
 // have finished all their tasks; backward, the parent has.  After the task,
 // each of its fronts counts one finished task (release; the waits acquire).
-// The order puts every task after those it waits for, and every CTA is
-// resident (cooperative launch), so the earliest unfinished task always
-// runs.  A wait gives up after d.wait_ns (kErrTimeout): false.
+// The order puts every task after those it waits for, every CTA runs its
+// tasks in order and every CTA is resident (cooperative launch), so the
+// earliest unfinished task always runs.  A wait gives up after d.wait_ns (kErrTimeout): false.
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -912,7 +960,6 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   __shared__ int s_pre[kCoopMaxInst + 1];
   __shared__ int s_kind[kCoopMaxInst];
   __shared__ __align__(8) uint64_t s_bar;
-  __shared__ long long s_task;  // dataflow sweeps: the task this CTA takes
   __shared__ __align__(16) BcrInst s_b0;  // instance 0's table (one load per kernel instead of one per task)
   const int nb = gridDim.x, ni = d.n_inst, R = rhs.n, nv = R * ni;
   static_assert(kBcrMaxRhs == 3, "selections below");
@@ -991,10 +1038,6 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
         const long long nz = 2ll * kBcrMaxRhs * pl.nd_fronts;
         for (long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x; z < nz; z += (long long)nb * blockDim.x)
           d.nd_done[z] = 0u;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-          d.nd_next[0] = 0ull;
-          d.nd_next[1] = 0ull;
-        }
       }
     }
     load_tab(0);
@@ -1031,22 +1074,25 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
           const int n = sw == 0 ? pl.nd_nf : pl.nd_nb;
           const int2* list = d.nd_flow + (sw == 0 ? 0 : pl.nd_nf);
           const long long total = (long long)R * n;
-          for (;;) {
-            if (threadIdx.x == 0) s_task = (long long)atomicAdd(d.nd_next + sw, 1ull);
-            __syncthreads();
-            const long long t = s_task;
-            __syncthreads();
-            if (t >= total) break;
+          // CTA b takes tasks b, b + nb, ... (each after the tasks it waits
+          // for); the next task's entry is loaded while this one runs
+          auto entry = [&](long long t) { return list[t - (t / n) * n]; };
+          int2 en = blockIdx.x < total ? entry(blockIdx.x) : make_int2(0, 0);
+          int4 T = blockIdx.x < total ? d.nd_task[en.x] : make_int4(0, 0, 0, 0);
+          for (long long t = blockIdx.x; t < total; t += nb) {
             const int rh = (int)(t / n);
-            const int2 en = list[t - (long long)rh * n];
-            if (!s_act[rh * ni + en.y]) continue;
-            const int4 T = d.nd_task[en.x];
-            if (!nd_wait_deps(d, pl, kind, rh, T)) return;
-            const BcrInst& B = en.y == 0 ? s_b0 : d.bcr_inst[en.y];
-            if (!run_nd_task(d, c, B, kind, T, d.bcr_f + rh * pl.rows, d.bcr_e + rh * pl.rows, x_of(rh),
-                             d.nd_w + rh * pl.nd_wrows))
-              return;
-            nd_signal(d, pl, kind, rh, T);
+            const long long tn = t + nb;
+            const int2 en_n = tn < total ? entry(tn) : en;
+            if (s_act[rh * ni + en.y]) {
+              if (!nd_wait_deps(d, pl, kind, rh, T)) return;
+              const BcrInst& B = en.y == 0 ? s_b0 : d.bcr_inst[en.y];
+              if (!run_nd_task(d, c, B, kind, T, d.bcr_f + rh * pl.rows, d.bcr_e + rh * pl.rows, x_of(rh),
+                               d.nd_w + rh * pl.nd_wrows))
+                return;
+              nd_signal(d, pl, kind, rh, T);
+            }
+            en = en_n;
+            if (tn < total) T = d.nd_task[en.x];
           }
           if (!grid_sync(d, nb)) return;
         }
