@@ -374,12 +374,12 @@ constexpr int kNdMaxDepth = 40;
 constexpr int kNdWarpMaxS = 64;     // fronts with a separator up to this size run one per warp
 constexpr int kNdWarpMaxU = 192;    // ... and an update set up to this size
 constexpr int kNdTaskFloats = 16384;  // matrix floats per task of a large front (row chunks)
-constexpr int kNdTaskFronts = 16;     // small fronts per task at most (one per warp)
-constexpr int kNdTaskRows = 4096;     // rows per task of a large front at most (kNdTaskFloats / 4)
+constexpr int kNdTaskFronts = 8;      // small fronts per task at most (one per warp of a half CTA)
+constexpr int kNdTaskRows = 2048;     // rows per task of a large front at most
 constexpr int kNdWarpStage = 2048;    // matrix floats of a warp's front (staged in shared memory) at most
-constexpr int kNdStageFloats = 16 * kNdWarpStage;  // a task's staged matrix rows at most (16 warps per CTA)
-static_assert(kNdTaskFloats <= kNdStageFloats && kNdWarpStage * kNdTaskFronts <= kNdStageFloats, "tasks stage whole");
-static_assert(kNdTaskFloats / 4 <= kNdTaskRows, "a task of 4-float rows fits");
+constexpr int kNdStageFloats = 16 * kNdWarpStage;  // the CTA's stage; a task's matrix rows take half at most
+static_assert(kNdTaskFloats <= kNdStageFloats / 2 && kNdWarpStage * kNdTaskFronts <= kNdStageFloats / 2,
+              "tasks stage whole in a half CTA's stage");
 struct BcrInst {
   int K;                    // 2^K >= n1
   int N;                    // block size N2

@@ -40,7 +40,7 @@ constexpr int kRangesPerPass = kBcrThreads / kBcrSub;  // partial-sum ranges a C
 // and U rows (kNdWarpArea floats per warp); a tiny front's (kNdTinyArea per
 // 8-lane group, four groups per warp)
 constexpr int kNdVecCap = kBcrWarps * kBcrMaxNWide - kNdTaskRows;
-static_assert(kNdStageFloats == kBcrWarps * kNdWarpStage && kNdTaskFronts <= kBcrWarps, "one front per warp");
+static_assert(kNdStageFloats == kBcrWarps * kNdWarpStage && kNdTaskFronts <= kBcrWarps / 2, "one front per warp");
 // per-warp area, forward: v_S, z_S, the U rows, the separator's node indices;
 // backward: x_U, N x_U, the separator's node indices, z_S, x (doubles)
 constexpr int kNdWarpArea = 8 * kNdWarpMaxS;   // 512 floats
@@ -595,12 +595,61 @@ __device__ __forceinline__ void nd_back_store(const DevPtrs& d, const NdFront& F
 // by one bulk copy issued before the vectors are gathered; the vectors live in the wide kernel's
 // reduction buffer (a large front's at [0, kNdVecCap) and its task rows'
 // values after it; kNdWarpArea floats per warp, kNdTinyArea per 8-lane group).
-__device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, const int4 T, float* fb, float* eb,
-                            double* xb, float* wb) {
+// A nested-dissection worker: the whole CTA (barrier 0), or one half of it
+// (named barriers 1 and 2, 256 threads each) in the dataflow sweeps, so that
+// an SM has two tasks in flight.  Its vectors, stage and copy barrier are its
+// own.
+struct NdUnit {
+  int t, n, nw;   // thread within the unit, threads, warps
+  int id;         // named barrier (0: __syncthreads)
+  float* red;     // the unit's vector areas
+  float* sbuf;    // the unit's matrix stage
+  uint64_t* bar;  // the unit's copy barrier
+  int vcap;       // floats of a large front's vector; its task rows' values follow
+  __device__ __forceinline__ void sync() const {
+    if (id == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+  }
+  __device__ __forceinline__ bool sync_and(bool p) const {
+    if (id == 0) return __syncthreads_and(p) != 0;
+    unsigned r;
+    asm volatile(
+        "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.and.pred po, %2, %3, pi;\n"
+        " selp.u32 %0, 1, 0, po;\n}\n"
+        : "=r"(r)
+        : "r"((unsigned)p), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+  }
+};
+
+// mbar_wait for a unit's copies (every thread of the unit).
+__device__ bool nd_mbar_wait(const NdUnit& U, uint64_t* bar, unsigned parity, int32_t* err) {
+  bool ok = false;
+  for (long long k = 0; k < (1ll << 22); ++k) {
+    if (mbar_try_wait(bar, parity)) {
+      ok = true;
+      break;
+    }
+    if ((k & 1023) == 1023 && ((*(volatile int32_t*)err) & kErrTimeout)) break;
+    __nanosleep(32);
+  }
+  if (!ok) {
+    atomicOr(err, kErrTimeout);
+    for (long long k = 0; k < (1ll << 22); ++k) {
+      if (mbar_try_wait(bar, parity)) break;
+      __nanosleep(64);
+    }
+  }
+  return U.sync_and(ok);
+}
+
+__device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const NdUnit& U, const BcrInst& B, int kind, const int4 T,
+                            float* fb, float* eb, double* xb, float* wb) {
   const float* f = fb + B.foff;
   float* e = eb + B.foff;
   double* x = xb + B.node_off;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = U.t & 31, warp = U.t >> 5;
   const bool fwd = kind == kNdFwd;
   const float* mat = (const float*)d.bcr;
   // the task's matrix range [m0, m1)
@@ -619,51 +668,51 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
   }
   // the layout keeps every task within the stage (kNdStageFloats): a larger
   // one is a table fault, reported as a capacity error and not computed
-  if (m1 - m0 > kNdStageFloats) {
-    if (threadIdx.x == 0) atomicOr(c.err, kErrCapacity);
+  if (m1 - m0 > kNdStageFloats / 2) {
+    if (U.t == 0) atomicOr(c.err, kErrCapacity);
     return true;
   }
   const bool staged = m1 > m0;
-  if (staged && threadIdx.x == 0) {
+  if (staged && U.t == 0) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the earlier tasks' reads
-    mbar_expect_tx(c.bar, (unsigned)(m1 - m0) * 4u);
-    bulk_g2s(c.sbuf, mat + m0, (unsigned)(m1 - m0) * 4u, c.bar);
+    mbar_expect_tx(U.bar, (unsigned)(m1 - m0) * 4u);
+    bulk_g2s(U.sbuf, mat + m0, (unsigned)(m1 - m0) * 4u, U.bar);
   }
   // matrix float o of the buffer in the stage
-  auto at = [&](long long o) { return c.sbuf + (o - m0); };
+  auto at = [&](long long o) { return U.sbuf + (o - m0); };
   auto wait = [&]() {
     if (!staged) return true;
-    if (!mbar_wait(c.bar, c.parity, c.err)) return false;
+    if (!nd_mbar_wait(U, U.bar, c.parity, c.err)) return false;
     c.parity ^= 1u;
     return true;
   };
   if (T.w == 0) {
     const NdFront F = d.nd_front[T.x];
-    float* v = c.red;
-    float* res = c.red + kNdVecCap;
+    float* v = U.red;
+    float* res = U.red + U.vcap;
     const int r0 = T.y, r1 = T.y + T.z;
     if (fwd) {
-      nd_rhs_into(d, F, 0, F.s, F.sp, v, f, wb, threadIdx.x, blockDim.x);
+      nd_rhs_into(d, F, 0, F.s, F.sp, v, f, wb, U.t, U.n);
       const int u0 = max(r0, F.s);  // the task's U rows start with their right-hand sides
-      if (u0 < r1) nd_rhs_into(d, F, u0, r1 - u0, r1 - u0, res + (u0 - r0), f, wb, threadIdx.x, blockDim.x);
-      __syncthreads();
+      if (u0 < r1) nd_rhs_into(d, F, u0, r1 - u0, r1 - u0, res + (u0 - r0), f, wb, U.t, U.n);
+      U.sync();
       if (!wait()) return false;
       const int fs = F.s;
-      rows_dot_any(F.sp >> 2, at(m0), F.sp >> 2, r0, r1, r0, (const float4*)v, lane, warp, kBcrWarps,
+      rows_dot_any(F.sp >> 2, at(m0), F.sp >> 2, r0, r1, r0, (const float4*)v, lane, warp, U.nw,
                   [=](int a, float acc) { res[a - r0] = a < fs ? acc : res[a - r0] - acc; });
-      __syncthreads();
-      nd_fwd_store(d, F, r0, r1, res, e, wb, threadIdx.x, blockDim.x);
+      U.sync();
+      nd_fwd_store(d, F, r0, r1, res, e, wb, U.t, U.n);
     } else {
-      nd_xu_into(d, F, F.up, v, e, threadIdx.x, blockDim.x);
-      __syncthreads();
+      nd_xu_into(d, F, F.up, v, e, U.t, U.n);
+      U.sync();
       if (!wait()) return false;
       if (F.u > 0)
-        rows_dot_any(F.up >> 2, at(m0), F.up >> 2, r0, r1, r0, (const float4*)v, lane, warp, kBcrWarps,
+        rows_dot_any(F.up >> 2, at(m0), F.up >> 2, r0, r1, r0, (const float4*)v, lane, warp, U.nw,
                     [=](int a, float acc) { res[a - r0] = acc; });
-      __syncthreads();
-      nd_back_store(d, F, r0, r1, F.u > 0 ? res : nullptr, e, x, B.N, threadIdx.x, blockDim.x);
+      U.sync();
+      nd_back_store(d, F, r0, r1, F.u > 0 ? res : nullptr, e, x, B.N, U.t, U.n);
     }
-    __syncthreads();
+    U.sync();
     return true;
   }
   if (T.w == 2) {
@@ -672,7 +721,7 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
     // four float4), 8 backward (up <= kNdTinyU = 48): the sums do not depend
     // on the other fronts of the warp
     const int g = lane >> 3, gl = lane & 7;
-    float* a0 = c.red + warp * kNdWarpArea + g * kNdTinyArea;
+    float* a0 = U.red + warp * kNdWarpArea + g * kNdTinyArea;
     const int k = 4 * warp + g;
     const bool has = k < T.z;
     NdFront F;
@@ -689,10 +738,10 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
         nd_rhs_into(d, F, 0, F.s, F.sp, vs, f, wb, gl, 8, si);
         nd_rhs_into(d, F, F.s, F.u, F.u, ru, f, wb, gl, 8);
       }
-      __syncthreads();
+      U.sync();
       if (!wait()) return false;
       if (nmax > 0) {
-        const float* m = has ? at(F.FM) : c.sbuf;
+        const float* m = has ? at(F.FM) : U.sbuf;
         const int fs = has ? F.s : 0;
         auto put = [=](int a, float acc) {
           if (a < fs) rs[a] = acc;
@@ -715,10 +764,10 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
         nd_xu_into(d, F, F.up, vu, e, gl, 8);
         nd_sx_into(d, F, si, sz, sx, e, x, B.N, gl, 8);
       }
-      __syncthreads();
+      U.sync();
       if (!wait()) return false;
       if (nmax > 0) {
-        const float* m = has ? at(F.NB) : c.sbuf;
+        const float* m = has ? at(F.NB) : U.sbuf;
         auto put = [=](int a, float acc) { rs[a] = acc; };
         rows_dot_grp<8>(m, n4, nrows, nmax, (const float4*)vu, n4, gl, put);
       }
@@ -730,11 +779,11 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
           x[(long long)si[a] + B.N] = sx[a] + (double)val;
         }
     }
-    __syncthreads();
+    U.sync();
     return true;
   }
   // small fronts, one per warp
-  float* a0 = c.red + warp * kNdWarpArea;
+  float* a0 = U.red + warp * kNdWarpArea;
   const bool has = warp < T.z;
   NdFront F;
   if (has) F = d.nd_front[T.x + warp];
@@ -747,7 +796,7 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
       nd_rhs_into(d, F, 0, F.s, F.sp, vs, f, wb, lane, 32, si);
       nd_rhs_into(d, F, F.s, F.u, F.u, ru, f, wb, lane, 32);
     }
-    __syncthreads();
+    U.sync();
     if (!wait()) return false;
     if (has) {
       const int fs = F.s;
@@ -770,7 +819,7 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
       nd_xu_into(d, F, F.up, vu, e, lane, 32);
       nd_sx_into(d, F, si, sz, sx, e, x, B.N, lane, 32);
     }
-    __syncthreads();
+    U.sync();
     if (!wait()) return false;
     if (has) {
       if (F.u > 0)
@@ -786,7 +835,7 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
   }
   // the next task's copy overwrites the staged rows and its vectors the
   // per-warp areas: every warp finishes here first
-  __syncthreads();
+  U.sync();
   return true;
 }
 
@@ -794,7 +843,8 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind
 __device__ __forceinline__ bool run_nd(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int l, int q, float* fb,
                                        float* eb, double* xb, float* wb) {
   const int4 T = d.nd_task[(kind == kNdFwd ? B.nd_ft[l] : B.nd_bt[l]) + q];
-  return run_nd_task(d, c, B, kind, T, fb, eb, xb, wb);
+  const NdUnit U{(int)threadIdx.x, (int)blockDim.x, kBcrWarps, 0, c.red, c.sbuf, c.bar, kNdVecCap};
+  return run_nd_task(d, c, U, B, kind, T, fb, eb, xb, wb);
 }
 
 // ---- dataflow sweeps (BcrPlan::nd_flow) ----
@@ -812,14 +862,14 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-__device__ bool nd_wait_deps(const DevPtrs& d, const BcrPlan& pl, int kind, int rh, const int4 T) {
+__device__ bool nd_wait_deps(const DevPtrs& d, const BcrPlan& pl, const NdUnit& U, int kind, int rh, const int4 T) {
   const int nfr = T.w == 0 ? 1 : T.z;
   const int sw = kind == kNdFwd ? 0 : 1;
   const unsigned* done = d.nd_done + ((long long)sw * kBcrMaxRhs + rh) * pl.nd_fronts;
   const int32_t* need = d.nd_need + (long long)sw * pl.nd_fronts;
   bool ok = true;
-  if ((int)threadIdx.x < nfr) {
-    const NdFront& F = d.nd_front[T.x + threadIdx.x];
+  if (U.t < nfr) {
+    const NdFront& F = d.nd_front[T.x + U.t];
     int dep[2] = {-1, -1};
     if (kind == kNdFwd) {
       dep[0] = F.child[0];
@@ -849,15 +899,16 @@ __device__ bool nd_wait_deps(const DevPtrs& d, const BcrPlan& pl, int kind, int 
       }
     }
   }
-  return __syncthreads_and(ok) != 0;
+  return U.sync_and(ok);
 }
 
-// After a task (its last __syncthreads behind it): each front counts one.
-__device__ __forceinline__ void nd_signal(const DevPtrs& d, const BcrPlan& pl, int kind, int rh, const int4 T) {
+// After a task (its last unit barrier behind it): each front counts one.
+__device__ __forceinline__ void nd_signal(const DevPtrs& d, const BcrPlan& pl, const NdUnit& U, int kind, int rh,
+                                          const int4 T) {
   const int nfr = T.w == 0 ? 1 : T.z;
   const int sw = kind == kNdFwd ? 0 : 1;
-  if ((int)threadIdx.x < nfr) {
-    unsigned* p = d.nd_done + ((long long)sw * kBcrMaxRhs + rh) * pl.nd_fronts + T.x + threadIdx.x;
+  if (U.t < nfr) {
+    unsigned* p = d.nd_done + ((long long)sw * kBcrMaxRhs + rh) * pl.nd_fronts + T.x + U.t;
     __threadfence();
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
   }
@@ -960,6 +1011,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   __shared__ int s_pre[kCoopMaxInst + 1];
   __shared__ int s_kind[kCoopMaxInst];
   __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_bar2;  // the second unit's copy barrier (dataflow sweeps)
   __shared__ __align__(16) BcrInst s_b0;  // instance 0's table (one load per kernel instead of one per task)
   const int nb = gridDim.x, ni = d.n_inst, R = rhs.n, nv = R * ni;
   static_assert(kBcrMaxRhs == 3, "selections below");
@@ -976,7 +1028,10 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   }
   const int tsub = pl.task_sub;
   for (int v = threadIdx.x; v < nv; v += blockDim.x) s_act[v] = only < 0 || v % ni == only;
-  if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    mbar_init(&s_bar2, 1);
+  }
   for (int w = threadIdx.x; w < (int)(sizeof(BcrInst) / 4); w += blockDim.x)
     ((int*)&s_b0)[w] = ((const int*)d.bcr_inst)[w];
   // this thread's entries of the next phase's task tables, loaded before a
@@ -1074,26 +1129,35 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
           const int n = sw == 0 ? pl.nd_nf : pl.nd_nb;
           const int2* list = d.nd_flow + (sw == 0 ? 0 : pl.nd_nf);
           const long long total = (long long)R * n;
-          // CTA b takes tasks b, b + nb, ... (each after the tasks it waits
-          // for); the next task's entry is loaded while this one runs
+          // unit u (two per CTA) takes tasks u, u + 2 nb, ... (each after
+          // the tasks it waits for); the next task's entry is loaded while
+          // this one runs
+          const int h = threadIdx.x >= kBcrThreads / 2 ? 1 : 0;
+          const NdUnit U{(int)threadIdx.x - h * (kBcrThreads / 2), kBcrThreads / 2, kBcrWarps / 2, 1 + h,
+                         red + h * (kBcrWarps / 2) * MAXN, s_dyn + h * (kNdStageFloats / 2), h ? &s_bar2 : &s_bar,
+                         (kBcrWarps / 2) * MAXN - kNdTaskRows};
+          const long long u0 = 2ll * blockIdx.x + h, nu = 2ll * nb;
           auto entry = [&](long long t) { return list[t - (t / n) * n]; };
-          int2 en = blockIdx.x < total ? entry(blockIdx.x) : make_int2(0, 0);
-          int4 T = blockIdx.x < total ? d.nd_task[en.x] : make_int4(0, 0, 0, 0);
-          for (long long t = blockIdx.x; t < total; t += nb) {
+          int2 en = u0 < total ? entry(u0) : make_int2(0, 0);
+          int4 T = u0 < total ? d.nd_task[en.x] : make_int4(0, 0, 0, 0);
+          bool good = true;
+          for (long long t = u0; t < total && good; t += nu) {
             const int rh = (int)(t / n);
-            const long long tn = t + nb;
+            const long long tn = t + nu;
             const int2 en_n = tn < total ? entry(tn) : en;
             if (s_act[rh * ni + en.y]) {
-              if (!nd_wait_deps(d, pl, kind, rh, T)) return;
+              good = nd_wait_deps(d, pl, U, kind, rh, T);
               const BcrInst& B = en.y == 0 ? s_b0 : d.bcr_inst[en.y];
-              if (!run_nd_task(d, c, B, kind, T, d.bcr_f + rh * pl.rows, d.bcr_e + rh * pl.rows, x_of(rh),
-                               d.nd_w + rh * pl.nd_wrows))
-                return;
-              nd_signal(d, pl, kind, rh, T);
+              if (good)
+                good = run_nd_task(d, c, U, B, kind, T, d.bcr_f + rh * pl.rows, d.bcr_e + rh * pl.rows, x_of(rh),
+                                   d.nd_w + rh * pl.nd_wrows);
+              if (good) nd_signal(d, pl, U, kind, rh, T);
             }
             en = en_n;
             if (tn < total) T = d.nd_task[en.x];
           }
+          // (a unit that gave up goes on to the grid barrier, which sees the
+          // time-out bit and ends the kernel)
           if (!grid_sync(d, nb)) return;
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt[0] += 1;
@@ -1180,7 +1244,7 @@ int bcr_configure(SolvePlan& pl, BcrInst* bi, int ni, int sms) {
   int any_bcr = 0;
   for (int k = 0; k < ni; ++k) any_bcr |= !bi[k].nd;
   pl.bcr.wide = !any_bcr ? 2 : (widest > kBcrMaxN || any_nd ? 1 : 0);
-  if (pl.bcr.nd_floats > kNdVecCap) return 0;
+  if (pl.bcr.nd_floats > (kBcrWarps / 2) * kBcrMaxNWide - kNdTaskRows) return 0;  // a half CTA's vector area
   const long long budget = (long long)optin - static_smem(pl.bcr.wide ? kBcrMaxNWide : kBcrMaxN);
   const void* kern = kernel_for(pl.bcr);
   // tail chunks: about one per CTA when the tails are few, else one row per warp

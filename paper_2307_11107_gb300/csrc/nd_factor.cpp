@@ -480,7 +480,7 @@ void nd_solve_host(const NdFactor& f, const double* r, double* e, bool fp64) {
 }
 
 int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u, int warp_floats, int task_floats,
-              int task_fronts, int stage_floats, int ctas, NdUpload& up, NdLevels& lv) {
+              int task_rows, int task_fronts, int stage_floats, int ctas, NdUpload& up, NdLevels& lv) {
   const int nf = (int)f.fronts.size();
   const int64_t front0 = (int64_t)up.fronts.size(), idx0 = (int64_t)up.idx.size(), g0 = (int64_t)up.gather.size();
   std::vector<int> order;  // deepest level first
@@ -547,7 +547,7 @@ int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u
       if (large(F)) {
         const int rows = fwd ? F.s + F.u : F.s;
         const int width = fwd ? F.sp : std::max(4, F.up);
-        const int nr = std::max(1, task_floats / width);
+        const int nr = std::max(1, std::min(task_rows, task_floats / width));
         for (int r = 0; r < rows; r += nr) up.tasks.push_back(NdTask{(int)(front0 + q), r, std::min(nr, rows - r), 0});
         ++q;
         continue;

@@ -99,7 +99,8 @@ struct NdLevels {
 // buffer (FM first, then NB) and its update vectors at float `wb`.  Fronts
 // with s > warp_s, u > warp_u or more than warp_floats matrix floats in a
 // sweep are large in that sweep (row chunks of at most task_floats matrix
-// floats, each a task of the whole CTA); the small fronts of a level are
+// floats and task_rows rows, each a task of a whole worker); the small
+// fronts of a level are
 // spread over `ctas` tasks (at most task_fronts each, one per warp), so that a
 // level keeps every CTA busy, the tiny ones four to a warp when there are at
 // least four per CTA.  A task's matrix rows are one contiguous range of at
@@ -108,7 +109,7 @@ struct NdLevels {
 // absolute offsets into one right-hand side's update vectors (-1: none).
 // Returns the floats of shared memory a large front's vector needs.
 int nd_layout(const NdFactor& f, int64_t mat, int64_t wb, int warp_s, int warp_u, int warp_floats, int task_floats,
-              int task_fronts, int stage_floats, int ctas, NdUpload& up, NdLevels& lv);
+              int task_rows, int task_fronts, int stage_floats, int ctas, NdUpload& up, NdLevels& lv);
 
 // The sweeps as the device runs them, task by task from the tables above, for
 // one instance of `up` (task ranges lv, tree depth `depth`; its matrices in

@@ -94,8 +94,8 @@ int main(int argc, char** argv) {
   apic::NdUpload up;
   apic::NdLevels l0, l1;
   const int64_t mat1 = ((f.fm_total + f.nb_total + 63) / 64) * 64, w1 = ((f.w_total + 63) / 64) * 64;
-  apic::nd_layout(f, 0, 0, 64, 192, 2048, 16384, 16, 32768, 152, up, l0);
-  apic::nd_layout(f, mat1, w1, 64, 192, 2048, 16384, 16, 32768, 152, up, l1);
+  apic::nd_layout(f, 0, 0, 64, 192, 2048, 16384, 2048, 8, 16384, 304, up, l0);
+  apic::nd_layout(f, mat1, w1, 64, 192, 2048, 16384, 2048, 8, 16384, 304, up, l1);
   std::vector<float> matbuf((size_t)(2 * mat1), 0.0f);
   for (int k = 0; k < 2; ++k) {
     std::copy(f.fm.begin(), f.fm.end(), matbuf.begin() + k * mat1);
@@ -123,7 +123,7 @@ int main(int argc, char** argv) {
       fw = (int64_t)t.n * A.sp;
       bw = (int64_t)t.n * A.up;
     }
-    big += (fwd ? fw : bw) > 32768;  // the task's matrix rows fit the device's stage
+    big += (fwd ? fw : bw) > 16384;  // the task's matrix rows fit a worker's stage
   }
   if (gaps || big) {
     std::printf("FAIL %lld task fronts not contiguous, %lld tasks beyond the stage\n", gaps, big);
