@@ -1044,7 +1044,7 @@ static int setup(apic_sim* S) {
           // task layout: an instance computes the same alone or in a batch)
           const int nd_ctas = std::max(1, (int)std::lround(sms * (double)I.nodes / nd_nodes));
           nd_need = std::max(nd_need, nd_layout(nds[k], off, nd_w, kNdWarpMaxS, kNdWarpMaxU, kNdWarpStage, kNdTaskFloats,
-                                                kNdTaskRows, kNdTaskFronts, kNdStageFloats / 2, 2 * nd_ctas,
+                                                kNdTaskRows, kNdTaskFronts, kNdUnitStage, kNdUnits * nd_ctas,
                                                 ndu, lvl));
           B.nd = 1;
           B.nd_depth = nds[k].depth;
@@ -2481,7 +2481,7 @@ static bool adjoint_setup(apic_sim* S, int K) {
     const int f0 = (int)up.fronts.size();
     NdLevels lv;
     nd_layout(fs[k], mat, w, kNdWarpMaxS, kNdWarpMaxU, kNdWarpStage, kNdTaskFloats, kNdTaskRows, kNdTaskFronts,
-              kNdStageFloats / 2, 1, up, lv);
+              kNdUnitStage, 1, up, lv);
     mat0[k] = mat;
     mat += fs[k].fm_total + fs[k].nb_total;
     w += fs[k].w_total;

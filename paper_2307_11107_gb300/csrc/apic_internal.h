@@ -373,13 +373,21 @@ constexpr int kNdBack = 8;    // x_S = z_S - (F_SS^-1 F_SU) x_U, and x += e
 constexpr int kNdMaxDepth = 40;
 constexpr int kNdWarpMaxS = 64;     // fronts with a separator up to this size run one per warp
 constexpr int kNdWarpMaxU = 192;    // ... and an update set up to this size
-constexpr int kNdTaskFloats = 16384;  // matrix floats per task of a large front (row chunks)
-constexpr int kNdTaskFronts = 8;      // small fronts per task at most (one per warp of a half CTA)
-constexpr int kNdTaskRows = 2048;     // rows per task of a large front at most
+#ifndef APIC_ND_UNITS
+#define APIC_ND_UNITS 4
+#endif
+// The dataflow sweeps split each solve CTA (16 warps) into kNdUnits workers,
+// each with its own task; the task limits follow from a worker's share.
+constexpr int kNdUnits = APIC_ND_UNITS;
 constexpr int kNdWarpStage = 2048;    // matrix floats of a warp's front (staged in shared memory) at most
-constexpr int kNdStageFloats = 16 * kNdWarpStage;  // the CTA's stage; a task's matrix rows take half at most
-static_assert(kNdTaskFloats <= kNdStageFloats / 2 && kNdWarpStage * kNdTaskFronts <= kNdStageFloats / 2,
-              "tasks stage whole in a half CTA's stage");
+constexpr int kNdStageFloats = 16 * kNdWarpStage;  // the CTA's stage
+constexpr int kNdUnitStage = kNdStageFloats / kNdUnits;  // a task's staged matrix rows at most
+constexpr int kNdTaskFloats = kNdUnitStage;  // matrix floats per task of a large front (row chunks)
+constexpr int kNdTaskFronts = 16 / kNdUnits;  // small fronts per task at most (one per warp of a worker)
+constexpr int kNdTaskRows = 2048 / kNdUnits;  // rows per task of a large front at most
+static_assert((kNdUnits == 1 || kNdUnits == 2 || kNdUnits == 4 || kNdUnits == 8) &&
+                  kNdWarpStage * kNdTaskFronts <= kNdUnitStage,
+              "workers of whole warps; tasks stage whole in a worker's stage");
 struct BcrInst {
   int K;                    // 2^K >= n1
   int N;                    // block size N2

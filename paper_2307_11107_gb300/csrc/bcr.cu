@@ -40,7 +40,7 @@ constexpr int kRangesPerPass = kBcrThreads / kBcrSub;  // partial-sum ranges a C
 // and U rows (kNdWarpArea floats per warp); a tiny front's (kNdTinyArea per
 // 8-lane group, four groups per warp)
 constexpr int kNdVecCap = kBcrWarps * kBcrMaxNWide - kNdTaskRows;
-static_assert(kNdStageFloats == kBcrWarps * kNdWarpStage && kNdTaskFronts <= kBcrWarps / 2, "one front per warp");
+static_assert(kNdStageFloats == kBcrWarps * kNdWarpStage && kNdTaskFronts * kNdUnits == kBcrWarps, "one front per warp");
 // per-warp area, forward: v_S, z_S, the U rows, the separator's node indices;
 // backward: x_U, N x_U, the separator's node indices, z_S, x (doubles)
 constexpr int kNdWarpArea = 8 * kNdWarpMaxS;   // 512 floats
@@ -666,9 +666,9 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const NdUnit& U, const Bcr
       m1 = fwd ? FL.FM + (long long)(FL.s + FL.u) * FL.sp : FL.NB + (long long)FL.s * FL.up;
     }
   }
-  // the layout keeps every task within the stage (kNdStageFloats): a larger
+  // the layout keeps every task within a worker's stage (kNdUnitStage): a larger
   // one is a table fault, reported as a capacity error and not computed
-  if (m1 - m0 > kNdStageFloats / 2) {
+  if (m1 - m0 > kNdUnitStage) {
     if (U.t == 0) atomicOr(c.err, kErrCapacity);
     return true;
   }
@@ -1011,7 +1011,7 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   __shared__ int s_pre[kCoopMaxInst + 1];
   __shared__ int s_kind[kCoopMaxInst];
   __shared__ __align__(8) uint64_t s_bar;
-  __shared__ __align__(8) uint64_t s_bar2;  // the second unit's copy barrier (dataflow sweeps)
+  __shared__ __align__(8) uint64_t s_ubar[kNdUnits];  // the workers' copy barriers (dataflow sweeps)
   __shared__ __align__(16) BcrInst s_b0;  // instance 0's table (one load per kernel instead of one per task)
   const int nb = gridDim.x, ni = d.n_inst, R = rhs.n, nv = R * ni;
   static_assert(kBcrMaxRhs == 3, "selections below");
@@ -1028,10 +1028,8 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
   }
   const int tsub = pl.task_sub;
   for (int v = threadIdx.x; v < nv; v += blockDim.x) s_act[v] = only < 0 || v % ni == only;
-  if (threadIdx.x == 0) {
-    mbar_init(&s_bar, 1);
-    mbar_init(&s_bar2, 1);
-  }
+  if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+  if (threadIdx.x < kNdUnits) mbar_init(&s_ubar[threadIdx.x], 1);
   for (int w = threadIdx.x; w < (int)(sizeof(BcrInst) / 4); w += blockDim.x)
     ((int*)&s_b0)[w] = ((const int*)d.bcr_inst)[w];
   // this thread's entries of the next phase's task tables, loaded before a
@@ -1132,11 +1130,11 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
           // unit u (two per CTA) takes tasks u, u + 2 nb, ... (each after
           // the tasks it waits for); the next task's entry is loaded while
           // this one runs
-          const int h = threadIdx.x >= kBcrThreads / 2 ? 1 : 0;
-          const NdUnit U{(int)threadIdx.x - h * (kBcrThreads / 2), kBcrThreads / 2, kBcrWarps / 2, 1 + h,
-                         red + h * (kBcrWarps / 2) * MAXN, s_dyn + h * (kNdStageFloats / 2), h ? &s_bar2 : &s_bar,
-                         (kBcrWarps / 2) * MAXN - kNdTaskRows};
-          const long long u0 = 2ll * blockIdx.x + h, nu = 2ll * nb;
+          constexpr int UT = kBcrThreads / kNdUnits, UW = kBcrWarps / kNdUnits;
+          const int h = (int)threadIdx.x / UT;
+          const NdUnit U{(int)threadIdx.x - h * UT, UT, UW, kNdUnits == 1 ? 0 : 1 + h, red + h * UW * MAXN,
+                         s_dyn + h * kNdUnitStage, s_ubar + h, UW * MAXN - kNdTaskRows};
+          const long long u0 = (long long)kNdUnits * blockIdx.x + h, nu = (long long)kNdUnits * nb;
           auto entry = [&](long long t) { return list[t - (t / n) * n]; };
           int2 en = u0 < total ? entry(u0) : make_int2(0, 0);
           int4 T = u0 < total ? d.nd_task[en.x] : make_int4(0, 0, 0, 0);
@@ -1244,7 +1242,7 @@ int bcr_configure(SolvePlan& pl, BcrInst* bi, int ni, int sms) {
   int any_bcr = 0;
   for (int k = 0; k < ni; ++k) any_bcr |= !bi[k].nd;
   pl.bcr.wide = !any_bcr ? 2 : (widest > kBcrMaxN || any_nd ? 1 : 0);
-  if (pl.bcr.nd_floats > (kBcrWarps / 2) * kBcrMaxNWide - kNdTaskRows) return 0;  // a half CTA's vector area
+  if (pl.bcr.nd_floats > (kBcrWarps / kNdUnits) * kBcrMaxNWide - kNdTaskRows) return 0;  // a worker's vector area
   const long long budget = (long long)optin - static_smem(pl.bcr.wide ? kBcrMaxNWide : kBcrMaxN);
   const void* kern = kernel_for(pl.bcr);
   // tail chunks: about one per CTA when the tails are few, else one row per warp
