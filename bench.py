@@ -491,16 +491,19 @@ def main():
     n_avg = float(res.mean())
     peaks, src = measured_peaks()
     achieved = BYTES_PER_PARTICLE_STEP * n_avg / (push_ms / 1e3) / 1e9
+    # the push kernel that ran: the FP32 vector push unless APIC_PUSH4=0
+    vector = cfg.get("precision", "fp32") != "fp64" and os.environ.get("APIC_PUSH4", "1") != "0"
+    kernel = "k_push4" if vector else "k_push"
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "k_push_traffic.txt")) as f:
             for line in f:
-                if line.startswith("dram_bytes_per_particle"):
+                if vector and line.startswith("dram_bytes_per_particle"):
                     traffic = float(line.split()[1]) * n_avg
     except Exception:
         pass
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": "k_push",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kernel,
             "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP, "peak_source": src,
             "push_ms": push_ms, "phase_ms_per_step": {k: v / kt for k, v in st["phase_ms"].items()}}
     # the whole step against the same roofline: the particle state's bytes per
