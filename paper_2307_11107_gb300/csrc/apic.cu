@@ -1292,6 +1292,35 @@ static int setup(apic_sim* S) {
       S->h2d((int32_t*)d.nd_idx, ndu.idx.data(), ndu.idx.size());
       S->h2d((int32_t*)d.nd_gather, ndu.gather.data(), ndu.gather.size());
       S->h2d((NdTask*)d.nd_task, ndu.tasks.data(), ndu.tasks.size());
+      {  // every task's matrix range (forward rows of FM, backward rows of NB)
+        std::vector<longlong2> tr(ndu.tasks.size(), make_longlong2(0, 0));
+        for (int k = 0; k < ni; ++k) {
+          if (!use_nd[k]) continue;
+          const BcrInst& B = bcr_in[k];
+          for (int sw = 0; sw < 2; ++sw) {
+            const int32_t* lv = sw == 0 ? B.nd_ft : B.nd_bt;
+            for (int t = lv[0]; t < lv[B.nd_depth + 1]; ++t) {
+              const NdTask& T = ndu.tasks[t];
+              const NdFront& F0 = ndu.fronts[T.front];
+              long long m0, m1;
+              if (T.warp == 0) {
+                const int width = sw == 0 ? F0.sp : F0.up;
+                m0 = (sw == 0 ? F0.FM : F0.NB) + (long long)T.r0 * width;
+                m1 = m0 + (sw == 0 || F0.u > 0 ? (long long)T.n * width : 0);
+              } else {
+                const NdFront& FL = ndu.fronts[T.front + T.n - 1];
+                m0 = sw == 0 ? F0.FM : F0.NB;
+                m1 = sw == 0 ? FL.FM + (long long)(FL.s + FL.u) * FL.sp : FL.NB + (long long)FL.s * FL.up;
+              }
+              tr[t] = make_longlong2(m0, m1);
+            }
+          }
+        }
+        d.nd_trange = (const longlong2*)A(sizeof(longlong2) * tr.size());
+        if (S->status != APIC_OK) return S->status;
+        S->h2d((longlong2*)d.nd_trange, tr.data(), tr.size());
+        if (!S->sync()) return S->status;  // tr goes out of scope
+      }
       for (int k = 0; k < ni; ++k) {
         if (!use_nd[k]) continue;
         const BcrInst& B = bcr_in[k];

@@ -195,6 +195,7 @@ struct DevPtrs {
   const int32_t* nd_idx;
   const int32_t* nd_gather;
   const int4* nd_task;
+  const longlong2* nd_trange;  // per task: its matrix floats [x, y) in bcr (one contiguous range)
   float* nd_w;
   // dataflow sweeps (BcrPlan::nd_flow): the forward then the backward task
   // order (task, instance; every task after the tasks it depends on), the

@@ -644,40 +644,36 @@ __device__ bool nd_mbar_wait(const NdUnit& U, uint64_t* bar, unsigned parity, in
   return U.sync_and(ok);
 }
 
+// Issue the bulk copy of task `tr`'s matrix rows into the unit's stage (its
+// thread 0; after the unit's earlier reads of the stage).
+__device__ __forceinline__ void nd_issue(const DevPtrs& d, const NdUnit& U, const longlong2 tr) {
+  if (U.t == 0 && tr.y > tr.x && tr.y - tr.x <= kNdUnitStage) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(U.bar, (unsigned)(tr.y - tr.x) * 4u);
+    bulk_g2s(U.sbuf, (const float*)d.bcr + tr.x, (unsigned)(tr.y - tr.x) * 4u, U.bar);
+  }
+}
+
+// issued: the task's copy was issued before (nd_issue), e.g. while its
+// dependencies were awaited.
 __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const NdUnit& U, const BcrInst& B, int kind, const int4 T,
-                            float* fb, float* eb, double* xb, float* wb) {
+                            const longlong2 tr, bool issued, float* fb, float* eb, double* xb, float* wb) {
   const float* f = fb + B.foff;
   float* e = eb + B.foff;
   double* x = xb + B.node_off;
   const int lane = U.t & 31, warp = U.t >> 5;
   const bool fwd = kind == kNdFwd;
   const float* mat = (const float*)d.bcr;
-  // the task's matrix range [m0, m1)
-  long long m0, m1;
-  {
-    const NdFront F0 = d.nd_front[T.x];
-    if (T.w == 0) {
-      const int width = fwd ? F0.sp : F0.up;
-      m0 = (fwd ? F0.FM : F0.NB) + (long long)T.y * width;
-      m1 = m0 + (fwd || F0.u > 0 ? (long long)T.z * width : 0);
-    } else {
-      const NdFront FL = d.nd_front[T.x + T.z - 1];
-      m0 = fwd ? F0.FM : F0.NB;
-      m1 = fwd ? FL.FM + (long long)(FL.s + FL.u) * FL.sp : FL.NB + (long long)FL.s * FL.up;
-    }
-  }
-  // the layout keeps every task within a worker's stage (kNdUnitStage): a larger
-  // one is a table fault, reported as a capacity error and not computed
+  // the task's matrix range [m0, m1) (the layout keeps it within a worker's
+  // stage, kNdUnitStage: a larger one is a table fault, reported as a
+  // capacity error and not computed)
+  const long long m0 = tr.x, m1 = tr.y;
   if (m1 - m0 > kNdUnitStage) {
     if (U.t == 0) atomicOr(c.err, kErrCapacity);
     return true;
   }
   const bool staged = m1 > m0;
-  if (staged && U.t == 0) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the earlier tasks' reads
-    mbar_expect_tx(U.bar, (unsigned)(m1 - m0) * 4u);
-    bulk_g2s(U.sbuf, mat + m0, (unsigned)(m1 - m0) * 4u, U.bar);
-  }
+  if (!issued) nd_issue(d, U, tr);
   // matrix float o of the buffer in the stage
   auto at = [&](long long o) { return U.sbuf + (o - m0); };
   auto wait = [&]() {
@@ -842,9 +838,9 @@ __device__ bool run_nd_task(const DevPtrs& d, Ctx& c, const NdUnit& U, const Bcr
 // Task q of level l of instance B's sweep `kind`.
 __device__ __forceinline__ bool run_nd(const DevPtrs& d, Ctx& c, const BcrInst& B, int kind, int l, int q, float* fb,
                                        float* eb, double* xb, float* wb) {
-  const int4 T = d.nd_task[(kind == kNdFwd ? B.nd_ft[l] : B.nd_bt[l]) + q];
+  const int t = (kind == kNdFwd ? B.nd_ft[l] : B.nd_bt[l]) + q;
   const NdUnit U{(int)threadIdx.x, (int)blockDim.x, kBcrWarps, 0, c.red, c.sbuf, c.bar, kNdVecCap};
-  return run_nd_task(d, c, U, B, kind, T, fb, eb, xb, wb);
+  return run_nd_task(d, c, U, B, kind, d.nd_task[t], d.nd_trange[t], false, fb, eb, xb, wb);
 }
 
 // ---- dataflow sweeps (BcrPlan::nd_flow) ----
@@ -1144,11 +1140,15 @@ __global__ void __launch_bounds__(kBcrThreads, 1) k_solve_bcr(DevPtrs d, BcrPlan
             const long long tn = t + nu;
             const int2 en_n = tn < total ? entry(tn) : en;
             if (s_act[rh * ni + en.y]) {
+              // the matrix rows are static: their copy runs while the
+              // dependencies are awaited
+              const longlong2 tr = d.nd_trange[en.x];
+              nd_issue(d, U, tr);
               good = nd_wait_deps(d, pl, U, kind, rh, T);
               const BcrInst& B = en.y == 0 ? s_b0 : d.bcr_inst[en.y];
               if (good)
-                good = run_nd_task(d, c, U, B, kind, T, d.bcr_f + rh * pl.rows, d.bcr_e + rh * pl.rows, x_of(rh),
-                                   d.nd_w + rh * pl.nd_wrows);
+                good = run_nd_task(d, c, U, B, kind, T, tr, true, d.bcr_f + rh * pl.rows, d.bcr_e + rh * pl.rows,
+                                   x_of(rh), d.nd_w + rh * pl.nd_wrows);
               if (good) nd_signal(d, pl, U, kind, rh, T);
             }
             en = en_n;
