@@ -505,7 +505,8 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kernel,
             "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP, "peak_source": src,
-            "push_ms": push_ms, "phase_ms_per_step": {k: v / kt for k, v in st["phase_ms"].items()}}
+            "push_ms": push_ms, "phase_ms_per_step": {k: v / kt for k, v in st["phase_ms"].items()},
+            "sort_ms_per_sort": st["sort_ms"] / st["timed_sorts"] if st["timed_sorts"] else None}
     # the whole step against the same roofline: the particle state's bytes per
     # step over the step time (the solve, sort and injection add time, not bytes)
     full = BYTES_PER_PARTICLE_STEP * total_adv / args.steps / (ms / args.steps / 1e3) / 1e9
@@ -539,6 +540,8 @@ def main():
         del sim
         torch.cuda.synchronize()
         sim2 = apic.Sim(cfg2)
+        if tuned is not None:  # the schedule measured above, applied without measuring again
+            sim2.set_schedule(tiles["sort_interval"], tiles["win_rows"], tiles["chunk_group"], tiles["chunk_items"])
         ke = min(args.steps, 500)
         h2d = sum(p.numel() * 8 for p in pinned)
         barrier()

@@ -255,6 +255,8 @@ typedef struct {
   int32_t win_rows;             /* node rows of the push's shared-memory deposit window in use */
   int32_t chunk_group;          /* consecutive particle chunks a push CTA takes at a time */
   int32_t chunk_items;          /* FP32 push: particles per thread of a chunk (16: 4096 per chunk, 32: 8192) */
+  int64_t timed_sorts;          /* particle sorts run inside apic_step_timed */
+  double sort_ms;               /* CUDA-event time of those sorts, summed */
 } apic_stats_t;
 
 /* Poisson solvers (chosen at creation) */
@@ -302,6 +304,20 @@ int apic_step_timed(apic_sim* sim, int32_t n_steps);
  * steps_per_trial < 1), those of apic_step. */
 #define APIC_TUNE_CANDIDATES 7
 int apic_autotune(apic_sim* sim, int32_t steps_per_trial, int32_t* sort_interval, double* ms_per_step);
+
+/* Apply a schedule chosen earlier (by apic_autotune on the same workload, as
+ * apic_stats reported it) without measuring again.  Each argument 0 leaves
+ * that setting unchanged; otherwise sort_interval >= 1 (the simulation must
+ * have been created with sorting: sort_interval > 0 in some instance's
+ * config, which allocates the second particle buffer), win_rows 2..16 node
+ * rows of the push's deposit window, chunk_group 1..64 chunks per claim,
+ * chunk_items 16 or 32 particles per thread of a push chunk (FP32; ignored
+ * for FP64).  Waits for the work in flight, then recaptures the step graphs
+ * at the next step; results are those of apic_step under any schedule (the
+ * deposits are fixed-point sums).  Errors: INVALID_ARG (a value out of
+ * range, sort_interval > 0 without sorting), a sticky error. */
+int apic_set_schedule(apic_sim* sim, int32_t sort_interval, int32_t win_rows, int32_t chunk_group,
+                      int32_t chunk_items);
 
 /* ---- Sensitivity window (forward mode) and its adjoint (reverse mode) ------
  * Derivatives of window-averaged grain outputs with respect to the grain

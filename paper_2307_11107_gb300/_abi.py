@@ -22,7 +22,8 @@ NT, NH = 7, 11
 SYMBOLS = ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
            "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_last_error",
            "apic_num_instances", "apic_stats", "apic_step_timed", "apic_deposit_static", "apic_sensitivity",
-           "apic_adjoint", "apic_adjoint_window", "apic_autotune", "apic_probe_fp32_fma", "apic_check_wait_limit")
+           "apic_adjoint", "apic_adjoint_window", "apic_autotune", "apic_probe_fp32_fma", "apic_check_wait_limit",
+           "apic_set_schedule")
 TUNE_INTERVALS = (2, 4, 6, 8, 12, 16, 24)
 NPAR, NOUT = 3, 5
 PARAMS = ("alpha", "phi_g", "B")
@@ -70,7 +71,7 @@ class Stats(C.Structure):
                 ("kernels_per_iter", C.c_int32), ("timed_steps", C.c_int64), ("phase_ms", C.c_double * NPHASE),
                 ("solver", C.c_int32), ("kernels_per_sort", C.c_int32), ("sorts", C.c_int64),
                 ("sort_interval", C.c_int32), ("win_rows", C.c_int32), ("chunk_group", C.c_int32),
-                ("chunk_items", C.c_int32)]
+                ("chunk_items", C.c_int32), ("timed_sorts", C.c_int64), ("sort_ms", C.c_double)]
 
 
 SOLVERS = ("multigrid BiCGSTAB, per-phase kernels", "multigrid BiCGSTAB, one cooperative launch",
@@ -112,10 +113,11 @@ def load():
     L.apic_autotune.argtypes = [vp, i32, C.POINTER(i32), dp]
     L.apic_probe_fp32_fma.argtypes = [vp, i32, dp]
     L.apic_check_wait_limit.argtypes = [vp, i64]
+    L.apic_set_schedule.argtypes = [vp, i32, i32, i32, i32]
     for name in ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
                  "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_stats", "apic_step_timed",
                  "apic_deposit_static", "apic_sensitivity", "apic_adjoint", "apic_autotune", "apic_probe_fp32_fma",
-                 "apic_check_wait_limit", "apic_adjoint_window"):
+                 "apic_check_wait_limit", "apic_adjoint_window", "apic_set_schedule"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -159,8 +159,11 @@ struct apic_sim {
   long long max_inj = 0;
   int push_grid = 0;
   int max_n2 = 0;                     // widest grid of the batch (cells in x2)
+  int max_n1 = 0;                     // most cell rows of the batch (cells in x1)
   double* phi_save = nullptr;
   int32_t* h_err = nullptr;
+  unsigned char* h_tally = nullptr;   // pinned staging of apic_tallies (the largest instance's copies)
+  size_t h_tally_bytes = 0;
   bool cond_loop = true;              // Krylov loop as a graph while-node (else a fixed unrolled loop)
   int coop = 0;                       // CTAs of the cooperative whole-solve kernel (0: per-phase kernels)
   cudaGraphExec_t phase_exec[2][APIC_NPHASE] = {};
@@ -168,6 +171,9 @@ struct apic_sim {
   cudaEvent_t ev[APIC_NPHASE + 1] = {};
   double phase_ms[APIC_NPHASE] = {};
   long long timed_steps = 0;
+  long long timed_sorts = 0;          // sorts inside apic_step_timed, and their CUDA-event time
+  double sort_ms = 0.0;
+  cudaEvent_t sort_ev[2] = {};
   long long slots = 0;                // particle slots of one buffer (all populations)
   long long sorts = 0;                // particle sorts launched
   size_t bcr_bytes = 0;               // reduction blocks + tail inverse (one device range)
@@ -1220,7 +1226,6 @@ static int setup(apic_sim* S) {
     d.yR = A(R * slots);
     d.yZ = A(R * slots);
     d.yT = A(R * slots);
-    d.keys = (int32_t*)A(sizeof(int32_t) * slots);
     d.cell_cnt = (unsigned*)A(sizeof(unsigned) * total_cells);
     d.cell_off = (unsigned long long*)A(sizeof(unsigned long long) * (total_cells + 1));
     d.scan_tmp = (unsigned long long*)A(sizeof(unsigned long long) * ((total_cells + 1023) / 1024 + 1));
@@ -1464,8 +1469,12 @@ static int setup(apic_sim* S) {
   // conditional while node (profilers do not replay kernels of graphs that
   // hold conditional nodes)
   if (const char* cl = std::getenv("APIC_COND_LOOP")) S->cond_loop = std::atoi(cl) != 0;
-  for (const Inst& I : S->inst) S->max_n2 = std::max(S->max_n2, I.n2);
-  push_window_rows<Real>(S->max_n2);  // the occupancy query happens here, not inside a graph capture
+  for (const Inst& I : S->inst) {
+    S->max_n2 = std::max(S->max_n2, I.n2);
+    S->max_n1 = std::max(S->max_n1, I.n1);
+  }
+  push_window_rows<Real>(S->max_n2);  // the occupancy queries happen here, not inside a graph capture
+  sort_setup<Real>(S->max_n1);
   for (const Inst& I : S->inst) S->chord = S->chord || (I.flags & APIC_CHORD_ABSORB) != 0;
   // the whole Poisson solve as one cooperative kernel, unless disabled or not co-residable
   const char* env = std::getenv("APIC_SOLVER");
@@ -1566,11 +1575,14 @@ extern "C" int apic_destroy(apic_sim* S) {
   drop_graphs(S);
   for (int p = 0; p <= APIC_NPHASE; ++p)
     if (S->ev[p]) cudaEventDestroy(S->ev[p]);
+  for (cudaEvent_t e : S->sort_ev)
+    if (e) cudaEventDestroy(e);
   S->dfree_all();
   cudaStreamSynchronize(S->stream);
   if (S->cap) cudaStreamDestroy(S->cap);
   if (S->cap2) cudaStreamDestroy(S->cap2);
   if (S->h_err) cudaFreeHost(S->h_err);
+  if (S->h_tally) cudaFreeHost(S->h_tally);
   delete S;
   return APIC_OK;
 }
@@ -1664,7 +1676,7 @@ static bool enqueue_phase(apic_sim* S, const DevPtrs& d, int p, cudaStream_t s) 
       break;
     case 4: launch_inject<Real>(d, S->max_inj, s); break;
     case 5: launch_step_end(d, s); break;
-    case 6: launch_sort<Real>(d, S->push_grid, s); break;  // not a step phase: the particle sort
+    case 6: launch_sort<Real>(d, S->push_grid, S->max_n1, s); break;  // not a step phase: the particle sort
   }
   return true;
 }
@@ -1802,9 +1814,15 @@ static int step_timed_impl(apic_sim* S, int n) {
         if (!capture<Real>(S, S->view(q), p, p + 1, &S->phase_graph[q][p], &S->phase_exec[q][p])) return S->status;
     for (int p = 0; p <= APIC_NPHASE; ++p)
       if (!S->ev[p] && !S->ck(cudaEventCreate(&S->ev[p]), "event create")) return S->status;
+    for (cudaEvent_t& e : S->sort_ev)
+      if (!e && !S->ck(cudaEventCreate(&e), "event create")) return S->status;
   }
   for (int k = 0; k < n; ++k) {
-    if (!launch_step<Real>(S, nullptr)) return S->status;  // sort when due (not timed)
+    // the sort when due, timed on its own
+    const bool sorting = S->sort_interval > 0 && S->host_step % S->sort_interval == 0;
+    if (sorting) S->ck(cudaEventRecord(S->sort_ev[0], S->stream), "event record");
+    if (!launch_step<Real>(S, nullptr)) return S->status;
+    if (sorting) S->ck(cudaEventRecord(S->sort_ev[1], S->stream), "event record");
     S->host_step -= 1;
     S->ck(cudaEventRecord(S->ev[0], S->stream), "event record");
     for (int p = 0; p < APIC_NPHASE; ++p) {
@@ -1817,6 +1835,12 @@ static int step_timed_impl(apic_sim* S, int n) {
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, S->ev[p], S->ev[p + 1]);
       S->phase_ms[p] += ms;
+    }
+    if (sorting) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, S->sort_ev[0], S->sort_ev[1]);
+      S->sort_ms += ms;
+      S->timed_sorts += 1;
     }
   }
   S->timed_steps += n;
@@ -1874,6 +1898,8 @@ extern "C" int apic_stats(apic_sim* S, apic_stats_t* out) {
                                        : (S->coop > 0 ? APIC_SOLVER_MG_COOP : APIC_SOLVER_MG_KERNELS);
   out->sorts = S->sorts;
   out->kernels_per_sort = 6;
+  out->timed_sorts = S->timed_sorts;
+  out->sort_ms = S->sort_ms;
   for (int p = 0; p < APIC_NPHASE; ++p) out->phase_ms[p] = S->phase_ms[p];
   return APIC_OK;
 }
@@ -1995,6 +2021,23 @@ extern "C" int apic_autotune(apic_sim* S, int32_t steps_per_trial, int32_t* sort
                                    : autotune_impl<float>(S, steps_per_trial, sort_interval, ms_per_step);
 }
 
+extern "C" int apic_set_schedule(apic_sim* S, int32_t sort_interval, int32_t win_rows, int32_t chunk_group,
+                                 int32_t chunk_items) {
+  if (!S) return APIC_ERR_INVALID_ARG;
+  if (S->status != APIC_OK) return S->status;
+  if (sort_interval < 0 || (sort_interval > 0 && S->sort_interval <= 0)) return APIC_ERR_INVALID_ARG;
+  if (win_rows != 0 && (win_rows < 2 || win_rows > 16)) return APIC_ERR_INVALID_ARG;
+  if (chunk_group < 0 || chunk_group > 64) return APIC_ERR_INVALID_ARG;
+  if (chunk_items != 0 && chunk_items != 16 && chunk_items != 32) return APIC_ERR_INVALID_ARG;
+  if (!S->sync()) return S->status;
+  if (sort_interval > 0) S->sort_interval = sort_interval;
+  if (win_rows > 0) S->win_rows = win_rows;
+  if (chunk_group > 0) S->chunk_group = chunk_group;
+  if (chunk_items > 0 && S->precision != APIC_FP64) S->chunk_items = chunk_items;
+  drop_graphs(S);  // recaptured at the next step
+  return APIC_OK;
+}
+
 extern "C" int apic_step(apic_sim* S, int32_t n_steps) {
   if (!S) return APIC_ERR_INVALID_ARG;
   if (S->status != APIC_OK) return S->status;
@@ -2065,20 +2108,37 @@ extern "C" int apic_tallies(apic_sim* S, int32_t instance, apic_tallies_t* out) 
   if (instance < 0 || instance >= S->n_inst) return APIC_ERR_INVALID_ARG;
   if (S->status != APIC_OK) return S->status;  // sticky
   const Inst& I = S->inst[instance];
+  // every copy into one pinned staging block, stream-ordered after the
+  // steps, then a single synchronisation
+  auto words = [](const Inst& J) {
+    return (size_t)J.n_species * ((size_t)J.n2 * kTallyBinWords + kTallyStepWords);
+  };
+  const size_t o_stp = 0, o_sol = o_stp + sizeof(StepState), o_ps = o_sol + sizeof(SolverState);
+  const size_t o_hist = o_ps + 2 * sizeof(PopState);
+  if (!S->h_tally) {
+    size_t most = 0;
+    for (const Inst& J : S->inst) most = std::max(most, (size_t)J.hist_cap * kNH * sizeof(double) + words(J) * 8);
+    S->h_tally_bytes = o_hist + most;
+    if (!S->ck(cudaMallocHost(&S->h_tally, S->h_tally_bytes), "cudaMallocHost")) return S->status;
+  }
+  const size_t tw = words(I);
+  const size_t nh = (size_t)I.hist_cap * kNH;
+  double* hist = (double*)(S->h_tally + o_hist);
+  unsigned long long* tfix = (unsigned long long*)(S->h_tally + o_hist + nh * sizeof(double));
+  PopState* psd = (PopState*)(S->h_tally + o_ps);
+  if (out->bins) S->d2h(tfix, S->d.tfix + I.bin_off, tw);
+  S->d2h((StepState*)(S->h_tally + o_stp), S->d.stp + instance, 1);
+  S->d2h((SolverState*)(S->h_tally + o_sol), S->d.sol + instance, 1);
+  S->d2h(psd, S->d.ps + I.pop0, (size_t)I.n_species);  // the instance's populations are consecutive
+  S->d2h(hist, S->d.hist + I.hist_off, nh);
   if (!S->sync()) return S->status;
-  const long long tw = (long long)I.n_species * ((long long)I.n2 * kTallyBinWords + kTallyStepWords);
-  std::vector<unsigned long long> tfix((size_t)tw);
-  if (out->bins) S->d2h(tfix.data(), S->d.tfix + I.bin_off, (size_t)tw);
   StepState stp;
   SolverState sol;
-  S->d2h(&stp, S->d.stp + instance, 1);
-  S->d2h(&sol, S->d.sol + instance, 1);
+  std::memcpy(&stp, S->h_tally + o_stp, sizeof(stp));
+  std::memcpy(&sol, S->h_tally + o_sol, sizeof(sol));
   PopState ps[2];
   std::memset(ps, 0, sizeof(ps));
-  for (int s = 0; s < I.n_species; ++s) S->d2h(&ps[s], S->d.ps + I.pop0 + s, 1);
-  std::vector<double> hist((size_t)I.hist_cap * kNH);
-  S->d2h(hist.data(), S->d.hist + I.hist_off, hist.size());
-  if (!S->sync()) return S->status;
+  for (int s = 0; s < I.n_species; ++s) ps[s] = psd[s];
   if (out->bins) {
     // bins from the fixed-point sums (tally_fixed.cuh): charge = hits q w,
     // momenta and L_z times m w v_th, energy times m w v_th^2, plus the
@@ -2087,7 +2147,7 @@ extern "C" int apic_tallies(apic_sim* S, int32_t instance, apic_tallies_t* out) 
       const Pop& P = S->pop[I.pop0 + s];
       const double mwu = P.m * P.w * P.tunit;
       for (int j = 0; j < I.n2; ++j) {
-        const unsigned long long* b = tfix.data() + (P.tfix_off - I.bin_off) + (size_t)j * kTallyBinWords;
+        const unsigned long long* b = tfix + (P.tfix_off - I.bin_off) + (size_t)j * kTallyBinWords;
         double* o = out->bins + ((size_t)s * I.n2 + j) * kNT;
         const double hits = (double)b[0];
         o[0] = hits;
@@ -2120,7 +2180,7 @@ extern "C" int apic_tallies(apic_sim* S, int32_t instance, apic_tallies_t* out) 
     long long first = stp.step - w;  // oldest row written
     for (long long r = 0; r < w; ++r) {
       long long src = (first + r) % I.hist_cap;
-      std::memcpy(out->history + r * kNH, hist.data() + src * kNH, sizeof(double) * kNH);
+      std::memcpy(out->history + r * kNH, hist + src * kNH, sizeof(double) * kNH);
     }
     out->history_rows = w;
   } else {

@@ -141,7 +141,6 @@ struct DevPtrs {
   void *x1, *x2, *vR, *vZ, *vT;
   void *y1, *y2, *yR, *yZ, *yT;  // second buffer (sort)
   int32_t* holes;
-  int32_t* keys;                  // sort keys per slot
   unsigned* cell_cnt;             // sort: particles per global cell
   unsigned long long* cell_off;   // sort: exclusive prefix over cells (size cells + 1)
   unsigned long long* scan_tmp;   // sort: block sums of the scan
@@ -311,8 +310,13 @@ template <class Real>
 int push_window_rows(int max_n2);
 template <class Real>
 void launch_inject(const DevPtrs& d, long long max_inj, cudaStream_t s);
+// The particle sort (count, scan, scatter) for grids of up to max_rows cell
+// rows; sort_setup queries its passes' occupancy once per row count (call at
+// set-up, before any capture).
 template <class Real>
-void launch_sort(const DevPtrs& d, int grid, cudaStream_t s);
+void sort_setup(int max_rows);
+template <class Real>
+void launch_sort(const DevPtrs& d, int grid, int max_rows, cudaStream_t s);
 template <class Real>
 void launch_gather_particles(const DevPtrs& d, int pop, double* out, long long* n_out, cudaStream_t s);
 

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdlib>
 
 #include <cstdint>
@@ -23,6 +24,7 @@ namespace apic {
 namespace {
 
 #include "particle_common.cuh"
+#include "bulk_copy.cuh"
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPushItems = 8;    // particles per thread per chunk
@@ -1241,12 +1243,12 @@ __global__ void __launch_bounds__(256) k_inject(DevPtrs d) {
 // ---------------------------------------------------------------------------
 // Counting sort of every population by grid row (the push's deposit window
 // covers whole rows), which also drops freed slots: count -> exclusive scan
-// over all (population, row) bins -> scatter into the second buffer.  Each
-// CTA histograms its chunk in shared memory and touches the global counters
-// once per row it holds.
+// over all (population, row) bins -> scatter into the second buffer.  Both
+// passes stream their chunks through shared memory with bulk asynchronous
+// copies issued several chunks ahead; a CTA histograms its chunk there and
+// touches the global counters once per row the chunk holds (recently sorted
+// particles: one to three rows).
 // ---------------------------------------------------------------------------
-constexpr int kSortItems = 8;
-
 __device__ __forceinline__ void chunk_prefix(const DevPtrs& d, long long CH, long long* pre) {
   if (threadIdx.x == 0) {
     long long a = 0;
@@ -1270,50 +1272,6 @@ __device__ __forceinline__ unsigned warp_count(unsigned* counter, int key) {
   if (key >= 0 && lane == leader) base = atomicAdd(counter + key, (unsigned)__popc(grp));
   base = __shfl_sync(kFull, base, leader);
   return base + rank;
-}
-
-__global__ void __launch_bounds__(256) k_sort_count(DevPtrs d) {
-  extern __shared__ unsigned s_hist[];
-  __shared__ long long pre[kMaxPop + 1];
-  const long long CH = (long long)kSortItems * blockDim.x;
-  chunk_prefix(d, CH, pre);
-  const Real* X1 = (const Real*)d.x1;
-  for (long long chunk = blockIdx.x; chunk < pre[d.n_pop]; chunk += gridDim.x) {
-    const int pop = find_pop(pre, d.n_pop, chunk);
-    const Pop& P = d.pop[pop];
-    const Inst& I = d.inst[P.inst];
-    const long long npop = d.ps[pop].n, c0 = (chunk - pre[pop]) * CH;
-    const int nrows = I.n1;
-    // grid row in the particle precision (the key only orders the particles);
-    // the reciprocal once per chunk, not an FP64 division per particle
-    const Real ih1 = (Real)(1.0 / I.h1);
-    for (int r = threadIdx.x; r < nrows; r += blockDim.x) s_hist[r] = 0u;
-    __syncthreads();
-    // all of the thread's loads first (kSortItems in flight), then the keys
-    Real xs[kSortItems];
-#pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-      const long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
-      xs[it] = k < npop ? X1[P.base + k] : Real(1);
-    }
-#pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-      const long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
-      int row = -1;
-      if (k < npop) {
-        if (xs[it] < Real(0)) {
-          row = (int)floor((xs[it] + Real(1)) * ih1);
-          row = row < 0 ? 0 : (row > nrows - 1 ? nrows - 1 : row);
-        }
-        d.keys[P.base + k] = row;
-      }
-      warp_count(s_hist, row);
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < nrows; r += blockDim.x)
-      if (s_hist[r]) atomicAdd(d.cell_cnt + P.cell_off + r, s_hist[r]);
-    __syncthreads();
-  }
 }
 
 // Exclusive scan of cell_cnt into cell_off: per-block scan (1024 cells) ...
@@ -1376,74 +1334,302 @@ __global__ void __launch_bounds__(1024) k_scan_add(DevPtrs d) {
   }
 }
 
-// Scatter every live particle into its row's range of the second buffer.
-__global__ void __launch_bounds__(256) k_sort_scatter(DevPtrs d) {
-  extern __shared__ unsigned s_hist[];  // [2][nrows]: chunk counts, then local cursors
-  __shared__ long long pre[kMaxPop + 1];
-  const long long CH = (long long)kSortItems * blockDim.x;
-  chunk_prefix(d, CH, pre);
-  for (long long chunk = blockIdx.x; chunk < pre[d.n_pop]; chunk += gridDim.x) {
-    const int pop = find_pop(pre, d.n_pop, chunk);
-    const Pop& P = d.pop[pop];
+// Grid row of a stored x1 (row -1: a freed slot, x1 > 0), one expression for
+// the count and the scatter so that both place every particle in the same row.
+__device__ __forceinline__ int sort_row(Real x, Real ih1, int nrows) {
+  if (!(x < Real(0))) return -1;
+  int row = (int)floor((x + Real(1)) * ih1);
+  return row < 0 ? 0 : (row > nrows - 1 ? nrows - 1 : row);
+}
+
+// A population's constants of the sort, read once per CTA.
+struct SortConst {
+  long long base, cell_off, n;
+  Real ih1;  // 1 / h1 in the particle precision (the row key only orders the particles)
+  int nrows;
+};
+
+__device__ __forceinline__ void sort_consts(const DevPtrs& d, SortConst* sc) {
+  for (int p = threadIdx.x; p < d.n_pop; p += blockDim.x) {
+    const Pop& P = d.pop[p];
     const Inst& I = d.inst[P.inst];
-    const long long npop = d.ps[pop].n, c0 = (chunk - pre[pop]) * CH;
-    const int nrows = I.n1;
-    unsigned* cnt = s_hist;
-    unsigned* cur = s_hist + nrows;
-    for (int r = threadIdx.x; r < nrows; r += blockDim.x) cnt[r] = 0u;
-    __syncthreads();
-    // the thread's keys, all loads in flight at once; kept for the placement
-    int rows[kSortItems];
+    sc[p] = SortConst{P.base, P.cell_off, d.ps[p].n, (Real)(1.0 / I.h1), I.n1};
+  }
+}
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+
+// 16-byte vectors of the particle precision (a population's slot range
+// starts on a 16-byte boundary and holds a multiple of four slots).
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using T = float4;
+  static constexpr int kN = 4;
+  __device__ static float get(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+};
+template <>
+struct Vec16<double> {
+  using T = double2;
+  static constexpr int kN = 2;
+  __device__ static double get(const double2& v, int k) { return k == 0 ? v.x : v.y; }
+};
+using RealV = Vec16<Real>;
+
+// Count pass: every CTA takes a contiguous share of each population (whole
+// 16-byte vectors, kCountUnroll of them in flight per thread), counts runs of
+// equal rows in registers (recently sorted particles change row rarely), adds
+// a run to a shared-memory histogram when it ends, and adds the histogram's
+// rows [lo, hi] to cell_cnt once per population.
+constexpr int kCountUnroll = 4;
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_count(DevPtrs d, int hist_rows) {
+  extern __shared__ unsigned hist[];  // [hist_rows]
+  __shared__ SortConst sc[kMaxPop];
+  __shared__ int s_lo[2], s_hi[2];  // population p's row range in [p & 1] (reset for p + 2)
+  sort_consts(d, sc);
+  for (int r = threadIdx.x; r < hist_rows; r += blockDim.x) hist[r] = 0u;
+  if (threadIdx.x < 2) {
+    s_lo[threadIdx.x] = INT_MAX;
+    s_hi[threadIdx.x] = -1;
+  }
+  __syncthreads();
+  for (int pop = 0; pop < d.n_pop; ++pop) {
+    const SortConst P = sc[pop];
+    const typename RealV::T* X = (const typename RealV::T*)((const Real*)d.x1 + P.base);
+    const long long groups = (P.n + RealV::kN - 1) / RealV::kN;
+    const long long per = (groups + gridDim.x - 1) / gridDim.x;
+    const long long g0 = (long long)blockIdx.x * per, g1 = min(groups, g0 + per);
+    int run = -1, len = 0, lo = INT_MAX, hi = -1;
+    for (long long g = g0 + threadIdx.x; g < g1; g += (long long)kCountUnroll * kSortThreads) {
+      typename RealV::T v[kCountUnroll];
 #pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-      const long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
-      rows[it] = k < npop ? d.keys[P.base + k] : -1;
+      for (int u = 0; u < kCountUnroll; ++u) {
+        const long long gu = g + (long long)u * kSortThreads;
+        if (gu < g1) v[u] = X[gu];
+      }
+#pragma unroll
+      for (int u = 0; u < kCountUnroll; ++u) {
+        const long long gu = g + (long long)u * kSortThreads;
+#pragma unroll
+        for (int k = 0; k < RealV::kN; ++k) {
+          const int row = gu < g1 && gu * RealV::kN + k < P.n ? sort_row(RealV::get(v[u], k), P.ih1, P.nrows) : -1;
+          if (row >= 0) {
+            if (row != run) {
+              if (len) atomicAdd(hist + run, (unsigned)len);
+              run = row;
+              len = 0;
+            }
+            ++len;
+            lo = min(lo, row);
+            hi = max(hi, row);
+          }
+        }
+      }
     }
-#pragma unroll
-    for (int it = 0; it < kSortItems; ++it) warp_count(cnt, rows[it]);
+    if (len) atomicAdd(hist + run, (unsigned)len);
+    lo = __reduce_min_sync(kFull, lo);
+    hi = __reduce_max_sync(kFull, hi);
+    if ((threadIdx.x & 31) == 0 && hi >= 0) {
+      atomicMin(&s_lo[pop & 1], lo);
+      atomicMax(&s_hi[pop & 1], hi);
+    }
     __syncthreads();
-    // reserve this chunk's range of every row it holds
+    // no live particle: the empty range [0, -1]
+    const int r1 = s_hi[pop & 1], r0 = r1 >= 0 ? s_lo[pop & 1] : 0;
+    for (int r = r0 + threadIdx.x; r <= r1; r += blockDim.x) {
+      const unsigned c = hist[r];
+      if (c) {
+        atomicAdd(d.cell_cnt + P.cell_off + r, c);
+        hist[r] = 0u;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_lo[pop & 1] = INT_MAX;
+      s_hi[pop & 1] = -1;
+    }
+  }
+}
+
+// Scatter pass: chunks of kScatterItems x 256 consecutive slots of one
+// population, the five state arrays of a CTA's next chunks streamed into
+// shared-memory stages by bulk asynchronous copies while it places the
+// current one.
+constexpr int kScatterItems = 8;
+constexpr int kScatterChunk = kScatterItems * kSortThreads;
+constexpr int kScatterStages = 2;
+constexpr int kScatterStageBytes = 5 * kScatterChunk * (int)sizeof(Real);
+static_assert(kScatterItems * kSortWarps % 32 == 0, "whole entries per lane in the chunk-order prefix");
+
+static int scatter_smem(int hist_rows) {
+  return kScatterStages * kScatterStageBytes + 2 * hist_rows * (int)sizeof(unsigned);
+}
+
+// Bulk copies of chunk `chunk`'s state arrays into a stage (thread 0).  The
+// population's slot range starts on a 16-byte boundary and holds a multiple
+// of four slots, so the copy rounded up to whole 16-byte units stays inside it.
+__device__ __forceinline__ void scatter_issue(const DevPtrs& d, const long long* pre, const SortConst* sc,
+                                              long long chunk, Real* stage, uint64_t* bar) {
+  const int pop = find_pop(pre, d.n_pop, chunk);
+  const SortConst& P = sc[pop];
+  const long long c0 = (chunk - pre[pop]) * kScatterChunk;
+  const long long n = min((long long)kScatterChunk, P.n - c0);
+  const unsigned bytes = (unsigned)(((n + 3) & ~3ll) * (long long)sizeof(Real));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(bar, 5u * bytes);
+  const Real* src[5] = {(const Real*)d.x1, (const Real*)d.x2, (const Real*)d.vR, (const Real*)d.vZ,
+                        (const Real*)d.vT};
+#pragma unroll
+  for (int a = 0; a < 5; ++a) bulk_g2s(stage + a * kScatterChunk, src[a] + P.base + c0, bytes, bar);
+}
+
+// The chunks blockIdx.x, blockIdx.x + gridDim.x, ... of every population:
+// each reserves its range of every row it holds (cell_off + an atomic on
+// cell_cnt, which the scan cleared) and writes its live particles there in
+// the second buffer.  Recently sorted particles put most chunks in one row:
+// its range is the chunk's live particles and their positions follow the
+// chunk order (ballots, then an exclusive prefix over the (item, warp)
+// blocks); a chunk over several rows counts and places per row in shared
+// memory.  A copy that never lands sets kErrTimeout, and the CTA leaves after
+// the copies still in flight.
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(DevPtrs d, int hist_rows) {
+  extern __shared__ __align__(128) unsigned char s_raw[];
+  Real* stages = (Real*)s_raw;
+  unsigned* cnt = (unsigned*)(s_raw + (size_t)kScatterStages * kScatterStageBytes);
+  unsigned* cur = cnt + hist_rows;  // the chunk's next position in each row
+  __shared__ long long pre[kMaxPop + 1];
+  __shared__ SortConst sc[kMaxPop];
+  __shared__ __align__(8) uint64_t bar[kScatterStages];
+  __shared__ int s_r0, s_r1;        // rows of the chunk: [s_r0, s_r1]
+  __shared__ unsigned s_base;       // first position of a one-row chunk
+  __shared__ unsigned s_wc[kScatterItems * kSortWarps];  // live particles per (item, warp), then their prefix
+  sort_consts(d, sc);
+  chunk_prefix(d, kScatterChunk, pre);  // (its barrier publishes sc too)
+  const long long nch = pre[d.n_pop];
+  for (int r = threadIdx.x; r < hist_rows; r += blockDim.x) cnt[r] = 0u;
+  if (threadIdx.x == 0) {
+    s_r0 = INT_MAX;
+    s_r1 = -1;
+    for (int q = 0; q < kScatterStages; ++q) mbar_init(&bar[q], 1);
+    for (int q = 0; q < kScatterStages; ++q) {
+      const long long c = blockIdx.x + (long long)q * gridDim.x;
+      if (c < nch) scatter_issue(d, pre, sc, c, stages + (size_t)q * 5 * kScatterChunk, &bar[q]);
+    }
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Real* dstp[5] = {(Real*)d.y1, (Real*)d.y2, (Real*)d.yR, (Real*)d.yZ, (Real*)d.yT};
+  long long local = 0;
+  for (long long chunk = blockIdx.x; chunk < nch; chunk += gridDim.x, ++local) {
+    const int q = (int)(local % kScatterStages);
+    Real* st = stages + (size_t)q * 5 * kScatterChunk;
+    const int pop = find_pop(pre, d.n_pop, chunk);
+    const SortConst& P = sc[pop];
+    const long long c0 = (chunk - pre[pop]) * kScatterChunk;
+    if (!mbar_wait(&bar[q], (unsigned)((local / kScatterStages) & 1), d.err)) {
+      // the later stages' copies in flight land before the CTA leaves
+      if (threadIdx.x == 0)
+        for (long long j = local + 1; j < local + kScatterStages && chunk + (j - local) * gridDim.x < nch; ++j)
+          for (long long k = 0; k < (1ll << 22); ++k) {
+            if (mbar_try_wait(&bar[j % kScatterStages], (unsigned)((j / kScatterStages) & 1))) break;
+            __nanosleep(64);
+          }
+      return;
+    }
+    // the chunk's rows and their range
+    int rows[kScatterItems];
+    int lo = INT_MAX, hi = -1;
+#pragma unroll
+    for (int it = 0; it < kScatterItems; ++it) {
+      const int j = it * kSortThreads + threadIdx.x;
+      rows[it] = c0 + j < P.n ? sort_row(st[j], P.ih1, P.nrows) : -1;
+      if (rows[it] >= 0) {
+        lo = min(lo, rows[it]);
+        hi = max(hi, rows[it]);
+      }
+    }
+    lo = __reduce_min_sync(kFull, lo);
+    hi = __reduce_max_sync(kFull, hi);
+    if (lane == 0 && hi >= 0) {
+      atomicMin(&s_r0, lo);
+      atomicMax(&s_r1, hi);
+    }
+    __syncthreads();
+    const int r1 = s_r1, r0 = r1 >= 0 ? s_r0 : 0;  // no live particle: the empty range [0, -1]
     const unsigned long long first = d.cell_off[P.cell_off];
-    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
-      unsigned c = cnt[r];
-      cur[r] = c ? (unsigned)(d.cell_off[P.cell_off + r] - first) + atomicAdd(d.cell_cnt + P.cell_off + r, c) : 0u;
-    }
-    __syncthreads();
-    // the states of half the thread's items in flight at once while the
-    // other half is placed
-    constexpr int kHalf = kSortItems / 2;
-    static_assert(kSortItems % 2 == 0, "two halves");
+    if (r0 == r1) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      Real v1[kHalf], v2[kHalf], vR[kHalf], vZ[kHalf], vT[kHalf];
+      for (int it = 0; it < kScatterItems; ++it) {
+        const unsigned m = __ballot_sync(kFull, rows[it] >= 0);
+        if (lane == 0) s_wc[it * kSortWarps + w] = __popc(m);
+      }
+      __syncthreads();
+      if (w == 0) {
+        constexpr int kPer = kScatterItems * kSortWarps / 32;
+        unsigned v[kPer], sum = 0;
 #pragma unroll
-      for (int u = 0; u < kHalf; ++u) {
-        const int it = h * kHalf + u;
-        const long long k = c0 + (long long)it * blockDim.x + threadIdx.x;
+        for (int k = 0; k < kPer; ++k) {
+          v[k] = s_wc[lane * kPer + k];
+          sum += v[k];
+        }
+        unsigned incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned t = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += t;
+        }
+        unsigned ex = incl - sum;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+          s_wc[lane * kPer + k] = ex;
+          ex += v[k];
+        }
+        if (lane == 31)
+          s_base = (unsigned)(d.cell_off[P.cell_off + r0] - first) + atomicAdd(d.cell_cnt + P.cell_off + r0, incl);
+      }
+      __syncthreads();
+      const unsigned base = s_base, below = (1u << lane) - 1u;
+#pragma unroll
+      for (int it = 0; it < kScatterItems; ++it) {
+        const unsigned m = __ballot_sync(kFull, rows[it] >= 0);
         if (rows[it] >= 0) {
-          const long long slot = P.base + k;
-          v1[u] = ((const Real*)d.x1)[slot];
-          v2[u] = ((const Real*)d.x2)[slot];
-          vR[u] = ((const Real*)d.vR)[slot];
-          vZ[u] = ((const Real*)d.vZ)[slot];
-          vT[u] = ((const Real*)d.vT)[slot];
-        }
-      }
+          const int j = it * kSortThreads + threadIdx.x;
+          const long long dst = P.base + (long long)(base + s_wc[it * kSortWarps + w] + __popc(m & below));
 #pragma unroll
-      for (int u = 0; u < kHalf; ++u) {
-        const int row = rows[h * kHalf + u];
-        const unsigned pos = warp_count(cur, row);
-        if (row >= 0) {
-          const long long dst = P.base + (long long)pos;
-          ((Real*)d.y1)[dst] = v1[u];
-          ((Real*)d.y2)[dst] = v2[u];
-          ((Real*)d.yR)[dst] = vR[u];
-          ((Real*)d.yZ)[dst] = vZ[u];
-          ((Real*)d.yT)[dst] = vT[u];
+          for (int a = 0; a < 5; ++a) dstp[a][dst] = st[a * kScatterChunk + j];
         }
       }
+    } else {
+#pragma unroll
+      for (int it = 0; it < kScatterItems; ++it) warp_count(cnt, rows[it]);
+      __syncthreads();
+      for (int r = r0 + threadIdx.x; r <= r1; r += blockDim.x) {
+        const unsigned c = cnt[r];
+        cur[r] = c ? (unsigned)(d.cell_off[P.cell_off + r] - first) + atomicAdd(d.cell_cnt + P.cell_off + r, c) : 0u;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int it = 0; it < kScatterItems; ++it) {
+        const unsigned pos = warp_count(cur, rows[it]);
+        if (rows[it] >= 0) {
+          const int j = it * kSortThreads + threadIdx.x;
+          const long long dst = P.base + (long long)pos;
+#pragma unroll
+          for (int a = 0; a < 5; ++a) dstp[a][dst] = st[a * kScatterChunk + j];
+        }
+      }
+      for (int r = r0 + threadIdx.x; r <= r1; r += blockDim.x) cnt[r] = 0u;
     }
-    __syncthreads();
+    __syncthreads();  // the stage and the counters are free
+    if (threadIdx.x == 0) {
+      s_r0 = INT_MAX;
+      s_r1 = -1;
+      const long long nx = chunk + (long long)kScatterStages * gridDim.x;
+      if (nx < nch) scatter_issue(d, pre, sc, nx, st, &bar[q]);
+    }
   }
 }
 
@@ -1588,18 +1774,42 @@ void launch_inject<Real>(const DevPtrs& d, long long max_inj, cudaStream_t s) {
   k_inject<<<g, 256, 0, s>>>(d);
 }
 
+// Resident CTAs per SM of the two sort passes for grids of up to `rows` cell
+// rows (their dynamic shared memory grows with the rows), from the occupancy
+// calculator, cached per row count.
+static int s_sort_ctas[2][4097] = {};
+
+static int count_smem(int hist_rows) { return hist_rows * (int)sizeof(unsigned); }
+
 template <>
-void launch_sort<Real>(const DevPtrs& d, int grid, cudaStream_t s) {
-  const int sm = 2 * 4097 * (int)sizeof(unsigned);
-  cudaFuncSetAttribute(k_sort_count, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+void sort_setup<Real>(int max_rows) {
+  max_rows = std::max(1, std::min(4096, max_rows));
+  if (s_sort_ctas[0][max_rows] > 0) return;
+  const void* kern[2] = {(const void*)k_sort_count, (const void*)k_sort_scatter};
+  const int smem[2] = {count_smem(max_rows), scatter_smem(max_rows)};
+  const int most[2] = {8, 4};
+  for (int k = 0; k < 2; ++k) {
+    // the limit for the largest grid, so that every simulation's launches fit it
+    cudaFuncSetAttribute(kern[k], cudaFuncAttributeMaxDynamicSharedMemorySize, k ? scatter_smem(4096) : count_smem(4096));
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern[k], kSortThreads, smem[k]) != cudaSuccess) per = 1;
+    s_sort_ctas[k][max_rows] = std::max(1, std::min(most[k], per));
+  }
+  cudaGetLastError();
+}
+
+template <>
+void launch_sort<Real>(const DevPtrs& d, int grid, int max_rows, cudaStream_t s) {
+  const int sms = std::max(1, grid / 4);  // the caller's grid is 4 CTAs per SM
+  max_rows = std::max(1, std::min(4096, max_rows));
+  sort_setup<Real>(max_rows);
   cudaMemsetAsync(d.cell_cnt, 0, sizeof(unsigned) * d.total_cells, s);
-  k_sort_count<<<grid, 256, sm, s>>>(d);
+  k_sort_count<<<sms * s_sort_ctas[0][max_rows], kSortThreads, count_smem(max_rows), s>>>(d, max_rows);
   int nb = (int)((d.total_cells + 1023) / 1024);
   k_scan_blocks<<<nb, 1024, 0, s>>>(d);
   k_scan_top<<<1, 1024, 0, s>>>(d, nb);
   k_scan_add<<<nb, 1024, 0, s>>>(d);
-  k_sort_scatter<<<grid, 256, sm, s>>>(d);
+  k_sort_scatter<<<sms * s_sort_ctas[1][max_rows], kSortThreads, scatter_smem(max_rows), s>>>(d, max_rows);
   k_sort_finish<<<(d.n_pop + 63) / 64, 64, 0, s>>>(d);
 }
 

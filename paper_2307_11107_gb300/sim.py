@@ -154,7 +154,8 @@ class Sim:
                     phase_ms=dict(zip(_abi.PHASES, [float(v) for v in st.phase_ms])),
                     solver=_abi.SOLVERS[int(st.solver)], sorts=int(st.sorts),
                     kernels_per_sort=int(st.kernels_per_sort), sort_interval=int(st.sort_interval),
-                    win_rows=int(st.win_rows), chunk_group=int(st.chunk_group), chunk_items=int(st.chunk_items))
+                    win_rows=int(st.win_rows), chunk_group=int(st.chunk_group), chunk_items=int(st.chunk_items),
+                    timed_sorts=int(st.timed_sorts), sort_ms=float(st.sort_ms))
 
     def tallies(self, instance=0, history=True):
         c = self.cfgs[instance]
@@ -233,6 +234,11 @@ class Sim:
         """apic_check_wait_limit: returns the status code (APIC_ERR_TIMEOUT,
         -6, is the expected one) without raising."""
         return int(self._lib.apic_check_wait_limit(self.h, int(limit_ns)))
+
+    def set_schedule(self, sort_interval=0, win_rows=0, chunk_group=0, chunk_items=0):
+        """Apply a schedule chosen earlier (apic_set_schedule); 0 keeps a setting."""
+        self._check(self._lib.apic_set_schedule(self.h, int(sort_interval), int(win_rows), int(chunk_group),
+                                                int(chunk_items)))
 
     def autotune(self, steps_per_trial=16):
         """Sort-interval autotuning (apic_autotune): returns the interval kept

@@ -36,7 +36,7 @@ def test_struct_layout_matches_header():
     int main(void) {
       printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(apic_config_t), sizeof(apic_tallies_t), sizeof(apic_species_t),
              offsetof(apic_config_t, seed), offsetof(apic_config_t, poisson_tol), offsetof(apic_tallies_t, step),
-             sizeof(apic_stats_t), offsetof(apic_stats_t, chunk_group));
+             sizeof(apic_stats_t), offsetof(apic_stats_t, sort_ms));
       return 0;
     }'''
     with tempfile.TemporaryDirectory() as td:
@@ -47,7 +47,7 @@ def test_struct_layout_matches_header():
         vals = list(map(int, subprocess.check_output([exe]).split()))
     exp = [ctypes.sizeof(_abi.Config), ctypes.sizeof(_abi.Tallies), ctypes.sizeof(_abi.Species),
            _abi.Config.seed.offset, _abi.Config.poisson_tol.offset, _abi.Tallies.step.offset,
-           ctypes.sizeof(_abi.Stats), _abi.Stats.chunk_group.offset]
+           ctypes.sizeof(_abi.Stats), _abi.Stats.sort_ms.offset]
     assert vals == exp
 
 
@@ -69,4 +69,5 @@ def test_null_arguments():
     assert L.apic_create(None, None, None, None) == -1
     assert L.apic_destroy(None) == 0
     assert L.apic_step(None, 1) == -1
+    assert L.apic_set_schedule(None, 0, 0, 0, 0) == -1
     assert L.apic_last_error(None) == b"null simulation"

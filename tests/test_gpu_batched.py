@@ -99,6 +99,44 @@ def test_batched_reduction_poisson_matches_banded_lu(direct, monkeypatch):
     s.close()
 
 
+def test_set_schedule_applies_and_leaves_results_unchanged():
+    """A schedule applied by apic_set_schedule is the one in use (the stats
+    report it, and timed steps time their sorts), out-of-range values are
+    refused, and the fixed-point deposits and tallies make the results
+    bit-identical to those of the default schedule."""
+    import paper_2307_11107_gb300 as apic
+    apic.build()
+    cfgs = _instances("fp32")
+    runs = []
+    for sched in (None, (2, 4, 2, 32)):
+        s = apic.Sim(cfgs)
+        for k, c in enumerate(cfgs):
+            for sp in range(len(c["species"])):
+                s.load_volume(sp, c["species"][sp]["n_init"], instance=k)
+        s.step(3)
+        if sched is not None:
+            for bad in ((-1, 0, 0, 0), (0, 1, 0, 0), (0, 17, 0, 0), (0, 0, 65, 0), (0, 0, 0, 24)):
+                with pytest.raises(RuntimeError):
+                    s.set_schedule(*bad)
+            s.set_schedule(*sched)
+            st = s.stats()
+            assert (st["sort_interval"], st["win_rows"], st["chunk_group"], st["chunk_items"]) == sched
+        s.step(4)
+        s.step_timed(4)
+        st = s.stats()
+        si = st["sort_interval"]
+        assert st["timed_sorts"] == sum(1 for k in range(7, 11) if k % si == 0)
+        assert (st["sort_ms"] > 0.0) == (st["timed_sorts"] > 0)
+        runs.append([s.tallies(k) for k in range(len(cfgs))] + [s.field("phi", instance=k) for k in range(len(cfgs))])
+        s.close()
+    a, b = runs
+    for k in range(len(cfgs)):
+        assert np.array_equal(a[k]["bins"], b[k]["bins"])
+        assert a[k]["counts"] == b[k]["counts"]
+        assert np.array_equal(a[k]["history"][:, [1, 2, 4, 5, 9]], b[k]["history"][:, [1, 2, 4, 5, 9]])
+        assert np.array_equal(a[len(cfgs) + k], b[len(cfgs) + k])
+
+
 def test_autotune_keeps_a_candidate_and_stepping_stays_valid():
     """The autotuner times every sort interval, keeps the fastest, tunes the
     push's tiles at it and leaves a simulation that steps on with consistent
