@@ -170,9 +170,17 @@ __device__ __forceinline__ void cell_add(const CellWin& W, int ci, int cj, unsig
                                          unsigned S) {
   const int rr = ci - W.row0;
   if (rr >= 0 && rr < W.rows) {
+    // the two 64-bit moments by 32-bit shared-memory atomics (64-bit ones
+    // measured about three times as costly): the halves of `a` never carry
+    // (sum q1 and sum q2 stay below 2^32 between flushes), the low half of `m`
+    // passes its carry to the high half
     unsigned long long* c = W.s + win_a(rr, cj, W.n2);
-    atomicAdd(c, a);
-    atomicAdd(c + win_m(W.plane), m);
+    unsigned* a32 = (unsigned*)c;
+    unsigned* m32 = (unsigned*)(c + win_m(W.plane));
+    atomicAdd(a32, (unsigned)a);
+    atomicAdd(a32 + 1, (unsigned)(a >> 32));
+    const unsigned lo = (unsigned)m, old = atomicAdd(m32, lo);
+    atomicAdd(m32 + 1, (unsigned)(m >> 32) + (old + lo < old ? 1u : 0u));
   } else {
     unsigned long long w[4];
     corner_weights(a, m, S, w);
