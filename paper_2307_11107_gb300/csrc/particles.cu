@@ -1386,17 +1386,19 @@ struct Vec16<double> {
 };
 using RealV = Vec16<Real>;
 
-// Count pass: every CTA takes a contiguous share of each population (whole
-// 16-byte vectors, kCountUnroll of them in flight per thread), counts runs of
-// equal rows in registers (recently sorted particles change row rarely), adds
-// a run to a shared-memory histogram when it ends, and adds the histogram's
-// rows [lo, hi] to cell_cnt once per population.
+// Count pass: every CTA takes a contiguous share of the populations' slots
+// laid end to end (whole 16-byte vectors, kCountUnroll of them in flight per
+// thread; a share spans one or a few populations), counts runs of equal rows
+// in registers (recently sorted particles change row rarely), adds a run to a
+// shared-memory histogram when it ends, and adds the histogram's rows
+// [lo, hi] to cell_cnt once per population of the share.
 constexpr int kCountUnroll = 4;
 
 __global__ void __launch_bounds__(kSortThreads) k_sort_count(DevPtrs d, int hist_rows) {
   extern __shared__ unsigned hist[];  // [hist_rows]
   __shared__ SortConst sc[kMaxPop];
   __shared__ int s_lo[2], s_hi[2];  // population p's row range in [p & 1] (reset for p + 2)
+  __shared__ long long gpre[kMaxPop + 1];  // vectors of the populations before p
   sort_consts(d, sc);
   for (int r = threadIdx.x; r < hist_rows; r += blockDim.x) hist[r] = 0u;
   if (threadIdx.x < 2) {
@@ -1404,12 +1406,24 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_count(DevPtrs d, int hist
     s_hi[threadIdx.x] = -1;
   }
   __syncthreads();
-  for (int pop = 0; pop < d.n_pop; ++pop) {
+  if (threadIdx.x == 0) {
+    long long a = 0;
+    for (int p = 0; p < d.n_pop; ++p) {
+      gpre[p] = a;
+      a += (sc[p].n + RealV::kN - 1) / RealV::kN;
+    }
+    gpre[d.n_pop] = a;
+  }
+  __syncthreads();
+  const long long total = gpre[d.n_pop];
+  const long long per = (total + gridDim.x - 1) / gridDim.x;
+  const long long G0 = (long long)blockIdx.x * per, G1 = min(total, G0 + per);
+  if (G0 >= G1) return;  // (uniform over the CTA)
+  const int p0 = find_pop(gpre, d.n_pop, G0), p1 = find_pop(gpre, d.n_pop, G1 - 1);
+  for (int pop = p0; pop <= p1; ++pop) {
     const SortConst P = sc[pop];
     const typename RealV::T* X = (const typename RealV::T*)((const Real*)d.x1 + P.base);
-    const long long groups = (P.n + RealV::kN - 1) / RealV::kN;
-    const long long per = (groups + gridDim.x - 1) / gridDim.x;
-    const long long g0 = (long long)blockIdx.x * per, g1 = min(groups, g0 + per);
+    const long long g0 = max(G0, gpre[pop]) - gpre[pop], g1 = min(G1, gpre[pop + 1]) - gpre[pop];
     int run = -1, len = 0, lo = INT_MAX, hi = -1;
     for (long long g = g0 + threadIdx.x; g < g1; g += (long long)kCountUnroll * kSortThreads) {
       typename RealV::T v[kCountUnroll];
