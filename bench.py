@@ -542,7 +542,7 @@ def main():
         sim2 = apic.Sim(cfg2)
         if tuned is not None:  # the schedule measured above, applied without measuring again
             sim2.set_schedule(tiles["sort_interval"], tiles["win_rows"], tiles["chunk_group"], tiles["chunk_items"])
-        ke = min(args.steps, 500)
+        ke = min(args.steps, 1000)  # the timed run's steps (the upload amortised over as many)
         h2d = sum(p.numel() * 8 for p in pinned)
         barrier()
         t0 = time.perf_counter()
