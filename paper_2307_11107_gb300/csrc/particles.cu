@@ -1251,10 +1251,11 @@ __global__ void __launch_bounds__(256) k_inject(DevPtrs d) {
 // ---------------------------------------------------------------------------
 // Counting sort of every population by grid row (the push's deposit window
 // covers whole rows), which also drops freed slots: count -> exclusive scan
-// over all (population, row) bins -> scatter into the second buffer.  Both
-// passes stream their chunks through shared memory with bulk asynchronous
-// copies issued several chunks ahead; a CTA histograms its chunk there and
-// touches the global counters once per row the chunk holds (recently sorted
+// over all (population, row) bins -> scatter into the second buffer.  The
+// count reads x1 alone as 16-byte vectors and counts runs of equal rows in
+// registers; the scatter streams its chunks' states through shared memory
+// with bulk asynchronous copies issued a chunk ahead.  Both touch the global
+// counters once per row a CTA's share or chunk holds (recently sorted
 // particles: one to three rows).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void chunk_prefix(const DevPtrs& d, long long CH, long long* pre) {
