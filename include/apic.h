@@ -218,6 +218,37 @@ int apic_step(apic_sim* sim, int32_t n_steps);
  * calls (sticky). */
 int apic_tallies(apic_sim* sim, int32_t instance, apic_tallies_t* out);
 
+/* ---- Checkpoint / resume (no counterpart in the paper) ----------------------
+ * A checkpoint holds what the next apic_step calls depend on, for every
+ * instance of the object: each population's live particle slots (the five
+ * state arrays of Sec. 2's macro-particles) and free-slot stack, its counts,
+ * Philox draws consumed and injection carry, the solver and step scalars
+ * (step index, grain charge and force), phi (the next solve's start), the
+ * deposit accumulators of the last step, the node gradients, the fixed-point
+ * tallies and the history ring, and the step counter and sort interval of the
+ * object.  Because every random draw is a counter-based Philox draw, steps
+ * after apic_checkpoint_load give the tallies, fields and particle set of the
+ * uninterrupted run bit for bit (particles may sit in other slots: the sort's
+ * placement within a row depends on scheduling).  A sensitivity window in
+ * progress is not part of a checkpoint.  The buffer is plain host memory in
+ * the layout of this library version (a header, then the arrays); its size
+ * depends on the particle counts at the time of the call.
+ *
+ * apic_checkpoint_size: *bytes = the size a checkpoint of the current state
+ *   takes.  Errors: INVALID_ARG (NULL), a sticky error.
+ * apic_checkpoint_save: waits for the work in flight and copies the state into
+ *   buf (host, bytes long).  Errors: INVALID_ARG (NULL, bytes too small), a
+ *   sticky error, CUDA.
+ * apic_checkpoint_load: replaces this object's state with the checkpoint in
+ *   buf, made by an object created with the same configurations (the same
+ *   instances, grids, species capacities and history sizes).  Errors:
+ *   INVALID_ARG (NULL, a buffer that is not a checkpoint of this layout, or
+ *   of an object with other sizes, counts above a capacity), a sticky error,
+ *   CUDA.  A refused checkpoint leaves the object unchanged. */
+int apic_checkpoint_size(apic_sim* sim, int64_t* bytes);
+int apic_checkpoint_save(apic_sim* sim, void* buf, int64_t bytes);
+int apic_checkpoint_load(apic_sim* sim, const void* buf, int64_t bytes);
+
 /* Solve Eqs. 6-7 for `instance` with the GPU solver.  rho: host [n1+1][n2+1]
  * charge density, or NULL for the density of the current particles.
  * phi_out: host [n1+1][n2+1].  The simulation's own potential is unchanged. */

@@ -23,7 +23,7 @@ SYMBOLS = ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "a
            "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_last_error",
            "apic_num_instances", "apic_stats", "apic_step_timed", "apic_deposit_static", "apic_sensitivity",
            "apic_adjoint", "apic_adjoint_window", "apic_autotune", "apic_probe_fp32_fma", "apic_check_wait_limit",
-           "apic_set_schedule")
+           "apic_set_schedule", "apic_checkpoint_size", "apic_checkpoint_save", "apic_checkpoint_load")
 TUNE_INTERVALS = (2, 4, 6, 8, 12, 16, 24)
 NPAR, NOUT = 3, 5
 PARAMS = ("alpha", "phi_g", "B")
@@ -114,10 +114,14 @@ def load():
     L.apic_probe_fp32_fma.argtypes = [vp, i32, dp]
     L.apic_check_wait_limit.argtypes = [vp, i64]
     L.apic_set_schedule.argtypes = [vp, i32, i32, i32, i32]
+    L.apic_checkpoint_size.argtypes = [vp, C.POINTER(i64)]
+    L.apic_checkpoint_save.argtypes = [vp, vp, i64]
+    L.apic_checkpoint_load.argtypes = [vp, vp, i64]
     for name in ("apic_create", "apic_create_batch", "apic_destroy", "apic_inject", "apic_step", "apic_tallies",
                  "apic_solve_poisson", "apic_get_particles", "apic_get_field", "apic_stats", "apic_step_timed",
                  "apic_deposit_static", "apic_sensitivity", "apic_adjoint", "apic_autotune", "apic_probe_fp32_fma",
-                 "apic_check_wait_limit", "apic_adjoint_window", "apic_set_schedule"):
+                 "apic_check_wait_limit", "apic_adjoint_window", "apic_set_schedule",
+                 "apic_checkpoint_size", "apic_checkpoint_save", "apic_checkpoint_load"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -2189,6 +2189,174 @@ extern "C" int apic_tallies(apic_sim* S, int32_t instance, apic_tallies_t* out) 
   return APIC_OK;
 }
 
+// ---- Checkpoint / resume --------------------------------------------------
+// The state the next steps depend on: every population's live slots [0, n)
+// of the five state arrays (the current particle buffer) and its free-slot
+// stack, the population, solver and step scalars (counts, Philox draws
+// consumed, injection carries, step index, grain charge), the node arrays
+// carried from step to step (phi as the next solve's start, phi_prev, rho,
+// the deposit accumulators of the last push and injection, the gradients and
+// their pair table, the surface field), the fixed-point tallies and the
+// history ring, and the host's step counter and sort interval.  Draws are
+// counter-based (Philox on the population's draw count), so a resumed run
+// draws what the uninterrupted one draws.
+namespace {
+constexpr unsigned long long kCkptMagic = 0x31504b4343495041ull;  // "APICCKP1"
+struct CkptHeader {
+  unsigned long long magic;
+  int32_t version, precision, n_inst, n_pop;
+  int64_t total_nodes, bins, hist, en, bytes;
+  int64_t host_step, sorts, loop_iters;
+  int32_t sort_interval, dirty;
+};
+
+struct CkptSizes {
+  int64_t bins = 0, hist = 0, en = 0;
+};
+
+CkptSizes ckpt_sizes(const apic_sim* S) {
+  CkptSizes z;
+  for (const Inst& I : S->inst) {
+    z.bins += (int64_t)I.n_species * ((int64_t)I.n2 * kTallyBinWords + kTallyStepWords);
+    z.hist += (int64_t)I.hist_cap * kNH;
+    z.en += I.N2;
+  }
+  return z;
+}
+
+// Bytes of a checkpoint whose populations hold ps[p].n slots and ps[p].n_holes free slots.
+int64_t ckpt_bytes(const apic_sim* S, const PopState* ps) {
+  const CkptSizes z = ckpt_sizes(S);
+  const int64_t R = S->precision == APIC_FP64 ? 8 : 4, nodes = S->d.total_nodes;
+  int64_t b = sizeof(CkptHeader) + (int64_t)sizeof(PopState) * S->n_pop +
+              (int64_t)(sizeof(SolverState) + sizeof(StepState)) * S->n_inst;
+  for (int p = 0; p < S->n_pop; ++p) b += ps[p].n * 5 * R + ps[p].n_holes * 4;
+  b += 3 * 8 * nodes + 2 * 8 * nodes + 2 * R * nodes + (S->d.H ? 16 * nodes : 0);
+  b += 8 * (z.bins + z.hist + z.en);
+  return b;
+}
+
+// The node-sized and table arrays in checkpoint order: device pointer, bytes.
+std::vector<std::pair<void*, int64_t>> ckpt_arrays(const apic_sim* S) {
+  const CkptSizes z = ckpt_sizes(S);
+  const DevPtrs& d = S->d;
+  const int64_t R = S->precision == APIC_FP64 ? 8 : 4, nodes = d.total_nodes;
+  std::vector<std::pair<void*, int64_t>> a = {
+      {d.rho, 8 * nodes}, {d.phi, 8 * nodes}, {d.phi_prev, 8 * nodes}, {d.acc, 16 * nodes}, {d.G, 2 * R * nodes}};
+  if (d.H) a.push_back({d.H, 16 * nodes});
+  a.push_back({d.tfix, 8 * z.bins});
+  a.push_back({d.hist, 8 * z.hist});
+  a.push_back({d.en, 8 * z.en});
+  return a;
+}
+}  // namespace
+
+extern "C" int apic_checkpoint_size(apic_sim* S, int64_t* bytes) {
+  if (!S || !bytes) return APIC_ERR_INVALID_ARG;
+  if (S->status != APIC_OK) return S->status;
+  std::vector<PopState> ps(S->n_pop);
+  if (!S->d2h(ps.data(), S->d.ps, ps.size()) || !S->sync()) return S->status;
+  *bytes = ckpt_bytes(S, ps.data());
+  return APIC_OK;
+}
+
+extern "C" int apic_checkpoint_save(apic_sim* S, void* buf, int64_t bytes) {
+  if (!S || !buf) return APIC_ERR_INVALID_ARG;
+  if (S->status != APIC_OK) return S->status;
+  std::vector<PopState> ps(S->n_pop);
+  if (!S->d2h(ps.data(), S->d.ps, ps.size()) || !S->sync()) return S->status;
+  const int64_t need = ckpt_bytes(S, ps.data());
+  if (bytes < need) return APIC_ERR_INVALID_ARG;
+  const CkptSizes z = ckpt_sizes(S);
+  long long loops = 0;
+  if (!S->d2h(&loops, S->d.cnt, 1) || !S->sync()) return S->status;
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = kCkptMagic;
+  h.version = 1;
+  h.precision = S->precision;
+  h.n_inst = S->n_inst;
+  h.n_pop = S->n_pop;
+  h.total_nodes = S->d.total_nodes;
+  h.bins = z.bins;
+  h.hist = z.hist;
+  h.en = z.en;
+  h.bytes = need;
+  h.host_step = S->host_step;
+  h.sorts = S->sorts;
+  h.loop_iters = loops;
+  h.sort_interval = S->sort_interval;
+  h.dirty = S->dirty ? 1 : 0;
+  unsigned char* o = (unsigned char*)buf;
+  std::memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  std::memcpy(o, ps.data(), sizeof(PopState) * ps.size());
+  o += sizeof(PopState) * ps.size();
+  auto get = [&](const void* src, int64_t n) {
+    if (n > 0) S->ck(cudaMemcpyAsync(o, src, (size_t)n, cudaMemcpyDeviceToHost, S->stream), "checkpoint D2H");
+    o += n;
+  };
+  get(S->d.sol, (int64_t)sizeof(SolverState) * S->n_inst);
+  get(S->d.stp, (int64_t)sizeof(StepState) * S->n_inst);
+  const DevPtrs v = S->view(S->par);
+  const int64_t R = S->precision == APIC_FP64 ? 8 : 4;
+  void* arr[5] = {v.x1, v.x2, v.vR, v.vZ, v.vT};
+  for (int p = 0; p < S->n_pop; ++p) {
+    const Pop& P = S->pop[p];
+    for (void* a : arr) get((const unsigned char*)a + P.base * R, ps[p].n * R);
+    get(S->d.holes + P.base, ps[p].n_holes * 4);
+  }
+  for (const auto& a : ckpt_arrays(S)) get(a.first, a.second);
+  if (!S->sync()) return S->status;
+  return (int64_t)(o - (unsigned char*)buf) == need ? APIC_OK : S->fail(APIC_ERR_INVALID_ARG, "checkpoint layout");
+}
+
+extern "C" int apic_checkpoint_load(apic_sim* S, const void* buf, int64_t bytes) {
+  if (!S || !buf || bytes < (int64_t)sizeof(CkptHeader)) return APIC_ERR_INVALID_ARG;
+  if (S->status != APIC_OK) return S->status;
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  const CkptSizes z = ckpt_sizes(S);
+  if (h.magic != kCkptMagic || h.version != 1 || h.precision != S->precision || h.n_inst != S->n_inst ||
+      h.n_pop != S->n_pop || h.total_nodes != S->d.total_nodes || h.bins != z.bins || h.hist != z.hist ||
+      h.en != z.en || h.bytes > bytes || (h.sort_interval > 0) != (S->sort_interval > 0))
+    return APIC_ERR_INVALID_ARG;
+  const unsigned char* o = (const unsigned char*)buf + sizeof(h);
+  std::vector<PopState> ps(S->n_pop);
+  if ((int64_t)(sizeof(h) + sizeof(PopState) * ps.size()) > bytes) return APIC_ERR_INVALID_ARG;
+  std::memcpy(ps.data(), o, sizeof(PopState) * ps.size());
+  o += sizeof(PopState) * ps.size();
+  for (int p = 0; p < S->n_pop; ++p)
+    if (ps[p].n < 0 || ps[p].n > S->pop[p].cap || ps[p].n_holes < 0 || ps[p].n_holes > ps[p].n)
+      return APIC_ERR_INVALID_ARG;
+  if (ckpt_bytes(S, ps.data()) != h.bytes) return APIC_ERR_INVALID_ARG;
+  if (!S->sync()) return S->status;  // nothing of this simulation in flight
+  auto put = [&](void* dst, int64_t n) {
+    if (n > 0) S->ck(cudaMemcpyAsync(dst, o, (size_t)n, cudaMemcpyHostToDevice, S->stream), "checkpoint H2D");
+    o += n;
+  };
+  S->h2d(S->d.ps, ps.data(), ps.size());  // (the populations' scalars, read above)
+  put(S->d.sol, (int64_t)sizeof(SolverState) * S->n_inst);
+  put(S->d.stp, (int64_t)sizeof(StepState) * S->n_inst);
+  const DevPtrs v = S->view(S->par);
+  const int64_t R = S->precision == APIC_FP64 ? 8 : 4;
+  void* arr[5] = {v.x1, v.x2, v.vR, v.vZ, v.vT};
+  for (int p = 0; p < S->n_pop; ++p) {
+    const Pop& P = S->pop[p];
+    for (void* a : arr) put((unsigned char*)a + P.base * R, ps[p].n * R);
+    put(S->d.holes + P.base, ps[p].n_holes * 4);
+  }
+  for (const auto& a : ckpt_arrays(S)) put(a.first, a.second);
+  const long long loops = h.loop_iters;
+  S->h2d(S->d.cnt, &loops, 1);
+  if (!S->sync()) return S->status;  // (the host copies are pageable: complete before returning)
+  S->host_step = h.host_step;
+  S->sorts = h.sorts;
+  if (h.sort_interval > 0) S->sort_interval = h.sort_interval;
+  S->dirty = h.dirty != 0;
+  return APIC_OK;
+}
+
 // Solve of instance inst for the right-hand side in d.b (with its |b|^2
 // partials), from the guess in d.phi; the other instances keep their phi.
 template <class Real>

@@ -235,6 +235,21 @@ class Sim:
         -6, is the expected one) without raising."""
         return int(self._lib.apic_check_wait_limit(self.h, int(limit_ns)))
 
+    def checkpoint(self):
+        """The state the next steps depend on, as a host byte array
+        (apic_checkpoint_size / apic_checkpoint_save)."""
+        n = C.c_int64()
+        self._check(self._lib.apic_checkpoint_size(self.h, C.byref(n)))
+        buf = np.zeros(int(n.value), dtype=np.uint8)
+        self._check(self._lib.apic_checkpoint_save(self.h, buf.ctypes.data_as(C.c_void_p), int(n.value)))
+        return buf
+
+    def restore(self, buf):
+        """Replace the state with a checkpoint of an object created with the
+        same configurations (apic_checkpoint_load)."""
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(self._lib.apic_checkpoint_load(self.h, b.ctypes.data_as(C.c_void_p), int(b.size)))
+
     def set_schedule(self, sort_interval=0, win_rows=0, chunk_group=0, chunk_items=0):
         """Apply a schedule chosen earlier (apic_set_schedule); 0 keeps a setting."""
         self._check(self._lib.apic_set_schedule(self.h, int(sort_interval), int(win_rows), int(chunk_group),

@@ -70,4 +70,7 @@ def test_null_arguments():
     assert L.apic_destroy(None) == 0
     assert L.apic_step(None, 1) == -1
     assert L.apic_set_schedule(None, 0, 0, 0, 0) == -1
+    assert L.apic_checkpoint_size(None, None) == -1
+    assert L.apic_checkpoint_save(None, None, 0) == -1
+    assert L.apic_checkpoint_load(None, None, 0) == -1
     assert L.apic_last_error(None) == b"null simulation"
